@@ -1,0 +1,157 @@
+/*
+ * rte.h -- C ABI of the GB300 (sm_103a) implementation of the homogeneous-
+ * medium fast method of Fan, An & Ying, "Fast algorithms for integral
+ * formulations of steady-state radiative transfer equation" (arXiv 1802.03061).
+ *
+ * The library applies the Nystrom-discretised Fredholm operators of the
+ * paper with FFTs on the zero-padded (circulant-embedded) grid and solves the
+ * second-kind equation with a device GMRES.
+ *
+ *   2D, angular Fourier modes |k| <= L (Sec. 3.1.1, Eq. ani_2d_Fredholm;
+ *   discretisation Sec. 3.3, Eq. ani_discretization / ani_AU):
+ *       u = K u + b,     b = K~ g,  g = f delta_{k,0}
+ *       (K u)_{i,k} = mu_s sum_j sum_{k'=-L..L} K~_{(i,k),(j,k')} sigma_hat_{|k'|} u_{j,k'}
+ *       K~_{(i,k),(j,k')} = h^2 kappa(x_i - x_j) exp(i (k'-k) theta(x_i - x_j)),  i != j
+ *       kappa(r) = exp(-mu_t |r|) / (2 pi |r|)                      (Sec. 2.3.1)
+ *       K~_{(i,k),(i,k')} = integral over cell i of the same kernel  (Sec. 2.3)
+ *   3D isotropic (Sec. 2.1, Eq. iso_Fredholm; Sec. 2.3.1 with d = 3):
+ *       kappa(r) = exp(-mu_t |r|) / (4 pi |r|^2), h^3 cell volume.
+ *
+ * Grid: n cells per side on [0,1]^d (h = 1/n is usual but any h > 0 is
+ * accepted), cell centres x_i = ((i1+1/2)h, (i2+1/2)h[, (i3+1/2)h]).
+ *
+ * Field layouts (all arrays are dense, C order, x index fastest):
+ *   2D: "mode field"  double2 (or float2) [L+1][n][n]: modes k = 0..L,
+ *       interleaved (re, im).  Modes k < 0 are implied by u_{-k} = conj(u_k),
+ *       which holds for every field the solver produces (real f, real even
+ *       sigma_hat).  The imaginary part of mode 0 must be zero.
+ *   3D: double (or float) [n][n][n] real mean density.
+ *   Source f: double [n][n] (2D) or [n][n][n] (3D).
+ *
+ * Ownership: the plan owns every device buffer it allocates (kernel spectra,
+ * FFT intermediates, Krylov workspace), freed by rte_destroy.  The caller
+ * owns x, y, f, u and the stream.  Pointers named *_dev are device pointers;
+ * *_host are host pointers.  Calls are stream-ordered on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  A plan is not thread-safe.
+ *
+ * Errors: every call returns an rte_status; nothing else crosses the ABI.
+ * RTE_EINVAL for bad arguments (null pointers, n < 1, h <= 0, mu_t < 0,
+ * mu_s < 0, mu_s > mu_t (assumption (C2), Sec. 2.2), L < 0 or L > 8,
+ * |sigma_hat_0 - 1| > 1e-12 (the scattering kernel averages to one, Sec. 1),
+ * |sigma_hat_k| > 1 (needed by the contraction argument, Sec. 3.2)),
+ * RTE_EUNSUPPORTED for 3D with L > 0, RTE_ENOMEM when a device allocation
+ * fails, RTE_ECUDA for any other CUDA error, RTE_ENOCONV when the solve
+ * stops at maxit (u then holds the best iterate), RTE_ENAN when the source
+ * or the residual is not finite.
+ */
+#ifndef RTE_H
+#define RTE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int dim;   /* 2 or 3 */
+    int n[3];  /* cells per side; only n[0] is used (square/cubic grids) */
+} rte_grid;
+
+typedef enum {
+    RTE_OK = 0,
+    RTE_EINVAL = 1,
+    RTE_EUNSUPPORTED = 2,
+    RTE_ENOMEM = 3,
+    RTE_ECUDA = 4,
+    RTE_ENOCONV = 5,
+    RTE_ETIMEOUT = 6,
+    RTE_ENAN = 7
+} rte_status;
+
+typedef enum {
+    RTE_PREC_FP64 = 0,          /* FP64 FFTs, FP64 spectra, FP64 GMRES               */
+    RTE_PREC_MIXED_FP32 = 1,    /* FP32 inner GMRES / FFTs / spectra + FP64 refinement */
+    RTE_PREC_MIXED_BF16SPEC = 2 /* as above with the inner spectra stored in BF16      */
+} rte_prec;
+
+/* Solver options.  A zero-initialised struct selects the defaults given in
+ * brackets.  tol is the relative residual ||b - (I-K)u|| / ||b|| in the
+ * 2-norm over all modes -L..L, measured with the FP64 operator (the paper
+ * leaves the stopping rule to GMRES/MINRES, Sec. 2.4). */
+typedef struct {
+    rte_prec prec;     /* [RTE_PREC_FP64] */
+    double tol;        /* [1e-8] */
+    int restart;       /* [40] GMRES restart length, 1..128 */
+    int maxit;         /* [2000] total inner iterations */
+    double inner_tol;  /* [1e-4] relative tolerance of each inner (FP32) solve */
+    int use_guess;     /* [0] 1: u_dev holds an initial guess on entry */
+    int q_policy;      /* [0] 0: smallest even 2^a 3^b >= 2n-1; else Q itself */
+} rte_opts;
+
+typedef struct {
+    int iters;            /* GMRES iterations (inner ones for the mixed modes) */
+    int outer;            /* FP64 refinement steps (mixed modes), 0 for FP64  */
+    int converged;        /* 1 if relres_true <= tol                            */
+    double relres_true;   /* FP64 ||b - (I-K)u|| / ||b|| at exit                */
+    double ms_total;      /* wall time of the call (events on the stream)      */
+    double ms_pre;        /* plan creation time of this plan                   */
+    double est_err_bound; /* cond_est * relres_true, cond_est = (1+r)/(1-r), r = mu_s/mu_t */
+} rte_stats;
+
+typedef struct rte_plan_s* rte_plan;
+
+/* Create a plan: computes the singular-cell weights (Sec. 2.3), samples the
+ * kernels on the periodic zero-padded grid and stores their spectra
+ * (Sec. 2.3.1 "calculate the Fourier modes of kappa"; Sec. 3.3.1 for the
+ * mode-coupled kernels), all on the device.  sigma_hat: host array of L+1
+ * coefficients sigma_hat_0..L (sigma_hat_0 == 1).  opts may be NULL.
+ * The work is enqueued on cuda_stream and synchronised before return. */
+rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, double mu_t, double mu_s, int L,
+                           const double* sigma_hat, const rte_opts* opts, void* cuda_stream);
+
+/* y = K x (T.2's operator, Sec. 3.3).  x_dev, y_dev: FP64 fields in the
+ * layout above (2D double2 [L+1][n][n], 3D double [n]^3); may not alias. */
+rte_status rte_apply_K(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
+
+/* y = x - K x, the matrix A = I - K of Eq. ani_AU. */
+rte_status rte_apply_A(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
+
+/* FP32 versions used by the inner solves of the mixed modes: x_dev, y_dev are
+ * float2 [L+1][n][n] (2D) or float [n]^3 (3D); the spectra are FP32 or BF16
+ * as the plan's prec selects (FP32 for an FP64 plan). */
+rte_status rte_apply_K32(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
+
+/* b = K~ g (step T.1 / S.1): f_dev double [n]^d real source, b_dev an FP64
+ * field (all modes 0..L in 2D). */
+rte_status rte_rhs(rte_plan plan, const double* f_dev, void* b_dev, void* cuda_stream);
+
+/* Solve (I - K) u = K~ g (step T.2) for u.  f_dev: source; u_dev: FP64
+ * field, read as the initial guess when opts->use_guess, else zeroed.
+ * opts NULL = the plan's options.  stats may be NULL.  Synchronises the
+ * stream once at exit to fill stats. */
+rte_status rte_solve(rte_plan plan, const double* f_dev, void* u_dev, const rte_opts* opts,
+                     rte_stats* stats, void* cuda_stream);
+
+/* Same as rte_solve with host buffers: copies f_host to the device, solves,
+ * copies u back to u_host (FP64 field layout above, host memory). */
+rte_status rte_solve_host(rte_plan plan, const double* f_host, void* u_host, const rte_opts* opts,
+                          rte_stats* stats, void* cuda_stream);
+
+/* Sizes of this plan: n, Q, L, reals per field vector. Any pointer may be NULL. */
+rte_status rte_plan_info(rte_plan plan, int* n, int* Q, int* L, long* nreal);
+
+/* Cell weights the plan computed: D_m for m = 0..2L (2D) or D (3D) into
+ * host array out (2L+1 doubles, or 1). */
+rte_status rte_plan_cell_weights(rte_plan plan, double* out_host);
+
+/* Free all device memory of the plan.  NULL is accepted. */
+rte_status rte_destroy(rte_plan plan);
+
+const char* rte_status_str(rte_status s);
+
+/* Last CUDA error text seen by the library (for diagnostics). */
+const char* rte_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_H */

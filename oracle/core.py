@@ -313,7 +313,8 @@ def sampled_residual_2d(n, h, mu_t, mu_s, sigma_hat, f, u, rows):
     L = (u.shape[0] - 1) // 2
     D = cell_weights_2d(mu_t, h, 2 * L)
     Ku = apply_K_2d(n, h, mu_t, mu_s, sigma_hat, u, rows=rows, D=D)
-    b = rhs_2d(n, h, mu_t, L, f, rows=rows, D=D)
+    # the right-hand side couples only the source mode k' = 0: m = -L..L
+    b = rhs_2d(n, h, mu_t, L, f, rows=rows, D=D[L:3 * L + 1])
     ur = u.reshape(u.shape[0], -1)[:, rows]
     return b - ur + Ku, b
 

@@ -1,0 +1,164 @@
+"""ctypes binding of the C ABI in include/rte.h (argument marshalling only).
+
+Every function keeps the C name.  Device pointers are passed as integers
+(e.g. ``tensor.data_ptr()``), streams as ``torch.cuda.Stream.cuda_stream``
+integers.  A non-OK status raises :class:`RteError`, except RTE_ENOCONV from
+the solvers, which is reported in the returned stats.
+
+The library must have been built (``paper_1802_03061_gb300.build.build()``);
+there is no fallback of any kind when it is missing.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librte.so")
+
+RTE_OK, RTE_EINVAL, RTE_EUNSUPPORTED, RTE_ENOMEM, RTE_ECUDA, RTE_ENOCONV, RTE_ETIMEOUT, RTE_ENAN = range(8)
+PREC = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
+
+
+class RteError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s: %s%s" % (where, _status_str(status), (" (%s)" % detail) if detail else ""))
+
+
+class rte_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3)]
+
+
+class rte_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_guess", ctypes.c_int),
+                ("q_policy", ctypes.c_int)]
+
+
+class rte_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_pre", ctypes.c_double),
+                ("est_err_bound", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+VP = ctypes.c_void_p
+
+
+def lib():
+    """Load librte.so; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librte.so is not built (%s); run paper_1802_03061_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.rte_plan_create.argtypes = [ctypes.POINTER(VP), rte_grid, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(rte_opts), VP]
+        for name in ("rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_rhs"):
+            getattr(L, name).argtypes = [VP, VP, VP, VP]
+        L.rte_solve.argtypes = [VP, VP, VP, ctypes.POINTER(rte_opts), ctypes.POINTER(rte_stats), VP]
+        L.rte_solve_host.argtypes = [VP, VP, VP, ctypes.POINTER(rte_opts), ctypes.POINTER(rte_stats), VP]
+        L.rte_plan_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]
+        L.rte_plan_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
+        L.rte_destroy.argtypes = [VP]
+        L.rte_status_str.argtypes = [ctypes.c_int]
+        L.rte_status_str.restype = ctypes.c_char_p
+        L.rte_last_error.restype = ctypes.c_char_p
+        for name in ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_rhs", "rte_solve",
+                     "rte_solve_host", "rte_plan_info", "rte_plan_cell_weights", "rte_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _status_str(s):
+    try:
+        return lib().rte_status_str(int(s)).decode()
+    except Exception:
+        return "status %d" % s
+
+
+def _check(st, where, allow=()):
+    if st != RTE_OK and st not in allow:
+        raise RteError(st, where, lib().rte_last_error().decode())
+    return st
+
+
+def make_opts(prec="fp64", tol=1e-8, restart=40, maxit=2000, inner_tol=1e-4, use_guess=0, q_policy=0):
+    return rte_opts(PREC[prec] if isinstance(prec, str) else int(prec), tol, restart, maxit, inner_tol,
+                    int(use_guess), int(q_policy))
+
+
+def rte_plan_create(dim, n, h, mu_t, mu_s, L, sigma_hat, opts=None, stream=0):
+    g = rte_grid(dim, (ctypes.c_int * 3)(n, n, n))
+    sig = (ctypes.c_double * (L + 1))(*[float(v) for v in sigma_hat[:L + 1]])
+    out = VP()
+    st = lib().rte_plan_create(ctypes.byref(out), g, h, mu_t, mu_s, L, sig,
+                               ctypes.byref(opts) if opts is not None else None, VP(stream))
+    _check(st, "rte_plan_create")
+    return out
+
+
+def rte_apply_K(plan, x, y, stream=0):
+    _check(lib().rte_apply_K(plan, VP(x), VP(y), VP(stream)), "rte_apply_K")
+
+
+def rte_apply_A(plan, x, y, stream=0):
+    _check(lib().rte_apply_A(plan, VP(x), VP(y), VP(stream)), "rte_apply_A")
+
+
+def rte_apply_K32(plan, x, y, stream=0):
+    _check(lib().rte_apply_K32(plan, VP(x), VP(y), VP(stream)), "rte_apply_K32")
+
+
+def rte_rhs(plan, f, b, stream=0):
+    _check(lib().rte_rhs(plan, VP(f), VP(b), VP(stream)), "rte_rhs")
+
+
+def rte_solve(plan, f, u, opts=None, stream=0):
+    stats = rte_stats()
+    st = lib().rte_solve(plan, VP(f), VP(u), ctypes.byref(opts) if opts is not None else None,
+                         ctypes.byref(stats), VP(stream))
+    _check(st, "rte_solve", allow=(RTE_ENOCONV,))
+    d = stats.as_dict()
+    d["status"] = st
+    return d
+
+
+def rte_solve_host(plan, f_host, u_host, opts=None, stream=0):
+    stats = rte_stats()
+    st = lib().rte_solve_host(plan, VP(f_host), VP(u_host), ctypes.byref(opts) if opts is not None else None,
+                              ctypes.byref(stats), VP(stream))
+    _check(st, "rte_solve_host", allow=(RTE_ENOCONV,))
+    d = stats.as_dict()
+    d["status"] = st
+    return d
+
+
+def rte_plan_info(plan):
+    n, Q, L, nr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_long()
+    _check(lib().rte_plan_info(plan, ctypes.byref(n), ctypes.byref(Q), ctypes.byref(L), ctypes.byref(nr)),
+           "rte_plan_info")
+    return dict(n=n.value, Q=Q.value, L=L.value, nreal=nr.value)
+
+
+def rte_plan_cell_weights(plan, count):
+    out = (ctypes.c_double * count)()
+    _check(lib().rte_plan_cell_weights(plan, out), "rte_plan_cell_weights")
+    return list(out)
+
+
+def rte_destroy(plan):
+    _check(lib().rte_destroy(plan), "rte_destroy")
+
+
+def rte_status_str(s):
+    return _status_str(s)
+
+
+def rte_last_error():
+    return lib().rte_last_error().decode()

@@ -1,0 +1,71 @@
+// Shared device/host utilities of the RTE operator library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define RTE_MAX_L 8                      // largest angular truncation |k| <= L
+#define RTE_MAX_CH (2 * RTE_MAX_L + 1)   // real channels of a J-symmetric field
+#define RTE_MAX_STAGES 16
+
+// ----------------------------------------------------------------------------
+// complex helpers, templated on the real type (float or double)
+// ----------------------------------------------------------------------------
+template <typename R> struct cplx_of;
+template <> struct cplx_of<float> { using T = float2; };
+template <> struct cplx_of<double> { using T = double2; };
+
+template <typename T> struct real_of;
+template <> struct real_of<float2> { using R = float; };
+template <> struct real_of<double2> { using R = double; };
+
+template <typename T> __host__ __device__ __forceinline__ T mk(typename real_of<T>::R x, typename real_of<T>::R y) {
+    T r; r.x = x; r.y = y; return r;
+}
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ T cconj(T a) { return mk<T>(a.x, -a.y); }
+// multiply by DIR * i (DIR = +1 or -1)
+template <int DIR, typename T> __device__ __forceinline__ T cmul_i(T a) {
+    return DIR > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+template <typename T> __device__ __forceinline__ T cscale(T a, typename real_of<T>::R s) {
+    return mk<T>(a.x * s, a.y * s);
+}
+
+// storage conversions for kernel spectra (double2 / float2 / bf16x2)
+__device__ __forceinline__ double2 ld_spec(const double2* p, long i, double2) { return p[i]; }
+__device__ __forceinline__ float2 ld_spec(const double2* p, long i, float2) {
+    double2 v = p[i]; return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ float2 ld_spec(const float2* p, long i, float2) { return p[i]; }
+__device__ __forceinline__ double2 ld_spec(const float2* p, long i, double2) {
+    float2 v = p[i]; return make_double2(v.x, v.y);
+}
+__device__ __forceinline__ float2 ld_spec(const __nv_bfloat162* p, long i, float2) {
+    return __bfloat1622float2(p[i]);
+}
+__device__ __forceinline__ double2 ld_spec(const __nv_bfloat162* p, long i, double2) {
+    float2 v = __bfloat1622float2(p[i]); return make_double2(v.x, v.y);
+}
+
+// ----------------------------------------------------------------------------
+// FFT schedule: Q = product of radices in {2,3,4,8}
+// ----------------------------------------------------------------------------
+struct FftSched {
+    int Q;
+    int ns;
+    int radix[RTE_MAX_STAGES];
+};
+
+// ----------------------------------------------------------------------------
+// error plumbing
+// ----------------------------------------------------------------------------
+#define RTE_CUDA_TRY(expr)                                       \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return rte_cuda_fail(_e, #expr);  \
+    } while (0)

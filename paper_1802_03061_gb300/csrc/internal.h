@@ -1,0 +1,101 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/rte.h"
+#include "common.cuh"
+
+rte_status rte_cuda_fail(cudaError_t e, const char* what);
+
+// Which linear map a pass sequence applies (Sec. 3.3, steps T.1 and T.2).
+enum MixKind { MIX_K = 0, MIX_RHS = 1 };
+
+// Krylov workspace of one precision.
+struct KrylovWs {
+    int m = 0;             // restart length (basis holds m+1 vectors)
+    void* V = nullptr;     // (m+1) x nr reals (float or double)
+    void* w = nullptr;     // nr reals
+    double* part = nullptr;  // partial sums [RTE_DOT_CHUNKS_MAX][nblk]
+    double* st = nullptr;    // device GMRES state (see krylov.cu)
+    void* exec = nullptr;    // cached graph of one Arnoldi step
+};
+
+struct rte_plan_s {
+    int dim = 2;
+    int n = 0;             // cells per side
+    int Q = 0;             // padded FFT length per dimension (even, >= 2n-1)
+    int H = 0;             // Q/2 + 1 half-spectrum columns
+    int L = 0;
+    int nch = 1;           // real channels 2L+1
+    long ncell = 0;        // n^dim
+    long nr = 0;           // reals per field vector: 2D 2(L+1)n^2, 3D n^3
+    double h = 0, mu_t = 0, mu_s = 0;
+    double sigma_hat[RTE_MAX_L + 1];
+    rte_opts opts;
+    FftSched sched;
+    // twiddle tables exp(-2 pi i t/Q), t < Q
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+    // kernel spectra (already scaled by 1/Q^dim).
+    // 2D: [H][2L+1][Q] complex for m = 0..2L.  3D: real octant [H][H][H].
+    double2* S64 = nullptr;
+    float2* S32 = nullptr;
+    __nv_bfloat162* S16 = nullptr;
+    double* S3_64 = nullptr;
+    float* S3_32 = nullptr;
+    // cell weights D_m, m = 0..2L (2D) or D (3D), computed on the device
+    double* Dm = nullptr;
+    // pass intermediates: 2D [nch][H][n] complex; 3D T1 [n][H][n], T2 [H][Q][n]
+    void* T64 = nullptr;
+    void* T32 = nullptr;
+    void* U64 = nullptr;   // second 3D intermediate (FP64)
+    void* U32 = nullptr;   // second 3D intermediate (FP32)
+    void* Tsplit = nullptr;    // [nch][H][Q] complex FP64 for the split column path
+    void* Tsplit32 = nullptr;  // same, FP32
+    bool col_split64 = false;
+    bool col_split32 = false;
+    // solve buffers (FP64): b, r, u, tmp
+    double* b64 = nullptr;
+    double* r64 = nullptr;
+    double* x64 = nullptr;
+    double* t64 = nullptr;
+    float* r32 = nullptr;
+    float* d32 = nullptr;
+    double* dscal = nullptr;  // device scalar (residual norm)
+    // host-side staging for rte_solve_host
+    double* f_dev = nullptr;
+    double* u_dev = nullptr;
+    KrylovWs k64, k32;
+    double* hst = nullptr;   // pinned host mirror of small device state (64 doubles)
+    double ms_pre = 0.0;
+    int nsm = 152;
+};
+
+// spectra.cu
+rte_status plan_build_spectra(rte_plan p, cudaStream_t s);
+void make_sched(FftSched* s, int Q);
+int choose_Q(int n);
+
+// op2d.cu : out = a*x + b*(K x) + c*z   (K replaced by K~g for MIX_RHS)
+rte_status op2d_apply64(rte_plan p, MixKind kind, const double* x, const double* xin_real,
+                        double* out, double a, double b, double c, const double* z, cudaStream_t s);
+rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
+                        const float* z, cudaStream_t s);
+// op3d.cu
+rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,
+                        double c, const double* z, cudaStream_t s);
+rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
+                        const float* z, cudaStream_t s);
+
+// krylov.cu
+rte_status krylov_solve(rte_plan p, const double* f, double* u, const rte_opts* o, rte_stats* st,
+                        cudaStream_t s);
+rte_status krylov_free(rte_plan p);
+
+// dispatch helpers (rte_api.cu)
+rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,
+                        double c, const double* z, cudaStream_t s);
+rte_status plan_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
+                        const float* z, cudaStream_t s);

@@ -1,0 +1,362 @@
+// 2D operator passes: y = a*x + b*(K x) + c*z  (or b*(K~ g) for the RHS).
+//
+// The field u has modes k = 0..L with u_{-k} = conj(u_k); its 2L+1 real
+// channels are Re u_0, Re u_k, Im u_k.  K is a translation-invariant
+// convolution on the real channels (Sec. 3.3.1: per (k,k') the kernel only
+// depends on x - y), so the passes are
+//   1. row pass    : weight by mu_s sigma_hat_k, zero-pad each row to Q,
+//                    complex FFT along x of u_k (k >= 1) or of two packed rows
+//                    of u_0, split into the half spectra (xi_x = 0..Q/2) of
+//                    the real channels; write T[c][xi_x][y] (y contiguous).
+//   2. column pass : per xi_x: FFT along y of every channel (zero padded),
+//                    per frequency the (2L+1)x(2L+1) mode mix with the
+//                    spectra S_m, m = 0..2L (Sec. 3.3.1 remark: the kernel
+//                    depends only on k - k'), inverse FFT, keep y < n.
+//   3. inverse row : rebuild the full x spectrum of u_k = Re + i Im from the
+//                    two half spectra, inverse FFT, keep x < n, epilogue.
+//
+// Mode mix.  With P_m = (S_m + S_{-m})/2, M_m = (S_m - S_{-m})/2 and
+// S_{-m}(xi) = (-1)^m conj(S_m(xi)) (kappa real and even), the spectra of the
+// real output channels are, for k = 0..L (A = spectrum of Re w, B of Im w,
+// w_k = mu_s sigma_hat_k u_k):
+//   Re v_k : P_k A_0 + sum_{k'=1..L} (P_{k-k'} + P_{k+k'}) A_k' + i (M_{k-k'} - M_{k+k'}) B_k'
+//   Im v_k : -i M_k A_0 + sum_{k'} -i (M_{k-k'} + M_{k+k'}) A_k' + (P_{k-k'} - P_{k+k'}) B_k'
+// For even m, P_m = Re S_m and M_m = i Im S_m; for odd m, P_m = i Im S_m and
+// M_m = Re S_m; P_{-m} = P_m, M_{-m} = -M_m.  Every coefficient is therefore
+// purely real or purely imaginary, known at compile time for fixed (k, k').
+#pragma once
+#include "fft.cuh"
+#include "internal.h"
+
+// channel index of Re u_k / Im u_k
+__host__ __device__ __forceinline__ int chA(int k) { return k == 0 ? 0 : 2 * k - 1; }
+__host__ __device__ __forceinline__ int chB(int k) { return 2 * k; }
+
+struct RowParams {
+    int n, Q, H, L, RB;
+    FftSched sc;
+    double wk[RTE_MAX_L + 1];  // per-mode input weight
+};
+
+// ---------------------------------------------------------------------------
+// 1. forward row pass
+//    x: [L+1][n][n] complex (may be null when f is given), f: real [n][n]
+//    source that replaces the mode-0 input (RHS).  out: T [nch][H][n].
+//    grid (ceil(n/RB), nmodes_in), block 256.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_fwd(const T* __restrict__ x, const double* __restrict__ f,
+                                                 T* __restrict__ out, const T* __restrict__ tw, RowParams p) {
+    using R = typename real_of<T>::R;
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, RB = p.RB;
+    const int k = blockIdx.y;
+    const int y0 = blockIdx.x * RB;
+    const int nl = (k == 0) ? RB / 2 : RB;
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)RB * Q;
+    load_twiddles(twl, tw, Q);
+    const R w = (R)p.wk[k];
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx / Q, e = idx - li * Q;
+        T v = mk<T>(0, 0);
+        if (e < n) {
+            if (k == 0) {
+                const int ya = y0 + 2 * li, yb = ya + 1;
+                R a = 0, b = 0;
+                if (f) {
+                    if (ya < n) a = (R)f[(long)ya * n + e];
+                    if (yb < n) b = (R)f[(long)yb * n + e];
+                } else {
+                    if (ya < n) a = x[(long)ya * n + e].x;
+                    if (yb < n) b = x[(long)yb * n + e].x;
+                }
+                v = mk<T>(w * a, w * b);
+            } else {
+                const int y = y0 + li;
+                if (y < n) {
+                    T u = x[((long)k * n + y) * n + e];
+                    v = mk<T>(w * u.x, w * u.y);
+                }
+            }
+        }
+        buf[idx] = v;
+    }
+    __syncthreads();
+    T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl);
+    // split Z = F + i G (F, G real rows) into their half spectra:
+    //   F(xi) = (Z(xi) + conj Z(-xi))/2,  G(xi) = (Z(xi) - conj Z(-xi))/(2i)
+    const int rows = (k == 0) ? RB : RB;
+    for (int idx = threadIdx.x; idx < H * rows; idx += blockDim.x) {
+        const int r = idx % rows, xi = idx / rows;
+        const int y = y0 + r;
+        if (y >= n) continue;
+        int line, which, ch;
+        if (k == 0) { line = r >> 1; which = r & 1; ch = 0; }
+        else { line = r; which = -1; ch = -1; }
+        const T Z = res[line * Q + xi];
+        const T Zm = res[line * Q + (xi == 0 ? 0 : Q - xi)];
+        const T Fv = mk<T>((R)0.5 * (Z.x + Zm.x), (R)0.5 * (Z.y - Zm.y));
+        const T Gv = mk<T>((R)0.5 * (Z.y + Zm.y), (R)-0.5 * (Z.x - Zm.x));
+        if (k == 0) {
+            out[((long)ch * H + xi) * n + y] = which == 0 ? Fv : Gv;
+        } else {
+            out[((long)chA(k) * H + xi) * n + y] = Fv;
+            out[((long)chB(k) * H + xi) * n + y] = Gv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. inverse row pass + epilogue  out = a*x + b*v + c*z
+//    in: T [nch][H][n] (column-pass output), grid (ceil(n/RB), L+1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const T* __restrict__ x,
+                                                 const T* __restrict__ z, T* __restrict__ out,
+                                                 const T* __restrict__ tw, RowParams p,
+                                                 typename real_of<T>::R a, typename real_of<T>::R b,
+                                                 typename real_of<T>::R c) {
+    using R = typename real_of<T>::R;
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, RB = p.RB;
+    const int k = blockIdx.y;
+    const int y0 = blockIdx.x * RB;
+    const int nl = (k == 0) ? RB / 2 : RB;
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)RB * Q;
+    load_twiddles(twl, tw, Q);
+    // Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
+    for (int idx = threadIdx.x; idx < H * nl; idx += blockDim.x) {
+        const int li = idx % nl, xi = idx / nl;
+        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
+        if (k == 0) {
+            const int ya = y0 + 2 * li, yb = ya + 1;
+            if (ya < n) Fv = in[((long)0 * H + xi) * n + ya];
+            if (yb < n) Gv = in[((long)0 * H + xi) * n + yb];
+        } else {
+            const int y = y0 + li;
+            if (y < n) {
+                Fv = in[((long)chA(k) * H + xi) * n + y];
+                Gv = in[((long)chB(k) * H + xi) * n + y];
+            }
+        }
+        buf[li * Q + xi] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) buf[li * Q + (Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+    }
+    __syncthreads();
+    T* res = fft_lines<1>(buf, tmp, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        const int li = idx / n, e = idx - li * n;
+        const T v = res[li * Q + e];
+        if (k == 0) {
+            const int ya = y0 + 2 * li, yb = ya + 1;
+            if (ya < n) {
+                const long o = (long)ya * n + e;
+                T r = mk<T>(b * v.x, 0);
+                if (x) { r.x += a * x[o].x; r.y += a * x[o].y; }
+                if (z) { r.x += c * z[o].x; r.y += c * z[o].y; }
+                out[o] = r;
+            }
+            if (yb < n) {
+                const long o = (long)yb * n + e;
+                T r = mk<T>(b * v.y, 0);
+                if (x) { r.x += a * x[o].x; r.y += a * x[o].y; }
+                if (z) { r.x += c * z[o].x; r.y += c * z[o].y; }
+                out[o] = r;
+            }
+        } else {
+            const int y = y0 + li;
+            if (y < n) {
+                const long o = ((long)k * n + y) * n + e;
+                T r = mk<T>(b * v.x, b * v.y);
+                if (x) { r.x += a * x[o].x; r.y += a * x[o].y; }
+                if (z) { r.x += c * z[o].x; r.y += c * z[o].y; }
+                out[o] = r;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. mode mix at one frequency: X[c] (in) -> X[c] (out), tagged coefficients
+// ---------------------------------------------------------------------------
+// acc += s * v  (im == false)   or   acc += (i s) * v  (im == true)
+template <typename T>
+__device__ __forceinline__ void tmac(T& acc, typename real_of<T>::R s, bool im, T v) {
+    if (im) { acc.x -= s * v.y; acc.y += s * v.x; }
+    else { acc.x += s * v.x; acc.y += s * v.y; }
+}
+
+template <int L, typename T>
+__device__ __forceinline__ void mode_mix(const typename real_of<T>::R* sr, const typename real_of<T>::R* si,
+                                         const T* in, T* outv) {
+    using R = typename real_of<T>::R;
+    // P(m): value, imag flag ; M(m): value, imag flag (m may be negative)
+#define PV(m) ((((m) < 0 ? -(m) : (m)) & 1) ? si[(m) < 0 ? -(m) : (m)] : sr[(m) < 0 ? -(m) : (m)])
+#define PI_(m) ((((m) < 0 ? -(m) : (m)) & 1) != 0)
+#define MV(m) (((m) < 0 ? (R)-1 : (R)1) * ((((m) < 0 ? -(m) : (m)) & 1) ? sr[(m) < 0 ? -(m) : (m)] : si[(m) < 0 ? -(m) : (m)]))
+#define MI_(m) ((((m) < 0 ? -(m) : (m)) & 1) == 0)
+#pragma unroll
+    for (int k = 0; k <= L; ++k) {
+        T Ra = mk<T>(0, 0), Ia = mk<T>(0, 0);
+        const T A0 = in[0];
+        tmac(Ra, PV(k), PI_(k), A0);
+        // -i * M(k):  M imag (k even): -i * i m = m (real) ; M real (k odd): -i m (imag, -m)
+        if (MI_(k)) tmac(Ia, MV(k), false, A0);
+        else tmac(Ia, -MV(k), true, A0);
+#pragma unroll
+        for (int kp = 1; kp <= L; ++kp) {
+            const T A = in[chA(kp)], B = in[chB(kp)];
+            const int d = k - kp, s = k + kp;
+            // (P_d + P_s) A   (P_d, P_s share parity)
+            tmac(Ra, PV(d) + PV(s), PI_(d), A);
+            // i (M_d - M_s) B
+            {
+                const R vm = MV(d) - MV(s);
+                if (MI_(d)) tmac(Ra, -vm, false, B);  // i * (i vm) = -vm
+                else tmac(Ra, vm, true, B);
+            }
+            // -i (M_d + M_s) A
+            {
+                const R vm = MV(d) + MV(s);
+                if (MI_(d)) tmac(Ia, vm, false, A);   // -i * (i vm) = vm
+                else tmac(Ia, -vm, true, A);
+            }
+            // (P_d - P_s) B
+            tmac(Ia, PV(d) - PV(s), PI_(d), B);
+        }
+        outv[chA(k)] = Ra;
+        if (k > 0) outv[chB(k)] = Ia;
+    }
+#undef PV
+#undef PI_
+#undef MV
+#undef MI_
+}
+
+struct ColParams {
+    int n, Q, H, L, nin, G;   // nin: input channels (nch for K, 1 for the RHS)
+    FftSched sc;
+};
+
+// load S_m(xi_x, xi_y), m = 0..2L, into (sr, si)
+template <int L, typename T, typename TS>
+__device__ __forceinline__ void load_spec(const TS* __restrict__ S, int kx, int ky, int Q,
+                                          typename real_of<T>::R* sr, typename real_of<T>::R* si) {
+#pragma unroll
+    for (int m = 0; m <= 2 * L; ++m) {
+        const T v = ld_spec(S, ((long)kx * (2 * L + 1) + m) * Q + ky, T());
+        sr[m] = v.x;
+        si[m] = v.y;
+    }
+}
+
+// channels [c0, c0+cnt) of X (line stride Q) through an FFT, result left in X
+template <int DIR, typename T>
+__device__ void fft_channels(T* X, T* tmp, int c0, int cnt, int G, const FftSched& sc, const T* twl) {
+    const int Q = sc.Q;
+    for (int g0 = c0; g0 < c0 + cnt; g0 += G) {
+        const int nl = min(G, c0 + cnt - g0);
+        T* res = fft_lines<DIR>(X + (long)g0 * Q, tmp, nl, Q, sc, twl);
+        if (res != X + (long)g0 * Q) {
+            for (int i = threadIdx.x; i < nl * Q; i += blockDim.x) X[(long)g0 * Q + i] = res[i];
+            __syncthreads();
+        }
+    }
+}
+
+// fused column pass, one block per xi_x; T is updated in place
+template <int L, typename T, typename TS>
+__global__ void __launch_bounds__(256) k_col_fused(T* __restrict__ Tb, const TS* __restrict__ S,
+                                                   const T* __restrict__ tw, ColParams p) {
+    constexpr int NCH = 2 * L + 1;
+    using R = typename real_of<T>::R;
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H;
+    const int kx = blockIdx.x;
+    T* twl = sm;
+    T* X = sm + Q;
+    T* tmp = X + (long)NCH * Q;
+    load_twiddles(twl, tw, Q);
+    for (int idx = threadIdx.x; idx < p.nin * Q; idx += blockDim.x) {
+        const int c = idx / Q, e = idx - c * Q;
+        X[idx] = e < n ? Tb[((long)c * H + kx) * n + e] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    fft_channels<-1>(X, tmp, 0, p.nin, p.G, p.sc, twl);
+    for (int ky = threadIdx.x; ky < Q; ky += blockDim.x) {
+        R sr[2 * L + 1], si[2 * L + 1];
+        load_spec<L, T>(S, kx, ky, Q, sr, si);
+        T in[NCH], o[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) in[c] = c < p.nin ? X[(long)c * Q + ky] : mk<T>(0, 0);
+        mode_mix<L, T>(sr, si, in, o);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) X[(long)c * Q + ky] = o[c];
+    }
+    __syncthreads();
+    fft_channels<1>(X, tmp, 0, NCH, p.G, p.sc, twl);
+    for (int idx = threadIdx.x; idx < NCH * n; idx += blockDim.x) {
+        const int c = idx / n, e = idx - c * n;
+        Tb[((long)c * H + kx) * n + e] = X[(long)c * Q + e];
+    }
+}
+
+// split column pass (when all channels of a column do not fit in shared
+// memory): per xi_x FFT channel groups between Tb [nch][H][n] and the full
+// column spectra Ts [nch][H][Q]; the mix runs pointwise on Ts.
+template <typename T>
+__global__ void __launch_bounds__(256) k_col_fft_split(T* __restrict__ Tb, T* __restrict__ Ts,
+                                                       const T* __restrict__ tw, ColParams p, int fwd,
+                                                       int nchan) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, G = p.G;
+    const int kx = blockIdx.x;
+    T* twl = sm;
+    T* X = sm + Q;
+    T* tmp = X + (long)G * Q;
+    load_twiddles(twl, tw, Q);
+    for (int c0 = 0; c0 < nchan; c0 += G) {
+        const int nl = min(G, nchan - c0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+            const int c = c0 + idx / Q, e = idx % Q;
+            T v;
+            if (fwd) v = e < n ? Tb[((long)c * H + kx) * n + e] : mk<T>(0, 0);
+            else v = Ts[((long)c * H + kx) * Q + e];
+            X[idx] = v;
+        }
+        __syncthreads();
+        T* res = fwd ? fft_lines<-1>(X, tmp, nl, Q, p.sc, twl) : fft_lines<1>(X, tmp, nl, Q, p.sc, twl);
+        for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+            const int c = c0 + idx / Q, e = idx % Q;
+            if (fwd) Ts[((long)c * H + kx) * Q + e] = res[idx];
+            else if (e < n) Tb[((long)c * H + kx) * n + e] = res[idx];
+        }
+    }
+}
+
+template <int L, typename T, typename TS>
+__global__ void k_mix_pointwise(T* __restrict__ Ts, const TS* __restrict__ S, ColParams p) {
+    constexpr int NCH = 2 * L + 1;
+    using R = typename real_of<T>::R;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Q = p.Q, H = p.H;
+    if (idx >= (long)H * Q) return;
+    const int kx = (int)(idx / Q), ky = (int)(idx % Q);
+    R sr[2 * L + 1], si[2 * L + 1];
+    load_spec<L, T>(S, kx, ky, Q, sr, si);
+    T in[NCH], o[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) in[c] = c < p.nin ? Ts[((long)c * H + kx) * Q + ky] : mk<T>(0, 0);
+    mode_mix<L, T>(sr, si, in, o);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) Ts[((long)c * H + kx) * Q + ky] = o[c];
+}

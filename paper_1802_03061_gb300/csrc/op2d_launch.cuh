@@ -1,0 +1,119 @@
+// Host launchers of the 2D passes, instantiated per precision in op2d_64.cu
+// and op2d_32.cu.
+#pragma once
+#include "op2d.cuh"
+
+#define RTE_SMEM_OPTIN 232448   // 227 KB dynamic shared memory per block on sm_103a
+
+template <typename K> static cudaError_t allow_smem(K kern) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RTE_SMEM_OPTIN);
+}
+
+template <typename T> static int rows_per_block(int Q) {
+    int rb = 65536 / (2 * Q * (int)sizeof(T));
+    if (rb > 16) rb = 16;
+    if (rb < 2) rb = 2;
+    return rb & ~1;
+}
+
+template <typename T> static size_t row_smem(int Q, int RB) { return (size_t)(Q + 2 * RB * Q) * sizeof(T); }
+
+// Column pass choice: fused (all channels resident) when it fits.
+template <typename T> static bool col_fits(int nch, int Q) {
+    return (size_t)(Q + nch * Q + Q) * sizeof(T) <= 200 * 1024;
+}
+template <typename T> static int col_group(int nch, int Q) {
+    long left = 200L * 1024 / (long)sizeof(T) - (long)Q - (long)nch * Q;
+    int G = (int)(left / Q);
+    if (G > nch) G = nch;
+    if (G < 1) G = 1;
+    return G;
+}
+template <typename T> static int split_group(int nch, int Q) {
+    long G = (200L * 1024 / (long)sizeof(T) / Q - 1) / 2;
+    if (G > nch) G = nch;
+    if (G < 1) G = 1;
+    return (int)G;
+}
+
+template <int L, typename T, typename TS>
+static cudaError_t launch_col(T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split, cudaStream_t s) {
+    constexpr int NCH = 2 * L + 1;
+    const int Q = cp.Q;
+    cudaError_t e;
+    if (!split) {
+        static bool once = false;
+        if (!once) { e = allow_smem(k_col_fused<L, T, TS>); if (e != cudaSuccess) return e; once = true; }
+        cp.G = col_group<T>(NCH, Q);
+        const size_t smem = (size_t)(Q + NCH * Q + cp.G * Q) * sizeof(T);
+        k_col_fused<L, T, TS><<<cp.H, 256, smem, s>>>(Tb, S, tw, cp);
+        return cudaGetLastError();
+    }
+    static bool once2 = false;
+    if (!once2) { e = allow_smem(k_col_fft_split<T>); if (e != cudaSuccess) return e; once2 = true; }
+    cp.G = split_group<T>(NCH, Q);
+    const size_t smem = (size_t)(Q + 2 * cp.G * Q) * sizeof(T);
+    k_col_fft_split<T><<<cp.H, 256, smem, s>>>(Tb, Ts, tw, cp, 1, cp.nin);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long tot = (long)cp.H * Q;
+    k_mix_pointwise<L, T, TS><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Ts, S, cp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_col_fft_split<T><<<cp.H, 256, smem, s>>>(Tb, Ts, tw, cp, 0, NCH);
+    return cudaGetLastError();
+}
+
+template <typename T, typename TS>
+static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split,
+                                cudaStream_t s) {
+    switch (L) {
+        case 0: return launch_col<0>(Tb, Ts, S, tw, cp, split, s);
+        case 1: return launch_col<1>(Tb, Ts, S, tw, cp, split, s);
+        case 2: return launch_col<2>(Tb, Ts, S, tw, cp, split, s);
+        case 3: return launch_col<3>(Tb, Ts, S, tw, cp, split, s);
+        case 4: return launch_col<4>(Tb, Ts, S, tw, cp, split, s);
+        case 5: return launch_col<5>(Tb, Ts, S, tw, cp, split, s);
+        case 6: return launch_col<6>(Tb, Ts, S, tw, cp, split, s);
+        case 7: return launch_col<7>(Tb, Ts, S, tw, cp, split, s);
+        case 8: return launch_col<8>(Tb, Ts, S, tw, cp, split, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// out = a*x + b*(Op x) + c*z ; Op = K (MIX_K) or K~ on the source f (MIX_RHS)
+template <typename T, typename TS>
+static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* f, T* out, double a, double b,
+                            double c, const T* z, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
+                            cudaStream_t s) {
+    using R = typename real_of<T>::R;
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_row_fwd<T>)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_row_inv<T>)) != cudaSuccess) return e;
+        once = true;
+    }
+    RowParams rp;
+    rp.n = p->n; rp.Q = p->Q; rp.H = p->H; rp.L = p->L;
+    rp.RB = rows_per_block<T>(p->Q);
+    rp.sc = p->sched;
+    for (int k = 0; k <= RTE_MAX_L; ++k) rp.wk[k] = 0.0;
+    if (kind == MIX_K) {
+        for (int k = 0; k <= p->L; ++k) rp.wk[k] = p->mu_s * p->sigma_hat[k];
+    } else {
+        rp.wk[0] = 1.0;
+    }
+    const int nmod_in = kind == MIX_K ? p->L + 1 : 1;
+    const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
+    const size_t smr = row_smem<T>(p->Q, rp.RB);
+    k_row_fwd<T><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw, rp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ColParams cp;
+    cp.n = p->n; cp.Q = p->Q; cp.H = p->H; cp.L = p->L;
+    cp.nin = kind == MIX_K ? p->nch : 1;
+    cp.G = 1;
+    cp.sc = p->sched;
+    if ((e = dispatch_col<T, TS>(p->L, Tb, Ts, S, tw, cp, split, s)) != cudaSuccess) return e;
+    const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
+    k_row_inv<T><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b, (R)c);
+    return cudaGetLastError();
+}

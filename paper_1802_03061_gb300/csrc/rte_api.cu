@@ -1,0 +1,275 @@
+// C ABI entry points (include/rte.h): plan lifetime, operator application,
+// right-hand side, solve.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "internal.h"
+
+static thread_local char g_last_error[256] = "";
+
+rte_status rte_cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();  // clear a sticky non-fatal error state where possible
+    return e == cudaErrorMemoryAllocation ? RTE_ENOMEM : RTE_ECUDA;
+}
+
+extern "C" const char* rte_last_error(void) { return g_last_error; }
+
+extern "C" const char* rte_status_str(rte_status s) {
+    switch (s) {
+        case RTE_OK: return "ok";
+        case RTE_EINVAL: return "invalid argument";
+        case RTE_EUNSUPPORTED: return "unsupported configuration";
+        case RTE_ENOMEM: return "device out of memory";
+        case RTE_ECUDA: return "CUDA error";
+        case RTE_ENOCONV: return "solver did not reach the tolerance";
+        case RTE_ETIMEOUT: return "device wait timed out";
+        case RTE_ENAN: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+static bool smooth23(int q) {
+    if (q < 1) return false;
+    while (q % 2 == 0) q /= 2;
+    while (q % 3 == 0) q /= 3;
+    return q == 1;
+}
+
+static void fill_defaults(rte_opts* o) {
+    if (o->tol <= 0) o->tol = 1e-8;
+    if (o->restart <= 0) o->restart = 40;
+    if (o->restart > 128) o->restart = 128;
+    if (o->maxit <= 0) o->maxit = 2000;
+    if (o->inner_tol <= 0) o->inner_tol = 1e-4;
+}
+
+template <typename P> static rte_status dalloc(P** p, size_t bytes) {
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(g_last_error, sizeof(g_last_error), "cudaMalloc(%zu) failed", bytes);
+        return RTE_ENOMEM;
+    }
+    return RTE_OK;
+}
+
+rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
+                        const double* z, cudaStream_t s) {
+    if (p->dim == 2)
+        return op2d_apply64(p, kind, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? x : nullptr, out, a, b, c, z, s);
+    return op3d_apply64(p, kind, x, out, a, b, c, z, s);
+}
+
+rte_status plan_apply32(rte_plan p, const float* x, float* out, float a, float b, float c, const float* z,
+                        cudaStream_t s) {
+    if (p->dim == 2) return op2d_apply32(p, x, out, a, b, c, z, s);
+    return op3d_apply32(p, x, out, a, b, c, z, s);
+}
+
+extern "C" rte_status rte_destroy(rte_plan p) {
+    if (!p) return RTE_OK;
+    cudaDeviceSynchronize();
+    krylov_free(p);
+    void* bufs[] = {p->tw64, p->tw32, p->S64, p->S32, p->S16, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
+                    p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
+                    p->d32, p->dscal, p->f_dev, p->u_dev};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->hst) cudaFreeHost(p->hst);
+    delete p;
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, double mu_t, double mu_s, int L,
+                                      const double* sigma_hat, const rte_opts* opts, void* cuda_stream) {
+    if (!out) return RTE_EINVAL;
+    *out = nullptr;
+    if (grid.dim != 2 && grid.dim != 3) return RTE_EINVAL;
+    const int n = grid.n[0];
+    if (n < 1 || !(h > 0) || !isfinite(h)) return RTE_EINVAL;
+    if (!(mu_t >= 0) || !(mu_s >= 0) || !(mu_s <= mu_t) || !isfinite(mu_t)) return RTE_EINVAL;
+    if (L < 0 || L > RTE_MAX_L) return RTE_EINVAL;
+    if (L > 0 && !sigma_hat) return RTE_EINVAL;
+    if (sigma_hat) {
+        if (fabs(sigma_hat[0] - 1.0) > 1e-12) return RTE_EINVAL;
+        for (int k = 1; k <= L; ++k)
+            if (!(fabs(sigma_hat[k]) <= 1.0)) return RTE_EINVAL;
+    }
+    if (grid.dim == 3 && L > 0) return RTE_EUNSUPPORTED;
+    rte_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    fill_defaults(&o);
+    if (o.prec < RTE_PREC_FP64 || o.prec > RTE_PREC_MIXED_BF16SPEC) return RTE_EINVAL;
+    int Q = choose_Q(n);
+    if (o.q_policy > 0) {
+        Q = o.q_policy;
+        if (Q < 2 * n - 1 || (Q & 1) || !smooth23(Q)) return RTE_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rte_plan p = new rte_plan_s();
+    p->dim = grid.dim;
+    p->n = n;
+    p->Q = Q;
+    p->H = Q / 2 + 1;
+    p->L = L;
+    p->nch = 2 * L + 1;
+    p->h = h;
+    p->mu_t = mu_t;
+    p->mu_s = mu_s;
+    for (int k = 0; k <= RTE_MAX_L; ++k) p->sigma_hat[k] = (k <= L && sigma_hat) ? sigma_hat[k] : (k == 0 ? 1.0 : 0.0);
+    p->opts = o;
+    make_sched(&p->sched, Q);
+    p->ncell = grid.dim == 2 ? (long)n * n : (long)n * n * n;
+    p->nr = grid.dim == 2 ? 2L * (L + 1) * n * n : p->ncell;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+
+    rte_status st = RTE_OK;
+    const int H = p->H, nch = p->nch;
+#define TRY(x)                      \
+    do {                            \
+        st = (x);                   \
+        if (st != RTE_OK) goto fail; \
+    } while (0)
+    TRY(dalloc(&p->tw64, Q * sizeof(double2)));
+    TRY(dalloc(&p->tw32, Q * sizeof(float2)));
+    TRY(dalloc(&p->Dm, (2 * RTE_MAX_L + 1) * sizeof(double)));
+    if (grid.dim == 2) {
+        const size_t ns = (size_t)H * nch * Q;
+        TRY(dalloc(&p->S64, ns * sizeof(double2)));
+        TRY(dalloc(&p->S32, ns * sizeof(float2)));
+        TRY(dalloc(&p->S16, ns * sizeof(__nv_bfloat162)));
+        const size_t nt = (size_t)nch * H * n;
+        TRY(dalloc((double2**)&p->T64, nt * sizeof(double2)));
+        TRY(dalloc((float2**)&p->T32, nt * sizeof(float2)));
+        p->col_split64 = (size_t)(Q + nch * Q + Q) * sizeof(double2) > 200 * 1024;
+        p->col_split32 = (size_t)(Q + nch * Q + Q) * sizeof(float2) > 200 * 1024;
+        if (p->col_split64) TRY(dalloc((double2**)&p->Tsplit, (size_t)nch * H * Q * sizeof(double2)));
+        if (p->col_split32) TRY(dalloc((float2**)&p->Tsplit32, (size_t)nch * H * Q * sizeof(float2)));
+    } else {
+        const size_t ns = (size_t)H * H * H;
+        TRY(dalloc(&p->S3_64, ns * sizeof(double)));
+        TRY(dalloc(&p->S3_32, ns * sizeof(float)));
+        const size_t n1 = (size_t)n * H * n;   // after x pass: [z][xi_x][y]
+        const size_t n2 = (size_t)H * Q * n;   // after y pass: [xi_x][xi_y][z]
+        TRY(dalloc((double2**)&p->T64, n1 * sizeof(double2)));
+        TRY(dalloc((double2**)&p->U64, n2 * sizeof(double2)));
+        TRY(dalloc((float2**)&p->T32, n1 * sizeof(float2)));
+        TRY(dalloc((float2**)&p->U32, n2 * sizeof(float2)));
+    }
+    TRY(dalloc(&p->b64, p->nr * sizeof(double)));
+    TRY(dalloc(&p->r64, p->nr * sizeof(double)));
+    TRY(dalloc(&p->x64, p->nr * sizeof(double)));
+    TRY(dalloc(&p->t64, p->nr * sizeof(double)));
+    TRY(dalloc(&p->r32, p->nr * sizeof(float)));
+    TRY(dalloc(&p->d32, p->nr * sizeof(float)));
+    TRY(dalloc(&p->dscal, 8 * sizeof(double)));
+    TRY(dalloc(&p->f_dev, p->ncell * sizeof(double)));
+    TRY(dalloc(&p->u_dev, p->nr * sizeof(double)));
+    if (cudaMallocHost((void**)&p->hst, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        st = RTE_ENOMEM;
+        goto fail;
+    }
+    TRY(plan_build_spectra(p, s));
+    // one application in each precision: validates the launch shapes and
+    // sets the kernels' shared-memory attributes before any graph capture
+    if (cudaMemsetAsync(p->x64, 0, p->nr * sizeof(double), s) != cudaSuccess) { st = RTE_ECUDA; goto fail; }
+    if (cudaMemsetAsync(p->r32, 0, p->nr * sizeof(float), s) != cudaSuccess) { st = RTE_ECUDA; goto fail; }
+    TRY(plan_apply64(p, MIX_K, p->x64, p->t64, 1.0, -1.0, 0.0, nullptr, s));
+    TRY(plan_apply32(p, p->r32, p->d32, 1.0f, -1.0f, 0.0f, nullptr, s));
+    {
+        cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { st = rte_cuda_fail(ce, "plan_create"); goto fail; }
+    }
+#undef TRY
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        p->ms_pre = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = p;
+    return RTE_OK;
+fail:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rte_destroy(p);
+    return st;
+}
+
+extern "C" rte_status rte_apply_K(rte_plan p, const void* x, void* y, void* stream) {
+    if (!p || !x || !y || x == y) return RTE_EINVAL;
+    return plan_apply64(p, MIX_K, (const double*)x, (double*)y, 0.0, 1.0, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_apply_A(rte_plan p, const void* x, void* y, void* stream) {
+    if (!p || !x || !y || x == y) return RTE_EINVAL;
+    return plan_apply64(p, MIX_K, (const double*)x, (double*)y, 1.0, -1.0, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_apply_K32(rte_plan p, const void* x, void* y, void* stream) {
+    if (!p || !x || !y || x == y) return RTE_EINVAL;
+    return plan_apply32(p, (const float*)x, (float*)y, 0.0f, 1.0f, 0.0f, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_rhs(rte_plan p, const double* f, void* b, void* stream) {
+    if (!p || !f || !b) return RTE_EINVAL;
+    return plan_apply64(p, MIX_RHS, f, (double*)b, 0.0, 1.0, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_solve(rte_plan p, const double* f, void* u, const rte_opts* opts, rte_stats* stats,
+                                void* stream) {
+    if (!p || !f || !u) return RTE_EINVAL;
+    rte_opts o = opts ? *opts : p->opts;
+    fill_defaults(&o);
+    if (o.prec < RTE_PREC_FP64 || o.prec > RTE_PREC_MIXED_BF16SPEC) return RTE_EINVAL;
+    // every plan holds FP64, FP32 and BF16 spectra; the solve picks its own
+    const rte_prec saved = p->opts.prec;
+    p->opts.prec = o.prec;
+    rte_status st = krylov_solve(p, f, (double*)u, &o, stats, (cudaStream_t)stream);
+    p->opts.prec = saved;
+    return st;
+}
+
+extern "C" rte_status rte_solve_host(rte_plan p, const double* f_host, void* u_host, const rte_opts* opts,
+                                     rte_stats* stats, void* stream) {
+    if (!p || !f_host || !u_host) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    RTE_CUDA_TRY(cudaMemcpyAsync(p->f_dev, f_host, p->ncell * sizeof(double), cudaMemcpyHostToDevice, s));
+    rte_opts o = opts ? *opts : p->opts;
+    if (o.use_guess)
+        RTE_CUDA_TRY(cudaMemcpyAsync(p->u_dev, u_host, p->nr * sizeof(double), cudaMemcpyHostToDevice, s));
+    rte_status st = rte_solve(p, p->f_dev, p->u_dev, &o, stats, stream);
+    if (st != RTE_OK && st != RTE_ENOCONV) return st;
+    RTE_CUDA_TRY(cudaMemcpyAsync(u_host, p->u_dev, p->nr * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RTE_CUDA_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
+extern "C" rte_status rte_plan_info(rte_plan p, int* n, int* Q, int* L, long* nreal) {
+    if (!p) return RTE_EINVAL;
+    if (n) *n = p->n;
+    if (Q) *Q = p->Q;
+    if (L) *L = p->L;
+    if (nreal) *nreal = p->nr;
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_plan_cell_weights(rte_plan p, double* out) {
+    if (!p || !out) return RTE_EINVAL;
+    const int cnt = p->dim == 2 ? 2 * p->L + 1 : 1;
+    RTE_CUDA_TRY(cudaMemcpy(out, p->Dm, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    return RTE_OK;
+}

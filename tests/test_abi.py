@@ -1,0 +1,69 @@
+"""CPU checks of the boundary: the library builds, loads and exports every
+function that include/rte.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(rte_\w+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared()
+    for must in ("rte_plan_create", "rte_apply_K", "rte_solve", "rte_destroy", "rte_rhs"):
+        assert must in names
+
+
+def test_library_loads_and_exports_all_symbols():
+    from paper_1802_03061_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    from paper_1802_03061_gb300 import _binding as B
+    assert B.rte_status_str(B.RTE_EINVAL) == "invalid argument"
+    assert B.rte_status_str(B.RTE_ENOCONV).startswith("solver")
+
+
+def test_binding_refuses_missing_library(tmp_path, monkeypatch):
+    from paper_1802_03061_gb300 import _binding as B
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(RuntimeError):
+        B.lib()
+
+
+@pytest.mark.parametrize("args", [
+    dict(n=8, mu_t=1.0, mu_s=2.0, L=0, sig=[1.0]),          # mu_s > mu_t (C2)
+    dict(n=8, mu_t=1.0, mu_s=0.5, L=1, sig=[0.9, 0.1]),     # sigma_hat_0 != 1
+    dict(n=8, mu_t=1.0, mu_s=0.5, L=1, sig=[1.0, 1.5]),     # |sigma_hat_k| > 1
+    dict(n=0, mu_t=1.0, mu_s=0.5, L=0, sig=[1.0]),          # empty grid
+    dict(n=8, mu_t=-1.0, mu_s=0.0, L=0, sig=[1.0]),         # negative mu_t
+    dict(n=8, mu_t=1.0, mu_s=0.5, L=9, sig=[1.0] * 10),     # L beyond the supported 8
+])
+def test_plan_create_rejects_invalid_arguments_before_any_device_call(args):
+    from paper_1802_03061_gb300 import _binding as B
+    with pytest.raises(B.RteError) as ei:
+        B.rte_plan_create(2, args["n"], 0.125, args["mu_t"], args["mu_s"], args["L"], args["sig"])
+    assert ei.value.status == B.RTE_EINVAL
+
+
+def test_plan_create_3d_anisotropic_unsupported():
+    from paper_1802_03061_gb300 import _binding as B
+    with pytest.raises(B.RteError) as ei:
+        B.rte_plan_create(3, 8, 0.125, 1.0, 0.5, 1, [1.0, 0.5])
+    assert ei.value.status == B.RTE_EUNSUPPORTED
