@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark: solves to 1e-8 relative residual per second on one GB300.
+
+Workload (default): 2D anisotropic Henyey-Greenstein transport regime,
+256 x 256 cells on the unit square, |k| <= 8 (17 angular modes), g = 0.5,
+mu_t = 10, mu_s = 9, source = 4 seeded Gaussians (centres U[0.2,0.8]^2,
+widths U[0.03,0.1]); inner FP32 FFT / mode mix with BF16 kernel spectra,
+FP64 outer refinement; stop at FP64 ||b - (I-K)u|| / ||b|| <= 1e-8.
+
+A step is one solve (right-hand side T.1 + refinement/GMRES T.2) of one
+synthetic source, with the plan (cell weights, kernel samples, spectra) made
+once beforehand; its time T_pre is reported in config.  The plain FP64
+GMRES solve of the same problem is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun each rank solves its own replicas (independent problems, no
+collective on the data path); value = all solves / max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time-to-1e-8 residual & matvec GB/s (HBM roofline %): mixed+learned vs plain FP64"
+UNIT = "solves/s"
+WORKLOAD = "hg2d_transport_256_L8: 256x256, |k|<=8, HG g=0.5, mu_t=10, mu_s=9, 4 Gaussians; tol 1e-8"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing on a bounded sample
+# ----------------------------------------------------------------------------
+def oracle_sample(prob, rows_sample, seed=0):
+    """Direct-sum K u at `rows_sample` cells of the full-size workload, timed;
+    returns (seconds per full matvec extrapolated, threads, rows)."""
+    import oracle
+    n = prob["n"]
+    L = len(prob["sigma_hat"]) - 1
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((2 * L + 1, n, n)) + 1j * rng.standard_normal((2 * L + 1, n, n))
+    rows = rng.choice(n * n, size=rows_sample, replace=False)
+    D = oracle.cell_weights_2d(prob["mu_t"], prob["h"], 2 * L)
+    t0 = time.perf_counter()
+    oracle.apply_K_2d(n, prob["h"], prob["mu_t"], prob["mu_s"], prob["sigma_hat"], u, rows=rows, D=D)
+    dt = time.perf_counter() - t0
+    return dt / rows_sample * n * n, oracle.num_threads(), rows_sample
+
+
+def oracle_matvec_count(prob, n_small=16):
+    """Matvecs the plain FP64 GMRES needs at tolerance 1e-8 for this physics,
+    counted with the oracle's own GMRES on an n_small grid of the same domain."""
+    import oracle
+    import rte_synth
+    L = len(prob["sigma_hat"]) - 1
+    small = rte_synth.hg2d_transport(n=n_small, L=L, g=float(prob["sigma_hat"][1]) if L else 0.0,
+                                     mu_t=prob["mu_t"], mu_s=prob["mu_s"], seed=2)
+    h = 1.0 / n_small
+    D = oracle.cell_weights_2d(prob["mu_t"], h, 2 * L)
+    b = oracle.rhs_2d(n_small, h, prob["mu_t"], L, small["f"], D=D[L:3 * L + 1])
+    cnt = [0]
+
+    def A(t):
+        cnt[0] += 1
+        return t - oracle.apply_K_2d(n_small, h, prob["mu_t"], prob["mu_s"], prob["sigma_hat"], t, D=D)
+
+    oracle.gmres(A, b, tol=1e-8, restart=40)
+    return cnt[0] + 1  # + the right-hand side
+
+
+def run_reference(args):
+    """The oracle timed on the host cores on bounded samples of the workload."""
+    import rte_synth
+    prob = rte_synth.hg2d_transport()
+    nmv = oracle_matvec_count(prob)
+    rows = args.ref_rows
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(prob, max(4, rows // 8), seed=99)
+    ts = []
+    threads = 1
+    for k in range(args.steps):
+        t_mv, threads, _ = oracle_sample(prob, rows, seed=k)
+        ts.append(t_mv * nmv)
+    t_solve = float(np.mean(ts))
+    value = 1.0 / t_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "oracle": "direct O(N^2) Nystrom sum, FP64, OpenMP",
+                   "matvecs_per_solve": nmv},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d sampled cells x all 17 modes of K u per step, extrapolated to a full "
+                                   "matvec x %d matvecs (plain GMRES count at n=16, same physics)" % (rows, nmv)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------
+def run_native(args):
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Plan
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    _build.build()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    base = rte_synth.hg2d_transport()
+    n, L = base["n"], len(base["sigma_hat"]) - 1
+    plan = Plan(n, mu_t=base["mu_t"], mu_s=base["mu_s"], sigma_hat=base["sigma_hat"], prec=args.prec, tol=1e-8,
+                restart=args.restart)
+    t_pre_ms = None
+    nsteps = args.steps + args.warmup
+    # inputs resident in HBM before timing: one seeded source per step
+    srcs = []
+    for i in range(nsteps):
+        pr = rte_synth.hg2d_transport(seed=2 + 1000 * rank + i)
+        srcs.append(torch.from_numpy(pr["f"]).cuda())
+    u = plan.empty()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    stats_all = []
+    for i in range(args.warmup):
+        _, st = plan.solve(srcs[i], u=None)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    l0 = B.rte_kernel_launches()
+    tot_ms = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    for i in range(args.warmup, nsteps):
+        flush.zero_()
+        e0.record(stream)
+        _, st = plan.solve(srcs[i])
+        e1.record(stream)
+        e1.synchronize()
+        tot_ms += e0.elapsed_time(e1)
+        stats_all.append(st)
+    torch.cuda.synchronize()
+    launches = B.rte_kernel_launches() - l0
+    clk = clocks.stop()
+    t_max = tot_ms
+    if ws > 1:
+        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = t_max / args.steps
+    value = ws * args.steps / (t_max / 1e3)
+    ok = all(s["converged"] for s in stats_all)
+    iters = float(np.mean([s["iters"] for s in stats_all]))
+    outer = float(np.mean([s["outer"] for s in stats_all]))
+    relres = max(s["relres_true"] for s in stats_all)
+    t_pre_ms = stats_all[0]["ms_pre"]
+
+    # plain FP64 GMRES on the same problems (context for the metric)
+    fp64_ms = []
+    fp64_its = []
+    for i in range(min(3, args.steps)):
+        flush.zero_()
+        e0.record(stream)
+        _, st = plan.solve(srcs[args.warmup + i], prec="fp64")
+        e1.record(stream)
+        e1.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+        fp64_its.append(st["iters"])
+
+    # e2e: host buffers (pinned), copies inside the timed region
+    f_host = torch.from_numpy(np.ascontiguousarray(rte_synth.hg2d_transport(seed=2)["f"])).pin_memory()
+    u_host = torch.zeros(plan.shape(), dtype=torch.complex128).pin_memory()
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.rte_solve_host(plan.handle, f_host.data_ptr(), u_host.data_ptr(), plan.opts, int(stream.cuda_stream))
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = ws / (float(np.mean(e2e_ms)) / 1e3)
+
+    # roofline of the dominant kernels: per-pass CUDA-event timing
+    reps = 50
+    ms32 = B.rte_time_passes(plan.handle, 1, reps, int(stream.cuda_stream))
+    ms64 = B.rte_time_passes(plan.handle, 0, reps, int(stream.cuda_stream))
+    H, Q, nch = plan.Q // 2 + 1, plan.Q, 2 * L + 1
+    s_spec = {"mixed_bf16": 4, "mixed_fp32": 8, "fp64": 16}[args.prec]
+    col_bytes32 = nch * H * n * 8 * 2 + H * nch * Q * s_spec       # T in + T out + spectra
+    col_bytes64 = nch * H * n * 16 * 2 + H * nch * Q * 16
+    mv_bytes32 = 2 * n * n * nch * 4 + nch * (Q * Q // 2) * s_spec  # algorithmic bytes of one K application
+    hbm_peak, peak_src = peaks()
+    ach = col_bytes32 / (ms32[1] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16 inner, f64 refinement" if args.prec != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "prec": args.prec, "restart": args.restart, "Q": plan.Q,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "t_pre_ms": t_pre_ms, "iters_mean": iters, "outer_mean": outer, "relres_max": relres,
+                   "all_converged": ok, "fp64_ms_per_solve": float(np.mean(fp64_ms)),
+                   "fp64_iters": float(np.mean(fp64_its)),
+                   "speedup_vs_fp64": float(np.mean(fp64_ms)) / ms_per_step,
+                   "pass_ms_fp32": ms32, "pass_ms_fp64": ms64,
+                   "matvec_fp32_ms": sum(ms32), "matvec_fp32_useful_GBs": mv_bytes32 / (sum(ms32) * 1e-3) / 1e9,
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"kernel": "column pass (FFT_y, mode mix, iFFT_y), FP32, BF16 spectra", "bound": "hbm",
+                     "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": col_bytes32, "ms_per_launch": ms32[1]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * n * 8,
+                "d2h_bytes_per_step": int(plan.info["nreal"]) * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_mv, threads, rows = oracle_sample(base, args.ref_rows)
+        nmv = iters + outer + 1
+        line["cpu_baseline"] = {"value": 1.0 / (t_mv * nmv), "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "%d sampled cells x 17 modes of the direct-sum K u, extrapolated to a "
+                                          "full matvec x %.0f matvecs (the mixed solve's count)" % (rows, nmv)}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--prec", default="mixed_bf16", choices=["mixed_bf16", "mixed_fp32", "fp64"])
+    ap.add_argument("--restart", type=int, default=40)
+    ap.add_argument("--ref-rows", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        ws, rank, _ = dist_env()
+        if rank != 0:
+            return
+        run_reference(args)
+        return
+    run_native(args)
+
+
+if __name__ == "__main__":
+    main()

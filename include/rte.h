@@ -143,6 +143,18 @@ rte_status rte_plan_info(rte_plan plan, int* n, int* Q, int* L, long* nreal);
  * host array out (2L+1 doubles, or 1). */
 rte_status rte_plan_cell_weights(rte_plan plan, double* out_host);
 
+/* Diagnostics (no counterpart in the paper).
+ * rte_time_passes: average duration in ms of each FFT pass of one K
+ * application -- ms_out[0] row pass, [1] column pass (FFT, mode mix, inverse
+ * FFT), [2] inverse row pass -- over `reps` back-to-back launches, timed with
+ * CUDA events on cuda_stream.  inner = 0 times the FP64 passes, inner = 1 the
+ * FP32 passes with the plan's inner spectra.  Operates on plan-owned scratch
+ * vectors.  2D plans only (RTE_EUNSUPPORTED for 3D).
+ * rte_kernel_launches: number of kernels this library has launched so far in
+ * the process (host-side counter; a replayed graph adds its kernel nodes). */
+rte_status rte_time_passes(rte_plan plan, int inner, int reps, double* ms_out_host, void* cuda_stream);
+long long rte_kernel_launches(void);
+
 /* Free all device memory of the plan.  NULL is accepted. */
 rte_status rte_destroy(rte_plan plan);
 

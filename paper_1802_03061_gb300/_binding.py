@@ -65,6 +65,9 @@ def lib():
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]
         L.rte_plan_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
         L.rte_destroy.argtypes = [VP]
+        L.rte_time_passes.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
+        L.rte_time_passes.restype = ctypes.c_int
+        L.rte_kernel_launches.restype = ctypes.c_longlong
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
         L.rte_last_error.restype = ctypes.c_char_p
@@ -150,6 +153,16 @@ def rte_plan_cell_weights(plan, count):
     out = (ctypes.c_double * count)()
     _check(lib().rte_plan_cell_weights(plan, out), "rte_plan_cell_weights")
     return list(out)
+
+
+def rte_time_passes(plan, inner, reps, stream=0, npass=3):
+    out = (ctypes.c_double * npass)()
+    _check(lib().rte_time_passes(plan, int(inner), int(reps), out, VP(stream)), "rte_time_passes")
+    return list(out)
+
+
+def rte_kernel_launches():
+    return int(lib().rte_kernel_launches())
 
 
 def rte_destroy(plan):

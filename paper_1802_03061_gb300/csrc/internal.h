@@ -8,6 +8,10 @@
 #include "common.cuh"
 
 rte_status rte_cuda_fail(cudaError_t e, const char* what);
+// host-side count of kernel launches issued by the library (graph replays
+// add the kernel nodes they contain)
+void rte_count_launches(long k);
+extern "C" long long rte_kernel_launches(void);
 
 // Which linear map a pass sequence applies (Sec. 3.3, steps T.1 and T.2).
 enum MixKind { MIX_K = 0, MIX_RHS = 1 };
@@ -20,6 +24,7 @@ struct KrylovWs {
     double* part = nullptr;  // partial sums [RTE_DOT_CHUNKS_MAX][nblk]
     double* st = nullptr;    // device GMRES state (see krylov.cu)
     void* exec = nullptr;    // cached graph of one Arnoldi step
+    long long nodes = 0;     // kernels in that graph
 };
 
 struct rte_plan_s {
@@ -83,6 +88,8 @@ rte_status op2d_apply64(rte_plan p, MixKind kind, const double* x, const double*
                         double* out, double a, double b, double c, const double* z, cudaStream_t s);
 rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);
+rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s);
+rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s);
 // op3d.cu
 rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,
                         double c, const double* z, cudaStream_t s);

@@ -246,8 +246,10 @@ template <typename T>
 static rte_status dev_norm(const T* v, long nr, long nw1, double* part, double* out, cudaStream_t s) {
     dim3 g(DOT_NBLK, 1);
     k_dot_part<T><<<g, 256, 0, s>>>(v, nr, v, nullptr, 1, nw1, part);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_dot_finish<<<1, 256, 0, s>>>(part, DOT_NBLK, nullptr, 1, out, 1);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
@@ -265,6 +267,7 @@ static rte_status arnoldi_step(Gm<T>& G, cudaStream_t s) {
     const long nr = G.nr;
     const int gr = grid_for(nr);
     k_copy_vj<T><<<gr, 256, 0, s>>>(G.V, G.vin, nr, G.st);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     rte_status e = apply_A_T(G.p, G.vin, G.w, s);
     if (e != RTE_OK) return e;
@@ -272,26 +275,35 @@ static rte_status arnoldi_step(Gm<T>& G, cudaStream_t s) {
     const dim3 gd(DOT_NBLK, GM_MMAX / DOT_CHUNK);
     // pass 1
     k_dot_part<T><<<gd, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_dot_finish<<<1, 256, 0, s>>>(G.part, DOT_NBLK, jp, 1, G.st->hA, 0);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_multi_axpy<T><<<gr, 256, 0, s>>>(G.V, nr, G.w, G.st->hA, jp, 1, -1.0);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     // pass 2 (re-orthogonalisation)
     k_dot_part<T><<<gd, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_dot_finish<<<1, 256, 0, s>>>(G.part, DOT_NBLK, jp, 1, G.st->hB, 0);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_multi_axpy<T><<<gr, 256, 0, s>>>(G.V, nr, G.w, G.st->hB, jp, 1, -1.0);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     // norm, Givens, new basis vector
     rte_status e2 = dev_norm<T>(G.w, nr, G.nw1, G.part, &G.st->nrm, s);
     if (e2 != RTE_OK) return e2;
     k_givens<<<1, 1, 0, s>>>(G.st);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_scale_to_basis<T><<<gr, 256, 0, s>>>(G.w, G.V, nr, G.st);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     k_advance<<<1, 1, 0, s>>>(G.st);
+    rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
@@ -374,7 +386,11 @@ static rte_status gmres_T(rte_plan p, KrylovWs& ws, const T* rhs, T* x, bool x_z
         cudaStream_t cs;
         RTE_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         RTE_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const long long before = rte_kernel_launches();
         rte_status ce = arnoldi_step<T>(G, cs);
+        const long long captured = rte_kernel_launches() - before;
+        rte_count_launches(-captured);  // captured, not executed
+        ws.nodes = captured;
         cudaError_t ee = cudaStreamEndCapture(cs, &graph);
         cudaStreamDestroy(cs);
         if (ce != RTE_OK) { if (graph) cudaGraphDestroy(graph); return ce; }
@@ -397,14 +413,17 @@ static rte_status gmres_T(rte_plan p, KrylovWs& ws, const T* rhs, T* x, bool x_z
             e = apply_A_T(p, x, G.w, s);
             if (e != RTE_OK) { result = e; break; }
             k_rsub<T><<<gr, 256, 0, s>>>(rhs, G.w, nr);
+            rte_count_launches(1);
             RTE_CUDA_TRY(cudaGetLastError());
         }
         first = false;
         e = dev_norm<T>(G.w, nr, G.nw1, G.part, &G.st->nrm, s);
         if (e != RTE_OK) { result = e; break; }
         k_cycle_init<<<1, 1, 0, s>>>(G.st, m, target);
+        rte_count_launches(1);
         RTE_CUDA_TRY(cudaGetLastError());
         k_scale_inv<T, T><<<gr, 256, 0, s>>>(G.w, G.V, nr, &G.st->nrm);
+        rte_count_launches(1);
         RTE_CUDA_TRY(cudaGetLastError());
         HostStatus hs;
         e = read_status(G.st, &hs, pinned, s);
@@ -417,6 +436,7 @@ static rte_status gmres_T(rte_plan p, KrylovWs& ws, const T* rhs, T* x, bool x_z
         int steps = 0;
         while (true) {
             RTE_CUDA_TRY(cudaGraphLaunch(exec, s));
+            rte_count_launches(ws.nodes);
             ++steps;
             e = read_status(G.st, &hs, pinned, s);
             if (e != RTE_OK) { result = e; break; }
@@ -427,8 +447,10 @@ static rte_status gmres_T(rte_plan p, KrylovWs& ws, const T* rhs, T* x, bool x_z
         last_res = hs.res;
         // x += V y
         k_solve_tri<<<1, 1, 0, s>>>(G.st);
+        rte_count_launches(1);
         RTE_CUDA_TRY(cudaGetLastError());
         k_multi_axpy<T><<<gr, 256, 0, s>>>(G.V, nr, x, G.st->y, &G.st->j, 0, 1.0);
+        rte_count_launches(1);
         RTE_CUDA_TRY(cudaGetLastError());
         if (!isfinite(hs.res)) { result = RTE_ENAN; break; }
         if (hs.conv) break;
@@ -502,6 +524,7 @@ rte_status krylov_solve(rte_plan p, const double* f, double* u, const rte_opts* 
             const double tol_in = o->tol * bnorm / rn;
             result = gmres_T<double>(p, p->k64, p->r64, p->x64, true, tol_in * 0.5, m, o->maxit, &its, &est, s);
             k_add64<<<gr, 256, 0, s>>>(u, p->x64, nr);
+            rte_count_launches(1);
             RTE_CUDA_TRY(cudaGetLastError());
         }
         iters = its;
@@ -527,6 +550,7 @@ rte_status krylov_solve(rte_plan p, const double* f, double* u, const rte_opts* 
             p->hst[9] = rn;
             RTE_CUDA_TRY(cudaMemcpyAsync(p->dscal, p->hst + 9, sizeof(double), cudaMemcpyHostToDevice, s));
             k_scale_inv<double, float><<<gr, 256, 0, s>>>(p->r64, p->r32, nr, p->dscal);
+            rte_count_launches(1);
             RTE_CUDA_TRY(cudaGetLastError());
             float* d32 = p->d32;
             RTE_CUDA_TRY(cudaMemsetAsync(d32, 0, nr * sizeof(float), s));
@@ -542,6 +566,7 @@ rte_status krylov_solve(rte_plan p, const double* f, double* u, const rte_opts* 
             if (ie != RTE_OK && ie != RTE_ENOCONV) { result = ie; break; }
             // u += rn * d32
             k_axpy_scaled<float><<<gr, 256, 0, s>>>(u, d32, nr, p->dscal);
+            rte_count_launches(1);
             RTE_CUDA_TRY(cudaGetLastError());
         }
     }

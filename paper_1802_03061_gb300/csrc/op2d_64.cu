@@ -10,3 +10,12 @@ rte_status op2d_apply64(rte_plan p, MixKind kind, const double* x, const double*
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_apply64");
     return RTE_OK;
 }
+
+rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s) {
+    cudaError_t e = op2d_time<double2, double2>(
+        p, reinterpret_cast<const double2*>(p->x64), reinterpret_cast<double2*>(p->t64),
+        reinterpret_cast<double2*>(p->T64), reinterpret_cast<double2*>(p->Tsplit), p->S64, p->tw64,
+        p->col_split64, reps, ms, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_time64");
+    return RTE_OK;
+}

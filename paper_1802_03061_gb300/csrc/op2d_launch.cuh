@@ -80,10 +80,11 @@ static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, C
 }
 
 // out = a*x + b*(Op x) + c*z ; Op = K (MIX_K) or K~ on the source f (MIX_RHS)
+// stage: -1 all three passes; 0 row pass; 1 column pass; 2 inverse row pass
 template <typename T, typename TS>
 static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* f, T* out, double a, double b,
                             double c, const T* z, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
-                            cudaStream_t s) {
+                            cudaStream_t s, int stage = -1) {
     using R = typename real_of<T>::R;
     static bool once = false;
     cudaError_t e;
@@ -103,17 +104,51 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* 
         rp.wk[0] = 1.0;
     }
     const int nmod_in = kind == MIX_K ? p->L + 1 : 1;
-    const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
     const size_t smr = row_smem<T>(p->Q, rp.RB);
-    k_row_fwd<T><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw, rp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ColParams cp;
-    cp.n = p->n; cp.Q = p->Q; cp.H = p->H; cp.L = p->L;
-    cp.nin = kind == MIX_K ? p->nch : 1;
-    cp.G = 1;
-    cp.sc = p->sched;
-    if ((e = dispatch_col<T, TS>(p->L, Tb, Ts, S, tw, cp, split, s)) != cudaSuccess) return e;
-    const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
-    k_row_inv<T><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b, (R)c);
-    return cudaGetLastError();
+    if (stage < 0 || stage == 0) {
+        const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
+        k_row_fwd<T><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw, rp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        rte_count_launches(1);
+    }
+    if (stage < 0 || stage == 1) {
+        ColParams cp;
+        cp.n = p->n; cp.Q = p->Q; cp.H = p->H; cp.L = p->L;
+        cp.nin = kind == MIX_K ? p->nch : 1;
+        cp.G = 1;
+        cp.sc = p->sched;
+        if ((e = dispatch_col<T, TS>(p->L, Tb, Ts, S, tw, cp, split, s)) != cudaSuccess) return e;
+        rte_count_launches(split ? 3 : 1);
+    }
+    if (stage < 0 || stage == 2) {
+        const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
+        k_row_inv<T><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b, (R)c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        rte_count_launches(1);
+    }
+    return cudaSuccess;
+}
+
+// average duration of each pass over `reps` back-to-back launches (CUDA
+// events on stream s); ms[0..2] = row, column, inverse row
+template <typename T, typename TS>
+static cudaError_t op2d_time(rte_plan p, const T* x, T* out, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
+                             int reps, double* ms, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = op2d_run<T, TS>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[st] = t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
 }

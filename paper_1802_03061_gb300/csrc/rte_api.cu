@@ -16,6 +16,17 @@ rte_status rte_cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* rte_last_error(void) { return g_last_error; }
 
+static long long g_launches = 0;
+void rte_count_launches(long k) { __atomic_add_fetch(&g_launches, (long long)k, __ATOMIC_RELAXED); }
+extern "C" long long rte_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+extern "C" rte_status rte_time_passes(rte_plan p, int inner, int reps, double* ms_out, void* stream) {
+    if (!p || !ms_out || reps < 1) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->dim != 2) return RTE_EUNSUPPORTED;
+    return inner ? op2d_time32(p, reps, ms_out, s) : op2d_time64(p, reps, ms_out, s);
+}
+
 extern "C" const char* rte_status_str(rte_status s) {
     switch (s) {
         case RTE_OK: return "ok";
