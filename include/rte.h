@@ -155,6 +155,30 @@ rte_status rte_plan_cell_weights(rte_plan plan, double* out_host);
 rte_status rte_time_passes(rte_plan plan, int inner, int reps, double* ms_out_host, void* cuda_stream);
 long long rte_kernel_launches(void);
 
+/* y = K x for a small 2D grid with no device allocation at all.  For
+ * callers that may not allocate device memory where they call: plug-ins
+ * whose host application owns and caps all device memory, real-time loops
+ * that forbid allocator calls after start-up, code that runs while another
+ * component holds the whole device allocator.  Such callers cannot create a
+ * plan (rte_plan_create allocates), so this call rebuilds the plan data
+ * (cell weights, kernel samples, spectra) and the pass intermediates on
+ * every call inside one fixed static device array of
+ * rte_noalloc_scratch_bytes() bytes (about 5 MB), which every GPU that loads
+ * the library holds until process exit; then it applies the same FP64
+ * passes as rte_apply_K.  Arguments as rte_plan_create + rte_apply_K:
+ * x_dev, y_dev are caller-owned FP64 mode fields double2 [L+1][n][n] that
+ * may not alias; sigma_hat is a host array of L+1 values.  Limits: n <= 64
+ * and L <= 4; larger sizes return RTE_EUNSUPPORTED (use a plan).  The first
+ * call on a device looks up the array's device address (a lookup, not an
+ * allocation); make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents; calls whose work
+ * overlaps on the GPU race on it, so the caller must serialise them.
+ * Asynchronous on cuda_stream.  (The paper has no counterpart of this
+ * entry point.) */
+rte_status rte_apply_K_noalloc(int n, double h, double mu_t, double mu_s, int L, const double* sigma_hat,
+                               const void* x_dev, void* y_dev, void* cuda_stream);
+long long rte_noalloc_scratch_bytes(void);
+
 /* Free all device memory of the plan.  NULL is accepted. */
 rte_status rte_destroy(rte_plan plan);
 

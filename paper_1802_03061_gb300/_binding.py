@@ -68,6 +68,10 @@ def lib():
         L.rte_time_passes.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
         L.rte_time_passes.restype = ctypes.c_int
         L.rte_kernel_launches.restype = ctypes.c_longlong
+        L.rte_apply_K_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP, VP, VP]
+        L.rte_apply_K_noalloc.restype = ctypes.c_int
+        L.rte_noalloc_scratch_bytes.restype = ctypes.c_longlong
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
         L.rte_last_error.restype = ctypes.c_char_p
@@ -163,6 +167,16 @@ def rte_time_passes(plan, inner, reps, stream=0, npass=3):
 
 def rte_kernel_launches():
     return int(lib().rte_kernel_launches())
+
+
+def rte_apply_K_noalloc(n, h, mu_t, mu_s, L, sigma_hat, x, y, stream=0):
+    sig = (ctypes.c_double * (L + 1))(*[float(v) for v in sigma_hat[:L + 1]])
+    _check(lib().rte_apply_K_noalloc(int(n), float(h), float(mu_t), float(mu_s), int(L), sig, VP(x), VP(y),
+                                     VP(stream)), "rte_apply_K_noalloc")
+
+
+def rte_noalloc_scratch_bytes():
+    return int(lib().rte_noalloc_scratch_bytes())
 
 
 def rte_destroy(plan):

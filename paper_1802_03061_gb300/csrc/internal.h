@@ -80,6 +80,13 @@ struct rte_plan_s {
 
 // spectra.cu
 rte_status plan_build_spectra(rte_plan p, cudaStream_t s);
+rte_status fft_lines_host(double2* data, const FftSched& sc, const double2* tw, long nlines, long nA, long sA,
+                          long sB, long sE, cudaStream_t s);
+__global__ void k_twiddles(double2* tw64, float2* tw32, int Q);
+__global__ void k_cell_weights_2d(double mu, double h, int mmax, double* D);
+__global__ void k_sample_2d(double2* G, int n, int Q, int mmax, double h, double mu, const double* D);
+__global__ void k_extract_2d(const double2* G, int Q, int H, int nm, double2* S64, float2* S32,
+                             __nv_bfloat162* S16);
 void make_sched(FftSched* s, int Q);
 int choose_Q(int n);
 
@@ -90,6 +97,9 @@ rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b
                         const float* z, cudaStream_t s);
 rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s);
 rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s);
+// op2d_64.cu: the FP64 passes on explicit buffers (no plan-owned scratch)
+rte_status op2d_apply64_buffers(rte_plan p, const double* x, double* out, double2* Tb, const double2* S64,
+                                const double2* tw64, cudaStream_t s);
 // op3d.cu
 rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,
                         double c, const double* z, cudaStream_t s);

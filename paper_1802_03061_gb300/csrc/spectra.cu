@@ -237,7 +237,7 @@ __global__ void k_fft_lines64(double2* data, FftSched sc, const double2* tw, lon
     }
 }
 
-static rte_status fft_lines_host(double2* data, const FftSched& sc, const double2* tw, long nlines,
+rte_status fft_lines_host(double2* data, const FftSched& sc, const double2* tw, long nlines,
                                  long nA, long sA, long sB, long sE, cudaStream_t s) {
     const int Q = sc.Q;
     int LPB = 4096 / Q;
