@@ -18,14 +18,19 @@ enum MixKind { MIX_K = 0, MIX_RHS = 1 };
 
 // Krylov workspace of one precision.
 struct KrylovWs {
-    int m = 0;             // restart length (basis holds m+1 vectors)
-    void* V = nullptr;     // (m+1) x nr reals (float or double)
-    void* w = nullptr;     // nr reals
-    double* part = nullptr;  // partial sums [RTE_DOT_CHUNKS_MAX][nblk]
+    int m = 0;               // restart length (basis holds m+2 vectors; slot m+1 = matvec input)
+    void* V = nullptr;       // (m+2) x nr reals (float or double)
+    void* w = nullptr;       // nr reals
+    double* part = nullptr;  // partial sums [(m+1)][tiles]
     double* st = nullptr;    // device GMRES state (see krylov.cu)
-    void* exec = nullptr;    // cached graph of one Arnoldi step
-    long long nodes = 0;     // kernels in that graph
+    void* exec_first = nullptr;    // cycle graph, x = 0 on entry
+    void* exec_restart = nullptr;  // cycle graph, residual from x
+    long long nodes_first = 0, nodes_restart = 0, nodes_body = 0;
+    int key = -1;                  // precision / orthogonalisation the graphs were made for
+    const void* rhs = nullptr;     // vectors the graphs are bound to
+    void* x = nullptr;
 };
+void krylov_free_ws(KrylovWs& ws);
 
 struct rte_plan_s {
     int dim = 2;
@@ -69,6 +74,7 @@ struct rte_plan_s {
     float* r32 = nullptr;
     float* d32 = nullptr;
     double* dscal = nullptr;  // device scalar (residual norm)
+    double* part64 = nullptr; // partial sums of plan-level norms
     // host-side staging for rte_solve_host
     double* f_dev = nullptr;
     double* u_dev = nullptr;

@@ -84,7 +84,7 @@ extern "C" rte_status rte_destroy(rte_plan p) {
     krylov_free(p);
     void* bufs[] = {p->tw64, p->tw32, p->S64, p->S32, p->S16, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
-                    p->d32, p->dscal, p->f_dev, p->u_dev};
+                    p->d32, p->dscal, p->part64, p->f_dev, p->u_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->hst) cudaFreeHost(p->hst);
@@ -183,6 +183,7 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     TRY(dalloc(&p->r32, p->nr * sizeof(float)));
     TRY(dalloc(&p->d32, p->nr * sizeof(float)));
     TRY(dalloc(&p->dscal, 8 * sizeof(double)));
+    TRY(dalloc(&p->part64, (size_t)((p->nr + 2047) / 2048 + 1) * sizeof(double)));
     TRY(dalloc(&p->f_dev, p->ncell * sizeof(double)));
     TRY(dalloc(&p->u_dev, p->nr * sizeof(double)));
     if (cudaMallocHost((void**)&p->hst, 64 * sizeof(double)) != cudaSuccess) {
