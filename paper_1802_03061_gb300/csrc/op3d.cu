@@ -1,7 +1,262 @@
-// placeholder, replaced by the 3D passes
+// 3D isotropic operator passes: y = a*x + b*(K x) + c*z  (or b*(K~ f)).
+//
+// Sec. 2.3.1 with d = 3: kappa(r) = exp(-mu_t|r|)/(4 pi |r|^2) is a
+// convolution on the zero-padded Q^3 grid, so K x = mu_s * iFFT(S * FFT(x)),
+// with the real, even spectrum S stored as its octant [H][H][H].  Passes:
+//   X  : two real rows packed into one complex FFT along x, split into the
+//        half spectra xi_x = 0..Q/2              -> T1[z][xi_x][y]
+//   Y  : FFT along y (zero padded), per (z, xi_x) -> T2[xi_x][xi_y][z]
+//   Z  : FFT along z, multiply by S, inverse FFT, keep z < n (in place)
+//   Y' : inverse FFT along y, keep y < n           -> T1[z][xi_x][y]
+//   X' : Hermitian completion of two rows, inverse complex FFT, keep x < n,
+//        epilogue.
+// Each intermediate is laid out so that the next pass reads contiguous lines.
+#include "fft.cuh"
 #include "internal.h"
-rte_status op3d_apply64(rte_plan, MixKind, const double*, double*, double, double, double, const double*,
-                        cudaStream_t) { return RTE_EUNSUPPORTED; }
-rte_status op3d_apply32(rte_plan, const float*, float*, float, float, float, const float*, cudaStream_t) {
-    return RTE_EUNSUPPORTED;
+
+#define RTE_SMEM_OPTIN 232448
+
+struct P3 {
+    int n, Q, H, B;  // B: lines (rows / z values / columns) per block
+    FftSched sc;
+};
+
+__device__ __forceinline__ int fold(int a, int Q) { return a <= Q / 2 ? a : Q - a; }
+
+// X: in real [n][n][n] (x fastest); grid (ceil(n/B), n), B even
+template <typename T, typename R>
+__global__ void __launch_bounds__(256) k3_x_fwd(const R* __restrict__ x, T* __restrict__ T1, const T* __restrict__ tw,
+                                                P3 p, double w) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, B = p.B;
+    const int z = blockIdx.y, y0 = blockIdx.x * B, nl = B / 2;
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)nl * Q;
+    load_twiddles(twl, tw, Q);
+    using RR = typename real_of<T>::R;
+    const RR ww = (RR)w;
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx / Q, e = idx - li * Q;
+        const int ya = y0 + 2 * li, yb = ya + 1;
+        RR a = 0, b = 0;
+        if (e < n) {
+            if (ya < n) a = (RR)x[((long)z * n + ya) * n + e];
+            if (yb < n) b = (RR)x[((long)z * n + yb) * n + e];
+        }
+        buf[idx] = mk<T>(ww * a, ww * b);
+    }
+    __syncthreads();
+    T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < H * B; idx += blockDim.x) {
+        const int r = idx % B, xi = idx / B;
+        const int y = y0 + r;
+        if (y >= n) continue;
+        const int line = r >> 1;
+        const T Z = res[line * Q + xi];
+        const T Zm = res[line * Q + (xi == 0 ? 0 : Q - xi)];
+        T v;
+        if ((r & 1) == 0) v = mk<T>((RR)0.5 * (Z.x + Zm.x), (RR)0.5 * (Z.y - Zm.y));
+        else v = mk<T>((RR)0.5 * (Z.y + Zm.y), (RR)-0.5 * (Z.x - Zm.x));
+        T1[((long)z * H + xi) * n + y] = v;
+    }
+}
+
+// Y: T1[z][xi_x][y] -> T2[xi_x][xi_y][z]; grid (ceil(n/B), H): B consecutive z
+template <typename T>
+__global__ void __launch_bounds__(256) k3_y_fwd(const T* __restrict__ T1, T* __restrict__ T2, const T* __restrict__ tw,
+                                                P3 p) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, B = p.B;
+    const int kx = blockIdx.y, z0 = blockIdx.x * B;
+    const int nl = min(B, n - z0);
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)B * Q;
+    load_twiddles(twl, tw, Q);
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx / Q, e = idx - li * Q;
+        buf[idx] = e < n ? T1[((long)(z0 + li) * H + kx) * n + e] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx % nl, ky = idx / nl;
+        T2[((long)kx * Q + ky) * n + z0 + li] = res[li * Q + ky];
+    }
+}
+
+// Z: per (xi_x, xi_y) line along z: FFT, * S, iFFT, keep z < n; grid ceil(H*Q/B)
+template <typename T, typename TS>
+__global__ void __launch_bounds__(256) k3_z_mix(T* __restrict__ T2, const TS* __restrict__ S, const T* __restrict__ tw,
+                                                P3 p) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    using RR = typename real_of<T>::R;
+    const int n = p.n, Q = p.Q, H = p.H, B = p.B;
+    const long l0 = (long)blockIdx.x * B;
+    const long nlines = (long)H * Q;
+    const int nl = (int)min((long)B, nlines - l0);
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)B * Q;
+    load_twiddles(twl, tw, Q);
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx / Q, e = idx - li * Q;
+        buf[idx] = e < n ? T2[(l0 + li) * n + e] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx / Q, kz = idx - li * Q;
+        const long l = l0 + li;
+        const int kx = (int)(l / Q), ky = (int)(l % Q);
+        const RR s = (RR)S[((long)kx * H + fold(ky, Q)) * H + fold(kz, Q)];
+        res[idx] = cscale(res[idx], s);
+    }
+    __syncthreads();
+    T* other = (res == buf) ? tmp : buf;
+    T* res2 = fft_lines<1>(res, other, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        const int li = idx / n, e = idx - li * n;
+        T2[(l0 + li) * n + e] = res2[li * Q + e];
+    }
+}
+
+// Y': T2[xi_x][xi_y][z] -> T1[z][xi_x][y], y < n; grid (ceil(n/B), H)
+template <typename T>
+__global__ void __launch_bounds__(256) k3_y_inv(const T* __restrict__ T2, T* __restrict__ T1, const T* __restrict__ tw,
+                                                P3 p) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, B = p.B;
+    const int kx = blockIdx.y, z0 = blockIdx.x * B;
+    const int nl = min(B, n - z0);
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)B * Q;
+    load_twiddles(twl, tw, Q);
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
+        const int li = idx % nl, ky = idx / nl;
+        buf[li * Q + ky] = T2[((long)kx * Q + ky) * n + z0 + li];
+    }
+    __syncthreads();
+    T* res = fft_lines<1>(buf, tmp, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        const int li = idx / n, e = idx - li * n;
+        T1[((long)(z0 + li) * H + kx) * n + e] = res[li * Q + e];
+    }
+}
+
+// X': T1[z][xi_x][y] -> out[z][y][x] = a*x + b*v + c*zv; grid (ceil(n/B), n)
+template <typename T, typename R>
+__global__ void __launch_bounds__(256) k3_x_inv(const T* __restrict__ T1, const R* __restrict__ x,
+                                                const R* __restrict__ zv, R* __restrict__ out, const T* __restrict__ tw,
+                                                P3 p, double a, double b, double c) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, B = p.B;
+    const int z = blockIdx.y, y0 = blockIdx.x * B, nl = B / 2;
+    T* twl = sm;
+    T* buf = sm + Q;
+    T* tmp = buf + (long)nl * Q;
+    load_twiddles(twl, tw, Q);
+    for (int idx = threadIdx.x; idx < H * nl; idx += blockDim.x) {
+        const int li = idx % nl, xi = idx / nl;
+        const int ya = y0 + 2 * li, yb = ya + 1;
+        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
+        if (ya < n) Fv = T1[((long)z * H + xi) * n + ya];
+        if (yb < n) Gv = T1[((long)z * H + xi) * n + yb];
+        buf[li * Q + xi] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) buf[li * Q + (Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+    }
+    __syncthreads();
+    T* res = fft_lines<1>(buf, tmp, nl, Q, p.sc, twl);
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        const int li = idx / n, e = idx - li * n;
+        const T v = res[li * Q + e];
+        const int ya = y0 + 2 * li, yb = ya + 1;
+        if (ya < n) {
+            const long o = ((long)z * n + ya) * n + e;
+            double r = b * (double)v.x;
+            if (x) r += a * (double)x[o];
+            if (zv) r += c * (double)zv[o];
+            out[o] = (R)r;
+        }
+        if (yb < n) {
+            const long o = ((long)z * n + yb) * n + e;
+            double r = b * (double)v.y;
+            if (x) r += a * (double)x[o];
+            if (zv) r += c * (double)zv[o];
+            out[o] = (R)r;
+        }
+    }
+}
+
+template <typename K> static cudaError_t allow(K k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, RTE_SMEM_OPTIN);
+}
+
+template <typename T> static int lines_per_block(int Q) {
+    int b = 65536 / (2 * Q * (int)sizeof(T));
+    if (b > 16) b = 16;
+    if (b < 2) b = 2;
+    return b & ~1;
+}
+
+template <typename T, typename R, typename TS>
+static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, double b, double c, const R* z,
+                            T* T1, T* T2, const TS* S, const T* tw, cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow(k3_x_fwd<T, R>)) != cudaSuccess) return e;
+        if ((e = allow(k3_y_fwd<T>)) != cudaSuccess) return e;
+        if ((e = allow(k3_z_mix<T, TS>)) != cudaSuccess) return e;
+        if ((e = allow(k3_y_inv<T>)) != cudaSuccess) return e;
+        if ((e = allow(k3_x_inv<T, R>)) != cudaSuccess) return e;
+        once = true;
+    }
+    P3 pp;
+    pp.n = p->n;
+    pp.Q = p->Q;
+    pp.H = p->H;
+    pp.sc = p->sched;
+    const int n = p->n, Q = p->Q, H = p->H;
+    pp.B = lines_per_block<T>(Q);
+    const int B = pp.B;
+    const size_t smx = (size_t)(Q + 2 * (B / 2) * Q) * sizeof(T);
+    const size_t smy = (size_t)(Q + 2 * B * Q) * sizeof(T);
+    k3_x_fwd<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(x, T1, tw, pp, w);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k3_y_fwd<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T1, T2, tw, pp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long nz = ((long)H * Q + B - 1) / B;
+    k3_z_mix<T, TS><<<(unsigned)nz, 256, smy, s>>>(T2, S, tw, pp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k3_y_inv<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T2, T1, tw, pp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k3_x_inv<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(T1, x, z, out, tw, pp, a, b, c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    rte_count_launches(5);
+    return cudaSuccess;
+}
+
+rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
+                        const double* z, cudaStream_t s) {
+    const double w = kind == MIX_K ? p->mu_s : 1.0;
+    cudaError_t e = op3d_run<double2, double, double>(p, x, out, w, kind == MIX_K ? a : 0.0, b, c, z,
+                                                      (double2*)p->T64, (double2*)p->U64, p->S3_64, p->tw64, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply64");
+    return RTE_OK;
+}
+
+rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c, const float* z,
+                        cudaStream_t s) {
+    cudaError_t e = op3d_run<float2, float, float>(p, x, out, p->mu_s, a, b, c, z, (float2*)p->T32, (float2*)p->U32,
+                                                   p->S3_32, p->tw32, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply32");
+    return RTE_OK;
 }

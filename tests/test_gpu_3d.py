@@ -1,0 +1,111 @@
+"""GPU parity of the 3D isotropic path (C ABI) against the oracle.
+
+Tolerances as in the 2D tests: FP64 1e-12 relative L2, FP32 1e-5, solves
+within cond_est * tol, cond_est = (1 + mu_s/mu_t)/(1 - mu_s/mu_t).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import rte_synth
+from _util import rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_03061_gb300 import build
+    build.build()
+
+
+def _plan(n, mu_t, mu_s, **kw):
+    from paper_1802_03061_gb300 import Plan
+    return Plan(n, mu_t=mu_t, mu_s=mu_s, sigma_hat=[1.0], dim=3, **kw)
+
+
+CASES = [(1, 1.0, 0.5), (2, 2.0, 1.0), (3, 5.0, 4.0), (6, 3.0, 2.9), (9, 30.0, 29.0), (16, 100.0, 99.5)]
+
+
+@pytest.mark.parametrize("n,mu_t,mu_s", CASES)
+def test_cell_weight_3d(n, mu_t, mu_s):
+    p = _plan(n, mu_t, mu_s)
+    assert p.cell_weights()[0] == pytest.approx(oracle.cell_weight_3d(mu_t, 1.0 / n), rel=1e-13)
+    p.close()
+
+
+@pytest.mark.parametrize("n,mu_t,mu_s", CASES)
+def test_apply_K_3d_fp64_matches_direct_sum(n, mu_t, mu_s):
+    p = _plan(n, mu_t, mu_s)
+    x = np.random.default_rng(n).standard_normal((n, n, n))
+    y = p.apply_K(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.apply_K_3d(n, 1.0 / n, mu_t, mu_s, x)
+    assert rel(y, ref) < 1e-12
+    ya = p.apply_A(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(ya, x - ref) < 1e-12
+    b = p.rhs(torch.from_numpy(x)).cpu().numpy()
+    assert rel(b, ref / mu_s) < 1e-12
+    p.close()
+
+
+@pytest.mark.parametrize("n", [6, 16])
+def test_apply_K32_3d(n):
+    p = _plan(n, 10.0, 9.0, prec="mixed_fp32")
+    x = np.random.default_rng(1).standard_normal((n, n, n)).astype(np.float32)
+    y = p.apply_K32(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.apply_K_3d(n, 1.0 / n, 10.0, 9.0, x.astype(np.float64))
+    assert rel(y, ref) < 1e-5
+    p.close()
+
+
+def test_apply_K_3d_full_size_sampled():
+    """128^3 (zero padded to 256^3), mu_t = 100, mu_s = 99.5: FP64 K x against
+    the oracle's direct sum at sampled cells."""
+    n = 128
+    p = _plan(n, 100.0, 99.5)
+    x = rte_synth.iso3d_diffusion()["f"]
+    y = p.apply_K(torch.from_numpy(x).cuda()).cpu().numpy()
+    # cells where the field is significant: relative L2 at 1e-12; far cells
+    # (values down to 1e-30 of the peak): absolute error at FP64 rounding of the peak
+    rng = np.random.default_rng(2)
+    support = np.flatnonzero(x.reshape(-1) > 1e-2 * x.max())
+    near = rng.choice(support, size=24, replace=False)
+    ref = oracle.apply_K_3d(n, 1.0 / n, 100.0, 99.5, x, rows=near)
+    assert rel(y.reshape(-1)[near], ref) < 1e-12
+    far = rng.choice(n ** 3, size=24, replace=False)
+    ref_far = oracle.apply_K_3d(n, 1.0 / n, 100.0, 99.5, x, rows=far)
+    assert np.abs(y.reshape(-1)[far] - ref_far).max() < 1e-14 * np.abs(ref).max()
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_solve_3d_small_against_dense(prec):
+    n, mu_t, mu_s = 8, 20.0, 19.0
+    f = rte_synth.gaussian_3d(n, (0.45, 0.5, 0.55), 0.15)
+    p = _plan(n, mu_t, mu_s, prec=prec)
+    u_ref, _ = oracle.solve_dense_3d(n, 1.0 / n, mu_t, mu_s, f)
+    u, st = p.solve(torch.from_numpy(f), tol=1e-10)
+    assert st["converged"] and st["relres_true"] <= 1e-10
+    cond = (1 + mu_s / mu_t) / (1 - mu_s / mu_t)
+    assert rel(u.cpu().numpy(), u_ref) <= 2 * cond * 1e-10
+    p.close()
+
+
+def test_solve_3d_diffusion_full_size():
+    """The 128^3 diffusion-regime workload (mu_t = 100, mu_s = 99.5) in the
+    mixed mode: converged to 1e-8, and the oracle's FP64 direct-sum residual
+    at sampled cells agrees."""
+    prob = rte_synth.iso3d_diffusion()
+    n = prob["n"]
+    p = _plan(n, prob["mu_t"], prob["mu_s"], prec="mixed_fp32", restart=60, maxit=3000)
+    u, st = p.solve(torch.from_numpy(prob["f"]), tol=1e-8)
+    assert st["converged"] and st["relres_true"] <= 1e-8
+    # sample where the source is significant (far away b is ~e^-30 of its peak)
+    support = np.flatnonzero(prob["f"].reshape(-1) > 1e-2 * prob["f"].max())
+    rows = np.random.default_rng(5).choice(support, size=16, replace=False)
+    r, b = oracle.sampled_residual_3d(n, 1.0 / n, prob["mu_t"], prob["mu_s"], prob["f"], u.cpu().numpy(), rows)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
+    p.close()
