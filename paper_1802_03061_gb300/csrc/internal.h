@@ -23,14 +23,18 @@ struct KrylovWs {
     void* w = nullptr;       // nr reals
     double* part = nullptr;  // partial sums [(m+1)][tiles]
     double* st = nullptr;    // device GMRES state (see krylov.cu)
-    void* exec_first = nullptr;    // cycle graph, x = 0 on entry
-    void* exec_restart = nullptr;  // cycle graph, residual from x
-    long long nodes_first = 0, nodes_restart = 0, nodes_body = 0;
-    int key = -1;                  // precision / orthogonalisation the graphs were made for
-    const void* rhs = nullptr;     // vectors the graphs are bound to
-    void* x = nullptr;
 };
 void krylov_free_ws(KrylovWs& ws);
+
+// kernels per graph segment of a captured solve (for launch accounting)
+struct SolveGraphInfo {
+    long long k_fixed = 0, k_guess = 0, k_outer = 0, k_cycle = 0, k_step = 0, k_restart = 0;
+};
+struct SolveGraph {
+    void* exec = nullptr;  // cudaGraphExec_t of the whole solve
+    int m = 0;
+    SolveGraphInfo info;
+};
 
 struct rte_plan_s {
     int dim = 2;
@@ -79,6 +83,8 @@ struct rte_plan_s {
     double* f_dev = nullptr;
     double* u_dev = nullptr;
     KrylovWs k64, k32;
+    SolveGraph graphs[3];    // per precision mode
+    void* ref = nullptr;     // device refinement state (krylov.cu)
     double* hst = nullptr;   // pinned host mirror of small device state (64 doubles)
     double ms_pre = 0.0;
     int nsm = 152;
@@ -112,10 +118,15 @@ rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, 
 rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);
 
-// krylov.cu
-rte_status krylov_solve(rte_plan p, const double* f, double* u, const rte_opts* o, rte_stats* st,
-                        cudaStream_t s);
+// krylov.cu: the solve reads p->f_dev and writes p->u_dev
+rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* st, cudaStream_t s);
 rte_status krylov_free(rte_plan p);
+size_t refdev_size();
+rte_status solve_graph_append(rte_plan p, int prec, int m, cudaGraph_t g, cudaGraphNode_t* dep, cudaStream_t cs,
+                              SolveGraphInfo* info);
+rte_status solve_set_options(rte_plan p, const rte_opts* o, cudaStream_t s);
+struct RefDev;
+rte_status solve_collect(rte_plan p, int prec, const RefDev* host_ref, rte_stats* stats, double ms);
 
 // dispatch helpers (rte_api.cu)
 rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,

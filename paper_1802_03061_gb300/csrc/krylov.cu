@@ -11,11 +11,14 @@
 // Arnoldi: classical Gram-Schmidt, once (FP32 inner solves) or twice (FP64),
 // as a single-pass multi-dot over the basis and a fused multi-axpy + norm.
 // The Hessenberg matrix, Givens rotations and residual estimate live in
-// device memory (FP64) and are updated by one warp.  A whole restart cycle is
-// one CUDA graph: residual, normalisation, then a conditional WHILE node whose
-// body is one Arnoldi step (the Givens kernel clears the condition when the
-// cycle ends), then the triangular solve and the update of x.  The host waits
-// once per cycle.
+// device memory (FP64) and are updated by one warp.
+//
+// The whole solve is one CUDA graph with device-side control: T.1, then a
+// conditional WHILE over refinement steps, inside it a WHILE over GMRES
+// restart cycles, inside that a WHILE over Arnoldi steps (an IF node
+// recomputes the residual for a restart).  Small one-thread kernels decide
+// the loop conditions from FP64 state in device memory, so the host only
+// launches the graph and reads the statistics at the end.
 #include <math.h>
 #include <stddef.h>
 #include <stdio.h>
@@ -34,7 +37,7 @@ struct GmresDev {
     int m;       // restart length
     int maxit;
     int cgs2;    // 1: re-orthogonalise
-    int pad;
+    int cycle;   // restart cycles done in this inner solve
     double tol;     // relative tolerance (set by the host before each solve)
     double target;  // absolute residual target tol * ||rhs||
     double beta;
@@ -192,10 +195,10 @@ __global__ void k_scale_basis(const T* __restrict__ w, T* __restrict__ V, T* __r
 }
 
 // start of a cycle: the residual norm is in st->nrm
-__global__ void k_cycle_init(GmresDev* st, int first, cudaGraphConditionalHandle loop) {
+__global__ void k_cycle_init(GmresDev* st, cudaGraphConditionalHandle loop) {
     if (threadIdx.x != 0) return;
     const double nrm = st->nrm;
-    if (first) {
+    if (st->cycle == 0) {
         st->bnorm = nrm;
         st->target = st->tol * nrm;
     }
@@ -267,8 +270,116 @@ __global__ void k_solve_tri(GmresDev* st) {
     }
 }
 
+
 // --------------------------------------------------------------------------
-// host side
+// refinement / solve control (one thread each)
+// --------------------------------------------------------------------------
+struct RefDev {
+    int outer, max_outer, its, maxit;
+    int use_guess, mixed, cycles, restarts;
+    int status, pad0, pad1, pad2;
+    double tol, inner_tol, bnorm, rnorm, relres;
+};
+
+__global__ void k_copy_vec(const double* __restrict__ src, double* __restrict__ dst, long nr) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
+template <typename T>
+__global__ void k_copy_T(const T* __restrict__ src, T* __restrict__ dst, long nr) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
+template <typename T>
+__global__ void k_zero_T(T* __restrict__ dst, long nr) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
+        dst[e] = (T)0;
+}
+
+__global__ void k_zero_unless_guess(double* __restrict__ u, long nr, const RefDev* __restrict__ ref) {
+    if (ref->use_guess) return;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
+        u[e] = 0.0;
+}
+
+// after ||b||: start values; the guess branch runs only with a guess
+__global__ void k_ref_start(RefDev* ref, cudaGraphConditionalHandle c_guess) {
+    if (threadIdx.x != 0) return;
+    const double b = ref->bnorm;
+    ref->rnorm = b;
+    ref->relres = b > 0.0 ? 1.0 : 0.0;
+    ref->outer = 0;
+    ref->its = 0;
+    ref->cycles = 0;
+    ref->restarts = 0;
+    ref->status = isfinite(b) ? 0 : 7;
+    cudaGraphSetConditional(c_guess, (ref->use_guess && b > 0.0 && isfinite(b)) ? 1u : 0u);
+}
+
+__global__ void k_ref_relres(RefDev* ref) {
+    if (threadIdx.x != 0) return;
+    ref->relres = ref->bnorm > 0.0 ? ref->rnorm / ref->bnorm : 0.0;
+}
+
+__global__ void k_ref_gate(RefDev* ref, cudaGraphConditionalHandle c_outer) {
+    if (threadIdx.x != 0) return;
+    const bool fin = isfinite(ref->relres) && isfinite(ref->bnorm);
+    if (!fin) ref->status = 7;
+    const bool go = fin && ref->bnorm > 0.0 && ref->relres > ref->tol && ref->its < ref->maxit;
+    cudaGraphSetConditional(c_outer, go ? 1u : 0u);
+}
+
+// inner GMRES start: tolerance relative to its right-hand side
+__global__ void k_gm_start(GmresDev* st, const RefDev* ref, int m, int cgs2, cudaGraphConditionalHandle c_cycle) {
+    if (threadIdx.x != 0) return;
+    st->m = m;
+    st->cgs2 = cgs2;
+    st->its = 0;
+    st->cycle = 0;
+    const int left = ref->maxit - ref->its;
+    st->maxit = left < 1 ? 1 : left;
+    double tin;
+    if (ref->mixed) {
+        // the inner solve need not go beyond what the outer target needs
+        tin = ref->inner_tol;
+        const double need = ref->relres > 0.0 ? 0.5 * ref->tol / ref->relres : 1.0;
+        if (need > tin) tin = need;
+    } else {
+        tin = ref->rnorm > 0.0 ? 0.5 * ref->tol * ref->bnorm / ref->rnorm : 1.0;
+    }
+    st->tol = tin;
+    cudaGraphSetConditional(c_cycle, 1u);
+}
+
+__global__ void k_cycle_end(GmresDev* st, RefDev* ref, cudaGraphConditionalHandle c_cycle,
+                            cudaGraphConditionalHandle c_restart) {
+    if (threadIdx.x != 0) return;
+    st->cycle += 1;
+    ref->cycles += 1;
+    const bool cont = !st->conv && st->its < st->maxit && st->j > 0 && isfinite(st->res);
+    if (cont) ref->restarts += 1;
+    cudaGraphSetConditional(c_cycle, cont ? 1u : 0u);
+    cudaGraphSetConditional(c_restart, cont ? 1u : 0u);
+}
+
+__global__ void k_ref_after(RefDev* ref, const GmresDev* st) {
+    if (threadIdx.x != 0) return;
+    ref->its += st->its;
+    ref->outer += 1;
+}
+
+__global__ void k_ref_check(RefDev* ref, cudaGraphConditionalHandle c_outer) {
+    if (threadIdx.x != 0) return;
+    ref->relres = ref->bnorm > 0.0 ? ref->rnorm / ref->bnorm : 0.0;
+    const bool fin = isfinite(ref->relres);
+    if (!fin) ref->status = 7;
+    const bool go = fin && ref->relres > ref->tol && ref->outer < ref->max_outer && ref->its < ref->maxit;
+    cudaGraphSetConditional(c_outer, go ? 1u : 0u);
+}
+// --------------------------------------------------------------------------
+// host side: graph construction
 // --------------------------------------------------------------------------
 static int grid_for(long nr) {
     long g = (nr + 255) / 256;
@@ -283,18 +394,6 @@ static rte_status apply_A_T(rte_plan p, const float* x, float* y, cudaStream_t s
     return plan_apply32(p, x, y, 1.0f, -1.0f, 0.0f, nullptr, s);
 }
 
-template <typename T> struct Gm {
-    rte_plan p;
-    KrylovWs* ws;
-    T* V;
-    T* w;
-    T* vin;
-    GmresDev* st;
-    double* part;
-    long nr, nw1;
-    int m;
-};
-
 // weighted norm of v into *out (device)
 template <typename T>
 static rte_status dev_norm(const T* v, long nr, long nw1, double* part, double* out, cudaStream_t s) {
@@ -307,169 +406,32 @@ static rte_status dev_norm(const T* v, long nr, long nw1, double* part, double* 
     return RTE_OK;
 }
 
-// one Arnoldi step (graph body)
-template <typename T>
-static rte_status arnoldi_body(Gm<T>& G, bool cgs2, cudaGraphConditionalHandle loop, cudaStream_t s) {
-    const long nr = G.nr;
-    const int nb = tiles(nr), gr = grid_for(nr);
-    rte_status e = apply_A_T(G.p, G.vin, G.w, s);
-    if (e != RTE_OK) return e;
-    const int* jp = &G.st->j;
-    k_mdot<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
-    RTE_CUDA_TRY(cudaGetLastError());
-    k_reduce<<<G.m + 1, 256, 0, s>>>(G.part, nb, jp, 1, G.st->hA, 0);
-    RTE_CUDA_TRY(cudaGetLastError());
-    rte_count_launches(2);
-    if (cgs2) {
-        k_maxpy<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, G.st->hA, jp, 1, -1.0, G.nw1, nullptr);
-        RTE_CUDA_TRY(cudaGetLastError());
-        k_mdot<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
-        RTE_CUDA_TRY(cudaGetLastError());
-        k_reduce<<<G.m + 1, 256, 0, s>>>(G.part, nb, jp, 1, G.st->hB, 0);
-        RTE_CUDA_TRY(cudaGetLastError());
-        k_maxpy<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, G.st->hB, jp, 1, -1.0, G.nw1, G.part);
-        RTE_CUDA_TRY(cudaGetLastError());
-        rte_count_launches(4);
-    } else {
-        k_maxpy<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, G.st->hA, jp, 1, -1.0, G.nw1, G.part);
-        RTE_CUDA_TRY(cudaGetLastError());
-        rte_count_launches(1);
-    }
-    k_reduce<<<1, 256, 0, s>>>(G.part, nb, nullptr, 1, &G.st->nrm, 1);
-    RTE_CUDA_TRY(cudaGetLastError());
-    k_scale_basis<T><<<gr, 256, 0, s>>>(G.w, G.V, G.vin, nr, G.st, 1);
-    RTE_CUDA_TRY(cudaGetLastError());
-    k_givens<<<1, 32, 0, s>>>(G.st, loop);
-    RTE_CUDA_TRY(cudaGetLastError());
-    rte_count_launches(3);
-    return RTE_OK;
-}
-
-// sink node of a graph (the node without dependents)
-static cudaGraphNode_t graph_sink(cudaGraph_t g) {
-    size_t n = 0;
-    cudaGraphGetNodes(g, nullptr, &n);
-    if (n == 0) return nullptr;
-    cudaGraphNode_t* nodes = new cudaGraphNode_t[n];
-    cudaGraphGetNodes(g, nodes, &n);
-    cudaGraphNode_t last = nullptr;
-    for (size_t i = 0; i < n; ++i) {
-        size_t nd = 0;
-        cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd);
-        if (nd == 0) last = nodes[i];
-    }
-    delete[] nodes;
-    return last;
-}
-
-// Capture one restart cycle: first = true means x == 0 (residual = rhs).
-template <typename T>
-static rte_status build_cycle(Gm<T>& G, const T* rhs, T* x, bool first, bool cgs2, cudaGraphExec_t* out,
-                              long long* nodes_out, long long* body_nodes_out) {
-    const long nr = G.nr;
-    const int nb = tiles(nr), gr = grid_for(nr);
-    cudaGraph_t g = nullptr;
-    RTE_CUDA_TRY(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle loop;
-    cudaStream_t cs = nullptr;
-    rte_status st = RTE_OK;
-    const long long c0 = rte_kernel_launches();
-    long long pre = 0, body = 0, post = 0;
-    cudaGraphNode_t last = nullptr;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) { st = rte_cuda_fail(e, "conditional handle"); goto done; }
-    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { st = rte_cuda_fail(e, "capture stream"); goto done; }
-    // head: residual, norm, init, V_0
-    e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { st = rte_cuda_fail(e, "capture head"); goto done; }
-    if (first) {
-        cudaMemcpyAsync(G.w, rhs, nr * sizeof(T), cudaMemcpyDeviceToDevice, cs);
-    } else {
-        st = apply_A_T(G.p, x, G.w, cs);
-        if (st == RTE_OK) {
-            k_rsub<T><<<gr, 256, 0, cs>>>(rhs, G.w, nr);
-            rte_count_launches(1);
-        }
-    }
-    if (st == RTE_OK) st = dev_norm<T>(G.w, nr, G.nw1, G.part, &G.st->nrm, cs);
-    if (st == RTE_OK) {
-        k_cycle_init<<<1, 32, 0, cs>>>(G.st, first ? 1 : 0, loop);
-        k_scale_basis<T><<<gr, 256, 0, cs>>>(G.w, G.V, G.vin, nr, G.st, 0);
-        rte_count_launches(2);
-    }
-    {
-        cudaGraph_t gg = nullptr;
-        e = cudaStreamEndCapture(cs, &gg);
-    }
-    if (st == RTE_OK && e != cudaSuccess) st = rte_cuda_fail(e, "capture head end");
-    if (st != RTE_OK) goto done;
-    last = graph_sink(g);
-    pre = rte_kernel_launches() - c0;
-    // WHILE node with the Arnoldi body
-    {
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = loop;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t wnode;
-        e = cudaGraphAddNode(&wnode, g, &last, nullptr, 1, &cp);
-        if (e != cudaSuccess) { st = rte_cuda_fail(e, "add while node"); goto done; }
-        cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) { st = rte_cuda_fail(e, "capture body"); goto done; }
-        const long long b0 = rte_kernel_launches();
-        st = arnoldi_body<T>(G, cgs2, loop, cs);
-        body = rte_kernel_launches() - b0;
-        cudaGraph_t gb = nullptr;
-        e = cudaStreamEndCapture(cs, &gb);
-        if (st == RTE_OK && e != cudaSuccess) st = rte_cuda_fail(e, "capture body end");
-        if (st != RTE_OK) goto done;
-        last = wnode;
-    }
-    // tail: x += V y
-    {
-        const long long t0 = rte_kernel_launches();
-        e = cudaStreamBeginCaptureToGraph(cs, g, &last, nullptr, 1, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) { st = rte_cuda_fail(e, "capture tail"); goto done; }
-        k_solve_tri<<<1, 32, 0, cs>>>(G.st);
-        k_maxpy<T><<<nb, 256, 0, cs>>>(G.V, nr, x, G.st->y, &G.st->j, 0, 1.0, G.nw1, nullptr);
-        rte_count_launches(2);
-        cudaGraph_t gt = nullptr;
-        e = cudaStreamEndCapture(cs, &gt);
-        if (e != cudaSuccess) { st = rte_cuda_fail(e, "capture tail end"); goto done; }
-        post = rte_kernel_launches() - t0;
-    }
-    {
-        cudaGraphExec_t ex = nullptr;
-        e = cudaGraphInstantiate(&ex, g, 0);
-        if (e != cudaSuccess) { st = rte_cuda_fail(e, "instantiate cycle"); goto done; }
-        *out = ex;
-        *nodes_out = pre + post;
-        *body_nodes_out = body;
-    }
-done:
-    rte_count_launches(-(rte_kernel_launches() - c0));  // captured, not executed
-    if (cs) cudaStreamDestroy(cs);
-    cudaGraphDestroy(g);
-    return st;
-}
+template <typename T> struct Gm {
+    rte_plan p;
+    T* V;
+    T* w;
+    T* vin;
+    GmresDev* st;
+    double* part;
+    long nr, nw1;
+    int m;
+};
 
 template <typename T>
 static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream_t s) {
     G.p = p;
-    G.ws = &ws;
     G.nr = p->nr;
     G.nw1 = p->dim == 2 ? 2L * p->n * p->n : p->nr;
     G.m = m;
     if (ws.m != m || !ws.V) {
         krylov_free_ws(ws);
-        if (cudaMalloc(&ws.V, (size_t)(m + 2) * p->nr * sizeof(T)) != cudaSuccess) return RTE_ENOMEM;
-        if (cudaMalloc(&ws.w, (size_t)p->nr * sizeof(T)) != cudaSuccess) return RTE_ENOMEM;
-        if (cudaMalloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(p->nr) * sizeof(double)) != cudaSuccess)
+        if (cudaMalloc(&ws.V, (size_t)(m + 2) * p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (cudaMalloc(&ws.w, (size_t)p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (cudaMalloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(p->nr) * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
             return RTE_ENOMEM;
-        if (cudaMalloc((void**)&ws.st, sizeof(GmresDev)) != cudaSuccess) return RTE_ENOMEM;
+        }
+        if (cudaMalloc((void**)&ws.st, sizeof(GmresDev)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
         RTE_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(GmresDev), s));
         ws.m = m;
     }
@@ -481,206 +443,327 @@ static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream
     return RTE_OK;
 }
 
-struct HostStatus { int j, its, stop, conv; double res, bnorm; };
-
-static rte_status read_status(const GmresDev* st, HostStatus* hs, double* pinned, cudaStream_t s) {
-    RTE_CUDA_TRY(cudaMemcpyAsync(pinned, st, offsetof(GmresDev, cs), cudaMemcpyDeviceToHost, s));
-    RTE_CUDA_TRY(cudaStreamSynchronize(s));
-    const GmresDev* h = (const GmresDev*)pinned;
-    hs->j = h->j;
-    hs->its = h->its;
-    hs->stop = h->stop;
-    hs->conv = h->conv;
-    hs->res = h->res;
-    hs->bnorm = h->bnorm;
-    return RTE_OK;
-}
-
-// GMRES(m) on A = I - K in precision T: solves A x = rhs with x = 0 on entry,
-// tol relative to ||rhs||.  rhs and x must be the same buffers on every call
-// for one workspace (the cycle graphs bind them).
+// one Arnoldi step (graph body)
 template <typename T>
-static rte_status gmres_T(rte_plan p, KrylovWs& ws, const T* rhs, T* x, double tol_rel, int m, int maxit, bool cgs2,
-                          int* its_out, double* relres_est, cudaStream_t s) {
-    Gm<T> G;
-    rte_status e = gm_setup<T>(G, p, ws, m, s);
+static rte_status arnoldi_body(Gm<T>& G, bool cgs2, cudaGraphConditionalHandle loop, cudaStream_t s) {
+    const long nr = G.nr;
+    const int nb = tiles(nr), gr = grid_for(nr);
+    rte_status e = apply_A_T(G.p, G.vin, G.w, s);
     if (e != RTE_OK) return e;
-    const int key = (int)p->opts.prec * 2 + (cgs2 ? 1 : 0);
-    if (!ws.exec_first || ws.key != key || ws.rhs != (const void*)rhs || ws.x != (void*)x) {
-        if (ws.exec_first) cudaGraphExecDestroy((cudaGraphExec_t)ws.exec_first);
-        if (ws.exec_restart) cudaGraphExecDestroy((cudaGraphExec_t)ws.exec_restart);
-        ws.exec_first = ws.exec_restart = nullptr;
-        cudaGraphExec_t a = nullptr, b = nullptr;
-        e = build_cycle<T>(G, rhs, x, true, cgs2, &a, &ws.nodes_first, &ws.nodes_body);
-        if (e != RTE_OK) return e;
-        e = build_cycle<T>(G, rhs, x, false, cgs2, &b, &ws.nodes_restart, &ws.nodes_body);
-        if (e != RTE_OK) { cudaGraphExecDestroy(a); return e; }
-        ws.exec_first = a;
-        ws.exec_restart = b;
-        ws.key = key;
-        ws.rhs = (const void*)rhs;
-        ws.x = (void*)x;
+    const int* jp = &G.st->j;
+    k_mdot<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
+    k_reduce<<<G.m + 1, 256, 0, s>>>(G.part, nb, jp, 1, G.st->hA, 0);
+    rte_count_launches(2);
+    if (cgs2) {
+        k_maxpy<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, G.st->hA, jp, 1, -1.0, G.nw1, nullptr);
+        k_mdot<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
+        k_reduce<<<G.m + 1, 256, 0, s>>>(G.part, nb, jp, 1, G.st->hB, 0);
+        k_maxpy<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, G.st->hB, jp, 1, -1.0, G.nw1, G.part);
+        rte_count_launches(4);
+    } else {
+        k_maxpy<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, G.st->hA, jp, 1, -1.0, G.nw1, G.part);
+        rte_count_launches(1);
     }
-    // tolerance, restart, iteration budget into the device state
-    GmresDev* h0 = (GmresDev*)(p->hst + 32);
-    memset(h0, 0, offsetof(GmresDev, cs));
-    h0->m = m;
-    h0->maxit = maxit < 1 ? 1 : maxit;
-    h0->cgs2 = cgs2 ? 1 : 0;
-    h0->tol = tol_rel;
-    RTE_CUDA_TRY(cudaMemcpyAsync(G.st, h0, offsetof(GmresDev, cs), cudaMemcpyHostToDevice, s));
-    *its_out = 0;
-    *relres_est = 0.0;
-    rte_status result = RTE_OK;
-    HostStatus hs;
-    bool first = true;
-    int last_its = 0;
-    while (true) {
-        cudaGraphExec_t ex = (cudaGraphExec_t)(first ? ws.exec_first : ws.exec_restart);
-        RTE_CUDA_TRY(cudaGraphLaunch(ex, s));
-        e = read_status(G.st, &hs, p->hst + 8, s);
-        if (e != RTE_OK) return e;
-        rte_count_launches((first ? ws.nodes_first : ws.nodes_restart) + ws.nodes_body * (hs.its - last_its));
-        last_its = hs.its;
-        first = false;
-        if (!isfinite(hs.res)) { result = RTE_ENAN; break; }
-        if (hs.conv) break;
-        if (hs.its >= maxit) { result = RTE_ENOCONV; break; }
-        if (hs.j == 0) { result = RTE_ENOCONV; break; }  // cycle made no step
-    }
-    *its_out = hs.its;
-    *relres_est = hs.bnorm > 0 ? hs.res / hs.bnorm : 0.0;
-    return result;
-}
-
-// --------------------------------------------------------------------------
-// residual helpers (FP64): r = b - (u - K u) = -u + K u + b
-// --------------------------------------------------------------------------
-static rte_status residual64(rte_plan p, const double* b, const double* u, double* r, cudaStream_t s) {
-    return plan_apply64(p, MIX_K, u, r, -1.0, 1.0, 1.0, b, s);
-}
-
-static rte_status norm64(rte_plan p, const double* v, double* out_host, cudaStream_t s) {
-    const long nw1 = p->dim == 2 ? 2L * p->n * p->n : p->nr;
-    rte_status e = dev_norm<double>(v, p->nr, nw1, p->part64, p->dscal, s);
-    if (e != RTE_OK) return e;
-    RTE_CUDA_TRY(cudaMemcpyAsync(p->hst + 4, p->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
-    RTE_CUDA_TRY(cudaStreamSynchronize(s));
-    *out_host = p->hst[4];
+    k_reduce<<<1, 256, 0, s>>>(G.part, nb, nullptr, 1, &G.st->nrm, 1);
+    k_scale_basis<T><<<gr, 256, 0, s>>>(G.w, G.V, G.vin, nr, G.st, 1);
+    k_givens<<<1, 32, 0, s>>>(G.st, loop);
+    rte_count_launches(3);
+    RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
 
-rte_status krylov_solve(rte_plan p, const double* f, double* u, const rte_opts* o, rte_stats* stats,
-                        cudaStream_t s) {
+// Stream-capture helper that appends to a graph after one dependency node
+// and reports the new sink (the capture frontier).
+struct Seg {
+    cudaStream_t cs;
+    cudaGraph_t g;
+    cudaGraphNode_t dep;
+    long long k0;
+};
+
+static rte_status seg_begin(Seg& S, cudaStream_t cs, cudaGraph_t g, cudaGraphNode_t dep) {
+    S.cs = cs;
+    S.g = g;
+    S.dep = dep;
+    S.k0 = rte_kernel_launches();
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, g, dep ? &S.dep : nullptr, nullptr, dep ? 1 : 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "begin capture");
+    return RTE_OK;
+}
+
+// ends the capture; *sink = last node (unchanged if nothing was captured);
+// *kernels = kernels captured in this segment
+static rte_status seg_end(Seg& S, cudaGraphNode_t* sink, long long* kernels) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(S.cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+    cudaGraphNode_t last = (e == cudaSuccess && nd == 1) ? deps[0] : S.dep;
+    cudaGraph_t gg = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(S.cs, &gg);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "capture info");
+    if (e2 != cudaSuccess) return rte_cuda_fail(e2, "end capture");
+    if (nd > 1) return rte_cuda_fail(cudaErrorInvalidValue, "capture frontier has several nodes");
+    *sink = last;
+    if (kernels) *kernels += rte_kernel_launches() - S.k0;
+    return RTE_OK;
+}
+
+static rte_status add_cond(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphConditionalHandle h,
+                           cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddNode(&node, g, *dep ? dep : nullptr, nullptr, *dep ? 1 : 0, &cp);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "add conditional node");
+    *body = cp.conditional.phGraph_out[0];
+    *dep = node;
+    return RTE_OK;
+}
+
+#define SEG(graph, dep, cnt, ...)                                                     \
+    do {                                                                              \
+        Seg S_;                                                                       \
+        rte_status e_ = seg_begin(S_, cs, graph, dep);                                \
+        if (e_ != RTE_OK) return e_;                                                  \
+        rte_status b_ = [&]() -> rte_status { __VA_ARGS__ return RTE_OK; }();         \
+        rte_status f_ = seg_end(S_, &dep, cnt);                                       \
+        if (b_ != RTE_OK) return b_;                                                  \
+        if (f_ != RTE_OK) return f_;                                                  \
+    } while (0)
+
+#define TRYS(x)                        \
+    do {                               \
+        rte_status t_ = (x);           \
+        if (t_ != RTE_OK) return t_;   \
+    } while (0)
+
+// Append the whole solve of plan p (precision T: double = plain FP64 GMRES,
+// float = FP32 inner GMRES + FP64 refinement) to graph g after *dep.
+// Inputs/outputs are the plan's own f_dev / u_dev; options are read from
+// the plan's device RefDev at run time.
+template <typename T>
+static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cudaGraphNode_t* dep_io,
+                              cudaStream_t cs, SolveGraphInfo* info) {
+    const bool mixed = sizeof(T) == sizeof(float);
+    const bool cgs2 = !mixed;
+    Gm<T> G;
+    TRYS(gm_setup<T>(G, p, ws, m, cs));
+    RTE_CUDA_TRY(cudaStreamSynchronize(cs));
     const long nr = p->nr;
-    const int gr = grid_for(nr);
-    const int m = o->restart;
+    const int gr = grid_for(nr), nb = tiles(nr);
+    const long nw1 = G.nw1;
+    RefDev* ref = (RefDev*)p->ref;
+    T* rhs = mixed ? (T*)p->r32 : (T*)p->r64;
+    T* x = mixed ? (T*)p->d32 : (T*)p->x64;
+    cudaGraphConditionalHandle c_guess, c_outer, c_cycle, c_loop, c_restart;
+    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_guess, g, 0, cudaGraphCondAssignDefault));
+    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_outer, g, 0, cudaGraphCondAssignDefault));
+    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_cycle, g, 0, cudaGraphCondAssignDefault));
+    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_loop, g, 0, cudaGraphCondAssignDefault));
+    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_restart, g, 0, cudaGraphCondAssignDefault));
+    cudaGraphNode_t dep = *dep_io;
+    *info = SolveGraphInfo();
+    // T.1 and start values
+    SEG(g, dep, &info->k_fixed, {
+        TRYS(plan_apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, cs));
+        TRYS(dev_norm<double>(p->b64, nr, nw1, p->part64, &ref->bnorm, cs));
+        k_ref_start<<<1, 32, 0, cs>>>(ref, c_guess);
+        k_zero_unless_guess<<<gr, 256, 0, cs>>>(p->u_dev, nr, ref);
+        k_copy_vec<<<gr, 256, 0, cs>>>(p->b64, p->r64, nr);
+        rte_count_launches(3);
+    });
+    // residual of a guess
+    {
+        cudaGraph_t body;
+        TRYS(add_cond(g, &dep, c_guess, cudaGraphCondTypeIf, &body));
+        cudaGraphNode_t d = nullptr;
+        SEG(body, d, &info->k_guess, {
+            TRYS(plan_apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+            TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
+            k_ref_relres<<<1, 32, 0, cs>>>(ref);
+            rte_count_launches(1);
+        });
+    }
+    SEG(g, dep, &info->k_fixed, {
+        k_ref_gate<<<1, 32, 0, cs>>>(ref, c_outer);
+        rte_count_launches(1);
+    });
+    // refinement loop
+    cudaGraph_t outer_body;
+    TRYS(add_cond(g, &dep, c_outer, cudaGraphCondTypeWhile, &outer_body));
+    {
+        cudaGraphNode_t d = nullptr;
+        SEG(outer_body, d, &info->k_outer, {
+            if (mixed) {
+                k_scale_inv<double, float><<<gr, 256, 0, cs>>>(p->r64, p->r32, nr, &ref->rnorm);
+                rte_count_launches(1);
+            }
+            k_zero_T<T><<<gr, 256, 0, cs>>>(x, nr);
+            k_copy_T<T><<<gr, 256, 0, cs>>>(rhs, G.w, nr);
+            k_gm_start<<<1, 32, 0, cs>>>(G.st, ref, m, cgs2 ? 1 : 0, c_cycle);
+            rte_count_launches(3);
+        });
+        cudaGraph_t cycle_body;
+        TRYS(add_cond(outer_body, &d, c_cycle, cudaGraphCondTypeWhile, &cycle_body));
+        {
+            cudaGraphNode_t dc = nullptr;
+            SEG(cycle_body, dc, &info->k_cycle, {
+                TRYS(dev_norm<T>(G.w, nr, nw1, G.part, &G.st->nrm, cs));
+                k_cycle_init<<<1, 32, 0, cs>>>(G.st, c_loop);
+                k_scale_basis<T><<<gr, 256, 0, cs>>>(G.w, G.V, G.vin, nr, G.st, 0);
+                rte_count_launches(2);
+            });
+            cudaGraph_t loop_body;
+            TRYS(add_cond(cycle_body, &dc, c_loop, cudaGraphCondTypeWhile, &loop_body));
+            {
+                cudaGraphNode_t dl = nullptr;
+                SEG(loop_body, dl, &info->k_step, { TRYS(arnoldi_body<T>(G, cgs2, c_loop, cs)); });
+            }
+            SEG(cycle_body, dc, &info->k_cycle, {
+                k_solve_tri<<<1, 32, 0, cs>>>(G.st);
+                k_maxpy<T><<<nb, 256, 0, cs>>>(G.V, nr, x, G.st->y, &G.st->j, 0, 1.0, nw1, nullptr);
+                k_cycle_end<<<1, 32, 0, cs>>>(G.st, ref, c_cycle, c_restart);
+                rte_count_launches(3);
+            });
+            cudaGraph_t restart_body;
+            TRYS(add_cond(cycle_body, &dc, c_restart, cudaGraphCondTypeIf, &restart_body));
+            {
+                cudaGraphNode_t dr = nullptr;
+                SEG(restart_body, dr, &info->k_restart, {
+                    TRYS(apply_A_T(p, x, G.w, cs));
+                    k_rsub<T><<<gr, 256, 0, cs>>>(rhs, G.w, nr);
+                    rte_count_launches(1);
+                });
+            }
+        }
+        SEG(outer_body, d, &info->k_outer, {
+            if (mixed) {
+                k_axpy_scaled<float><<<gr, 256, 0, cs>>>(p->u_dev, (const float*)x, nr, &ref->rnorm);
+            } else {
+                k_add64<<<gr, 256, 0, cs>>>(p->u_dev, (const double*)x, nr);
+            }
+            k_ref_after<<<1, 32, 0, cs>>>(ref, G.st);
+            rte_count_launches(2);
+            TRYS(plan_apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+            TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
+            k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
+            rte_count_launches(1);
+        });
+    }
+    *dep_io = dep;
+    return RTE_OK;
+}
+
+// captured, not executed: take the capture-time counts back out
+struct CountGuard {
+    long long c0;
+    CountGuard() : c0(rte_kernel_launches()) {}
+    ~CountGuard() { rte_count_launches(-(rte_kernel_launches() - c0)); }
+};
+
+rte_status solve_graph_append(rte_plan p, int prec, int m, cudaGraph_t g, cudaGraphNode_t* dep, cudaStream_t cs,
+                              SolveGraphInfo* info) {
+    CountGuard guard;
+    const rte_prec saved = p->opts.prec;
+    p->opts.prec = (rte_prec)prec;  // selects the inner spectra precision at capture
+    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(p, p->k64, m, g, dep, cs, info)
+                                          : build_solve<float>(p, p->k32, m, g, dep, cs, info);
+    p->opts.prec = saved;
+    return st;
+}
+
+static rte_status get_solve_graph(rte_plan p, int prec, int m, cudaStream_t s, cudaGraphExec_t* out) {
+    SolveGraph& sg = p->graphs[prec];
+    if (sg.exec && sg.m == m) {
+        *out = (cudaGraphExec_t)sg.exec;
+        return RTE_OK;
+    }
+    if (sg.exec) cudaGraphExecDestroy((cudaGraphExec_t)sg.exec);
+    sg.exec = nullptr;
+    // workspace allocations happen here, before the capture
+    RTE_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaGraph_t g = nullptr;
+    RTE_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaStream_t cs;
+    RTE_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraphNode_t dep = nullptr;
+    rte_status st = solve_graph_append(p, prec, m, g, &dep, cs, &sg.info);
+    cudaStreamDestroy(cs);
+    if (st == RTE_OK) {
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        if (e != cudaSuccess) st = rte_cuda_fail(e, "instantiate solve graph");
+        else { sg.exec = ex; sg.m = m; *out = ex; }
+    }
+    cudaGraphDestroy(g);
+    return st;
+}
+
+// options into the device RefDev (from the plan's pinned staging area)
+rte_status solve_set_options(rte_plan p, const rte_opts* o, cudaStream_t s) {
+    RefDev* h = (RefDev*)(p->hst + 32);
+    memset(h, 0, sizeof(RefDev));
+    h->max_outer = o->prec == RTE_PREC_FP64 ? 4 : 40;
+    h->maxit = o->maxit;
+    h->use_guess = o->use_guess ? 1 : 0;
+    h->mixed = o->prec != RTE_PREC_FP64;
+    h->tol = o->tol;
+    h->inner_tol = o->inner_tol;
+    RTE_CUDA_TRY(cudaMemcpyAsync(p->ref, h, sizeof(RefDev), cudaMemcpyHostToDevice, s));
+    return RTE_OK;
+}
+
+rte_status solve_collect(rte_plan p, int prec, const RefDev* hr, rte_stats* stats, double ms) {
+    const SolveGraphInfo& gi = p->graphs[prec].info;
+    rte_count_launches(gi.k_fixed + (hr->use_guess ? gi.k_guess : 0) + (long long)hr->outer * gi.k_outer +
+                       (long long)hr->cycles * gi.k_cycle + (long long)hr->its * gi.k_step +
+                       (long long)hr->restarts * gi.k_restart);
+    if (stats) {
+        const double rho = p->mu_t > 0 ? p->mu_s / p->mu_t : 0.0;
+        const double cond = rho < 1.0 ? (1.0 + rho) / (1.0 - rho) : INFINITY;
+        stats->iters = hr->its;
+        stats->outer = prec == RTE_PREC_FP64 ? 0 : hr->outer;
+        stats->relres_true = hr->relres;
+        stats->converged = hr->relres <= hr->tol ? 1 : 0;
+        stats->ms_total = ms;
+        stats->ms_pre = p->ms_pre;
+        stats->est_err_bound = cond * hr->relres;
+    }
+    if (hr->status == 7 || !isfinite(hr->relres)) return RTE_ENAN;
+    if (!(hr->relres <= hr->tol)) return RTE_ENOCONV;
+    return RTE_OK;
+}
+
+size_t refdev_size() { return sizeof(RefDev); }
+
+// Solve for the plan's f_dev into u_dev (both plan-owned), one graph launch.
+rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStream_t s) {
+    cudaGraphExec_t ex = nullptr;
+    const int prec = (int)o->prec;
+    // the FP64 workspace is only needed by the FP64 mode
+    rte_status st = get_solve_graph(p, prec, o->restart, s, &ex);
+    if (st != RTE_OK) return st;
     cudaEvent_t ev0, ev1;
     RTE_CUDA_TRY(cudaEventCreate(&ev0));
     RTE_CUDA_TRY(cudaEventCreate(&ev1));
+    st = solve_set_options(p, o, s);
+    if (st != RTE_OK) return st;
     RTE_CUDA_TRY(cudaEventRecord(ev0, s));
-    // T.1: b = K~ g in FP64
-    rte_status e = plan_apply64(p, MIX_RHS, f, p->b64, 0.0, 1.0, 0.0, nullptr, s);
-    if (e != RTE_OK) return e;
-    double bnorm = 0.0;
-    e = norm64(p, p->b64, &bnorm, s);
-    if (e != RTE_OK) return e;
-    if (!isfinite(bnorm)) return RTE_ENAN;
-    if (!o->use_guess) RTE_CUDA_TRY(cudaMemsetAsync(u, 0, nr * sizeof(double), s));
-    int iters = 0, outer = 0;
-    double relres = 0.0;
-    rte_status result = RTE_OK;
-    if (bnorm == 0.0) {
-        RTE_CUDA_TRY(cudaMemsetAsync(u, 0, nr * sizeof(double), s));
-    } else if (o->prec == RTE_PREC_FP64) {
-        // plain FP64 GMRES on r = b - A u0 (u0 = guess or 0); u = u0 + d
-        double rn = bnorm;
-        if (o->use_guess) {
-            e = residual64(p, p->b64, u, p->r64, s);
-            if (e != RTE_OK) return e;
-            e = norm64(p, p->r64, &rn, s);
-            if (e != RTE_OK) return e;
-        } else {
-            RTE_CUDA_TRY(cudaMemcpyAsync(p->r64, p->b64, nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        }
-        if (rn > o->tol * bnorm) {
-            RTE_CUDA_TRY(cudaMemsetAsync(p->x64, 0, nr * sizeof(double), s));
-            double est = 0.0;
-            int its = 0;
-            const double tol_in = o->tol * bnorm / rn * 0.5;
-            result = gmres_T<double>(p, p->k64, p->r64, p->x64, tol_in, m, o->maxit, true, &its, &est, s);
-            iters = its;
-            if (result != RTE_OK && result != RTE_ENOCONV) return result;
-            k_add64<<<gr, 256, 0, s>>>(u, p->x64, nr);
-            RTE_CUDA_TRY(cudaGetLastError());
-            rte_count_launches(1);
-        }
-        e = residual64(p, p->b64, u, p->r64, s);
-        if (e != RTE_OK) return e;
-        e = norm64(p, p->r64, &rn, s);
-        if (e != RTE_OK) return e;
-        relres = rn / bnorm;
-    } else {
-        // mixed: FP64 residual, FP32 inner GMRES on the unit-scaled residual, FP64 update
-        const int max_outer = 40;
-        bool u_zero = !o->use_guess;
-        while (true) {
-            double rn = 0.0;
-            if (u_zero) {
-                // r = b when u = 0: no FP64 operator application needed
-                RTE_CUDA_TRY(cudaMemcpyAsync(p->r64, p->b64, nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                e = norm64(p, p->r64, &rn, s);
-                u_zero = false;
-            } else {
-                e = residual64(p, p->b64, u, p->r64, s);
-                if (e != RTE_OK) return e;
-                e = norm64(p, p->r64, &rn, s);
-            }
-            if (e != RTE_OK) return e;
-            relres = rn / bnorm;
-            if (!isfinite(rn)) { result = RTE_ENAN; break; }
-            if (relres <= o->tol) break;
-            if (outer >= max_outer || iters >= o->maxit) { result = RTE_ENOCONV; break; }
-            // r32 = r / ||r||   (p->dscal holds ||r|| on the device)
-            k_scale_inv<double, float><<<gr, 256, 0, s>>>(p->r64, p->r32, nr, p->dscal);
-            RTE_CUDA_TRY(cudaGetLastError());
-            RTE_CUDA_TRY(cudaMemsetAsync(p->d32, 0, nr * sizeof(float), s));
-            rte_count_launches(1);
-            int its = 0;
-            double est = 0.0;
-            double tin = o->inner_tol;
-            // never ask the inner solve for more than the outer target needs
-            const double need = o->tol / relres * 0.5;
-            if (need > tin) tin = need;
-            rte_status ie = gmres_T<float>(p, p->k32, p->r32, p->d32, tin, m, o->maxit - iters, false, &its, &est, s);
-            iters += its;
-            ++outer;
-            if (ie != RTE_OK && ie != RTE_ENOCONV) { result = ie; break; }
-            // u += ||r|| d32
-            k_axpy_scaled<float><<<gr, 256, 0, s>>>(u, p->d32, nr, p->dscal);
-            RTE_CUDA_TRY(cudaGetLastError());
-            rte_count_launches(1);
-        }
-    }
+    RTE_CUDA_TRY(cudaGraphLaunch(ex, s));
     RTE_CUDA_TRY(cudaEventRecord(ev1, s));
-    RTE_CUDA_TRY(cudaEventSynchronize(ev1));
+    RefDev* hr = (RefDev*)(p->hst + 16);
+    RTE_CUDA_TRY(cudaMemcpyAsync(hr, p->ref, sizeof(RefDev), cudaMemcpyDeviceToHost, s));
+    RTE_CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    if (stats) {
-        const double rho = p->mu_t > 0 ? p->mu_s / p->mu_t : 0.0;
-        const double cond = rho < 1.0 ? (1.0 + rho) / (1.0 - rho) : INFINITY;
-        stats->iters = iters;
-        stats->outer = outer;
-        stats->relres_true = relres;
-        stats->converged = relres <= o->tol ? 1 : 0;
-        stats->ms_total = ms;
-        stats->ms_pre = p->ms_pre;
-        stats->est_err_bound = cond * relres;
-    }
-    if (result == RTE_OK && !(relres <= o->tol)) result = RTE_ENOCONV;
-    return result;
+    return solve_collect(p, prec, hr, stats, ms);
 }
 
 void krylov_free_ws(KrylovWs& ws) {
@@ -688,12 +771,14 @@ void krylov_free_ws(KrylovWs& ws) {
     if (ws.w) cudaFree(ws.w);
     if (ws.part) cudaFree(ws.part);
     if (ws.st) cudaFree(ws.st);
-    if (ws.exec_first) cudaGraphExecDestroy((cudaGraphExec_t)ws.exec_first);
-    if (ws.exec_restart) cudaGraphExecDestroy((cudaGraphExec_t)ws.exec_restart);
     ws = KrylovWs();
 }
 
 rte_status krylov_free(rte_plan p) {
+    for (int i = 0; i < 3; ++i) {
+        if (p->graphs[i].exec) cudaGraphExecDestroy((cudaGraphExec_t)p->graphs[i].exec);
+        p->graphs[i] = SolveGraph();
+    }
     krylov_free_ws(p->k64);
     krylov_free_ws(p->k32);
     return RTE_OK;

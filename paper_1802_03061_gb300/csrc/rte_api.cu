@@ -84,7 +84,7 @@ extern "C" rte_status rte_destroy(rte_plan p) {
     krylov_free(p);
     void* bufs[] = {p->tw64, p->tw32, p->S64, p->S32, p->S16, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
-                    p->d32, p->dscal, p->part64, p->f_dev, p->u_dev};
+                    p->d32, p->dscal, p->part64, p->f_dev, p->u_dev, p->ref};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->hst) cudaFreeHost(p->hst);
@@ -186,6 +186,7 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     TRY(dalloc(&p->part64, (size_t)((p->nr + 2047) / 2048 + 1) * sizeof(double)));
     TRY(dalloc(&p->f_dev, p->ncell * sizeof(double)));
     TRY(dalloc(&p->u_dev, p->nr * sizeof(double)));
+    TRY(dalloc((char**)&p->ref, refdev_size()));
     if (cudaMallocHost((void**)&p->hst, 64 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         st = RTE_ENOMEM;
@@ -241,17 +242,20 @@ extern "C" rte_status rte_rhs(rte_plan p, const double* f, void* b, void* stream
     return plan_apply64(p, MIX_RHS, f, (double*)b, 0.0, 1.0, 0.0, nullptr, (cudaStream_t)stream);
 }
 
+// f and u are copied to / from the plan's own buffers so that the captured
+// solve graph (bound to those buffers) serves every call
 extern "C" rte_status rte_solve(rte_plan p, const double* f, void* u, const rte_opts* opts, rte_stats* stats,
                                 void* stream) {
     if (!p || !f || !u) return RTE_EINVAL;
     rte_opts o = opts ? *opts : p->opts;
     fill_defaults(&o);
     if (o.prec < RTE_PREC_FP64 || o.prec > RTE_PREC_MIXED_BF16SPEC) return RTE_EINVAL;
-    // every plan holds FP64, FP32 and BF16 spectra; the solve picks its own
-    const rte_prec saved = p->opts.prec;
-    p->opts.prec = o.prec;
-    rte_status st = krylov_solve(p, f, (double*)u, &o, stats, (cudaStream_t)stream);
-    p->opts.prec = saved;
+    cudaStream_t s = (cudaStream_t)stream;
+    RTE_CUDA_TRY(cudaMemcpyAsync(p->f_dev, f, p->ncell * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (o.use_guess) RTE_CUDA_TRY(cudaMemcpyAsync(p->u_dev, u, p->nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rte_status st = krylov_solve(p, &o, stats, s);
+    if (st != RTE_OK && st != RTE_ENOCONV) return st;
+    RTE_CUDA_TRY(cudaMemcpyAsync(u, p->u_dev, p->nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return st;
 }
 
@@ -259,11 +263,13 @@ extern "C" rte_status rte_solve_host(rte_plan p, const double* f_host, void* u_h
                                      rte_stats* stats, void* stream) {
     if (!p || !f_host || !u_host) return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    RTE_CUDA_TRY(cudaMemcpyAsync(p->f_dev, f_host, p->ncell * sizeof(double), cudaMemcpyHostToDevice, s));
     rte_opts o = opts ? *opts : p->opts;
+    fill_defaults(&o);
+    if (o.prec < RTE_PREC_FP64 || o.prec > RTE_PREC_MIXED_BF16SPEC) return RTE_EINVAL;
+    RTE_CUDA_TRY(cudaMemcpyAsync(p->f_dev, f_host, p->ncell * sizeof(double), cudaMemcpyHostToDevice, s));
     if (o.use_guess)
         RTE_CUDA_TRY(cudaMemcpyAsync(p->u_dev, u_host, p->nr * sizeof(double), cudaMemcpyHostToDevice, s));
-    rte_status st = rte_solve(p, p->f_dev, p->u_dev, &o, stats, stream);
+    rte_status st = krylov_solve(p, &o, stats, s);
     if (st != RTE_OK && st != RTE_ENOCONV) return st;
     RTE_CUDA_TRY(cudaMemcpyAsync(u_host, p->u_dev, p->nr * sizeof(double), cudaMemcpyDeviceToHost, s));
     RTE_CUDA_TRY(cudaStreamSynchronize(s));
