@@ -143,6 +143,47 @@ rte_status rte_plan_info(rte_plan plan, int* n, int* Q, int* L, long* nreal);
  * host array out (2L+1 doubles, or 1). */
 rte_status rte_plan_cell_weights(rte_plan plan, double* out_host);
 
+/* ---- Batched solves (task extension: many sources and coefficient sets on
+ * grids of uneven size solved by one graph launch; no counterpart in the
+ * paper, which solves one problem at a time) ---- */
+typedef struct {
+    int n;                    /* cells per side (2D) */
+    double h, mu_t, mu_s;     /* as rte_plan_create */
+    int L;
+    const double* sigma_hat;  /* host, L+1 values, sigma_hat[0] == 1 */
+    int q;                    /* padded FFT length, 0 = default (see rte_autotune) */
+    int rows_per_block;       /* row-pass tile, 0 = default (see rte_autotune) */
+} rte_instance_desc;
+typedef struct rte_batch_s* rte_batch;
+
+/* Create plans for `count` 2D instances and capture one CUDA graph holding
+ * every instance's whole solve (T.1 + refinement + GMRES, device-controlled)
+ * as independent branches.  opts: precision, tolerance, restart, maxit,
+ * inner_tol shared by all instances (use_guess is ignored: zero start).
+ * Owns all device memory; RTE_ENOMEM if it does not fit. */
+rte_status rte_batch_create(rte_batch* out, int count, const rte_instance_desc* descs, const rte_opts* opts,
+                            void* cuda_stream);
+/* Offsets (in doubles) of instance i's source f (n^2 doubles) and solution u
+ * (2(L+1)n^2 doubles, the FP64 mode-field layout) in the packed arrays that
+ * rte_batch_solve takes; arrays of count+1 entries (last = total). */
+rte_status rte_batch_layout(rte_batch b, long* f_offsets_host, long* u_offsets_host);
+/* Solve every instance: f_packed_dev / u_packed_dev are caller-owned device
+ * arrays in the rte_batch_layout packing.  stats_host (count entries, may be
+ * NULL) receives each instance's statistics; ms_out (may be NULL) the device
+ * time of the graph launch.  Returns the first non-OK instance status. */
+rte_status rte_batch_solve(rte_batch b, const double* f_packed_dev, double* u_packed_dev, rte_stats* stats_host,
+                           double* ms_out, void* cuda_stream);
+rte_status rte_batch_destroy(rte_batch b);
+
+/* Autotuner: for a 2D grid of n cells per side and truncation L, time the
+ * FP32 operator application (prec = RTE_PREC_MIXED_FP32 or _BF16SPEC) for
+ * the candidate padded lengths Q (the smallest even 2^a 3^b >= 2n-1 and the
+ * next two) and row tiles {2,4,8,16}, `reps` applications each, with CUDA
+ * events on cuda_stream; returns the fastest (Q, rows per block) and its time
+ * in ms per application.  Allocates temporary plans. */
+rte_status rte_autotune(int n, int L, int prec, int reps, int* Q_out, int* rows_per_block_out, double* ms_out,
+                        void* cuda_stream);
+
 /* Diagnostics (no counterpart in the paper).
  * rte_time_passes: average duration in ms of each FFT pass of one K
  * application -- ms_out[0] row pass, [1] column pass (FFT, mode mix, inverse

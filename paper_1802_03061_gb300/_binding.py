@@ -43,6 +43,12 @@ class rte_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class rte_instance_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("h", ctypes.c_double), ("mu_t", ctypes.c_double), ("mu_s", ctypes.c_double),
+                ("L", ctypes.c_int), ("sigma_hat", ctypes.POINTER(ctypes.c_double)), ("q", ctypes.c_int),
+                ("rows_per_block", ctypes.c_int)]
+
+
 _lib = None
 VP = ctypes.c_void_p
 
@@ -72,6 +78,15 @@ def lib():
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP, VP, VP]
         L.rte_apply_K_noalloc.restype = ctypes.c_int
         L.rte_noalloc_scratch_bytes.restype = ctypes.c_longlong
+        L.rte_batch_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(rte_instance_desc),
+                                       ctypes.POINTER(rte_opts), VP]
+        L.rte_batch_layout.argtypes = [VP, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
+        L.rte_batch_solve.argtypes = [VP, VP, VP, ctypes.POINTER(rte_stats), ctypes.POINTER(ctypes.c_double), VP]
+        L.rte_batch_destroy.argtypes = [VP]
+        L.rte_autotune.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), VP]
+        for name in ("rte_batch_create", "rte_batch_layout", "rte_batch_solve", "rte_batch_destroy", "rte_autotune"):
+            getattr(L, name).restype = ctypes.c_int
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
         L.rte_last_error.restype = ctypes.c_char_p
@@ -177,6 +192,50 @@ def rte_apply_K_noalloc(n, h, mu_t, mu_s, L, sigma_hat, x, y, stream=0):
 
 def rte_noalloc_scratch_bytes():
     return int(lib().rte_noalloc_scratch_bytes())
+
+
+def rte_batch_create(instances, opts=None, stream=0):
+    """instances: sequence of dicts with n, h, mu_t, mu_s, sigma_hat (and optional q, rows_per_block)."""
+    count = len(instances)
+    descs = (rte_instance_desc * count)()
+    keep = []
+    for i, d in enumerate(instances):
+        sig = [float(v) for v in d["sigma_hat"]]
+        arr = (ctypes.c_double * len(sig))(*sig)
+        keep.append(arr)
+        descs[i] = rte_instance_desc(int(d["n"]), float(d["h"]), float(d["mu_t"]), float(d["mu_s"]), len(sig) - 1,
+                                     arr, int(d.get("q", 0)), int(d.get("rows_per_block", 0)))
+    out = VP()
+    st = lib().rte_batch_create(ctypes.byref(out), count, descs, ctypes.byref(opts) if opts is not None else None,
+                                VP(stream))
+    _check(st, "rte_batch_create")
+    return out
+
+
+def rte_batch_layout(batch, count):
+    f = (ctypes.c_long * (count + 1))()
+    u = (ctypes.c_long * (count + 1))()
+    _check(lib().rte_batch_layout(batch, f, u), "rte_batch_layout")
+    return list(f), list(u)
+
+
+def rte_batch_solve(batch, count, f_packed, u_packed, stream=0):
+    stats = (rte_stats * count)()
+    ms = ctypes.c_double()
+    st = lib().rte_batch_solve(batch, VP(f_packed), VP(u_packed), stats, ctypes.byref(ms), VP(stream))
+    _check(st, "rte_batch_solve", allow=(RTE_ENOCONV,))
+    return st, [x.as_dict() for x in stats], ms.value
+
+
+def rte_batch_destroy(batch):
+    _check(lib().rte_batch_destroy(batch), "rte_batch_destroy")
+
+
+def rte_autotune(n, L, prec="mixed_fp32", reps=20, stream=0):
+    q, rb, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().rte_autotune(int(n), int(L), PREC[prec] if isinstance(prec, str) else int(prec), int(reps),
+                              ctypes.byref(q), ctypes.byref(rb), ctypes.byref(ms), VP(stream)), "rte_autotune")
+    return q.value, rb.value, ms.value
 
 
 def rte_destroy(plan):

@@ -87,6 +87,7 @@ struct rte_plan_s {
     void* ref = nullptr;     // device refinement state (krylov.cu)
     double* hst = nullptr;   // pinned host mirror of small device state (64 doubles)
     double ms_pre = 0.0;
+    int rb_force = 0;        // row-pass rows per block chosen by the autotuner (0 = default)
     int nsm = 152;
 };
 
@@ -127,6 +128,10 @@ rte_status solve_graph_append(rte_plan p, int prec, int m, cudaGraph_t g, cudaGr
 rte_status solve_set_options(rte_plan p, const rte_opts* o, cudaStream_t s);
 struct RefDev;
 rte_status solve_collect(rte_plan p, int prec, const RefDev* host_ref, rte_stats* stats, double ms);
+void launch_ref_load(rte_plan p, const void* tmpl, cudaStream_t s);
+void launch_ref_store(rte_plan p, void* dst, cudaStream_t s);
+void launch_copy(const double* src, double* dst, long n, cudaStream_t s);
+void fill_ref_template(void* host, const rte_opts* o);
 
 // dispatch helpers (rte_api.cu)
 rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,

@@ -783,3 +783,37 @@ rte_status krylov_free(rte_plan p) {
     krylov_free_ws(p->k32);
     return RTE_OK;
 }
+
+// --------------------------------------------------------------------------
+// batch support: options from a device template, state out to a packed array
+// --------------------------------------------------------------------------
+__global__ void k_ref_load(RefDev* ref, const RefDev* __restrict__ tmpl) {
+    if (threadIdx.x == 0) *ref = *tmpl;
+}
+__global__ void k_ref_store(const RefDev* __restrict__ ref, RefDev* __restrict__ dst) {
+    if (threadIdx.x == 0) *dst = *ref;
+}
+
+void launch_ref_load(rte_plan p, const void* tmpl, cudaStream_t s) {
+    k_ref_load<<<1, 32, 0, s>>>((RefDev*)p->ref, (const RefDev*)tmpl);
+    rte_count_launches(1);
+}
+void launch_ref_store(rte_plan p, void* dst, cudaStream_t s) {
+    k_ref_store<<<1, 32, 0, s>>>((const RefDev*)p->ref, (RefDev*)dst);
+    rte_count_launches(1);
+}
+void launch_copy(const double* src, double* dst, long n, cudaStream_t s) {
+    k_copy_vec<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+    rte_count_launches(1);
+}
+// host image of the options template (same fields solve_set_options writes)
+void fill_ref_template(void* host, const rte_opts* o) {
+    RefDev* h = (RefDev*)host;
+    memset(h, 0, sizeof(RefDev));
+    h->max_outer = o->prec == RTE_PREC_FP64 ? 4 : 40;
+    h->maxit = o->maxit;
+    h->use_guess = 0;
+    h->mixed = o->prec != RTE_PREC_FP64;
+    h->tol = o->tol;
+    h->inner_tol = o->inner_tol;
+}

@@ -96,6 +96,8 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* 
     RowParams rp;
     rp.n = p->n; rp.Q = p->Q; rp.H = p->H; rp.L = p->L;
     rp.RB = rows_per_block<T>(p->Q);
+    if (p->rb_force >= 2 && p->rb_force <= 16 && row_smem<T>(p->Q, p->rb_force & ~1) <= 200 * 1024)
+        rp.RB = p->rb_force & ~1;
     rp.sc = p->sched;
     for (int k = 0; k <= RTE_MAX_L; ++k) rp.wk[k] = 0.0;
     if (kind == MIX_K) {

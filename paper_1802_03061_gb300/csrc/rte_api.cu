@@ -291,3 +291,66 @@ extern "C" rte_status rte_plan_cell_weights(rte_plan p, double* out) {
     RTE_CUDA_TRY(cudaMemcpy(out, p->Dm, cnt * sizeof(double), cudaMemcpyDeviceToHost));
     return RTE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// autotuner: padded length Q and row tile by measurement
+// ---------------------------------------------------------------------------
+extern "C" rte_status rte_autotune(int n, int L, int prec, int reps, int* Q_out, int* rb_out, double* ms_out,
+                                   void* stream) {
+    if (n < 1 || L < 0 || L > RTE_MAX_L || reps < 1) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    double sig[RTE_MAX_L + 1];
+    for (int k = 0; k <= L; ++k) sig[k] = k == 0 ? 1.0 : 0.5;
+    int cands[3];
+    int nc = 0;
+    int q = choose_Q(n);
+    while (nc < 3) {
+        cands[nc++] = q;
+        ++q;
+        while (q % 2 || !smooth23(q)) ++q;
+    }
+    double best = 1e30;
+    int bq = cands[0], brb = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int c = 0; c < nc; ++c) {
+        rte_opts o;
+        memset(&o, 0, sizeof(o));
+        o.prec = (rte_prec)(prec == RTE_PREC_FP64 ? RTE_PREC_MIXED_FP32 : prec);
+        o.q_policy = cands[c];
+        rte_grid g;
+        g.dim = 2;
+        g.n[0] = g.n[1] = g.n[2] = n;
+        rte_plan p = nullptr;
+        rte_status st = rte_plan_create(&p, g, 1.0 / n, 1.0, 0.5, L, sig, &o, stream);
+        if (st != RTE_OK) continue;
+        const int rbs[4] = {2, 4, 8, 16};
+        for (int r = 0; r < 4; ++r) {
+            p->rb_force = rbs[r];
+            st = plan_apply32(p, p->r32, p->d32, 1.0f, -1.0f, 0.0f, nullptr, s);  // warm-up
+            if (st != RTE_OK) break;
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < reps && st == RTE_OK; ++i)
+                st = plan_apply32(p, p->r32, p->d32, 1.0f, -1.0f, 0.0f, nullptr, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double t = ms / reps;
+            if (st == RTE_OK && t < best) {
+                best = t;
+                bq = cands[c];
+                brb = rbs[r];
+            }
+        }
+        rte_destroy(p);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best >= 1e30) return RTE_ECUDA;
+    if (Q_out) *Q_out = bq;
+    if (rb_out) *rb_out = brb;
+    if (ms_out) *ms_out = best;
+    return RTE_OK;
+}

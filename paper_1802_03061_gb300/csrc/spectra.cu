@@ -70,7 +70,7 @@ __device__ void gl_node(int N, int i, double* x, double* w) {
         pp = N * (z * p1 - p2) / (z * z - 1.0);
         double z1 = z;
         z = z1 - p1 / pp;
-        if (fabs(z - z1) < 1e-16) break;
+        if (fabs(z - z1) < 1e-15) break;
     }
     // final derivative at the converged node
     double p1 = 1.0, p2 = 0.0;
@@ -108,7 +108,16 @@ __global__ void k_cell_weights_2d(double mu, double h, int mmax, double* D) {
         sincos(phi, &s, &c);
         const double R = a / fmax(fabs(c), fabs(s));
         const double rad = radial_factor(mu, R) * w * (M_PI / 8);
-        for (int m = 0; m <= mmax; ++m) part[m] += cos(m * phi) * rad;
+        // cos(m phi) by the Chebyshev recurrence c_m = 2 cos(phi) c_{m-1} - c_{m-2}
+        double cm2 = 1.0, cm1 = c;
+        part[0] += rad;
+        if (mmax >= 1) part[1] += c * rad;
+        for (int m = 2; m <= mmax; ++m) {
+            const double cm = 2.0 * c * cm1 - cm2;
+            part[m] += cm * rad;
+            cm2 = cm1;
+            cm1 = cm;
+        }
     }
     for (int m = 0; m <= mmax; ++m) acc[i][m] = part[m];
     __syncthreads();

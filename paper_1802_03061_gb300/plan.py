@@ -1,8 +1,43 @@
 """Torch-tensor convenience wrapper over the C ABI (allocation and streams only)."""
+import json
+import os
+
 import numpy as np
 import torch
 
 from . import _binding as B
+
+TUNE_CACHE = os.environ.get("RTE_TUNE_CACHE",
+                            os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json"))
+
+
+def autotune(shapes, prec="mixed_fp32", reps=10, cache_path=TUNE_CACHE, stream=None):
+    """Pick (Q, rows per block) for each (n, L) by measurement (rte_autotune),
+    persisting results in a JSON cache keyed by device name, n, L and prec."""
+    dev = torch.cuda.get_device_name()
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
+            cache = {}
+    out = {}
+    changed = False
+    for (n, L) in sorted(set(shapes)):
+        key = "%s|%d|%d|%s" % (dev, n, L, prec)
+        if key not in cache:
+            q, rb, ms = B.rte_autotune(n, L, prec, reps, _stream_ptr(stream))
+            cache[key] = {"q": q, "rows_per_block": rb, "ms": ms}
+            changed = True
+        out[(n, L)] = cache[key]
+    if changed and cache_path:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1)
+        os.replace(tmp, cache_path)
+    return out
 
 
 def _stream_ptr(stream):
@@ -102,6 +137,60 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             B.rte_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent 2D instances solved by one graph launch.
+
+    instances: list of dicts (n, h, mu_t, mu_s, sigma_hat[, q, rows_per_block]).
+    """
+
+    def __init__(self, instances, prec="mixed_fp32", tol=1e-8, restart=30, maxit=2000, inner_tol=1e-4, stream=None,
+                 tune=False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.instances = [dict(d) for d in instances]
+        if tune:
+            shapes = [(int(d["n"]), len(d["sigma_hat"]) - 1) for d in self.instances]
+            best = autotune(shapes, prec if prec != "fp64" else "mixed_fp32")
+            for d in self.instances:
+                t = best[(int(d["n"]), len(d["sigma_hat"]) - 1)]
+                d["q"], d["rows_per_block"] = t["q"], t["rows_per_block"]
+        self.count = len(self.instances)
+        self.opts = B.make_opts(prec, tol, restart, maxit, inner_tol, 0, 0)
+        self.handle = B.rte_batch_create(self.instances, self.opts, _stream_ptr(stream))
+        self.f_off, self.u_off = B.rte_batch_layout(self.handle, self.count)
+
+    def pack_sources(self, sources):
+        f = torch.empty(self.f_off[-1], dtype=torch.float64, device="cuda")
+        for i, src in enumerate(sources):
+            f[self.f_off[i]:self.f_off[i + 1]] = torch.as_tensor(src, dtype=torch.float64).reshape(-1).to("cuda")
+        return f
+
+    def unpack(self, u_packed, i):
+        d = self.instances[i]
+        L = len(d["sigma_hat"]) - 1
+        n = int(d["n"])
+        seg = u_packed[self.u_off[i]:self.u_off[i + 1]]
+        return torch.view_as_complex(seg.view(L + 1, n, n, 2))
+
+    def solve(self, f_packed, u_packed=None, stream=None):
+        if u_packed is None:
+            u_packed = torch.zeros(self.u_off[-1], dtype=torch.float64, device="cuda")
+        st, stats, ms = B.rte_batch_solve(self.handle, self.count, f_packed.data_ptr(), u_packed.data_ptr(),
+                                          _stream_ptr(stream))
+        return u_packed, stats, ms
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.rte_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

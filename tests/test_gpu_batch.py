@@ -1,0 +1,96 @@
+"""Batched solves (one graph launch, uneven instances) against single solves
+and the oracle.  Mixed tolerance: cond_est * tol per instance."""
+import numpy as np
+import pytest
+
+import oracle
+import rte_synth
+from _util import rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_03061_gb300 import build
+    build.build()
+
+
+def _small_instances(count=12, seed=21):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice([6, 8, 11, 16]))
+        L = int(rng.choice([0, 1, 2, 4]))
+        out.append(rte_synth.random_instance_2d(rng, n, L))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["mixed_fp32", "fp64"])
+def test_small_batch_matches_dense_oracle(prec):
+    from paper_1802_03061_gb300 import Batch
+    inst = _small_instances()
+    b = Batch(inst, prec=prec, tol=1e-10)
+    f = b.pack_sources([d["f"] for d in inst])
+    u, stats, ms = b.solve(f)
+    torch.cuda.synchronize()
+    for i, d in enumerate(inst):
+        assert stats[i]["converged"] and stats[i]["relres_true"] <= 1e-10
+        L = len(d["sigma_hat"]) - 1
+        u_ref, _ = oracle.solve_dense_2d(d["n"], d["h"], d["mu_t"], d["mu_s"], d["sigma_hat"], d["f"])
+        rho = d["mu_s"] / d["mu_t"]
+        cond = (1 + rho) / (1 - rho)
+        assert rel(b.unpack(u, i).cpu().numpy(), u_ref[L:]) <= 2 * cond * 1e-10
+    # a second launch of the same graph gives the same answers
+    u2, stats2, _ = b.solve(f)
+    assert torch.equal(u, u2)
+    b.close()
+
+
+def test_batch_matches_single_plan_solves():
+    from paper_1802_03061_gb300 import Batch, Plan
+    inst = _small_instances(count=6, seed=5)
+    b = Batch(inst, prec="mixed_bf16", tol=1e-9)
+    f = b.pack_sources([d["f"] for d in inst])
+    u, stats, _ = b.solve(f)
+    for i, d in enumerate(inst):
+        p = Plan(d["n"], h=d["h"], mu_t=d["mu_t"], mu_s=d["mu_s"], sigma_hat=d["sigma_hat"], prec="mixed_bf16",
+                 restart=30)
+        us, st = p.solve(torch.from_numpy(d["f"]), tol=1e-9)
+        assert st["iters"] == stats[i]["iters"]
+        assert rel(b.unpack(u, i).cpu().numpy(), us.cpu().numpy()) < 1e-12
+        p.close()
+    b.close()
+
+
+def test_autotuner_returns_a_valid_choice():
+    from paper_1802_03061_gb300 import _binding as B
+    q, rb, ms = B.rte_autotune(96, 2, "mixed_fp32", 5)
+    assert q >= 191 and q % 2 == 0 and rb in (2, 4, 8, 16) and ms > 0
+
+
+def test_full_batch_workload_512_instances():
+    """512 instances, sides in {64..512}, L in {0,2,4,8}, mu_t log-U[1,50],
+    mu_s/mu_t U[0.5,0.99], HG g U[0,0.8], 1-6 Gaussians: one launch, every
+    instance to 1e-8; the oracle's sampled FP64 residual for the n = 64 ones."""
+    from paper_1802_03061_gb300 import Batch
+    inst = rte_synth.batch_instances()
+    b = Batch(inst, prec="mixed_fp32", tol=1e-8, restart=30, maxit=4000)
+    f = b.pack_sources([d["f"] for d in inst])
+    u, stats, ms = b.solve(f)
+    assert all(s["converged"] for s in stats), [i for i, s in enumerate(stats) if not s["converged"]][:10]
+    assert max(s["relres_true"] for s in stats) <= 1e-8
+    small = [i for i, d in enumerate(inst) if d["n"] == 64][:4]
+    for i in small:
+        d = inst[i]
+        L = len(d["sigma_hat"]) - 1
+        uf = b.unpack(u, i).cpu().numpy()
+        full = np.concatenate([np.conj(uf[:0:-1]), uf]) if L else uf
+        supp = np.flatnonzero(d["f"].reshape(-1) > 1e-2 * d["f"].max())
+        rows = np.random.default_rng(i).choice(supp, size=12, replace=False)
+        r, bb = oracle.sampled_residual_2d(d["n"], d["h"], d["mu_t"], d["mu_s"], d["sigma_hat"], d["f"], full, rows)
+        assert np.linalg.norm(r) / np.linalg.norm(bb) < 1e-7
+    b.close()
