@@ -174,6 +174,8 @@ rte_status rte_batch_layout(rte_batch b, long* f_offsets_host, long* u_offsets_h
 rte_status rte_batch_solve(rte_batch b, const double* f_packed_dev, double* u_packed_dev, rte_stats* stats_host,
                            double* ms_out, void* cuda_stream);
 rte_status rte_batch_destroy(rte_batch b);
+/* The plan of instance i (owned by the batch; valid until rte_batch_destroy). */
+rte_status rte_batch_plan(rte_batch b, int i, rte_plan* out);
 
 /* Autotuner: for a 2D grid of n cells per side and truncation L, time the
  * FP32 operator application (prec = RTE_PREC_MIXED_FP32 or _BF16SPEC) for
@@ -183,6 +185,46 @@ rte_status rte_batch_destroy(rte_batch b);
  * in ms per application.  Allocates temporary plans. */
 rte_status rte_autotune(int n, int L, int prec, int reps, int* Q_out, int* rows_per_block_out, double* ms_out,
                         void* cuda_stream);
+
+/* ---- Learned initial guess (task extension; no counterpart in the paper) ----
+ * A 3x3 convolutional network on the 2D grid: NHWC BF16 activations with 16
+ * input channels (the 2L+1 real channels of b = K~ g scaled by s_b, f / fmax,
+ * log(mu_t)/4, mu_s/mu_t, sigma_hat_1, zero padding), hidden width 64, 16
+ * output channels of which the first 2L+1 are the scaled correction:
+ * u0 = b + s_b * net.  FP32 accumulation on the BF16 tensor cores; trained on
+ * the GPU by the library's own forward, data-gradient and weight-gradient
+ * kernels with Adam.  The solve uses u0 through opts->use_guess and falls
+ * back to the zero start when ||b - (I-K) u0|| >= ||b||. */
+typedef struct rte_cnn_s* rte_cnn;
+/* cin, cout in {16, 32}; width = 64; depth >= 2. */
+rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth, int cout, unsigned long long seed,
+                          void* cuda_stream);
+rte_status rte_cnn_destroy(rte_cnn net);
+/* y_dev (f32 [B][H][W][cout]) = net(X_dev), X_dev bf16 [B][H][W][cin]. */
+rte_status rte_cnn_forward(rte_cnn net, const void* X_dev, int B, int H, int W, float* y_dev, void* cuda_stream);
+/* One training step on a batch: loss = mean over pixels and the first `used`
+ * output channels of (net(X) - T)^2 (T bf16 [B][H][W][cout]); weight and bias
+ * gradients are left in the layers; an Adam step with rate lr when lr > 0.
+ * loss_out (host, may be NULL) receives the loss (synchronises). */
+rte_status rte_cnn_train_step(rte_cnn net, const void* X_dev, const void* T_dev, int B, int H, int W, int used,
+                              float lr, float* loss_out, void* cuda_stream);
+/* Device pointers of layer l: weights f32 [9][cin][cout] (tap = 3(dy+1)+(dx+1)),
+ * bias f32 [cout], and their gradients from the last training step. */
+rte_status rte_cnn_layer(rte_cnn net, int l, int* cin, int* cout, float** w_dev, float** bias_dev, float** gw_dev,
+                         float** gb_dev);
+/* Refresh the BF16 weight copies after the FP32 weights were written. */
+rte_status rte_cnn_sync_weights(rte_cnn net, void* cuda_stream);
+/* Network input (cin channels, 2L+5 <= cin) / training target (cout
+ * channels, 2L+1 <= cout) of plan p (2D) from the source f (double [n][n]),
+ * b = K~ g and, for targets, the solution u (FP64 mode fields); s_b scales b
+ * and the correction, fmax scales f.  X_dev / T_dev: bf16 [n][n][cin|cout]. */
+rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const double* b_dev, double s_b, double fmax,
+                              void* X_dev, void* cuda_stream);
+rte_status rte_guess_targets(rte_plan p, int cout, const double* u_dev, const double* b_dev, double s_b, void* T_dev,
+                             void* cuda_stream);
+/* u0_dev (FP64 mode field) = b + s_b * net(features); X_scratch_dev: bf16 [n][n][cin]. */
+rte_status rte_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, const double* b_dev, double s_b, double fmax,
+                           void* X_scratch_dev, void* u0_dev, void* cuda_stream);
 
 /* Diagnostics (no counterpart in the paper).
  * rte_time_passes: average duration in ms of each FFT pass of one K

@@ -87,6 +87,24 @@ def lib():
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), VP]
         for name in ("rte_batch_create", "rte_batch_layout", "rte_batch_solve", "rte_batch_destroy", "rte_autotune"):
             getattr(L, name).restype = ctypes.c_int
+        FP = ctypes.POINTER(ctypes.c_float)
+        L.rte_cnn_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_ulonglong, VP]
+        L.rte_cnn_destroy.argtypes = [VP]
+        L.rte_cnn_forward.argtypes = [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, VP, VP]
+        L.rte_cnn_train_step.argtypes = [VP, VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_float, FP, VP]
+        L.rte_cnn_layer.argtypes = [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP)]
+        L.rte_cnn_sync_weights.argtypes = [VP, VP]
+        L.rte_guess_features.argtypes = [VP, ctypes.c_int, VP, VP, ctypes.c_double, ctypes.c_double, VP, VP]
+        L.rte_guess_targets.argtypes = [VP, ctypes.c_int, VP, VP, ctypes.c_double, VP, VP]
+        L.rte_guess_apply.argtypes = [VP, VP, VP, VP, ctypes.c_double, ctypes.c_double, VP, VP, VP]
+        L.rte_batch_plan.argtypes = [VP, ctypes.c_int, ctypes.POINTER(VP)]
+        for name in ("rte_cnn_create", "rte_cnn_destroy", "rte_cnn_forward", "rte_cnn_train_step", "rte_cnn_layer",
+                     "rte_cnn_sync_weights", "rte_guess_features", "rte_guess_targets", "rte_guess_apply",
+                     "rte_batch_plan"):
+            getattr(L, name).restype = ctypes.c_int
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
         L.rte_last_error.restype = ctypes.c_char_p
@@ -236,6 +254,59 @@ def rte_autotune(n, L, prec="mixed_fp32", reps=20, stream=0):
     _check(lib().rte_autotune(int(n), int(L), PREC[prec] if isinstance(prec, str) else int(prec), int(reps),
                               ctypes.byref(q), ctypes.byref(rb), ctypes.byref(ms), VP(stream)), "rte_autotune")
     return q.value, rb.value, ms.value
+
+
+def rte_batch_plan(batch, i):
+    out = VP()
+    _check(lib().rte_batch_plan(batch, int(i), ctypes.byref(out)), "rte_batch_plan")
+    return out
+
+
+def rte_cnn_create(cin=16, width=64, depth=6, cout=16, seed=0, stream=0):
+    out = VP()
+    _check(lib().rte_cnn_create(ctypes.byref(out), cin, width, depth, cout, seed, VP(stream)), "rte_cnn_create")
+    return out
+
+
+def rte_cnn_destroy(net):
+    _check(lib().rte_cnn_destroy(net), "rte_cnn_destroy")
+
+
+def rte_cnn_forward(net, X, B, H, W, y, stream=0):
+    _check(lib().rte_cnn_forward(net, VP(X), B, H, W, VP(y), VP(stream)), "rte_cnn_forward")
+
+
+def rte_cnn_train_step(net, X, T, B, H, W, used, lr, want_loss=True, stream=0):
+    loss = ctypes.c_float()
+    _check(lib().rte_cnn_train_step(net, VP(X), VP(T), B, H, W, used, float(lr),
+                                    ctypes.byref(loss) if want_loss else None, VP(stream)), "rte_cnn_train_step")
+    return loss.value
+
+
+def rte_cnn_layer(net, l):
+    ci, co = ctypes.c_int(), ctypes.c_int()
+    w, b, gw, gb = VP(), VP(), VP(), VP()
+    _check(lib().rte_cnn_layer(net, l, ctypes.byref(ci), ctypes.byref(co), ctypes.byref(w), ctypes.byref(b),
+                               ctypes.byref(gw), ctypes.byref(gb)), "rte_cnn_layer")
+    return dict(cin=ci.value, cout=co.value, w=w.value, b=b.value, gw=gw.value, gb=gb.value)
+
+
+def rte_cnn_sync_weights(net, stream=0):
+    _check(lib().rte_cnn_sync_weights(net, VP(stream)), "rte_cnn_sync_weights")
+
+
+def rte_guess_features(plan, cin, f, b, s_b, fmax, X, stream=0):
+    _check(lib().rte_guess_features(plan, cin, VP(f), VP(b), float(s_b), float(fmax), VP(X), VP(stream)),
+           "rte_guess_features")
+
+
+def rte_guess_targets(plan, cout, u, b, s_b, T, stream=0):
+    _check(lib().rte_guess_targets(plan, cout, VP(u), VP(b), float(s_b), VP(T), VP(stream)), "rte_guess_targets")
+
+
+def rte_guess_apply(net, plan, f, b, s_b, fmax, Xs, u0, stream=0):
+    _check(lib().rte_guess_apply(net, plan, VP(f), VP(b), float(s_b), float(fmax), VP(Xs), VP(u0), VP(stream)),
+           "rte_guess_apply")
 
 
 def rte_destroy(plan):

@@ -52,7 +52,6 @@ extern "C" rte_status rte_batch_create(rte_batch* out, int count, const rte_inst
                                        const rte_opts* opts, void* stream) {
     if (!out || count < 1 || !descs) return RTE_EINVAL;
     *out = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
     rte_batch b = new rte_batch_s();
     rte_opts o;
     memset(&o, 0, sizeof(o));
@@ -146,7 +145,6 @@ extern "C" rte_status rte_batch_create(rte_batch* out, int count, const rte_inst
     }
     cudaGraphDestroy(g);
     if (st != RTE_OK) { rte_batch_destroy(b); return st; }
-    (void)s;
     *out = b;
     return RTE_OK;
 }
@@ -195,4 +193,10 @@ extern "C" rte_status rte_batch_solve(rte_batch b, const double* f_packed, doubl
         if (st != RTE_OK && worst == RTE_OK) worst = st;
     }
     return worst;
+}
+
+extern "C" rte_status rte_batch_plan(rte_batch b, int i, rte_plan* out) {
+    if (!b || !out || i < 0 || i >= b->count) return RTE_EINVAL;
+    *out = b->plans[i];
+    return RTE_OK;
 }

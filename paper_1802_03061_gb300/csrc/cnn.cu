@@ -1,0 +1,708 @@
+// Learned initial guess for the GMRES solve (task extension; the paper has
+// no counterpart): a small 3x3 convolutional network, NHWC BF16 activations,
+// FP32 accumulation on the BF16 tensor cores (mma.sync m16n8k16), trained on
+// the GPU by its own forward / data-gradient / weight-gradient kernels and
+// Adam.
+//
+// Layer l: Y = act(conv3x3(X, W_l) + bias_l), same padding (zeros outside the
+// image), channel counts padded to multiples of 16.  Weights W_l[tap][cin][cout]
+// (tap = 3*(dy+1) + (dx+1)); a master FP32 copy is updated by Adam, the BF16
+// copy feeds the kernels.
+//
+// Implicit GEMM: rows = output pixels (a run of 128 along x in one image row),
+// columns = output channels, reduction = 9 taps x input channels.  The
+// data gradient is the same product with the taps mirrored and W transposed;
+// the weight gradient reduces over pixels: dW[tap][ci][co] = sum_p
+// X[p + d(tap)][ci] dY[p][co], written as per-block partial sums and reduced
+// in a fixed order.
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+
+typedef __nv_bfloat16 bf16;
+
+#define CNN_TILE 128       // pixels per block (along x)
+#define CNN_WARPS 4        // 32 pixels per warp
+#define CNN_APAD 24        // smem row pitch (bf16) for 16-wide k slices: conflict-free fragments
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ---------------------------------------------------------------------------
+// forward / data-gradient convolution
+//   out[p][n] = sum_tap sum_c X[p + s*d(tap)][c] * Wt(tap, c, n)
+//   Wt(tap, c, n) = W[tap*sT + c*sC + n*sN]; s = +1 (forward) or -1 (data gradient,
+//   dX[q] = sum_tap dY[q - d(tap)] W[tap]^T)
+// X: [B][H][Wd][CX] bf16; out: [B][H][Wd][NOUT] (bf16 or f32)
+// grid: (ceil(Wd/128), H, B), block 128 threads
+// ---------------------------------------------------------------------------
+template <int NOUT>
+__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ X, int CX, const bf16* __restrict__ W, long sT,
+                                              long sC, long sN, int flip, const float* __restrict__ bias, int relu,
+                                              bf16* __restrict__ Ybf, float* __restrict__ Yf, int H, int Wd) {
+    __shared__ __align__(16) bf16 As[CNN_TILE * CNN_APAD];
+    __shared__ __align__(16) bf16 Bs[NOUT * CNN_APAD];
+    const int x0 = blockIdx.x * CNN_TILE, y = blockIdx.y, b = blockIdx.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    constexpr int NT = NOUT / 8;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const int sgn = flip ? -1 : 1;
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
+        const int yy = y + dy;
+        const int wt = tap;
+        for (int c0 = 0; c0 < CX; c0 += 16) {
+            __syncthreads();
+            // A tile: 128 pixels x 16 channels (one pixel per thread, 2 x 16 B)
+            {
+                const int i = threadIdx.x;
+                const int xx = x0 + i + dx;
+                uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < Wd && x0 + i < Wd) {
+                    const uint4* src = reinterpret_cast<const uint4*>(X + (((long)b * H + yy) * Wd + xx) * CX + c0);
+                    v0 = src[0];
+                    v1 = src[1];
+                }
+                uint4* dst = reinterpret_cast<uint4*>(As + i * CNN_APAD);
+                dst[0] = v0;
+                dst[1] = v1;
+            }
+            // B tile: [n][k] = Wt(tap, c0 + k, n)
+            for (int e = threadIdx.x; e < NOUT * 16; e += blockDim.x) {
+                const int n = e / 16, k = e % 16;
+                Bs[n * CNN_APAD + k] = W[wt * sT + (long)(c0 + k) * sC + (long)n * sN];
+            }
+            __syncthreads();
+            uint32_t af[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = warp * 32 + mt * 16 + g;
+                af[mt][0] = ld32(As + r * CNN_APAD + 2 * t);
+                af[mt][1] = ld32(As + (r + 8) * CNN_APAD + 2 * t);
+                af[mt][2] = ld32(As + r * CNN_APAD + 2 * t + 8);
+                af[mt][3] = ld32(As + (r + 8) * CNN_APAD + 2 * t + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                uint32_t bfr[2];
+                const int n = nt * 8 + g;
+                bfr[0] = ld32(Bs + n * CNN_APAD + 2 * t);
+                bfr[1] = ld32(Bs + n * CNN_APAD + 2 * t + 8);
+                mma_bf16(acc[0][nt], af[0], bfr);
+                mma_bf16(acc[1][nt], af[1], bfr);
+            }
+        }
+    }
+    // epilogue: bias, activation, store
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int px = x0 + warp * 32 + mt * 16 + g + 8 * half;
+            if (px >= Wd) continue;
+            const long o = (((long)b * H + y) * Wd + px) * NOUT;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int n = nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if (bias) { v0 += bias[n]; v1 += bias[n + 1]; }
+                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                if (Yf) {
+                    Yf[o + n] = v0;
+                    Yf[o + n + 1] = v1;
+                } else {
+                    *reinterpret_cast<__nv_bfloat162*>(Ybf + o + n) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient partials: part[blk][tap][ci][co] = sum over the block's
+// pixels of X[p + d(tap)][ci] * dY[p][co]; grid (nblk_pix, 9), block 128.
+// Each block reduces over PIXB pixels (rows of Wd pixels, whole rows).
+// ---------------------------------------------------------------------------
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY,
+                                                    float* __restrict__ part, int B, int H, int Wd, int rows_per_blk) {
+    // As: [ci][16 pixels], Bs: [co][16 pixels]
+    __shared__ __align__(16) bf16 As[CI * CNN_APAD];
+    __shared__ __align__(16) bf16 Bs[CO * CNN_APAD];
+    const int tap = blockIdx.y;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    // warp tiling of the CI x CO output: MT m-tiles (16) x NT n-tiles (8) per warp
+    constexpr int MTOT = CI / 16, NTOT = CO / 8;
+    constexpr int WM = (MTOT >= 2) ? 2 : 1;           // warps along m
+    constexpr int WN = CNN_WARPS / WM;                // warps along n
+    constexpr int MT = MTOT / WM, NT = NTOT / WN;
+    float acc[MT][NT > 0 ? NT : 1][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < (NT > 0 ? NT : 1); ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const int wm = warp % WM, wn = warp / WM;
+    const long rows_total = (long)B * H;
+    const long r0 = (long)blockIdx.x * rows_per_blk;
+    for (long rr = r0; rr < r0 + rows_per_blk && rr < rows_total; ++rr) {
+        const int b = (int)(rr / H), y = (int)(rr % H);
+        const int yy = y + dy;
+        for (int x0 = 0; x0 < Wd; x0 += 16) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < 16 * CI; e += blockDim.x) {
+                const int k = e / CI, ci = e % CI;
+                const int x = x0 + k, xx = x + dx;
+                bf16 v = __float2bfloat16(0.f);
+                if (x < Wd && yy >= 0 && yy < H && xx >= 0 && xx < Wd) v = X[(((long)b * H + yy) * Wd + xx) * CI + ci];
+                As[ci * CNN_APAD + k] = v;
+            }
+            for (int e = threadIdx.x; e < 16 * CO; e += blockDim.x) {
+                const int k = e / CO, co = e % CO;
+                const int x = x0 + k;
+                bf16 v = __float2bfloat16(0.f);
+                if (x < Wd) v = dY[(((long)b * H + y) * Wd + x) * CO + co];
+                Bs[co * CNN_APAD + k] = v;
+            }
+            __syncthreads();
+            if (NT > 0) {
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    uint32_t af[4];
+                    const int r = (wm * MT + mt) * 16 + g;
+                    af[0] = ld32(As + r * CNN_APAD + 2 * t);
+                    af[1] = ld32(As + (r + 8) * CNN_APAD + 2 * t);
+                    af[2] = ld32(As + r * CNN_APAD + 2 * t + 8);
+                    af[3] = ld32(As + (r + 8) * CNN_APAD + 2 * t + 8);
+#pragma unroll
+                    for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt) {
+                        uint32_t bfr[2];
+                        const int n = (wn * NT + nt) * 8 + g;
+                        bfr[0] = ld32(Bs + n * CNN_APAD + 2 * t);
+                        bfr[1] = ld32(Bs + n * CNN_APAD + 2 * t + 8);
+                        mma_bf16(acc[mt][nt], af, bfr);
+                    }
+                }
+            }
+        }
+    }
+    float* dst = part + ((long)blockIdx.x * 9 + tap) * CI * CO;
+    if (NT > 0) {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt) {
+                const int r = (wm * MT + mt) * 16 + g;
+                const int n = (wn * NT + nt) * 8 + 2 * t;
+                dst[r * CO + n] = acc[mt][nt][0];
+                dst[r * CO + n + 1] = acc[mt][nt][1];
+                dst[(r + 8) * CO + n] = acc[mt][nt][2];
+                dst[(r + 8) * CO + n + 1] = acc[mt][nt][3];
+            }
+    }
+}
+
+// dW[i] = sum_b part[b][i] (fixed order), i < 9*CI*CO
+__global__ void k_reduce_parts(const float* __restrict__ part, int nblk, long per, float* __restrict__ dW) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += part[(long)b * per + i];
+        dW[i] = s;
+    }
+}
+
+// bias gradient: db[c] = sum_p dY[p][c]; one block per channel
+__global__ void k_bias_grad(const bf16* __restrict__ dY, long P, int C, float* __restrict__ db) {
+    const int c = blockIdx.x;
+    __shared__ float red[256];
+    float s = 0.f;
+    for (long p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dY[p * C + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] = red[0];
+}
+
+// dY *= (Y > 0)
+__global__ void k_relu_bwd(bf16* __restrict__ dY, const bf16* __restrict__ Y, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(Y[i]) > 0.f)) dY[i] = __float2bfloat16(0.f);
+}
+
+// mean squared error over the first `used` of C channels; dOut = d loss / d out (bf16)
+__global__ void k_mse(const float* __restrict__ out, const bf16* __restrict__ tgt, long P, int C, int used,
+                      bf16* __restrict__ dOut, float* __restrict__ loss_part) {
+    __shared__ float red[256];
+    const double inv = 1.0 / ((double)P * used);
+    float s = 0.f;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < P * C; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        float d = 0.f;
+        if (c < used) {
+            d = out[i] - __bfloat162float(tgt[i]);
+            s += d * d;
+        }
+        dOut[i] = __float2bfloat16((float)(2.0 * inv) * d);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = (float)(red[0] * inv);
+}
+
+// Adam (Kingma & Ba) on FP32 master weights; BF16 copy refreshed
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
+                       bf16* __restrict__ wb, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16(a[i]);
+}
+
+// deterministic weight init: uniform(-a, a) from a counter hash (splitmix64)
+__global__ void k_init_uniform(float* __restrict__ w, long n, unsigned long long seed, float a) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float u = (float)((z >> 40) * (1.0 / 16777216.0));
+        w[i] = (2.f * u - 1.f) * a;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// features and output mapping for the RTE solve (2D mode fields, L <= 7)
+//   channels: b_c / s (2L+1 real channels of b = K~ g), f / fmax, log(mu_t)/4,
+//   mu_s/mu_t, g, zeros to CIN
+//   u0 = b + s * net_c  (first 2L+1 output channels)
+// ---------------------------------------------------------------------------
+__global__ void k_features(const double* __restrict__ bmode, const double* __restrict__ f, int n, int L, double s_b,
+                           double fmax, float p0, float p1, float p2, int CIN, bf16* __restrict__ X) {
+    const long P = (long)n * n;
+    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
+        bf16* xp = X + p * CIN;
+        int c = 0;
+        const double inv = s_b > 0 ? 1.0 / s_b : 0.0;
+        xp[c++] = __float2bfloat16((float)(bmode[2 * p] * inv));
+        for (int k = 1; k <= L; ++k) {
+            xp[c++] = __float2bfloat16((float)(bmode[2 * (k * P + p)] * inv));
+            xp[c++] = __float2bfloat16((float)(bmode[2 * (k * P + p) + 1] * inv));
+        }
+        xp[c++] = __float2bfloat16((float)(fmax > 0 ? f[p] / fmax : 0.0));
+        xp[c++] = __float2bfloat16(p0);
+        xp[c++] = __float2bfloat16(p1);
+        xp[c++] = __float2bfloat16(p2);
+        while (c < CIN) xp[c++] = __float2bfloat16(0.f);
+    }
+}
+
+__global__ void k_targets(const double* __restrict__ umode, const double* __restrict__ bmode, int n, int L, double s_b,
+                          int COUT, bf16* __restrict__ Yt) {
+    const long P = (long)n * n;
+    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
+        bf16* yp = Yt + p * COUT;
+        int c = 0;
+        const double inv = s_b > 0 ? 1.0 / s_b : 0.0;
+        yp[c++] = __float2bfloat16((float)((umode[2 * p] - bmode[2 * p]) * inv));
+        for (int k = 1; k <= L; ++k) {
+            const long o = 2 * (k * P + p);
+            yp[c++] = __float2bfloat16((float)((umode[o] - bmode[o]) * inv));
+            yp[c++] = __float2bfloat16((float)((umode[o + 1] - bmode[o + 1]) * inv));
+        }
+        while (c < COUT) yp[c++] = __float2bfloat16(0.f);
+    }
+}
+
+__global__ void k_guess_out(const float* __restrict__ net, const double* __restrict__ bmode, int n, int L, double s_b,
+                            int COUT, double* __restrict__ u0) {
+    const long P = (long)n * n;
+    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
+        const float* np = net + p * COUT;
+        u0[2 * p] = bmode[2 * p] + s_b * np[0];
+        u0[2 * p + 1] = 0.0;
+        int c = 1;
+        for (int k = 1; k <= L; ++k) {
+            const long o = 2 * (k * P + p);
+            u0[o] = bmode[o] + s_b * np[c++];
+            u0[o + 1] = bmode[o + 1] + s_b * np[c++];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct CnnLayer {
+    int cin, cout;   // padded channel counts
+    float* w = nullptr;
+    float* bias = nullptr;
+    bf16* wb = nullptr;
+    float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr, *gw = nullptr, *gb = nullptr;
+};
+
+struct rte_cnn_s {
+    int cin = 16, width = 64, depth = 6, cout = 16;
+    std::vector<CnnLayer> layers;
+    // activations for the current batch shape
+    int B = 0, H = 0, W = 0;
+    std::vector<bf16*> act;    // act[0] = input, act[l+1] = output of layer l (bf16), last layer f32 in out_f
+    float* out_f = nullptr;
+    bf16* g0 = nullptr;        // gradient buffers (ping-pong), size P * max(width, cin, cout)
+    bf16* g1 = nullptr;
+    float* part = nullptr;     // weight-gradient partials
+    long part_cap = 0;
+    float* loss_part = nullptr;
+    float* loss_host = nullptr;
+    long step = 0;
+};
+
+static int nblk_pix(int B, int H) {
+    long rows = (long)B * H;
+    int rpb = 16;
+    return (int)((rows + rpb - 1) / rpb);
+}
+
+static cudaError_t conv_fwd(const bf16* X, int CX, const CnnLayer& Lr, bool relu, bf16* Ybf, float* Yf, int B, int H,
+                            int W, cudaStream_t s) {
+    dim3 grid((W + CNN_TILE - 1) / CNN_TILE, H, B);
+    const long sT = (long)Lr.cin * Lr.cout, sC = Lr.cout, sN = 1;
+    if (Lr.cout == 64)
+        k_conv<64><<<grid, 128, 0, s>>>(X, CX, Lr.wb, sT, sC, sN, 0, Lr.bias, relu, Ybf, Yf, H, W);
+    else if (Lr.cout == 32)
+        k_conv<32><<<grid, 128, 0, s>>>(X, CX, Lr.wb, sT, sC, sN, 0, Lr.bias, relu, Ybf, Yf, H, W);
+    else if (Lr.cout == 16)
+        k_conv<16><<<grid, 128, 0, s>>>(X, CX, Lr.wb, sT, sC, sN, 0, Lr.bias, relu, Ybf, Yf, H, W);
+    else
+        return cudaErrorInvalidValue;
+    rte_count_launches(1);
+    return cudaGetLastError();
+}
+
+// dX[p][ci] = sum_tap sum_co dY[p - d(tap)][co] W[tap][ci][co]
+static cudaError_t conv_dgrad(const bf16* dY, const CnnLayer& Lr, bf16* dX, int B, int H, int W, cudaStream_t s) {
+    dim3 grid((W + CNN_TILE - 1) / CNN_TILE, H, B);
+        // Wt(tap, c = co, n = ci) = W[tap][ci][co]: sC = 1 (co), sN = cout (ci)
+    const long sT = (long)Lr.cin * Lr.cout, sC = 1, sN = Lr.cout;
+    if (Lr.cin == 64)
+        k_conv<64><<<grid, 128, 0, s>>>(dY, Lr.cout, Lr.wb, sT, sC, sN, 1, nullptr, 0, dX, nullptr, H, W);
+    else if (Lr.cin == 32)
+        k_conv<32><<<grid, 128, 0, s>>>(dY, Lr.cout, Lr.wb, sT, sC, sN, 1, nullptr, 0, dX, nullptr, H, W);
+    else if (Lr.cin == 16)
+        k_conv<16><<<grid, 128, 0, s>>>(dY, Lr.cout, Lr.wb, sT, sC, sN, 1, nullptr, 0, dX, nullptr, H, W);
+    else
+        return cudaErrorInvalidValue;
+    rte_count_launches(1);
+    return cudaGetLastError();
+}
+
+static cudaError_t conv_wgrad(rte_cnn c, const bf16* X, const bf16* dY, CnnLayer& Lr, int B, int H, int W,
+                              cudaStream_t s) {
+    const int nb = nblk_pix(B, H);
+    const long per = 9L * Lr.cin * Lr.cout;
+    if ((long)nb * per > c->part_cap) return cudaErrorInvalidValue;
+    dim3 grid(nb, 9);
+    if (Lr.cin == 64 && Lr.cout == 64) k_conv_wgrad<64, 64><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
+    else if (Lr.cin == 16 && Lr.cout == 64) k_conv_wgrad<16, 64><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
+    else if (Lr.cin == 32 && Lr.cout == 64) k_conv_wgrad<32, 64><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
+    else if (Lr.cin == 64 && Lr.cout == 16) k_conv_wgrad<64, 16><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
+    else if (Lr.cin == 64 && Lr.cout == 32) k_conv_wgrad<64, 32><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
+    else return cudaErrorInvalidValue;
+    k_reduce_parts<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(c->part, nb, per, Lr.gw);
+    k_bias_grad<<<Lr.cout, 256, 0, s>>>(dY, (long)B * H * W, Lr.cout, Lr.gb);
+    rte_count_launches(3);
+    return cudaGetLastError();
+}
+
+static void cnn_free_acts(rte_cnn c) {
+    for (bf16* a : c->act) if (a) cudaFree(a);
+    c->act.clear();
+    if (c->out_f) cudaFree(c->out_f);
+    if (c->g0) cudaFree(c->g0);
+    if (c->g1) cudaFree(c->g1);
+    if (c->part) cudaFree(c->part);
+    if (c->loss_part) cudaFree(c->loss_part);
+    c->out_f = nullptr;
+    c->g0 = c->g1 = nullptr;
+    c->part = nullptr;
+    c->loss_part = nullptr;
+    c->B = c->H = c->W = 0;
+}
+
+static rte_status cnn_ensure(rte_cnn c, int B, int H, int W) {
+    if (c->B == B && c->H == H && c->W == W) return RTE_OK;
+    cnn_free_acts(c);
+    const long P = (long)B * H * W;
+    c->act.assign(c->depth + 1, nullptr);
+    for (int l = 0; l <= c->depth; ++l) {
+        const int ch = l == 0 ? c->cin : c->layers[l - 1].cout;
+        if (cudaMalloc((void**)&c->act[l], P * ch * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+    }
+    const int wmax = c->width > c->cin ? c->width : c->cin;
+    if (cudaMalloc((void**)&c->out_f, P * c->cout * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->g0, P * wmax * sizeof(bf16)) != cudaSuccess ||
+        cudaMalloc((void**)&c->g1, P * wmax * sizeof(bf16)) != cudaSuccess) {
+        cudaGetLastError();
+        return RTE_ENOMEM;
+    }
+    c->part_cap = (long)nblk_pix(B, H) * 9 * 64 * 64;
+    if (cudaMalloc((void**)&c->part, c->part_cap * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->loss_part, 1024 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return RTE_ENOMEM;
+    }
+    c->B = B;
+    c->H = H;
+    c->W = W;
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_cnn_destroy(rte_cnn c) {
+    if (!c) return RTE_OK;
+    cudaDeviceSynchronize();
+    cnn_free_acts(c);
+    for (CnnLayer& L : c->layers) {
+        void* ptrs[] = {L.w, L.bias, L.wb, L.mw, L.vw, L.mb, L.vb, L.gw, L.gb};
+        for (void* p : ptrs) if (p) cudaFree(p);
+    }
+    if (c->loss_host) cudaFreeHost(c->loss_host);
+    delete c;
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth, int cout, unsigned long long seed,
+                                     void* stream) {
+    if (!out || depth < 2 || (cin != 16 && cin != 32) || (width != 64) || (cout != 16 && cout != 32)) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    rte_cnn c = new rte_cnn_s();
+    c->cin = cin;
+    c->width = width;
+    c->depth = depth;
+    c->cout = cout;
+    c->layers.resize(depth);
+    for (int l = 0; l < depth; ++l) {
+        CnnLayer& L = c->layers[l];
+        L.cin = l == 0 ? cin : width;
+        L.cout = l == depth - 1 ? cout : width;
+        const long nw = 9L * L.cin * L.cout;
+        bool ok = cudaMalloc((void**)&L.w, nw * 4) == cudaSuccess && cudaMalloc((void**)&L.wb, nw * 2) == cudaSuccess &&
+                  cudaMalloc((void**)&L.mw, nw * 4) == cudaSuccess && cudaMalloc((void**)&L.vw, nw * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.gw, nw * 4) == cudaSuccess && cudaMalloc((void**)&L.bias, L.cout * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.mb, L.cout * 4) == cudaSuccess && cudaMalloc((void**)&L.vb, L.cout * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.gb, L.cout * 4) == cudaSuccess;
+        if (!ok) { cudaGetLastError(); rte_cnn_destroy(c); return RTE_ENOMEM; }
+        // He-uniform init; the last layer starts small so the first guess is ~b
+        const float a = (l == depth - 1 ? 0.1f : 1.0f) * sqrtf(6.f / (9.f * L.cin));
+        k_init_uniform<<<256, 256, 0, s>>>(L.w, nw, seed * 131 + l, a);
+        k_to_bf16<<<256, 256, 0, s>>>(L.w, L.wb, nw);
+        cudaMemsetAsync(L.bias, 0, L.cout * 4, s);
+        cudaMemsetAsync(L.mw, 0, nw * 4, s);
+        cudaMemsetAsync(L.vw, 0, nw * 4, s);
+        cudaMemsetAsync(L.mb, 0, L.cout * 4, s);
+        cudaMemsetAsync(L.vb, 0, L.cout * 4, s);
+        rte_count_launches(2);
+    }
+    if (cudaMallocHost((void**)&c->loss_host, 1024 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        rte_cnn_destroy(c);
+        return RTE_ENOMEM;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { rte_cnn_destroy(c); return rte_cuda_fail(e, "rte_cnn_create"); }
+    *out = c;
+    return RTE_OK;
+}
+
+static rte_status cnn_forward_internal(rte_cnn c, const bf16* X, int B, int H, int W, cudaStream_t s) {
+    rte_status st = cnn_ensure(c, B, H, W);
+    if (st != RTE_OK) return st;
+    const long P = (long)B * H * W;
+    RTE_CUDA_TRY(cudaMemcpyAsync(c->act[0], X, P * c->cin * sizeof(bf16), cudaMemcpyDeviceToDevice, s));
+    for (int l = 0; l < c->depth; ++l) {
+        const CnnLayer& L = c->layers[l];
+        const bool last = l == c->depth - 1;
+        cudaError_t e = conv_fwd(c->act[l], L.cin, L, !last, last ? nullptr : c->act[l + 1], last ? c->out_f : nullptr,
+                                 B, H, W, s);
+        if (e != cudaSuccess) return rte_cuda_fail(e, "cnn forward");
+    }
+    return RTE_OK;
+}
+
+// y_out (device, f32 [B][H][W][cout]) = net(X)
+extern "C" rte_status rte_cnn_forward(rte_cnn c, const void* X_dev, int B, int H, int W, float* y_dev, void* stream) {
+    if (!c || !X_dev || !y_dev || B < 1 || H < 1 || W < 1) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    rte_status st = cnn_forward_internal(c, (const bf16*)X_dev, B, H, W, s);
+    if (st != RTE_OK) return st;
+    RTE_CUDA_TRY(cudaMemcpyAsync(y_dev, c->out_f, (long)B * H * W * c->cout * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return RTE_OK;
+}
+
+// backward from dOut (bf16 [P][cout]) through all layers into the weight gradients
+static rte_status cnn_backward(rte_cnn c, const bf16* dOut, int B, int H, int W, cudaStream_t s) {
+    const long P = (long)B * H * W;
+    RTE_CUDA_TRY(cudaMemcpyAsync(c->g0, dOut, P * c->cout * sizeof(bf16), cudaMemcpyDeviceToDevice, s));
+    bf16* gcur = c->g0;
+    bf16* gnext = c->g1;
+    for (int l = c->depth - 1; l >= 0; --l) {
+        CnnLayer& L = c->layers[l];
+        if (l < c->depth - 1) {
+            k_relu_bwd<<<1024, 256, 0, s>>>(gcur, c->act[l + 1], P * L.cout);
+            rte_count_launches(1);
+        }
+        cudaError_t e = conv_wgrad(c, c->act[l], gcur, L, B, H, W, s);
+        if (e != cudaSuccess) return rte_cuda_fail(e, "cnn wgrad");
+        if (l > 0) {
+            e = conv_dgrad(gcur, L, gnext, B, H, W, s);
+            if (e != cudaSuccess) return rte_cuda_fail(e, "cnn dgrad");
+            bf16* t = gcur;
+            gcur = gnext;
+            gnext = t;
+        }
+    }
+    return RTE_OK;
+}
+
+// gradients of 0.5 * sum ... are exposed for testing: loss = mean over P x used
+// of (net - target)^2; one Adam step when lr > 0.  X, T: bf16 [B][H][W][16].
+extern "C" rte_status rte_cnn_train_step(rte_cnn c, const void* X_dev, const void* T_dev, int B, int H, int W,
+                                         int used, float lr, float* loss_out, void* stream) {
+    if (!c || !X_dev || !T_dev || B < 1 || used < 1 || used > c->cout) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    rte_status st = cnn_forward_internal(c, (const bf16*)X_dev, B, H, W, s);
+    if (st != RTE_OK) return st;
+    const long P = (long)B * H * W;
+    const int nb = 512;
+    k_mse<<<nb, 256, 0, s>>>(c->out_f, (const bf16*)T_dev, P, c->cout, used, c->g1, c->loss_part);
+    RTE_CUDA_TRY(cudaGetLastError());
+    rte_count_launches(1);
+    // dOut sits in g1; backward copies it into g0 first
+    st = cnn_backward(c, c->g1, B, H, W, s);
+    if (st != RTE_OK) return st;
+    if (lr > 0.f) {
+        c->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
+        for (CnnLayer& L : c->layers) {
+            const long nw = 9L * L.cin * L.cout;
+            k_adam<<<256, 256, 0, s>>>(L.w, L.mw, L.vw, L.gw, L.wb, nw, lr, b1, b2, 1e-8f, c1, c2);
+            k_adam<<<1, 256, 0, s>>>(L.bias, L.mb, L.vb, L.gb, nullptr, L.cout, lr, b1, b2, 1e-8f, c1, c2);
+            rte_count_launches(2);
+        }
+        RTE_CUDA_TRY(cudaGetLastError());
+    }
+    if (loss_out) {
+        RTE_CUDA_TRY(cudaMemcpyAsync(c->loss_host, c->loss_part, nb * sizeof(float), cudaMemcpyDeviceToHost, s));
+        RTE_CUDA_TRY(cudaStreamSynchronize(s));
+        double t = 0.0;
+        for (int i = 0; i < nb; ++i) t += c->loss_host[i];
+        *loss_out = (float)t;
+    }
+    return RTE_OK;
+}
+
+// layer access for checks and checkpoints: weights [9][cin][cout] f32, bias [cout]
+extern "C" rte_status rte_cnn_layer(rte_cnn c, int l, int* cin, int* cout, float** w_dev, float** bias_dev,
+                                    float** gw_dev, float** gb_dev) {
+    if (!c || l < 0 || l >= c->depth) return RTE_EINVAL;
+    CnnLayer& L = c->layers[l];
+    if (cin) *cin = L.cin;
+    if (cout) *cout = L.cout;
+    if (w_dev) *w_dev = L.w;
+    if (bias_dev) *bias_dev = L.bias;
+    if (gw_dev) *gw_dev = L.gw;
+    if (gb_dev) *gb_dev = L.gb;
+    return RTE_OK;
+}
+
+// refresh the BF16 weights after the FP32 ones were written from outside
+extern "C" rte_status rte_cnn_sync_weights(rte_cnn c, void* stream) {
+    if (!c) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (CnnLayer& L : c->layers) {
+        k_to_bf16<<<256, 256, 0, s>>>(L.w, L.wb, 9L * L.cin * L.cout);
+        rte_count_launches(1);
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the learned guess for a plan: u0 = b + s_b * net(features(b, f, params))
+// ---------------------------------------------------------------------------
+extern "C" rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const double* b_dev, double s_b,
+                                         double fmax, void* X_dev, void* stream) {
+    if (!p || p->dim != 2 || !f_dev || !b_dev || !X_dev || (cin != 16 && cin != 32) || 2 * p->L + 5 > cin)
+        return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float p0 = (float)(log(p->mu_t > 1e-30 ? p->mu_t : 1e-30) / 4.0);
+    const float p1 = (float)(p->mu_t > 0 ? p->mu_s / p->mu_t : 0.0);
+    const float p2 = (float)(p->L >= 1 ? p->sigma_hat[1] : 0.0);
+    k_features<<<512, 256, 0, s>>>(b_dev, f_dev, p->n, p->L, s_b, fmax, p0, p1, p2, cin, (bf16*)X_dev);
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_guess_targets(rte_plan p, int cout, const double* u_dev, const double* b_dev, double s_b,
+                                        void* T_dev, void* stream) {
+    if (!p || p->dim != 2 || !u_dev || !b_dev || !T_dev || (cout != 16 && cout != 32) || 2 * p->L + 1 > cout)
+        return RTE_EINVAL;
+    k_targets<<<512, 256, 0, (cudaStream_t)stream>>>(u_dev, b_dev, p->n, p->L, s_b, cout, (bf16*)T_dev);
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_guess_apply(rte_cnn c, rte_plan p, const double* f_dev, const double* b_dev, double s_b,
+                                      double fmax, void* X_scratch_dev, void* u0_dev, void* stream) {
+    if (!c || !p || p->dim != 2 || 2 * p->L + 1 > c->cout) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    rte_status st = rte_guess_features(p, c->cin, f_dev, b_dev, s_b, fmax, X_scratch_dev, stream);
+    if (st != RTE_OK) return st;
+    st = cnn_forward_internal(c, (const bf16*)X_scratch_dev, 1, p->n, p->n, s);
+    if (st != RTE_OK) return st;
+    k_guess_out<<<512, 256, 0, s>>>(c->out_f, b_dev, p->n, p->L, s_b, c->cout, (double*)u0_dev);
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}

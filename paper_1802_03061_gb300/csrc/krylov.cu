@@ -323,6 +323,25 @@ __global__ void k_ref_relres(RefDev* ref) {
     ref->relres = ref->bnorm > 0.0 ? ref->rnorm / ref->bnorm : 0.0;
 }
 
+// a guess whose residual is not below ||b|| (or not finite) is replaced by
+// the zero start: u = 0, r = b
+__global__ void k_guess_fallback(double* __restrict__ u, double* __restrict__ r, const double* __restrict__ b, long nr,
+                                 const RefDev* __restrict__ ref) {
+    if (ref->rnorm < ref->bnorm) return;  // false for NaN as well: fall back
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x) {
+        u[e] = 0.0;
+        r[e] = b[e];
+    }
+}
+__global__ void k_guess_fallback_state(RefDev* ref) {
+    if (threadIdx.x != 0) return;
+    if (!(ref->rnorm < ref->bnorm)) {
+        ref->rnorm = ref->bnorm;
+        ref->relres = ref->bnorm > 0.0 ? 1.0 : 0.0;
+        ref->pad0 = 1;  // guess rejected
+    }
+}
+
 __global__ void k_ref_gate(RefDev* ref, cudaGraphConditionalHandle c_outer) {
     if (threadIdx.x != 0) return;
     const bool fin = isfinite(ref->relres) && isfinite(ref->bnorm);
@@ -585,8 +604,10 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cu
         SEG(body, d, &info->k_guess, {
             TRYS(plan_apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
             TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
+            k_guess_fallback<<<gr, 256, 0, cs>>>(p->u_dev, p->r64, p->b64, nr, ref);
+            k_guess_fallback_state<<<1, 32, 0, cs>>>(ref);
             k_ref_relres<<<1, 32, 0, cs>>>(ref);
-            rte_count_launches(1);
+            rte_count_launches(3);
         });
     }
     SEG(g, dep, &info->k_fixed, {

@@ -18,3 +18,20 @@ def random_packed(rng, L, n):
 
 def rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def bf16_round(a):
+    """Round to bfloat16 (round to nearest even on the upper 16 bits of FP32)."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    rnd = ((u >> 16) & 1) + 0x7FFF
+    u = ((u + rnd) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def to_bf16_bits(a):
+    """float array -> uint16 bfloat16 bit patterns (round to nearest even)."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    rnd = ((u >> 16) & 1) + 0x7FFF
+    return ((u + rnd) >> 16).astype(np.uint16)
