@@ -216,15 +216,18 @@ rte_status rte_cnn_layer(rte_cnn net, int l, int* cin, int* cout, float** w_dev,
 rte_status rte_cnn_sync_weights(rte_cnn net, void* cuda_stream);
 /* Network input (cin channels, 2L+5 <= cin) / training target (cout
  * channels, 2L+1 <= cout) of plan p (2D) from the source f (double [n][n]),
- * b = K~ g and, for targets, the solution u (FP64 mode fields); s_b scales b
- * and the correction, fmax scales f.  X_dev / T_dev: bf16 [n][n][cin|cout]. */
-rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const double* b_dev, double s_b, double fmax,
-                              void* X_dev, void* cuda_stream);
-rte_status rte_guess_targets(rte_plan p, int cout, const double* u_dev, const double* b_dev, double s_b, void* T_dev,
-                             void* cuda_stream);
-/* u0_dev (FP64 mode field) = b + s_b * net(features); X_scratch_dev: bf16 [n][n][cin]. */
-rte_status rte_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, const double* b_dev, double s_b, double fmax,
-                           void* X_scratch_dev, void* u0_dev, void* cuda_stream);
+ * b = K~ g and, for targets, the solution u (FP64 mode fields).  The scales
+ * s_b = RMS of b's real channels and fmax = max |f| are computed on the
+ * device.  X_dev / T_dev: bf16 [n][n][cin|cout]. */
+rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const double* b_dev, void* X_dev,
+                              void* cuda_stream);
+rte_status rte_guess_targets(rte_plan p, int cout, const double* f_dev, const double* u_dev, const double* b_dev,
+                             void* T_dev, void* cuda_stream);
+/* The learned initial guess: b_out_dev = K~ g (step T.1, FP64 mode field),
+ * then u0_dev = b + s_b * net(features).  X_scratch_dev: bf16 [n][n][cin].
+ * Pass u0 to rte_solve with opts->use_guess = 1. */
+rte_status rte_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, double* b_out_dev, void* X_scratch_dev,
+                           void* u0_dev, void* cuda_stream);
 
 /* Diagnostics (no counterpart in the paper).
  * rte_time_passes: average duration in ms of each FFT pass of one K

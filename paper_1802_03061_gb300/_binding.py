@@ -97,9 +97,9 @@ def lib():
         L.rte_cnn_layer.argtypes = [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP)]
         L.rte_cnn_sync_weights.argtypes = [VP, VP]
-        L.rte_guess_features.argtypes = [VP, ctypes.c_int, VP, VP, ctypes.c_double, ctypes.c_double, VP, VP]
-        L.rte_guess_targets.argtypes = [VP, ctypes.c_int, VP, VP, ctypes.c_double, VP, VP]
-        L.rte_guess_apply.argtypes = [VP, VP, VP, VP, ctypes.c_double, ctypes.c_double, VP, VP, VP]
+        L.rte_guess_features.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP]
+        L.rte_guess_targets.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP, VP]
+        L.rte_guess_apply.argtypes = [VP, VP, VP, VP, VP, VP, VP]
         L.rte_batch_plan.argtypes = [VP, ctypes.c_int, ctypes.POINTER(VP)]
         for name in ("rte_cnn_create", "rte_cnn_destroy", "rte_cnn_forward", "rte_cnn_train_step", "rte_cnn_layer",
                      "rte_cnn_sync_weights", "rte_guess_features", "rte_guess_targets", "rte_guess_apply",
@@ -295,18 +295,16 @@ def rte_cnn_sync_weights(net, stream=0):
     _check(lib().rte_cnn_sync_weights(net, VP(stream)), "rte_cnn_sync_weights")
 
 
-def rte_guess_features(plan, cin, f, b, s_b, fmax, X, stream=0):
-    _check(lib().rte_guess_features(plan, cin, VP(f), VP(b), float(s_b), float(fmax), VP(X), VP(stream)),
-           "rte_guess_features")
+def rte_guess_features(plan, cin, f, b, X, stream=0):
+    _check(lib().rte_guess_features(plan, cin, VP(f), VP(b), VP(X), VP(stream)), "rte_guess_features")
 
 
-def rte_guess_targets(plan, cout, u, b, s_b, T, stream=0):
-    _check(lib().rte_guess_targets(plan, cout, VP(u), VP(b), float(s_b), VP(T), VP(stream)), "rte_guess_targets")
+def rte_guess_targets(plan, cout, f, u, b, T, stream=0):
+    _check(lib().rte_guess_targets(plan, cout, VP(f), VP(u), VP(b), VP(T), VP(stream)), "rte_guess_targets")
 
 
-def rte_guess_apply(net, plan, f, b, s_b, fmax, Xs, u0, stream=0):
-    _check(lib().rte_guess_apply(net, plan, VP(f), VP(b), float(s_b), float(fmax), VP(Xs), VP(u0), VP(stream)),
-           "rte_guess_apply")
+def rte_guess_apply(net, plan, f, b_out, Xs, u0, stream=0):
+    _check(lib().rte_guess_apply(net, plan, VP(f), VP(b_out), VP(Xs), VP(u0), VP(stream)), "rte_guess_apply")
 
 
 def rte_destroy(plan):

@@ -316,9 +316,35 @@ __global__ void k_init_uniform(float* __restrict__ w, long n, unsigned long long
 //   mu_s/mu_t, g, zeros to CIN
 //   u0 = b + s * net_c  (first 2L+1 output channels)
 // ---------------------------------------------------------------------------
-__global__ void k_features(const double* __restrict__ bmode, const double* __restrict__ f, int n, int L, double s_b,
-                           double fmax, float p0, float p1, float p2, int CIN, bf16* __restrict__ X) {
+// sc[0] = RMS of the 2L+1 real channels of b, sc[1] = max |f|  (one block)
+__global__ void k_guess_scales(const double* __restrict__ bmode, const double* __restrict__ f, int n, int L,
+                               double* __restrict__ sc) {
+    __shared__ double r1[1024], r2[1024];
     const long P = (long)n * n;
+    const long nb = 2L * (L + 1) * P;
+    double s = 0.0, m = 0.0;
+    for (long i = threadIdx.x; i < nb; i += blockDim.x) s += bmode[i] * bmode[i];
+    for (long i = threadIdx.x; i < P; i += blockDim.x) m = fmax(m, fabs(f[i]));
+    r1[threadIdx.x] = s;
+    r2[threadIdx.x] = m;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            r1[threadIdx.x] += r1[threadIdx.x + k];
+            r2[threadIdx.x] = fmax(r2[threadIdx.x], r2[threadIdx.x + k]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sc[0] = sqrt(r1[0] / ((2.0 * L + 1.0) * P));
+        sc[1] = r2[0];
+    }
+}
+
+__global__ void k_features(const double* __restrict__ bmode, const double* __restrict__ f, int n, int L,
+                           const double* __restrict__ sc, float p0, float p1, float p2, int CIN, bf16* __restrict__ X) {
+    const long P = (long)n * n;
+    const double s_b = sc[0], fmax = sc[1];
     for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
         bf16* xp = X + p * CIN;
         int c = 0;
@@ -336,9 +362,10 @@ __global__ void k_features(const double* __restrict__ bmode, const double* __res
     }
 }
 
-__global__ void k_targets(const double* __restrict__ umode, const double* __restrict__ bmode, int n, int L, double s_b,
-                          int COUT, bf16* __restrict__ Yt) {
+__global__ void k_targets(const double* __restrict__ umode, const double* __restrict__ bmode, int n, int L,
+                          const double* __restrict__ sc, int COUT, bf16* __restrict__ Yt) {
     const long P = (long)n * n;
+    const double s_b = sc[0];
     for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
         bf16* yp = Yt + p * COUT;
         int c = 0;
@@ -353,9 +380,10 @@ __global__ void k_targets(const double* __restrict__ umode, const double* __rest
     }
 }
 
-__global__ void k_guess_out(const float* __restrict__ net, const double* __restrict__ bmode, int n, int L, double s_b,
-                            int COUT, double* __restrict__ u0) {
+__global__ void k_guess_out(const float* __restrict__ net, const double* __restrict__ bmode, int n, int L,
+                            const double* __restrict__ sc, int COUT, double* __restrict__ u0) {
     const long P = (long)n * n;
+    const double s_b = sc[0];
     for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
         const float* np = net + p * COUT;
         u0[2 * p] = bmode[2 * p] + s_b * np[0];
@@ -668,40 +696,58 @@ extern "C" rte_status rte_cnn_sync_weights(rte_cnn c, void* stream) {
 
 // ---------------------------------------------------------------------------
 // the learned guess for a plan: u0 = b + s_b * net(features(b, f, params))
+// (scales s_b, fmax computed on the device into the plan's dscal[2..3])
 // ---------------------------------------------------------------------------
-extern "C" rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const double* b_dev, double s_b,
-                                         double fmax, void* X_dev, void* stream) {
+static rte_status guess_scales(rte_plan p, const double* f_dev, const double* b_dev, cudaStream_t s) {
+    k_guess_scales<<<1, 1024, 0, s>>>(b_dev, f_dev, p->n, p->L, p->dscal + 2);
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const double* b_dev, void* X_dev,
+                                         void* stream) {
     if (!p || p->dim != 2 || !f_dev || !b_dev || !X_dev || (cin != 16 && cin != 32) || 2 * p->L + 5 > cin)
         return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    rte_status st = guess_scales(p, f_dev, b_dev, s);
+    if (st != RTE_OK) return st;
     const float p0 = (float)(log(p->mu_t > 1e-30 ? p->mu_t : 1e-30) / 4.0);
     const float p1 = (float)(p->mu_t > 0 ? p->mu_s / p->mu_t : 0.0);
     const float p2 = (float)(p->L >= 1 ? p->sigma_hat[1] : 0.0);
-    k_features<<<512, 256, 0, s>>>(b_dev, f_dev, p->n, p->L, s_b, fmax, p0, p1, p2, cin, (bf16*)X_dev);
+    k_features<<<512, 256, 0, s>>>(b_dev, f_dev, p->n, p->L, p->dscal + 2, p0, p1, p2, cin, (bf16*)X_dev);
     rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
 
-extern "C" rte_status rte_guess_targets(rte_plan p, int cout, const double* u_dev, const double* b_dev, double s_b,
-                                        void* T_dev, void* stream) {
-    if (!p || p->dim != 2 || !u_dev || !b_dev || !T_dev || (cout != 16 && cout != 32) || 2 * p->L + 1 > cout)
+extern "C" rte_status rte_guess_targets(rte_plan p, int cout, const double* f_dev, const double* u_dev,
+                                        const double* b_dev, void* T_dev, void* stream) {
+    if (!p || p->dim != 2 || !f_dev || !u_dev || !b_dev || !T_dev || (cout != 16 && cout != 32) ||
+        2 * p->L + 1 > cout)
         return RTE_EINVAL;
-    k_targets<<<512, 256, 0, (cudaStream_t)stream>>>(u_dev, b_dev, p->n, p->L, s_b, cout, (bf16*)T_dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    rte_status st = guess_scales(p, f_dev, b_dev, s);
+    if (st != RTE_OK) return st;
+    k_targets<<<512, 256, 0, s>>>(u_dev, b_dev, p->n, p->L, p->dscal + 2, cout, (bf16*)T_dev);
     rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
 
-extern "C" rte_status rte_guess_apply(rte_cnn c, rte_plan p, const double* f_dev, const double* b_dev, double s_b,
-                                      double fmax, void* X_scratch_dev, void* u0_dev, void* stream) {
-    if (!c || !p || p->dim != 2 || 2 * p->L + 1 > c->cout) return RTE_EINVAL;
+// b_out: caller buffer for b = K~ g (FP64 mode field), computed here
+extern "C" rte_status rte_guess_apply(rte_cnn c, rte_plan p, const double* f_dev, double* b_out_dev, void* X_scratch_dev,
+                                      void* u0_dev, void* stream) {
+    if (!c || !p || p->dim != 2 || !f_dev || !b_out_dev || !X_scratch_dev || !u0_dev || 2 * p->L + 1 > c->cout)
+        return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    rte_status st = rte_guess_features(p, c->cin, f_dev, b_dev, s_b, fmax, X_scratch_dev, stream);
+    rte_status st = plan_apply64(p, MIX_RHS, f_dev, b_out_dev, 0.0, 1.0, 0.0, nullptr, s);
+    if (st != RTE_OK) return st;
+    st = rte_guess_features(p, c->cin, f_dev, b_out_dev, X_scratch_dev, stream);
     if (st != RTE_OK) return st;
     st = cnn_forward_internal(c, (const bf16*)X_scratch_dev, 1, p->n, p->n, s);
     if (st != RTE_OK) return st;
-    k_guess_out<<<512, 256, 0, s>>>(c->out_f, b_dev, p->n, p->L, s_b, c->cout, (double*)u0_dev);
+    k_guess_out<<<512, 256, 0, s>>>(c->out_f, b_out_dev, p->n, p->L, p->dscal + 2, c->cout, (double*)u0_dev);
     rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
