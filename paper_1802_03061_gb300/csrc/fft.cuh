@@ -72,12 +72,25 @@ __device__ __forceinline__ void fft_stage(const T* __restrict__ in, T* __restric
     const int per = Q / R;
     const int tot = nl * per;
     const int step = Q / (Ns * R);
+    // power-of-two lengths: index arithmetic by shifts and masks
+    const bool p2 = (Q & (Q - 1)) == 0;
+    const int lper = p2 ? __ffs(per) - 1 : 0;
+    const int lns = p2 ? __ffs(Ns) - 1 : 0;
     for (int job = threadIdx.x; job < tot; job += blockDim.x) {
-        const int line = job / per;
-        const int j = job - line * per;
+        int line, j, k, jq;
+        if (p2) {
+            line = job >> lper;
+            j = job & (per - 1);
+            k = j & (Ns - 1);
+            jq = j >> lns;
+        } else {
+            line = job / per;
+            j = job - line * per;
+            jq = j / Ns;
+            k = j - jq * Ns;
+        }
         const T* a = in + (long)line * ld;
         T* b = out + (long)line * ld;
-        const int k = j % Ns;
         T v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = a[j + r * per];
@@ -89,7 +102,7 @@ __device__ __forceinline__ void fft_stage(const T* __restrict__ in, T* __restric
         if (R == 3) bfly3<DIR>(v);
         if (R == 4) bfly4<DIR>(v);
         if (R == 8) bfly8<DIR>(v);
-        const int d = (j / Ns) * Ns * R + k;
+        const int d = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) b[d + r * Ns] = v[r];
     }

@@ -22,9 +22,14 @@ template <typename T> static size_t row_smem(int Q, int RB) { return (size_t)(Q 
 template <typename T> static bool col_fits(int nch, int Q) {
     return (size_t)(Q + nch * Q + Q) * sizeof(T) <= 200 * 1024;
 }
+// FFT group size of the fused column pass: as many channels per FFT sweep as
+// still let two blocks share an SM (about 110 KB each), else one block
 template <typename T> static int col_group(int nch, int Q) {
+    long left2 = 110L * 1024 / (long)sizeof(T) - (long)Q - (long)nch * Q;
+    int G = (int)(left2 / Q);
+    if (G >= 4 || G >= nch) return G > nch ? nch : G;
     long left = 200L * 1024 / (long)sizeof(T) - (long)Q - (long)nch * Q;
-    int G = (int)(left / Q);
+    G = (int)(left / Q);
     if (G > nch) G = nch;
     if (G < 1) G = 1;
     return G;
