@@ -388,6 +388,28 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_profile_solve(args):
+    """One plan, one warm-up solve, one solve: a clean launch list for ncu."""
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Plan
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    base = rte_synth.hg2d_transport()
+    plan = Plan(base["n"], mu_t=base["mu_t"], mu_s=base["mu_s"], sigma_hat=base["sigma_hat"], prec=args.prec,
+                tol=1e-8, restart=args.restart, inner_tol=args.inner_tol)
+    f = torch.from_numpy(base["f"]).cuda()
+    plan.solve(f)
+    torch.cuda.synchronize()
+    _, st = plan.solve(f)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": st}))
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,12 +422,16 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="hg2d_transport", choices=["hg2d_transport", "batch512"])
+    ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         ws, rank, _ = dist_env()
         if rank != 0:
             return
         run_reference(args)
+        return
+    if args.profile_solve:
+        run_profile_solve(args)
         return
     if args.workload == "batch512":
         run_batch(args)

@@ -66,6 +66,55 @@ template <int DIR, typename T> __device__ __forceinline__ void bfly8(T* v) {
     v[7] = csub(e[3], o3);
 }
 
+// radix-8 butterfly whose inputs 4..7 are zero (zero-padded line, first stage)
+template <int DIR, typename T> __device__ __forceinline__ void bfly8_half(T* v) {
+    using R = typename real_of<T>::R;
+    const R r2 = (R)0.70710678118654752440084436210485;
+    // even part DFT4(v0, v2, 0, 0), odd part DFT4(v1, v3, 0, 0)
+    const T e0 = cadd(v[0], v[2]), e2 = csub(v[0], v[2]);
+    const T w2 = cmul_i<DIR>(v[2]);
+    const T e1 = cadd(v[0], w2), e3 = csub(v[0], w2);
+    const T o0 = cadd(v[1], v[3]), o2s = csub(v[1], v[3]);
+    const T w3 = cmul_i<DIR>(v[3]);
+    const T o1s = cadd(v[1], w3), o3s = csub(v[1], w3);
+    const T o1 = mk<T>(r2 * (o1s.x - DIR * o1s.y), r2 * (o1s.y + DIR * o1s.x));
+    const T o2 = cmul_i<DIR>(o2s);
+    const T o3 = mk<T>(r2 * (-o3s.x - DIR * o3s.y), r2 * (-o3s.y + DIR * o3s.x));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+// First stage (Ns = 1) of a radix-8 schedule on lines whose entries at
+// index >= Q/2 are zero (zero padding, n <= Q/2): inputs r = 4..7 are zero.
+template <int DIR, typename T>
+__device__ __forceinline__ void fft_stage8_first_half(const T* __restrict__ in, T* __restrict__ out, int nl, int ld,
+                                                      int Q) {
+    const int per = Q / 8;
+    const int tot = nl * per;
+    const bool p2 = (Q & (Q - 1)) == 0;
+    const int lper = p2 ? __ffs(per) - 1 : 0;
+    for (int job = threadIdx.x; job < tot; job += blockDim.x) {
+        int line, j;
+        if (p2) { line = job >> lper; j = job & (per - 1); }
+        else { line = job / per; j = job - line * per; }
+        const T* a = in + (long)line * ld;
+        T* b = out + (long)line * ld;
+        T v[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = a[j + r * per];
+        bfly8_half<DIR>(v);
+        const int d = j * 8;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) b[d + r] = v[r];
+    }
+}
+
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void fft_stage(const T* __restrict__ in, T* __restrict__ out, int nl, int ld,
                                           int Q, int Ns, const T* __restrict__ tw) {
@@ -110,14 +159,17 @@ __device__ __forceinline__ void fft_stage(const T* __restrict__ in, T* __restric
 
 // Runs all stages; returns the buffer (buf or tmp) that holds the result.
 // Ends with a __syncthreads(); the caller must have synchronised before.
+// half_zero: the entries at index >= Q/2 of every line are zero (prunes
+// the first radix-8 stage).
 template <int DIR, typename T>
-__device__ T* fft_lines(T* buf, T* tmp, int nl, int ld, const FftSched& s, const T* tw) {
+__device__ T* fft_lines(T* buf, T* tmp, int nl, int ld, const FftSched& s, const T* tw, bool half_zero = false) {
     T* in = buf;
     T* out = tmp;
     int Ns = 1;
     for (int st = 0; st < s.ns; ++st) {
         const int R = s.radix[st];
-        if (R == 8) fft_stage<8, DIR>(in, out, nl, ld, s.Q, Ns, tw);
+        if (st == 0 && R == 8 && half_zero) fft_stage8_first_half<DIR>(in, out, nl, ld, s.Q);
+        else if (R == 8) fft_stage<8, DIR>(in, out, nl, ld, s.Q, Ns, tw);
         else if (R == 4) fft_stage<4, DIR>(in, out, nl, ld, s.Q, Ns, tw);
         else if (R == 3) fft_stage<3, DIR>(in, out, nl, ld, s.Q, Ns, tw);
         else fft_stage<2, DIR>(in, out, nl, ld, s.Q, Ns, tw);

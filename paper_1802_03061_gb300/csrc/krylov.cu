@@ -50,9 +50,42 @@ struct GmresDev {
 };
 
 // --------------------------------------------------------------------------
-// vector kernels (T = float or double storage; FP64 accumulation)
+// vector kernels (T = float or double storage)
 // element e has weight 1 when e < nw1 (mode 0), else 2
+//
+// FP64 is about 1/64 of the FP32 rate on this GPU, so for FP32 vectors the
+// inner products keep double-precision accuracy with error-free
+// transformations on the FP32 units: a*b = p + e exactly (p = fl(a*b),
+// e = fma(a, b, -p)) and s + t = sum + err exactly (Knuth's TwoSum), giving
+// (hi, lo) pairs with about 48 significant bits.  The _rn intrinsics keep the
+// compiler from contracting the transformations into FMAs.
 // --------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// (hi, lo) += (bh, bl)
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+    float s, e;
+    two_sum(hi, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// (hi, lo) += a * b
+__device__ __forceinline__ void ff_fma(float& hi, float& lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    ff_add(hi, lo, p, pe);
+}
+__device__ __forceinline__ void ff_warp_sum(float& hi, float& lo) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float bl = __shfl_down_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, bh, bl);
+    }
+}
 template <typename T>
 __global__ void __launch_bounds__(256) k_mdot(const T* __restrict__ V, long nr, const T* __restrict__ w,
                                               const int* __restrict__ cnt_src, int cnt_add, long nw1,
@@ -60,23 +93,43 @@ __global__ void __launch_bounds__(256) k_mdot(const T* __restrict__ V, long nr, 
     const int count = (cnt_src ? *cnt_src : 0) + cnt_add;
     __shared__ double red[GM_MMAX + 1][8];
     const long base = (long)blockIdx.x * TILE + threadIdx.x;
-    double wv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const long e = base + 256 * q;
-        wv[q] = e < nr ? (double)w[e] * (e < nw1 ? 1.0 : 2.0) : 0.0;
-    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = 0; i < count; ++i) {
-        const T* v = V + (long)i * nr;
-        double s = 0.0;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        float wv[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const long e = base + 256 * q;
-            if (e < nr) s += (double)v[e] * wv[q];
+            wv[q] = e < nr ? (float)w[e] * (e < nw1 ? 1.f : 2.f) : 0.f;
         }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[i][wid] = s;
+        for (int i = 0; i < count; ++i) {
+            const T* v = V + (long)i * nr;
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const long e = base + 256 * q;
+                if (e < nr) ff_fma(hi, lo, (float)v[e], wv[q]);
+            }
+            ff_warp_sum(hi, lo);
+            if (lane == 0) red[i][wid] = (double)hi + (double)lo;
+        }
+    } else {
+        double wv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long e = base + 256 * q;
+            wv[q] = e < nr ? (double)w[e] * (e < nw1 ? 1.0 : 2.0) : 0.0;
+        }
+        for (int i = 0; i < count; ++i) {
+            const T* v = V + (long)i * nr;
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const long e = base + 256 * q;
+                if (e < nr) s += (double)v[e] * wv[q];
+            }
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) red[i][wid] = s;
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
@@ -116,31 +169,64 @@ __global__ void __launch_bounds__(256) k_maxpy(const T* __restrict__ V, long nr,
     for (int i = threadIdx.x; i < count; i += blockDim.x) c[i] = sgn * coef[i];
     __syncthreads();
     const long base = (long)blockIdx.x * TILE + threadIdx.x;
-    double acc[8];
+    double sqd = 0.0;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // the result is stored in FP32: FP32 arithmetic, compensated norm
+        float acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (int i = 0; i < count; ++i) {
-        const T* v = V + (long)i * nr;
-        const double ci = c[i];
+        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+        for (int i = 0; i < count; ++i) {
+            const T* v = V + (long)i * nr;
+            const float ci = (float)c[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const long e = base + 256 * q;
+                if (e < nr) acc[q] = fmaf(ci, (float)v[e], acc[q]);
+            }
+        }
+        float hi = 0.f, lo = 0.f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const long e = base + 256 * q;
-            if (e < nr) acc[q] += ci * (double)v[e];
+            if (e < nr) {
+                const float nv = (float)w[e] + acc[q];
+                w[e] = (T)nv;
+                if (part) ff_fma(hi, lo, nv, nv * (e < nw1 ? 1.f : 2.f));
+            }
         }
-    }
-    double sq = 0.0;
+        if (part) {
+            ff_warp_sum(hi, lo);
+            sqd = (double)hi + (double)lo;
+        }
+    } else {
+        double acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const long e = base + 256 * q;
-        if (e < nr) {
-            const T nv = (T)((double)w[e] + acc[q]);
-            w[e] = nv;
-            sq += (double)nv * (double)nv * (e < nw1 ? 1.0 : 2.0);
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int i = 0; i < count; ++i) {
+            const T* v = V + (long)i * nr;
+            const double ci = c[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const long e = base + 256 * q;
+                if (e < nr) acc[q] += ci * (double)v[e];
+            }
         }
+        double sq = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long e = base + 256 * q;
+            if (e < nr) {
+                const T nv = (T)((double)w[e] + acc[q]);
+                w[e] = nv;
+                sq += (double)nv * (double)nv * (e < nw1 ? 1.0 : 2.0);
+            }
+        }
+        if (part)
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+        sqd = sq;
     }
     if (part) {
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sqd;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
@@ -185,10 +271,10 @@ __global__ void k_scale_basis(const T* __restrict__ w, T* __restrict__ V, T* __r
                               const GmresDev* __restrict__ st, int off) {
     const int slot = st->j + off;
     const double nrm = st->nrm;
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    const T inv = (T)(nrm > 0.0 ? 1.0 / nrm : 0.0);  // in the storage precision
     T* dst = V + (long)slot * nr;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x) {
-        const T v = (T)((double)w[e] * inv);
+        const T v = w[e] * inv;
         dst[e] = v;
         vin[e] = v;
     }

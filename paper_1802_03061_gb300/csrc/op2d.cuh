@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_row_fwd(const T* __restrict__ x, const 
         buf[idx] = v;
     }
     __syncthreads();
-    T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl);
+    T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl, 2 * n <= Q);
     // split Z = F + i G (F, G real rows) into their half spectra:
     //   F(xi) = (Z(xi) + conj Z(-xi))/2,  G(xi) = (Z(xi) - conj Z(-xi))/(2i)
     const int rows = (k == 0) ? RB : RB;
@@ -239,6 +239,26 @@ __device__ __forceinline__ void mode_mix(const typename real_of<T>::R* sr, const
 #undef MI_
 }
 
+// the mode mix when only A_0 is nonzero (right-hand side K~ g):
+//   Re v_k = P_k A_0,  Im v_k = -i M_k A_0
+template <int L, typename T>
+__device__ __forceinline__ void mode_mix_rhs(const typename real_of<T>::R* sr, const typename real_of<T>::R* si,
+                                             T A0, T* outv) {
+#pragma unroll
+    for (int k = 0; k <= L; ++k) {
+        T Ra = mk<T>(0, 0), Ia = mk<T>(0, 0);
+        if (k & 1) {
+            tmac(Ra, si[k], true, A0);   // P_k = i Im S_k
+            tmac(Ia, -sr[k], true, A0);  // -i M_k, M_k = Re S_k
+        } else {
+            tmac(Ra, sr[k], false, A0);  // P_k = Re S_k
+            tmac(Ia, si[k], false, A0);  // -i M_k = -i (i Im S_k) = Im S_k
+        }
+        outv[chA(k)] = Ra;
+        if (k > 0) outv[chB(k)] = Ia;
+    }
+}
+
 struct ColParams {
     int n, Q, H, L, nin, G;   // nin: input channels (nch for K, 1 for the RHS)
     FftSched sc;
@@ -258,11 +278,12 @@ __device__ __forceinline__ void load_spec(const TS* __restrict__ S, int kx, int 
 
 // channels [c0, c0+cnt) of X (line stride Q) through an FFT, result left in X
 template <int DIR, typename T>
-__device__ void fft_channels(T* X, T* tmp, int c0, int cnt, int G, const FftSched& sc, const T* twl) {
+__device__ void fft_channels(T* X, T* tmp, int c0, int cnt, int G, const FftSched& sc, const T* twl,
+                             bool half_zero = false) {
     const int Q = sc.Q;
     for (int g0 = c0; g0 < c0 + cnt; g0 += G) {
         const int nl = min(G, c0 + cnt - g0);
-        T* res = fft_lines<DIR>(X + (long)g0 * Q, tmp, nl, Q, sc, twl);
+        T* res = fft_lines<DIR>(X + (long)g0 * Q, tmp, nl, Q, sc, twl, half_zero);
         if (res != X + (long)g0 * Q) {
             for (int i = threadIdx.x; i < nl * Q; i += blockDim.x) X[(long)g0 * Q + i] = res[i];
             __syncthreads();
@@ -289,16 +310,28 @@ __global__ void __launch_bounds__(256) k_col_fused(T* __restrict__ Tb, const TS*
         X[idx] = e < n ? Tb[((long)c * H + kx) * n + e] : mk<T>(0, 0);
     }
     __syncthreads();
-    fft_channels<-1>(X, tmp, 0, p.nin, p.G, p.sc, twl);
-    for (int ky = threadIdx.x; ky < Q; ky += blockDim.x) {
-        R sr[2 * L + 1], si[2 * L + 1];
-        load_spec<L, T>(S, kx, ky, Q, sr, si);
-        T in[NCH], o[NCH];
+    fft_channels<-1>(X, tmp, 0, p.nin, p.G, p.sc, twl, 2 * n <= Q);
+    if (p.nin == 1) {
+        // right-hand side: only the mode-0 channel is nonzero
+        for (int ky = threadIdx.x; ky < Q; ky += blockDim.x) {
+            R sr[2 * L + 1], si[2 * L + 1];
+            load_spec<L, T>(S, kx, ky, Q, sr, si);
+            T o[NCH];
+            mode_mix_rhs<L, T>(sr, si, X[ky], o);
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) in[c] = c < p.nin ? X[(long)c * Q + ky] : mk<T>(0, 0);
-        mode_mix<L, T>(sr, si, in, o);
+            for (int c = 0; c < NCH; ++c) X[(long)c * Q + ky] = o[c];
+        }
+    } else {
+        for (int ky = threadIdx.x; ky < Q; ky += blockDim.x) {
+            R sr[2 * L + 1], si[2 * L + 1];
+            load_spec<L, T>(S, kx, ky, Q, sr, si);
+            T in[NCH], o[NCH];
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) X[(long)c * Q + ky] = o[c];
+            for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * Q + ky];
+            mode_mix<L, T>(sr, si, in, o);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) X[(long)c * Q + ky] = o[c];
+        }
     }
     __syncthreads();
     fft_channels<1>(X, tmp, 0, NCH, p.G, p.sc, twl);
