@@ -57,6 +57,8 @@ struct rte_plan_s {
     double2* S64 = nullptr;
     float2* S32 = nullptr;
     __nv_bfloat162* S16 = nullptr;
+    float2* S32p = nullptr;          // FP32 / BF16 spectra in the warp column pass's slot order
+    __nv_bfloat162* S16p = nullptr;
     double* S3_64 = nullptr;
     float* S3_32 = nullptr;
     // cell weights D_m, m = 0..2L (2D) or D (3D), computed on the device
@@ -109,6 +111,7 @@ rte_status op2d_apply64(rte_plan p, MixKind kind, const double* x, const double*
 rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);
 rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s);
+rte_status op2d_permute_spectra(rte_plan p, cudaStream_t s);
 rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s);
 // op2d_64.cu: the FP64 passes on explicit buffers (no plan-owned scratch)
 rte_status op2d_apply64_buffers(rte_plan p, const double* x, double* out, double2* Tb, const double2* S64,

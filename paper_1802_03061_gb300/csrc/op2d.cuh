@@ -27,6 +27,7 @@
 #pragma once
 #include "fft.cuh"
 #include "internal.h"
+#include "wfft.cuh"
 
 // channel index of Re u_k / Im u_k
 __host__ __device__ __forceinline__ int chA(int k) { return k == 0 ? 0 : 2 * k - 1; }
@@ -392,4 +393,84 @@ __global__ void k_mix_pointwise(T* __restrict__ Ts, const TS* __restrict__ S, Co
     mode_mix<L, T>(sr, si, in, o);
 #pragma unroll
     for (int c = 0; c < NCH; ++c) Ts[((long)c * H + kx) * Q + ky] = o[c];
+}
+
+// ---------------------------------------------------------------------------
+// column pass with the warp-register FFT (FP32, Q = 32 R, R = 2..16): one
+// block per xi_x, each warp transforms whole channel columns.  Spectra of
+// all channels meet in shared memory in the slot layout s = k1 * 32 + lane
+// (frequency xi_y = k1 + R brev5(lane)), the same layout the plan stores the
+// permuted spectra Sp[xi_x][m][s] in; the inverse starts from that layout.
+// ---------------------------------------------------------------------------
+template <int L, int R, typename TS>
+__global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const TS* __restrict__ Sp,
+                                                  const float2* __restrict__ tw, int n, int H, int nin) {
+    constexpr int NCH = 2 * L + 1;
+    constexpr int Q = 32 * R;
+    extern __shared__ unsigned char smraw[];
+    float2* twl = reinterpret_cast<float2*>(smraw);
+    float2* X = twl + Q;  // [NCH][Q] in slot layout
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int kx = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < nin; c += nw) {
+        float2 v[R];
+        const float2* col = Tb + ((long)c * H + kx) * n;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = lane + 32 * r;
+            v[r] = y < n ? col[y] : make_float2(0.f, 0.f);
+        }
+        warp_fft_fwd<R>(v, twl);
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) X[(long)c * Q + k1 * 32 + lane] = v[k1];
+    }
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < Q; sl += blockDim.x) {
+        float sr[2 * L + 1], si[2 * L + 1];
+#pragma unroll
+        for (int m = 0; m <= 2 * L; ++m) {
+            const float2 v = ld_spec(Sp, ((long)kx * (2 * L + 1) + m) * Q + sl, float2());
+            sr[m] = v.x;
+            si[m] = v.y;
+        }
+        float2 o[NCH];
+        if (nin == 1) {
+            mode_mix_rhs<L, float2>(sr, si, X[sl], o);
+        } else {
+            float2 in[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * Q + sl];
+            mode_mix<L, float2>(sr, si, in, o);
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) X[(long)c * Q + sl] = o[c];
+    }
+    __syncthreads();
+    for (int c = warp; c < NCH; c += nw) {
+        float2 v[R];
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) v[k1] = X[(long)c * Q + k1 * 32 + lane];
+        warp_fft_inv<R>(v, twl);
+        float2* col = Tb + ((long)c * H + kx) * n;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = lane + 32 * r;
+            if (y < n) col[y] = v[r];
+        }
+    }
+}
+
+// Sp[xi_x][m][k1 * 32 + lane] = S[xi_x][m][k1 + R brev5(lane)]
+template <typename TS>
+__global__ void k_permute_spec(const TS* __restrict__ S, TS* __restrict__ Sp, long rows, int Q) {
+    const int R = Q / 32;
+    const long tot = rows * Q;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
+        const long row = i / Q;
+        const int sl = (int)(i % Q);
+        const int k1 = sl >> 5, lane = sl & 31;
+        Sp[i] = S[row * Q + k1 + R * brev5(lane)];
+    }
 }

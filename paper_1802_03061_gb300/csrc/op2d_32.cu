@@ -11,10 +11,10 @@ rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b
     float2* Ts = reinterpret_cast<float2*>(p->Tsplit32);
     if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC)
         e = op2d_run<float2, __nv_bfloat162>(p, MIX_K, xx, nullptr, oo, a, b, c, zz, Tb, Ts, p->S16, p->tw32,
-                                             p->col_split32, s);
+                                             p->col_split32, s, -1, p->S16p);
     else
         e = op2d_run<float2, float2>(p, MIX_K, xx, nullptr, oo, a, b, c, zz, Tb, Ts, p->S32, p->tw32,
-                                     p->col_split32, s);
+                                     p->col_split32, s, -1, p->S32p);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_apply32");
     return RTE_OK;
 }
@@ -26,9 +26,22 @@ rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s) {
     float2* Tb = reinterpret_cast<float2*>(p->T32);
     float2* Ts = reinterpret_cast<float2*>(p->Tsplit32);
     if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC)
-        e = op2d_time<float2, __nv_bfloat162>(p, xx, oo, Tb, Ts, p->S16, p->tw32, p->col_split32, reps, ms, s);
+        e = op2d_time<float2, __nv_bfloat162>(p, xx, oo, Tb, Ts, p->S16, p->tw32, p->col_split32, reps, ms, s,
+                                              p->S16p);
     else
-        e = op2d_time<float2, float2>(p, xx, oo, Tb, Ts, p->S32, p->tw32, p->col_split32, reps, ms, s);
+        e = op2d_time<float2, float2>(p, xx, oo, Tb, Ts, p->S32, p->tw32, p->col_split32, reps, ms, s, p->S32p);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_time32");
+    return RTE_OK;
+}
+
+// plan time: spectra copies in the warp column pass's slot order
+rte_status op2d_permute_spectra(rte_plan p, cudaStream_t s) {
+    if (!p->S32p) return RTE_OK;
+    const long rows = (long)p->H * p->nch;
+    k_permute_spec<float2><<<1024, 256, 0, s>>>(p->S32, p->S32p, rows, p->Q);
+    k_permute_spec<__nv_bfloat162><<<1024, 256, 0, s>>>(p->S16, p->S16p, rows, p->Q);
+    rte_count_launches(2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_permute_spectra");
     return RTE_OK;
 }

@@ -67,6 +67,47 @@ static cudaError_t launch_col(T* Tb, T* Ts, const TS* S, const T* tw, ColParams 
     return cudaGetLastError();
 }
 
+template <int L, int R, typename TS>
+static cudaError_t launch_col_warp(float2* Tb, const TS* Sp, const float2* tw, const ColParams& cp, cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) { e = allow_smem(k_col_warp<L, R, TS>); if (e != cudaSuccess) return e; once = true; }
+    const size_t smem = (size_t)(32 * R) * sizeof(float2) * (1 + 2 * L + 1);
+    k_col_warp<L, R, TS><<<cp.H, 256, smem, s>>>(Tb, Sp, tw, cp.n, cp.H, cp.nin);
+    return cudaGetLastError();
+}
+
+template <int L, typename TS>
+static cudaError_t launch_col_warp_q(float2* Tb, const TS* Sp, const float2* tw, const ColParams& cp, cudaStream_t s) {
+    switch (cp.Q) {
+        case 64: return launch_col_warp<L, 2>(Tb, Sp, tw, cp, s);
+        case 128: return launch_col_warp<L, 4>(Tb, Sp, tw, cp, s);
+        case 256: return launch_col_warp<L, 8>(Tb, Sp, tw, cp, s);
+        case 512: return launch_col_warp<L, 16>(Tb, Sp, tw, cp, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TS>
+static cudaError_t dispatch_col_warp(int L, float2* Tb, const TS* Sp, const float2* tw, const ColParams& cp,
+                                     cudaStream_t s) {
+    switch (L) {
+        case 0: return launch_col_warp_q<0>(Tb, Sp, tw, cp, s);
+        case 1: return launch_col_warp_q<1>(Tb, Sp, tw, cp, s);
+        case 2: return launch_col_warp_q<2>(Tb, Sp, tw, cp, s);
+        case 3: return launch_col_warp_q<3>(Tb, Sp, tw, cp, s);
+        case 4: return launch_col_warp_q<4>(Tb, Sp, tw, cp, s);
+        case 5: return launch_col_warp_q<5>(Tb, Sp, tw, cp, s);
+        case 6: return launch_col_warp_q<6>(Tb, Sp, tw, cp, s);
+        case 7: return launch_col_warp_q<7>(Tb, Sp, tw, cp, s);
+        case 8: return launch_col_warp_q<8>(Tb, Sp, tw, cp, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// the warp-register column pass applies to FP32 with Q in {64, 128, 256, 512}
+static inline bool col_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512; }
+
 template <typename T, typename TS>
 static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split,
                                 cudaStream_t s) {
@@ -89,7 +130,7 @@ static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, C
 template <typename T, typename TS>
 static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* f, T* out, double a, double b,
                             double c, const T* z, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
-                            cudaStream_t s, int stage = -1) {
+                            cudaStream_t s, int stage = -1, const TS* Sp = nullptr) {
     using R = typename real_of<T>::R;
     static bool once = false;
     cudaError_t e;
@@ -124,8 +165,15 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* 
         cp.nin = kind == MIX_K ? p->nch : 1;
         cp.G = 1;
         cp.sc = p->sched;
-        if ((e = dispatch_col<T, TS>(p->L, Tb, Ts, S, tw, cp, split, s)) != cudaSuccess) return e;
-        rte_count_launches(split ? 3 : 1);
+        bool warp_path = false;
+        if constexpr (sizeof(T) == sizeof(float2)) {
+            if (Sp && col_warp_ok(p->Q)) {
+                if ((e = dispatch_col_warp<TS>(p->L, (float2*)Tb, Sp, (const float2*)tw, cp, s)) != cudaSuccess) return e;
+                warp_path = true;
+            }
+        }
+        if (!warp_path && (e = dispatch_col<T, TS>(p->L, Tb, Ts, S, tw, cp, split, s)) != cudaSuccess) return e;
+        rte_count_launches(split && !warp_path ? 3 : 1);
     }
     if (stage < 0 || stage == 2) {
         const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
@@ -140,7 +188,7 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* 
 // events on stream s); ms[0..2] = row, column, inverse row
 template <typename T, typename TS>
 static cudaError_t op2d_time(rte_plan p, const T* x, T* out, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
-                             int reps, double* ms, cudaStream_t s) {
+                             int reps, double* ms, cudaStream_t s, const TS* Sp = nullptr) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -148,7 +196,7 @@ static cudaError_t op2d_time(rte_plan p, const T* x, T* out, T* Tb, T* Ts, const
     for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
         cudaEventRecord(e0, s);
         for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = op2d_run<T, TS>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st);
+            e = op2d_run<T, TS>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st, Sp);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float t = 0.f;

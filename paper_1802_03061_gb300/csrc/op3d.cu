@@ -13,6 +13,7 @@
 // Each intermediate is laid out so that the next pass reads contiguous lines.
 #include "fft.cuh"
 #include "internal.h"
+#include "wfft.cuh"
 
 #define RTE_SMEM_OPTIN 232448
 
@@ -125,6 +126,43 @@ __global__ void __launch_bounds__(256) k3_z_mix(T* __restrict__ T2, const TS* __
     }
 }
 
+// Z with the warp-register FFT (FP32, Q = 32 R): one warp per (xi_x, xi_y)
+// line, 8 lines per block; the spectrum multiply happens in the forward
+// transform's output layout, so the inverse follows with no data movement.
+template <int R>
+__global__ void __launch_bounds__(256) k3_z_mix_warp(float2* __restrict__ T2, const float* __restrict__ S,
+                                                     const float2* __restrict__ tw, int n, int H, long nlines) {
+    constexpr int Q = 32 * R;
+    __shared__ float2 twl[Q];
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (line >= nlines) return;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int z = lane + 32 * r;
+        v[r] = z < n ? T2[line * n + z] : make_float2(0.f, 0.f);
+    }
+    warp_fft_fwd<R>(v, twl);
+    const int kx = (int)(line / Q), ky = (int)(line % Q);
+    const float* Srow = S + ((long)kx * H + fold(ky, Q)) * H;
+    const int k2 = brev5(lane);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+        const float sv = Srow[fold(k1 + R * k2, Q)];
+        v[k1].x *= sv;
+        v[k1].y *= sv;
+    }
+    warp_fft_inv<R>(v, twl);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int z = lane + 32 * r;
+        if (z < n) T2[line * n + z] = v[r];
+    }
+}
+
 // Y': T2[xi_x][xi_y][z] -> T1[z][xi_x][y], y < n; grid (ceil(n/B), H)
 template <typename T>
 __global__ void __launch_bounds__(256) k3_y_inv(const T* __restrict__ T2, T* __restrict__ T1, const T* __restrict__ tw,
@@ -233,8 +271,20 @@ static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k3_y_fwd<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T1, T2, tw, pp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const long nz = ((long)H * Q + B - 1) / B;
-    k3_z_mix<T, TS><<<(unsigned)nz, 256, smy, s>>>(T2, S, tw, pp);
+    const long nlines = (long)H * Q;
+    if constexpr (sizeof(T) == sizeof(float2) && sizeof(TS) == sizeof(float)) {
+        if (Q == 64 || Q == 128 || Q == 256 || Q == 512) {
+            const unsigned nb = (unsigned)((nlines + 7) / 8);
+            if (Q == 64) k3_z_mix_warp<2><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
+            if (Q == 128) k3_z_mix_warp<4><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
+            if (Q == 256) k3_z_mix_warp<8><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
+            if (Q == 512) k3_z_mix_warp<16><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
+        } else {
+            k3_z_mix<T, TS><<<(unsigned)((nlines + B - 1) / B), 256, smy, s>>>(T2, S, tw, pp);
+        }
+    } else {
+        k3_z_mix<T, TS><<<(unsigned)((nlines + B - 1) / B), 256, smy, s>>>(T2, S, tw, pp);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k3_y_inv<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T2, T1, tw, pp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
