@@ -115,6 +115,12 @@ rte_status rte_apply_K(rte_plan plan, const void* x_dev, void* y_dev, void* cuda
 /* y = x - K x, the matrix A = I - K of Eq. ani_AU. */
 rte_status rte_apply_A(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
 
+/* y = K x to FP64 accuracy computed in float-float arithmetic (pairs of
+ * FP32 numbers, ~48 significant bits) on the FP32 units; this is how the
+ * mixed-precision solve forms its right-hand side and residuals, because
+ * FP64 units are scarce on this GPU.  Same layouts as rte_apply_K. */
+rte_status rte_apply_K64e(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
+
 /* FP32 versions used by the inner solves of the mixed modes: x_dev, y_dev are
  * float2 [L+1][n][n] (2D) or float [n]^3 (3D); the spectra are FP32 or BF16
  * as the plan's prec selects (FP32 for an FP64 plan). */

@@ -63,7 +63,7 @@ def lib():
         L.rte_plan_create.argtypes = [ctypes.POINTER(VP), rte_grid, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(rte_opts), VP]
-        for name in ("rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_rhs"):
+        for name in ("rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_apply_K64e", "rte_rhs"):
             getattr(L, name).argtypes = [VP, VP, VP, VP]
         L.rte_solve.argtypes = [VP, VP, VP, ctypes.POINTER(rte_opts), ctypes.POINTER(rte_stats), VP]
         L.rte_solve_host.argtypes = [VP, VP, VP, ctypes.POINTER(rte_opts), ctypes.POINTER(rte_stats), VP]
@@ -108,7 +108,8 @@ def lib():
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
         L.rte_last_error.restype = ctypes.c_char_p
-        for name in ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_rhs", "rte_solve",
+        for name in ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_apply_K64e", "rte_rhs",
+                     "rte_solve",
                      "rte_solve_host", "rte_plan_info", "rte_plan_cell_weights", "rte_destroy"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -149,6 +150,10 @@ def rte_apply_K(plan, x, y, stream=0):
 
 def rte_apply_A(plan, x, y, stream=0):
     _check(lib().rte_apply_A(plan, VP(x), VP(y), VP(stream)), "rte_apply_A")
+
+
+def rte_apply_K64e(plan, x, y, stream=0):
+    _check(lib().rte_apply_K64e(plan, VP(x), VP(y), VP(stream)), "rte_apply_K64e")
 
 
 def rte_apply_K32(plan, x, y, stream=0):

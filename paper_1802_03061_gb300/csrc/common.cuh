@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "ff.cuh"
+
 #define RTE_MAX_L 8                      // largest angular truncation |k| <= L
 #define RTE_MAX_CH (2 * RTE_MAX_L + 1)   // real channels of a J-symmetric field
 #define RTE_MAX_STAGES 16
@@ -18,6 +20,7 @@ template <> struct cplx_of<double> { using T = double2; };
 template <typename T> struct real_of;
 template <> struct real_of<float2> { using R = float; };
 template <> struct real_of<double2> { using R = double; };
+template <> struct real_of<ffc> { using R = ff; };
 
 template <typename T> __host__ __device__ __forceinline__ T mk(typename real_of<T>::R x, typename real_of<T>::R y) {
     T r; r.x = x; r.y = y; return r;
@@ -36,7 +39,14 @@ template <typename T> __device__ __forceinline__ T cscale(T a, typename real_of<
     return mk<T>(a.x * s, a.y * s);
 }
 
-// storage conversions for kernel spectra (double2 / float2 / bf16x2)
+// storage conversions between field storage and compute types
+template <typename T, typename TF> __device__ __forceinline__ T to_c(TF v) { return v; }
+template <> __device__ __forceinline__ ffc to_c<ffc, double2>(double2 v) { return to_ffc(v); }
+template <typename TF, typename T> __device__ __forceinline__ TF to_f(T v) { return v; }
+template <> __device__ __forceinline__ double2 to_f<double2, ffc>(ffc v) { return to_double2(v); }
+
+// storage conversions for kernel spectra (double2 / float2 / bf16x2 / ffc)
+__device__ __forceinline__ ffc ld_spec(const ffc* p, long i, ffc) { return p[i]; }
 __device__ __forceinline__ double2 ld_spec(const double2* p, long i, double2) { return p[i]; }
 __device__ __forceinline__ float2 ld_spec(const double2* p, long i, float2) {
     double2 v = p[i]; return make_float2((float)v.x, (float)v.y);

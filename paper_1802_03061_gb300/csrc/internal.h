@@ -57,6 +57,9 @@ struct rte_plan_s {
     double2* S64 = nullptr;
     float2* S32 = nullptr;
     __nv_bfloat162* S16 = nullptr;
+    ffc* Sff = nullptr;              // float-float copy of S64 (FP64-accurate passes on FP32 units)
+    ff* S3ff = nullptr;
+    ffc* twff = nullptr;
     float2* S32p = nullptr;          // FP32 / BF16 spectra in the warp column pass's slot order
     __nv_bfloat162* S16p = nullptr;
     double* S3_64 = nullptr;
@@ -112,6 +115,14 @@ rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b
                         const float* z, cudaStream_t s);
 rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s);
 rte_status op2d_permute_spectra(rte_plan p, cudaStream_t s);
+// op2d_ff.cu / op3d.cu: FP64-accurate applications in float-float arithmetic
+rte_status op2d_apply_ff(rte_plan p, MixKind kind, const double* x, const double* f, double* out, double a, double b,
+                         double c, const double* z, cudaStream_t s);
+rte_status op3d_apply_ff(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
+                         const double* z, cudaStream_t s);
+rte_status plan_split_ff(rte_plan p, cudaStream_t s);
+rte_status plan_apply64e(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
+                         const double* z, cudaStream_t s);
 rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s);
 // op2d_64.cu: the FP64 passes on explicit buffers (no plan-owned scratch)
 rte_status op2d_apply64_buffers(rte_plan p, const double* x, double* out, double2* Tb, const double2* S64,

@@ -674,8 +674,11 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cu
     cudaGraphNode_t dep = *dep_io;
     *info = SolveGraphInfo();
     // T.1 and start values
+    // FP64-accurate applications: float-float on the FP32 units in the mixed
+    // mode, native FP64 in the plain FP64 mode
+    auto apply64 = mixed ? plan_apply64e : plan_apply64;
     SEG(g, dep, &info->k_fixed, {
-        TRYS(plan_apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, cs));
+        TRYS(apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, cs));
         TRYS(dev_norm<double>(p->b64, nr, nw1, p->part64, &ref->bnorm, cs));
         k_ref_start<<<1, 32, 0, cs>>>(ref, c_guess);
         k_zero_unless_guess<<<gr, 256, 0, cs>>>(p->u_dev, nr, ref);
@@ -688,7 +691,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cu
         TRYS(add_cond(g, &dep, c_guess, cudaGraphCondTypeIf, &body));
         cudaGraphNode_t d = nullptr;
         SEG(body, d, &info->k_guess, {
-            TRYS(plan_apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+            TRYS(apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
             TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
             k_guess_fallback<<<gr, 256, 0, cs>>>(p->u_dev, p->r64, p->b64, nr, ref);
             k_guess_fallback_state<<<1, 32, 0, cs>>>(ref);
@@ -756,7 +759,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cu
             }
             k_ref_after<<<1, 32, 0, cs>>>(ref, G.st);
             rte_count_launches(2);
-            TRYS(plan_apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+            TRYS(apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
             TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
             k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
             rte_count_launches(1);

@@ -45,8 +45,8 @@ struct RowParams {
 //    source that replaces the mode-0 input (RHS).  out: T [nch][H][n].
 //    grid (ceil(n/RB), nmodes_in), block 256.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_row_fwd(const T* __restrict__ x, const double* __restrict__ f,
+template <typename T, typename TF>
+__global__ void __launch_bounds__(256) k_row_fwd(const TF* __restrict__ x, const double* __restrict__ f,
                                                  T* __restrict__ out, const T* __restrict__ tw, RowParams p) {
     using R = typename real_of<T>::R;
     extern __shared__ unsigned char smraw[];
@@ -71,14 +71,14 @@ __global__ void __launch_bounds__(256) k_row_fwd(const T* __restrict__ x, const 
                     if (ya < n) a = (R)f[(long)ya * n + e];
                     if (yb < n) b = (R)f[(long)yb * n + e];
                 } else {
-                    if (ya < n) a = x[(long)ya * n + e].x;
-                    if (yb < n) b = x[(long)yb * n + e].x;
+                    if (ya < n) a = (R)x[(long)ya * n + e].x;
+                    if (yb < n) b = (R)x[(long)yb * n + e].x;
                 }
                 v = mk<T>(w * a, w * b);
             } else {
                 const int y = y0 + li;
                 if (y < n) {
-                    T u = x[((long)k * n + y) * n + e];
+                    T u = to_c<T>(x[((long)k * n + y) * n + e]);
                     v = mk<T>(w * u.x, w * u.y);
                 }
             }
@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(256) k_row_fwd(const T* __restrict__ x, const 
 // 3. inverse row pass + epilogue  out = a*x + b*v + c*z
 //    in: T [nch][H][n] (column-pass output), grid (ceil(n/RB), L+1)
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const T* __restrict__ x,
-                                                 const T* __restrict__ z, T* __restrict__ out,
+template <typename T, typename TF>
+__global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const TF* __restrict__ x,
+                                                 const TF* __restrict__ z, TF* __restrict__ out,
                                                  const T* __restrict__ tw, RowParams p,
                                                  typename real_of<T>::R a, typename real_of<T>::R b,
                                                  typename real_of<T>::R c) {
@@ -158,26 +158,26 @@ __global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const
             const int ya = y0 + 2 * li, yb = ya + 1;
             if (ya < n) {
                 const long o = (long)ya * n + e;
-                T r = mk<T>(b * v.x, 0);
-                if (x) { r.x += a * x[o].x; r.y += a * x[o].y; }
-                if (z) { r.x += c * z[o].x; r.y += c * z[o].y; }
-                out[o] = r;
+                T r = mk<T>(b * v.x, (R)0);
+                if (x) { const T xv = to_c<T>(x[o]); r.x += a * xv.x; r.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); r.x += c * zv.x; r.y += c * zv.y; }
+                out[o] = to_f<TF>(r);
             }
             if (yb < n) {
                 const long o = (long)yb * n + e;
-                T r = mk<T>(b * v.y, 0);
-                if (x) { r.x += a * x[o].x; r.y += a * x[o].y; }
-                if (z) { r.x += c * z[o].x; r.y += c * z[o].y; }
-                out[o] = r;
+                T r = mk<T>(b * v.y, (R)0);
+                if (x) { const T xv = to_c<T>(x[o]); r.x += a * xv.x; r.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); r.x += c * zv.x; r.y += c * zv.y; }
+                out[o] = to_f<TF>(r);
             }
         } else {
             const int y = y0 + li;
             if (y < n) {
                 const long o = ((long)k * n + y) * n + e;
                 T r = mk<T>(b * v.x, b * v.y);
-                if (x) { r.x += a * x[o].x; r.y += a * x[o].y; }
-                if (z) { r.x += c * z[o].x; r.y += c * z[o].y; }
-                out[o] = r;
+                if (x) { const T xv = to_c<T>(x[o]); r.x += a * xv.x; r.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); r.x += c * zv.x; r.y += c * zv.y; }
+                out[o] = to_f<TF>(r);
             }
         }
     }

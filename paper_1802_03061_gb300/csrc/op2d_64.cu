@@ -22,7 +22,7 @@ rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s) {
 
 rte_status op2d_apply64_buffers(rte_plan p, const double* x, double* out, double2* Tb, const double2* S64,
                                 const double2* tw64, cudaStream_t s) {
-    cudaError_t e = op2d_run<double2, double2>(p, MIX_K, reinterpret_cast<const double2*>(x), nullptr,
+    cudaError_t e = op2d_run<double2, double2, double2>(p, MIX_K, reinterpret_cast<const double2*>(x), nullptr,
                                                reinterpret_cast<double2*>(out), 0.0, 1.0, 0.0, nullptr, Tb,
                                                nullptr, S64, tw64, false, s);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_apply64_buffers");

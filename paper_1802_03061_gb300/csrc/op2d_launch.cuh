@@ -41,12 +41,28 @@ template <typename T> static int split_group(int nch, int Q) {
     return (int)G;
 }
 
+// float-float mode mix, instantiated in op2d_ff_mix_{a,b,c}.cu
+cudaError_t launch_mix_ff(int L, ffc* Ts, const ffc* S, const ColParams& cp, cudaStream_t s);
+cudaError_t launch_mix_ff_a(int L, ffc* Ts, const ffc* S, const ColParams& cp, cudaStream_t s);
+cudaError_t launch_mix_ff_b(int L, ffc* Ts, const ffc* S, const ColParams& cp, cudaStream_t s);
+cudaError_t launch_mix_ff_c(int L, ffc* Ts, const ffc* S, const ColParams& cp, cudaStream_t s);
+inline cudaError_t launch_mix_ff(int L, ffc* Ts, const ffc* S, const ColParams& cp, cudaStream_t s) {
+    return L <= 5 ? launch_mix_ff_a(L, Ts, S, cp, s) : (L <= 7 ? launch_mix_ff_b(L, Ts, S, cp, s)
+                                                                : launch_mix_ff_c(L, Ts, S, cp, s));
+}
+
+// split-only instantiations for float-float: the fused kernel would inline
+// the float-float mode mix into every FFT stage variant (slow to compile)
+template <typename T> struct allow_fused { static constexpr bool value = true; };
+template <> struct allow_fused<ffc> { static constexpr bool value = false; };
+
 template <int L, typename T, typename TS>
 static cudaError_t launch_col(T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split, cudaStream_t s) {
     constexpr int NCH = 2 * L + 1;
     const int Q = cp.Q;
     cudaError_t e;
-    if (!split) {
+    (void)split;
+    if constexpr (allow_fused<T>::value) if (!split) {
         static bool once = false;
         if (!once) { e = allow_smem(k_col_fused<L, T, TS>); if (e != cudaSuccess) return e; once = true; }
         cp.G = col_group<T>(NCH, Q);
@@ -60,9 +76,13 @@ static cudaError_t launch_col(T* Tb, T* Ts, const TS* S, const T* tw, ColParams 
     const size_t smem = (size_t)(Q + 2 * cp.G * Q) * sizeof(T);
     k_col_fft_split<T><<<cp.H, 256, smem, s>>>(Tb, Ts, tw, cp, 1, cp.nin);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const long tot = (long)cp.H * Q;
-    k_mix_pointwise<L, T, TS><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Ts, S, cp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if constexpr (allow_fused<T>::value) {
+        const long tot = (long)cp.H * Q;
+        k_mix_pointwise<L, T, TS><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Ts, S, cp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_mix_ff(L, (ffc*)Ts, (const ffc*)S, cp, s)) != cudaSuccess) return e;
+    }
     k_col_fft_split<T><<<cp.H, 256, smem, s>>>(Tb, Ts, tw, cp, 0, NCH);
     return cudaGetLastError();
 }
@@ -127,16 +147,16 @@ static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, C
 
 // out = a*x + b*(Op x) + c*z ; Op = K (MIX_K) or K~ on the source f (MIX_RHS)
 // stage: -1 all three passes; 0 row pass; 1 column pass; 2 inverse row pass
-template <typename T, typename TS>
-static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* f, T* out, double a, double b,
-                            double c, const T* z, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
+template <typename T, typename TS, typename TF = T>
+static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double* f, TF* out, double a, double b,
+                            double c, const TF* z, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
                             cudaStream_t s, int stage = -1, const TS* Sp = nullptr) {
     using R = typename real_of<T>::R;
     static bool once = false;
     cudaError_t e;
     if (!once) {
-        if ((e = allow_smem(k_row_fwd<T>)) != cudaSuccess) return e;
-        if ((e = allow_smem(k_row_inv<T>)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_row_fwd<T, TF>)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_row_inv<T, TF>)) != cudaSuccess) return e;
         once = true;
     }
     RowParams rp;
@@ -155,7 +175,7 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* 
     const size_t smr = row_smem<T>(p->Q, rp.RB);
     if (stage < 0 || stage == 0) {
         const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
-        k_row_fwd<T><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw, rp);
+        k_row_fwd<T, TF><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw, rp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         rte_count_launches(1);
     }
@@ -177,7 +197,7 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const T* x, const double* 
     }
     if (stage < 0 || stage == 2) {
         const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
-        k_row_inv<T><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b, (R)c);
+        k_row_inv<T, TF><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b, (R)c);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         rte_count_launches(1);
     }
@@ -196,7 +216,7 @@ static cudaError_t op2d_time(rte_plan p, const T* x, T* out, T* Tb, T* Ts, const
     for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
         cudaEventRecord(e0, s);
         for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = op2d_run<T, TS>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st, Sp);
+            e = op2d_run<T, TS, T>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st, Sp);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float t = 0.f;

@@ -310,3 +310,12 @@ rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b
     if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply32");
     return RTE_OK;
 }
+
+rte_status op3d_apply_ff(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
+                         const double* z, cudaStream_t s) {
+    const double w = kind == MIX_K ? p->mu_s : 1.0;
+    cudaError_t e = op3d_run<ffc, double, ff>(p, x, out, w, kind == MIX_K ? a : 0.0, b, c, z, (ffc*)p->T64,
+                                             (ffc*)p->U64, p->S3ff, p->twff, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply_ff");
+    return RTE_OK;
+}

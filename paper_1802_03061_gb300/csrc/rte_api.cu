@@ -72,6 +72,15 @@ rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, 
     return op3d_apply64(p, kind, x, out, a, b, c, z, s);
 }
 
+// FP64-accurate application in float-float arithmetic (used by the mixed
+// refinement for the right-hand side and the residual)
+rte_status plan_apply64e(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
+                         const double* z, cudaStream_t s) {
+    if (p->dim == 2)
+        return op2d_apply_ff(p, kind, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? x : nullptr, out, a, b, c, z, s);
+    return op3d_apply_ff(p, kind, x, out, a, b, c, z, s);
+}
+
 rte_status plan_apply32(rte_plan p, const float* x, float* out, float a, float b, float c, const float* z,
                         cudaStream_t s) {
     if (p->dim == 2) return op2d_apply32(p, x, out, a, b, c, z, s);
@@ -82,7 +91,7 @@ extern "C" rte_status rte_destroy(rte_plan p) {
     if (!p) return RTE_OK;
     cudaDeviceSynchronize();
     krylov_free(p);
-    void* bufs[] = {p->tw64, p->tw32, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
+    void* bufs[] = {p->tw64, p->tw32, p->twff, p->Sff, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
                     p->d32, p->dscal, p->part64, p->f_dev, p->u_dev, p->ref};
     for (void* b : bufs)
@@ -152,12 +161,14 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     } while (0)
     TRY(dalloc(&p->tw64, Q * sizeof(double2)));
     TRY(dalloc(&p->tw32, Q * sizeof(float2)));
+    TRY(dalloc(&p->twff, Q * sizeof(ffc)));
     TRY(dalloc(&p->Dm, (2 * RTE_MAX_L + 1) * sizeof(double)));
     if (grid.dim == 2) {
         const size_t ns = (size_t)H * nch * Q;
         TRY(dalloc(&p->S64, ns * sizeof(double2)));
         TRY(dalloc(&p->S32, ns * sizeof(float2)));
         TRY(dalloc(&p->S16, ns * sizeof(__nv_bfloat162)));
+        TRY(dalloc(&p->Sff, ns * sizeof(ffc)));
         if (Q == 64 || Q == 128 || Q == 256 || Q == 512) {
             TRY(dalloc(&p->S32p, ns * sizeof(float2)));
             TRY(dalloc(&p->S16p, ns * sizeof(__nv_bfloat162)));
@@ -167,12 +178,14 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
         TRY(dalloc((float2**)&p->T32, nt * sizeof(float2)));
         p->col_split64 = (size_t)(Q + nch * Q + Q) * sizeof(double2) > 200 * 1024;
         p->col_split32 = (size_t)(Q + nch * Q + Q) * sizeof(float2) > 200 * 1024;
-        if (p->col_split64) TRY(dalloc((double2**)&p->Tsplit, (size_t)nch * H * Q * sizeof(double2)));
+        // the float-float passes always take the split column path
+        TRY(dalloc((double2**)&p->Tsplit, (size_t)nch * H * Q * sizeof(double2)));
         if (p->col_split32) TRY(dalloc((float2**)&p->Tsplit32, (size_t)nch * H * Q * sizeof(float2)));
     } else {
         const size_t ns = (size_t)H * H * H;
         TRY(dalloc(&p->S3_64, ns * sizeof(double)));
         TRY(dalloc(&p->S3_32, ns * sizeof(float)));
+        TRY(dalloc(&p->S3ff, ns * sizeof(ff)));
         const size_t n1 = (size_t)n * H * n;   // after x pass: [z][xi_x][y]
         const size_t n2 = (size_t)H * Q * n;   // after y pass: [xi_x][xi_y][z]
         TRY(dalloc((double2**)&p->T64, n1 * sizeof(double2)));
@@ -198,12 +211,14 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     }
     TRY(plan_build_spectra(p, s));
     if (grid.dim == 2) TRY(op2d_permute_spectra(p, s));
+    TRY(plan_split_ff(p, s));
     // one application in each precision: validates the launch shapes and
     // sets the kernels' shared-memory attributes before any graph capture
     if (cudaMemsetAsync(p->x64, 0, p->nr * sizeof(double), s) != cudaSuccess) { st = RTE_ECUDA; goto fail; }
     if (cudaMemsetAsync(p->r32, 0, p->nr * sizeof(float), s) != cudaSuccess) { st = RTE_ECUDA; goto fail; }
     TRY(plan_apply64(p, MIX_K, p->x64, p->t64, 1.0, -1.0, 0.0, nullptr, s));
     TRY(plan_apply32(p, p->r32, p->d32, 1.0f, -1.0f, 0.0f, nullptr, s));
+    TRY(plan_apply64e(p, MIX_K, p->x64, p->t64, 1.0, -1.0, 0.0, nullptr, s));
     {
         cudaError_t ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { st = rte_cuda_fail(ce, "plan_create"); goto fail; }
@@ -235,6 +250,11 @@ extern "C" rte_status rte_apply_K(rte_plan p, const void* x, void* y, void* stre
 extern "C" rte_status rte_apply_A(rte_plan p, const void* x, void* y, void* stream) {
     if (!p || !x || !y || x == y) return RTE_EINVAL;
     return plan_apply64(p, MIX_K, (const double*)x, (double*)y, 1.0, -1.0, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_apply_K64e(rte_plan p, const void* x, void* y, void* stream) {
+    if (!p || !x || !y || x == y) return RTE_EINVAL;
+    return plan_apply64e(p, MIX_K, (const double*)x, (double*)y, 0.0, 1.0, 0.0, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" rte_status rte_apply_K32(rte_plan p, const void* x, void* y, void* stream) {

@@ -98,6 +98,13 @@ class Plan:
         B.rte_apply_A(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
         return y
 
+    def apply_K64e(self, x, y=None, stream=None):
+        """FP64-accurate K x in float-float arithmetic on the FP32 units."""
+        self._check(x)
+        y = self.empty() if y is None else y
+        B.rte_apply_K64e(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        return y
+
     def apply_K32(self, x, y=None, stream=None):
         self._check(x, fp32=True)
         y = self.empty(fp32=True) if y is None else y

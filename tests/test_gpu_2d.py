@@ -57,6 +57,9 @@ def test_apply_K_fp64_matches_direct_sum(n, L, mu_t, mu_s, g):
     assert rel(y, ref[L:]) < 1e-12
     ya = p.apply_A(torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(ya, x - ref[L:]) < 1e-12
+    # the same operator in float-float arithmetic on the FP32 units
+    ye = p.apply_K64e(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(ye, ref[L:]) < 1e-12
     p.close()
 
 

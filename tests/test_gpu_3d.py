@@ -48,6 +48,8 @@ def test_apply_K_3d_fp64_matches_direct_sum(n, mu_t, mu_s):
     assert rel(ya, x - ref) < 1e-12
     b = p.rhs(torch.from_numpy(x)).cpu().numpy()
     assert rel(b, ref / mu_s) < 1e-12
+    ye = p.apply_K64e(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(ye, ref) < 1e-12
     p.close()
 
 
