@@ -114,6 +114,7 @@ rte_status op2d_apply64(rte_plan p, MixKind kind, const double* x, const double*
 rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);
 rte_status op2d_time64(rte_plan p, int reps, double* ms, cudaStream_t s);
+rte_status op2d_time_ff(rte_plan p, int reps, double* ms, cudaStream_t s);
 rte_status op2d_permute_spectra(rte_plan p, cudaStream_t s);
 // op2d_ff.cu / op3d.cu: FP64-accurate applications in float-float arithmetic
 rte_status op2d_apply_ff(rte_plan p, MixKind kind, const double* x, const double* f, double* out, double a, double b,

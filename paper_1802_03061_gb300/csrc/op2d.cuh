@@ -193,9 +193,10 @@ __device__ __forceinline__ void tmac(T& acc, typename real_of<T>::R s, bool im, 
     else { acc.x += s * v.x; acc.y += s * v.y; }
 }
 
-template <int L, typename T>
+// outv: T* or any indexable that yields T& (a strided view of global memory)
+template <int L, typename T, typename O>
 __device__ __forceinline__ void mode_mix(const typename real_of<T>::R* sr, const typename real_of<T>::R* si,
-                                         const T* in, T* outv) {
+                                         const T* in, O&& outv) {
     using R = typename real_of<T>::R;
     // P(m): value, imag flag ; M(m): value, imag flag (m may be negative)
 #define PV(m) ((((m) < 0 ? -(m) : (m)) & 1) ? si[(m) < 0 ? -(m) : (m)] : sr[(m) < 0 ? -(m) : (m)])
@@ -259,6 +260,13 @@ __device__ __forceinline__ void mode_mix_rhs(const typename real_of<T>::R* sr, c
         if (k > 0) outv[chB(k)] = Ia;
     }
 }
+
+// a view of channel c at base[c * stride]
+template <typename T> struct Strided {
+    T* base;
+    long stride;
+    __device__ __forceinline__ T& operator[](int c) const { return base[c * stride]; }
+};
 
 struct ColParams {
     int n, Q, H, L, nin, G;   // nin: input channels (nch for K, 1 for the RHS)
@@ -387,12 +395,11 @@ __global__ void k_mix_pointwise(T* __restrict__ Ts, const TS* __restrict__ S, Co
     const int kx = (int)(idx / Q), ky = (int)(idx % Q);
     R sr[2 * L + 1], si[2 * L + 1];
     load_spec<L, T>(S, kx, ky, Q, sr, si);
-    T in[NCH], o[NCH];
+    T in[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) in[c] = c < p.nin ? Ts[((long)c * H + kx) * Q + ky] : mk<T>(0, 0);
-    mode_mix<L, T>(sr, si, in, o);
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) Ts[((long)c * H + kx) * Q + ky] = o[c];
+    // every input is in registers: the outputs go straight back in place
+    mode_mix<L, T>(sr, si, in, Strided<T>{Ts + (long)kx * Q + ky, (long)H * Q});
 }
 
 // ---------------------------------------------------------------------------

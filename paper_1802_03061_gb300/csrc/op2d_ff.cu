@@ -14,6 +14,14 @@ rte_status op2d_apply_ff(rte_plan p, MixKind kind, const double* x, const double
     return RTE_OK;
 }
 
+rte_status op2d_time_ff(rte_plan p, int reps, double* ms, cudaStream_t s) {
+    cudaError_t e = op2d_time<ffc, ffc, double2>(
+        p, reinterpret_cast<const double2*>(p->x64), reinterpret_cast<double2*>(p->t64),
+        reinterpret_cast<ffc*>(p->T64), reinterpret_cast<ffc*>(p->Tsplit), p->Sff, p->twff, true, reps, ms, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_time_ff");
+    return RTE_OK;
+}
+
 __global__ void k_split_ff2(const double2* __restrict__ src, ffc* __restrict__ dst, long n) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = to_ffc(src[i]);

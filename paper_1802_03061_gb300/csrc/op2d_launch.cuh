@@ -206,8 +206,8 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
 
 // average duration of each pass over `reps` back-to-back launches (CUDA
 // events on stream s); ms[0..2] = row, column, inverse row
-template <typename T, typename TS>
-static cudaError_t op2d_time(rte_plan p, const T* x, T* out, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
+template <typename T, typename TS, typename TF = T>
+static cudaError_t op2d_time(rte_plan p, const TF* x, TF* out, T* Tb, T* Ts, const TS* S, const T* tw, bool split,
                              int reps, double* ms, cudaStream_t s, const TS* Sp = nullptr) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -216,7 +216,7 @@ static cudaError_t op2d_time(rte_plan p, const T* x, T* out, T* Tb, T* Ts, const
     for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
         cudaEventRecord(e0, s);
         for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = op2d_run<T, TS, T>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st, Sp);
+            e = op2d_run<T, TS, TF>(p, MIX_K, x, nullptr, out, 1.0, -1.0, 0.0, nullptr, Tb, Ts, S, tw, split, s, st, Sp);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float t = 0.f;
