@@ -184,6 +184,155 @@ __global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const
 }
 
 // ---------------------------------------------------------------------------
+// 1w/3w. row passes with the warp-register FFT (FP32, Q = 32 R): one warp per
+// line (a row of u_k, or two packed rows of u_0), 8 lines per block.  The
+// transform stays in registers; shared memory only holds the spectra of the
+// block's lines (swizzled) for the half-spectrum split / rebuild, which keep
+// the same y-contiguous global layout as the generic passes.
+// grid (ceil(n / 8), modes), block 256; rows per block 8 (k >= 1) or 16 (k = 0)
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__ x, const double* __restrict__ f,
+                                                      float2* __restrict__ out, const float2* __restrict__ tw,
+                                                      RowParams p) {
+    constexpr int Q = 32 * R;
+    constexpr int LS = Q + 2;  // line stride: consecutive lines start 2 bank pairs apart
+    extern __shared__ unsigned char smraw[];
+    float2* twl = reinterpret_cast<float2*>(smraw);
+    float2* Z = twl + Q;
+    const int n = p.n, H = p.H;
+    const int k = blockIdx.y;
+    const int rows = k == 0 ? 16 : 8;
+    const int y0 = blockIdx.x * rows;
+    if (y0 >= n) return;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float wt = (float)p.wk[k];
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = lane + 32 * r;
+        float2 val = make_float2(0.f, 0.f);
+        if (e < n) {
+            if (k == 0) {
+                const int ya = y0 + 2 * w, yb = ya + 1;
+                float a = 0.f, b = 0.f;
+                if (f) {
+                    if (ya < n) a = (float)f[(long)ya * n + e];
+                    if (yb < n) b = (float)f[(long)yb * n + e];
+                } else {
+                    if (ya < n) a = x[(long)ya * n + e].x;
+                    if (yb < n) b = x[(long)yb * n + e].x;
+                }
+                val = make_float2(wt * a, wt * b);
+            } else {
+                const int y = y0 + w;
+                if (y < n) {
+                    const float2 u = x[((long)k * n + y) * n + e];
+                    val = make_float2(wt * u.x, wt * u.y);
+                }
+            }
+        }
+        v[r] = val;
+    }
+    warp_fft_fwd<R>(v, twl);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) Z[w * LS + swz16(k1 + R * brev5(lane))] = v[k1];
+    __syncthreads();
+    // split Z = F + i G into the half spectra (as in k_row_fwd)
+    for (int idx = threadIdx.x; idx < H * rows; idx += blockDim.x) {
+        const int r = idx % rows, xi = idx / rows;
+        const int y = y0 + r;
+        if (y >= n) continue;
+        const int line = k == 0 ? r >> 1 : r;
+        const float2 Zp = Z[line * LS + swz16(xi)];
+        const float2 Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
+        const float2 Fv = make_float2(0.5f * (Zp.x + Zm.x), 0.5f * (Zp.y - Zm.y));
+        const float2 Gv = make_float2(0.5f * (Zp.y + Zm.y), -0.5f * (Zp.x - Zm.x));
+        if (k == 0) {
+            out[(long)xi * n + y] = (r & 1) ? Gv : Fv;
+        } else {
+            out[((long)chA(k) * H + xi) * n + y] = Fv;
+            out[((long)chB(k) * H + xi) * n + y] = Gv;
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__ in, const float2* __restrict__ x,
+                                                      const float2* __restrict__ z, float2* __restrict__ out,
+                                                      const float2* __restrict__ tw, RowParams p, float a, float b,
+                                                      float c) {
+    constexpr int Q = 32 * R;
+    constexpr int LS = Q + 2;
+    extern __shared__ unsigned char smraw[];
+    float2* twl = reinterpret_cast<float2*>(smraw);
+    float2* Z = twl + Q;
+    const int n = p.n, H = p.H;
+    const int k = blockIdx.y;
+    const int rows = k == 0 ? 16 : 8;
+    const int y0 = blockIdx.x * rows;
+    if (y0 >= n) return;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    // Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
+    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
+        const int li = idx & 7, xi = idx >> 3;
+        float2 Fv = make_float2(0.f, 0.f), Gv = make_float2(0.f, 0.f);
+        if (k == 0) {
+            const int ya = y0 + 2 * li, yb = ya + 1;
+            if (ya < n) Fv = in[(long)xi * n + ya];
+            if (yb < n) Gv = in[(long)xi * n + yb];
+        } else {
+            const int y = y0 + li;
+            if (y < n) {
+                Fv = in[((long)chA(k) * H + xi) * n + y];
+                Gv = in[((long)chB(k) * H + xi) * n + y];
+            }
+        }
+        Z[li * LS + swz16(xi)] = make_float2(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = make_float2(Fv.x + Gv.y, Gv.x - Fv.y);
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 v[R];
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) v[k1] = Z[w * LS + swz16(k1 + R * brev5(lane))];
+    warp_fft_inv<R>(v, twl);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = lane + 32 * r;
+        if (e >= n) continue;
+        if (k == 0) {
+            const int ya = y0 + 2 * w, yb = ya + 1;
+            if (ya < n) {
+                const long o = (long)ya * n + e;
+                float2 q = make_float2(b * v[r].x, 0.f);
+                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = q;
+            }
+            if (yb < n) {
+                const long o = (long)yb * n + e;
+                float2 q = make_float2(b * v[r].y, 0.f);
+                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = q;
+            }
+        } else {
+            const int y = y0 + w;
+            if (y < n) {
+                const long o = ((long)k * n + y) * n + e;
+                float2 q = make_float2(b * v[r].x, b * v[r].y);
+                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = q;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 2. mode mix at one frequency: X[c] (in) -> X[c] (out), tagged coefficients
 // ---------------------------------------------------------------------------
 // acc += s * v  (im == false)   or   acc += (i s) * v  (im == true)

@@ -145,6 +145,37 @@ static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, C
     return cudaErrorInvalidValue;
 }
 
+// warp-register row passes (FP32 fields and compute, Q in {64, 128, 256, 512})
+template <typename T, typename TF> struct row_warp_types { static constexpr bool value = false; };
+template <> struct row_warp_types<float2, float2> { static constexpr bool value = true; };
+static inline size_t row_warp_smem(int Q) { return (size_t)(Q + 8 * (Q + 2)) * sizeof(float2); }
+
+static cudaError_t row_fwd_warp(int Q, dim3 grid, const float2* x, const double* f, float2* out, const float2* tw,
+                                const RowParams& rp, cudaStream_t s) {
+    const size_t sm = row_warp_smem(Q);
+    switch (Q) {
+        case 64: k_row_fwd_warp<2><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 128: k_row_fwd_warp<4><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 256: k_row_fwd_warp<8><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 512: k_row_fwd_warp<16><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t row_inv_warp(int Q, dim3 grid, const float2* in, const float2* x, const float2* z, float2* out,
+                                const float2* tw, const RowParams& rp, float a, float b, float c, cudaStream_t s) {
+    const size_t sm = row_warp_smem(Q);
+    switch (Q) {
+        case 64: k_row_inv_warp<2><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 128: k_row_inv_warp<4><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 256: k_row_inv_warp<8><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 512: k_row_inv_warp<16><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // out = a*x + b*(Op x) + c*z ; Op = K (MIX_K) or K~ on the source f (MIX_RHS)
 // stage: -1 all three passes; 0 row pass; 1 column pass; 2 inverse row pass
 template <typename T, typename TS, typename TF = T>
@@ -173,10 +204,22 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
     }
     const int nmod_in = kind == MIX_K ? p->L + 1 : 1;
     const size_t smr = row_smem<T>(p->Q, rp.RB);
+    bool row_warp = false;
+    if constexpr (row_warp_types<T, TF>::value) row_warp = col_warp_ok(p->Q) && p->rb_force < 2;
     if (stage < 0 || stage == 0) {
-        const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
-        k_row_fwd<T, TF><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw, rp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (row_warp) {
+            if constexpr (row_warp_types<T, TF>::value) {
+                const dim3 grid((p->n + 7) / 8, nmod_in);
+                if ((e = row_fwd_warp(p->Q, grid, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw,
+                                      rp, s)) != cudaSuccess)
+                    return e;
+            }
+        } else {
+            const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
+            k_row_fwd<T, TF><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw,
+                                                    rp);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         rte_count_launches(1);
     }
     if (stage < 0 || stage == 1) {
@@ -196,9 +239,19 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         rte_count_launches(split && !warp_path ? 3 : 1);
     }
     if (stage < 0 || stage == 2) {
-        const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
-        k_row_inv<T, TF><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b, (R)c);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (row_warp) {
+            if constexpr (row_warp_types<T, TF>::value) {
+                const dim3 grid2((p->n + 7) / 8, p->L + 1);
+                if ((e = row_inv_warp(p->Q, grid2, Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (float)a,
+                                      (float)b, (float)c, s)) != cudaSuccess)
+                    return e;
+            }
+        } else {
+            const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
+            k_row_inv<T, TF><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b,
+                                                     (R)c);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         rte_count_launches(1);
     }
     return cudaSuccess;

@@ -351,8 +351,9 @@ extern "C" rte_status rte_autotune(int n, int L, int prec, int reps, int* Q_out,
         rte_plan p = nullptr;
         rte_status st = rte_plan_create(&p, g, 1.0 / n, 1.0, 0.5, L, sig, &o, stream);
         if (st != RTE_OK) continue;
-        const int rbs[4] = {2, 4, 8, 16};
-        for (int r = 0; r < 4; ++r) {
+        // 0 = the default row passes (warp-register FFT where Q allows it)
+        const int rbs[5] = {0, 2, 4, 8, 16};
+        for (int r = 0; r < 5; ++r) {
             p->rb_force = rbs[r];
             st = plan_apply32(p, p->r32, p->d32, 1.0f, -1.0f, 0.0f, nullptr, s);  // warm-up
             if (st != RTE_OK) break;

@@ -16,6 +16,13 @@
 
 __device__ __forceinline__ int brev5(int l) { return __brev(l) >> 27; }
 
+// bank swizzle of a line of Q (a multiple of 16) complex values in shared
+// memory: xi -> xi ^ ((xi >> 4) & 15) stays inside its aligned group of 16,
+// so it is a bijection; the 32 lanes of a warp that store one register
+// (frequencies k1 + R brev5(lane), equal low bits) land on 16 distinct bank
+// pairs instead of one
+__device__ __forceinline__ int swz16(int xi) { return xi ^ ((xi >> 4) & 15); }
+
 template <int DIR, typename T> __device__ __forceinline__ void dft16(T* v) {
     // 16 = 4 x 4: inner DFT4 over n1 of x[4 n1 + n2], twiddle W16^{n2 k1}, outer DFT4 over n2
     using Rr = typename real_of<T>::R;

@@ -73,11 +73,16 @@ def test_rhs_matches_direct_sum(n, L, mu_t, mu_s, g):
     p.close()
 
 
+# q = 0: the default padded length (24, 48, 72 here: shared-memory FFT
+# passes); q = 32 * 2^j: the warp-register row and column passes with
+# R = 2, 4, 8, 16 registers per lane, n ragged against their 8/16-row blocks
 @pytest.mark.parametrize("prec,tol", [("mixed_fp32", 1e-5), ("mixed_bf16", 1e-2)])
-@pytest.mark.parametrize("n,L", [(12, 3), (20, 8), (33, 2)])
-def test_apply_K32(prec, tol, n, L):
+@pytest.mark.parametrize("n,L,q", [(12, 3, 0), (20, 8, 0), (33, 2, 0), (12, 3, 64), (20, 8, 128), (33, 2, 256),
+                                   (33, 5, 512), (64, 1, 128)])
+def test_apply_K32(prec, tol, n, L, q):
     sig = rte_synth.hg_sigma_hat(0.5, L)
-    p = _plan(n, 10.0, 9.0, sig, prec=prec)
+    p = _plan(n, 10.0, 9.0, sig, prec=prec, q_policy=q)
+    assert q == 0 or p.Q == q
     rng = np.random.default_rng(7)
     x = random_packed(rng, L, n)
     y = p.apply_K32(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
