@@ -58,6 +58,7 @@ struct rte_plan_s {
     float2* S32 = nullptr;
     __nv_bfloat162* S16 = nullptr;
     ffc* Sff = nullptr;              // float-float copy of S64 (FP64-accurate passes on FP32 units)
+    ffc* Sffp = nullptr;             // the same in the warp column pass's slot order (Q = 32 * 2^j)
     ff* S3ff = nullptr;
     ffc* twff = nullptr;
     float2* S32p = nullptr;          // FP32 / BF16 spectra in the warp column pass's slot order

@@ -342,18 +342,23 @@ __device__ __forceinline__ void tmac(T& acc, typename real_of<T>::R s, bool im, 
     else { acc.x += s * v.x; acc.y += s * v.y; }
 }
 
-// outv: T* or any indexable that yields T& (a strided view of global memory)
-template <int L, typename T, typename O>
-__device__ __forceinline__ void mode_mix(const typename real_of<T>::R* sr, const typename real_of<T>::R* si,
-                                         const T* in, O&& outv) {
+// in / outv: T* or any indexable that yields T / T& (a strided view of
+// global or shared memory)
+// sr / si: the real / imaginary parts of S_m, m = 0..2L, as arrays or any
+// indexable yielding R.  Only the outputs k with k % kmod == kres are formed
+// (several threads may share one frequency).
+template <int L, typename T, typename SR, typename SI, typename I, typename O>
+__device__ __forceinline__ void mode_mix(const SR& sr, const SI& si, I&& in, O&& outv, int kmod = 1, int kres = 0) {
     using R = typename real_of<T>::R;
     // P(m): value, imag flag ; M(m): value, imag flag (m may be negative)
 #define PV(m) ((((m) < 0 ? -(m) : (m)) & 1) ? si[(m) < 0 ? -(m) : (m)] : sr[(m) < 0 ? -(m) : (m)])
 #define PI_(m) ((((m) < 0 ? -(m) : (m)) & 1) != 0)
-#define MV(m) (((m) < 0 ? (R)-1 : (R)1) * ((((m) < 0 ? -(m) : (m)) & 1) ? sr[(m) < 0 ? -(m) : (m)] : si[(m) < 0 ? -(m) : (m)]))
+#define MV_(m) ((((m) < 0 ? -(m) : (m)) & 1) ? sr[(m) < 0 ? -(m) : (m)] : si[(m) < 0 ? -(m) : (m)])
+#define MV(m) ((m) < 0 ? -MV_(m) : MV_(m))
 #define MI_(m) ((((m) < 0 ? -(m) : (m)) & 1) == 0)
 #pragma unroll
     for (int k = 0; k <= L; ++k) {
+        if (k % kmod != kres) continue;
         T Ra = mk<T>(0, 0), Ia = mk<T>(0, 0);
         const T A0 = in[0];
         tmac(Ra, PV(k), PI_(k), A0);
@@ -387,6 +392,7 @@ __device__ __forceinline__ void mode_mix(const typename real_of<T>::R* sr, const
 #undef PV
 #undef PI_
 #undef MV
+#undef MV_
 #undef MI_
 }
 
@@ -534,6 +540,68 @@ __global__ void __launch_bounds__(256) k_col_fft_split(T* __restrict__ Tb, T* __
     }
 }
 
+// float-float mode mix.  The (2L+1)-channel state of a frequency (inputs and
+// spectra, 544 bytes at L = 8) does not fit in registers with useful
+// occupancy, so a block stages 32 frequencies in shared memory and its four
+// warps share them: warp g forms the outputs k = g (mod 4) for the 32
+// frequencies of its lanes, reading every operand afresh from shared memory
+// (volatile loads, so the compiler keeps no copies in registers).
+struct SmemFF {  // v[m * stride].x (part 0) or .y (part 1) as ff
+    const ffc* base;
+    int stride, part;
+    __device__ __forceinline__ ff operator[](int m) const {
+        ff r;
+        const unsigned a = (unsigned)__cvta_generic_to_shared(base + m * stride) + (unsigned)part * 8u;
+        asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.hi), "=f"(r.lo) : "r"(a));
+        return r;
+    }
+};
+struct SmemCol {  // v[c * stride] as ffc
+    const ffc* base;
+    int stride;
+    __device__ __forceinline__ ffc operator[](int c) const {
+        ffc r;
+        const unsigned a = (unsigned)__cvta_generic_to_shared(base + c * stride);
+        asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(r.x.hi), "=f"(r.x.lo), "=f"(r.y.hi), "=f"(r.y.lo)
+                     : "r"(a));
+        return r;
+    }
+};
+
+// grid ceil(H Q / 32), block 128
+template <int L>
+__global__ void __launch_bounds__(128) k_mix_ff(ffc* __restrict__ Ts, const ffc* __restrict__ S, ColParams p) {
+    constexpr int NCH = 2 * L + 1;
+    __shared__ ffc xin[NCH * 32];
+    __shared__ ffc spc[NCH * 32];
+    const int Q = p.Q, H = p.H;
+    const long tot = (long)H * Q, cs = (long)H * Q;
+    const long base = (long)blockIdx.x * 32;
+    for (int i = threadIdx.x; i < 2 * NCH * 32; i += blockDim.x) {
+        const int row = i >> 5;
+        const long idx = base + (i & 31);
+        ffc v = mk<ffc>(0, 0);
+        if (idx < tot) {
+            const int kx = (int)(idx / Q), ky = (int)(idx % Q);
+            if (row < NCH) {
+                if (row < p.nin) v = Ts[(long)row * cs + (long)kx * Q + ky];
+            } else {
+                v = S[((long)kx * NCH + (row - NCH)) * Q + ky];
+            }
+        }
+        if (row < NCH) xin[i] = v;
+        else spc[i - NCH * 32] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long idx = base + lane;
+    if (idx >= tot) return;
+    const int kx = (int)(idx / Q), ky = (int)(idx % Q);
+    mode_mix<L, ffc>(SmemFF{spc + lane, 32, 0}, SmemFF{spc + lane, 32, 1}, SmemCol{xin + lane, 32},
+                     Strided<ffc>{Ts + (long)kx * Q + ky, cs}, 4, warp);
+}
+
 template <int L, typename T, typename TS>
 __global__ void k_mix_pointwise(T* __restrict__ Ts, const TS* __restrict__ S, ColParams p) {
     constexpr int NCH = 2 * L + 1;
@@ -615,6 +683,58 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
             const int y = lane + 32 * r;
             if (y < n) col[y] = v[r];
         }
+    }
+}
+
+// Column FFTs of the float-float passes with the warp-register FFT: one
+// warp per line (channel c, frequency xi_x; line = c * H + xi_x), so the
+// kernels hold no channel group in shared memory and keep many warps per SM.
+// The forward leaves the spectrum in the slot order (s = k1 * 32 + lane) in
+// Ts [line][Q]; the pointwise mode mix then runs on the slot-ordered spectra
+// Sp, and the inverse starts from that order.
+template <int R>
+__global__ void __launch_bounds__(256) k_colw_fwd(const ffc* __restrict__ Tb, ffc* __restrict__ Ts,
+                                                  const ffc* __restrict__ tw, int n, int nlines) {
+    constexpr int Q = 32 * R;
+    __shared__ ffc twl[Q];
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= nlines) return;
+    const int lane = threadIdx.x & 31;
+    const ffc* col = Tb + (long)line * n;
+    ffc v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = lane + 32 * r;
+        v[r] = y < n ? col[y] : mk<ffc>(0, 0);
+    }
+    warp_fft_fwd<R>(v, twl);
+    ffc* o = Ts + (long)line * Q;
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) o[k1 * 32 + lane] = v[k1];
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_colw_inv(ffc* __restrict__ Tb, const ffc* __restrict__ Ts,
+                                                  const ffc* __restrict__ tw, int n, int nlines) {
+    constexpr int Q = 32 * R;
+    __shared__ ffc twl[Q];
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= nlines) return;
+    const int lane = threadIdx.x & 31;
+    const ffc* in = Ts + (long)line * Q;
+    ffc v[R];
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) v[k1] = in[k1 * 32 + lane];
+    warp_fft_inv<R>(v, twl);
+    ffc* col = Tb + (long)line * n;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = lane + 32 * r;
+        if (y < n) col[y] = v[r];
     }
 }
 

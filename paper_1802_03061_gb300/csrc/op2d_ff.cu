@@ -9,7 +9,7 @@ rte_status op2d_apply_ff(rte_plan p, MixKind kind, const double* x, const double
     cudaError_t e = op2d_run<ffc, ffc, double2>(
         p, kind, reinterpret_cast<const double2*>(x), f, reinterpret_cast<double2*>(out), a, b, c,
         reinterpret_cast<const double2*>(z), reinterpret_cast<ffc*>(p->T64), reinterpret_cast<ffc*>(p->Tsplit),
-        p->Sff, p->twff, true, s);
+        p->Sff, p->twff, true, s, -1, p->Sffp);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_apply_ff");
     return RTE_OK;
 }
@@ -17,7 +17,8 @@ rte_status op2d_apply_ff(rte_plan p, MixKind kind, const double* x, const double
 rte_status op2d_time_ff(rte_plan p, int reps, double* ms, cudaStream_t s) {
     cudaError_t e = op2d_time<ffc, ffc, double2>(
         p, reinterpret_cast<const double2*>(p->x64), reinterpret_cast<double2*>(p->t64),
-        reinterpret_cast<ffc*>(p->T64), reinterpret_cast<ffc*>(p->Tsplit), p->Sff, p->twff, true, reps, ms, s);
+        reinterpret_cast<ffc*>(p->T64), reinterpret_cast<ffc*>(p->Tsplit), p->Sff, p->twff, true, reps, ms, s,
+        p->Sffp);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_time_ff");
     return RTE_OK;
 }
@@ -25,6 +26,15 @@ rte_status op2d_time_ff(rte_plan p, int reps, double* ms, cudaStream_t s) {
 __global__ void k_split_ff2(const double2* __restrict__ src, ffc* __restrict__ dst, long n) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = to_ffc(src[i]);
+}
+// the same into the warp column pass's slot order: dst[row][k1 * 32 + lane] = src[row][k1 + R brev5(lane)]
+__global__ void k_split_ff2_slot(const double2* __restrict__ src, ffc* __restrict__ dst, long rows, int Q) {
+    const int R = Q / 32;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < rows * Q; i += (long)gridDim.x * blockDim.x) {
+        const long row = i / Q;
+        const int sl = (int)(i % Q);
+        dst[i] = to_ffc(src[row * Q + (sl >> 5) + R * brev5(sl & 31)]);
+    }
 }
 __global__ void k_split_ff(const double* __restrict__ src, ff* __restrict__ dst, long n) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -34,7 +44,8 @@ __global__ void k_split_ff(const double* __restrict__ src, ff* __restrict__ dst,
 // plan time: float-float copies of the twiddles and spectra
 rte_status plan_split_ff(rte_plan p, cudaStream_t s) {
     k_split_ff2<<<64, 256, 0, s>>>(p->tw64, p->twff, p->Q);
-    if (p->dim == 2) k_split_ff2<<<1024, 256, 0, s>>>(p->S64, p->Sff, (long)p->H * p->nch * p->Q);
+    if (p->dim == 2 && p->Sffp) k_split_ff2_slot<<<1024, 256, 0, s>>>(p->S64, p->Sffp, (long)p->H * p->nch, p->Q);
+    else if (p->dim == 2) k_split_ff2<<<1024, 256, 0, s>>>(p->S64, p->Sff, (long)p->H * p->nch * p->Q);
     else k_split_ff<<<1024, 256, 0, s>>>(p->S3_64, p->S3ff, (long)p->H * p->H * p->H);
     rte_count_launches(2);
     cudaError_t e = cudaGetLastError();

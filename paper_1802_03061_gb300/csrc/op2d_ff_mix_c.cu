@@ -1,13 +1,13 @@
-// Float-float mode-mix kernels (split column path), L = 8..8
+// Float-float mode-mix kernels (float-float column passes), L = 8..8
 // (separate units keep each compilation short).
 #include "op2d.cuh"
 #include "op2d_launch.cuh"
 
 cudaError_t launch_mix_ff_c(int L, ffc* Ts, const ffc* S, const ColParams& cp, cudaStream_t s) {
     const long tot = (long)cp.H * cp.Q;
-    const unsigned g = (unsigned)((tot + 255) / 256);
+    const unsigned g = (unsigned)((tot + 31) / 32);
     switch (L) {
-        case 8: k_mix_pointwise<8, ffc, ffc><<<g, 256, 0, s>>>(Ts, S, cp); break;
+        case 8: k_mix_ff<8><<<g, 128, 0, s>>>(Ts, S, cp); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -145,6 +145,32 @@ static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, C
     return cudaErrorInvalidValue;
 }
 
+// float-float column pass with the warp-register FFT: forward FFT of the
+// input channels' lines, pointwise mode mix on the slot-ordered spectra,
+// inverse FFT of all channels' lines (3 launches)
+static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw, const ColParams& cp,
+                           cudaStream_t s) {
+    const int lin = cp.nin * cp.H, lout = (2 * L + 1) * cp.H;
+    const unsigned gin = (unsigned)((lin + 7) / 8), gout = (unsigned)((lout + 7) / 8);
+    switch (cp.Q) {
+        case 64: k_colw_fwd<2><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 128: k_colw_fwd<4><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 256: k_colw_fwd<8><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 512: k_colw_fwd<16><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_mix_ff(L, Ts, Sp, cp, s)) != cudaSuccess) return e;
+    switch (cp.Q) {
+        case 64: k_colw_inv<2><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 128: k_colw_inv<4><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 256: k_colw_inv<8><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 512: k_colw_inv<16><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
+    }
+    return cudaGetLastError();
+}
+
 // warp-register row passes (FP32 fields and compute, Q in {64, 128, 256, 512})
 template <typename T, typename TF> struct row_warp_types { static constexpr bool value = false; };
 template <> struct row_warp_types<float2, float2> { static constexpr bool value = true; };
@@ -228,15 +254,24 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         cp.nin = kind == MIX_K ? p->nch : 1;
         cp.G = 1;
         cp.sc = p->sched;
+        int launches = split ? 3 : 1;
         bool warp_path = false;
         if constexpr (sizeof(T) == sizeof(float2)) {
             if (Sp && col_warp_ok(p->Q)) {
                 if ((e = dispatch_col_warp<TS>(p->L, (float2*)Tb, Sp, (const float2*)tw, cp, s)) != cudaSuccess) return e;
                 warp_path = true;
+                launches = 1;
+            }
+        }
+        if constexpr (!allow_fused<T>::value) {
+            if (Sp && col_warp_ok(p->Q)) {
+                if ((e = colw_ff(p->L, Tb, Ts, Sp, tw, cp, s)) != cudaSuccess) return e;
+                warp_path = true;
+                launches = 3;
             }
         }
         if (!warp_path && (e = dispatch_col<T, TS>(p->L, Tb, Ts, S, tw, cp, split, s)) != cudaSuccess) return e;
-        rte_count_launches(split && !warp_path ? 3 : 1);
+        rte_count_launches(launches);
     }
     if (stage < 0 || stage == 2) {
         if (row_warp) {

@@ -64,6 +64,21 @@ template <int DIR, typename T> __device__ __forceinline__ void dft16(T* v) {
     }
 }
 
+// exchange a complex value with lane ^ m
+__device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ double2 shfl_xor_c(double2 v, int m) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ ffc shfl_xor_c(ffc v, int m) {
+    ffc r;
+    r.x = ff(__shfl_xor_sync(0xffffffffu, v.x.hi, m), __shfl_xor_sync(0xffffffffu, v.x.lo, m));
+    r.y = ff(__shfl_xor_sync(0xffffffffu, v.y.hi, m), __shfl_xor_sync(0xffffffffu, v.y.lo, m));
+    return r;
+}
+template <typename T> __device__ __forceinline__ T cneg(T a) { return mk<T>(-a.x, -a.y); }
+
 template <int R, int DIR, typename T> __device__ __forceinline__ void dft_regs(T* v) {
     if (R == 2) bfly2<DIR>(v);
     if (R == 4) bfly4<DIR>(v);
@@ -79,16 +94,18 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, 
     dft_regs<R, -1>(v);
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<-1>(tw, lane * k1));
+    // lower lane: a + b; upper lane: (a - b) w, written branch-free as
+    // (+-own + partner) * w with w = 1 on the lower lane (exact)
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
         const bool upper = lane & h;
-        const T w = twid<-1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
+        const T tw1 = twid<-1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
+        const T w = upper ? tw1 : mk<T>(1, 0);
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) {
-            T pv;
-            pv.x = __shfl_xor_sync(0xffffffffu, v[k1].x, h);
-            pv.y = __shfl_xor_sync(0xffffffffu, v[k1].y, h);
-            v[k1] = upper ? cmul(csub(pv, v[k1]), w) : cadd(v[k1], pv);
+            const T pv = shfl_xor_c(v[k1], h);
+            const T own = upper ? cneg(v[k1]) : v[k1];
+            v[k1] = cmul(cadd(own, pv), w);
         }
     }
 }
@@ -97,16 +114,18 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, 
 template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, const T* tw) {
     constexpr int Q = 32 * R;
     const int lane = threadIdx.x & 31;
+    // lower lane: a + w b; upper lane: a - w b (a on the lower, b on the
+    // upper lane): one product per lane, on the upper lane's value
 #pragma unroll
     for (int h = 1; h <= 16; h <<= 1) {
         const bool upper = lane & h;
         const T w = twid<1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) {
-            T pv;
-            pv.x = __shfl_xor_sync(0xffffffffu, v[k1].x, h);
-            pv.y = __shfl_xor_sync(0xffffffffu, v[k1].y, h);
-            v[k1] = upper ? csub(pv, cmul(v[k1], w)) : cadd(v[k1], cmul(pv, w));
+            const T pv = shfl_xor_c(v[k1], h);
+            const T a = upper ? pv : v[k1];
+            const T m = cmul(upper ? v[k1] : pv, w);
+            v[k1] = cadd(a, upper ? cneg(m) : m);
         }
     }
 #pragma unroll
