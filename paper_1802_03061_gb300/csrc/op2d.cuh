@@ -545,36 +545,76 @@ __global__ void __launch_bounds__(256) k_col_fft_split(T* __restrict__ Tb, T* __
 // occupancy, so a block stages 32 frequencies in shared memory and its four
 // warps share them: warp g forms the outputs k = g (mod 4) for the 32
 // frequencies of its lanes, reading every operand afresh from shared memory
-// (volatile loads, so the compiler keeps no copies in registers).
-struct SmemFF {  // v[m * stride].x (part 0) or .y (part 1) as ff
-    const ffc* base;
-    int stride, part;
-    __device__ __forceinline__ ff operator[](int m) const {
-        ff r;
-        const unsigned a = (unsigned)__cvta_generic_to_shared(base + m * stride) + (unsigned)part * 8u;
-        asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.hi), "=f"(r.lo) : "r"(a));
-        return r;
+// (volatile loads, so the compiler keeps no copies in registers).  The loops
+// over k and k' stay rolled (unrolled, the float-float code outgrows the
+// instruction cache); the coefficient parities are still compile-time: all
+// outputs of a warp share the parity of k, and k' steps by two.
+__device__ __forceinline__ ff lds_ff(const ff* p) {
+    ff r;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.hi), "=f"(r.lo) : "r"(a));
+    return r;
+}
+__device__ __forceinline__ ffc lds_ffc(const ffc* p) {
+    ffc r;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x.hi), "=f"(r.x.lo), "=f"(r.y.hi), "=f"(r.y.lo)
+                 : "r"(a));
+    return r;
+}
+// acc += s v (IM = false) or acc += (i s) v (IM = true)
+template <bool IM> __device__ __forceinline__ void tmac_ff(ffc& acc, ff s, ffc v) {
+    if (IM) { acc.x -= s * v.y; acc.y += s * v.x; }
+    else { acc.x += s * v.x; acc.y += s * v.y; }
+}
+// the k' term of output k; ODD = parity of k - k' (= parity of k + k')
+template <bool ODD>
+__device__ __forceinline__ void mix_term_ff(ffc& Ra, ffc& Ia, int k, int kp, const ffc* in, const ff* sr,
+                                            const ff* si) {
+    const ffc A = lds_ffc(in + 32 * chA(kp)), B = lds_ffc(in + 32 * chB(kp));
+    const int d = k - kp, ad = d < 0 ? -d : d, sm = k + kp;
+    const ff* Pt = ODD ? si : sr;
+    const ff* Mt = ODD ? sr : si;
+    const ff pd = lds_ff(Pt + 32 * ad), ps = lds_ff(Pt + 32 * sm);
+    ff md = lds_ff(Mt + 32 * ad);
+    if (d < 0) md = -md;
+    const ff ms = lds_ff(Mt + 32 * sm);
+    tmac_ff<ODD>(Ra, pd + ps, A);                  // (P_d + P_s) A
+    const ff vm1 = md - ms;                        // i (M_d - M_s) B
+    tmac_ff<ODD>(Ra, ODD ? vm1 : -vm1, B);
+    const ff vm2 = md + ms;                        // -i (M_d + M_s) A
+    tmac_ff<ODD>(Ia, ODD ? -vm2 : vm2, A);
+    tmac_ff<ODD>(Ia, pd - ps, B);                  // (P_d - P_s) B
+}
+// outputs k = k0, k0 + 4, ... (all of parity KODD)
+template <int L, bool KODD>
+__device__ __forceinline__ void mix_outputs_ff(int k0, const ffc* in, const ff* sr, const ff* si, ffc* out,
+                                               long cs) {
+#pragma unroll 1
+    for (int k = k0; k <= L; k += 4) {
+        ffc Ra = mk<ffc>(0, 0), Ia = mk<ffc>(0, 0);
+        const ffc A0 = lds_ffc(in);
+        tmac_ff<KODD>(Ra, lds_ff((KODD ? si : sr) + 32 * k), A0);   // P_k A_0
+        const ff mk_ = lds_ff((KODD ? sr : si) + 32 * k);            // -i M_k A_0
+        tmac_ff<KODD>(Ia, KODD ? -mk_ : mk_, A0);
+#pragma unroll 1
+        for (int kp = 1; kp <= L; kp += 2) {
+            mix_term_ff<!KODD>(Ra, Ia, k, kp, in, sr, si);           // k' odd
+            if (kp + 1 <= L) mix_term_ff<KODD>(Ra, Ia, k, kp + 1, in, sr, si);
+        }
+        out[(long)chA(k) * cs] = Ra;
+        if (k > 0) out[(long)chB(k) * cs] = Ia;
     }
-};
-struct SmemCol {  // v[c * stride] as ffc
-    const ffc* base;
-    int stride;
-    __device__ __forceinline__ ffc operator[](int c) const {
-        ffc r;
-        const unsigned a = (unsigned)__cvta_generic_to_shared(base + c * stride);
-        asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(r.x.hi), "=f"(r.x.lo), "=f"(r.y.hi), "=f"(r.y.lo)
-                     : "r"(a));
-        return r;
-    }
-};
+}
 
 // grid ceil(H Q / 32), block 128
 template <int L>
 __global__ void __launch_bounds__(128) k_mix_ff(ffc* __restrict__ Ts, const ffc* __restrict__ S, ColParams p) {
     constexpr int NCH = 2 * L + 1;
-    __shared__ ffc xin[NCH * 32];
-    __shared__ ffc spc[NCH * 32];
+    __shared__ ffc xin[NCH * 32];  // [c][lane]
+    __shared__ ff sre[NCH * 32];   // [m][lane] Re S_m
+    __shared__ ff sim[NCH * 32];   // [m][lane] Im S_m
     const int Q = p.Q, H = p.H;
     const long tot = (long)H * Q, cs = (long)H * Q;
     const long base = (long)blockIdx.x * 32;
@@ -590,16 +630,24 @@ __global__ void __launch_bounds__(128) k_mix_ff(ffc* __restrict__ Ts, const ffc*
                 v = S[((long)kx * NCH + (row - NCH)) * Q + ky];
             }
         }
-        if (row < NCH) xin[i] = v;
-        else spc[i - NCH * 32] = v;
+        if (row < NCH) {
+            xin[i] = v;
+        } else {
+            sre[i - NCH * 32] = v.x;
+            sim[i - NCH * 32] = v.y;
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long idx = base + lane;
     if (idx >= tot) return;
     const int kx = (int)(idx / Q), ky = (int)(idx % Q);
-    mode_mix<L, ffc>(SmemFF{spc + lane, 32, 0}, SmemFF{spc + lane, 32, 1}, SmemCol{xin + lane, 32},
-                     Strided<ffc>{Ts + (long)kx * Q + ky, cs}, 4, warp);
+    ffc* out = Ts + (long)kx * Q + ky;
+    // P_m = Re S_m (m even) / i Im S_m (m odd); M_m = i Im S_m (even) / Re S_m (odd);
+    // P_{-m} = P_m, M_{-m} = -M_m (the same formulas as mode_mix); warp g
+    // forms k = g, g + 4, ..., all of the parity of g
+    if (warp & 1) mix_outputs_ff<L, true>(warp, xin + lane, sre + lane, sim + lane, out, cs);
+    else mix_outputs_ff<L, false>(warp, xin + lane, sre + lane, sim + lane, out, cs);
 }
 
 template <int L, typename T, typename TS>

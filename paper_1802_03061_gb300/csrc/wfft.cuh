@@ -86,6 +86,39 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_regs(T
     if (R == 16) dft16<DIR>(v);
 }
 
+// one decimation-in-frequency lane stage of span h: lower lane a + b, upper
+// lane (a - b) w, written branch-free as (+-own + partner) * w with w = 1 on
+// the lower lane (exact)
+template <int R, typename T> __device__ __forceinline__ void lane_stage_fwd(T* v, const T* tw, int h, int lane) {
+    constexpr int Q = 32 * R;
+    const bool upper = lane & h;
+    const T tw1 = twid<-1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
+    const T w = upper ? tw1 : mk<T>(1, 0);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+        const T pv = shfl_xor_c(v[k1], h);
+        const T own = upper ? cneg(v[k1]) : v[k1];
+        v[k1] = cmul(cadd(own, pv), w);
+    }
+}
+// one decimation-in-time lane stage: lower lane a + w b, upper lane a - w b
+// (a on the lower, b on the upper lane): one product per lane
+template <int R, typename T> __device__ __forceinline__ void lane_stage_inv(T* v, const T* tw, int h, int lane) {
+    constexpr int Q = 32 * R;
+    const bool upper = lane & h;
+    const T w = twid<1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+        const T pv = shfl_xor_c(v[k1], h);
+        const T a = upper ? pv : v[k1];
+        const T m = cmul(upper ? v[k1] : pv, w);
+        v[k1] = cadd(a, upper ? cneg(m) : m);
+    }
+}
+// wide types (float-float) keep the five lane stages rolled: unrolled, the
+// transform outgrows the instruction cache
+template <typename T> struct roll_lane_stages { static constexpr bool value = sizeof(T) > 8; };
+
 // forward: v[r] = x[lane + 32 r]  ->  v[k1] = X[k1 + R brev5(lane)]
 // tw: table exp(-2 pi i t / Q), Q = 32 R
 template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, const T* tw) {
@@ -94,39 +127,25 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, 
     dft_regs<R, -1>(v);
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<-1>(tw, lane * k1));
-    // lower lane: a + b; upper lane: (a - b) w, written branch-free as
-    // (+-own + partner) * w with w = 1 on the lower lane (exact)
+    if constexpr (roll_lane_stages<T>::value) {
+#pragma unroll 1
+        for (int h = 16; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
+    } else {
 #pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        const bool upper = lane & h;
-        const T tw1 = twid<-1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
-        const T w = upper ? tw1 : mk<T>(1, 0);
-#pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) {
-            const T pv = shfl_xor_c(v[k1], h);
-            const T own = upper ? cneg(v[k1]) : v[k1];
-            v[k1] = cmul(cadd(own, pv), w);
-        }
+        for (int h = 16; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
     }
+    (void)Q;
 }
 
 // inverse (unnormalised): v[k1] = X[k1 + R brev5(lane)]  ->  v[r] = Q x[lane + 32 r]
 template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, const T* tw) {
-    constexpr int Q = 32 * R;
     const int lane = threadIdx.x & 31;
-    // lower lane: a + w b; upper lane: a - w b (a on the lower, b on the
-    // upper lane): one product per lane, on the upper lane's value
+    if constexpr (roll_lane_stages<T>::value) {
+#pragma unroll 1
+        for (int h = 1; h <= 16; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
+    } else {
 #pragma unroll
-    for (int h = 1; h <= 16; h <<= 1) {
-        const bool upper = lane & h;
-        const T w = twid<1>(tw, (lane & (h - 1)) * (Q / (2 * h)));
-#pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) {
-            const T pv = shfl_xor_c(v[k1], h);
-            const T a = upper ? pv : v[k1];
-            const T m = cmul(upper ? v[k1] : pv, w);
-            v[k1] = cadd(a, upper ? cneg(m) : m);
-        }
+        for (int h = 1; h <= 16; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
     }
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<1>(tw, lane * k1));
