@@ -297,6 +297,7 @@ def run_native(args):
     mv_bytes32 = 2 * n * n * nch * 4 + nch * (Q * Q // 2) * s_spec  # algorithmic bytes of one K application
     hbm_peak, peak_src = peaks()
     ach = col_bytes32 / (ms32[1] * 1e-3) / 1e9
+    cufft_ms = cufft_pair_ms((L + 1, n, n), (plan.Q, plan.Q), real=False)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -314,6 +315,11 @@ def run_native(args):
                    "bf16_spectra_iters": float(np.mean(bf16_its)) if bf16_its else None,
                    "pass_ms_fp32": ms32, "pass_ms_fp64": ms64,
                    "matvec_fp32_ms": sum(ms32), "matvec_fp32_useful_GBs": mv_bytes32 / (sum(ms32) * 1e-3) / 1e9,
+                   "pass_ms_float_float": B.rte_time_passes(plan.handle, 2, reps, int(stream.cuda_stream)),
+                   "cufft_comparator_ms": cufft_ms,
+                   "cufft_comparator": "torch.fft (cuFFT) fft2 + ifft2 of the %d zero-padded complex mode fields "
+                                       "(%dx%d), FFT work only, no mode mix; compare matvec_fp32_ms"
+                                       % (L + 1, plan.Q, plan.Q),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"kernel": "column pass (FFT_y, mode mix, iFFT_y), FP32, %s spectra" % s_name, "bound": "hbm",
                      "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
@@ -335,6 +341,34 @@ def run_native(args):
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def cufft_pair_ms(shape_in, s_fft, real, reps=20):
+    """Comparator only (never on the product path): cuFFT (through torch.fft)
+    forward + inverse transforms of the same zero-padded volume the operator
+    transforms, without the mode mix; CUDA events, after warm-up."""
+    import torch
+
+    if real:
+        x = torch.randn(shape_in, dtype=torch.float32, device="cuda")
+        fwd = lambda: torch.fft.rfftn(x, s=s_fft)
+        inv = lambda X: torch.fft.irfftn(X, s=s_fft)
+    else:
+        x = torch.zeros(shape_in[:-2] + s_fft, dtype=torch.complex64, device="cuda")
+        x[..., :shape_in[-2], :shape_in[-1]] = torch.randn(shape_in, dtype=torch.complex64, device="cuda")
+        fwd = lambda: torch.fft.fft2(x)
+        inv = lambda X: torch.fft.ifft2(X)
+    for _ in range(3):
+        inv(fwd())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        inv(fwd())
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def run_batch(args):
@@ -441,6 +475,13 @@ def run_iso3d(args):
     e1.record(stream)
     e1.synchronize()
     mv64 = e0.elapsed_time(e1) / 5
+    e0.record(stream)
+    for _ in range(5):
+        plan.apply_K64e(x64)
+    e1.record(stream)
+    e1.synchronize()
+    mv64e = e0.elapsed_time(e1) / 5
+    cufft_ms = cufft_pair_ms((n, n, n), (plan.Q, plan.Q, plan.Q), real=True)
     H = plan.Q // 2 + 1
     alg32 = 2 * n ** 3 * 4 + H ** 3 * 4  # field in + out, octant spectrum (FP32)
     hbm, src = peaks()
@@ -454,7 +495,11 @@ def run_iso3d(args):
                        "outer_mean": float(np.mean([s_["outer"] for s_ in stats])),
                        "all_converged": all(s_["converged"] for s_ in stats),
                        "relres_max": max(s_["relres_true"] for s_ in stats),
-                       "matvec_fp32_ms": mv32, "matvec_fp64_ms": mv64, "t_pre_ms": stats[0]["ms_pre"],
+                       "matvec_fp32_ms": mv32, "matvec_fp64_ms": mv64, "matvec_float_float_ms": mv64e,
+                       "cufft_comparator_ms": cufft_ms,
+                       "cufft_comparator": "torch.fft (cuFFT) rfftn + irfftn of the field zero-padded to %d^3, "
+                                           "FFT work only; compare matvec_fp32_ms" % plan.Q,
+                       "t_pre_ms": stats[0]["ms_pre"],
                        "l2": "flushed before every timed step"},
             "roofline": {"kernel": "3D FP32 K application (5 passes)", "bound": "hbm",
                          "achieved": alg32 / (mv32 * 1e-3) / 1e9, "peak": hbm,
@@ -462,6 +507,90 @@ def run_iso3d(args):
                          "peak_source": src, "algorithmic_bytes_per_launch": alg32},
             "gpu_launches": int(launches), "clocks": clk}
     plan.close()
+    print(json.dumps(line))
+
+
+def run_learned(args):
+    """The learned-initial-guess workload: 2D 256^2, L = 4, HG g in [0, 0.7],
+    mu_t log-U[1, 50], mu_s/mu_t U[0.5, 0.99], 1-6 Gaussians.  Training data
+    are solver-generated (batched mixed solves), the network is trained on the
+    GPU by the library's kernels, then held-out seeds are solved to the same
+    FP64 residual 1e-8 from the zero start and from the learned guess (guess
+    time included).  A step is one held-out solve with the learned guess."""
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Plan, learned
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    n, L = 256, 4
+    t0 = time.perf_counter()
+    train = [rte_synth.learned_guess_instance(10 ** 6 + i, n=n, L=L) for i in range(args.train)]
+    net = learned.GuessNet(L=L, depth=6, seed=1)
+    X, T, gst = learned.generate(train, net.cin, net.cout, chunk=128)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    loss0 = net.loss(X[:64], T[:64])
+    t1 = time.perf_counter()
+    net.train(X, T, epochs=args.epochs, batch=8, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    loss1 = net.loss(X[:64], T[:64])
+    del X, T
+    torch.cuda.empty_cache()
+    held = [rte_synth.learned_guess_instance(i, n=n, L=L) for i in range(args.warmup + args.steps)]
+    learned.evaluate(net, held[:args.warmup])  # warm-up steps (discarded)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = B.rte_kernel_launches()
+    rows = learned.evaluate(net, held[args.warmup:])
+    launches = B.rte_kernel_launches() - l0
+    clk = clocks.stop()
+    sm = learned.summarize(rows)
+    # plain FP64 GPU solves of the first held-out instances (the metric's comparison)
+    fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fp64_ms, guess_only_ms = [], []
+    for d in held[args.warmup:args.warmup + min(4, args.steps)]:
+        p = Plan(n, h=d["h"], mu_t=d["mu_t"], mu_s=d["mu_s"], sigma_hat=d["sigma_hat"], prec="mixed_fp32",
+                 restart=30, maxit=4000)
+        f = torch.from_numpy(d["f"]).cuda()
+        net.guess(p, f)
+        e0.record()
+        net.guess(p, f)  # b = K~ g, features, network forward, u0
+        e1.record()
+        e1.synchronize()
+        guess_only_ms.append(e0.elapsed_time(e1))
+        p.solve(f, prec="fp64")
+        fl.zero_()
+        e0.record()
+        p.solve(f, prec="fp64")
+        e1.record()
+        e1.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+        p.close()
+    ms = sm["guess_ms"]
+    line = {"metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner (f32 spectra), f64 refinement; bf16 network", "data": "synthetic",
+            "config": {"workload": "learned_guess_256_L4: 256x256, L=4, HG g U[0,0.7], mu_t log-U[1,50], "
+                                   "mu_s/mu_t U[0.5,0.99], 1-6 Gaussians; held-out seeds 0..; tol 1e-8",
+                       "train_instances": args.train, "epochs": args.epochs, "generate_s": gen_s,
+                       "train_s": train_s, "loss_before": loss0, "loss_after": loss1,
+                       "zero_start_ms": sm["zero_ms"], "guess_ms": sm["guess_ms"],
+                       "zero_start_iters": sm["zero_iters"], "guess_iters": sm["guess_iters"],
+                       "guess_relres0_median": sm["guess_relres0_median"], "time_ratio": sm["time_ratio"],
+                       "all_converged": sm["all_converged"], "max_solution_diff": sm["max_solution_diff"],
+                       "fp64_ms_per_solve_first4": float(np.mean(fp64_ms)),
+                       "guess_only_ms_first4": float(np.mean(guess_only_ms)),
+                       "speedup_vs_fp64": float(np.mean(fp64_ms)) / ms,
+                       "l2": "flushed (256 MB write) before every timed solve"},
+            "gpu_launches": int(launches), "clocks": clk}
+    net.close()
     print(json.dumps(line))
 
 
@@ -498,7 +627,10 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hg2d_transport", choices=["hg2d_transport", "batch512", "iso3d"])
+    ap.add_argument("--workload", default="hg2d_transport",
+                    choices=["hg2d_transport", "batch512", "iso3d", "learned"])
+    ap.add_argument("--train", type=int, default=1024, help="learned workload: training instances")
+    ap.add_argument("--epochs", type=int, default=4, help="learned workload: training epochs")
     ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -515,6 +647,9 @@ def main():
         return
     if args.workload == "iso3d":
         run_iso3d(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
     run_native(args)
 
