@@ -44,6 +44,8 @@ struct GmresDev {
     double res;     // |g_{j}|, the residual estimate
     double nrm;     // last norm result
     double bnorm;   // ||rhs||
+    double vscale;  // FP32 steps: the newest basis vector V_j is stored unscaled; V_j * vscale is unit
+    unsigned int cnt1, cnt2;  // finished-block counters of the fused FP32 step kernels (reset by the last block)
     double cs[GM_MMAX], sn[GM_MMAX], g[GM_MMAX + 1];
     double Hc[(GM_MMAX + 1) * GM_MMAX];  // H[i + j*(m+1)]
     double hA[GM_MMAX + 1], hB[GM_MMAX + 1], y[GM_MMAX];
@@ -291,6 +293,7 @@ __global__ void k_cycle_init(GmresDev* st, cudaGraphConditionalHandle loop) {
     st->j = 0;
     st->stop = 0;
     st->conv = 0;
+    st->vscale = 1.0;  // V_0 is written normalised
     st->beta = nrm;
     st->res = nrm;
     for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
@@ -302,23 +305,16 @@ __global__ void k_cycle_init(GmresDev* st, cudaGraphConditionalHandle loop) {
     cudaGraphSetConditional(loop, skip ? 0u : 1u);
 }
 
-// One Givens update; column h = hA (+ hB), h_{j+1} = st->nrm.  One warp.
-__global__ void k_givens(GmresDev* st, cudaGraphConditionalHandle loop) {
-    __shared__ double col[GM_MMAX + 2], cs[GM_MMAX], sn[GM_MMAX];
+// One Givens update of column j from col[0..j] (Hessenberg column, FP64) and
+// h_{j+1} = hn; one thread.  Updates the residual estimate and the loop
+// condition.
+__device__ void givens_update(GmresDev* st, double* col, double hn, cudaGraphConditionalHandle loop) {
     const int j = st->j, m = st->m, ld = m + 1;
-    const int two = st->cgs2;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = st->hA[i] + (two ? st->hB[i] : 0.0);
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        cs[i] = st->cs[i];
-        sn[i] = st->sn[i];
-    }
-    __syncwarp();
-    if (threadIdx.x != 0) return;
-    const double hn = st->nrm;
     col[j + 1] = hn;
     for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        const double c = st->cs[i], sn = st->sn[i];
+        const double t = c * col[i] + sn * col[i + 1];
+        col[i + 1] = -sn * col[i] + c * col[i + 1];
         col[i] = t;
     }
     const double a = col[j], b = col[j + 1];
@@ -342,6 +338,156 @@ __global__ void k_givens(GmresDev* st, cudaGraphConditionalHandle loop) {
     if (j + 1 >= m || st->its >= st->maxit) stop = 1;
     st->stop = stop;
     cudaGraphSetConditional(loop, stop ? 0u : 1u);
+}
+
+// Givens step of the FP64 path: column h = hA (+ hB), h_{j+1} = st->nrm
+__global__ void k_givens(GmresDev* st, cudaGraphConditionalHandle loop) {
+    __shared__ double col[GM_MMAX + 2];
+    const int j = st->j;
+    const int two = st->cgs2;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = st->hA[i] + (two ? st->hB[i] : 0.0);
+    __syncwarp();
+    if (threadIdx.x != 0) return;
+    givens_update(st, col, st->nrm, loop);
+}
+
+// --------------------------------------------------------------------------
+// fused FP32 Arnoldi step (CGS1): two kernels after the matvec instead of six.
+// V_j arrives unscaled (the previous step stored w without dividing by its
+// norm); with s = vscale, A V_j = s * w_raw.
+//  k_step_dot : V_j <- s V_j (in place, once), h_i = <V_i, s w_raw>, i <= j;
+//               the last block to finish sums the per-block partials in a
+//               fixed order (deterministic) into hA.
+//  k_step_upd : w = s w_raw - sum_i h_i V_i, stored unscaled as V_{j+1} and as
+//               the next matvec input, partial ||w||^2; the last block forms
+//               the norm, vscale = 1/||w||, and the Givens update.
+// "Last block" = the block whose atomic increment of the finished counter
+// returns gridDim.x - 1 after a __threadfence(); nothing waits.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_step_dot(float* __restrict__ V, long nr, const float* __restrict__ w,
+                                                  GmresDev* __restrict__ st, long nw1, double* __restrict__ part) {
+    const int j = st->j, count = j + 1;
+    const float s = (float)st->vscale;
+    const bool rescale = s != 1.f;
+    const int nb = gridDim.x;
+    __shared__ double red[GM_MMAX + 1][8];
+    __shared__ bool last;
+    const long base = (long)blockIdx.x * TILE + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float wv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long e = base + 256 * q;
+        wv[q] = e < nr ? __fmul_rn(s, w[e]) * (e < nw1 ? 1.f : 2.f) : 0.f;
+    }
+    for (int i = 0; i < count; ++i) {
+        float* v = V + (long)i * nr;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long e = base + 256 * q;
+            if (e < nr) {
+                float vv = v[e];
+                if (i == j && rescale) {
+                    vv = __fmul_rn(vv, s);
+                    v[e] = vv;
+                }
+                ff_fma(hi, lo, vv, wv[q]);
+            }
+        }
+        ff_warp_sum(hi, lo);
+        if (lane == 0) red[i][wid] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[i][q];
+        part[(long)i * nb + blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt1, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = wid; i < count; i += 8) {
+        double t = 0.0;
+        for (int b = lane; b < nb; b += 32) t += __ldcg(part + (long)i * nb + b);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) st->hA[i] = t;
+    }
+    if (threadIdx.x == 0) st->cnt1 = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_step_upd(const float* __restrict__ V, long nr, const float* __restrict__ w,
+                                                  float* __restrict__ vin, GmresDev* __restrict__ st, long nw1,
+                                                  double* __restrict__ part, cudaGraphConditionalHandle loop) {
+    const int j = st->j, count = j + 1;
+    const float s = (float)st->vscale;
+    const int nb = gridDim.x;
+    __shared__ double c[GM_MMAX + 1];
+    __shared__ double red[256];
+    __shared__ bool last;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) c[i] = -st->hA[i];
+    __syncthreads();
+    const long base = (long)blockIdx.x * TILE + threadIdx.x;
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long e = base + 256 * q;
+        acc[q] = e < nr ? __fmul_rn(s, w[e]) : 0.f;
+    }
+    for (int i = 0; i < count; ++i) {
+        const float* v = V + (long)i * nr;
+        const float ci = (float)c[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long e = base + 256 * q;
+            if (e < nr) acc[q] = fmaf(ci, v[e], acc[q]);
+        }
+    }
+    float* vn = const_cast<float*>(V) + (long)(j + 1) * nr;
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long e = base + 256 * q;
+        if (e < nr) {
+            const float nv = acc[q];
+            vn[e] = nv;
+            vin[e] = nv;
+            ff_fma(hi, lo, nv, nv * (e < nw1 ? 1.f : 2.f));
+        }
+    }
+    ff_warp_sum(hi, lo);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt2, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(part + b);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double nrm = sqrt(red[0]);
+    st->nrm = nrm;
+    st->vscale = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    st->cnt2 = 0u;
+    for (int i = 0; i <= j; ++i) c[i] = st->hA[i];  // reuse shared storage for the column
+    givens_update(st, c, nrm, loop);
 }
 
 // back substitution H(0:k,0:k) y = g(0:k), k = st->j
@@ -556,6 +702,16 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, cudaGraphConditionalHandle l
     rte_status e = apply_A_T(G.p, G.vin, G.w, s);
     if (e != RTE_OK) return e;
     const int* jp = &G.st->j;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (!cgs2) {
+            k_step_dot<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
+            k_step_upd<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st, G.nw1,
+                                          G.part, loop);
+            rte_count_launches(2);
+            RTE_CUDA_TRY(cudaGetLastError());
+            return RTE_OK;
+        }
+    }
     k_mdot<T><<<nb, 256, 0, s>>>(G.V, nr, G.w, jp, 1, G.nw1, G.part);
     k_reduce<<<G.m + 1, 256, 0, s>>>(G.part, nb, jp, 1, G.st->hA, 0);
     rte_count_launches(2);
