@@ -11,6 +11,8 @@
 //   X' : Hermitian completion of two rows, inverse complex FFT, keep x < n,
 //        epilogue.
 // Each intermediate is laid out so that the next pass reads contiguous lines.
+#include <type_traits>
+
 #include "fft.cuh"
 #include "internal.h"
 #include "wfft.cuh"
@@ -233,6 +235,245 @@ __global__ void __launch_bounds__(256) k3_x_inv(const T* __restrict__ T1, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same five passes with the warp-register FFT (Q = 32 RQ, FP32 or
+// float-float compute), one warp per line:
+//   X  : 8 warps per block = 16 rows of one z plane (packed pairs), split
+//        through a swizzled shared line buffer     -> T1[z][xi_x][y]
+//   Y  : 16 warps per block = 16 consecutive z of one xi_x; the spectrum is
+//        written in the FFT's slot order s = k1*32 + lane (xi_y = k1 + RQ
+//        brev5(lane)) through a shared [s][z] tile -> T2[xi_x][s][z]
+//   Z  : per (xi_x, s) line: FFT, * S, iFFT in registers (in place)
+//   Y' : reads the slot order back into the inverse  -> T1[z][xi_x][y]
+//   X' : Hermitian rebuild, inverse FFT, epilogue in the compute type.
+// ---------------------------------------------------------------------------
+template <typename RO, typename RR> __device__ __forceinline__ RO out_cast(RR v) { return static_cast<RO>(v); }
+
+template <int RQ, typename T, typename RI>
+__global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __restrict__ T1,
+                                                 const T* __restrict__ tw, int n, int H, double w) {
+    constexpr int Q = 32 * RQ, LS = Q + 2;
+    using RR = typename real_of<T>::R;
+    extern __shared__ unsigned char smraw[];
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Z = twl + Q;
+    const int z = blockIdx.y, y0 = blockIdx.x * 16;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RR ww = (RR)w;
+    const int ya = y0 + 2 * wp, yb = ya + 1;
+    T v[RQ];
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int e = lane + 32 * r;
+        RR a = (RR)0, b = (RR)0;
+        if (e < n) {
+            if (ya < n) a = (RR)x[((long)z * n + ya) * n + e];
+            if (yb < n) b = (RR)x[((long)z * n + yb) * n + e];
+        }
+        v[r] = mk<T>(ww * a, ww * b);
+    }
+    warp_fft_fwd<RQ>(v, twl);
+#pragma unroll
+    for (int k1 = 0; k1 < RQ; ++k1) Z[wp * LS + swz16(k1 + RQ * brev5(lane))] = v[k1];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < H * 16; idx += blockDim.x) {
+        const int r = idx & 15, xi = idx >> 4;
+        const int y = y0 + r;
+        if (y >= n) continue;
+        const int line = r >> 1;
+        const T Zp = Z[line * LS + swz16(xi)];
+        const T Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
+        T o;
+        if ((r & 1) == 0) o = mk<T>((RR)0.5 * (Zp.x + Zm.x), (RR)0.5 * (Zp.y - Zm.y));
+        else o = mk<T>((RR)0.5 * (Zp.y + Zm.y), (RR)-0.5 * (Zp.x - Zm.x));
+        T1[((long)z * H + xi) * n + y] = o;
+    }
+}
+
+template <int RQ, typename T>
+__global__ void __launch_bounds__(512) k3w_y_fwd(const T* __restrict__ T1, T* __restrict__ T2,
+                                                 const T* __restrict__ tw, int n, int H) {
+    constexpr int Q = 32 * RQ, ZS = 17;
+    extern __shared__ unsigned char smraw[];
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Y = twl + Q;  // [s][ZS]
+    const int kx = blockIdx.y, z0 = blockIdx.x * 16;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = z0 + wp;
+    T v[RQ];
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int y = lane + 32 * r;
+        v[r] = (z < n && y < n) ? T1[((long)z * H + kx) * n + y] : mk<T>(0, 0);
+    }
+    warp_fft_fwd<RQ>(v, twl);
+#pragma unroll
+    for (int k1 = 0; k1 < RQ; ++k1) Y[(k1 * 32 + lane) * ZS + wp] = v[k1];
+    __syncthreads();
+    const int nz = min(16, n - z0);
+    for (int idx = threadIdx.x; idx < Q * 16; idx += blockDim.x) {
+        const int zl = idx & 15, sl = idx >> 4;
+        if (zl < nz) T2[((long)kx * Q + sl) * n + z0 + zl] = Y[sl * ZS + zl];
+    }
+}
+
+template <int RQ, typename T, typename TS>
+__global__ void __launch_bounds__(256) k3w_z_mix(T* __restrict__ T2, const TS* __restrict__ S,
+                                                 const T* __restrict__ tw, int n, int H, long nlines) {
+    constexpr int Q = 32 * RQ;
+    using RR = typename real_of<T>::R;
+    __shared__ T twl[Q];
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (line >= nlines) return;
+    T v[RQ];
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int z = lane + 32 * r;
+        v[r] = z < n ? T2[line * n + z] : mk<T>(0, 0);
+    }
+    warp_fft_fwd<RQ>(v, twl);
+    const int kx = (int)(line / Q), sl = (int)(line % Q);
+    const int ky = (sl >> 5) + RQ * brev5(sl & 31);  // slot -> frequency
+    const TS* Srow = S + ((long)kx * H + fold(ky, Q)) * H;
+    const int k2 = brev5(lane);
+#pragma unroll
+    for (int k1 = 0; k1 < RQ; ++k1) {
+        const RR sv = (RR)Srow[fold(k1 + RQ * k2, Q)];
+        v[k1] = mk<T>(v[k1].x * sv, v[k1].y * sv);
+    }
+    warp_fft_inv<RQ>(v, twl);
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int z = lane + 32 * r;
+        if (z < n) T2[line * n + z] = v[r];
+    }
+}
+
+template <int RQ, typename T>
+__global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __restrict__ T1,
+                                                 const T* __restrict__ tw, int n, int H) {
+    constexpr int Q = 32 * RQ, ZS = 17;
+    extern __shared__ unsigned char smraw[];
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Y = twl + Q;  // [s][ZS]
+    const int kx = blockIdx.y, z0 = blockIdx.x * 16;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    const int nz = min(16, n - z0);
+    for (int idx = threadIdx.x; idx < Q * 16; idx += blockDim.x) {
+        const int zl = idx & 15, sl = idx >> 4;
+        Y[sl * ZS + zl] = zl < nz ? T2[((long)kx * Q + sl) * n + z0 + zl] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T v[RQ];
+#pragma unroll
+    for (int k1 = 0; k1 < RQ; ++k1) v[k1] = Y[(k1 * 32 + lane) * ZS + wp];
+    warp_fft_inv<RQ>(v, twl);
+    const int z = z0 + wp;
+    if (z >= n) return;
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int y = lane + 32 * r;
+        if (y < n) T1[((long)z * H + kx) * n + y] = v[r];
+    }
+}
+
+template <int RQ, typename T, typename RI>
+__global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const RI* __restrict__ x,
+                                                 const RI* __restrict__ zv, RI* __restrict__ out,
+                                                 const T* __restrict__ tw, int n, int H, double a, double b,
+                                                 double c) {
+    constexpr int Q = 32 * RQ, LS = Q + 2;
+    using RR = typename real_of<T>::R;
+    extern __shared__ unsigned char smraw[];
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Z = twl + Q;
+    const int z = blockIdx.y, y0 = blockIdx.x * 16;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
+        const int li = idx & 7, xi = idx >> 3;
+        const int ya = y0 + 2 * li, yb = ya + 1;
+        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
+        if (ya < n) Fv = T1[((long)z * H + xi) * n + ya];
+        if (yb < n) Gv = T1[((long)z * H + xi) * n + yb];
+        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+    }
+    __syncthreads();
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T v[RQ];
+#pragma unroll
+    for (int k1 = 0; k1 < RQ; ++k1) v[k1] = Z[wp * LS + swz16(k1 + RQ * brev5(lane))];
+    warp_fft_inv<RQ>(v, twl);
+    const RR ra = (RR)a, rb = (RR)b, rc = (RR)c;
+    const int ya = y0 + 2 * wp, yb = ya + 1;
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int e = lane + 32 * r;
+        if (e >= n) continue;
+        if (ya < n) {
+            const long o = ((long)z * n + ya) * n + e;
+            RR q = rb * v[r].x;
+            if (x) q = q + ra * (RR)x[o];
+            if (zv) q = q + rc * (RR)zv[o];
+            out[o] = out_cast<RI>(q);
+        }
+        if (yb < n) {
+            const long o = ((long)z * n + yb) * n + e;
+            RR q = rb * v[r].y;
+            if (x) q = q + ra * (RR)x[o];
+            if (zv) q = q + rc * (RR)zv[o];
+            out[o] = out_cast<RI>(q);
+        }
+    }
+}
+
+template <int RQ, typename T, typename R, typename TS>
+static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, double a, double b, double c,
+                                 const R* z, T* T1, T* T2, const TS* S, const T* tw, cudaStream_t s) {
+    constexpr int Q = 32 * RQ;
+    static bool once = false;
+    cudaError_t e;
+    const size_t smx = (size_t)(Q + 8 * (Q + 2)) * sizeof(T);
+    const size_t smy = (size_t)(Q + Q * 17) * sizeof(T);
+    if (!once) {
+        if ((e = cudaFuncSetAttribute(k3w_x_fwd<RQ, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k3w_x_inv<RQ, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k3w_y_fwd<RQ, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k3w_y_inv<RQ, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
+            cudaSuccess)
+            return e;
+        once = true;
+    }
+    const unsigned gy = (unsigned)((n + 15) / 16);
+    k3w_x_fwd<RQ, T, R><<<dim3(gy, n), 256, smx, s>>>(x, T1, tw, n, H, w);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k3w_y_fwd<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T1, T2, tw, n, H);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long nlines = (long)H * Q;
+    k3w_z_mix<RQ, T, TS><<<(unsigned)((nlines + 7) / 8), 256, 0, s>>>(T2, S, tw, n, H, nlines);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k3w_y_inv<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T2, T1, tw, n, H);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k3w_x_inv<RQ, T, R><<<dim3(gy, n), 256, smx, s>>>(T1, x, z, out, tw, n, H, a, b, c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    rte_count_launches(5);
+    return cudaSuccess;
+}
+
 template <typename K> static cudaError_t allow(K k) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, RTE_SMEM_OPTIN);
 }
@@ -256,6 +497,16 @@ static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, 
         if ((e = allow(k3_y_inv<T>)) != cudaSuccess) return e;
         if ((e = allow(k3_x_inv<T, R>)) != cudaSuccess) return e;
         once = true;
+    }
+    if constexpr (!std::is_same<T, double2>::value) {
+        // FP32 and float-float: warp-register passes when Q = 32 * 2^j
+        switch (p->Q) {
+            case 64: return op3d_run_warp<2>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
+            case 128: return op3d_run_warp<4>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
+            case 256: return op3d_run_warp<8>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
+            case 512: return op3d_run_warp<16>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
+            default: break;
+        }
     }
     P3 pp;
     pp.n = p->n;

@@ -70,6 +70,30 @@ def test_apply_K32_3d(n):
     p.close()
 
 
+# q = 64, 128, 256, 512: the warp-register passes (FP32 and float-float) with
+# 2, 4, 8, 16 registers per lane; n ragged against their 16-row / 16-z blocks
+@pytest.mark.parametrize("n,q", [(12, 64), (20, 128), (24, 256), (9, 512)])
+def test_apply_K_3d_warp_passes(n, q):
+    mu_t, mu_s = 10.0, 9.0
+    p = _plan(n, mu_t, mu_s, prec="mixed_fp32", q_policy=q)
+    assert p.Q == q
+    x = np.random.default_rng(n).standard_normal((n, n, n))
+    x32 = x.astype(np.float32)
+    y32 = p.apply_K32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert rel(y32, oracle.apply_K_3d(n, 1.0 / n, mu_t, mu_s, x32.astype(np.float64))) < 1e-5
+    ref = oracle.apply_K_3d(n, 1.0 / n, mu_t, mu_s, x)
+    ye = p.apply_K64e(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(ye, ref) < 1e-12
+    # mixed solve: float-float RHS and residuals, FP32 inner passes
+    f = rte_synth.gaussian_3d(n, (0.45, 0.5, 0.55), 0.15)
+    u, st = p.solve(torch.from_numpy(f), tol=1e-10)
+    assert st["converged"] and st["relres_true"] <= 1e-10
+    rows = np.random.default_rng(7).choice(n ** 3, size=32, replace=False)
+    r, b = oracle.sampled_residual_3d(n, 1.0 / n, mu_t, mu_s, f, u.cpu().numpy(), rows)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
+    p.close()
+
+
 def test_apply_K_3d_full_size_sampled():
     """128^3 (zero padded to 256^3), mu_t = 100, mu_s = 99.5: FP64 K x against
     the oracle's direct sum at sampled cells."""
