@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__
                                                       float2* __restrict__ out, const float2* __restrict__ tw,
                                                       RowParams p) {
     constexpr int Q = 32 * R;
-    constexpr int LS = Q + 2;  // line stride: consecutive lines start 2 bank pairs apart
+    // line stride: holds the FFT scratch (Q + 32), consecutive lines 2 bank pairs apart
+    constexpr int LS = Q + 34;
     extern __shared__ unsigned char smraw[];
     float2* twl = reinterpret_cast<float2*>(smraw);
     float2* Z = twl + Q;
@@ -236,9 +237,9 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__
         }
         v[r] = val;
     }
-    warp_fft_fwd<R>(v, twl);
+    warp_fft_fwd<R>(v, twl, Z + w * LS);  // the line doubles as the FFT scratch
 #pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) Z[w * LS + swz16(k1 + R * brev5(lane))] = v[k1];
+    for (int j = 0; j < R; ++j) Z[w * LS + swz16(wfreq<R>(j, lane))] = v[j];
     __syncthreads();
     // split Z = F + i G into the half spectra (as in k_row_fwd)
     for (int idx = threadIdx.x; idx < H * rows; idx += blockDim.x) {
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__
                                                       const float2* __restrict__ tw, RowParams p, float a, float b,
                                                       float c) {
     constexpr int Q = 32 * R;
-    constexpr int LS = Q + 2;
+    constexpr int LS = Q + 34;
     extern __shared__ unsigned char smraw[];
     float2* twl = reinterpret_cast<float2*>(smraw);
     float2* Z = twl + Q;
@@ -297,8 +298,9 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2 v[R];
 #pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) v[k1] = Z[w * LS + swz16(k1 + R * brev5(lane))];
-    warp_fft_inv<R>(v, twl);
+    for (int j = 0; j < R; ++j) v[j] = Z[w * LS + swz16(wfreq<R>(j, lane))];
+    __syncwarp();
+    warp_fft_inv<R>(v, twl, Z + w * LS);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int e = lane + 32 * r;
@@ -671,7 +673,7 @@ __global__ void k_mix_pointwise(T* __restrict__ Ts, const TS* __restrict__ S, Co
 // column pass with the warp-register FFT (FP32, Q = 32 R, R = 2..16): one
 // block per xi_x, each warp transforms whole channel columns.  Spectra of
 // all channels meet in shared memory in the slot layout s = k1 * 32 + lane
-// (frequency xi_y = k1 + R brev5(lane)), the same layout the plan stores the
+// (frequency xi_y = wfreq<R>(k1, lane)), the same layout the plan stores the
 // permuted spectra Sp[xi_x][m][s] in; the inverse starts from that layout.
 // ---------------------------------------------------------------------------
 template <int L, int R, typename TS>
@@ -682,10 +684,11 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
     extern __shared__ unsigned char smraw[];
     float2* twl = reinterpret_cast<float2*>(smraw);
     float2* X = twl + Q;  // [NCH][Q] in slot layout
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    __syncthreads();
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    float2* scr = X + (long)NCH * Q + (long)warp * wfft_shape<R>::SCRATCH;  // this warp's FFT scratch
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    __syncthreads();
     for (int c = warp; c < nin; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;
@@ -694,7 +697,7 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
             const int y = lane + 32 * r;
             v[r] = y < n ? col[y] : make_float2(0.f, 0.f);
         }
-        warp_fft_fwd<R>(v, twl);
+        warp_fft_fwd<R>(v, twl, scr);
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) X[(long)c * Q + k1 * 32 + lane] = v[k1];
     }
@@ -724,7 +727,7 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
         float2 v[R];
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) v[k1] = X[(long)c * Q + k1 * 32 + lane];
-        warp_fft_inv<R>(v, twl);
+        warp_fft_inv<R>(v, twl, scr);
         float2* col = Tb + ((long)c * H + kx) * n;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -740,11 +743,14 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
 // The forward leaves the spectrum in the slot order (s = k1 * 32 + lane) in
 // Ts [line][Q]; the pointwise mode mix then runs on the slot-ordered spectra
 // Sp, and the inverse starts from that order.
+// dynamic shared memory: the twiddle table (Q) and 8 warps' FFT scratch
 template <int R>
 __global__ void __launch_bounds__(256) k_colw_fwd(const ffc* __restrict__ Tb, ffc* __restrict__ Ts,
                                                   const ffc* __restrict__ tw, int n, int nlines) {
     constexpr int Q = 32 * R;
-    __shared__ ffc twl[Q];
+    extern __shared__ unsigned char smraw[];
+    ffc* twl = reinterpret_cast<ffc*>(smraw);
+    ffc* scr = twl + Q + (threadIdx.x >> 5) * wfft_shape<R>::SCRATCH;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     __syncthreads();
     const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -757,7 +763,7 @@ __global__ void __launch_bounds__(256) k_colw_fwd(const ffc* __restrict__ Tb, ff
         const int y = lane + 32 * r;
         v[r] = y < n ? col[y] : mk<ffc>(0, 0);
     }
-    warp_fft_fwd<R>(v, twl);
+    warp_fft_fwd<R>(v, twl, scr);
     ffc* o = Ts + (long)line * Q;
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) o[k1 * 32 + lane] = v[k1];
@@ -767,7 +773,9 @@ template <int R>
 __global__ void __launch_bounds__(256) k_colw_inv(ffc* __restrict__ Tb, const ffc* __restrict__ Ts,
                                                   const ffc* __restrict__ tw, int n, int nlines) {
     constexpr int Q = 32 * R;
-    __shared__ ffc twl[Q];
+    extern __shared__ unsigned char smraw[];
+    ffc* twl = reinterpret_cast<ffc*>(smraw);
+    ffc* scr = twl + Q + (threadIdx.x >> 5) * wfft_shape<R>::SCRATCH;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     __syncthreads();
     const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -777,7 +785,7 @@ __global__ void __launch_bounds__(256) k_colw_inv(ffc* __restrict__ Tb, const ff
     ffc v[R];
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) v[k1] = in[k1 * 32 + lane];
-    warp_fft_inv<R>(v, twl);
+    warp_fft_inv<R>(v, twl, scr);
     ffc* col = Tb + (long)line * n;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -786,7 +794,7 @@ __global__ void __launch_bounds__(256) k_colw_inv(ffc* __restrict__ Tb, const ff
     }
 }
 
-// Sp[xi_x][m][k1 * 32 + lane] = S[xi_x][m][k1 + R brev5(lane)]
+// Sp[xi_x][m][k1 * 32 + lane] = S[xi_x][m][wfreq(k1, lane)]
 template <typename TS>
 __global__ void k_permute_spec(const TS* __restrict__ S, TS* __restrict__ Sp, long rows, int Q) {
     const int R = Q / 32;
@@ -795,6 +803,6 @@ __global__ void k_permute_spec(const TS* __restrict__ S, TS* __restrict__ Sp, lo
         const long row = i / Q;
         const int sl = (int)(i % Q);
         const int k1 = sl >> 5, lane = sl & 31;
-        Sp[i] = S[row * Q + k1 + R * brev5(lane)];
+        Sp[i] = S[row * Q + wfreq_rt(R, k1, lane)];
     }
 }

@@ -92,7 +92,7 @@ static cudaError_t launch_col_warp(float2* Tb, const TS* Sp, const float2* tw, c
     static bool once = false;
     cudaError_t e;
     if (!once) { e = allow_smem(k_col_warp<L, R, TS>); if (e != cudaSuccess) return e; once = true; }
-    const size_t smem = (size_t)(32 * R) * sizeof(float2) * (1 + 2 * L + 1);
+    const size_t smem = ((size_t)(32 * R) * (1 + 2 * L + 1) + 8 * wfft_shape<R>::SCRATCH) * sizeof(float2);
     k_col_warp<L, R, TS><<<cp.H, 256, smem, s>>>(Tb, Sp, tw, cp.n, cp.H, cp.nin);
     return cudaGetLastError();
 }
@@ -152,21 +152,32 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
                            cudaStream_t s) {
     const int lin = cp.nin * cp.H, lout = (2 * L + 1) * cp.H;
     const unsigned gin = (unsigned)((lin + 7) / 8), gout = (unsigned)((lout + 7) / 8);
+    const size_t sm = (size_t)(cp.Q + 8 * (cp.Q + 32)) * sizeof(ffc);  // twiddles + 8 FFT scratches
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_colw_fwd<2>)) != cudaSuccess || (e = allow_smem(k_colw_fwd<4>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_fwd<8>)) != cudaSuccess || (e = allow_smem(k_colw_fwd<16>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_inv<2>)) != cudaSuccess || (e = allow_smem(k_colw_inv<4>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_inv<8>)) != cudaSuccess || (e = allow_smem(k_colw_inv<16>)) != cudaSuccess)
+            return e;
+        once = true;
+    }
     switch (cp.Q) {
-        case 64: k_colw_fwd<2><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
-        case 128: k_colw_fwd<4><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
-        case 256: k_colw_fwd<8><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
-        case 512: k_colw_fwd<16><<<gin, 256, 0, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 64: k_colw_fwd<2><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 128: k_colw_fwd<4><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 256: k_colw_fwd<8><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 512: k_colw_fwd<16><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         default: return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = launch_mix_ff(L, Ts, Sp, cp, s)) != cudaSuccess) return e;
     switch (cp.Q) {
-        case 64: k_colw_inv<2><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
-        case 128: k_colw_inv<4><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
-        case 256: k_colw_inv<8><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
-        case 512: k_colw_inv<16><<<gout, 256, 0, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 64: k_colw_inv<2><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 128: k_colw_inv<4><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 256: k_colw_inv<8><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 512: k_colw_inv<16><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
     }
     return cudaGetLastError();
 }
@@ -174,7 +185,7 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
 // warp-register row passes (FP32 fields and compute, Q in {64, 128, 256, 512})
 template <typename T, typename TF> struct row_warp_types { static constexpr bool value = false; };
 template <> struct row_warp_types<float2, float2> { static constexpr bool value = true; };
-static inline size_t row_warp_smem(int Q) { return (size_t)(Q + 8 * (Q + 2)) * sizeof(float2); }
+static inline size_t row_warp_smem(int Q) { return (size_t)(Q + 8 * (Q + 34)) * sizeof(float2); }
 
 static cudaError_t row_fwd_warp(int Q, dim3 grid, const float2* x, const double* f, float2* out, const float2* tw,
                                 const RowParams& rp, cudaStream_t s) {

@@ -128,43 +128,6 @@ __global__ void __launch_bounds__(256) k3_z_mix(T* __restrict__ T2, const TS* __
     }
 }
 
-// Z with the warp-register FFT (FP32, Q = 32 R): one warp per (xi_x, xi_y)
-// line, 8 lines per block; the spectrum multiply happens in the forward
-// transform's output layout, so the inverse follows with no data movement.
-template <int R>
-__global__ void __launch_bounds__(256) k3_z_mix_warp(float2* __restrict__ T2, const float* __restrict__ S,
-                                                     const float2* __restrict__ tw, int n, int H, long nlines) {
-    constexpr int Q = 32 * R;
-    __shared__ float2 twl[Q];
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (line >= nlines) return;
-    float2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int z = lane + 32 * r;
-        v[r] = z < n ? T2[line * n + z] : make_float2(0.f, 0.f);
-    }
-    warp_fft_fwd<R>(v, twl);
-    const int kx = (int)(line / Q), ky = (int)(line % Q);
-    const float* Srow = S + ((long)kx * H + fold(ky, Q)) * H;
-    const int k2 = brev5(lane);
-#pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) {
-        const float sv = Srow[fold(k1 + R * k2, Q)];
-        v[k1].x *= sv;
-        v[k1].y *= sv;
-    }
-    warp_fft_inv<R>(v, twl);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int z = lane + 32 * r;
-        if (z < n) T2[line * n + z] = v[r];
-    }
-}
-
 // Y': T2[xi_x][xi_y][z] -> T1[z][xi_x][y], y < n; grid (ceil(n/B), H)
 template <typename T>
 __global__ void __launch_bounds__(256) k3_y_inv(const T* __restrict__ T2, T* __restrict__ T1, const T* __restrict__ tw,
@@ -241,8 +204,8 @@ __global__ void __launch_bounds__(256) k3_x_inv(const T* __restrict__ T1, const 
 //   X  : 8 warps per block = 16 rows of one z plane (packed pairs), split
 //        through a swizzled shared line buffer     -> T1[z][xi_x][y]
 //   Y  : 16 warps per block = 16 consecutive z of one xi_x; the spectrum is
-//        written in the FFT's slot order s = k1*32 + lane (xi_y = k1 + RQ
-//        brev5(lane)) through a shared [s][z] tile -> T2[xi_x][s][z]
+//        written in the FFT's slot order s = j*32 + lane (xi_y =
+//        wfreq<RQ>(j, lane)) through a shared [s][z] tile -> T2[xi_x][s][z]
 //   Z  : per (xi_x, s) line: FFT, * S, iFFT in registers (in place)
 //   Y' : reads the slot order back into the inverse  -> T1[z][xi_x][y]
 //   X' : Hermitian rebuild, inverse FFT, epilogue in the compute type.
@@ -252,7 +215,7 @@ template <typename RO, typename RR> __device__ __forceinline__ RO out_cast(RR v)
 template <int RQ, typename T, typename RI>
 __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __restrict__ T1,
                                                  const T* __restrict__ tw, int n, int H, double w) {
-    constexpr int Q = 32 * RQ, LS = Q + 2;
+    constexpr int Q = 32 * RQ, LS = Q + 34;  // a line also holds the warp's FFT scratch (Q + 32)
     using RR = typename real_of<T>::R;
     extern __shared__ unsigned char smraw[];
     T* twl = reinterpret_cast<T*>(smraw);
@@ -274,9 +237,9 @@ __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __
         }
         v[r] = mk<T>(ww * a, ww * b);
     }
-    warp_fft_fwd<RQ>(v, twl);
+    warp_fft_fwd<RQ>(v, twl, Z + wp * LS);
 #pragma unroll
-    for (int k1 = 0; k1 < RQ; ++k1) Z[wp * LS + swz16(k1 + RQ * brev5(lane))] = v[k1];
+    for (int j = 0; j < RQ; ++j) Z[wp * LS + swz16(wfreq<RQ>(j, lane))] = v[j];
     __syncthreads();
     for (int idx = threadIdx.x; idx < H * 16; idx += blockDim.x) {
         const int r = idx & 15, xi = idx >> 4;
@@ -298,7 +261,7 @@ __global__ void __launch_bounds__(512) k3w_y_fwd(const T* __restrict__ T1, T* __
     constexpr int Q = 32 * RQ, ZS = 17;
     extern __shared__ unsigned char smraw[];
     T* twl = reinterpret_cast<T*>(smraw);
-    T* Y = twl + Q;  // [s][ZS]
+    T* Y = twl + Q;  // [s][ZS] tile; before it is written, the 16 warps' FFT scratch
     const int kx = blockIdx.y, z0 = blockIdx.x * 16;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     __syncthreads();
@@ -310,7 +273,8 @@ __global__ void __launch_bounds__(512) k3w_y_fwd(const T* __restrict__ T1, T* __
         const int y = lane + 32 * r;
         v[r] = (z < n && y < n) ? T1[((long)z * H + kx) * n + y] : mk<T>(0, 0);
     }
-    warp_fft_fwd<RQ>(v, twl);
+    warp_fft_fwd<RQ>(v, twl, Y + wp * wfft_shape<RQ>::SCRATCH);
+    __syncthreads();  // every warp is done with its scratch
 #pragma unroll
     for (int k1 = 0; k1 < RQ; ++k1) Y[(k1 * 32 + lane) * ZS + wp] = v[k1];
     __syncthreads();
@@ -326,10 +290,12 @@ __global__ void __launch_bounds__(256) k3w_z_mix(T* __restrict__ T2, const TS* _
                                                  const T* __restrict__ tw, int n, int H, long nlines) {
     constexpr int Q = 32 * RQ;
     using RR = typename real_of<T>::R;
-    __shared__ T twl[Q];
+    extern __shared__ unsigned char smraw[];
+    T* twl = reinterpret_cast<T*>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* scr = twl + Q + warp * wfft_shape<RQ>::SCRATCH;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (line >= nlines) return;
     T v[RQ];
@@ -338,17 +304,16 @@ __global__ void __launch_bounds__(256) k3w_z_mix(T* __restrict__ T2, const TS* _
         const int z = lane + 32 * r;
         v[r] = z < n ? T2[line * n + z] : mk<T>(0, 0);
     }
-    warp_fft_fwd<RQ>(v, twl);
+    warp_fft_fwd<RQ>(v, twl, scr);
     const int kx = (int)(line / Q), sl = (int)(line % Q);
-    const int ky = (sl >> 5) + RQ * brev5(sl & 31);  // slot -> frequency
+    const int ky = wfreq<RQ>(sl >> 5, sl & 31);  // slot -> frequency
     const TS* Srow = S + ((long)kx * H + fold(ky, Q)) * H;
-    const int k2 = brev5(lane);
 #pragma unroll
-    for (int k1 = 0; k1 < RQ; ++k1) {
-        const RR sv = (RR)Srow[fold(k1 + RQ * k2, Q)];
-        v[k1] = mk<T>(v[k1].x * sv, v[k1].y * sv);
+    for (int j = 0; j < RQ; ++j) {
+        const RR sv = (RR)Srow[fold(wfreq<RQ>(j, lane), Q)];
+        v[j] = mk<T>(v[j].x * sv, v[j].y * sv);
     }
-    warp_fft_inv<RQ>(v, twl);
+    warp_fft_inv<RQ>(v, twl, scr);
 #pragma unroll
     for (int r = 0; r < RQ; ++r) {
         const int z = lane + 32 * r;
@@ -362,7 +327,7 @@ __global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __
     constexpr int Q = 32 * RQ, ZS = 17;
     extern __shared__ unsigned char smraw[];
     T* twl = reinterpret_cast<T*>(smraw);
-    T* Y = twl + Q;  // [s][ZS]
+    T* Y = twl + Q;  // [s][ZS] tile, then the 16 warps' FFT scratch
     const int kx = blockIdx.y, z0 = blockIdx.x * 16;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     const int nz = min(16, n - z0);
@@ -375,7 +340,8 @@ __global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __
     T v[RQ];
 #pragma unroll
     for (int k1 = 0; k1 < RQ; ++k1) v[k1] = Y[(k1 * 32 + lane) * ZS + wp];
-    warp_fft_inv<RQ>(v, twl);
+    __syncthreads();  // the tile is read; its space becomes the warps' FFT scratch
+    warp_fft_inv<RQ>(v, twl, Y + wp * wfft_shape<RQ>::SCRATCH);
     const int z = z0 + wp;
     if (z >= n) return;
 #pragma unroll
@@ -390,7 +356,7 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
                                                  const RI* __restrict__ zv, RI* __restrict__ out,
                                                  const T* __restrict__ tw, int n, int H, double a, double b,
                                                  double c) {
-    constexpr int Q = 32 * RQ, LS = Q + 2;
+    constexpr int Q = 32 * RQ, LS = Q + 34;
     using RR = typename real_of<T>::R;
     extern __shared__ unsigned char smraw[];
     T* twl = reinterpret_cast<T*>(smraw);
@@ -410,8 +376,9 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T v[RQ];
 #pragma unroll
-    for (int k1 = 0; k1 < RQ; ++k1) v[k1] = Z[wp * LS + swz16(k1 + RQ * brev5(lane))];
-    warp_fft_inv<RQ>(v, twl);
+    for (int j = 0; j < RQ; ++j) v[j] = Z[wp * LS + swz16(wfreq<RQ>(j, lane))];
+    __syncwarp();
+    warp_fft_inv<RQ>(v, twl, Z + wp * LS);
     const RR ra = (RR)a, rb = (RR)b, rc = (RR)c;
     const int ya = y0 + 2 * wp, yb = ya + 1;
 #pragma unroll
@@ -441,8 +408,10 @@ static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, dou
     constexpr int Q = 32 * RQ;
     static bool once = false;
     cudaError_t e;
-    const size_t smx = (size_t)(Q + 8 * (Q + 2)) * sizeof(T);
-    const size_t smy = (size_t)(Q + Q * 17) * sizeof(T);
+    using W = wfft_shape<RQ>;
+    const size_t smx = (size_t)(Q + 8 * (Q + 34)) * sizeof(T);
+    const size_t smy = (size_t)(Q + (Q * 17 > 16 * W::SCRATCH ? Q * 17 : 16 * W::SCRATCH)) * sizeof(T);
+    const size_t smz = (size_t)(Q + 8 * W::SCRATCH) * sizeof(T);
     if (!once) {
         if ((e = cudaFuncSetAttribute(k3w_x_fwd<RQ, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) !=
             cudaSuccess)
@@ -456,6 +425,9 @@ static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, dou
         if ((e = cudaFuncSetAttribute(k3w_y_inv<RQ, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) !=
             cudaSuccess)
             return e;
+        if ((e = cudaFuncSetAttribute(k3w_z_mix<RQ, T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smz)) != cudaSuccess)
+            return e;
         once = true;
     }
     const unsigned gy = (unsigned)((n + 15) / 16);
@@ -464,7 +436,7 @@ static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, dou
     k3w_y_fwd<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T1, T2, tw, n, H);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const long nlines = (long)H * Q;
-    k3w_z_mix<RQ, T, TS><<<(unsigned)((nlines + 7) / 8), 256, 0, s>>>(T2, S, tw, n, H, nlines);
+    k3w_z_mix<RQ, T, TS><<<(unsigned)((nlines + 7) / 8), 256, smz, s>>>(T2, S, tw, n, H, nlines);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k3w_y_inv<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T2, T1, tw, n, H);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -523,19 +495,7 @@ static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, 
     k3_y_fwd<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T1, T2, tw, pp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const long nlines = (long)H * Q;
-    if constexpr (sizeof(T) == sizeof(float2) && sizeof(TS) == sizeof(float)) {
-        if (Q == 64 || Q == 128 || Q == 256 || Q == 512) {
-            const unsigned nb = (unsigned)((nlines + 7) / 8);
-            if (Q == 64) k3_z_mix_warp<2><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
-            if (Q == 128) k3_z_mix_warp<4><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
-            if (Q == 256) k3_z_mix_warp<8><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
-            if (Q == 512) k3_z_mix_warp<16><<<nb, 256, 0, s>>>((float2*)T2, (const float*)S, (const float2*)tw, n, H, nlines);
-        } else {
-            k3_z_mix<T, TS><<<(unsigned)((nlines + B - 1) / B), 256, smy, s>>>(T2, S, tw, pp);
-        }
-    } else {
-        k3_z_mix<T, TS><<<(unsigned)((nlines + B - 1) / B), 256, smy, s>>>(T2, S, tw, pp);
-    }
+    k3_z_mix<T, TS><<<(unsigned)((nlines + B - 1) / B), 256, smy, s>>>(T2, S, tw, pp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k3_y_inv<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T2, T1, tw, pp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

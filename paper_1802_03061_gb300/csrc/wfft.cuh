@@ -1,26 +1,31 @@
-// Warp-register FFT of length Q = 32 R (R = 2, 4, 8, 16): one warp per line,
-// no shared memory traffic and no block barriers inside the transform.
+// Warp FFT of length Q = 32 R (R = 2, 4, 8, 16): one warp per line, the data
+// in registers, one transpose through a per-warp shared scratch.
 //
 // Lane l, register r holds x[l + 32 r] (coalesced loads).  With
-// k = k1 + R k2:   X[k] = sum_l W32^{l k2} W_Q^{l k1} (sum_r x[l + 32 r] W_R^{r k1})
-// so the forward transform is an R-point DFT in registers, a twiddle
-// W_Q^{l k1}, and a 32-point decimation-in-frequency DFT across the lanes
-// (butterflies with __shfl_xor_sync).  The result sits at lane l, register
-// k1 as X[k1 + R brev5(l)].  The inverse takes exactly that layout: a
-// 32-point decimation-in-time DFT across lanes (the mirror of the forward),
-// the conjugate twiddle, then the R-point inverse DFT in registers, and
-// returns x in the natural (l + 32 r) layout -- so a fused
-// FFT -> pointwise -> inverse FFT moves no data between its halves.
+// xi = k1 + R kappa (k1 < R, kappa < 32) and n = l + 32 r,
+//   X[xi] = sum_l W32^{l kappa} [ W_Q^{l k1} sum_r x[l + 32 r] W_R^{r k1} ],
+// i.e. an R-point DFT in registers and a twiddle (step 1), then 32-point DFTs
+// over l, one per k1 (step 2).  Step 2 does not run over five cross-lane
+// stages: the R x 32 block is transposed through shared memory so that the
+// P = 32/R lanes L = P k1 + b (b < P) share the DFT of k1, lane b holding the
+// inputs l = P m + b (m < R).  Splitting kappa = kappa' + R c (kappa' < R,
+// c < P),
+//   X[k1 + R (kappa' + R c)] = sum_b W_P^{b c} W32^{b kappa'} DFT_R[m](Y[P m + b])[kappa'],
+// so each lane does a second R-point DFT in registers and a twiddle, and the
+// P lanes finish with log2(P) decimation-in-frequency radix-2 stages
+// (__shfl_xor_sync).  Lane L = P k1 + b, register j then holds
+// X[k1 + R (j + R brev(b))] (brev over log2 P bits; wfreq below).  The
+// inverse mirrors every step and returns x in the natural (l + 32 r) layout,
+// so a fused FFT -> pointwise -> inverse FFT needs no reordering.  Counted in
+// instructions this is about half of a transform with five lane stages.
 #pragma once
 #include "fft.cuh"
 
-__device__ __forceinline__ int brev5(int l) { return __brev(l) >> 27; }
-
 // bank swizzle of a line of Q (a multiple of 16) complex values in shared
 // memory: xi -> xi ^ ((xi >> 4) & 15) stays inside its aligned group of 16,
-// so it is a bijection; the 32 lanes of a warp that store one register
-// (frequencies k1 + R brev5(lane), equal low bits) land on 16 distinct bank
-// pairs instead of one
+// so it is a bijection; it spreads the frequencies that the 32 lanes of a
+// warp hold in one register (which differ mostly in their high bits) over
+// the banks
 __device__ __forceinline__ int swz16(int xi) { return xi ^ ((xi >> 4) & 15); }
 
 template <int DIR, typename T> __device__ __forceinline__ void dft16(T* v) {
@@ -115,38 +120,69 @@ template <int R, typename T> __device__ __forceinline__ void lane_stage_inv(T* v
         v[k1] = cadd(a, upper ? cneg(m) : m);
     }
 }
-// wide types (float-float) keep the five lane stages rolled: unrolled, the
-// transform outgrows the instruction cache
-template <typename T> struct roll_lane_stages { static constexpr bool value = sizeof(T) > 8; };
 
-// forward: v[r] = x[lane + 32 r]  ->  v[k1] = X[k1 + R brev5(lane)]
-// tw: table exp(-2 pi i t / Q), Q = 32 R
-template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, const T* tw) {
-    constexpr int Q = 32 * R;
+template <int R> struct wfft_shape {
+    static constexpr int Q = 32 * R;
+    static constexpr int P = 32 / R;                            // lanes per 32-point DFT in step 2
+    static constexpr int LP = R == 16 ? 1 : R == 8 ? 2 : R == 4 ? 3 : 4;  // log2 P
+    static constexpr int ST = 32 + P;                           // scratch row stride (bank spread)
+    static constexpr int SCRATCH = R * ST;                      // scratch elements per warp (Q + 32)
+};
+
+// frequency held by register j of lane L after the forward transform
+template <int R> __device__ __forceinline__ int wfreq(int j, int lane) {
+    using W = wfft_shape<R>;
+    const int b = lane & (W::P - 1);
+    const int c = (int)(__brev((unsigned)b) >> (32 - W::LP));
+    return (lane >> W::LP) + R * (j + R * c);
+}
+// the same with R known at run time (plan-time permutations)
+__device__ __forceinline__ int wfreq_rt(int R, int j, int lane) {
+    const int P = 32 / R, LP = __ffs(P) - 1;
+    const int b = lane & (P - 1);
+    const int c = (int)(__brev((unsigned)b) >> (32 - LP));
+    return (lane >> LP) + R * (j + R * c);
+}
+
+// forward: v[r] = x[lane + 32 r]  ->  v[j] = X[wfreq<R>(j, lane)]
+// tw: table exp(-2 pi i t / Q); S: this warp's scratch (wfft_shape<R>::SCRATCH
+// elements of shared memory)
+template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, const T* tw, T* S) {
+    using W = wfft_shape<R>;
     const int lane = threadIdx.x & 31;
     dft_regs<R, -1>(v);
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<-1>(tw, lane * k1));
-    if constexpr (roll_lane_stages<T>::value) {
-#pragma unroll 1
-        for (int h = 16; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
-    } else {
 #pragma unroll
-        for (int h = 16; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
-    }
-    (void)Q;
+    for (int k1 = 0; k1 < R; ++k1) S[k1 * W::ST + lane] = v[k1];
+    __syncwarp();
+    const int g = lane >> W::LP, b = lane & (W::P - 1);
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = S[g * W::ST + W::P * m + b];
+    __syncwarp();
+    dft_regs<R, -1>(v);
+#pragma unroll
+    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], twid<-1>(tw, b * j * R));
+#pragma unroll
+    for (int h = W::P / 2; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
 }
 
-// inverse (unnormalised): v[k1] = X[k1 + R brev5(lane)]  ->  v[r] = Q x[lane + 32 r]
-template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, const T* tw) {
+// inverse (unnormalised): v[j] = X[wfreq<R>(j, lane)]  ->  v[r] = Q x[lane + 32 r]
+template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, const T* tw, T* S) {
+    using W = wfft_shape<R>;
     const int lane = threadIdx.x & 31;
-    if constexpr (roll_lane_stages<T>::value) {
-#pragma unroll 1
-        for (int h = 1; h <= 16; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
-    } else {
 #pragma unroll
-        for (int h = 1; h <= 16; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
-    }
+    for (int h = 1; h <= W::P / 2; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
+    const int g = lane >> W::LP, b = lane & (W::P - 1);
+#pragma unroll
+    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], twid<1>(tw, b * j * R));
+    dft_regs<R, 1>(v);
+#pragma unroll
+    for (int m = 0; m < R; ++m) S[g * W::ST + W::P * m + b] = v[m];
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) v[k1] = S[k1 * W::ST + lane];
+    __syncwarp();
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<1>(tw, lane * k1));
     dft_regs<R, 1>(v);
