@@ -364,6 +364,187 @@ __global__ void k_givens(GmresDev* st, cudaGraphConditionalHandle loop) {
 // "Last block" = the block whose atomic increment of the finished counter
 // returns gridDim.x - 1 after a __threadfence(); nothing waits.
 // --------------------------------------------------------------------------
+// Vectorised forms for nr % 4 == 0 (every basis vector then starts on a
+// 16-byte boundary): thread t of a block owns elements [4t, 4t+4) and
+// [1024 + 4t, 1024 + 4t + 4) of the block's TILE, read as float4, and the
+// loop over basis vectors is unrolled by four, so each thread keeps eight
+// 16-byte loads in flight -- enough bytes in flight per SM for the loop to
+// run at HBM speed rather than at load latency.
+__device__ __forceinline__ float4 f4scale(float4 a, float s) {
+    return make_float4(__fmul_rn(a.x, s), __fmul_rn(a.y, s), __fmul_rn(a.z, s), __fmul_rn(a.w, s));
+}
+__device__ __forceinline__ void ff_fma4(float& hi, float& lo, float4 a, const float* b) {
+    ff_fma(hi, lo, a.x, b[0]);
+    ff_fma(hi, lo, a.y, b[1]);
+    ff_fma(hi, lo, a.z, b[2]);
+    ff_fma(hi, lo, a.w, b[3]);
+}
+
+__global__ void __launch_bounds__(256) k_step_dot4(float* __restrict__ V, long nr, const float* __restrict__ w,
+                                                   GmresDev* __restrict__ st, long nw1, double* __restrict__ part) {
+    const int j = st->j, count = j + 1;
+    const float s = (float)st->vscale;
+    const bool rescale = s != 1.f;
+    const int nb = gridDim.x;
+    __shared__ double red[GM_MMAX + 1][8];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long e0 = (long)blockIdx.x * TILE + 4 * threadIdx.x, e1 = e0 + 1024;
+    const bool in0 = e0 < nr, in1 = e1 < nr;
+    float wv[8];
+    {
+        const float4 a = in0 ? *reinterpret_cast<const float4*>(w + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = in1 ? *reinterpret_cast<const float4*>(w + e1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float av[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long e = (q < 4 ? e0 : e1) + (q & 3);
+            wv[q] = __fmul_rn(s, av[q]) * (e < nw1 ? 1.f : 2.f);
+        }
+    }
+    for (int i0 = 0; i0 < count; i0 += 4) {
+        float4 va[4], vb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k;
+            const float* v = V + (long)i * nr;
+            va[k] = (i < count && in0) ? *reinterpret_cast<const float4*>(v + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            vb[k] = (i < count && in1) ? *reinterpret_cast<const float4*>(v + e1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float hi[4], lo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k;
+            if (i == j && rescale) {
+                float* v = V + (long)i * nr;
+                va[k] = f4scale(va[k], s);
+                vb[k] = f4scale(vb[k], s);
+                if (in0) *reinterpret_cast<float4*>(v + e0) = va[k];
+                if (in1) *reinterpret_cast<float4*>(v + e1) = vb[k];
+            }
+            hi[k] = 0.f;
+            lo[k] = 0.f;
+            ff_fma4(hi[k], lo[k], va[k], wv);
+            ff_fma4(hi[k], lo[k], vb[k], wv + 4);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float bh = __shfl_down_sync(0xffffffffu, hi[k], o);
+                const float bl = __shfl_down_sync(0xffffffffu, lo[k], o);
+                ff_add(hi[k], lo[k], bh, bl);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (i0 + k < count) red[i0 + k][wid] = (double)hi[k] + (double)lo[k];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[i][q];
+        part[(long)i * nb + blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt1, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = wid; i < count; i += 8) {
+        double t = 0.0;
+        for (int b = lane; b < nb; b += 32) t += __ldcg(part + (long)i * nb + b);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) st->hA[i] = t;
+    }
+    if (threadIdx.x == 0) st->cnt1 = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_step_upd4(const float* __restrict__ V, long nr, const float* __restrict__ w,
+                                                   float* __restrict__ vin, GmresDev* __restrict__ st, long nw1,
+                                                   double* __restrict__ part, cudaGraphConditionalHandle loop) {
+    const int j = st->j, count = j + 1;
+    const float s = (float)st->vscale;
+    const int nb = gridDim.x;
+    __shared__ double c[GM_MMAX + 1];
+    __shared__ double red[256];
+    __shared__ bool last;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) c[i] = -st->hA[i];
+    __syncthreads();
+    const long e0 = (long)blockIdx.x * TILE + 4 * threadIdx.x, e1 = e0 + 1024;
+    const bool in0 = e0 < nr, in1 = e1 < nr;
+    float4 a0 = in0 ? f4scale(*reinterpret_cast<const float4*>(w + e0), s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a1 = in1 ? f4scale(*reinterpret_cast<const float4*>(w + e1), s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i0 = 0; i0 < count; i0 += 4) {
+        float4 va[4], vb[4];
+        float ck[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k;
+            const float* v = V + (long)i * nr;
+            const bool ok = i < count;
+            ck[k] = ok ? (float)c[i] : 0.f;
+            va[k] = (ok && in0) ? *reinterpret_cast<const float4*>(v + e0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            vb[k] = (ok && in1) ? *reinterpret_cast<const float4*>(v + e1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a0.x = fmaf(ck[k], va[k].x, a0.x); a0.y = fmaf(ck[k], va[k].y, a0.y);
+            a0.z = fmaf(ck[k], va[k].z, a0.z); a0.w = fmaf(ck[k], va[k].w, a0.w);
+            a1.x = fmaf(ck[k], vb[k].x, a1.x); a1.y = fmaf(ck[k], vb[k].y, a1.y);
+            a1.z = fmaf(ck[k], vb[k].z, a1.z); a1.w = fmaf(ck[k], vb[k].w, a1.w);
+        }
+    }
+    float* vn = const_cast<float*>(V) + (long)(j + 1) * nr;
+    float hi = 0.f, lo = 0.f;
+    if (in0) {
+        *reinterpret_cast<float4*>(vn + e0) = a0;
+        *reinterpret_cast<float4*>(vin + e0) = a0;
+        const float av[4] = {a0.x, a0.y, a0.z, a0.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ff_fma(hi, lo, av[q], av[q] * (e0 + q < nw1 ? 1.f : 2.f));
+    }
+    if (in1) {
+        *reinterpret_cast<float4*>(vn + e1) = a1;
+        *reinterpret_cast<float4*>(vin + e1) = a1;
+        const float bv[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ff_fma(hi, lo, bv[q], bv[q] * (e1 + q < nw1 ? 1.f : 2.f));
+    }
+    ff_warp_sum(hi, lo);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt2, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(part + b);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double nrm = sqrt(red[0]);
+    st->nrm = nrm;
+    st->vscale = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    st->cnt2 = 0u;
+    for (int i = 0; i <= j; ++i) c[i] = st->hA[i];
+    givens_update(st, c, nrm, loop);
+}
+
 __global__ void __launch_bounds__(256) k_step_dot(float* __restrict__ V, long nr, const float* __restrict__ w,
                                                   GmresDev* __restrict__ st, long nw1, double* __restrict__ part) {
     const int j = st->j, count = j + 1;
@@ -704,9 +885,15 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, cudaGraphConditionalHandle l
     const int* jp = &G.st->j;
     if constexpr (sizeof(T) == sizeof(float)) {
         if (!cgs2) {
-            k_step_dot<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
-            k_step_upd<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st, G.nw1,
-                                          G.part, loop);
+            if (nr % 4 == 0) {
+                k_step_dot4<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
+                k_step_upd4<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
+                                               G.nw1, G.part, loop);
+            } else {
+                k_step_dot<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
+                k_step_upd<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
+                                              G.nw1, G.part, loop);
+            }
             rte_count_launches(2);
             RTE_CUDA_TRY(cudaGetLastError());
             return RTE_OK;
