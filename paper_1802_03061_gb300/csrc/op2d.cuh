@@ -400,9 +400,9 @@ __device__ __forceinline__ void mode_mix(const SR& sr, const SI& si, I&& in, O&&
 
 // the mode mix when only A_0 is nonzero (right-hand side K~ g):
 //   Re v_k = P_k A_0,  Im v_k = -i M_k A_0
-template <int L, typename T>
+template <int L, typename T, typename O>
 __device__ __forceinline__ void mode_mix_rhs(const typename real_of<T>::R* sr, const typename real_of<T>::R* si,
-                                             T A0, T* outv) {
+                                             T A0, O&& outv) {
 #pragma unroll
     for (int k = 0; k <= L; ++k) {
         T Ra = mk<T>(0, 0), Ia = mk<T>(0, 0);
@@ -678,17 +678,18 @@ __global__ void k_mix_pointwise(T* __restrict__ Ts, const TS* __restrict__ S, Co
 // ---------------------------------------------------------------------------
 template <int L, int R, typename TS>
 __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const TS* __restrict__ Sp,
-                                                  const float2* __restrict__ tw, int n, int H, int nin) {
+                                                     const float2* __restrict__ tw, int n, int H, int nin) {
     constexpr int NCH = 2 * L + 1;
     constexpr int Q = 32 * R;
+    // channel c occupies QS = Q + 32 slots: its spectrum in slot order, and
+    // while its column is being transformed, the warp's FFT scratch; the
+    // twiddles are read from global memory (L1-resident).  (Three blocks per
+    // SM would need <= 85 registers: the mix then spills and runs slower.)
+    constexpr int QS = wfft_shape<R>::SCRATCH;
     extern __shared__ unsigned char smraw[];
-    float2* twl = reinterpret_cast<float2*>(smraw);
-    float2* X = twl + Q;  // [NCH][Q] in slot layout
+    float2* X = reinterpret_cast<float2*>(smraw);  // [NCH][QS]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    float2* scr = X + (long)NCH * Q + (long)warp * wfft_shape<R>::SCRATCH;  // this warp's FFT scratch
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    __syncthreads();
     for (int c = warp; c < nin; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;
@@ -697,9 +698,10 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
             const int y = lane + 32 * r;
             v[r] = y < n ? col[y] : make_float2(0.f, 0.f);
         }
-        warp_fft_fwd<R>(v, twl, scr);
+        float2* Xc = X + (long)c * QS;
+        warp_fft_fwd<R>(v, tw, Xc);
 #pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) X[(long)c * Q + k1 * 32 + lane] = v[k1];
+        for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
     }
     __syncthreads();
     for (int sl = threadIdx.x; sl < Q; sl += blockDim.x) {
@@ -710,24 +712,24 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
             sr[m] = v.x;
             si[m] = v.y;
         }
-        float2 o[NCH];
+        // every input of this slot is read before any output is written
         if (nin == 1) {
-            mode_mix_rhs<L, float2>(sr, si, X[sl], o);
+            mode_mix_rhs<L, float2>(sr, si, X[sl], Strided<float2>{X + sl, QS});
         } else {
             float2 in[NCH];
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * Q + sl];
-            mode_mix<L, float2>(sr, si, in, o);
+            for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * QS + sl];
+            mode_mix<L, float2>(sr, si, in, Strided<float2>{X + sl, QS});
         }
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) X[(long)c * Q + sl] = o[c];
     }
     __syncthreads();
     for (int c = warp; c < NCH; c += nw) {
         float2 v[R];
+        float2* Xc = X + (long)c * QS;
 #pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) v[k1] = X[(long)c * Q + k1 * 32 + lane];
-        warp_fft_inv<R>(v, twl, scr);
+        for (int k1 = 0; k1 < R; ++k1) v[k1] = Xc[k1 * 32 + lane];
+        __syncwarp();
+        warp_fft_inv<R>(v, tw, Xc);
         float2* col = Tb + ((long)c * H + kx) * n;
 #pragma unroll
         for (int r = 0; r < R; ++r) {

@@ -92,7 +92,7 @@ static cudaError_t launch_col_warp(float2* Tb, const TS* Sp, const float2* tw, c
     static bool once = false;
     cudaError_t e;
     if (!once) { e = allow_smem(k_col_warp<L, R, TS>); if (e != cudaSuccess) return e; once = true; }
-    const size_t smem = ((size_t)(32 * R) * (1 + 2 * L + 1) + 8 * wfft_shape<R>::SCRATCH) * sizeof(float2);
+    const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2);
     k_col_warp<L, R, TS><<<cp.H, 256, smem, s>>>(Tb, Sp, tw, cp.n, cp.H, cp.nin);
     return cudaGetLastError();
 }
