@@ -741,7 +741,9 @@ extern "C" rte_status rte_guess_apply(rte_cnn c, rte_plan p, const double* f_dev
     if (!c || !p || p->dim != 2 || !f_dev || !b_out_dev || !X_scratch_dev || !u0_dev || 2 * p->L + 1 > c->cout)
         return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    rte_status st = plan_apply64(p, MIX_RHS, f_dev, b_out_dev, 0.0, 1.0, 0.0, nullptr, s);
+    // b = K~ g for the features and the guess base: the float-float
+    // application (FP64-accurate, on the FP32 units)
+    rte_status st = plan_apply64e(p, MIX_RHS, f_dev, b_out_dev, 0.0, 1.0, 0.0, nullptr, s);
     if (st != RTE_OK) return st;
     st = rte_guess_features(p, c->cin, f_dev, b_out_dev, X_scratch_dev, stream);
     if (st != RTE_OK) return st;
