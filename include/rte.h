@@ -223,6 +223,16 @@ rte_status rte_cnn_layer(rte_cnn net, int l, int* cin, int* cout, float** w_dev,
                          float** gb_dev);
 /* Refresh the BF16 weight copies after the FP32 weights were written. */
 rte_status rte_cnn_sync_weights(rte_cnn net, void* cuda_stream);
+/* Write the FP32 weights and biases to a file (host path): "RTECNN01", int32
+ * cin, width, depth, cout, then per layer int32 cin_l, cout_l, f32
+ * w[9][cin_l][cout_l], f32 bias[cout_l], host byte order.  Synchronises the
+ * device.  RTE_EINVAL if the file cannot be written. */
+rte_status rte_cnn_save(rte_cnn net, const char* path);
+/* Read a file written by rte_cnn_save into a network of the same shape
+ * (cin, width, depth, cout, per-layer sizes) and refresh the BF16 copies on
+ * cuda_stream.  RTE_EINVAL (network unchanged) if the file is missing,
+ * truncated, or of another shape. */
+rte_status rte_cnn_load(rte_cnn net, const char* path, void* cuda_stream);
 /* Network input (cin channels, 2L+5 <= cin) / training target (cout
  * channels, 2L+1 <= cout) of plan p (2D) from the source f (double [n][n]),
  * b = K~ g and, for targets, the solution u (FP64 mode fields).  The scales

@@ -97,13 +97,15 @@ def lib():
         L.rte_cnn_layer.argtypes = [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP)]
         L.rte_cnn_sync_weights.argtypes = [VP, VP]
+        L.rte_cnn_save.argtypes = [VP, ctypes.c_char_p]
+        L.rte_cnn_load.argtypes = [VP, ctypes.c_char_p, VP]
         L.rte_guess_features.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP]
         L.rte_guess_targets.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP, VP]
         L.rte_guess_apply.argtypes = [VP, VP, VP, VP, VP, VP, VP]
         L.rte_batch_plan.argtypes = [VP, ctypes.c_int, ctypes.POINTER(VP)]
         for name in ("rte_cnn_create", "rte_cnn_destroy", "rte_cnn_forward", "rte_cnn_train_step", "rte_cnn_layer",
-                     "rte_cnn_sync_weights", "rte_guess_features", "rte_guess_targets", "rte_guess_apply",
-                     "rte_batch_plan"):
+                     "rte_cnn_sync_weights", "rte_cnn_save", "rte_cnn_load", "rte_guess_features",
+                     "rte_guess_targets", "rte_guess_apply", "rte_batch_plan"):
             getattr(L, name).restype = ctypes.c_int
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
@@ -298,6 +300,14 @@ def rte_cnn_layer(net, l):
 
 def rte_cnn_sync_weights(net, stream=0):
     _check(lib().rte_cnn_sync_weights(net, VP(stream)), "rte_cnn_sync_weights")
+
+
+def rte_cnn_save(net, path):
+    _check(lib().rte_cnn_save(net, str(path).encode()), "rte_cnn_save")
+
+
+def rte_cnn_load(net, path, stream=0):
+    _check(lib().rte_cnn_load(net, str(path).encode(), VP(stream)), "rte_cnn_load")
 
 
 def rte_guess_features(plan, cin, f, b, X, stream=0):

@@ -695,6 +695,69 @@ extern "C" rte_status rte_cnn_sync_weights(rte_cnn c, void* stream) {
 }
 
 // ---------------------------------------------------------------------------
+// weights file: "RTECNN01", int32 cin, width, depth, cout, then per layer
+// int32 cin_l, cout_l, f32 w[9][cin_l][cout_l], f32 bias[cout_l]
+// (host byte order)
+// ---------------------------------------------------------------------------
+static const char kCnnMagic[8] = {'R', 'T', 'E', 'C', 'N', 'N', '0', '1'};
+
+extern "C" rte_status rte_cnn_save(rte_cnn c, const char* path) {
+    if (!c || !path) return RTE_EINVAL;
+    RTE_CUDA_TRY(cudaDeviceSynchronize());
+    FILE* f = fopen(path, "wb");
+    if (!f) return rte_fail(RTE_EINVAL, "rte_cnn_save: cannot open the file");
+    bool ok = fwrite(kCnnMagic, 1, 8, f) == 8;
+    const int hdr[4] = {c->cin, c->width, c->depth, c->cout};
+    ok = ok && fwrite(hdr, sizeof(int), 4, f) == 4;
+    std::vector<float> buf;
+    for (const CnnLayer& L : c->layers) {
+        if (!ok) break;
+        const int dims[2] = {L.cin, L.cout};
+        ok = fwrite(dims, sizeof(int), 2, f) == 2;
+        const size_t nw = 9ull * L.cin * L.cout;
+        buf.resize(nw + L.cout);
+        if (cudaMemcpy(buf.data(), L.w, nw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(buf.data() + nw, L.bias, L.cout * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(f);
+            return rte_cuda_fail(cudaGetLastError(), "rte_cnn_save");
+        }
+        ok = ok && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    }
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return rte_fail(RTE_EINVAL, "rte_cnn_save: writing the file failed");
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_cnn_load(rte_cnn c, const char* path, void* stream) {
+    if (!c || !path) return RTE_EINVAL;
+    FILE* f = fopen(path, "rb");
+    if (!f) return rte_fail(RTE_EINVAL, "rte_cnn_load: cannot open the file");
+    char magic[8];
+    int hdr[4];
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kCnnMagic, 8) == 0 && fread(hdr, sizeof(int), 4, f) == 4 &&
+              hdr[0] == c->cin && hdr[1] == c->width && hdr[2] == c->depth && hdr[3] == c->cout;
+    std::vector<std::vector<float>> host(c->layers.size());
+    for (size_t l = 0; ok && l < c->layers.size(); ++l) {
+        const CnnLayer& L = c->layers[l];
+        int dims[2];
+        ok = fread(dims, sizeof(int), 2, f) == 2 && dims[0] == L.cin && dims[1] == L.cout;
+        if (!ok) break;
+        host[l].resize(9ull * L.cin * L.cout + L.cout);
+        ok = fread(host[l].data(), sizeof(float), host[l].size(), f) == host[l].size();
+    }
+    fclose(f);
+    if (!ok) return rte_fail(RTE_EINVAL, "rte_cnn_load: not a weights file of this network's shape");
+    // nothing on the device changes unless the whole file was valid
+    for (size_t l = 0; l < c->layers.size(); ++l) {
+        const CnnLayer& L = c->layers[l];
+        const size_t nw = 9ull * L.cin * L.cout;
+        RTE_CUDA_TRY(cudaMemcpy(L.w, host[l].data(), nw * sizeof(float), cudaMemcpyHostToDevice));
+        RTE_CUDA_TRY(cudaMemcpy(L.bias, host[l].data() + nw, L.cout * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return rte_cnn_sync_weights(c, stream);
+}
+
+// ---------------------------------------------------------------------------
 // the learned guess for a plan: u0 = b + s_b * net(features(b, f, params))
 // (scales s_b, fmax computed on the device into the plan's dscal[2..3])
 // ---------------------------------------------------------------------------

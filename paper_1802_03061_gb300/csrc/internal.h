@@ -8,6 +8,8 @@
 #include "common.cuh"
 
 rte_status rte_cuda_fail(cudaError_t e, const char* what);
+// records msg as the last error text and returns st
+rte_status rte_fail(rte_status st, const char* msg);
 // host-side count of kernel launches issued by the library (graph replays
 // add the kernel nodes they contain)
 void rte_count_launches(long k);

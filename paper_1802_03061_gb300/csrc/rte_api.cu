@@ -14,6 +14,11 @@ rte_status rte_cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? RTE_ENOMEM : RTE_ECUDA;
 }
 
+rte_status rte_fail(rte_status st, const char* msg) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    return st;
+}
+
 extern "C" const char* rte_last_error(void) { return g_last_error; }
 
 static long long g_launches = 0;

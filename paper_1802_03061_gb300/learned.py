@@ -98,6 +98,14 @@ class GuessNet:
             _view(d["b"], (d["cout"],)).copy_(torch.from_numpy(np.asarray(st["b%d" % l], np.float32)))
         B.rte_cnn_sync_weights(self.handle)
 
+    def save(self, path):
+        """Weights to a file (library format, rte_cnn_save)."""
+        B.rte_cnn_save(self.handle, path)
+
+    def load(self, path, stream=None):
+        """Weights from a file written by save() for a network of this shape."""
+        B.rte_cnn_load(self.handle, path, _stream_ptr(stream))
+
     def close(self):
         if getattr(self, "handle", None):
             B.rte_cnn_destroy(self.handle)

@@ -105,3 +105,37 @@ def test_training_reduces_loss():
     l1 = B.rte_cnn_train_step(net, Xd.data_ptr(), Td.data_ptr(), Bn, H, W, 1, 0.0)
     assert l1 < 0.1 * l0
     B.rte_cnn_destroy(net)
+
+
+def test_weights_file_round_trip(tmp_path):
+    """rte_cnn_save / rte_cnn_load: a second network of the same shape loads
+    the first one's weights and then computes the same forward output; a file
+    of another shape or a truncated file is refused and leaves it unchanged."""
+    from paper_1802_03061_gb300 import _binding as B
+    net1, _ = _make(4, 16, 16, 3)
+    net2, _ = _make(4, 16, 16, 9)
+    path = tmp_path / "w.bin"
+    B.rte_cnn_save(net1, path)
+    X = torch.from_numpy(np.random.default_rng(1).standard_normal((1, 8, 40, 16)).astype(np.float32)).to(
+        torch.bfloat16).cuda()
+
+    def fwd(net):
+        Y = torch.empty((1, 8, 40, 16), dtype=torch.float32, device="cuda")
+        B.rte_cnn_forward(net, X.data_ptr(), 1, 8, 40, Y.data_ptr())
+        torch.cuda.synchronize()
+        return Y.cpu().numpy()
+
+    y1, y2 = fwd(net1), fwd(net2)
+    assert rel(y2, y1) > 1e-2                      # different seeds, different networks
+    B.rte_cnn_load(net2, path)
+    assert np.array_equal(fwd(net2), y1)
+    other, _ = _make(3, 16, 16, 3)                 # another depth
+    with pytest.raises(B.RteError):
+        B.rte_cnn_load(other, path)
+    bad = tmp_path / "short.bin"
+    bad.write_bytes(path.read_bytes()[:100])
+    with pytest.raises(B.RteError):
+        B.rte_cnn_load(net1, bad)
+    assert np.array_equal(fwd(net1), y1)
+    for n in (net1, net2, other):
+        B.rte_cnn_destroy(n)
