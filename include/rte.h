@@ -73,6 +73,14 @@ typedef enum {
     RTE_PREC_MIXED_BF16SPEC = 2 /* as above with the inner spectra stored in BF16      */
 } rte_prec;
 
+/* Krylov method of the FP32 inner solves of the mixed modes.  GMRES (the
+ * default); MINRES (Paige-Saunders, three-term recurrence) where the operator
+ * is symmetric, i.e. L = 0 (Sec. 2.3.1: the isotropic Nystrom matrix is
+ * symmetric and the paper solves that case with MINRES) -- for L > 0, or a
+ * restart length below 5, MINRES requests run GMRES.  The plain FP64 mode
+ * always uses GMRES. */
+typedef enum { RTE_INNER_GMRES = 0, RTE_INNER_MINRES = 1 } rte_inner_solver;
+
 /* Solver options.  A zero-initialised struct selects the defaults given in
  * brackets.  tol is the relative residual ||b - (I-K)u|| / ||b|| in the
  * 2-norm over all modes -L..L, measured with the FP64 operator (the paper
@@ -85,6 +93,7 @@ typedef struct {
     double inner_tol;  /* [1e-4] relative tolerance of each inner (FP32) solve */
     int use_guess;     /* [0] 1: u_dev holds an initial guess on entry */
     int q_policy;      /* [0] 0: smallest even 2^a 3^b >= 2n-1; else Q itself */
+    int inner_solver;  /* [RTE_INNER_GMRES] Krylov method of the FP32 inner solves */
 } rte_opts;
 
 typedef struct {

@@ -122,7 +122,7 @@ extern "C" rte_status rte_batch_create(rte_batch* out, int count, const rte_inst
             e = cudaStreamEndCapture(cs, &gg);
             if (e != cudaSuccess || nd != 1) { st = rte_cuda_fail(e, "batch capture end"); break; }
         }
-        st = solve_graph_append(p, b->prec, b->m, g, &dep, cs, &b->info[i]);
+        st = solve_graph_append(p, b->prec, b->m, solve_uses_minres(p, &b->opts), g, &dep, cs, &b->info[i]);
         if (st != RTE_OK) break;
         // tail: solution and state out
         {

@@ -35,6 +35,7 @@ struct SolveGraphInfo {
 struct SolveGraph {
     void* exec = nullptr;  // cudaGraphExec_t of the whole solve
     int m = 0;
+    bool minres = false;   // inner solves by MINRES (else GMRES)
     SolveGraphInfo info;
 };
 
@@ -141,8 +142,9 @@ rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b
 rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* st, cudaStream_t s);
 rte_status krylov_free(rte_plan p);
 size_t refdev_size();
-rte_status solve_graph_append(rte_plan p, int prec, int m, cudaGraph_t g, cudaGraphNode_t* dep, cudaStream_t cs,
-                              SolveGraphInfo* info);
+bool solve_uses_minres(const rte_plan p, const rte_opts* o);
+rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, cudaGraph_t g, cudaGraphNode_t* dep,
+                              cudaStream_t cs, SolveGraphInfo* info);
 rte_status solve_set_options(rte_plan p, const rte_opts* o, cudaStream_t s);
 struct RefDev;
 rte_status solve_collect(rte_plan p, int prec, const RefDev* host_ref, rte_stats* stats, double ms);

@@ -45,7 +45,11 @@ struct GmresDev {
     double nrm;     // last norm result
     double bnorm;   // ||rhs||
     double vscale;  // FP32 steps: the newest basis vector V_j is stored unscaled; V_j * vscale is unit
-    unsigned int cnt1, cnt2;  // finished-block counters of the fused FP32 step kernels (reset by the last block)
+    unsigned int cnt1, cnt2, cnt3;  // finished-block counters of the fused FP32 kernels (reset by the last block)
+    // MINRES (symmetric L = 0 inner solves): step number and the Lanczos / QR recurrence scalars
+    int mr_it;
+    double mr_beta1, mr_beta, mr_oldb, mr_alfa, mr_dbar, mr_epsln, mr_oldeps, mr_delta, mr_gamma, mr_phi,
+        mr_phibar, mr_cs, mr_sn;
     double cs[GM_MMAX], sn[GM_MMAX], g[GM_MMAX + 1];
     double Hc[(GM_MMAX + 1) * GM_MMAX];  // H[i + j*(m+1)]
     double hA[GM_MMAX + 1], hB[GM_MMAX + 1], y[GM_MMAX];
@@ -875,6 +879,237 @@ static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream
     return RTE_OK;
 }
 
+// --------------------------------------------------------------------------
+// MINRES (Paige & Saunders) for the inner solves of symmetric operators: for
+// L = 0 the Nystrom matrix is symmetric (Sec. 2.3.1, Eq. iso_discretization),
+// and the paper solves that case with MINRES.  Lanczos three-term recurrence
+// with unnormalised vectors r1, r2 (rotating through three buffers B[0..2]
+// by the step number), QR of the tridiagonal matrix by one Givens rotation
+// per step, search directions w rotating through W[0..2], so a step streams
+// a fixed number of vectors instead of the whole Arnoldi basis.  Step it
+// (1-based), with v = vin the normalised Lanczos vector and y = A v:
+//   alpha = v.(y - (beta/oldb) r1)            (k_mr_dot; r1 term from it = 2)
+//   y' = y - (beta/oldb) r1 - (alpha/beta) r2, beta' = |y'|     (k_mr_upd)
+//   delta = cs dbar + sn alpha,  gbar = sn dbar - cs alpha,
+//   eps = sn beta',  dbar = -cs beta',  gamma = |(gbar, beta')|,
+//   cs = gbar/gamma, sn = beta'/gamma, phi = cs phibar, phibar = sn phibar
+//   w = (v - oldeps w1 - delta w2)/gamma, x += phi w, v = y'/beta'  (k_mr_sol)
+// |phibar| is the residual norm of the inner system.  Dots in EFT
+// arithmetic, scalars FP64; the "last block" reductions are those of the
+// fused GMRES step (deterministic, nothing waits).
+// --------------------------------------------------------------------------
+__global__ void k_mr_start(GmresDev* st, const RefDev* ref, cudaGraphConditionalHandle loop) {
+    if (threadIdx.x != 0) return;
+    const int left = ref->maxit - ref->its;
+    st->maxit = left < 1 ? 1 : left;
+    st->its = 0;
+    double tin = ref->inner_tol;  // as k_gm_start (mixed mode)
+    const double need = ref->relres > 0.0 ? 0.5 * ref->tol / ref->relres : 1.0;
+    if (need > tin) tin = need;
+    st->tol = tin;
+    const double b1 = st->nrm;
+    st->mr_it = 1;
+    st->mr_beta1 = b1;
+    st->mr_beta = b1;
+    st->mr_oldb = 0.0;
+    st->mr_dbar = 0.0;
+    st->mr_epsln = 0.0;
+    st->mr_phibar = b1;
+    st->mr_cs = -1.0;
+    st->mr_sn = 0.0;
+    st->target = tin * b1;
+    st->res = b1;
+    st->conv = !(b1 > st->target) ? 1 : 0;
+    const bool go = isfinite(b1) && b1 > st->target;
+    cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
+// B[2] = rhs, vin = rhs / beta1, W[0..2] = 0, x = 0
+__global__ void k_mr_init(const float* __restrict__ rhs, float* __restrict__ B, float* __restrict__ W,
+                          float* __restrict__ vin, float* __restrict__ x, long nr, const GmresDev* __restrict__ st) {
+    const double b1 = st->mr_beta1;
+    const float inv = b1 > 0.0 ? (float)(1.0 / b1) : 0.f;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x) {
+        const float r = rhs[e];
+        B[2 * nr + e] = r;
+        vin[e] = r * inv;
+        W[e] = 0.f;
+        W[nr + e] = 0.f;
+        W[2 * nr + e] = 0.f;
+        x[e] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mr_dot(const float* __restrict__ v, const float* __restrict__ y,
+                                                const float* __restrict__ B, GmresDev* __restrict__ st, long nr,
+                                                long nw1, double* __restrict__ part) {
+    const int it = st->mr_it;
+    const float* r1 = B + (long)(it % 3) * nr;
+    const bool two = it >= 2;
+    const int nb = gridDim.x;
+    __shared__ double red[2][8];
+    __shared__ bool last;
+    const long base = (long)blockIdx.x * TILE + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float ha = 0.f, la = 0.f, hc = 0.f, lc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long e = base + 256 * q;
+        if (e < nr) {
+            const float vv = v[e] * (e < nw1 ? 1.f : 2.f);
+            ff_fma(ha, la, vv, y[e]);
+            if (two) ff_fma(hc, lc, vv, r1[e]);
+        }
+    }
+    ff_warp_sum(ha, la);
+    ff_warp_sum(hc, lc);
+    if (lane == 0) {
+        red[0][wid] = (double)ha + (double)la;
+        red[1][wid] = (double)hc + (double)lc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[threadIdx.x][q];
+        part[(long)threadIdx.x * nb + blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt1, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (wid < 2) {
+        double t = 0.0;
+        for (int b = lane; b < nb; b += 32) t += __ldcg(part + (long)wid * nb + b);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) red[wid][0] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double c = two ? st->mr_beta / st->mr_oldb : 0.0;
+        st->mr_alfa = red[0][0] - c * red[1][0];
+        st->cnt1 = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mr_upd(const float* __restrict__ y, float* __restrict__ B,
+                                                GmresDev* __restrict__ st, long nr, long nw1,
+                                                double* __restrict__ part, cudaGraphConditionalHandle loop) {
+    const int it = st->mr_it;
+    const float* r1 = B + (long)(it % 3) * nr;
+    const float* r2 = B + (long)((it + 1) % 3) * nr;
+    float* out = B + (long)((it + 2) % 3) * nr;
+    const double beta = st->mr_beta;
+    const float c1 = it >= 2 ? (float)(beta / st->mr_oldb) : 0.f;
+    const float c2 = (float)(st->mr_alfa / beta);
+    const int nb = gridDim.x;
+    __shared__ double red[256];
+    __shared__ bool last;
+    const long base = (long)blockIdx.x * TILE + threadIdx.x;
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long e = base + 256 * q;
+        if (e < nr) {
+            const float nv = fmaf(-c2, r2[e], fmaf(-c1, r1[e], y[e]));
+            out[e] = nv;
+            ff_fma(hi, lo, nv, nv * (e < nw1 ? 1.f : 2.f));
+        }
+    }
+    ff_warp_sum(hi, lo);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt2, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(part + b);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double bnew = sqrt(red[0]);
+    const double alfa = st->mr_alfa, cs = st->mr_cs, sn = st->mr_sn, dbar = st->mr_dbar;
+    st->mr_oldb = beta;
+    st->mr_beta = bnew;
+    st->mr_oldeps = st->mr_epsln;
+    st->mr_delta = cs * dbar + sn * alfa;
+    const double gbar = sn * dbar - cs * alfa;
+    st->mr_epsln = sn * bnew;
+    st->mr_dbar = -cs * bnew;
+    double gamma = hypot(gbar, bnew);
+    if (!(gamma > 1e-300)) gamma = 1e-300;
+    const double cn = gbar / gamma, snn = bnew / gamma;
+    st->mr_cs = cn;
+    st->mr_sn = snn;
+    st->mr_gamma = gamma;
+    st->mr_phi = cn * st->mr_phibar;
+    st->mr_phibar = snn * st->mr_phibar;
+    st->res = fabs(st->mr_phibar);
+    st->its += 1;
+    st->cnt2 = 0u;
+    int stop = 0;
+    if (st->res <= st->target) { stop = 1; st->conv = 1; }
+    if (!(bnew > 1e-300) || !isfinite(st->res)) stop = 1;  // invariant subspace reached, or non-finite
+    if (st->its >= st->maxit) stop = 1;
+    st->stop = stop;
+    cudaGraphSetConditional(loop, stop ? 0u : 1u);
+}
+
+__global__ void __launch_bounds__(256) k_mr_sol(float* __restrict__ vin, const float* __restrict__ B,
+                                                float* __restrict__ W, float* __restrict__ x,
+                                                GmresDev* __restrict__ st, long nr) {
+    const int it = st->mr_it;
+    const float* w1 = W + (long)(it % 3) * nr;
+    const float* w2 = W + (long)((it + 1) % 3) * nr;
+    float* wn = W + (long)((it + 2) % 3) * nr;
+    const float* yn = B + (long)((it + 2) % 3) * nr;
+    const float ig = (float)(1.0 / st->mr_gamma);
+    const float oe = (float)st->mr_oldeps, dl = (float)st->mr_delta, ph = (float)st->mr_phi;
+    const double bn = st->mr_beta;
+    const float ib = bn > 1e-300 ? (float)(1.0 / bn) : 0.f;
+    const int nb = gridDim.x;
+    __shared__ bool last;
+    const long base = (long)blockIdx.x * TILE + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long e = base + 256 * q;
+        if (e < nr) {
+            const float wv = (vin[e] - oe * w1[e] - dl * w2[e]) * ig;
+            wn[e] = wv;
+            x[e] = fmaf(ph, wv, x[e]);
+            vin[e] = yn[e] * ib;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->cnt3, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        st->mr_it = it + 1;
+        st->cnt3 = 0u;
+    }
+}
+
+__global__ void k_mr_after(RefDev* ref, const GmresDev* st) {
+    if (threadIdx.x != 0) return;
+    ref->its += st->its;
+    ref->outer += 1;
+    ref->cycles += 1;
+}
+
 // one Arnoldi step (graph body)
 template <typename T>
 static rte_status arnoldi_body(Gm<T>& G, bool cgs2, cudaGraphConditionalHandle loop, cudaStream_t s) {
@@ -995,9 +1230,10 @@ static rte_status add_cond(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphConditi
 // Inputs/outputs are the plan's own f_dev / u_dev; options are read from
 // the plan's device RefDev at run time.
 template <typename T>
-static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cudaGraphNode_t* dep_io,
+static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, cudaGraph_t g, cudaGraphNode_t* dep_io,
                               cudaStream_t cs, SolveGraphInfo* info) {
     const bool mixed = sizeof(T) == sizeof(float);
+    const bool use_mr = mixed && minres && m >= 5;  // MINRES buffers: basis slots 0..5
     const bool cgs2 = !mixed;
     Gm<T> G;
     TRYS(gm_setup<T>(G, p, ws, m, cs));
@@ -1008,12 +1244,16 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cu
     RefDev* ref = (RefDev*)p->ref;
     T* rhs = mixed ? (T*)p->r32 : (T*)p->r64;
     T* x = mixed ? (T*)p->d32 : (T*)p->x64;
-    cudaGraphConditionalHandle c_guess, c_outer, c_cycle, c_loop, c_restart;
+    cudaGraphConditionalHandle c_guess = 0, c_outer = 0, c_cycle = 0, c_loop = 0, c_restart = 0;
+    // every handle must belong to a conditional node of the graph: the
+    // restart-cycle handles exist only with GMRES inner solves
     RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_guess, g, 0, cudaGraphCondAssignDefault));
     RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_outer, g, 0, cudaGraphCondAssignDefault));
-    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_cycle, g, 0, cudaGraphCondAssignDefault));
     RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_loop, g, 0, cudaGraphCondAssignDefault));
-    RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_restart, g, 0, cudaGraphCondAssignDefault));
+    if (!use_mr) {
+        RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_cycle, g, 0, cudaGraphCondAssignDefault));
+        RTE_CUDA_TRY(cudaGraphConditionalHandleCreate(&c_restart, g, 0, cudaGraphCondAssignDefault));
+    }
     cudaGraphNode_t dep = *dep_io;
     *info = SolveGraphInfo();
     // T.1 and start values
@@ -1049,6 +1289,47 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, cudaGraph_t g, cu
     // refinement loop
     cudaGraph_t outer_body;
     TRYS(add_cond(g, &dep, c_outer, cudaGraphCondTypeWhile, &outer_body));
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (use_mr) {
+            // inner solve: MINRES on the FP32 operator
+            cudaGraphNode_t d = nullptr;
+            float* B = (float*)G.V;
+            float* W = B + 3 * nr;
+            SEG(outer_body, d, &info->k_outer, {
+                k_scale_inv<double, float><<<gr, 256, 0, cs>>>(p->r64, p->r32, nr, &ref->rnorm);
+                rte_count_launches(1);
+            });
+            SEG(outer_body, d, &info->k_cycle, {
+                TRYS(dev_norm<float>((const float*)rhs, nr, nw1, G.part, &G.st->nrm, cs));
+                k_mr_start<<<1, 32, 0, cs>>>(G.st, ref, c_loop);
+                k_mr_init<<<gr, 256, 0, cs>>>((const float*)rhs, B, W, (float*)G.vin, (float*)x, nr, G.st);
+                rte_count_launches(2);
+            });
+            cudaGraph_t loop_body;
+            TRYS(add_cond(outer_body, &d, c_loop, cudaGraphCondTypeWhile, &loop_body));
+            {
+                cudaGraphNode_t dl = nullptr;
+                SEG(loop_body, dl, &info->k_step, {
+                    TRYS(apply_A_T(p, (const float*)G.vin, (float*)G.w, cs));
+                    k_mr_dot<<<nb, 256, 0, cs>>>((const float*)G.vin, (const float*)G.w, B, G.st, nr, nw1, G.part);
+                    k_mr_upd<<<nb, 256, 0, cs>>>((const float*)G.w, B, G.st, nr, nw1, G.part, c_loop);
+                    k_mr_sol<<<nb, 256, 0, cs>>>((float*)G.vin, B, W, (float*)x, G.st, nr);
+                    rte_count_launches(3);
+                });
+            }
+            SEG(outer_body, d, &info->k_outer, {
+                k_axpy_scaled<float><<<gr, 256, 0, cs>>>(p->u_dev, (const float*)x, nr, &ref->rnorm);
+                k_mr_after<<<1, 32, 0, cs>>>(ref, G.st);
+                rte_count_launches(2);
+                TRYS(apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+                TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
+                k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
+                rte_count_launches(1);
+            });
+            *dep_io = dep;
+            return RTE_OK;
+        }
+    }
     {
         cudaGraphNode_t d = nullptr;
         SEG(outer_body, d, &info->k_outer, {
@@ -1119,20 +1400,25 @@ struct CountGuard {
     ~CountGuard() { rte_count_launches(-(rte_kernel_launches() - c0)); }
 };
 
-rte_status solve_graph_append(rte_plan p, int prec, int m, cudaGraph_t g, cudaGraphNode_t* dep, cudaStream_t cs,
-                              SolveGraphInfo* info) {
+// MINRES inner solves: requested, symmetric operator (L = 0), mixed mode
+bool solve_uses_minres(const rte_plan p, const rte_opts* o) {
+    return o->prec != RTE_PREC_FP64 && p->L == 0 && o->inner_solver == RTE_INNER_MINRES && o->restart >= 5;
+}
+
+rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, cudaGraph_t g, cudaGraphNode_t* dep,
+                              cudaStream_t cs, SolveGraphInfo* info) {
     CountGuard guard;
     const rte_prec saved = p->opts.prec;
     p->opts.prec = (rte_prec)prec;  // selects the inner spectra precision at capture
-    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(p, p->k64, m, g, dep, cs, info)
-                                          : build_solve<float>(p, p->k32, m, g, dep, cs, info);
+    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(p, p->k64, m, false, g, dep, cs, info)
+                                          : build_solve<float>(p, p->k32, m, minres, g, dep, cs, info);
     p->opts.prec = saved;
     return st;
 }
 
-static rte_status get_solve_graph(rte_plan p, int prec, int m, cudaStream_t s, cudaGraphExec_t* out) {
+static rte_status get_solve_graph(rte_plan p, int prec, int m, bool minres, cudaStream_t s, cudaGraphExec_t* out) {
     SolveGraph& sg = p->graphs[prec];
-    if (sg.exec && sg.m == m) {
+    if (sg.exec && sg.m == m && sg.minres == minres) {
         *out = (cudaGraphExec_t)sg.exec;
         return RTE_OK;
     }
@@ -1145,13 +1431,13 @@ static rte_status get_solve_graph(rte_plan p, int prec, int m, cudaStream_t s, c
     cudaStream_t cs;
     RTE_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraphNode_t dep = nullptr;
-    rte_status st = solve_graph_append(p, prec, m, g, &dep, cs, &sg.info);
+    rte_status st = solve_graph_append(p, prec, m, minres, g, &dep, cs, &sg.info);
     cudaStreamDestroy(cs);
     if (st == RTE_OK) {
         cudaGraphExec_t ex = nullptr;
         cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
         if (e != cudaSuccess) st = rte_cuda_fail(e, "instantiate solve graph");
-        else { sg.exec = ex; sg.m = m; *out = ex; }
+        else { sg.exec = ex; sg.m = m; sg.minres = minres; *out = ex; }
     }
     cudaGraphDestroy(g);
     return st;
@@ -1199,7 +1485,7 @@ rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStr
     cudaGraphExec_t ex = nullptr;
     const int prec = (int)o->prec;
     // the FP64 workspace is only needed by the FP64 mode
-    rte_status st = get_solve_graph(p, prec, o->restart, s, &ex);
+    rte_status st = get_solve_graph(p, prec, o->restart, solve_uses_minres(p, o), s, &ex);
     if (st != RTE_OK) return st;
     cudaEvent_t ev0, ev1;
     RTE_CUDA_TRY(cudaEventCreate(&ev0));
