@@ -429,6 +429,23 @@ def run_batch(args):
         conv = conv and all(s_["converged"] for s_ in stats)
     launches = B.rte_kernel_launches() - l0
     clk = clocks.stop()
+    # the same instances solved one after another, each by its own plan's
+    # graph (f and u copied through the plan's buffers): the batch graph's gain
+    seq_ms = None
+    if ws == 1:
+        fs = [f[b.f_off[i]:b.f_off[i + 1]] for i in range(len(inst))]
+        us = [u[b.u_off[i]:b.u_off[i + 1]] for i in range(len(inst))]
+        plans = [B.rte_batch_plan(b.handle, i) for i in range(len(inst))]
+        for i in range(len(inst)):  # first use captures each plan's solve graph
+            B.rte_solve(plans[i], fs[i].data_ptr(), us[i].data_ptr(), b.opts, int(stream.cuda_stream))
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(len(inst)):
+            B.rte_solve(plans[i], fs[i].data_ptr(), us[i].data_ptr(), b.opts, int(stream.cuda_stream))
+        e1.record(stream)
+        e1.synchronize()
+        seq_ms = e0.elapsed_time(e1)
     t_max, solved, _ = replicas.aggregate(tot, len(inst) * args.steps)
     if ws > 1:
         torch.distributed.barrier()
@@ -439,6 +456,7 @@ def run_batch(args):
             "config": {"workload": "batch512: 512 2D instances, sides U{64..512}, L U{0,2,4,8}, mu_t logU[1,50], "
                                    "mu_s/mu_t U[0.5,0.99], HG g U[0,0.8], 1-6 Gaussians; one graph launch; tol 1e-8",
                        "all_converged": conv, "iters_total": int(sum(s_["iters"] for s_ in stats)),
+                       "sequential_single_solves_ms": seq_ms,
                        "instances_on_rank0": len(inst), "parallelism": "instances sharded by cost" if ws > 1
                        else "single GPU",
                        "create_s": t_create, "l2": "flushed before every timed step"},
