@@ -184,23 +184,24 @@ __global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const
 }
 
 // ---------------------------------------------------------------------------
-// 1w/3w. row passes with the warp-register FFT (FP32, Q = 32 R): one warp per
-// line (a row of u_k, or two packed rows of u_0), 8 lines per block.  The
-// transform stays in registers; shared memory only holds the spectra of the
-// block's lines (swizzled) for the half-spectrum split / rebuild, which keep
-// the same y-contiguous global layout as the generic passes.
+// 1w/3w. row passes with the warp FFT (Q = 32 R; FP32 or float-float compute
+// T, field storage TF): one warp per line (a row of u_k, or two packed rows
+// of u_0), 8 lines per block.  The transform stays in registers; shared
+// memory holds each warp's FFT scratch and then the spectra of the block's
+// lines (swizzled) for the half-spectrum split / rebuild, which keep the same
+// y-contiguous global layout as the generic passes.
 // grid (ceil(n / 8), modes), block 256; rows per block 8 (k >= 1) or 16 (k = 0)
 // ---------------------------------------------------------------------------
-template <int R>
-__global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__ x, const double* __restrict__ f,
-                                                      float2* __restrict__ out, const float2* __restrict__ tw,
-                                                      RowParams p) {
+template <int R, typename T, typename TF>
+__global__ void __launch_bounds__(256) k_row_fwd_warp(const TF* __restrict__ x, const double* __restrict__ f,
+                                                      T* __restrict__ out, const T* __restrict__ tw, RowParams p) {
+    using RR = typename real_of<T>::R;
     constexpr int Q = 32 * R;
     // line stride: holds the FFT scratch (Q + 32), consecutive lines 2 bank pairs apart
     constexpr int LS = Q + 34;
     extern __shared__ unsigned char smraw[];
-    float2* twl = reinterpret_cast<float2*>(smraw);
-    float2* Z = twl + Q;
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Z = twl + Q;
     const int n = p.n, H = p.H;
     const int k = blockIdx.y;
     const int rows = k == 0 ? 16 : 8;
@@ -209,29 +210,29 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float wt = (float)p.wk[k];
-    float2 v[R];
+    const RR wt = (RR)p.wk[k];
+    T v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int e = lane + 32 * r;
-        float2 val = make_float2(0.f, 0.f);
+        T val = mk<T>(0, 0);
         if (e < n) {
             if (k == 0) {
                 const int ya = y0 + 2 * w, yb = ya + 1;
-                float a = 0.f, b = 0.f;
+                RR a = (RR)0, b = (RR)0;
                 if (f) {
-                    if (ya < n) a = (float)f[(long)ya * n + e];
-                    if (yb < n) b = (float)f[(long)yb * n + e];
+                    if (ya < n) a = (RR)f[(long)ya * n + e];
+                    if (yb < n) b = (RR)f[(long)yb * n + e];
                 } else {
-                    if (ya < n) a = x[(long)ya * n + e].x;
-                    if (yb < n) b = x[(long)yb * n + e].x;
+                    if (ya < n) a = to_c<T>(x[(long)ya * n + e]).x;
+                    if (yb < n) b = to_c<T>(x[(long)yb * n + e]).x;
                 }
-                val = make_float2(wt * a, wt * b);
+                val = mk<T>(wt * a, wt * b);
             } else {
                 const int y = y0 + w;
                 if (y < n) {
-                    const float2 u = x[((long)k * n + y) * n + e];
-                    val = make_float2(wt * u.x, wt * u.y);
+                    const T u = to_c<T>(x[((long)k * n + y) * n + e]);
+                    val = mk<T>(wt * u.x, wt * u.y);
                 }
             }
         }
@@ -247,10 +248,10 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__
         const int y = y0 + r;
         if (y >= n) continue;
         const int line = k == 0 ? r >> 1 : r;
-        const float2 Zp = Z[line * LS + swz16(xi)];
-        const float2 Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
-        const float2 Fv = make_float2(0.5f * (Zp.x + Zm.x), 0.5f * (Zp.y - Zm.y));
-        const float2 Gv = make_float2(0.5f * (Zp.y + Zm.y), -0.5f * (Zp.x - Zm.x));
+        const T Zp = Z[line * LS + swz16(xi)];
+        const T Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
+        const T Fv = mk<T>((RR)0.5 * (Zp.x + Zm.x), (RR)0.5 * (Zp.y - Zm.y));
+        const T Gv = mk<T>((RR)0.5 * (Zp.y + Zm.y), (RR)-0.5 * (Zp.x - Zm.x));
         if (k == 0) {
             out[(long)xi * n + y] = (r & 1) ? Gv : Fv;
         } else {
@@ -260,16 +261,18 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const float2* __restrict__
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__ in, const float2* __restrict__ x,
-                                                      const float2* __restrict__ z, float2* __restrict__ out,
-                                                      const float2* __restrict__ tw, RowParams p, float a, float b,
-                                                      float c) {
+template <int R, typename T, typename TF>
+__global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, const TF* __restrict__ x,
+                                                      const TF* __restrict__ z, TF* __restrict__ out,
+                                                      const T* __restrict__ tw, RowParams p,
+                                                      typename real_of<T>::R a, typename real_of<T>::R b,
+                                                      typename real_of<T>::R c) {
+    using RR = typename real_of<T>::R;
     constexpr int Q = 32 * R;
     constexpr int LS = Q + 34;
     extern __shared__ unsigned char smraw[];
-    float2* twl = reinterpret_cast<float2*>(smraw);
-    float2* Z = twl + Q;
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Z = twl + Q;
     const int n = p.n, H = p.H;
     const int k = blockIdx.y;
     const int rows = k == 0 ? 16 : 8;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__
     // Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
         const int li = idx & 7, xi = idx >> 3;
-        float2 Fv = make_float2(0.f, 0.f), Gv = make_float2(0.f, 0.f);
+        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
         if (k == 0) {
             const int ya = y0 + 2 * li, yb = ya + 1;
             if (ya < n) Fv = in[(long)xi * n + ya];
@@ -291,12 +294,12 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__
                 Gv = in[((long)chB(k) * H + xi) * n + y];
             }
         }
-        Z[li * LS + swz16(xi)] = make_float2(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = make_float2(Fv.x + Gv.y, Gv.x - Fv.y);
+        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 v[R];
+    T v[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = Z[w * LS + swz16(wfreq<R>(j, lane))];
     __syncwarp();
@@ -309,26 +312,26 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const float2* __restrict__
             const int ya = y0 + 2 * w, yb = ya + 1;
             if (ya < n) {
                 const long o = (long)ya * n + e;
-                float2 q = make_float2(b * v[r].x, 0.f);
-                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
-                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
-                out[o] = q;
+                T q = mk<T>(b * v[r].x, (RR)0);
+                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = to_f<TF>(q);
             }
             if (yb < n) {
                 const long o = (long)yb * n + e;
-                float2 q = make_float2(b * v[r].y, 0.f);
-                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
-                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
-                out[o] = q;
+                T q = mk<T>(b * v[r].y, (RR)0);
+                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = to_f<TF>(q);
             }
         } else {
             const int y = y0 + w;
             if (y < n) {
                 const long o = ((long)k * n + y) * n + e;
-                float2 q = make_float2(b * v[r].x, b * v[r].y);
-                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
-                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
-                out[o] = q;
+                T q = mk<T>(b * v[r].x, b * v[r].y);
+                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = to_f<TF>(q);
             }
         }
     }

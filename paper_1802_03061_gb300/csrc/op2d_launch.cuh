@@ -182,32 +182,58 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
     return cudaGetLastError();
 }
 
-// warp-register row passes (FP32 fields and compute, Q in {64, 128, 256, 512})
+// warp row passes (Q in {64, 128, 256, 512}) for FP32 fields and compute.  The
+// kernels also instantiate for float-float on FP64 fields, but there the
+// shared-memory passes are faster (the float-float inverse needs 193 registers
+// per thread in the warp form), so the float-float passes stay Stockham.
 template <typename T, typename TF> struct row_warp_types { static constexpr bool value = false; };
 template <> struct row_warp_types<float2, float2> { static constexpr bool value = true; };
-static inline size_t row_warp_smem(int Q) { return (size_t)(Q + 8 * (Q + 34)) * sizeof(float2); }
+template <typename T> static inline size_t row_warp_smem(int Q) { return (size_t)(Q + 8 * (Q + 34)) * sizeof(T); }
 
-static cudaError_t row_fwd_warp(int Q, dim3 grid, const float2* x, const double* f, float2* out, const float2* tw,
+template <typename T, typename TF>
+static cudaError_t row_fwd_warp(int Q, dim3 grid, const TF* x, const double* f, T* out, const T* tw,
                                 const RowParams& rp, cudaStream_t s) {
-    const size_t sm = row_warp_smem(Q);
+    const size_t sm = row_warp_smem<T>(Q);
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_row_fwd_warp<2, T, TF>)) != cudaSuccess ||
+            (e = allow_smem(k_row_fwd_warp<4, T, TF>)) != cudaSuccess ||
+            (e = allow_smem(k_row_fwd_warp<8, T, TF>)) != cudaSuccess ||
+            (e = allow_smem(k_row_fwd_warp<16, T, TF>)) != cudaSuccess)
+            return e;
+        once = true;
+    }
     switch (Q) {
-        case 64: k_row_fwd_warp<2><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
-        case 128: k_row_fwd_warp<4><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
-        case 256: k_row_fwd_warp<8><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
-        case 512: k_row_fwd_warp<16><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 64: k_row_fwd_warp<2, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 128: k_row_fwd_warp<4, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 256: k_row_fwd_warp<8, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 512: k_row_fwd_warp<16, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-static cudaError_t row_inv_warp(int Q, dim3 grid, const float2* in, const float2* x, const float2* z, float2* out,
-                                const float2* tw, const RowParams& rp, float a, float b, float c, cudaStream_t s) {
-    const size_t sm = row_warp_smem(Q);
+template <typename T, typename TF>
+static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, const TF* z, TF* out, const T* tw,
+                                const RowParams& rp, typename real_of<T>::R a, typename real_of<T>::R b,
+                                typename real_of<T>::R c, cudaStream_t s) {
+    const size_t sm = row_warp_smem<T>(Q);
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_row_inv_warp<2, T, TF>)) != cudaSuccess ||
+            (e = allow_smem(k_row_inv_warp<4, T, TF>)) != cudaSuccess ||
+            (e = allow_smem(k_row_inv_warp<8, T, TF>)) != cudaSuccess ||
+            (e = allow_smem(k_row_inv_warp<16, T, TF>)) != cudaSuccess)
+            return e;
+        once = true;
+    }
     switch (Q) {
-        case 64: k_row_inv_warp<2><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
-        case 128: k_row_inv_warp<4><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
-        case 256: k_row_inv_warp<8><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
-        case 512: k_row_inv_warp<16><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 64: k_row_inv_warp<2, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 128: k_row_inv_warp<4, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 256: k_row_inv_warp<8, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 512: k_row_inv_warp<16, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -247,8 +273,8 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         if (row_warp) {
             if constexpr (row_warp_types<T, TF>::value) {
                 const dim3 grid((p->n + 7) / 8, nmod_in);
-                if ((e = row_fwd_warp(p->Q, grid, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw,
-                                      rp, s)) != cudaSuccess)
+                if ((e = row_fwd_warp<T, TF>(p->Q, grid, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr,
+                                             Tb, tw, rp, s)) != cudaSuccess)
                     return e;
             }
         } else {
@@ -288,8 +314,8 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         if (row_warp) {
             if constexpr (row_warp_types<T, TF>::value) {
                 const dim3 grid2((p->n + 7) / 8, p->L + 1);
-                if ((e = row_inv_warp(p->Q, grid2, Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (float)a,
-                                      (float)b, (float)c, s)) != cudaSuccess)
+                if ((e = row_inv_warp<T, TF>(p->Q, grid2, Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a,
+                                             (R)b, (R)c, s)) != cudaSuccess)
                     return e;
             }
         } else {
