@@ -94,6 +94,11 @@ typedef struct {
     int use_guess;     /* [0] 1: u_dev holds an initial guess on entry */
     int q_policy;      /* [0] 0: smallest even 2^a 3^b >= 2n-1; else Q itself */
     int inner_solver;  /* [RTE_INNER_GMRES] Krylov method of the FP32 inner solves */
+    int precond;       /* [0] 1: periodic preconditioner for the inner GMRES (mixed modes; 2D needs
+                          Q = 32 * 2^j, 64 <= Q <= 512, else it is not used): GMRES on (I-K) M with
+                          M = crop (I - C)^{-1} pad, C the convolution on the periodic padded grid,
+                          inverted per frequency; same answer, fewer inner iterations.  Not in the
+                          paper.  Built on the first solve that asks for it (allocates). */
 } rte_opts;
 
 typedef struct {
@@ -134,6 +139,14 @@ rte_status rte_apply_K64e(rte_plan plan, const void* x_dev, void* y_dev, void* c
  * float2 [L+1][n][n] (2D) or float [n]^3 (3D); the spectra are FP32 or BF16
  * as the plan's prec selects (FP32 for an FP64 plan). */
 rte_status rte_apply_K32(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
+/* The periodic preconditioner of the inner solves (see rte_opts.precond) on an
+ * FP32 field: y = M x = crop((I - C)^{-1} pad(x)), C the convolution with the
+ * plan's kernel samples on the Q^d periodic grid, inverted per frequency (a
+ * scalar in 3D, a (2L+1) x (2L+1) matrix in 2D, stored in BF16).  Layout as
+ * rte_apply_K32.  Builds the preconditioner data on the first call
+ * (allocates device memory).  RTE_EUNSUPPORTED for 2D plans whose Q is not
+ * 32 * 2^j (64 <= Q <= 512).  Not in the paper. */
+rte_status rte_apply_precond32(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
 
 /* b = K~ g (step T.1 / S.1): f_dev double [n]^d real source, b_dev an FP64
  * field (all modes 0..L in 2D). */

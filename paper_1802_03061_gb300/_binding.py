@@ -31,7 +31,7 @@ class rte_grid(ctypes.Structure):
 class rte_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_guess", ctypes.c_int),
-                ("q_policy", ctypes.c_int), ("inner_solver", ctypes.c_int)]
+                ("q_policy", ctypes.c_int), ("inner_solver", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class rte_stats(ctypes.Structure):
@@ -63,7 +63,7 @@ def lib():
         L.rte_plan_create.argtypes = [ctypes.POINTER(VP), rte_grid, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(rte_opts), VP]
-        for name in ("rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_apply_K64e", "rte_rhs"):
+        for name in ("rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_apply_K64e", "rte_apply_precond32", "rte_rhs"):
             getattr(L, name).argtypes = [VP, VP, VP, VP]
         L.rte_solve.argtypes = [VP, VP, VP, ctypes.POINTER(rte_opts), ctypes.POINTER(rte_stats), VP]
         L.rte_solve_host.argtypes = [VP, VP, VP, ctypes.POINTER(rte_opts), ctypes.POINTER(rte_stats), VP]
@@ -110,7 +110,8 @@ def lib():
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
         L.rte_last_error.restype = ctypes.c_char_p
-        for name in ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_apply_K64e", "rte_rhs",
+        for name in ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_apply_K32", "rte_apply_K64e",
+                     "rte_apply_precond32", "rte_rhs",
                      "rte_solve",
                      "rte_solve_host", "rte_plan_info", "rte_plan_cell_weights", "rte_destroy"):
             getattr(L, name).restype = ctypes.c_int
@@ -135,10 +136,10 @@ INNER = {"gmres": 0, "minres": 1}
 
 
 def make_opts(prec="fp64", tol=1e-8, restart=40, maxit=2000, inner_tol=1e-4, use_guess=0, q_policy=0,
-              inner_solver="gmres"):
+              inner_solver="gmres", precond=0):
     return rte_opts(PREC[prec] if isinstance(prec, str) else int(prec), tol, restart, maxit, inner_tol,
                     int(use_guess), int(q_policy),
-                    INNER[inner_solver] if isinstance(inner_solver, str) else int(inner_solver))
+                    INNER[inner_solver] if isinstance(inner_solver, str) else int(inner_solver), int(precond))
 
 
 def rte_plan_create(dim, n, h, mu_t, mu_s, L, sigma_hat, opts=None, stream=0):
@@ -165,6 +166,10 @@ def rte_apply_K64e(plan, x, y, stream=0):
 
 def rte_apply_K32(plan, x, y, stream=0):
     _check(lib().rte_apply_K32(plan, VP(x), VP(y), VP(stream)), "rte_apply_K32")
+
+
+def rte_apply_precond32(plan, x, y, stream=0):
+    _check(lib().rte_apply_precond32(plan, VP(x), VP(y), VP(stream)), "rte_apply_precond32")
 
 
 def rte_rhs(plan, f, b, stream=0):

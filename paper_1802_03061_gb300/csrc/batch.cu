@@ -94,6 +94,14 @@ extern "C" rte_status rte_batch_create(rte_batch* out, int count, const rte_inst
         rte_batch_destroy(b);
         return RTE_ENOMEM;
     }
+    // preconditioner data (allocates): before any capture
+    for (int i = 0; i < count && st == RTE_OK; ++i)
+        if (solve_uses_precond(b->plans[i], &b->opts)) st = plan_precond_build(b->plans[i], (cudaStream_t)stream);
+    if (st == RTE_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) st = RTE_ECUDA;
+    if (st != RTE_OK) {
+        rte_batch_destroy(b);
+        return st;
+    }
     // build the batch graph: one independent branch per instance
     cudaGraph_t g = nullptr;
     cudaStream_t cs = nullptr;
@@ -122,7 +130,8 @@ extern "C" rte_status rte_batch_create(rte_batch* out, int count, const rte_inst
             e = cudaStreamEndCapture(cs, &gg);
             if (e != cudaSuccess || nd != 1) { st = rte_cuda_fail(e, "batch capture end"); break; }
         }
-        st = solve_graph_append(p, b->prec, b->m, solve_uses_minres(p, &b->opts), g, &dep, cs, &b->info[i]);
+        st = solve_graph_append(p, b->prec, b->m, solve_uses_minres(p, &b->opts), solve_uses_precond(p, &b->opts), g,
+                                &dep, cs, &b->info[i]);
         if (st != RTE_OK) break;
         // tail: solution and state out
         {

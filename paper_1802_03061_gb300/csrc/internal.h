@@ -36,6 +36,7 @@ struct SolveGraph {
     void* exec = nullptr;  // cudaGraphExec_t of the whole solve
     int m = 0;
     bool minres = false;   // inner solves by MINRES (else GMRES)
+    bool pc = false;       // inner GMRES with the periodic preconditioner
     SolveGraphInfo info;
 };
 
@@ -68,6 +69,13 @@ struct rte_plan_s {
     __nv_bfloat162* S16p = nullptr;
     double* S3_64 = nullptr;
     float* S3_32 = nullptr;
+    // periodic preconditioner (precond.cu), built on first use: 3D inverse
+    // spectrum [H][H][H]; 2D tagged inverse matrices [H][nch][nch][Q] (BF16)
+    float* S3p = nullptr;
+    __nv_bfloat16* Pp = nullptr;
+    float* pv1 = nullptr;      // FP32 field temporaries of the preconditioned solve
+    float* pv2 = nullptr;
+    bool pc_ready = false;
     // cell weights D_m, m = 0..2L (2D) or D (3D), computed on the device
     double* Dm = nullptr;
     // pass intermediates: 2D [nch][H][n] complex; 3D T1 [n][H][n], T2 [H][Q][n]
@@ -135,6 +143,11 @@ rte_status op2d_apply64_buffers(rte_plan p, const double* x, double* out, double
 // op3d.cu
 rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,
                         double c, const double* z, cudaStream_t s);
+// precond.cu
+bool plan_precond_supported(const rte_plan p);
+rte_status plan_precond_build(rte_plan p, cudaStream_t s);
+rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t s);
+cudaError_t op3d_run_pc32(rte_plan p, const float* x, float* out, cudaStream_t s);
 rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);
 
@@ -143,8 +156,9 @@ rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* st, cudaStream
 rte_status krylov_free(rte_plan p);
 size_t refdev_size();
 bool solve_uses_minres(const rte_plan p, const rte_opts* o);
-rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, cudaGraph_t g, cudaGraphNode_t* dep,
-                              cudaStream_t cs, SolveGraphInfo* info);
+bool solve_uses_precond(const rte_plan p, const rte_opts* o);
+rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, bool pc, cudaGraph_t g,
+                              cudaGraphNode_t* dep, cudaStream_t cs, SolveGraphInfo* info);
 rte_status solve_set_options(rte_plan p, const rte_opts* o, cudaStream_t s);
 struct RefDev;
 rte_status solve_collect(rte_plan p, int prec, const RefDev* host_ref, rte_stats* stats, double ms);

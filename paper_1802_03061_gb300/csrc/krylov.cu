@@ -709,6 +709,13 @@ __global__ void k_copy_T(const T* __restrict__ src, T* __restrict__ dst, long nr
         dst[e] = src[e];
 }
 
+// x += d
+template <typename T>
+__global__ void k_add_T(T* __restrict__ x, const T* __restrict__ d, long nr) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
+        x[e] += d[e];
+}
+
 template <typename T>
 __global__ void k_zero_T(T* __restrict__ dst, long nr) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
@@ -1112,10 +1119,20 @@ __global__ void k_mr_after(RefDev* ref, const GmresDev* st) {
 
 // one Arnoldi step (graph body)
 template <typename T>
-static rte_status arnoldi_body(Gm<T>& G, bool cgs2, cudaGraphConditionalHandle loop, cudaStream_t s) {
+static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditionalHandle loop, cudaStream_t s) {
     const long nr = G.nr;
     const int nb = tiles(nr), gr = grid_for(nr);
-    rte_status e = apply_A_T(G.p, G.vin, G.w, s);
+    rte_status e;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (pc) {  // right preconditioning: w = A (M v)
+            if ((e = plan_apply_pc32(G.p, (const float*)G.vin, G.p->pv1, s)) != RTE_OK) return e;
+            e = apply_A_T(G.p, (const float*)G.p->pv1, (float*)G.w, s);
+        } else {
+            e = apply_A_T(G.p, G.vin, G.w, s);
+        }
+    } else {
+        e = apply_A_T(G.p, G.vin, G.w, s);
+    }
     if (e != RTE_OK) return e;
     const int* jp = &G.st->j;
     if constexpr (sizeof(T) == sizeof(float)) {
@@ -1230,10 +1247,12 @@ static rte_status add_cond(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphConditi
 // Inputs/outputs are the plan's own f_dev / u_dev; options are read from
 // the plan's device RefDev at run time.
 template <typename T>
-static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, cudaGraph_t g, cudaGraphNode_t* dep_io,
+static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool pc, cudaGraph_t g,
+                              cudaGraphNode_t* dep_io,
                               cudaStream_t cs, SolveGraphInfo* info) {
     const bool mixed = sizeof(T) == sizeof(float);
     const bool use_mr = mixed && minres && m >= 5;  // MINRES buffers: basis slots 0..5
+    const bool use_pc = mixed && pc && !use_mr;      // preconditioned inner GMRES
     const bool cgs2 = !mixed;
     Gm<T> G;
     TRYS(gm_setup<T>(G, p, ws, m, cs));
@@ -1356,13 +1375,26 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, cuda
             TRYS(add_cond(cycle_body, &dc, c_loop, cudaGraphCondTypeWhile, &loop_body));
             {
                 cudaGraphNode_t dl = nullptr;
-                SEG(loop_body, dl, &info->k_step, { TRYS(arnoldi_body<T>(G, cgs2, c_loop, cs)); });
+                SEG(loop_body, dl, &info->k_step, { TRYS(arnoldi_body<T>(G, cgs2, use_pc, c_loop, cs)); });
             }
             SEG(cycle_body, dc, &info->k_cycle, {
                 k_solve_tri<<<1, 32, 0, cs>>>(G.st);
-                k_maxpy<T><<<nb, 256, 0, cs>>>(G.V, nr, x, G.st->y, &G.st->j, 0, 1.0, nw1, nullptr);
+                if (use_pc) {
+                    // x += M (V y)
+                    if constexpr (sizeof(T) == sizeof(float)) {
+                        k_zero_T<float><<<gr, 256, 0, cs>>>(p->pv2, nr);
+                        k_maxpy<float><<<nb, 256, 0, cs>>>((const float*)G.V, nr, p->pv2, G.st->y, &G.st->j, 0, 1.0,
+                                                          nw1, nullptr);
+                        TRYS(plan_apply_pc32(p, p->pv2, p->pv1, cs));
+                        k_add_T<float><<<gr, 256, 0, cs>>>((float*)x, p->pv1, nr);
+                        rte_count_launches(3);
+                    }
+                } else {
+                    k_maxpy<T><<<nb, 256, 0, cs>>>(G.V, nr, x, G.st->y, &G.st->j, 0, 1.0, nw1, nullptr);
+                    rte_count_launches(1);
+                }
                 k_cycle_end<<<1, 32, 0, cs>>>(G.st, ref, c_cycle, c_restart);
-                rte_count_launches(3);
+                rte_count_launches(2);
             });
             cudaGraph_t restart_body;
             TRYS(add_cond(cycle_body, &dc, c_restart, cudaGraphCondTypeIf, &restart_body));
@@ -1405,20 +1437,27 @@ bool solve_uses_minres(const rte_plan p, const rte_opts* o) {
     return o->prec != RTE_PREC_FP64 && p->L == 0 && o->inner_solver == RTE_INNER_MINRES && o->restart >= 5;
 }
 
-rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, cudaGraph_t g, cudaGraphNode_t* dep,
-                              cudaStream_t cs, SolveGraphInfo* info) {
+// periodic preconditioner for the FP32 inner GMRES: requested, mixed mode,
+// GMRES inner solves, and a plan shape the preconditioner supports
+bool solve_uses_precond(const rte_plan p, const rte_opts* o) {
+    return o->prec != RTE_PREC_FP64 && o->precond != 0 && !solve_uses_minres(p, o) && plan_precond_supported(p);
+}
+
+rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, bool pc, cudaGraph_t g,
+                              cudaGraphNode_t* dep, cudaStream_t cs, SolveGraphInfo* info) {
     CountGuard guard;
     const rte_prec saved = p->opts.prec;
     p->opts.prec = (rte_prec)prec;  // selects the inner spectra precision at capture
-    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(p, p->k64, m, false, g, dep, cs, info)
-                                          : build_solve<float>(p, p->k32, m, minres, g, dep, cs, info);
+    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(p, p->k64, m, false, false, g, dep, cs, info)
+                                          : build_solve<float>(p, p->k32, m, minres, pc, g, dep, cs, info);
     p->opts.prec = saved;
     return st;
 }
 
-static rte_status get_solve_graph(rte_plan p, int prec, int m, bool minres, cudaStream_t s, cudaGraphExec_t* out) {
+static rte_status get_solve_graph(rte_plan p, int prec, int m, bool minres, bool pc, cudaStream_t s,
+                                  cudaGraphExec_t* out) {
     SolveGraph& sg = p->graphs[prec];
-    if (sg.exec && sg.m == m && sg.minres == minres) {
+    if (sg.exec && sg.m == m && sg.minres == minres && sg.pc == pc) {
         *out = (cudaGraphExec_t)sg.exec;
         return RTE_OK;
     }
@@ -1431,13 +1470,14 @@ static rte_status get_solve_graph(rte_plan p, int prec, int m, bool minres, cuda
     cudaStream_t cs;
     RTE_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraphNode_t dep = nullptr;
-    rte_status st = solve_graph_append(p, prec, m, minres, g, &dep, cs, &sg.info);
+    rte_status st = pc ? plan_precond_build(p, s) : RTE_OK;  // allocates: before the capture
+    if (st == RTE_OK) st = solve_graph_append(p, prec, m, minres, pc, g, &dep, cs, &sg.info);
     cudaStreamDestroy(cs);
     if (st == RTE_OK) {
         cudaGraphExec_t ex = nullptr;
         cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
         if (e != cudaSuccess) st = rte_cuda_fail(e, "instantiate solve graph");
-        else { sg.exec = ex; sg.m = m; sg.minres = minres; *out = ex; }
+        else { sg.exec = ex; sg.m = m; sg.minres = minres; sg.pc = pc; *out = ex; }
     }
     cudaGraphDestroy(g);
     return st;
@@ -1485,7 +1525,7 @@ rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStr
     cudaGraphExec_t ex = nullptr;
     const int prec = (int)o->prec;
     // the FP64 workspace is only needed by the FP64 mode
-    rte_status st = get_solve_graph(p, prec, o->restart, solve_uses_minres(p, o), s, &ex);
+    rte_status st = get_solve_graph(p, prec, o->restart, solve_uses_minres(p, o), solve_uses_precond(p, o), s, &ex);
     if (st != RTE_OK) return st;
     cudaEvent_t ev0, ev1;
     RTE_CUDA_TRY(cudaEventCreate(&ev0));

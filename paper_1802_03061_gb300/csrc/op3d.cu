@@ -530,3 +530,10 @@ rte_status op3d_apply_ff(rte_plan p, MixKind kind, const double* x, double* out,
     if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply_ff");
     return RTE_OK;
 }
+
+// the periodic preconditioner's 3D application out = M x (precond.cu): the
+// same passes with the inverse spectrum and unit input weight
+cudaError_t op3d_run_pc32(rte_plan p, const float* x, float* out, cudaStream_t s) {
+    return op3d_run<float2, float, float>(p, x, out, 1.0, 0.0, 1.0, 0.0, nullptr, (float2*)p->T32, (float2*)p->U32,
+                                          p->S3p, p->tw32, s);
+}

@@ -1,0 +1,279 @@
+// Periodic (circulant) preconditioner for the FP32 inner solves.
+//
+// The operator K is a convolution cropped to the n^d cells (Sec. 2.3.1,
+// 3.3.1): K x = crop(C pad(x)), where C is the convolution with the same kernel
+// samples on the Q^d periodic grid.  C is diagonal in Fourier space -- a scalar
+// per frequency for d = 3 (L = 0), a (2L+1) x (2L+1) matrix T(xi) on the real
+// channels for d = 2 -- so (I - C)^{-1} is exact and cheap on the periodic
+// grid, and M = crop (I - C)^{-1} pad approximates (I - K)^{-1} everywhere
+// except near the boundary of the square / cube.  GMRES on A M (right
+// preconditioning: the inner solves still measure the true residual) then
+// needs a few iterations instead of tens.  Not in the paper (which runs
+// GMRES / MINRES without a preconditioner); the answer is the same to the
+// solve's tolerance.
+//
+// T(xi) has entries that are purely real or purely imaginary, imaginary
+// exactly when the modes of the two channels differ in parity (see the mode
+// mix in op2d.cuh), so with Phi = diag(i^{parity}) the matrix Phi^-1 T Phi is
+// real and (I - T)^{-1} has the same pattern: one real number per entry.  They
+// are stored in BF16 (the preconditioner only has to be close, not exact) as
+// Pp[xi_x][c][c'][slot], slot order of the warp column pass, and scaled by
+// 1/Q^2 for the unnormalised transforms of the passes.
+#include "op2d_launch.cuh"
+
+__host__ __device__ __forceinline__ int ch_mode(int c) { return (c + 1) >> 1; }
+
+// 3D: S3p = (1/Q^3) / (1 - mu_s Q^3 S3)  (S3 already holds FFT(g) / Q^3)
+__global__ void k_build_pc3d(const double* __restrict__ S3, float* __restrict__ S3p, long tot, double mu_s,
+                             double Q3) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x)
+        S3p[i] = (float)((1.0 / Q3) / (1.0 - mu_s * Q3 * S3[i]));
+}
+
+// 2D: one thread per (xi_x, slot).  T[c][c'] = Q^2 * mix(S(xi))[c][c'] * w(c')
+// with w = mu_s sigma_hat_{k(c')} (the row pass's input weights); Gauss-Jordan
+// with partial pivoting on I - T in complex FP64.
+template <int L>
+__global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __restrict__ Pp, int H, int Q, int R,
+                             RowParams rp, double Q2) {
+    constexpr int NCH = 2 * L + 1;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)H * Q) return;
+    const int kx = (int)(idx / Q), sl = (int)(idx % Q);
+    const int ky = wfreq_rt(R, sl >> 5, sl & 31);
+    double sr[2 * L + 1], si[2 * L + 1];
+#pragma unroll
+    for (int m = 0; m <= 2 * L; ++m) {
+        const double2 v = S64[((long)kx * NCH + m) * Q + ky];
+        sr[m] = v.x;
+        si[m] = v.y;
+    }
+    double2 A[NCH][NCH];  // I - T, then its inverse (Gauss-Jordan in place)
+    for (int cp = 0; cp < NCH; ++cp) {
+        double2 in[NCH], o[NCH];
+        for (int c = 0; c < NCH; ++c) in[c] = make_double2(c == cp ? 1.0 : 0.0, 0.0);
+        mode_mix<L, double2>(sr, si, in, o);
+        const double w = rp.wk[ch_mode(cp)] * Q2;
+        for (int c = 0; c < NCH; ++c) A[c][cp] = make_double2((c == cp ? 1.0 : 0.0) - w * o[c].x, -w * o[c].y);
+    }
+    double2 Inv[NCH][NCH];
+    for (int r = 0; r < NCH; ++r)
+        for (int c = 0; c < NCH; ++c) Inv[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    for (int col = 0; col < NCH; ++col) {
+        int piv = col;
+        double best = hypot(A[col][col].x, A[col][col].y);
+        for (int r = col + 1; r < NCH; ++r) {
+            const double a = hypot(A[r][col].x, A[r][col].y);
+            if (a > best) { best = a; piv = r; }
+        }
+        if (piv != col) {
+            for (int c = 0; c < NCH; ++c) {
+                double2 t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t;
+                t = Inv[col][c]; Inv[col][c] = Inv[piv][c]; Inv[piv][c] = t;
+            }
+        }
+        const double2 d = A[col][col];
+        const double dd = d.x * d.x + d.y * d.y;
+        const double2 inv = make_double2(d.x / dd, -d.y / dd);
+        for (int c = 0; c < NCH; ++c) {
+            A[col][c] = cmul(A[col][c], inv);
+            Inv[col][c] = cmul(Inv[col][c], inv);
+        }
+        for (int r = 0; r < NCH; ++r) {
+            if (r == col) continue;
+            const double2 f = A[r][col];
+            for (int c = 0; c < NCH; ++c) {
+                A[r][c] = csub(A[r][c], cmul(f, A[col][c]));
+                Inv[r][c] = csub(Inv[r][c], cmul(f, Inv[col][c]));
+            }
+        }
+    }
+    for (int c = 0; c < NCH; ++c)
+        for (int cp = 0; cp < NCH; ++cp) {
+            const bool im = ((ch_mode(c) ^ ch_mode(cp)) & 1) != 0;
+            const double v = (im ? Inv[c][cp].y : Inv[c][cp].x) / Q2;
+            Pp[(((long)kx * NCH + c) * NCH + cp) * Q + sl] = __float2bfloat16_rn((float)v);
+        }
+}
+
+// column pass of the preconditioner: FFT_y of every channel, per slot the
+// dense tagged (2L+1)^2 product with Pp, inverse FFT_y (as k_col_warp)
+template <int L, int R>
+__global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb, const __nv_bfloat16* __restrict__ Pp,
+                                                     const float2* __restrict__ tw, int n, int H) {
+    constexpr int NCH = 2 * L + 1;
+    constexpr int Q = 32 * R;
+    constexpr int QS = wfft_shape<R>::SCRATCH;
+    extern __shared__ unsigned char smraw[];
+    float2* X = reinterpret_cast<float2*>(smraw);  // [NCH][QS]
+    const int kx = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < NCH; c += nw) {
+        float2 v[R];
+        const float2* col = Tb + ((long)c * H + kx) * n;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = lane + 32 * r;
+            v[r] = y < n ? col[y] : make_float2(0.f, 0.f);
+        }
+        float2* Xc = X + (long)c * QS;
+        warp_fft_fwd<R>(v, tw, Xc);
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
+    }
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < Q; sl += blockDim.x) {
+        float2 in[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * QS + sl];
+        const __nv_bfloat16* P = Pp + (long)kx * NCH * NCH * Q + sl;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int cp = 0; cp < NCH; ++cp) {
+                const float v = __bfloat162float(P[(long)(c * NCH + cp) * Q]);
+                if ((ch_mode(c) ^ ch_mode(cp)) & 1) {  // entry i v
+                    acc.x -= v * in[cp].y;
+                    acc.y += v * in[cp].x;
+                } else {
+                    acc.x += v * in[cp].x;
+                    acc.y += v * in[cp].y;
+                }
+            }
+            X[(long)c * QS + sl] = acc;
+        }
+    }
+    __syncthreads();
+    for (int c = warp; c < NCH; c += nw) {
+        float2 v[R];
+        float2* Xc = X + (long)c * QS;
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) v[k1] = Xc[k1 * 32 + lane];
+        __syncwarp();
+        warp_fft_inv<R>(v, tw, Xc);
+        float2* col = Tb + ((long)c * H + kx) * n;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = lane + 32 * r;
+            if (y < n) col[y] = v[r];
+        }
+    }
+}
+
+template <int L, int R>
+static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
+                                 cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_col_warp_pc<L, R>)) != cudaSuccess) return e;
+        once = true;
+    }
+    const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2);
+    k_col_warp_pc<L, R><<<H, 256, smem, s>>>(Tb, Pp, tw, n, H);
+    return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_col_pc_q(int Q, float2* Tb, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
+                                   cudaStream_t s) {
+    switch (Q) {
+        case 64: return launch_col_pc<L, 2>(Tb, Pp, tw, n, H, s);
+        case 128: return launch_col_pc<L, 4>(Tb, Pp, tw, n, H, s);
+        case 256: return launch_col_pc<L, 8>(Tb, Pp, tw, n, H, s);
+        case 512: return launch_col_pc<L, 16>(Tb, Pp, tw, n, H, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int L>
+static cudaError_t build_pc2d(rte_plan p, const RowParams& rp, cudaStream_t s) {
+    const long tot = (long)p->H * p->Q;
+    k_build_pc2d<L><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(p->S64, p->Pp, p->H, p->Q, p->Q / 32, rp,
+                                                                  (double)p->Q * p->Q);
+    return cudaGetLastError();
+}
+
+static RowParams pc_rowparams(rte_plan p, bool unit) {
+    RowParams rp;
+    rp.n = p->n; rp.Q = p->Q; rp.H = p->H; rp.L = p->L;
+    rp.RB = 8;
+    rp.sc = p->sched;
+    for (int k = 0; k <= RTE_MAX_L; ++k) rp.wk[k] = 0.0;
+    for (int k = 0; k <= p->L; ++k) rp.wk[k] = unit ? 1.0 : p->mu_s * p->sigma_hat[k];
+    return rp;
+}
+
+bool plan_precond_supported(const rte_plan p) {
+    return p->dim == 3 || col_warp_ok(p->Q);
+}
+
+// builds the preconditioner data once per plan (allocates; call outside any capture)
+rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
+    if (p->pc_ready) return RTE_OK;
+    if (!plan_precond_supported(p)) return RTE_EUNSUPPORTED;
+    cudaError_t e = cudaSuccess;
+    if (!p->pv1 && cudaMalloc((void**)&p->pv1, p->nr * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond buffer");
+    if (!p->pv2 && cudaMalloc((void**)&p->pv2, p->nr * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond buffer");
+    if (p->dim == 3) {
+        const long tot = (long)p->H * p->H * p->H;
+        if (cudaMalloc((void**)&p->S3p, tot * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond spectrum");
+        const double Q3 = (double)p->Q * p->Q * p->Q;
+        k_build_pc3d<<<1024, 256, 0, s>>>(p->S3_64, p->S3p, tot, p->mu_s, Q3);
+        e = cudaGetLastError();
+    } else {
+        const long tot = (long)p->H * p->Q * p->nch * p->nch;
+        if (cudaMalloc((void**)&p->Pp, tot * sizeof(__nv_bfloat16)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond matrices");
+        const RowParams rp = pc_rowparams(p, false);
+        switch (p->L) {
+            case 0: e = build_pc2d<0>(p, rp, s); break;
+            case 1: e = build_pc2d<1>(p, rp, s); break;
+            case 2: e = build_pc2d<2>(p, rp, s); break;
+            case 3: e = build_pc2d<3>(p, rp, s); break;
+            case 4: e = build_pc2d<4>(p, rp, s); break;
+            case 5: e = build_pc2d<5>(p, rp, s); break;
+            case 6: e = build_pc2d<6>(p, rp, s); break;
+            case 7: e = build_pc2d<7>(p, rp, s); break;
+            case 8: e = build_pc2d<8>(p, rp, s); break;
+        }
+    }
+    rte_count_launches(1);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "plan_precond_build");
+    p->pc_ready = true;
+    return RTE_OK;
+}
+
+// out = M x (FP32 fields, the plan's FP32 layout); the plan's pass buffers
+rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t s) {
+    if (!p->pc_ready) return RTE_EINVAL;
+    cudaError_t e;
+    if (p->dim == 3) {
+        e = op3d_run_pc32(p, x, out, s);
+    } else {
+        const RowParams rp = pc_rowparams(p, true);
+        float2* Tb = (float2*)p->T32;
+        const dim3 grid((p->n + 7) / 8, p->L + 1);
+        e = row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
+        if (e == cudaSuccess) {
+            switch (p->L) {
+                case 0: e = launch_col_pc_q<0>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 1: e = launch_col_pc_q<1>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 2: e = launch_col_pc_q<2>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 3: e = launch_col_pc_q<3>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 4: e = launch_col_pc_q<4>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 5: e = launch_col_pc_q<5>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 6: e = launch_col_pc_q<6>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 7: e = launch_col_pc_q<7>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                case 8: e = launch_col_pc_q<8>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
+                default: e = cudaErrorInvalidValue;
+            }
+        }
+        if (e == cudaSuccess)
+            e = row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
+                                             0.f, s);
+        rte_count_launches(3);
+    }
+    if (e != cudaSuccess) return rte_cuda_fail(e, "plan_apply_pc32");
+    return RTE_OK;
+}

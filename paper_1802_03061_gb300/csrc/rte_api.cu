@@ -97,7 +97,7 @@ extern "C" rte_status rte_destroy(rte_plan p) {
     if (!p) return RTE_OK;
     cudaDeviceSynchronize();
     krylov_free(p);
-    void* bufs[] = {p->tw64, p->tw32, p->twff, p->Sff, p->Sffp, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
+    void* bufs[] = {p->S3p, p->Pp, p->pv1, p->pv2, p->tw64, p->tw32, p->twff, p->Sff, p->Sffp, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
                     p->d32, p->dscal, p->part64, p->f_dev, p->u_dev, p->ref};
     for (void* b : bufs)
@@ -268,6 +268,14 @@ extern "C" rte_status rte_apply_K64e(rte_plan p, const void* x, void* y, void* s
 extern "C" rte_status rte_apply_K32(rte_plan p, const void* x, void* y, void* stream) {
     if (!p || !x || !y || x == y) return RTE_EINVAL;
     return plan_apply32(p, (const float*)x, (float*)y, 0.0f, 1.0f, 0.0f, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_apply_precond32(rte_plan p, const void* x, void* y, void* stream) {
+    if (!p || !x || !y || x == y) return RTE_EINVAL;
+    if (!plan_precond_supported(p)) return RTE_EUNSUPPORTED;
+    rte_status st = plan_precond_build(p, (cudaStream_t)stream);
+    if (st != RTE_OK) return st;
+    return plan_apply_pc32(p, (const float*)x, (float*)y, (cudaStream_t)stream);
 }
 
 extern "C" rte_status rte_rhs(rte_plan p, const double* f, void* b, void* stream) {
