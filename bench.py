@@ -200,7 +200,7 @@ def run_native(args):
     base = rte_synth.hg2d_transport()
     n, L = base["n"], len(base["sigma_hat"]) - 1
     plan = Plan(n, mu_t=base["mu_t"], mu_s=base["mu_s"], sigma_hat=base["sigma_hat"], prec=args.prec, tol=1e-8,
-                restart=args.restart, inner_tol=args.inner_tol)
+                restart=args.restart, inner_tol=args.inner_tol, precond=args.precond)
     t_pre_ms = None
     nsteps = args.steps + args.warmup
     # inputs resident in HBM before timing: one seeded source per step
@@ -259,6 +259,21 @@ def run_native(args):
         fp64_ms.append(e0.elapsed_time(e1))
         fp64_its.append(st["iters"])
 
+    # the same problems with the other preconditioner setting (the paper's
+    # GMRES has none)
+    alt_ms, alt_its = [], []
+    if args.prec != "fp64":
+        alt = 1 - args.precond
+        plan.solve(srcs[0], precond=alt)
+        for i in range(min(5, args.steps)):
+            flush.zero_()
+            e0.record(stream)
+            _, st = plan.solve(srcs[args.warmup + i], precond=alt)
+            e1.record(stream)
+            e1.synchronize()
+            alt_ms.append(e0.elapsed_time(e1))
+            alt_its.append(st["iters"])
+
     # the same problems with BF16 inner spectra (best inner tolerance for them)
     bf16_ms = []
     bf16_its = []
@@ -311,6 +326,13 @@ def run_native(args):
                    "all_converged": ok, "fp64_ms_per_solve": float(np.mean(fp64_ms)),
                    "fp64_iters": float(np.mean(fp64_its)),
                    "speedup_vs_fp64": float(np.mean(fp64_ms)) / ms_per_step,
+                   "precond": bool(args.precond and args.prec != "fp64"),
+                   ("unpreconditioned" if args.precond else "preconditioned") + "_ms_per_solve":
+                       float(np.mean(alt_ms)) if alt_ms else None,
+                   ("unpreconditioned" if args.precond else "preconditioned") + "_iters":
+                       float(np.mean(alt_its)) if alt_its else None,
+                   "pass_ms_precond": B.rte_time_passes(plan.handle, 3, reps, int(stream.cuda_stream))
+                   if args.prec != "fp64" else None,
                    "bf16_spectra_ms_per_solve": float(np.mean(bf16_ms)) if bf16_ms else None,
                    "bf16_spectra_iters": float(np.mean(bf16_its)) if bf16_its else None,
                    "pass_ms_fp32": ms32, "pass_ms_fp64": ms64,
@@ -401,7 +423,7 @@ def run_batch(args):
     # instances are independent: each rank solves a cost-balanced share
     inst = [all_inst[i] for i in replicas.shard(all_inst, ws, rank)]
     t0 = time.perf_counter()
-    b = Batch(inst, prec="mixed_fp32", tol=1e-8, restart=30, maxit=4000, tune=True)
+    b = Batch(inst, prec="mixed_fp32", tol=1e-8, restart=30, maxit=4000, tune=True, precond=args.precond)
     t_create = time.perf_counter() - t0
     f = b.pack_sources([d["f"] for d in inst])
     u = torch.zeros(b.u_off[-1], dtype=torch.float64, device="cuda")
@@ -457,6 +479,9 @@ def run_batch(args):
                                    "mu_s/mu_t U[0.5,0.99], HG g U[0,0.8], 1-6 Gaussians; one graph launch; tol 1e-8",
                        "all_converged": conv, "iters_total": int(sum(s_["iters"] for s_ in stats)),
                        "sequential_single_solves_ms": seq_ms,
+                       "precond": bool(args.precond),
+                       "precond_note": "periodic preconditioner on instances whose padded side Q is 64, 128, 256 "
+                                       "or 512; none on the others" if args.precond else None,
                        "instances_on_rank0": len(inst), "parallelism": "instances sharded by cost" if ws > 1
                        else "single GPU",
                        "create_s": t_create, "l2": "flushed before every timed step"},
@@ -482,7 +507,7 @@ def run_iso3d(args):
     prob = rte_synth.iso3d_diffusion()
     n = prob["n"]
     plan = Plan(n, mu_t=prob["mu_t"], mu_s=prob["mu_s"], sigma_hat=[1.0], dim=3, prec=args.prec, tol=1e-8,
-                restart=60, maxit=4000, inner_tol=args.inner_tol)
+                restart=60, maxit=4000, inner_tol=args.inner_tol, precond=args.precond)
     srcs = [torch.from_numpy(rte_synth.iso3d_diffusion(seed=3 + i)["f"]).cuda() for i in range(args.steps + args.warmup)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for i in range(args.warmup):
@@ -504,13 +529,26 @@ def run_iso3d(args):
         stats.append(st)
     launches = B.rte_kernel_launches() - l0
     clk = clocks.stop()
-    # the same solves with MINRES inner solves (the operator is symmetric for L = 0)
-    plan.solve(srcs[0], inner_solver="minres")
+    # the other preconditioner setting
+    alt = 1 - args.precond
+    plan.solve(srcs[0], precond=alt)
+    a_ms, a_its = [], []
+    for i in range(args.warmup, args.warmup + min(5, args.steps)):
+        flush.zero_()
+        e0.record(stream)
+        _, st = plan.solve(srcs[i], precond=alt)
+        e1.record(stream)
+        e1.synchronize()
+        a_ms.append(e0.elapsed_time(e1))
+        a_its.append(st["iters"])
+    # the same solves with MINRES inner solves (the operator is symmetric for
+    # L = 0; unpreconditioned)
+    plan.solve(srcs[0], inner_solver="minres", precond=0)
     g_ms, g_its = [], []
     for i in range(args.warmup, args.warmup + min(5, args.steps)):
         flush.zero_()
         e0.record(stream)
-        _, st = plan.solve(srcs[i], inner_solver="minres")
+        _, st = plan.solve(srcs[i], inner_solver="minres", precond=0)
         e1.record(stream)
         e1.synchronize()
         g_ms.append(e0.elapsed_time(e1))
@@ -553,6 +591,10 @@ def run_iso3d(args):
                        "all_converged": all(s_["converged"] for s_ in stats),
                        "relres_max": max(s_["relres_true"] for s_ in stats),
                        "inner_solver": "GMRES",
+                       "precond": bool(args.precond and args.prec != "fp64"),
+                       ("unpreconditioned" if args.precond else "preconditioned") + "_ms_per_solve":
+                           float(np.mean(a_ms)),
+                       ("unpreconditioned" if args.precond else "preconditioned") + "_iters": float(np.mean(a_its)),
                        "minres_inner_ms_per_solve": float(np.mean(g_ms)), "minres_inner_iters": float(np.mean(g_its)),
                        "matvec_fp32_ms": mv32, "matvec_fp64_ms": mv64, "matvec_float_float_ms": mv64e,
                        "cufft_comparator_ms": cufft_ms,
@@ -654,19 +696,25 @@ def run_learned(args):
 
 
 def run_profile_solve(args):
-    """One plan, one warm-up solve, one solve: a clean launch list for ncu."""
+    """One plan, one warm-up solve, one solve: a clean launch list for ncu.
+    With the preconditioner on, its three passes are also launched twice on
+    their own (kernels inside the solve graph's conditional nodes are not
+    profiled)."""
     import torch
 
     import rte_synth
     from paper_1802_03061_gb300 import Plan
+    from paper_1802_03061_gb300 import _binding as B
     from paper_1802_03061_gb300 import build as _build
 
     torch.cuda.set_device(0)
     _build.build()
     base = rte_synth.hg2d_transport()
     plan = Plan(base["n"], mu_t=base["mu_t"], mu_s=base["mu_s"], sigma_hat=base["sigma_hat"], prec=args.prec,
-                tol=1e-8, restart=args.restart, inner_tol=args.inner_tol)
+                tol=1e-8, restart=args.restart, inner_tol=args.inner_tol, precond=args.precond)
     f = torch.from_numpy(base["f"]).cuda()
+    if args.precond and args.prec != "fp64":
+        B.rte_time_passes(plan.handle, 3, 2, int(torch.cuda.current_stream().cuda_stream))
     plan.solve(f)
     torch.cuda.synchronize()
     _, st = plan.solve(f)
@@ -684,6 +732,8 @@ def main():
     ap.add_argument("--prec", default="mixed_fp32", choices=["mixed_bf16", "mixed_fp32", "fp64"])
     ap.add_argument("--restart", type=int, default=40)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--precond", type=int, default=1, choices=[0, 1],
+                    help="periodic circulant right preconditioner in the FP32 inner solves (not in the paper)")
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="hg2d_transport",

@@ -276,8 +276,9 @@ rte_status rte_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, double*
  * FFT), [2] inverse row pass -- over `reps` back-to-back launches, timed with
  * CUDA events on cuda_stream.  inner = 0 times the FP64 passes, inner = 1 the
  * FP32 passes with the plan's inner spectra, inner = 2 the float-float passes
- * of rte_apply_K64e.  Operates on plan-owned scratch
- * vectors.  2D plans only (RTE_EUNSUPPORTED for 3D).
+ * of rte_apply_K64e, inner = 3 the passes of rte_apply_precond32 (building
+ * the preconditioner first if needed: allocates).  Operates on plan-owned
+ * scratch vectors.  2D plans only (RTE_EUNSUPPORTED for 3D).
  * rte_kernel_launches: number of kernels this library has launched so far in
  * the process (host-side counter; a replayed graph adds its kernel nodes). */
 rte_status rte_time_passes(rte_plan plan, int inner, int reps, double* ms_out_host, void* cuda_stream);

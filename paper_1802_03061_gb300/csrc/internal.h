@@ -147,6 +147,7 @@ rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, 
 bool plan_precond_supported(const rte_plan p);
 rte_status plan_precond_build(rte_plan p, cudaStream_t s);
 rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t s);
+rte_status plan_time_pc(rte_plan p, int reps, double* ms, cudaStream_t s);
 cudaError_t op3d_run_pc32(rte_plan p, const float* x, float* out, cudaStream_t s);
 rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);

@@ -15,13 +15,28 @@
 // T(xi) has entries that are purely real or purely imaginary, imaginary
 // exactly when the modes of the two channels differ in parity (see the mode
 // mix in op2d.cuh), so with Phi = diag(i^{parity}) the matrix Phi^-1 T Phi is
-// real and (I - T)^{-1} has the same pattern: one real number per entry.  They
-// are stored in BF16 (the preconditioner only has to be close, not exact) as
-// Pp[xi_x][c][c'][slot], slot order of the warp column pass, and scaled by
-// 1/Q^2 for the unnormalised transforms of the passes.
+// real and (I - T)^{-1} has the same pattern: one real number per entry.
+// Mirroring xi_y -> -xi_y reverses the angle of every kernel sample, which maps
+// mode k to -k; on the real channels (A_k, B_k) = ((u_k + u_-k)/2,
+// (u_k - u_-k)/2i) that is A -> A, B -> -B, so (I - T(xi_x, -xi_y))^{-1} =
+// S (I - T(xi_x, xi_y))^{-1} S with S = diag(+1 on A, -1 on B).  Only xi_y in
+// [0, Q/2] is stored, in BF16 (the preconditioner only has to be close, not
+// exact), as Pp[xi_x][c][c'][xi_y] with rows of pc_row(Q) = Q/2 + 8 entries,
+// scaled by 1/Q^2 for the unnormalised transforms of the passes.
 #include "op2d_launch.cuh"
 
 __host__ __device__ __forceinline__ int ch_mode(int c) { return (c + 1) >> 1; }
+__host__ __device__ __forceinline__ bool ch_isB(int c) { return c > 0 && !(c & 1); }
+// table row length (xi_y = 0..Q/2, padded to 16 bytes)
+__host__ __device__ __forceinline__ int pc_row(int Q) { return Q / 2 + 8; }
+
+// slot (j * 32 + lane) of the warp FFT that holds frequency xi: the inverse
+// of wfreq<R>
+template <int R> __device__ __forceinline__ int wslot(int xi) {
+    using W = wfft_shape<R>;
+    const int b = (int)(__brev((unsigned)(xi / (R * R))) >> (32 - W::LP));
+    return ((xi / R) % R) * 32 + (((xi % R) << W::LP) | b);
+}
 
 // 3D: S3p = (1/Q^3) / (1 - mu_s Q^3 S3)  (S3 already holds FFT(g) / Q^3)
 __global__ void k_build_pc3d(const double* __restrict__ S3, float* __restrict__ S3p, long tot, double mu_s,
@@ -30,17 +45,17 @@ __global__ void k_build_pc3d(const double* __restrict__ S3, float* __restrict__ 
         S3p[i] = (float)((1.0 / Q3) / (1.0 - mu_s * Q3 * S3[i]));
 }
 
-// 2D: one thread per (xi_x, slot).  T[c][c'] = Q^2 * mix(S(xi))[c][c'] * w(c')
-// with w = mu_s sigma_hat_{k(c')} (the row pass's input weights); Gauss-Jordan
-// with partial pivoting on I - T in complex FP64.
+// 2D: one thread per (xi_x, xi_y), xi_y = 0..Q/2.  T[c][c'] = Q^2 *
+// mix(S(xi))[c][c'] * w(c') with w = mu_s sigma_hat_{k(c')} (the row pass's
+// input weights); Gauss-Jordan with partial pivoting on I - T in complex FP64.
 template <int L>
-__global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __restrict__ Pp, int H, int Q, int R,
+__global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __restrict__ Pp, int H, int Q,
                              RowParams rp, double Q2) {
     constexpr int NCH = 2 * L + 1;
+    const int QH = Q / 2 + 1, QR = pc_row(Q);
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)H * Q) return;
-    const int kx = (int)(idx / Q), sl = (int)(idx % Q);
-    const int ky = wfreq_rt(R, sl >> 5, sl & 31);
+    if (idx >= (long)H * QH) return;
+    const int kx = (int)(idx / QH), ky = (int)(idx % QH);
     double sr[2 * L + 1], si[2 * L + 1];
 #pragma unroll
     for (int m = 0; m <= 2 * L; ++m) {
@@ -92,22 +107,94 @@ __global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __r
         for (int cp = 0; cp < NCH; ++cp) {
             const bool im = ((ch_mode(c) ^ ch_mode(cp)) & 1) != 0;
             const double v = (im ? Inv[c][cp].y : Inv[c][cp].x) / Q2;
-            Pp[(((long)kx * NCH + c) * NCH + cp) * Q + sl] = __float2bfloat16_rn((float)v);
+            Pp[(((long)kx * NCH + c) * NCH + cp) * QR + ky] = __float2bfloat16_rn((float)v);
         }
 }
 
-// column pass of the preconditioner: FFT_y of every channel, per slot the
-// dense tagged (2L+1)^2 product with Pp, inverse FFT_y (as k_col_warp)
+// y[c] += sum_c' P[c][c'] x[c'] for one frequency (tagged entries: i v when
+// the channel modes differ in parity); sg = -1 mirrors (S P S)
+template <int L>
+__device__ __forceinline__ void pc_mix_one(float2* X, int QS, int sl, const __nv_bfloat16* P, int QR) {
+    constexpr int NCH = 2 * L + 1;
+    float2 in[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) in[c] = X[c * QS + sl];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int cp = 0; cp < NCH; ++cp) {
+            const float v = __bfloat162float(P[(c * NCH + cp) * QR]);
+            if ((ch_mode(c) ^ ch_mode(cp)) & 1) {
+                acc.x -= v * in[cp].y;
+                acc.y += v * in[cp].x;
+            } else {
+                acc.x += v * in[cp].x;
+                acc.y += v * in[cp].y;
+            }
+        }
+        X[c * QS + sl] = acc;
+    }
+}
+
+// the pair (xi, Q - xi): one load of P serves both, the mirror with S P S
+template <int L>
+__device__ __forceinline__ void pc_mix_pair(float2* X, int QS, int s1, int s2, const __nv_bfloat16* P, int QR) {
+    constexpr int NCH = 2 * L + 1;
+    float2 a[NCH], b[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        a[c] = X[c * QS + s1];
+        b[c] = X[c * QS + s2];
+    }
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int cp = 0; cp < NCH; ++cp) {
+            const float v = __bfloat162float(P[(c * NCH + cp) * QR]);
+            const float w = ch_isB(c) != ch_isB(cp) ? -v : v;
+            if ((ch_mode(c) ^ ch_mode(cp)) & 1) {
+                ra.x -= v * a[cp].y;
+                ra.y += v * a[cp].x;
+                rb.x -= w * b[cp].y;
+                rb.y += w * b[cp].x;
+            } else {
+                ra.x += v * a[cp].x;
+                ra.y += v * a[cp].y;
+                rb.x += w * b[cp].x;
+                rb.y += w * b[cp].y;
+            }
+        }
+        X[c * QS + s1] = ra;
+        X[c * QS + s2] = rb;
+    }
+}
+
+// column pass of the preconditioner: FFT_y of every channel, per frequency
+// the dense tagged (2L+1)^2 product with Pp, inverse FFT_y (as k_col_warp).
+// The block's slice of Pp is prefetched into L2 while the forward FFTs run.
 template <int L, int R>
 __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb, const __nv_bfloat16* __restrict__ Pp,
                                                      const float2* __restrict__ tw, int n, int H) {
     constexpr int NCH = 2 * L + 1;
     constexpr int Q = 32 * R;
+    constexpr int QR = Q / 2 + 8;
     constexpr int QS = wfft_shape<R>::SCRATCH;
+    constexpr unsigned SLICE = NCH * NCH * QR * 2;  // bytes, a multiple of 16
+    constexpr unsigned CHUNK = 16384;
     extern __shared__ unsigned char smraw[];
     float2* X = reinterpret_cast<float2*>(smraw);  // [NCH][QS]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * NCH * QR;
+    if (warp == nw - 1) {
+        const char* base = reinterpret_cast<const char*>(Pk);
+        for (unsigned off = lane * CHUNK; off < SLICE; off += 32 * CHUNK) {
+            const unsigned sz = SLICE - off < CHUNK ? SLICE - off : CHUNK;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(sz) : "memory");
+        }
+    }
     for (int c = warp; c < NCH; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;
@@ -122,26 +209,12 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
         for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
     }
     __syncthreads();
-    for (int sl = threadIdx.x; sl < Q; sl += blockDim.x) {
-        float2 in[NCH];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * QS + sl];
-        const __nv_bfloat16* P = Pp + (long)kx * NCH * NCH * Q + sl;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int cp = 0; cp < NCH; ++cp) {
-                const float v = __bfloat162float(P[(long)(c * NCH + cp) * Q]);
-                if ((ch_mode(c) ^ ch_mode(cp)) & 1) {  // entry i v
-                    acc.x -= v * in[cp].y;
-                    acc.y += v * in[cp].x;
-                } else {
-                    acc.x += v * in[cp].x;
-                    acc.y += v * in[cp].y;
-                }
-            }
-            X[(long)c * QS + sl] = acc;
+    for (int t = threadIdx.x; t < Q / 2; t += blockDim.x) {
+        if (t == 0) {  // xi = 0 and xi = Q/2 are their own mirrors
+            pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR);
+            pc_mix_one<L>(X, QS, wslot<R>(Q / 2), Pk + Q / 2, QR);
+        } else {
+            pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(Q - t), Pk + t, QR);
         }
     }
     __syncthreads();
@@ -189,8 +262,8 @@ static cudaError_t launch_col_pc_q(int Q, float2* Tb, const __nv_bfloat16* Pp, c
 
 template <int L>
 static cudaError_t build_pc2d(rte_plan p, const RowParams& rp, cudaStream_t s) {
-    const long tot = (long)p->H * p->Q;
-    k_build_pc2d<L><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(p->S64, p->Pp, p->H, p->Q, p->Q / 32, rp,
+    const long tot = (long)p->H * (p->Q / 2 + 1);
+    k_build_pc2d<L><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(p->S64, p->Pp, p->H, p->Q, rp,
                                                                   (double)p->Q * p->Q);
     return cudaGetLastError();
 }
@@ -223,8 +296,10 @@ rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
         k_build_pc3d<<<1024, 256, 0, s>>>(p->S3_64, p->S3p, tot, p->mu_s, Q3);
         e = cudaGetLastError();
     } else {
-        const long tot = (long)p->H * p->Q * p->nch * p->nch;
+        const long tot = (long)p->H * pc_row(p->Q) * p->nch * p->nch;
         if (cudaMalloc((void**)&p->Pp, tot * sizeof(__nv_bfloat16)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond matrices");
+        if ((e = cudaMemsetAsync(p->Pp, 0, tot * sizeof(__nv_bfloat16), s)) != cudaSuccess)
+            return rte_cuda_fail(e, "plan_precond_build");
         const RowParams rp = pc_rowparams(p, false);
         switch (p->L) {
             case 0: e = build_pc2d<0>(p, rp, s); break;
@@ -244,36 +319,67 @@ rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
     return RTE_OK;
 }
 
+// one pass of the 2D application: 0 row, 1 column (mix with Pp), 2 inverse row
+static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cudaStream_t s) {
+    const RowParams rp = pc_rowparams(p, true);
+    float2* Tb = (float2*)p->T32;
+    const dim3 grid((p->n + 7) / 8, p->L + 1);
+    if (st == 0) return row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
+    if (st == 2)
+        return row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
+                                            0.f, s);
+    switch (p->L) {
+        case 0: return launch_col_pc_q<0>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 1: return launch_col_pc_q<1>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 2: return launch_col_pc_q<2>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 3: return launch_col_pc_q<3>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 4: return launch_col_pc_q<4>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 5: return launch_col_pc_q<5>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 6: return launch_col_pc_q<6>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 7: return launch_col_pc_q<7>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 8: return launch_col_pc_q<8>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // out = M x (FP32 fields, the plan's FP32 layout); the plan's pass buffers
 rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t s) {
     if (!p->pc_ready) return RTE_EINVAL;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if (p->dim == 3) {
         e = op3d_run_pc32(p, x, out, s);
     } else {
-        const RowParams rp = pc_rowparams(p, true);
-        float2* Tb = (float2*)p->T32;
-        const dim3 grid((p->n + 7) / 8, p->L + 1);
-        e = row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
-        if (e == cudaSuccess) {
-            switch (p->L) {
-                case 0: e = launch_col_pc_q<0>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 1: e = launch_col_pc_q<1>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 2: e = launch_col_pc_q<2>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 3: e = launch_col_pc_q<3>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 4: e = launch_col_pc_q<4>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 5: e = launch_col_pc_q<5>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 6: e = launch_col_pc_q<6>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 7: e = launch_col_pc_q<7>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                case 8: e = launch_col_pc_q<8>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s); break;
-                default: e = cudaErrorInvalidValue;
-            }
-        }
-        if (e == cudaSuccess)
-            e = row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
-                                             0.f, s);
+        for (int st = 0; st < 3 && e == cudaSuccess; ++st) e = pc2d_pass(p, st, x, out, s);
         rte_count_launches(3);
     }
     if (e != cudaSuccess) return rte_cuda_fail(e, "plan_apply_pc32");
+    return RTE_OK;
+}
+
+// average ms of each 2D pass over reps back-to-back launches (plan scratch)
+rte_status plan_time_pc(rte_plan p, int reps, double* ms, cudaStream_t s) {
+    if (p->dim != 2) return RTE_EUNSUPPORTED;
+    rte_status st0 = plan_precond_build(p, s);
+    if (st0 != RTE_OK) return st0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return rte_fail(RTE_ECUDA, "plan_time_pc");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return rte_fail(RTE_ECUDA, "plan_time_pc");
+    }
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = pc2d_pass(p, st, p->pv1, p->pv2, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[st] = t / reps;
+    }
+    rte_count_launches(3L * reps);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "plan_time_pc");
     return RTE_OK;
 }

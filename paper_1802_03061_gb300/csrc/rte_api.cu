@@ -30,6 +30,7 @@ extern "C" rte_status rte_time_passes(rte_plan p, int inner, int reps, double* m
     cudaStream_t s = (cudaStream_t)stream;
     if (p->dim != 2) return RTE_EUNSUPPORTED;
     if (inner == 2) return op2d_time_ff(p, reps, ms_out, s);
+    if (inner == 3) return plan_time_pc(p, reps, ms_out, s);
     return inner ? op2d_time32(p, reps, ms_out, s) : op2d_time64(p, reps, ms_out, s);
 }
 

@@ -56,7 +56,8 @@ def _ref_precond_2d(n, Q, mu_t, mu_s, sig, x_full):
     return np.fft.ifft2(np.moveaxis(Y, -1, 0), axes=(1, 2))[:, :n, :n]
 
 
-@pytest.mark.parametrize("n,L,q", [(12, 2, 64), (20, 1, 128), (9, 3, 64)])
+@pytest.mark.parametrize("n,L,q", [(12, 2, 64), (20, 1, 128), (9, 3, 64), (12, 8, 64), (16, 4, 256),
+                                   (10, 2, 512), (7, 0, 512)])
 def test_precond_apply_2d_matches_reference(n, L, q):
     mu_t, mu_s = 10.0, 9.0
     sig = rte_synth.hg_sigma_hat(0.5, L)
