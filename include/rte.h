@@ -131,8 +131,8 @@ rte_status rte_apply_A(rte_plan plan, const void* x_dev, void* y_dev, void* cuda
 
 /* y = K x to FP64 accuracy computed in float-float arithmetic (pairs of
  * FP32 numbers, ~48 significant bits) on the FP32 units; this is how the
- * mixed-precision solve forms its right-hand side and residuals, because
- * FP64 units are scarce on this GPU.  Same layouts as rte_apply_K. */
+ * mixed-precision solve forms its residuals, because FP64 units are scarce on
+ * this GPU.  Same layouts as rte_apply_K. */
 rte_status rte_apply_K64e(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
 
 /* FP32 versions used by the inner solves of the mixed modes: x_dev, y_dev are
@@ -154,6 +154,10 @@ rte_status rte_rhs(rte_plan plan, const double* f_dev, void* b_dev, void* cuda_s
 
 /* Solve (I - K) u = K~ g (step T.2) for u.  f_dev: source; u_dev: FP64
  * field, read as the initial guess when opts->use_guess, else zeroed.
+ * Mixed modes: b = K~ g is formed in FP32 (the first inner right-hand side
+ * and ||b||), every residual in float-float as K~ (mu_s sigma_hat u + g) - u,
+ * which is b - (I - K) u for the exact b; stats->relres_true is its norm over
+ * ||b||.
  * opts NULL = the plan's options.  stats may be NULL.  Synchronises the
  * stream once at exit to fill stats. */
 rte_status rte_solve(rte_plan plan, const double* f_dev, void* u_dev, const rte_opts* opts,

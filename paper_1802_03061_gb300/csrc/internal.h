@@ -16,7 +16,10 @@ void rte_count_launches(long k);
 extern "C" long long rte_kernel_launches(void);
 
 // Which linear map a pass sequence applies (Sec. 3.3, steps T.1 and T.2).
-enum MixKind { MIX_K = 0, MIX_RHS = 1 };
+// MIX_K: K x;  MIX_RHS: K~ applied to the source f (mode 0);  MIX_KF: K x + K~ f
+// in one application (the source joins mode 0 of the input after the
+// mu_s sigma_hat weighting)
+enum MixKind { MIX_K = 0, MIX_RHS = 1, MIX_KF = 2 };
 
 // Krylov workspace of one precision.
 struct KrylovWs {
@@ -171,5 +174,8 @@ void fill_ref_template(void* host, const rte_opts* o);
 // dispatch helpers (rte_api.cu)
 rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b,
                         double c, const double* z, cudaStream_t s);
+rte_status op2d_rhs32(rte_plan p, float* out, cudaStream_t s);
+rte_status op3d_rhs32(rte_plan p, float* f32, float* out, cudaStream_t s);
+rte_status plan_rhs32(rte_plan p, float* out, cudaStream_t s);
 rte_status plan_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);

@@ -716,6 +716,12 @@ __global__ void k_add_T(T* __restrict__ x, const T* __restrict__ d, long nr) {
         x[e] += d[e];
 }
 
+// FP32 -> FP64 copy
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, long nr) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
+        dst[e] = (double)src[e];
+}
+
 template <typename T>
 __global__ void k_zero_T(T* __restrict__ dst, long nr) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
@@ -1277,10 +1283,23 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
     *info = SolveGraphInfo();
     // T.1 and start values
     // FP64-accurate applications: float-float on the FP32 units in the mixed
-    // mode, native FP64 in the plain FP64 mode
+    // mode, native FP64 in the plain FP64 mode.  The mixed mode forms b = K~ f
+    // in FP32 only (it is the first inner right-hand side and sets ||b||) and
+    // every residual as r = K~ (mu_s sigma_hat u + f) - u: one FP64-accurate
+    // application that equals b - (I - K) u with the exact b.
     auto apply64 = mixed ? plan_apply64e : plan_apply64;
+    auto residual = [&]() -> rte_status {
+        if (mixed) return apply64(p, MIX_KF, p->u_dev, p->r64, -1.0, 1.0, 0.0, nullptr, cs);
+        return apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs);
+    };
     SEG(g, dep, &info->k_fixed, {
-        TRYS(apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, cs));
+        if (mixed) {
+            TRYS(plan_rhs32(p, (float*)p->r32, cs));
+            k_widen<<<gr, 256, 0, cs>>>((const float*)p->r32, p->b64, nr);
+            rte_count_launches(1);
+        } else {
+            TRYS(apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, cs));
+        }
         TRYS(dev_norm<double>(p->b64, nr, nw1, p->part64, &ref->bnorm, cs));
         k_ref_start<<<1, 32, 0, cs>>>(ref, c_guess);
         k_zero_unless_guess<<<gr, 256, 0, cs>>>(p->u_dev, nr, ref);
@@ -1293,7 +1312,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
         TRYS(add_cond(g, &dep, c_guess, cudaGraphCondTypeIf, &body));
         cudaGraphNode_t d = nullptr;
         SEG(body, d, &info->k_guess, {
-            TRYS(apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+            TRYS(residual());
             TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
             k_guess_fallback<<<gr, 256, 0, cs>>>(p->u_dev, p->r64, p->b64, nr, ref);
             k_guess_fallback_state<<<1, 32, 0, cs>>>(ref);
@@ -1340,7 +1359,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
                 k_axpy_scaled<float><<<gr, 256, 0, cs>>>(p->u_dev, (const float*)x, nr, &ref->rnorm);
                 k_mr_after<<<1, 32, 0, cs>>>(ref, G.st);
                 rte_count_launches(2);
-                TRYS(apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+                TRYS(residual());
                 TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
                 k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
                 rte_count_launches(1);
@@ -1415,7 +1434,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
             }
             k_ref_after<<<1, 32, 0, cs>>>(ref, G.st);
             rte_count_launches(2);
-            TRYS(apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs));
+            TRYS(residual());
             TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
             k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
             rte_count_launches(1);

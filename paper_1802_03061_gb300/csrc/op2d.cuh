@@ -67,14 +67,15 @@ __global__ void __launch_bounds__(256) k_row_fwd(const TF* __restrict__ x, const
             if (k == 0) {
                 const int ya = y0 + 2 * li, yb = ya + 1;
                 R a = 0, b = 0;
-                if (f) {
-                    if (ya < n) a = (R)f[(long)ya * n + e];
-                    if (yb < n) b = (R)f[(long)yb * n + e];
-                } else {
-                    if (ya < n) a = (R)x[(long)ya * n + e].x;
-                    if (yb < n) b = (R)x[(long)yb * n + e].x;
+                if (x) {
+                    if (ya < n) a = w * (R)x[(long)ya * n + e].x;
+                    if (yb < n) b = w * (R)x[(long)yb * n + e].x;
                 }
-                v = mk<T>(w * a, w * b);
+                if (f) {  // the source joins unweighted (MIX_RHS: w = 1, no x)
+                    if (ya < n) a = a + (R)f[(long)ya * n + e];
+                    if (yb < n) b = b + (R)f[(long)yb * n + e];
+                }
+                v = mk<T>(a, b);
             } else {
                 const int y = y0 + li;
                 if (y < n) {
@@ -220,14 +221,15 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const TF* __restrict__ x, 
             if (k == 0) {
                 const int ya = y0 + 2 * w, yb = ya + 1;
                 RR a = (RR)0, b = (RR)0;
-                if (f) {
-                    if (ya < n) a = (RR)f[(long)ya * n + e];
-                    if (yb < n) b = (RR)f[(long)yb * n + e];
-                } else {
-                    if (ya < n) a = to_c<T>(x[(long)ya * n + e]).x;
-                    if (yb < n) b = to_c<T>(x[(long)yb * n + e]).x;
+                if (x) {
+                    if (ya < n) a = wt * to_c<T>(x[(long)ya * n + e]).x;
+                    if (yb < n) b = wt * to_c<T>(x[(long)yb * n + e]).x;
                 }
-                val = mk<T>(wt * a, wt * b);
+                if (f) {  // the source joins unweighted (MIX_RHS: no x)
+                    if (ya < n) a = a + (RR)f[(long)ya * n + e];
+                    if (yb < n) b = b + (RR)f[(long)yb * n + e];
+                }
+                val = mk<T>(a, b);
             } else {
                 const int y = y0 + w;
                 if (y < n) {

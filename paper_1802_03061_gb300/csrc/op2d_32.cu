@@ -20,6 +20,16 @@ rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b
     return RTE_OK;
 }
 
+// b = K~ f in FP32 (FP32 spectra): the inner solves' first right-hand side
+rte_status op2d_rhs32(rte_plan p, float* out, cudaStream_t s) {
+    cudaError_t e = op2d_run<float2, float2, float2>(p, MIX_RHS, nullptr, p->f_dev, reinterpret_cast<float2*>(out), 0.0, 1.0,
+                                             0.0, nullptr, reinterpret_cast<float2*>(p->T32),
+                                             reinterpret_cast<float2*>(p->Tsplit32), p->S32, p->tw32,
+                                             p->col_split32, s, -1, p->S32p);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_rhs32");
+    return RTE_OK;
+}
+
 rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s) {
     if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC) return op2d_time32_bf16(p, reps, ms, s);
     const float2* xx = reinterpret_cast<const float2*>(p->r32);

@@ -239,7 +239,8 @@ static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, cons
     return cudaGetLastError();
 }
 
-// out = a*x + b*(Op x) + c*z ; Op = K (MIX_K) or K~ on the source f (MIX_RHS)
+// out = a*x + b*(Op x) + c*z ; Op = K (MIX_K), K~ on the source f (MIX_RHS),
+// or K x + K~ f (MIX_KF)
 // stage: -1 all three passes; 0 row pass; 1 column pass; 2 inverse row pass
 template <typename T, typename TS, typename TF = T>
 static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double* f, TF* out, double a, double b,
@@ -260,12 +261,13 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         rp.RB = p->rb_force & ~1;
     rp.sc = p->sched;
     for (int k = 0; k <= RTE_MAX_L; ++k) rp.wk[k] = 0.0;
-    if (kind == MIX_K) {
+    const bool use_x = kind != MIX_RHS, use_f = kind != MIX_K;
+    if (use_x) {
         for (int k = 0; k <= p->L; ++k) rp.wk[k] = p->mu_s * p->sigma_hat[k];
     } else {
         rp.wk[0] = 1.0;
     }
-    const int nmod_in = kind == MIX_K ? p->L + 1 : 1;
+    const int nmod_in = use_x ? p->L + 1 : 1;
     const size_t smr = row_smem<T>(p->Q, rp.RB);
     bool row_warp = false;
     if constexpr (row_warp_types<T, TF>::value) row_warp = col_warp_ok(p->Q) && p->rb_force < 2;
@@ -273,13 +275,13 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         if (row_warp) {
             if constexpr (row_warp_types<T, TF>::value) {
                 const dim3 grid((p->n + 7) / 8, nmod_in);
-                if ((e = row_fwd_warp<T, TF>(p->Q, grid, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr,
+                if ((e = row_fwd_warp<T, TF>(p->Q, grid, use_x ? x : nullptr, use_f ? f : nullptr,
                                              Tb, tw, rp, s)) != cudaSuccess)
                     return e;
             }
         } else {
             const dim3 grid((p->n + rp.RB - 1) / rp.RB, nmod_in);
-            k_row_fwd<T, TF><<<grid, 256, smr, s>>>(kind == MIX_K ? x : nullptr, kind == MIX_RHS ? f : nullptr, Tb, tw,
+            k_row_fwd<T, TF><<<grid, 256, smr, s>>>(use_x ? x : nullptr, use_f ? f : nullptr, Tb, tw,
                                                     rp);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -288,7 +290,7 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
     if (stage < 0 || stage == 1) {
         ColParams cp;
         cp.n = p->n; cp.Q = p->Q; cp.H = p->H; cp.L = p->L;
-        cp.nin = kind == MIX_K ? p->nch : 1;
+        cp.nin = use_x ? p->nch : 1;
         cp.G = 1;
         cp.sc = p->sched;
         int launches = split ? 3 : 1;
@@ -314,13 +316,13 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         if (row_warp) {
             if constexpr (row_warp_types<T, TF>::value) {
                 const dim3 grid2((p->n + 7) / 8, p->L + 1);
-                if ((e = row_inv_warp<T, TF>(p->Q, grid2, Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a,
+                if ((e = row_inv_warp<T, TF>(p->Q, grid2, Tb, use_x ? x : nullptr, z, out, tw, rp, (R)a,
                                              (R)b, (R)c, s)) != cudaSuccess)
                     return e;
             }
         } else {
             const dim3 grid2((p->n + rp.RB - 1) / rp.RB, p->L + 1);
-            k_row_inv<T, TF><<<grid2, 256, smr, s>>>(Tb, kind == MIX_K ? x : nullptr, z, out, tw, rp, (R)a, (R)b,
+            k_row_inv<T, TF><<<grid2, 256, smr, s>>>(Tb, use_x ? x : nullptr, z, out, tw, rp, (R)a, (R)b,
                                                      (R)c);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

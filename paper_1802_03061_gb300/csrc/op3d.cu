@@ -29,7 +29,7 @@ __device__ __forceinline__ int fold(int a, int Q) { return a <= Q / 2 ? a : Q - 
 // X: in real [n][n][n] (x fastest); grid (ceil(n/B), n), B even
 template <typename T, typename R>
 __global__ void __launch_bounds__(256) k3_x_fwd(const R* __restrict__ x, T* __restrict__ T1, const T* __restrict__ tw,
-                                                P3 p, double w) {
+                                                P3 p, double w, const double* __restrict__ xf) {
     extern __shared__ unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const int n = p.n, Q = p.Q, H = p.H, B = p.B;
@@ -45,10 +45,14 @@ __global__ void __launch_bounds__(256) k3_x_fwd(const R* __restrict__ x, T* __re
         const int ya = y0 + 2 * li, yb = ya + 1;
         RR a = 0, b = 0;
         if (e < n) {
-            if (ya < n) a = (RR)x[((long)z * n + ya) * n + e];
-            if (yb < n) b = (RR)x[((long)z * n + yb) * n + e];
+            if (ya < n) a = ww * (RR)x[((long)z * n + ya) * n + e];
+            if (yb < n) b = ww * (RR)x[((long)z * n + yb) * n + e];
+            if (xf) {  // the source joins unweighted: K x + K~ f in one application
+                if (ya < n) a = a + (RR)xf[((long)z * n + ya) * n + e];
+                if (yb < n) b = b + (RR)xf[((long)z * n + yb) * n + e];
+            }
         }
-        buf[idx] = mk<T>(ww * a, ww * b);
+        buf[idx] = mk<T>(a, b);
     }
     __syncthreads();
     T* res = fft_lines<-1>(buf, tmp, nl, Q, p.sc, twl);
@@ -214,7 +218,8 @@ template <typename RO, typename RR> __device__ __forceinline__ RO out_cast(RR v)
 
 template <int RQ, typename T, typename RI>
 __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __restrict__ T1,
-                                                 const T* __restrict__ tw, int n, int H, double w) {
+                                                 const T* __restrict__ tw, int n, int H, double w,
+                                                 const double* __restrict__ xf) {
     constexpr int Q = 32 * RQ, LS = Q + 34;  // a line also holds the warp's FFT scratch (Q + 32)
     using RR = typename real_of<T>::R;
     extern __shared__ unsigned char smraw[];
@@ -232,10 +237,14 @@ __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __
         const int e = lane + 32 * r;
         RR a = (RR)0, b = (RR)0;
         if (e < n) {
-            if (ya < n) a = (RR)x[((long)z * n + ya) * n + e];
-            if (yb < n) b = (RR)x[((long)z * n + yb) * n + e];
+            if (ya < n) a = ww * (RR)x[((long)z * n + ya) * n + e];
+            if (yb < n) b = ww * (RR)x[((long)z * n + yb) * n + e];
+            if (xf) {  // the source joins unweighted: K x + K~ f in one application
+                if (ya < n) a = a + (RR)xf[((long)z * n + ya) * n + e];
+                if (yb < n) b = b + (RR)xf[((long)z * n + yb) * n + e];
+            }
         }
-        v[r] = mk<T>(ww * a, ww * b);
+        v[r] = mk<T>(a, b);
     }
     warp_fft_fwd<RQ>(v, twl, Z + wp * LS);
 #pragma unroll
@@ -404,7 +413,8 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
 
 template <int RQ, typename T, typename R, typename TS>
 static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, double a, double b, double c,
-                                 const R* z, T* T1, T* T2, const TS* S, const T* tw, cudaStream_t s) {
+                                 const R* z, T* T1, T* T2, const TS* S, const T* tw, cudaStream_t s,
+                                 const double* xf) {
     constexpr int Q = 32 * RQ;
     static bool once = false;
     cudaError_t e;
@@ -431,7 +441,7 @@ static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, dou
         once = true;
     }
     const unsigned gy = (unsigned)((n + 15) / 16);
-    k3w_x_fwd<RQ, T, R><<<dim3(gy, n), 256, smx, s>>>(x, T1, tw, n, H, w);
+    k3w_x_fwd<RQ, T, R><<<dim3(gy, n), 256, smx, s>>>(x, T1, tw, n, H, w, xf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k3w_y_fwd<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T1, T2, tw, n, H);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -459,7 +469,7 @@ template <typename T> static int lines_per_block(int Q) {
 
 template <typename T, typename R, typename TS>
 static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, double b, double c, const R* z,
-                            T* T1, T* T2, const TS* S, const T* tw, cudaStream_t s) {
+                            T* T1, T* T2, const TS* S, const T* tw, cudaStream_t s, const double* xf = nullptr) {
     static bool once = false;
     cudaError_t e;
     if (!once) {
@@ -473,10 +483,10 @@ static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, 
     if constexpr (!std::is_same<T, double2>::value) {
         // FP32 and float-float: warp-register passes when Q = 32 * 2^j
         switch (p->Q) {
-            case 64: return op3d_run_warp<2>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
-            case 128: return op3d_run_warp<4>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
-            case 256: return op3d_run_warp<8>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
-            case 512: return op3d_run_warp<16>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s);
+            case 64: return op3d_run_warp<2>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s, xf);
+            case 128: return op3d_run_warp<4>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s, xf);
+            case 256: return op3d_run_warp<8>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s, xf);
+            case 512: return op3d_run_warp<16>(p->n, p->H, x, out, w, a, b, c, z, T1, T2, S, tw, s, xf);
             default: break;
         }
     }
@@ -490,7 +500,7 @@ static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, 
     const int B = pp.B;
     const size_t smx = (size_t)(Q + 2 * (B / 2) * Q) * sizeof(T);
     const size_t smy = (size_t)(Q + 2 * B * Q) * sizeof(T);
-    k3_x_fwd<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(x, T1, tw, pp, w);
+    k3_x_fwd<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(x, T1, tw, pp, w, xf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k3_y_fwd<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T1, T2, tw, pp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -507,9 +517,10 @@ static cudaError_t op3d_run(rte_plan p, const R* x, R* out, double w, double a, 
 
 rte_status op3d_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
                         const double* z, cudaStream_t s) {
-    const double w = kind == MIX_K ? p->mu_s : 1.0;
-    cudaError_t e = op3d_run<double2, double, double>(p, x, out, w, kind == MIX_K ? a : 0.0, b, c, z,
-                                                      (double2*)p->T64, (double2*)p->U64, p->S3_64, p->tw64, s);
+    const double w = kind == MIX_RHS ? 1.0 : p->mu_s;
+    cudaError_t e = op3d_run<double2, double, double>(p, x, out, w, kind == MIX_RHS ? 0.0 : a, b, c, z,
+                                                      (double2*)p->T64, (double2*)p->U64, p->S3_64, p->tw64, s,
+                                                      kind == MIX_KF ? p->f_dev : nullptr);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply64");
     return RTE_OK;
 }
@@ -524,10 +535,28 @@ rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b
 
 rte_status op3d_apply_ff(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
                          const double* z, cudaStream_t s) {
-    const double w = kind == MIX_K ? p->mu_s : 1.0;
-    cudaError_t e = op3d_run<ffc, double, ff>(p, x, out, w, kind == MIX_K ? a : 0.0, b, c, z, (ffc*)p->T64,
-                                             (ffc*)p->U64, p->S3ff, p->twff, s);
+    // MIX_KF: K x + K~ f = K~ (mu_s x + f), the plan's source f
+    const double w = kind == MIX_RHS ? 1.0 : p->mu_s;
+    cudaError_t e = op3d_run<ffc, double, ff>(p, x, out, w, kind == MIX_RHS ? 0.0 : a, b, c, z, (ffc*)p->T64,
+                                             (ffc*)p->U64, p->S3ff, p->twff, s, kind == MIX_KF ? p->f_dev : nullptr);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_apply_ff");
+    return RTE_OK;
+}
+
+__global__ void k_narrow(const double* __restrict__ src, float* __restrict__ dst, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+// b = K~ f in FP32; f32 (n^3 floats) receives the source rounded to FP32
+rte_status op3d_rhs32(rte_plan p, float* f32, float* out, cudaStream_t s) {
+    k_narrow<<<1024, 256, 0, s>>>(p->f_dev, f32, p->ncell);
+    rte_count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = op3d_run<float2, float, float>(p, f32, out, 1.0, 0.0, 1.0, 0.0, nullptr, (float2*)p->T32, (float2*)p->U32,
+                                           p->S3_32, p->tw32, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op3d_rhs32");
     return RTE_OK;
 }
 

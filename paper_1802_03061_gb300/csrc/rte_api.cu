@@ -72,10 +72,16 @@ template <typename P> static rte_status dalloc(P** p, size_t bytes) {
     return RTE_OK;
 }
 
+// the operator's inputs by kind: x is the field (MIX_K, MIX_KF) or the source
+// (MIX_RHS); MIX_KF adds the plan's source f
+static const double* op_x(MixKind kind, const double* x) { return kind == MIX_RHS ? nullptr : x; }
+static const double* op_f(const rte_plan p, MixKind kind, const double* x) {
+    return kind == MIX_RHS ? x : kind == MIX_KF ? p->f_dev : nullptr;
+}
+
 rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
                         const double* z, cudaStream_t s) {
-    if (p->dim == 2)
-        return op2d_apply64(p, kind, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? x : nullptr, out, a, b, c, z, s);
+    if (p->dim == 2) return op2d_apply64(p, kind, op_x(kind, x), op_f(p, kind, x), out, a, b, c, z, s);
     return op3d_apply64(p, kind, x, out, a, b, c, z, s);
 }
 
@@ -83,9 +89,15 @@ rte_status plan_apply64(rte_plan p, MixKind kind, const double* x, double* out, 
 // refinement for the right-hand side and the residual)
 rte_status plan_apply64e(rte_plan p, MixKind kind, const double* x, double* out, double a, double b, double c,
                          const double* z, cudaStream_t s) {
-    if (p->dim == 2)
-        return op2d_apply_ff(p, kind, kind == MIX_K ? x : nullptr, kind == MIX_RHS ? x : nullptr, out, a, b, c, z, s);
+    if (p->dim == 2) return op2d_apply_ff(p, kind, op_x(kind, x), op_f(p, kind, x), out, a, b, c, z, s);
     return op3d_apply_ff(p, kind, x, out, a, b, c, z, s);
+}
+
+// b = K~ f in FP32 into the FP32 field layout (3D uses the plan's d32 as
+// scratch for the rounded source)
+rte_status plan_rhs32(rte_plan p, float* out, cudaStream_t s) {
+    if (p->dim == 2) return op2d_rhs32(p, out, s);
+    return op3d_rhs32(p, p->d32, out, s);
 }
 
 rte_status plan_apply32(rte_plan p, const float* x, float* out, float a, float b, float c, const float* z,

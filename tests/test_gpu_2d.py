@@ -196,3 +196,32 @@ def test_full_size_transport_256_sampled_residual():
     r, b = oracle.sampled_residual_2d(n, 1 / n, prob["mu_t"], prob["mu_s"], prob["sigma_hat"], prob["f"], uf, rows)
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
     p.close()
+
+
+def _wnorm(v):
+    """The solver's norm of a packed field: mode 0 once, modes k >= 1 twice
+    (their conjugates), i.e. the norm of the full 2L+1 mode vector."""
+    w = np.ones(v.shape[0])
+    w[1:] = 2.0
+    return float(np.sqrt(np.sum(w * np.sum(np.abs(v.reshape(v.shape[0], -1)) ** 2, axis=1))))
+
+
+@pytest.mark.parametrize("prec,q", [("mixed_fp32", 0), ("mixed_bf16", 0), ("mixed_fp32", 72)])
+def test_mixed_residual_equals_unfused_residual(prec, q):
+    """The mixed solve forms every residual as K~(mu_s sigma_hat u + g) - u in
+    one float-float application and b in FP32 only.  The residual rebuilt from
+    the FP64 right-hand side (rte_rhs) and rte_apply_K64e must give the same
+    relative residual: to 1e-12 absolute (an FP32-accurate residual would be
+    off by ~1e-7), the solver's ||b|| carrying an FP32 relative error."""
+    n, L = 24, 4
+    prob = rte_synth.hg2d_transport(n=n, L=L, seed=7)
+    p = _plan(n, prob["mu_t"], prob["mu_s"], prob["sigma_hat"], prec=prec, q_policy=q)
+    f = torch.from_numpy(prob["f"])
+    u, st = p.solve(f, tol=1e-9)
+    assert st["converged"]
+    b = p.rhs(f)
+    r = (b - u + p.apply_K64e(u)).cpu().numpy()
+    relres = _wnorm(r) / _wnorm(b.cpu().numpy())
+    assert relres <= 1e-9 * (1 + 1e-6)
+    assert abs(relres - st["relres_true"]) <= 1e-6 * relres + 1e-12
+    p.close()

@@ -142,3 +142,20 @@ def test_solve_3d_diffusion_full_size():
     r, b = oracle.sampled_residual_3d(n, 1.0 / n, prob["mu_t"], prob["mu_s"], prob["f"], u.cpu().numpy(), rows)
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
     p.close()
+
+
+@pytest.mark.parametrize("n,q", [(16, 0), (12, 48)])
+def test_mixed_residual_equals_unfused_residual_3d(n, q):
+    """3D: the fused float-float residual K~(mu_s u + f) - u of the mixed
+    solve against b (FP64 rte_rhs) - u + rte_apply_K64e(u)."""
+    mu_t, mu_s = 30.0, 29.0
+    f = torch.from_numpy(rte_synth.gaussian_3d(n, (0.45, 0.5, 0.55), 0.15))
+    p = _plan(n, mu_t, mu_s, prec="mixed_fp32", restart=60, q_policy=q)
+    u, st = p.solve(f, tol=1e-9)
+    assert st["converged"]
+    b = p.rhs(f)
+    r = (b - u + p.apply_K64e(u)).cpu().numpy()
+    relres = float(np.linalg.norm(r) / np.linalg.norm(b.cpu().numpy()))
+    assert relres <= 1e-9 * (1 + 1e-6)
+    assert abs(relres - st["relres_true"]) <= 1e-6 * relres + 1e-12
+    p.close()
