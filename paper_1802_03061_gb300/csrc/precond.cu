@@ -234,6 +234,63 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
     }
 }
 
+// the same pass with the shared-memory (Stockham, radix 2/3/4/8) FFT for the
+// other Q: every channel column of one xi_x resident in natural frequency
+// order, FFT groups of G columns (as k_col_fused)
+template <int L>
+__global__ void __launch_bounds__(256) k_col_pc_fused(float2* __restrict__ Tb, const __nv_bfloat16* __restrict__ Pp,
+                                                      const float2* __restrict__ tw, ColParams p) {
+    constexpr int NCH = 2 * L + 1;
+    extern __shared__ unsigned char smraw[];
+    float2* sm = reinterpret_cast<float2*>(smraw);
+    const int n = p.n, Q = p.Q, H = p.H, QR = pc_row(Q);
+    const int kx = blockIdx.x;
+    float2* twl = sm;
+    float2* X = sm + Q;
+    float2* tmp = X + (long)NCH * Q;
+    load_twiddles(twl, tw, Q);
+    for (int idx = threadIdx.x; idx < NCH * Q; idx += blockDim.x) {
+        const int c = idx / Q, e = idx - c * Q;
+        X[idx] = e < n ? Tb[((long)c * H + kx) * n + e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_channels<-1>(X, tmp, 0, NCH, p.G, p.sc, twl, 2 * n <= Q);
+    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * NCH * QR;
+    for (int t = threadIdx.x; t < Q / 2; t += blockDim.x) {
+        if (t == 0) {
+            pc_mix_one<L>(X, Q, 0, Pk, QR);
+            pc_mix_one<L>(X, Q, Q / 2, Pk + Q / 2, QR);
+        } else {
+            pc_mix_pair<L>(X, Q, t, Q - t, Pk + t, QR);
+        }
+    }
+    __syncthreads();
+    fft_channels<1>(X, tmp, 0, NCH, p.G, p.sc, twl);
+    for (int idx = threadIdx.x; idx < NCH * n; idx += blockDim.x) {
+        const int c = idx / n, e = idx - c * n;
+        Tb[((long)c * H + kx) * n + e] = X[(long)c * Q + e];
+    }
+}
+
+// shared memory of k_col_pc_fused: twiddles, the NCH columns, G FFT scratch lines
+static size_t pc_fused_smem(int nch, int Q, int G) { return (size_t)(Q + nch * Q + G * Q) * sizeof(float2); }
+
+template <int L>
+static cudaError_t launch_col_pc_fused(rte_plan p, float2* Tb, cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_col_pc_fused<L>)) != cudaSuccess) return e;
+        once = true;
+    }
+    ColParams cp;
+    cp.n = p->n; cp.Q = p->Q; cp.H = p->H; cp.L = L; cp.nin = 2 * L + 1;
+    cp.sc = p->sched;
+    cp.G = col_group<float2>(2 * L + 1, p->Q);
+    k_col_pc_fused<L><<<p->H, 256, pc_fused_smem(2 * L + 1, p->Q, cp.G), s>>>(Tb, p->Pp, p->tw32, cp);
+    return cudaGetLastError();
+}
+
 template <int L, int R>
 static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
                                  cudaStream_t s) {
@@ -278,8 +335,11 @@ static RowParams pc_rowparams(rte_plan p, bool unit) {
     return rp;
 }
 
+// 3D: every Q.  2D: the warp column pass (Q = 64..512, 32 * 2^j), else the
+// shared-memory pass while its columns fit in shared memory (Q <= 1024 at L = 8)
 bool plan_precond_supported(const rte_plan p) {
-    return p->dim == 3 || col_warp_ok(p->Q);
+    if (p->dim == 3 || col_warp_ok(p->Q)) return true;
+    return pc_fused_smem(p->nch, p->Q, col_group<float2>(p->nch, p->Q)) <= 200 * 1024;
 }
 
 // builds the preconditioner data once per plan (allocates; call outside any capture)
@@ -319,15 +379,47 @@ rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
     return RTE_OK;
 }
 
-// one pass of the 2D application: 0 row, 1 column (mix with Pp), 2 inverse row
+// one pass of the 2D application: 0 row, 1 column (mix with Pp), 2 inverse row;
+// warp-register passes for Q = 32 * 2^j (64..512), shared-memory ones otherwise
 static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cudaStream_t s) {
-    const RowParams rp = pc_rowparams(p, true);
+    RowParams rp = pc_rowparams(p, true);
     float2* Tb = (float2*)p->T32;
-    const dim3 grid((p->n + 7) / 8, p->L + 1);
-    if (st == 0) return row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
-    if (st == 2)
-        return row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
-                                            0.f, s);
+    const bool warp = col_warp_ok(p->Q);
+    if (st == 0 || st == 2) {
+        if (warp) {
+            const dim3 grid((p->n + 7) / 8, p->L + 1);
+            if (st == 0) return row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
+            return row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
+                                                0.f, s);
+        }
+        static bool once = false;
+        cudaError_t e;
+        if (!once) {
+            if ((e = allow_smem(k_row_fwd<float2, float2>)) != cudaSuccess) return e;
+            if ((e = allow_smem(k_row_inv<float2, float2>)) != cudaSuccess) return e;
+            once = true;
+        }
+        rp.RB = rows_per_block<float2>(p->Q);
+        const dim3 grid((p->n + rp.RB - 1) / rp.RB, p->L + 1);
+        const size_t smr = row_smem<float2>(p->Q, rp.RB);
+        if (st == 0) k_row_fwd<float2, float2><<<grid, 256, smr, s>>>((const float2*)x, nullptr, Tb, p->tw32, rp);
+        else k_row_inv<float2, float2><<<grid, 256, smr, s>>>(Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f, 0.f);
+        return cudaGetLastError();
+    }
+    if (!warp) {
+        switch (p->L) {
+            case 0: return launch_col_pc_fused<0>(p, Tb, s);
+            case 1: return launch_col_pc_fused<1>(p, Tb, s);
+            case 2: return launch_col_pc_fused<2>(p, Tb, s);
+            case 3: return launch_col_pc_fused<3>(p, Tb, s);
+            case 4: return launch_col_pc_fused<4>(p, Tb, s);
+            case 5: return launch_col_pc_fused<5>(p, Tb, s);
+            case 6: return launch_col_pc_fused<6>(p, Tb, s);
+            case 7: return launch_col_pc_fused<7>(p, Tb, s);
+            case 8: return launch_col_pc_fused<8>(p, Tb, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (p->L) {
         case 0: return launch_col_pc_q<0>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
         case 1: return launch_col_pc_q<1>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);

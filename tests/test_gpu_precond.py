@@ -57,7 +57,10 @@ def _ref_precond_2d(n, Q, mu_t, mu_s, sig, x_full):
 
 
 @pytest.mark.parametrize("n,L,q", [(12, 2, 64), (20, 1, 128), (9, 3, 64), (12, 8, 64), (16, 4, 256),
-                                   (10, 2, 512), (7, 0, 512)])
+                                   (10, 2, 512), (7, 0, 512),
+                                   # shared-memory (Stockham) passes: Q not 32 * 2^j, up to 1024
+                                   (12, 2, 72), (20, 1, 96), (10, 8, 48), (12, 4, 216), (9, 1, 768),
+                                   (7, 0, 1024)])
 def test_precond_apply_2d_matches_reference(n, L, q):
     mu_t, mu_s = 10.0, 9.0
     sig = rte_synth.hg_sigma_hat(0.5, L)
@@ -91,11 +94,12 @@ def test_precond_apply_3d_matches_reference():
     p.close()
 
 
-def test_preconditioned_solve_2d_against_dense():
+@pytest.mark.parametrize("q", [64, 72])
+def test_preconditioned_solve_2d_against_dense(q):
     n, L = 32, 2
     prob = rte_synth.hg2d_transport(n=n, L=L, seed=5)
     sig = prob["sigma_hat"]
-    p = _plan(n, prob["mu_t"], prob["mu_s"], sig, prec="mixed_fp32", q_policy=64)
+    p = _plan(n, prob["mu_t"], prob["mu_s"], sig, prec="mixed_fp32", q_policy=q)
     f = torch.from_numpy(prob["f"])
     u_ref, _ = oracle.solve_dense_2d(n, 1.0 / n, prob["mu_t"], prob["mu_s"], sig, prob["f"])
     u0, st0 = p.solve(f, tol=1e-10)
@@ -136,5 +140,30 @@ def test_preconditioned_full_size_transport_sampled_residual():
     rows = np.random.default_rng(11).choice(n * n, size=24, replace=False)
     r, b = oracle.sampled_residual_2d(n, 1.0 / n, prob["mu_t"], prob["mu_s"], sig, prob["f"],
                                       packed_to_full(u.cpu().numpy()), rows)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
+    p.close()
+
+
+def test_preconditioned_solve_q1024_sampled_residual():
+    """n = 512, L = 8 (Q = 1024, the shared-memory passes; the heaviest
+    instances of the batched workload): preconditioned and plain mixed solves
+    to 1e-8 agree within cond_est * tol, the preconditioned one in fewer
+    iterations, and the oracle's FP64 direct-sum residual at sampled cells
+    agrees."""
+    rng = np.random.default_rng(21)
+    d = rte_synth.random_instance_2d(rng, 512, 8)
+    n, sig = d["n"], d["sigma_hat"]
+    p = _plan(n, d["mu_t"], d["mu_s"], sig, prec="mixed_fp32", restart=30, maxit=4000)
+    assert p.Q == 1024
+    f = torch.from_numpy(d["f"])
+    u0, st0 = p.solve(f, tol=1e-8)
+    u1, st1 = p.solve(f, tol=1e-8, precond=1)
+    assert st0["converged"] and st1["converged"] and st1["relres_true"] <= 1e-8
+    assert st1["iters"] < st0["iters"]
+    rho = d["mu_s"] / d["mu_t"]
+    assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 2 * (1 + rho) / (1 - rho) * 1e-8
+    rows = np.random.default_rng(12).choice(n * n, size=8, replace=False)
+    r, b = oracle.sampled_residual_2d(n, 1.0 / n, d["mu_t"], d["mu_s"], sig, d["f"],
+                                      packed_to_full(u1.cpu().numpy()), rows)
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
     p.close()
