@@ -69,6 +69,7 @@ struct rte_plan_s {
     ff* S3ff = nullptr;
     ffc* twff = nullptr;
     float2* S32p = nullptr;          // FP32 / BF16 spectra in the warp column pass's slot order
+    float2* Tz32 = nullptr;          // Q = 1024: first-residue column results [nch][H][n]
     __nv_bfloat162* S16p = nullptr;
     double* S3_64 = nullptr;
     float* S3_32 = nullptr;

@@ -801,15 +801,165 @@ __global__ void __launch_bounds__(256) k_colw_inv(ffc* __restrict__ Tb, const ff
     }
 }
 
-// Sp[xi_x][m][k1 * 32 + lane] = S[xi_x][m][wfreq(k1, lane)]
+// ---------------------------------------------------------------------------
+// Q = 1024 as two 512-point warp FFTs.  The inputs have n <= Q/2 = 512
+// nonzero entries, so the padded transform splits by the residue r = xi mod 2:
+//   X[2k + r] = FFT_512( x[j] W_1024^{j r} )[k],
+// and the cropped inverse recombines y[j] = z_0[j] + W_1024^{-j} z_1[j] with
+// z_r = IFFT_512( X[2 . + r] ) (both unnormalised).  The spectra are stored
+// by slot_freq (slot r * 512 + s holds xi = 2 wfreq_512(s) + r).  tw is the
+// plan's table exp(-2 pi i t / 1024); the 512-point table is its even half.
+// ---------------------------------------------------------------------------
+
+// FP32 column pass (as k_col_warp, R = 16): a block runs the two residues one
+// after the other; residue 0's inverse goes to Tz, residue 1 adds its part and
+// writes Tb (whose input residue 1 has read by then).
+template <int L, typename TS>
+__global__ void __launch_bounds__(256, 2) k_col_warp2(float2* __restrict__ Tb, float2* __restrict__ Tz,
+                                                      const TS* __restrict__ Sp, const float2* __restrict__ tw,
+                                                      int n, int H, int nin) {
+    constexpr int NCH = 2 * L + 1;
+    constexpr int R = 16, QW = 512, Q = 1024;
+    constexpr int QS = wfft_shape<R>::SCRATCH;
+    extern __shared__ unsigned char smraw[];
+    float2* twl = reinterpret_cast<float2*>(smraw);  // exp(-2 pi i t / 512)
+    float2* X = twl + QW;                            // [NCH][QS]
+    const int kx = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
+    __syncthreads();
+    for (int r = 0; r < 2; ++r) {
+        for (int c = warp; c < nin; c += nw) {
+            float2 v[R];
+            const float2* col = Tb + ((long)c * H + kx) * n;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int y = lane + 32 * rr;
+                float2 a = make_float2(0.f, 0.f);
+                if (y < n) {
+                    a = col[y];
+                    if (r) a = cmul(a, tw[y]);
+                }
+                v[rr] = a;
+            }
+            float2* Xc = X + (long)c * QS;
+            warp_fft_fwd<R>(v, twl, Xc);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
+        }
+        __syncthreads();
+        for (int sl = threadIdx.x; sl < QW; sl += blockDim.x) {
+            float sr[2 * L + 1], si[2 * L + 1];
+#pragma unroll
+            for (int m = 0; m <= 2 * L; ++m) {
+                const float2 v = ld_spec(Sp, ((long)kx * (2 * L + 1) + m) * Q + r * QW + sl, float2());
+                sr[m] = v.x;
+                si[m] = v.y;
+            }
+            if (nin == 1) {
+                mode_mix_rhs<L, float2>(sr, si, X[sl], Strided<float2>{X + sl, QS});
+            } else {
+                float2 in[NCH];
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) in[c] = X[(long)c * QS + sl];
+                mode_mix<L, float2>(sr, si, in, Strided<float2>{X + sl, QS});
+            }
+        }
+        __syncthreads();
+        for (int c = warp; c < NCH; c += nw) {
+            float2 v[R];
+            float2* Xc = X + (long)c * QS;
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) v[k1] = Xc[k1 * 32 + lane];
+            __syncwarp();
+            warp_fft_inv<R>(v, twl, Xc);
+            float2* col = Tb + ((long)c * H + kx) * n;
+            float2* zc = Tz + ((long)c * H + kx) * n;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int y = lane + 32 * rr;
+                if (y < n) {
+                    if (r == 0) zc[y] = v[rr];
+                    else col[y] = cadd(zc[y], cmul(v[rr], cconj(tw[y])));
+                }
+            }
+        }
+        __syncthreads();  // residue 1 reuses X
+    }
+}
+
+// float-float column FFTs for Q = 1024 (as k_colw_fwd / k_colw_inv, one warp
+// per line): the forward writes both residues' spectra into the line of Ts,
+// the inverse adds the two residues' parts into Tb
+template <int R>  // 16: Q = 1024
+__global__ void __launch_bounds__(256) k_colw_fwd2(const ffc* __restrict__ Tb, ffc* __restrict__ Ts,
+                                                   const ffc* __restrict__ tw, int n, int nlines) {
+    constexpr int QW = 32 * R, Q = 2 * QW;
+    extern __shared__ unsigned char smraw[];
+    ffc* twl = reinterpret_cast<ffc*>(smraw);
+    ffc* scr = twl + QW + (threadIdx.x >> 5) * wfft_shape<R>::SCRATCH;
+    for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
+    __syncthreads();
+    const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= nlines) return;
+    const int lane = threadIdx.x & 31;
+    const ffc* col = Tb + (long)line * n;
+    for (int r = 0; r < 2; ++r) {
+        ffc v[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            const int y = lane + 32 * rr;
+            ffc a = mk<ffc>(0, 0);
+            if (y < n) {
+                a = col[y];
+                if (r) a = cmul(a, tw[y]);
+            }
+            v[rr] = a;
+        }
+        warp_fft_fwd<R>(v, twl, scr);
+        ffc* o = Ts + (long)line * Q + r * QW;
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) o[k1 * 32 + lane] = v[k1];
+    }
+}
+
+template <int R>  // 16: Q = 1024
+__global__ void __launch_bounds__(256) k_colw_inv2(ffc* __restrict__ Tb, const ffc* __restrict__ Ts,
+                                                   const ffc* __restrict__ tw, int n, int nlines) {
+    constexpr int QW = 32 * R, Q = 2 * QW;
+    extern __shared__ unsigned char smraw[];
+    ffc* twl = reinterpret_cast<ffc*>(smraw);
+    ffc* scr = twl + QW + (threadIdx.x >> 5) * wfft_shape<R>::SCRATCH;
+    for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
+    __syncthreads();
+    const int line = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= nlines) return;
+    const int lane = threadIdx.x & 31;
+    ffc* col = Tb + (long)line * n;
+    for (int r = 0; r < 2; ++r) {
+        ffc v[R];
+        const ffc* in = Ts + (long)line * Q + r * QW;
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) v[k1] = in[k1 * 32 + lane];
+        warp_fft_inv<R>(v, twl, scr);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            const int y = lane + 32 * rr;
+            if (y < n) {
+                if (r == 0) col[y] = v[rr];
+                else col[y] = cadd(col[y], cmul(v[rr], cconj(tw[y])));
+            }
+        }
+    }
+}
+
+// Sp[xi_x][m][sl] = S[xi_x][m][slot_freq(sl, Q)]
 template <typename TS>
 __global__ void k_permute_spec(const TS* __restrict__ S, TS* __restrict__ Sp, long rows, int Q) {
-    const int R = Q / 32;
     const long tot = rows * Q;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
         const long row = i / Q;
         const int sl = (int)(i % Q);
-        const int k1 = sl >> 5, lane = sl & 31;
-        Sp[i] = S[row * Q + wfreq_rt(R, k1, lane)];
+        Sp[i] = S[row * Q + slot_freq(sl, Q)];
     }
 }

@@ -27,13 +27,12 @@ __global__ void k_split_ff2(const double2* __restrict__ src, ffc* __restrict__ d
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = to_ffc(src[i]);
 }
-// the same into the warp column pass's slot order: dst[row][k1 * 32 + lane] = src[row][wfreq(k1, lane)]
+// the same into the warp column passes' slot order: dst[row][sl] = src[row][slot_freq(sl, Q)]
 __global__ void k_split_ff2_slot(const double2* __restrict__ src, ffc* __restrict__ dst, long rows, int Q) {
-    const int R = Q / 32;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < rows * Q; i += (long)gridDim.x * blockDim.x) {
         const long row = i / Q;
         const int sl = (int)(i % Q);
-        dst[i] = to_ffc(src[row * Q + wfreq_rt(R, sl >> 5, sl & 31)]);
+        dst[i] = to_ffc(src[row * Q + slot_freq(sl, Q)]);
     }
 }
 __global__ void k_split_ff(const double* __restrict__ src, ff* __restrict__ dst, long n) {

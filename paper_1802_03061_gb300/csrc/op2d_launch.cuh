@@ -97,36 +97,53 @@ static cudaError_t launch_col_warp(float2* Tb, const TS* Sp, const float2* tw, c
     return cudaGetLastError();
 }
 
+// Q = 1024: two 512-point residues per block (k_col_warp2), Tz holds the first
 template <int L, typename TS>
-static cudaError_t launch_col_warp_q(float2* Tb, const TS* Sp, const float2* tw, const ColParams& cp, cudaStream_t s) {
+static cudaError_t launch_col_warp2(float2* Tb, float2* Tz, const TS* Sp, const float2* tw, const ColParams& cp,
+                                   cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) { e = allow_smem(k_col_warp2<L, TS>); if (e != cudaSuccess) return e; once = true; }
+    const size_t smem = (size_t)(512 + (2 * L + 1) * wfft_shape<16>::SCRATCH) * sizeof(float2);
+    k_col_warp2<L, TS><<<cp.H, 256, smem, s>>>(Tb, Tz, Sp, tw, cp.n, cp.H, cp.nin);
+    return cudaGetLastError();
+}
+
+template <int L, typename TS>
+static cudaError_t launch_col_warp_q(float2* Tb, float2* Tz, const TS* Sp, const float2* tw, const ColParams& cp,
+                                     cudaStream_t s) {
     switch (cp.Q) {
         case 64: return launch_col_warp<L, 2>(Tb, Sp, tw, cp, s);
         case 128: return launch_col_warp<L, 4>(Tb, Sp, tw, cp, s);
         case 256: return launch_col_warp<L, 8>(Tb, Sp, tw, cp, s);
         case 512: return launch_col_warp<L, 16>(Tb, Sp, tw, cp, s);
+        case 1024: return Tz ? launch_col_warp2<L>(Tb, Tz, Sp, tw, cp, s) : cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename TS>
-static cudaError_t dispatch_col_warp(int L, float2* Tb, const TS* Sp, const float2* tw, const ColParams& cp,
-                                     cudaStream_t s) {
+static cudaError_t dispatch_col_warp(int L, float2* Tb, float2* Tz, const TS* Sp, const float2* tw,
+                                     const ColParams& cp, cudaStream_t s) {
     switch (L) {
-        case 0: return launch_col_warp_q<0>(Tb, Sp, tw, cp, s);
-        case 1: return launch_col_warp_q<1>(Tb, Sp, tw, cp, s);
-        case 2: return launch_col_warp_q<2>(Tb, Sp, tw, cp, s);
-        case 3: return launch_col_warp_q<3>(Tb, Sp, tw, cp, s);
-        case 4: return launch_col_warp_q<4>(Tb, Sp, tw, cp, s);
-        case 5: return launch_col_warp_q<5>(Tb, Sp, tw, cp, s);
-        case 6: return launch_col_warp_q<6>(Tb, Sp, tw, cp, s);
-        case 7: return launch_col_warp_q<7>(Tb, Sp, tw, cp, s);
-        case 8: return launch_col_warp_q<8>(Tb, Sp, tw, cp, s);
+        case 0: return launch_col_warp_q<0>(Tb, Tz, Sp, tw, cp, s);
+        case 1: return launch_col_warp_q<1>(Tb, Tz, Sp, tw, cp, s);
+        case 2: return launch_col_warp_q<2>(Tb, Tz, Sp, tw, cp, s);
+        case 3: return launch_col_warp_q<3>(Tb, Tz, Sp, tw, cp, s);
+        case 4: return launch_col_warp_q<4>(Tb, Tz, Sp, tw, cp, s);
+        case 5: return launch_col_warp_q<5>(Tb, Tz, Sp, tw, cp, s);
+        case 6: return launch_col_warp_q<6>(Tb, Tz, Sp, tw, cp, s);
+        case 7: return launch_col_warp_q<7>(Tb, Tz, Sp, tw, cp, s);
+        case 8: return launch_col_warp_q<8>(Tb, Tz, Sp, tw, cp, s);
     }
     return cudaErrorInvalidValue;
 }
 
-// the warp-register column pass applies to FP32 with Q in {64, 128, 256, 512}
-static inline bool col_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512; }
+// the warp-register column passes (FP32, float-float, preconditioner) take
+// Q in {64, 128, 256, 512} and Q = 1024 as two 512-point residues; the warp
+// row passes take Q <= 512
+static inline bool col_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024; }
+static inline bool row_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512; }
 
 template <typename T, typename TS>
 static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split,
@@ -152,14 +169,17 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
                            cudaStream_t s) {
     const int lin = cp.nin * cp.H, lout = (2 * L + 1) * cp.H;
     const unsigned gin = (unsigned)((lin + 7) / 8), gout = (unsigned)((lout + 7) / 8);
-    const size_t sm = (size_t)(cp.Q + 8 * (cp.Q + 32)) * sizeof(ffc);  // twiddles + 8 FFT scratches
+    // twiddles + 8 FFT scratches (Q = 1024: those of the 512-point residues)
+    const int QW = cp.Q > 512 ? 512 : cp.Q;
+    const size_t sm = (size_t)(QW + 8 * (QW + 32)) * sizeof(ffc);
     static bool once = false;
     cudaError_t e;
     if (!once) {
         if ((e = allow_smem(k_colw_fwd<2>)) != cudaSuccess || (e = allow_smem(k_colw_fwd<4>)) != cudaSuccess ||
             (e = allow_smem(k_colw_fwd<8>)) != cudaSuccess || (e = allow_smem(k_colw_fwd<16>)) != cudaSuccess ||
             (e = allow_smem(k_colw_inv<2>)) != cudaSuccess || (e = allow_smem(k_colw_inv<4>)) != cudaSuccess ||
-            (e = allow_smem(k_colw_inv<8>)) != cudaSuccess || (e = allow_smem(k_colw_inv<16>)) != cudaSuccess)
+            (e = allow_smem(k_colw_inv<8>)) != cudaSuccess || (e = allow_smem(k_colw_inv<16>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_fwd2<16>)) != cudaSuccess || (e = allow_smem(k_colw_inv2<16>)) != cudaSuccess)
             return e;
         once = true;
     }
@@ -168,6 +188,7 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
         case 128: k_colw_fwd<4><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         case 256: k_colw_fwd<8><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         case 512: k_colw_fwd<16><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 1024: k_colw_fwd2<16><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         default: return cudaErrorInvalidValue;
     }
     e = cudaGetLastError();
@@ -178,6 +199,7 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
         case 128: k_colw_inv<4><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
         case 256: k_colw_inv<8><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
         case 512: k_colw_inv<16><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 1024: k_colw_inv2<16><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
     }
     return cudaGetLastError();
 }
@@ -270,7 +292,7 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
     const int nmod_in = use_x ? p->L + 1 : 1;
     const size_t smr = row_smem<T>(p->Q, rp.RB);
     bool row_warp = false;
-    if constexpr (row_warp_types<T, TF>::value) row_warp = col_warp_ok(p->Q) && p->rb_force < 2;
+    if constexpr (row_warp_types<T, TF>::value) row_warp = row_warp_ok(p->Q) && p->rb_force < 2;
     if (stage < 0 || stage == 0) {
         if (row_warp) {
             if constexpr (row_warp_types<T, TF>::value) {
@@ -297,7 +319,8 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         bool warp_path = false;
         if constexpr (sizeof(T) == sizeof(float2)) {
             if (Sp && col_warp_ok(p->Q)) {
-                if ((e = dispatch_col_warp<TS>(p->L, (float2*)Tb, Sp, (const float2*)tw, cp, s)) != cudaSuccess) return e;
+                if ((e = dispatch_col_warp<TS>(p->L, (float2*)Tb, p->Tz32, Sp, (const float2*)tw, cp, s)) != cudaSuccess)
+                    return e;
                 warp_path = true;
                 launches = 1;
             }

@@ -234,6 +234,104 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
     }
 }
 
+// Q = 1024 as two 512-point residues r = xi mod 2 (as k_col_warp2): the
+// mirror Q - xi of a frequency of residue r has residue r too (Q - 2k =
+// 2(512 - k), Q - 2k - 1 = 2(511 - k) + 1), so the pairs stay within a residue:
+// r = 0 pairs k with 512 - k (k = 0 and 256 alone), r = 1 pairs k with 511 - k.
+template <int L>
+__global__ void __launch_bounds__(256, 2) k_col_warp_pc2(float2* __restrict__ Tb, float2* __restrict__ Tz,
+                                                         const __nv_bfloat16* __restrict__ Pp,
+                                                         const float2* __restrict__ tw, int n, int H) {
+    constexpr int NCH = 2 * L + 1;
+    constexpr int R = 16, QW = 512, Q = 1024;
+    constexpr int QR = Q / 2 + 8;
+    constexpr int QS = wfft_shape<R>::SCRATCH;
+    constexpr unsigned SLICE = NCH * NCH * QR * 2;
+    constexpr unsigned CHUNK = 16384;
+    extern __shared__ unsigned char smraw[];
+    float2* twl = reinterpret_cast<float2*>(smraw);  // exp(-2 pi i t / 512)
+    float2* X = twl + QW;                            // [NCH][QS]
+    const int kx = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * NCH * QR;
+    if (warp == nw - 1) {
+        const char* base = reinterpret_cast<const char*>(Pk);
+        for (unsigned off = lane * CHUNK; off < SLICE; off += 32 * CHUNK) {
+            const unsigned sz = SLICE - off < CHUNK ? SLICE - off : CHUNK;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(sz) : "memory");
+        }
+    }
+    for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
+    __syncthreads();
+    for (int r = 0; r < 2; ++r) {
+        for (int c = warp; c < NCH; c += nw) {
+            float2 v[R];
+            const float2* col = Tb + ((long)c * H + kx) * n;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int y = lane + 32 * rr;
+                float2 a = make_float2(0.f, 0.f);
+                if (y < n) {
+                    a = col[y];
+                    if (r) a = cmul(a, tw[y]);
+                }
+                v[rr] = a;
+            }
+            float2* Xc = X + (long)c * QS;
+            warp_fft_fwd<R>(v, twl, Xc);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < QW / 2; t += blockDim.x) {
+            if (r == 0) {
+                if (t == 0) {  // xi = 0 and xi = Q/2 are their own mirrors
+                    pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR);
+                    pc_mix_one<L>(X, QS, wslot<R>(QW / 2), Pk + QW, QR);
+                } else {
+                    pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - t), Pk + 2 * t, QR);
+                }
+            } else {
+                pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - 1 - t), Pk + 2 * t + 1, QR);
+            }
+        }
+        __syncthreads();
+        for (int c = warp; c < NCH; c += nw) {
+            float2 v[R];
+            float2* Xc = X + (long)c * QS;
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) v[k1] = Xc[k1 * 32 + lane];
+            __syncwarp();
+            warp_fft_inv<R>(v, twl, Xc);
+            float2* col = Tb + ((long)c * H + kx) * n;
+            float2* zc = Tz + ((long)c * H + kx) * n;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int y = lane + 32 * rr;
+                if (y < n) {
+                    if (r == 0) zc[y] = v[rr];
+                    else col[y] = cadd(zc[y], cmul(v[rr], cconj(tw[y])));
+                }
+            }
+        }
+        __syncthreads();  // residue 1 reuses X
+    }
+}
+
+template <int L>
+static cudaError_t launch_col_pc2(float2* Tb, float2* Tz, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
+                                  cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_col_warp_pc2<L>)) != cudaSuccess) return e;
+        once = true;
+    }
+    const size_t smem = (size_t)(512 + (2 * L + 1) * wfft_shape<16>::SCRATCH) * sizeof(float2);
+    k_col_warp_pc2<L><<<H, 256, smem, s>>>(Tb, Tz, Pp, tw, n, H);
+    return cudaGetLastError();
+}
+
 // the same pass with the shared-memory (Stockham, radix 2/3/4/8) FFT for the
 // other Q: every channel column of one xi_x resident in natural frequency
 // order, FFT groups of G columns (as k_col_fused)
@@ -306,9 +404,10 @@ static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const floa
 }
 
 template <int L>
-static cudaError_t launch_col_pc_q(int Q, float2* Tb, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
-                                   cudaStream_t s) {
+static cudaError_t launch_col_pc_q(int Q, float2* Tb, float2* Tz, const __nv_bfloat16* Pp, const float2* tw, int n,
+                                   int H, cudaStream_t s) {
     switch (Q) {
+        case 1024: return Tz ? launch_col_pc2<L>(Tb, Tz, Pp, tw, n, H, s) : cudaErrorInvalidValue;
         case 64: return launch_col_pc<L, 2>(Tb, Pp, tw, n, H, s);
         case 128: return launch_col_pc<L, 4>(Tb, Pp, tw, n, H, s);
         case 256: return launch_col_pc<L, 8>(Tb, Pp, tw, n, H, s);
@@ -386,7 +485,7 @@ static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cud
     float2* Tb = (float2*)p->T32;
     const bool warp = col_warp_ok(p->Q);
     if (st == 0 || st == 2) {
-        if (warp) {
+        if (row_warp_ok(p->Q)) {
             const dim3 grid((p->n + 7) / 8, p->L + 1);
             if (st == 0) return row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
             return row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
@@ -421,15 +520,15 @@ static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cud
         return cudaErrorInvalidValue;
     }
     switch (p->L) {
-        case 0: return launch_col_pc_q<0>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 1: return launch_col_pc_q<1>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 2: return launch_col_pc_q<2>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 3: return launch_col_pc_q<3>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 4: return launch_col_pc_q<4>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 5: return launch_col_pc_q<5>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 6: return launch_col_pc_q<6>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 7: return launch_col_pc_q<7>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
-        case 8: return launch_col_pc_q<8>(p->Q, Tb, p->Pp, p->tw32, p->n, p->H, s);
+        case 0: return launch_col_pc_q<0>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 1: return launch_col_pc_q<1>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 2: return launch_col_pc_q<2>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 3: return launch_col_pc_q<3>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 4: return launch_col_pc_q<4>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 5: return launch_col_pc_q<5>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 6: return launch_col_pc_q<6>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 7: return launch_col_pc_q<7>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 8: return launch_col_pc_q<8>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -110,7 +110,7 @@ extern "C" rte_status rte_destroy(rte_plan p) {
     if (!p) return RTE_OK;
     cudaDeviceSynchronize();
     krylov_free(p);
-    void* bufs[] = {p->S3p, p->Pp, p->pv1, p->pv2, p->tw64, p->tw32, p->twff, p->Sff, p->Sffp, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
+    void* bufs[] = {p->S3p, p->Pp, p->pv1, p->pv2, p->tw64, p->tw32, p->twff, p->Sff, p->Sffp, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->Tz32, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
                     p->d32, p->dscal, p->part64, p->f_dev, p->u_dev, p->ref};
     for (void* b : bufs)
@@ -187,10 +187,13 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
         TRY(dalloc(&p->S64, ns * sizeof(double2)));
         TRY(dalloc(&p->S32, ns * sizeof(float2)));
         TRY(dalloc(&p->S16, ns * sizeof(__nv_bfloat162)));
-        if (Q == 64 || Q == 128 || Q == 256 || Q == 512) {
+        if (Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024) {
             TRY(dalloc(&p->S32p, ns * sizeof(float2)));
             TRY(dalloc(&p->S16p, ns * sizeof(__nv_bfloat162)));
             TRY(dalloc(&p->Sffp, ns * sizeof(ffc)));
+            // Q = 1024: the column passes run two 512-point residues; the
+            // first residue's result waits here
+            if (Q == 1024) TRY(dalloc(&p->Tz32, (size_t)nch * H * n * sizeof(float2)));
         } else {
             TRY(dalloc(&p->Sff, ns * sizeof(ffc)));
         }

@@ -144,6 +144,16 @@ __device__ __forceinline__ int wfreq_rt(int R, int j, int lane) {
     return (lane >> LP) + R * (j + R * c);
 }
 
+// frequency of slot sl (= j * 32 + lane) of the column passes' spectra.
+// Q <= 512: the warp FFT's own order.  Q = 1024 runs as two 512-point warp
+// FFTs (residues r = xi mod 2, see k_col_warp2): slot r * 512 + s holds
+// xi = 2 wfreq_512(s) + r.
+__device__ __forceinline__ int slot_freq(int sl, int Q) {
+    if (Q <= 512) return wfreq_rt(Q / 32, sl >> 5, sl & 31);
+    const int r = sl >> 9, s = sl & 511;
+    return 2 * wfreq_rt(16, s >> 5, s & 31) + r;
+}
+
 // forward: v[r] = x[lane + 32 r]  ->  v[j] = X[wfreq<R>(j, lane)]
 // tw: table exp(-2 pi i t / Q); S: this warp's scratch (wfft_shape<R>::SCRATCH
 // elements of shared memory)

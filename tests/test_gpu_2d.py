@@ -63,6 +63,23 @@ def test_apply_K_fp64_matches_direct_sum(n, L, mu_t, mu_s, g):
     p.close()
 
 
+@pytest.mark.parametrize("n,L", [(20, 8), (33, 2), (7, 0), (40, 4)])
+def test_float_float_and_fp32_operators_at_q1024(n, L):
+    """Q = 1024 (two 512-point residues per column in the FP32 and float-float
+    column passes): K64e to 1e-12 and K32 to 1e-5 against the direct sum."""
+    sig = rte_synth.hg_sigma_hat(0.5, L)
+    p = _plan(n, 10.0, 9.0, sig, q_policy=1024)
+    assert p.Q == 1024
+    rng = np.random.default_rng(300 + n)
+    x = random_packed(rng, L, n)
+    ref = oracle.apply_K_2d(n, 1.0 / n, 10.0, 9.0, sig, packed_to_full(x))
+    ye = p.apply_K64e(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(ye, ref[L:]) < 1e-12
+    y = p.apply_K(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, ref[L:]) < 1e-12
+    p.close()
+
+
 @pytest.mark.parametrize("n,L,mu_t,mu_s,g", CASES)
 def test_rhs_matches_direct_sum(n, L, mu_t, mu_s, g):
     p = _plan(n, mu_t, mu_s, rte_synth.hg_sigma_hat(g, L))
@@ -78,7 +95,9 @@ def test_rhs_matches_direct_sum(n, L, mu_t, mu_s, g):
 # R = 2, 4, 8, 16 registers per lane, n ragged against their 8/16-row blocks
 @pytest.mark.parametrize("prec,tol", [("mixed_fp32", 1e-5), ("mixed_bf16", 1e-2)])
 @pytest.mark.parametrize("n,L,q", [(12, 3, 0), (20, 8, 0), (33, 2, 0), (12, 3, 64), (20, 8, 128), (33, 2, 256),
-                                   (33, 5, 512), (64, 1, 128)])
+                                   (33, 5, 512), (64, 1, 128),
+                                   # Q = 1024: two 512-point residues per column
+                                   (20, 8, 1024), (33, 2, 1024), (7, 0, 1024), (64, 4, 1024)])
 def test_apply_K32(prec, tol, n, L, q):
     sig = rte_synth.hg_sigma_hat(0.5, L)
     p = _plan(n, 10.0, 9.0, sig, prec=prec, q_policy=q)
@@ -206,7 +225,8 @@ def _wnorm(v):
     return float(np.sqrt(np.sum(w * np.sum(np.abs(v.reshape(v.shape[0], -1)) ** 2, axis=1))))
 
 
-@pytest.mark.parametrize("prec,q", [("mixed_fp32", 0), ("mixed_bf16", 0), ("mixed_fp32", 72)])
+@pytest.mark.parametrize("prec,q", [("mixed_fp32", 0), ("mixed_bf16", 0), ("mixed_fp32", 72), ("mixed_fp32", 1024),
+                                    ("mixed_bf16", 1024)])
 def test_mixed_residual_equals_unfused_residual(prec, q):
     """The mixed solve forms every residual as K~(mu_s sigma_hat u + g) - u in
     one float-float application and b in FP32 only.  The residual rebuilt from
