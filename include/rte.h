@@ -211,8 +211,9 @@ rte_status rte_batch_plan(rte_batch b, int i, rte_plan* out);
 
 /* Autotuner: for a 2D grid of n cells per side and truncation L, time the
  * FP32 operator application (prec = RTE_PREC_MIXED_FP32 or _BF16SPEC) for
- * the candidate padded lengths Q (the smallest even 2^a 3^b >= 2n-1 and the
- * next two) and row passes {0 = default: one warp per line with the FFT in
+ * the candidate padded lengths Q (the smallest even 2^a 3^b >= 2n-1, the
+ * next two, and the smallest power of two in 64..1024 that is >= 2n-1, whose
+ * column passes use the warp-register FFT) and row passes {0 = default: one warp per line with the FFT in
  * registers when Q = 32 * 2^j, 64 <= Q <= 512, else the shared-memory FFT
  * with 8 rows per block; or the shared-memory FFT with 2, 4, 8, 16 rows per
  * block}, `reps` applications each, with CUDA

@@ -358,7 +358,9 @@ extern "C" rte_status rte_autotune(int n, int L, int prec, int reps, int* Q_out,
     cudaStream_t s = (cudaStream_t)stream;
     double sig[RTE_MAX_L + 1];
     for (int k = 0; k <= L; ++k) sig[k] = k == 0 ? 1.0 : 0.5;
-    int cands[3];
+    // the three smallest admissible Q, and the smallest Q whose column passes
+    // run on the warp-register FFT (64, 128, ..., 1024) when it is not among them
+    int cands[4];
     int nc = 0;
     int q = choose_Q(n);
     while (nc < 3) {
@@ -366,6 +368,11 @@ extern "C" rte_status rte_autotune(int n, int L, int prec, int reps, int* Q_out,
         ++q;
         while (q % 2 || !smooth23(q)) ++q;
     }
+    for (int w = 64; w <= 1024; w *= 2)
+        if (w >= 2 * n - 1) {
+            if (w > cands[nc - 1]) cands[nc++] = w;
+            break;
+        }
     double best = 1e30;
     int bq = cands[0], brb = 0;
     cudaEvent_t e0, e1;
