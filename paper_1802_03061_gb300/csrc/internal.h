@@ -28,6 +28,7 @@ struct KrylovWs {
     void* w = nullptr;       // nr reals
     double* part = nullptr;  // partial sums [(m+1)][tiles]
     double* st = nullptr;    // device GMRES state (see krylov.cu)
+    void* Z = nullptr;       // preconditioned inner solves: (m+1) x nr floats, z_j = M v_j
 };
 void krylov_free_ws(KrylovWs& ws);
 

@@ -469,7 +469,8 @@ __global__ void __launch_bounds__(256) k_step_dot4(float* __restrict__ V, long n
 
 __global__ void __launch_bounds__(256) k_step_upd4(const float* __restrict__ V, long nr, const float* __restrict__ w,
                                                    float* __restrict__ vin, GmresDev* __restrict__ st, long nw1,
-                                                   double* __restrict__ part, cudaGraphConditionalHandle loop) {
+                                                   double* __restrict__ part, cudaGraphConditionalHandle loop,
+                                                   const float* __restrict__ zsrc, float* __restrict__ Z) {
     const int j = st->j, count = j + 1;
     const float s = (float)st->vscale;
     const int nb = gridDim.x;
@@ -504,6 +505,11 @@ __global__ void __launch_bounds__(256) k_step_upd4(const float* __restrict__ V, 
     }
     float* vn = const_cast<float*>(V) + (long)(j + 1) * nr;
     float hi = 0.f, lo = 0.f;
+    if (Z) {  // z_j = M v_j (see k_step_upd)
+        float* zj = Z + (long)j * nr;
+        if (in0) *reinterpret_cast<float4*>(zj + e0) = f4scale(*reinterpret_cast<const float4*>(zsrc + e0), s);
+        if (in1) *reinterpret_cast<float4*>(zj + e1) = f4scale(*reinterpret_cast<const float4*>(zsrc + e1), s);
+    }
     if (in0) {
         *reinterpret_cast<float4*>(vn + e0) = a0;
         *reinterpret_cast<float4*>(vin + e0) = a0;
@@ -605,9 +611,12 @@ __global__ void __launch_bounds__(256) k_step_dot(float* __restrict__ V, long nr
     if (threadIdx.x == 0) st->cnt1 = 0u;
 }
 
+// zsrc / Z (right-preconditioned steps): zsrc = M applied to this step's
+// unscaled input, stored scaled as z_j = M v_j in Z[j] for the cycle end
 __global__ void __launch_bounds__(256) k_step_upd(const float* __restrict__ V, long nr, const float* __restrict__ w,
                                                   float* __restrict__ vin, GmresDev* __restrict__ st, long nw1,
-                                                  double* __restrict__ part, cudaGraphConditionalHandle loop) {
+                                                  double* __restrict__ part, cudaGraphConditionalHandle loop,
+                                                  const float* __restrict__ zsrc, float* __restrict__ Z) {
     const int j = st->j, count = j + 1;
     const float s = (float)st->vscale;
     const int nb = gridDim.x;
@@ -642,6 +651,7 @@ __global__ void __launch_bounds__(256) k_step_upd(const float* __restrict__ V, l
             vn[e] = nv;
             vin[e] = nv;
             ff_fma(hi, lo, nv, nv * (e < nw1 ? 1.f : 2.f));
+            if (Z) Z[(long)j * nr + e] = s * zsrc[e];
         }
     }
     ff_warp_sum(hi, lo);
@@ -860,6 +870,7 @@ template <typename T> struct Gm {
     T* V;
     T* w;
     T* vin;
+    T* Z = nullptr;  // right-preconditioned: z_j = M v_j, j = 0..m
     GmresDev* st;
     double* part;
     long nr, nw1;
@@ -867,7 +878,7 @@ template <typename T> struct Gm {
 };
 
 template <typename T>
-static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream_t s) {
+static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream_t s, bool pc) {
     G.p = p;
     G.nr = p->nr;
     G.nw1 = p->dim == 2 ? 2L * p->n * p->n : p->nr;
@@ -884,7 +895,12 @@ static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream
         RTE_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(GmresDev), s));
         ws.m = m;
     }
+    if (pc && !ws.Z && cudaMalloc(&ws.Z, (size_t)(m + 1) * p->nr * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return RTE_ENOMEM;
+    }
     G.V = (T*)ws.V;
+    G.Z = (T*)ws.Z;
     G.vin = G.V + (long)(m + 1) * p->nr;  // slot m+1 is the matvec input
     G.w = (T*)ws.w;
     G.st = (GmresDev*)ws.st;
@@ -1146,11 +1162,13 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditiona
             if (nr % 4 == 0) {
                 k_step_dot4<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
                 k_step_upd4<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
-                                               G.nw1, G.part, loop);
+                                               G.nw1, G.part, loop, pc ? G.p->pv1 : nullptr,
+                                               pc ? (float*)G.Z : nullptr);
             } else {
                 k_step_dot<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
                 k_step_upd<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
-                                              G.nw1, G.part, loop);
+                                              G.nw1, G.part, loop, pc ? G.p->pv1 : nullptr,
+                                              pc ? (float*)G.Z : nullptr);
             }
             rte_count_launches(2);
             RTE_CUDA_TRY(cudaGetLastError());
@@ -1261,7 +1279,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
     const bool use_pc = mixed && pc && !use_mr;      // preconditioned inner GMRES
     const bool cgs2 = !mixed;
     Gm<T> G;
-    TRYS(gm_setup<T>(G, p, ws, m, cs));
+    TRYS(gm_setup<T>(G, p, ws, m, cs, use_pc));
     RTE_CUDA_TRY(cudaStreamSynchronize(cs));
     const long nr = p->nr;
     const int gr = grid_for(nr), nb = tiles(nr);
@@ -1399,15 +1417,9 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
             SEG(cycle_body, dc, &info->k_cycle, {
                 k_solve_tri<<<1, 32, 0, cs>>>(G.st);
                 if (use_pc) {
-                    // x += M (V y)
-                    if constexpr (sizeof(T) == sizeof(float)) {
-                        k_zero_T<float><<<gr, 256, 0, cs>>>(p->pv2, nr);
-                        k_maxpy<float><<<nb, 256, 0, cs>>>((const float*)G.V, nr, p->pv2, G.st->y, &G.st->j, 0, 1.0,
-                                                          nw1, nullptr);
-                        TRYS(plan_apply_pc32(p, p->pv2, p->pv1, cs));
-                        k_add_T<float><<<gr, 256, 0, cs>>>((float*)x, p->pv1, nr);
-                        rte_count_launches(3);
-                    }
+                    // x += M (V y) = Z y: the steps stored z_j = M v_j
+                    k_maxpy<T><<<nb, 256, 0, cs>>>((const T*)G.Z, nr, x, G.st->y, &G.st->j, 0, 1.0, nw1, nullptr);
+                    rte_count_launches(1);
                 } else {
                     k_maxpy<T><<<nb, 256, 0, cs>>>(G.V, nr, x, G.st->y, &G.st->j, 0, 1.0, nw1, nullptr);
                     rte_count_launches(1);
@@ -1569,6 +1581,7 @@ void krylov_free_ws(KrylovWs& ws) {
     if (ws.w) cudaFree(ws.w);
     if (ws.part) cudaFree(ws.part);
     if (ws.st) cudaFree(ws.st);
+    if (ws.Z) cudaFree(ws.Z);
     ws = KrylovWs();
 }
 
