@@ -69,7 +69,8 @@ def test_batch_matches_single_plan_solves():
 def test_autotuner_returns_a_valid_choice():
     from paper_1802_03061_gb300 import _binding as B
     q, rb, ms = B.rte_autotune(96, 2, "mixed_fp32", 5)
-    assert q >= 191 and q % 2 == 0 and rb in (2, 4, 8, 16) and ms > 0
+    # rb 0 = the default row passes (warp-register FFT where Q allows it)
+    assert q >= 191 and q % 2 == 0 and rb in (0, 2, 4, 8, 16) and ms > 0
 
 
 def test_full_batch_workload_512_instances():
