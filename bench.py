@@ -480,8 +480,8 @@ def run_batch(args):
                        "all_converged": conv, "iters_total": int(sum(s_["iters"] for s_ in stats)),
                        "sequential_single_solves_ms": seq_ms,
                        "precond": bool(args.precond),
-                       "precond_note": "periodic preconditioner on every instance (warp passes for Q = 64..512, "
-                                       "shared-memory passes for Q = 768, 1024)" if args.precond else None,
+                       "precond_note": "periodic preconditioner on every instance (warp-register column passes "
+                                       "for Q = 64..1024, shared-memory passes for other Q)" if args.precond else None,
                        "instances_on_rank0": len(inst), "parallelism": "instances sharded by cost" if ws > 1
                        else "single GPU",
                        "create_s": t_create, "l2": "flushed before every timed step"},
