@@ -94,11 +94,16 @@ typedef struct {
     int use_guess;     /* [0] 1: u_dev holds an initial guess on entry */
     int q_policy;      /* [0] 0: smallest even 2^a 3^b >= 2n-1; else Q itself */
     int inner_solver;  /* [RTE_INNER_GMRES] Krylov method of the FP32 inner solves */
-    int precond;       /* [0] 1: periodic preconditioner for the inner GMRES (mixed modes; 2D needs
-                          Q = 32 * 2^j, 64 <= Q <= 512, else it is not used): GMRES on (I-K) M with
-                          M = crop (I - C)^{-1} pad, C the convolution on the periodic padded grid,
-                          inverted per frequency; same answer, fewer inner iterations.  Not in the
-                          paper.  Built on the first solve that asks for it (allocates). */
+    int precond;       /* [0] 1: periodic preconditioner for the inner GMRES (mixed modes; 2D up to
+                          Q = 1024, else it is not used): GMRES on (I-K) M with M built from
+                          (I - C)^{-1}, C the convolution on the periodic padded grid, inverted per
+                          frequency; same answer, fewer inner iterations.  Not in the paper.  Built
+                          on the first solve that asks for it (allocates). */
+    int precond_lmax;  /* [0] 2D: the preconditioner inverts the modes |k| <= lmax (block lower
+                          triangular: the higher modes keep their coupling to those, not among
+                          themselves); 0 = the smallest lmax with (mu_s/mu_t) max_{k>lmax}
+                          |sigma_hat_k| <= 0.03, >= L = all modes.  Read when the preconditioner
+                          is built. */
 } rte_opts;
 
 typedef struct {

@@ -81,6 +81,7 @@ struct rte_plan_s {
     float* pv1 = nullptr;      // FP32 field temporaries of the preconditioned solve
     float* pv2 = nullptr;
     bool pc_ready = false;
+    int pc_nl = 0;                   // 2D: channels the preconditioner inverts (2 lmax + 1)
     // cell weights D_m, m = 0..2L (2D) or D (3D), computed on the device
     double* Dm = nullptr;
     // pass intermediates: 2D [nch][H][n] complex; 3D T1 [n][H][n], T2 [H][Q][n]

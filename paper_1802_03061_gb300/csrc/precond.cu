@@ -47,10 +47,15 @@ __global__ void k_build_pc3d(const double* __restrict__ S3, float* __restrict__ 
 
 // 2D: one thread per (xi_x, xi_y), xi_y = 0..Q/2.  T[c][c'] = Q^2 *
 // mix(S(xi))[c][c'] * w(c') with w = mu_s sigma_hat_{k(c')} (the row pass's
-// input weights); Gauss-Jordan with partial pivoting on I - T in complex FP64.
+// input weights).  With the first nl channels (modes |k| <= lmax) as the
+// inverted block, the stored matrix is P = T[:, <nl] (I - T_ll)^{-1}
+// (Gauss-Jordan with partial pivoting in complex FP64), so that
+// M x = x + crop P pad(x_<nl): for nl = 2L+1 this is (I - T)^{-1} exactly
+// (P = (I - T)^{-1} - I); for fewer channels the higher modes keep their
+// coupling to the inverted block and drop the weak rest.
 template <int L>
 __global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __restrict__ Pp, int H, int Q,
-                             RowParams rp, double Q2) {
+                             RowParams rp, double Q2, int nl) {
     constexpr int NCH = 2 * L + 1;
     const int QH = Q / 2 + 1, QR = pc_row(Q);
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,26 +68,29 @@ __global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __r
         sr[m] = v.x;
         si[m] = v.y;
     }
-    double2 A[NCH][NCH];  // I - T, then its inverse (Gauss-Jordan in place)
-    for (int cp = 0; cp < NCH; ++cp) {
+    double2 T[NCH][NCH];  // columns < nl used
+    for (int cp = 0; cp < nl; ++cp) {
         double2 in[NCH], o[NCH];
         for (int c = 0; c < NCH; ++c) in[c] = make_double2(c == cp ? 1.0 : 0.0, 0.0);
         mode_mix<L, double2>(sr, si, in, o);
         const double w = rp.wk[ch_mode(cp)] * Q2;
-        for (int c = 0; c < NCH; ++c) A[c][cp] = make_double2((c == cp ? 1.0 : 0.0) - w * o[c].x, -w * o[c].y);
+        for (int c = 0; c < NCH; ++c) T[c][cp] = make_double2(w * o[c].x, w * o[c].y);
     }
-    double2 Inv[NCH][NCH];
-    for (int r = 0; r < NCH; ++r)
-        for (int c = 0; c < NCH; ++c) Inv[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    for (int col = 0; col < NCH; ++col) {
+    double2 A[NCH][NCH], Inv[NCH][NCH];  // I - T_ll, then (I - T_ll)^{-1} (nl x nl)
+    for (int r = 0; r < nl; ++r)
+        for (int c = 0; c < nl; ++c) {
+            A[r][c] = make_double2((r == c ? 1.0 : 0.0) - T[r][c].x, -T[r][c].y);
+            Inv[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+        }
+    for (int col = 0; col < nl; ++col) {
         int piv = col;
         double best = hypot(A[col][col].x, A[col][col].y);
-        for (int r = col + 1; r < NCH; ++r) {
+        for (int r = col + 1; r < nl; ++r) {
             const double a = hypot(A[r][col].x, A[r][col].y);
             if (a > best) { best = a; piv = r; }
         }
         if (piv != col) {
-            for (int c = 0; c < NCH; ++c) {
+            for (int c = 0; c < nl; ++c) {
                 double2 t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t;
                 t = Inv[col][c]; Inv[col][c] = Inv[piv][c]; Inv[piv][c] = t;
             }
@@ -90,85 +98,99 @@ __global__ void k_build_pc2d(const double2* __restrict__ S64, __nv_bfloat16* __r
         const double2 d = A[col][col];
         const double dd = d.x * d.x + d.y * d.y;
         const double2 inv = make_double2(d.x / dd, -d.y / dd);
-        for (int c = 0; c < NCH; ++c) {
+        for (int c = 0; c < nl; ++c) {
             A[col][c] = cmul(A[col][c], inv);
             Inv[col][c] = cmul(Inv[col][c], inv);
         }
-        for (int r = 0; r < NCH; ++r) {
+        for (int r = 0; r < nl; ++r) {
             if (r == col) continue;
             const double2 f = A[r][col];
-            for (int c = 0; c < NCH; ++c) {
+            for (int c = 0; c < nl; ++c) {
                 A[r][c] = csub(A[r][c], cmul(f, A[col][c]));
                 Inv[r][c] = csub(Inv[r][c], cmul(f, Inv[col][c]));
             }
         }
     }
     for (int c = 0; c < NCH; ++c)
-        for (int cp = 0; cp < NCH; ++cp) {
-            const bool im = ((ch_mode(c) ^ ch_mode(cp)) & 1) != 0;
-            const double v = (im ? Inv[c][cp].y : Inv[c][cp].x) / Q2;
-            Pp[(((long)kx * NCH + c) * NCH + cp) * QR + ky] = __float2bfloat16_rn((float)v);
+        for (int cq = 0; cq < nl; ++cq) {
+            double2 v = make_double2(0.0, 0.0);
+            for (int cp = 0; cp < nl; ++cp) v = cadd(v, cmul(T[c][cp], Inv[cp][cq]));
+            const bool im = ((ch_mode(c) ^ ch_mode(cq)) & 1) != 0;
+            Pp[(((long)kx * NCH + c) * nl + cq) * QR + ky] = __float2bfloat16_rn((float)((im ? v.y : v.x) / Q2));
         }
 }
 
-// y[c] += sum_c' P[c][c'] x[c'] for one frequency (tagged entries: i v when
-// the channel modes differ in parity); sg = -1 mirrors (S P S)
-template <int L>
-__device__ __forceinline__ void pc_mix_one(float2* X, int QS, int sl, const __nv_bfloat16* P, int QR) {
+// y[c] = sum_{c' < nl} P[c][c'] x[c'] for one frequency (or the mirror pair
+// (xi, Q - xi), the mirror with S P S), every output channel c < 2L+1.  The
+// loop over the inverted inputs c' has a run-time bound; for each c' the
+// 2L+1 coefficients P[.][c'] are independent loads.  An entry is i v when the
+// channel modes differ in parity and its mirror sign flips when exactly one
+// of c, c' is a B channel; c' enters both only through (parity, B) -- uniform
+// over the block -- so a switch on them keeps every tag a compile-time constant.
+template <int L, bool PAIR, int PC, bool BC>
+__device__ __forceinline__ void pc_mix_term(float2* ra, float2* rb, float2 a, float2 b, const __nv_bfloat16* Pcp,
+                                            long cstride) {
     constexpr int NCH = 2 * L + 1;
-    float2 in[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) in[c] = X[c * QS + sl];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int cp = 0; cp < NCH; ++cp) {
-            const float v = __bfloat162float(P[(c * NCH + cp) * QR]);
-            if ((ch_mode(c) ^ ch_mode(cp)) & 1) {
-                acc.x -= v * in[cp].y;
-                acc.y += v * in[cp].x;
+        const float v = __bfloat162float(Pcp[c * cstride]);
+        const bool im = ((ch_mode(c) & 1) ^ PC) != 0;
+        if (im) {
+            ra[c].x -= v * a.y;
+            ra[c].y += v * a.x;
+        } else {
+            ra[c].x += v * a.x;
+            ra[c].y += v * a.y;
+        }
+        if (PAIR) {
+            const float w = ch_isB(c) != BC ? -v : v;
+            if (im) {
+                rb[c].x -= w * b.y;
+                rb[c].y += w * b.x;
             } else {
-                acc.x += v * in[cp].x;
-                acc.y += v * in[cp].y;
+                rb[c].x += w * b.x;
+                rb[c].y += w * b.y;
             }
         }
-        X[c * QS + sl] = acc;
     }
 }
 
-// the pair (xi, Q - xi): one load of P serves both, the mirror with S P S
-template <int L>
-__device__ __forceinline__ void pc_mix_pair(float2* X, int QS, int s1, int s2, const __nv_bfloat16* P, int QR) {
+template <int L, bool PAIR>
+__device__ __forceinline__ void pc_mix(float2* X, int QS, int s1, int s2, const __nv_bfloat16* P, int QR, int nl) {
     constexpr int NCH = 2 * L + 1;
-    float2 a[NCH], b[NCH];
+    float2 ra[NCH], rb[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        a[c] = X[c * QS + s1];
-        b[c] = X[c * QS + s2];
+        ra[c] = make_float2(0.f, 0.f);
+        rb[c] = make_float2(0.f, 0.f);
+    }
+    const long cstride = (long)nl * QR;  // P[c][c'] at P + c * nl * QR + c' * QR
+    for (int cp = 0; cp < nl; ++cp) {
+        const float2 a = X[cp * QS + s1];
+        const float2 b = PAIR ? X[cp * QS + s2] : make_float2(0.f, 0.f);
+        const __nv_bfloat16* Pcp = P + (long)cp * QR;
+        const int pc = ch_mode(cp) & 1;
+        const bool bc = ch_isB(cp);
+        if (pc == 0 && !bc) pc_mix_term<L, PAIR, 0, false>(ra, rb, a, b, Pcp, cstride);
+        else if (pc == 0) pc_mix_term<L, PAIR, 0, true>(ra, rb, a, b, Pcp, cstride);
+        else if (!bc) pc_mix_term<L, PAIR, 1, false>(ra, rb, a, b, Pcp, cstride);
+        else pc_mix_term<L, PAIR, 1, true>(ra, rb, a, b, Pcp, cstride);
     }
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int cp = 0; cp < NCH; ++cp) {
-            const float v = __bfloat162float(P[(c * NCH + cp) * QR]);
-            const float w = ch_isB(c) != ch_isB(cp) ? -v : v;
-            if ((ch_mode(c) ^ ch_mode(cp)) & 1) {
-                ra.x -= v * a[cp].y;
-                ra.y += v * a[cp].x;
-                rb.x -= w * b[cp].y;
-                rb.y += w * b[cp].x;
-            } else {
-                ra.x += v * a[cp].x;
-                ra.y += v * a[cp].y;
-                rb.x += w * b[cp].x;
-                rb.y += w * b[cp].y;
-            }
-        }
-        X[c * QS + s1] = ra;
-        X[c * QS + s2] = rb;
+        X[c * QS + s1] = ra[c];
+        if (PAIR) X[c * QS + s2] = rb[c];
     }
+}
+
+template <int L>
+__device__ __forceinline__ void pc_mix_one(float2* X, int QS, int sl, const __nv_bfloat16* P, int QR, int nl) {
+    pc_mix<L, false>(X, QS, sl, sl, P, QR, nl);
+}
+template <int L>
+__device__ __forceinline__ void pc_mix_pair(float2* X, int QS, int s1, int s2, const __nv_bfloat16* P, int QR,
+                                            int nl) {
+    pc_mix<L, true>(X, QS, s1, s2, P, QR, nl);
 }
 
 // column pass of the preconditioner: FFT_y of every channel, per frequency
@@ -176,26 +198,26 @@ __device__ __forceinline__ void pc_mix_pair(float2* X, int QS, int s1, int s2, c
 // The block's slice of Pp is prefetched into L2 while the forward FFTs run.
 template <int L, int R>
 __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb, const __nv_bfloat16* __restrict__ Pp,
-                                                     const float2* __restrict__ tw, int n, int H) {
+                                                     const float2* __restrict__ tw, int n, int H, int nl) {
     constexpr int NCH = 2 * L + 1;
     constexpr int Q = 32 * R;
     constexpr int QR = Q / 2 + 8;
     constexpr int QS = wfft_shape<R>::SCRATCH;
-    constexpr unsigned SLICE = NCH * NCH * QR * 2;  // bytes, a multiple of 16
     constexpr unsigned CHUNK = 16384;
+    const unsigned slice = NCH * nl * QR * 2;  // bytes, a multiple of 16
     extern __shared__ unsigned char smraw[];
     float2* X = reinterpret_cast<float2*>(smraw);  // [NCH][QS]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * NCH * QR;
+    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * nl * QR;
     if (warp == nw - 1) {
         const char* base = reinterpret_cast<const char*>(Pk);
-        for (unsigned off = lane * CHUNK; off < SLICE; off += 32 * CHUNK) {
-            const unsigned sz = SLICE - off < CHUNK ? SLICE - off : CHUNK;
+        for (unsigned off = lane * CHUNK; off < slice; off += 32 * CHUNK) {
+            const unsigned sz = slice - off < CHUNK ? slice - off : CHUNK;
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(sz) : "memory");
         }
     }
-    for (int c = warp; c < NCH; c += nw) {
+    for (int c = warp; c < nl; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;
 #pragma unroll
@@ -211,10 +233,10 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
     __syncthreads();
     for (int t = threadIdx.x; t < Q / 2; t += blockDim.x) {
         if (t == 0) {  // xi = 0 and xi = Q/2 are their own mirrors
-            pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR);
-            pc_mix_one<L>(X, QS, wslot<R>(Q / 2), Pk + Q / 2, QR);
+            pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR, nl);
+            pc_mix_one<L>(X, QS, wslot<R>(Q / 2), Pk + Q / 2, QR, nl);
         } else {
-            pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(Q - t), Pk + t, QR);
+            pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(Q - t), Pk + t, QR, nl);
         }
     }
     __syncthreads();
@@ -241,30 +263,30 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
 template <int L>
 __global__ void __launch_bounds__(256, 2) k_col_warp_pc2(float2* __restrict__ Tb, float2* __restrict__ Tz,
                                                          const __nv_bfloat16* __restrict__ Pp,
-                                                         const float2* __restrict__ tw, int n, int H) {
+                                                         const float2* __restrict__ tw, int n, int H, int nl) {
     constexpr int NCH = 2 * L + 1;
     constexpr int R = 16, QW = 512, Q = 1024;
     constexpr int QR = Q / 2 + 8;
     constexpr int QS = wfft_shape<R>::SCRATCH;
-    constexpr unsigned SLICE = NCH * NCH * QR * 2;
     constexpr unsigned CHUNK = 16384;
+    const unsigned slice = NCH * nl * QR * 2;
     extern __shared__ unsigned char smraw[];
     float2* twl = reinterpret_cast<float2*>(smraw);  // exp(-2 pi i t / 512)
     float2* X = twl + QW;                            // [NCH][QS]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * NCH * QR;
+    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * nl * QR;
     if (warp == nw - 1) {
         const char* base = reinterpret_cast<const char*>(Pk);
-        for (unsigned off = lane * CHUNK; off < SLICE; off += 32 * CHUNK) {
-            const unsigned sz = SLICE - off < CHUNK ? SLICE - off : CHUNK;
+        for (unsigned off = lane * CHUNK; off < slice; off += 32 * CHUNK) {
+            const unsigned sz = slice - off < CHUNK ? slice - off : CHUNK;
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(sz) : "memory");
         }
     }
     for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
     __syncthreads();
     for (int r = 0; r < 2; ++r) {
-        for (int c = warp; c < NCH; c += nw) {
+        for (int c = warp; c < nl; c += nw) {
             float2 v[R];
             const float2* col = Tb + ((long)c * H + kx) * n;
 #pragma unroll
@@ -286,13 +308,13 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc2(float2* __restrict__ Tb
         for (int t = threadIdx.x; t < QW / 2; t += blockDim.x) {
             if (r == 0) {
                 if (t == 0) {  // xi = 0 and xi = Q/2 are their own mirrors
-                    pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR);
-                    pc_mix_one<L>(X, QS, wslot<R>(QW / 2), Pk + QW, QR);
+                    pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR, nl);
+                    pc_mix_one<L>(X, QS, wslot<R>(QW / 2), Pk + QW, QR, nl);
                 } else {
-                    pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - t), Pk + 2 * t, QR);
+                    pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - t), Pk + 2 * t, QR, nl);
                 }
             } else {
-                pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - 1 - t), Pk + 2 * t + 1, QR);
+                pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - 1 - t), Pk + 2 * t + 1, QR, nl);
             }
         }
         __syncthreads();
@@ -320,7 +342,7 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc2(float2* __restrict__ Tb
 
 template <int L>
 static cudaError_t launch_col_pc2(float2* Tb, float2* Tz, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
-                                  cudaStream_t s) {
+                                  int nl, cudaStream_t s) {
     static bool once = false;
     cudaError_t e;
     if (!once) {
@@ -328,7 +350,7 @@ static cudaError_t launch_col_pc2(float2* Tb, float2* Tz, const __nv_bfloat16* P
         once = true;
     }
     const size_t smem = (size_t)(512 + (2 * L + 1) * wfft_shape<16>::SCRATCH) * sizeof(float2);
-    k_col_warp_pc2<L><<<H, 256, smem, s>>>(Tb, Tz, Pp, tw, n, H);
+    k_col_warp_pc2<L><<<H, 256, smem, s>>>(Tb, Tz, Pp, tw, n, H, nl);
     return cudaGetLastError();
 }
 
@@ -337,7 +359,7 @@ static cudaError_t launch_col_pc2(float2* Tb, float2* Tz, const __nv_bfloat16* P
 // order, FFT groups of G columns (as k_col_fused)
 template <int L>
 __global__ void __launch_bounds__(256) k_col_pc_fused(float2* __restrict__ Tb, const __nv_bfloat16* __restrict__ Pp,
-                                                      const float2* __restrict__ tw, ColParams p) {
+                                                      const float2* __restrict__ tw, ColParams p, int nl) {
     constexpr int NCH = 2 * L + 1;
     extern __shared__ unsigned char smraw[];
     float2* sm = reinterpret_cast<float2*>(smraw);
@@ -347,19 +369,19 @@ __global__ void __launch_bounds__(256) k_col_pc_fused(float2* __restrict__ Tb, c
     float2* X = sm + Q;
     float2* tmp = X + (long)NCH * Q;
     load_twiddles(twl, tw, Q);
-    for (int idx = threadIdx.x; idx < NCH * Q; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nl * Q; idx += blockDim.x) {
         const int c = idx / Q, e = idx - c * Q;
         X[idx] = e < n ? Tb[((long)c * H + kx) * n + e] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_channels<-1>(X, tmp, 0, NCH, p.G, p.sc, twl, 2 * n <= Q);
-    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * NCH * QR;
+    fft_channels<-1>(X, tmp, 0, nl, p.G, p.sc, twl, 2 * n <= Q);
+    const __nv_bfloat16* Pk = Pp + (long)kx * NCH * nl * QR;
     for (int t = threadIdx.x; t < Q / 2; t += blockDim.x) {
         if (t == 0) {
-            pc_mix_one<L>(X, Q, 0, Pk, QR);
-            pc_mix_one<L>(X, Q, Q / 2, Pk + Q / 2, QR);
+            pc_mix_one<L>(X, Q, 0, Pk, QR, nl);
+            pc_mix_one<L>(X, Q, Q / 2, Pk + Q / 2, QR, nl);
         } else {
-            pc_mix_pair<L>(X, Q, t, Q - t, Pk + t, QR);
+            pc_mix_pair<L>(X, Q, t, Q - t, Pk + t, QR, nl);
         }
     }
     __syncthreads();
@@ -385,12 +407,12 @@ static cudaError_t launch_col_pc_fused(rte_plan p, float2* Tb, cudaStream_t s) {
     cp.n = p->n; cp.Q = p->Q; cp.H = p->H; cp.L = L; cp.nin = 2 * L + 1;
     cp.sc = p->sched;
     cp.G = col_group<float2>(2 * L + 1, p->Q);
-    k_col_pc_fused<L><<<p->H, 256, pc_fused_smem(2 * L + 1, p->Q, cp.G), s>>>(Tb, p->Pp, p->tw32, cp);
+    k_col_pc_fused<L><<<p->H, 256, pc_fused_smem(2 * L + 1, p->Q, cp.G), s>>>(Tb, p->Pp, p->tw32, cp, p->pc_nl);
     return cudaGetLastError();
 }
 
 template <int L, int R>
-static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const float2* tw, int n, int H,
+static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const float2* tw, int n, int H, int nl,
                                  cudaStream_t s) {
     static bool once = false;
     cudaError_t e;
@@ -399,19 +421,19 @@ static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const floa
         once = true;
     }
     const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2);
-    k_col_warp_pc<L, R><<<H, 256, smem, s>>>(Tb, Pp, tw, n, H);
+    k_col_warp_pc<L, R><<<H, 256, smem, s>>>(Tb, Pp, tw, n, H, nl);
     return cudaGetLastError();
 }
 
 template <int L>
 static cudaError_t launch_col_pc_q(int Q, float2* Tb, float2* Tz, const __nv_bfloat16* Pp, const float2* tw, int n,
-                                   int H, cudaStream_t s) {
+                                   int H, int nl, cudaStream_t s) {
     switch (Q) {
-        case 1024: return Tz ? launch_col_pc2<L>(Tb, Tz, Pp, tw, n, H, s) : cudaErrorInvalidValue;
-        case 64: return launch_col_pc<L, 2>(Tb, Pp, tw, n, H, s);
-        case 128: return launch_col_pc<L, 4>(Tb, Pp, tw, n, H, s);
-        case 256: return launch_col_pc<L, 8>(Tb, Pp, tw, n, H, s);
-        case 512: return launch_col_pc<L, 16>(Tb, Pp, tw, n, H, s);
+        case 1024: return Tz ? launch_col_pc2<L>(Tb, Tz, Pp, tw, n, H, nl, s) : cudaErrorInvalidValue;
+        case 64: return launch_col_pc<L, 2>(Tb, Pp, tw, n, H, nl, s);
+        case 128: return launch_col_pc<L, 4>(Tb, Pp, tw, n, H, nl, s);
+        case 256: return launch_col_pc<L, 8>(Tb, Pp, tw, n, H, nl, s);
+        case 512: return launch_col_pc<L, 16>(Tb, Pp, tw, n, H, nl, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -420,7 +442,7 @@ template <int L>
 static cudaError_t build_pc2d(rte_plan p, const RowParams& rp, cudaStream_t s) {
     const long tot = (long)p->H * (p->Q / 2 + 1);
     k_build_pc2d<L><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(p->S64, p->Pp, p->H, p->Q, rp,
-                                                                  (double)p->Q * p->Q);
+                                                                  (double)p->Q * p->Q, p->pc_nl);
     return cudaGetLastError();
 }
 
@@ -442,6 +464,21 @@ bool plan_precond_supported(const rte_plan p) {
 }
 
 // builds the preconditioner data once per plan (allocates; call outside any capture)
+// modes the 2D preconditioner inverts: rte_opts.precond_lmax, else the
+// smallest lmax with (mu_s/mu_t) max_{k > lmax} |sigma_hat_k| <= 0.03 (the
+// coupling left out of the inverted block stays small)
+static int pc_lmax(const rte_plan p) {
+    const int L = p->L, req = p->opts.precond_lmax;
+    if (req > 0) return req < L ? req : L;
+    const double rho = p->mu_t > 0.0 ? p->mu_s / p->mu_t : 0.0;
+    for (int l = 0; l < L; ++l) {
+        double m = 0.0;
+        for (int k = l + 1; k <= L; ++k) m = fmax(m, fabs(p->sigma_hat[k]));
+        if (rho * m <= 0.03) return l;
+    }
+    return L;
+}
+
 rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
     if (p->pc_ready) return RTE_OK;
     if (!plan_precond_supported(p)) return RTE_EUNSUPPORTED;
@@ -455,7 +492,8 @@ rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
         k_build_pc3d<<<1024, 256, 0, s>>>(p->S3_64, p->S3p, tot, p->mu_s, Q3);
         e = cudaGetLastError();
     } else {
-        const long tot = (long)p->H * pc_row(p->Q) * p->nch * p->nch;
+        p->pc_nl = 2 * pc_lmax(p) + 1;
+        const long tot = (long)p->H * pc_row(p->Q) * p->nch * p->pc_nl;
         if (cudaMalloc((void**)&p->Pp, tot * sizeof(__nv_bfloat16)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond matrices");
         if ((e = cudaMemsetAsync(p->Pp, 0, tot * sizeof(__nv_bfloat16), s)) != cudaSuccess)
             return rte_cuda_fail(e, "plan_precond_build");
@@ -485,11 +523,13 @@ static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cud
     float2* Tb = (float2*)p->T32;
     const bool warp = col_warp_ok(p->Q);
     if (st == 0 || st == 2) {
+        // forward: the inverted modes 0..lmax; inverse: every mode, out = x + v
+        const int lmax = (p->pc_nl - 1) / 2;
         if (row_warp_ok(p->Q)) {
-            const dim3 grid((p->n + 7) / 8, p->L + 1);
+            const dim3 grid((p->n + 7) / 8, st == 0 ? lmax + 1 : p->L + 1);
             if (st == 0) return row_fwd_warp<float2, float2>(p->Q, grid, (const float2*)x, nullptr, Tb, p->tw32, rp, s);
-            return row_inv_warp<float2, float2>(p->Q, grid, Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f,
-                                                0.f, s);
+            return row_inv_warp<float2, float2>(p->Q, grid, Tb, (const float2*)x, nullptr, (float2*)out, p->tw32, rp,
+                                                1.f, 1.f, 0.f, s);
         }
         static bool once = false;
         cudaError_t e;
@@ -499,10 +539,11 @@ static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cud
             once = true;
         }
         rp.RB = rows_per_block<float2>(p->Q);
-        const dim3 grid((p->n + rp.RB - 1) / rp.RB, p->L + 1);
+        const dim3 grid((p->n + rp.RB - 1) / rp.RB, st == 0 ? lmax + 1 : p->L + 1);
         const size_t smr = row_smem<float2>(p->Q, rp.RB);
         if (st == 0) k_row_fwd<float2, float2><<<grid, 256, smr, s>>>((const float2*)x, nullptr, Tb, p->tw32, rp);
-        else k_row_inv<float2, float2><<<grid, 256, smr, s>>>(Tb, nullptr, nullptr, (float2*)out, p->tw32, rp, 0.f, 1.f, 0.f);
+        else k_row_inv<float2, float2><<<grid, 256, smr, s>>>(Tb, (const float2*)x, nullptr, (float2*)out, p->tw32, rp,
+                                                              1.f, 1.f, 0.f);
         return cudaGetLastError();
     }
     if (!warp) {
@@ -520,15 +561,15 @@ static cudaError_t pc2d_pass(rte_plan p, int st, const float* x, float* out, cud
         return cudaErrorInvalidValue;
     }
     switch (p->L) {
-        case 0: return launch_col_pc_q<0>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 1: return launch_col_pc_q<1>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 2: return launch_col_pc_q<2>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 3: return launch_col_pc_q<3>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 4: return launch_col_pc_q<4>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 5: return launch_col_pc_q<5>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 6: return launch_col_pc_q<6>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 7: return launch_col_pc_q<7>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
-        case 8: return launch_col_pc_q<8>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, s);
+        case 0: return launch_col_pc_q<0>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 1: return launch_col_pc_q<1>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 2: return launch_col_pc_q<2>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 3: return launch_col_pc_q<3>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 4: return launch_col_pc_q<4>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 5: return launch_col_pc_q<5>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 6: return launch_col_pc_q<6>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 7: return launch_col_pc_q<7>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
+        case 8: return launch_col_pc_q<8>(p->Q, Tb, p->Tz32, p->Pp, p->tw32, p->n, p->H, p->pc_nl, s);
     }
     return cudaErrorInvalidValue;
 }

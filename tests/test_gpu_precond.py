@@ -32,9 +32,12 @@ def _plan(n, mu_t, mu_s, sig, dim=2, **kw):
     return Plan(n, mu_t=mu_t, mu_s=mu_s, sigma_hat=sig, dim=dim, **kw)
 
 
-def _ref_precond_2d(n, Q, mu_t, mu_s, sig, x_full):
-    """Reference M x for the full mode field x_full [2L+1][n][n] (modes -L..L)."""
+def _ref_precond_2d(n, Q, mu_t, mu_s, sig, x_full, lmax=None):
+    """Reference M x for the full mode field x_full [2L+1][n][n] (modes -L..L):
+    M x = x + crop(P pad(x_low)), P = C[:, low] (I - C[low, low])^{-1} per
+    frequency, low = the modes |k| <= lmax (all modes: M = crop (I - C)^{-1} pad)."""
     L = len(sig) - 1
+    lmax = L if lmax is None else min(lmax, L)
     M = 2 * L + 1
     N = n * n
     Kt = core.assemble_ktilde_2d(n, 1.0 / n, mu_t, L)
@@ -47,13 +50,15 @@ def _ref_precond_2d(n, Q, mu_t, mu_s, sig, x_full):
                 for o2 in range(-(n - 1), n):
                     i1, i2 = max(o1, 0), max(o2, 0)
                     G[k, kp, o2 % Q, o1 % Q] = blk[i2 * n + i1, (i2 - o2) * n + (i1 - o1)]
-    C = mu_s * np.fft.fft2(G, axes=(2, 3)) * s_full[None, :, None, None]
-    Minv = np.linalg.inv(np.eye(M)[None, None] - np.moveaxis(C, (2, 3), (0, 1)))
-    V = np.zeros((M, Q, Q), complex)
-    V[:, :n, :n] = x_full
+    C = np.moveaxis(mu_s * np.fft.fft2(G, axes=(2, 3)) * s_full[None, :, None, None], (2, 3), (0, 1))
+    lo = np.arange(L - lmax, L + lmax + 1)
+    inv = np.linalg.inv(np.eye(len(lo))[None, None] - C[:, :, lo][:, :, :, lo])
+    Pm = np.einsum("abkl,ablm->abkm", C[:, :, :, lo], inv)
+    V = np.zeros((len(lo), Q, Q), complex)
+    V[:, :n, :n] = x_full[lo]
     F = np.moveaxis(np.fft.fft2(V, axes=(1, 2)), 0, -1)
-    Y = np.einsum("abkl,abl->abk", Minv, F)
-    return np.fft.ifft2(np.moveaxis(Y, -1, 0), axes=(1, 2))[:, :n, :n]
+    Y = np.einsum("abkl,abl->abk", Pm, F)
+    return x_full + np.fft.ifft2(np.moveaxis(Y, -1, 0), axes=(1, 2))[:, :n, :n]
 
 
 @pytest.mark.parametrize("n,L,q", [(12, 2, 64), (20, 1, 128), (9, 3, 64), (12, 8, 64), (16, 4, 256),
@@ -64,12 +69,14 @@ def _ref_precond_2d(n, Q, mu_t, mu_s, sig, x_full):
 def test_precond_apply_2d_matches_reference(n, L, q):
     mu_t, mu_s = 10.0, 9.0
     sig = rte_synth.hg_sigma_hat(0.5, L)
-    p = _plan(n, mu_t, mu_s, sig, prec="mixed_fp32", q_policy=q)
     x = random_packed(np.random.default_rng(n), L, n).astype(np.complex64)
-    y = p.apply_precond32(torch.from_numpy(x).cuda()).cpu().numpy()
-    ref = _ref_precond_2d(n, q, mu_t, mu_s, sig, packed_to_full(x.astype(complex)))
-    assert rel(y, ref[L:]) < 2e-2
-    p.close()
+    # every mode inverted, and (L >= 3) only |k| <= 1 with the block-lower-triangular rest
+    for lmax in ([L, 1] if L >= 3 else [L]):
+        p = _plan(n, mu_t, mu_s, sig, prec="mixed_fp32", q_policy=q, precond_lmax=max(lmax, 1) if lmax < L else 99)
+        y = p.apply_precond32(torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = _ref_precond_2d(n, q, mu_t, mu_s, sig, packed_to_full(x.astype(complex)), lmax)
+        assert rel(y, ref[L:]) < 2e-2, lmax
+        p.close()
 
 
 def test_precond_apply_3d_matches_reference():
