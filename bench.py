@@ -313,6 +313,25 @@ def run_native(args):
     hbm_peak, peak_src = peaks()
     ach = col_bytes32 / (ms32[1] * 1e-3) / 1e9
     cufft_ms = cufft_pair_ms((L + 1, n, n), (plan.Q, plan.Q), real=False)
+    op_roof = {"kernel": "k_col_warp: operator column pass (FFT_y, mode mix, iFFT_y), FP32, %s spectra" % s_name,
+               "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+               "traffic": COLPASS_TRAFFIC.get(("k_col_warp<8,16,float2>", n, L, plan.Q, args.prec)),
+               "peak_source": peak_src, "algorithmic_bytes_per_launch": col_bytes32, "ms_per_launch": ms32[1]}
+    roof = op_roof
+    ms_pc = None
+    if args.prec != "fp64" and args.precond:
+        # with the preconditioner on, its column pass is the solve's largest
+        # kernel (one launch per inner step, like the operator's, but longer):
+        # algorithmic bytes = T in (nl channels) + T out (2L+1) + the table
+        ms_pc = B.rte_time_passes(plan.handle, 3, reps, int(stream.cuda_stream))
+        nl = 2 * B.rte_precond_info(plan.handle) + 1
+        pc_bytes = nl * H * n * 8 + nch * H * n * 8 + nch * nl * (Q // 2 + 8) * H * 2
+        ach_pc = pc_bytes / (ms_pc[1] * 1e-3) / 1e9
+        roof = {"kernel": "k_col_warp_pc: preconditioner column pass (FFT_y of the inverted channels, "
+                          "BF16 table mix, iFFT_y), FP32", "bound": "hbm", "achieved": ach_pc, "peak": hbm_peak,
+                "unit": "GB/s", "frac": ach_pc / hbm_peak,
+                "traffic": PCPASS_TRAFFIC.get(("k_col_warp_pc<8,16>", n, L, plan.Q, nl)),
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": pc_bytes, "ms_per_launch": ms_pc[1]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -331,8 +350,8 @@ def run_native(args):
                        float(np.mean(alt_ms)) if alt_ms else None,
                    ("unpreconditioned" if args.precond else "preconditioned") + "_iters":
                        float(np.mean(alt_its)) if alt_its else None,
-                   "pass_ms_precond": B.rte_time_passes(plan.handle, 3, reps, int(stream.cuda_stream))
-                   if args.prec != "fp64" else None,
+                   "pass_ms_precond": ms_pc,
+                   "roofline_operator_column": op_roof,
                    "bf16_spectra_ms_per_solve": float(np.mean(bf16_ms)) if bf16_ms else None,
                    "bf16_spectra_iters": float(np.mean(bf16_its)) if bf16_its else None,
                    "pass_ms_fp32": ms32, "pass_ms_fp64": ms64,
@@ -343,11 +362,7 @@ def run_native(args):
                                        "(%dx%d), FFT work only, no mode mix; compare matvec_fp32_ms"
                                        % (L + 1, plan.Q, plan.Q),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": {"kernel": "column pass (FFT_y, mode mix, iFFT_y), FP32, %s spectra" % s_name, "bound": "hbm",
-                     "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                     "traffic": COLPASS_TRAFFIC.get(("k_col_warp<8,16,float2>", n, L, plan.Q, args.prec)),
-                     "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": col_bytes32, "ms_per_launch": ms32[1]},
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * n * 8,
                 "d2h_bytes_per_step": int(plan.info["nreal"]) * 8},
         "gpu_launches": int(launches),
@@ -372,6 +387,9 @@ def run_native(args):
 # version that capture measured and for this workload shape and precision
 # (None otherwise).
 COLPASS_TRAFFIC = {("k_col_warp<8,16,float2>", 256, 8, 512, "mixed_fp32"): 26912512}
+# the same for the preconditioner's column pass (inverted channels nl = 9),
+# profiles/k_col_warp_pc_hg2d_transport_256_L8.md
+PCPASS_TRAFFIC = {("k_col_warp_pc<8,16>", 256, 8, 512, 9): 25568256}
 
 
 def cufft_pair_ms(shape_in, s_fft, real, reps=20):

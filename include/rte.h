@@ -152,6 +152,10 @@ rte_status rte_apply_K32(rte_plan plan, const void* x_dev, void* y_dev, void* cu
  * (allocates device memory).  RTE_EUNSUPPORTED for 2D plans whose Q is not
  * 32 * 2^j (64 <= Q <= 512).  Not in the paper. */
 rte_status rte_apply_precond32(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
+/* The built preconditioner's inverted modes: *lmax_out = lmax (2D, |k| <=
+ * lmax; see rte_opts.precond_lmax), 0 for 3D.  RTE_EINVAL before it is built
+ * (the first preconditioned solve or rte_apply_precond32 builds it). */
+rte_status rte_precond_info(rte_plan plan, int* lmax_out);
 
 /* b = K~ g (step T.1 / S.1): f_dev double [n]^d real source, b_dev an FP64
  * field (all modes 0..L in 2D). */

@@ -71,6 +71,7 @@ def lib():
         L.rte_plan_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]
         L.rte_plan_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
+        L.rte_precond_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int)]
         L.rte_destroy.argtypes = [VP]
         L.rte_time_passes.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
         L.rte_time_passes.restype = ctypes.c_int
@@ -168,6 +169,12 @@ def rte_apply_K64e(plan, x, y, stream=0):
 
 def rte_apply_K32(plan, x, y, stream=0):
     _check(lib().rte_apply_K32(plan, VP(x), VP(y), VP(stream)), "rte_apply_K32")
+
+
+def rte_precond_info(plan):
+    lmax = ctypes.c_int()
+    _check(lib().rte_precond_info(plan, ctypes.byref(lmax)), "rte_precond_info")
+    return lmax.value
 
 
 def rte_apply_precond32(plan, x, y, stream=0):

@@ -286,6 +286,12 @@ extern "C" rte_status rte_apply_K32(rte_plan p, const void* x, void* y, void* st
     return plan_apply32(p, (const float*)x, (float*)y, 0.0f, 1.0f, 0.0f, nullptr, (cudaStream_t)stream);
 }
 
+extern "C" rte_status rte_precond_info(rte_plan p, int* lmax_out) {
+    if (!p || !lmax_out || !p->pc_ready) return RTE_EINVAL;
+    *lmax_out = p->dim == 2 ? (p->pc_nl - 1) / 2 : 0;
+    return RTE_OK;
+}
+
 extern "C" rte_status rte_apply_precond32(rte_plan p, const void* x, void* y, void* stream) {
     if (!p || !x || !y || x == y) return RTE_EINVAL;
     if (!plan_precond_supported(p)) return RTE_EUNSUPPORTED;

@@ -174,3 +174,18 @@ def test_preconditioned_solve_q1024_sampled_residual():
                                       packed_to_full(u1.cpu().numpy()), rows)
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
     p.close()
+
+
+def test_automatic_mode_truncation():
+    """The default lmax: the smallest with (mu_s/mu_t) max_{k>lmax} |sigma_hat_k|
+    <= 0.03 -- 4 for g = 0.5, mu_s/mu_t = 0.9 (0.9 * 0.5^5 = 0.028), all
+    modes for g = 0.8 at L = 8 (0.9 * 0.8^8 = 0.15), 0 without anisotropy."""
+    from paper_1802_03061_gb300 import _binding as B
+    x = None
+    for g, L, want in [(0.5, 8, 4), (0.8, 8, 8), (0.0, 4, 0), (0.5, 2, 2)]:
+        sig = rte_synth.hg_sigma_hat(g, L)
+        p = _plan(16, 10.0, 9.0, sig, prec="mixed_fp32")
+        x = torch.zeros(p.shape(), dtype=torch.complex64, device="cuda")
+        p.apply_precond32(x)
+        assert B.rte_precond_info(p.handle) == want, (g, L)
+        p.close()
