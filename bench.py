@@ -713,6 +713,67 @@ def run_learned(args):
     print(json.dumps(line))
 
 
+def run_inhom(args):
+    """The inhomogeneous-medium direct Nystrom apply (2D, isotropic): the
+    paper's test medium mu_s = 1 + 10 exp(-|x - c|^2/4), mu_t = mu_s + 0.2, on
+    an n x n grid; a step is one FP32 application y = K~ x (N^2 kernel
+    entries, each with a 5-point line integral of mu_t)."""
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Inhom
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    n = args.inhom_n
+    mu, _ = rte_synth.inhom_mu_t(n)
+    op = Inhom(mu)
+    x = torch.from_numpy(rte_synth.gaussian_mixture_2d(n, [(0.3, 0.6), (0.7, 0.4)], [0.05, 0.1])).float().cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        B.rte_inhom_apply32(op.handle, x.data_ptr(), y.data_ptr(), int(stream.cuda_stream))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = B.rte_kernel_launches()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        B.rte_inhom_apply32(op.handle, x.data_ptr(), y.data_ptr(), int(stream.cuda_stream))
+    e1.record(stream)
+    e1.synchronize()
+    launches = B.rte_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    N = n * n
+    pairs = float(N) * (N - 1)
+    line = {"metric": "inhomogeneous-medium K~ applications/s (direct Nystrom, 5-point line integrals)",
+            "value": 1e3 / ms, "unit": "applications/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "inhom_%d: %dx%d, mu_t = 1.2 + 10 exp(-|x - c|^2/4), FP32 apply" % (n, n, n),
+                       "kernel_entries_per_s": pairs / (ms * 1e-3),
+                       "l2": "mu_t and x stay in L2 / shared memory (%d KB): compute-bound" % (N * 8 // 1024)},
+            "gpu_launches": int(launches), "clocks": clk}
+    if not args.no_cpu_baseline:
+        import time as _t
+        from oracle import inhom as oinh
+        rows = np.arange(0, N, max(1, N // 64))[:64]
+        D = np.zeros((n, n))
+        t0 = _t.perf_counter()
+        oinh.apply_2d(mu, 1.0 / n, x.cpu().double().numpy(), rows=rows, D=D)
+        dt = _t.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / (dt * N / len(rows)), "unit": "applications/s", "cores": 1,
+                                "kind": "oracle", "sample": "%d rows of the direct sum, extrapolated to N = %d rows"
+                                % (len(rows), N)}
+    op.close()
+    print(json.dumps(line))
+
+
 def run_profile_solve(args):
     """One plan, one warm-up solve, one solve: a clean launch list for ncu.
     With the preconditioner on, its three passes are also launched twice on
@@ -754,8 +815,9 @@ def main():
                     help="periodic circulant right preconditioner in the FP32 inner solves (not in the paper)")
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inhom-n", type=int, default=256, help="inhom workload: cells per side")
     ap.add_argument("--workload", default="hg2d_transport",
-                    choices=["hg2d_transport", "batch512", "iso3d", "learned"])
+                    choices=["hg2d_transport", "batch512", "iso3d", "learned", "inhom"])
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=4, help="learned workload: training epochs")
     ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
@@ -769,6 +831,8 @@ def main():
     if args.profile_solve:
         run_profile_solve(args)
         return
+    if args.workload == "inhom":
+        return run_inhom(args)
     if args.workload == "batch512":
         run_batch(args)
         return

@@ -284,6 +284,30 @@ rte_status rte_guess_targets(rte_plan p, int cout, const double* f_dev, const do
 rte_status rte_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, double* b_out_dev, void* X_scratch_dev,
                            void* u0_dev, void* cuda_stream);
 
+/* ---- Inhomogeneous medium, isotropic scattering, 2D (Sec. 2.3,
+ * Eq. iso_discretization): the Nystrom matrix K~ applied directly, O(N^2).
+ * K~_ij = h^2 E(x_i, x_j) / (2 pi |x_i - x_j|) for i != j, with
+ * E(x, y) = exp(-|x - y| int_0^1 mu_t(x - s(x - y)) ds) by 5-point
+ * Gauss-Legendre along the segment; K~_ii = (2h/pi) ln(1 + sqrt 2) plus the
+ * smooth part (E - 1)/(2 pi r) integrated over the cell by the 15 x 15
+ * Gauss-Legendre rule (the split the paper describes after Eq. iso_AU).
+ * mu_t between its cell-centred samples: bilinear, index clamped to the grid.
+ * The solve of Eq. iso_AU needs A = diag(1/mu_s) - K~ on top of this apply. ---- */
+typedef struct rte_inhom_s* rte_inhom;
+/* mu_t_host: n*n cell values [i2][i1] (x fastest), >= 0 and finite, host
+ * memory, copied.  Computes the diagonal on the device (FP64).  RTE_EINVAL on
+ * bad arguments; RTE_ENOMEM when the device buffers cannot be allocated. */
+rte_status rte_inhom_create(rte_inhom* out, int n, double h, const double* mu_t_host, void* cuda_stream);
+/* y = K~ x, FP32 (x_dev, y_dev: float [n*n], device, must not alias;
+ * compensated summation) or FP64.  A block owns 32 output cells and splits
+ * the sources over 8 warps; mu_t staged in shared memory for n <= 110 (FP32)
+ * / 78 (FP64). */
+rte_status rte_inhom_apply32(rte_inhom op, const float* x_dev, float* y_dev, void* cuda_stream);
+rte_status rte_inhom_apply64(rte_inhom op, const double* x_dev, double* y_dev, void* cuda_stream);
+/* the diagonal K~_ii into diag_host (n*n doubles, host) */
+rte_status rte_inhom_diag(rte_inhom op, double* diag_host);
+rte_status rte_inhom_destroy(rte_inhom op);
+
 /* Diagnostics (no counterpart in the paper).
  * rte_time_passes: average duration in ms of each FFT pass of one K
  * application -- ms_out[0] row pass, [1] column pass (FFT, mode mix, inverse

@@ -72,6 +72,12 @@ def lib():
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]
         L.rte_plan_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
         L.rte_precond_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int)]
+        L.rte_inhom_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_double), VP]
+        L.rte_inhom_apply32.argtypes = [VP, VP, VP, VP]
+        L.rte_inhom_apply64.argtypes = [VP, VP, VP, VP]
+        L.rte_inhom_diag.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
+        L.rte_inhom_destroy.argtypes = [VP]
         L.rte_destroy.argtypes = [VP]
         L.rte_time_passes.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
         L.rte_time_passes.restype = ctypes.c_int
@@ -169,6 +175,37 @@ def rte_apply_K64e(plan, x, y, stream=0):
 
 def rte_apply_K32(plan, x, y, stream=0):
     _check(lib().rte_apply_K32(plan, VP(x), VP(y), VP(stream)), "rte_apply_K32")
+
+
+def rte_inhom_create(n, h, mu_t, stream=0):
+    """mu_t: n*n cell values (x fastest), host."""
+    import numpy as _np
+    arr = _np.ascontiguousarray(mu_t, dtype=_np.float64).reshape(-1)
+    if arr.size != n * n:
+        raise ValueError("mu_t must hold n*n values")
+    out = VP()
+    _check(lib().rte_inhom_create(ctypes.byref(out), int(n), float(h),
+                                  arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), VP(stream)),
+           "rte_inhom_create")
+    return out
+
+
+def rte_inhom_apply32(op, x, y, stream=0):
+    _check(lib().rte_inhom_apply32(op, VP(x), VP(y), VP(stream)), "rte_inhom_apply32")
+
+
+def rte_inhom_apply64(op, x, y, stream=0):
+    _check(lib().rte_inhom_apply64(op, VP(x), VP(y), VP(stream)), "rte_inhom_apply64")
+
+
+def rte_inhom_diag(op, count):
+    out = (ctypes.c_double * count)()
+    _check(lib().rte_inhom_diag(op, out), "rte_inhom_diag")
+    return list(out)
+
+
+def rte_inhom_destroy(op):
+    lib().rte_inhom_destroy(op)
 
 
 def rte_precond_info(plan):

@@ -217,3 +217,45 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Inhom:
+    """The inhomogeneous-medium isotropic Nystrom matrix K~ in 2D, applied
+    directly (see rte_inhom_create): mu_t is an (n, n) array of cell values
+    indexed [i2, i1]; fields are (n, n) tensors, float32 (apply32) or float64
+    (apply64)."""
+
+    def __init__(self, mu_t, h=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        mu_t = np.asarray(mu_t, dtype=np.float64)
+        self.n = int(mu_t.shape[0])
+        self.h = 1.0 / self.n if h is None else float(h)
+        self.handle = B.rte_inhom_create(self.n, self.h, mu_t, _stream_ptr(stream))
+
+    def _field(self, x, dt):
+        x = torch.as_tensor(x).to(device="cuda", dtype=dt).contiguous()
+        if tuple(x.shape) != (self.n, self.n):
+            raise ValueError("field shape must be (%d, %d)" % (self.n, self.n))
+        return x
+
+    def apply32(self, x, stream=None):
+        x = self._field(x, torch.float32)
+        y = torch.empty_like(x)
+        B.rte_inhom_apply32(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        return y
+
+    def apply64(self, x, stream=None):
+        x = self._field(x, torch.float64)
+        y = torch.empty_like(x)
+        B.rte_inhom_apply64(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        return y
+
+    def diag(self):
+        return np.array(B.rte_inhom_diag(self.handle, self.n * self.n)).reshape(self.n, self.n)
+
+    def close(self):
+        if self.handle:
+            B.rte_inhom_destroy(self.handle)
+            self.handle = None
+

@@ -122,3 +122,14 @@ def learned_guess_instance(seed, n=256, L=4):
     mu_t log-uniform in [1, 50], mu_s/mu_t in [0.5, 0.99], 1-6 Gaussians."""
     rng = np.random.default_rng(seed)
     return random_instance_2d(rng, n, L, g_range=(0.0, 0.7))
+
+
+def inhom_mu_t(n, rho=10.0, gap=0.2):
+    """Cell-centred mu_t of the inhomogeneous test medium: mu_s(x) = 1 + rho
+    exp(-|x - c|^2 / 4), c = (1/2, 1/2), and mu_t = mu_s + gap (the paper's
+    choice mu_t = mu_s + 0.2).  Returns (mu_t, mu_s), (n, n) arrays [i2, i1]."""
+    xc = (np.arange(n) + 0.5) / n
+    r2 = (xc[None, :] - 0.5) ** 2 + (xc[:, None] - 0.5) ** 2
+    mu_s = 1.0 + rho * np.exp(-r2 / 4.0)
+    return mu_s + gap, mu_s
+
