@@ -154,6 +154,10 @@ bool plan_precond_supported(const rte_plan p);
 rte_status plan_precond_build(rte_plan p, cudaStream_t s);
 rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t s);
 rte_status plan_time_pc(rte_plan p, int reps, double* ms, cudaStream_t s);
+// w = A M v and pv = M v for one preconditioned inner step (FP32)
+rte_status plan_apply_pcA32(rte_plan p, const float* v, float* pv, float* w, cudaStream_t s);
+rte_status op2d_apply32_stage(rte_plan p, const float* x, float* out, float a, float b, float c, int stage,
+                              cudaStream_t s);
 cudaError_t op3d_run_pc32(rte_plan p, const float* x, float* out, cudaStream_t s);
 rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c,
                         const float* z, cudaStream_t s);

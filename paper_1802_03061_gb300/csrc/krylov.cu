@@ -1146,9 +1146,8 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditiona
     const int nb = tiles(nr), gr = grid_for(nr);
     rte_status e;
     if constexpr (sizeof(T) == sizeof(float)) {
-        if (pc) {  // right preconditioning: w = A (M v)
-            if ((e = plan_apply_pc32(G.p, (const float*)G.vin, G.p->pv1, s)) != RTE_OK) return e;
-            e = apply_A_T(G.p, (const float*)G.p->pv1, (float*)G.w, s);
+        if (pc) {  // right preconditioning: w = A (M v), M v kept in pv1
+            e = plan_apply_pcA32(G.p, (const float*)G.vin, G.p->pv1, (float*)G.w, s);
         } else {
             e = apply_A_T(G.p, G.vin, G.w, s);
         }

@@ -339,6 +339,116 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
     }
 }
 
+// The preconditioned inner step applies M and then K to M's output.  The
+// inverse row pass of M and the forward row pass of K touch the same rows of
+// the same mode k and nothing else, so one kernel does both (FP32): rebuild
+// the row spectra from the column pass's half spectra, inverse warp FFT,
+// out = x + v (M's output, also K's input and the identity term of A later),
+// then out weighted by mu_s sigma_hat_k, forward warp FFT, and the half
+// spectra back into Tb (in place: a block reads and writes only its rows).
+// grid (ceil(n / 8), L+1), block 256; rows per block 8 (k >= 1) or 16 (k = 0)
+template <int R>
+__global__ void __launch_bounds__(256) k_row_invfwd_warp(float2* __restrict__ Tb, const float2* __restrict__ x,
+                                                         float2* __restrict__ out, const float2* __restrict__ tw,
+                                                         RowParams p) {
+    constexpr int Q = 32 * R;
+    constexpr int LS = Q + 34;
+    extern __shared__ unsigned char smraw[];
+    float2* twl = reinterpret_cast<float2*>(smraw);
+    float2* Z = twl + Q;
+    const int n = p.n, H = p.H;
+    const int k = blockIdx.y;
+    const int rows = k == 0 ? 16 : 8;
+    const int y0 = blockIdx.x * rows;
+    if (y0 >= n) return;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    // M: Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
+    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
+        const int li = idx & 7, xi = idx >> 3;
+        float2 Fv = make_float2(0.f, 0.f), Gv = make_float2(0.f, 0.f);
+        if (k == 0) {
+            const int ya = y0 + 2 * li, yb = ya + 1;
+            if (ya < n) Fv = Tb[(long)xi * n + ya];
+            if (yb < n) Gv = Tb[(long)xi * n + yb];
+        } else {
+            const int y = y0 + li;
+            if (y < n) {
+                Fv = Tb[((long)chA(k) * H + xi) * n + y];
+                Gv = Tb[((long)chB(k) * H + xi) * n + y];
+            }
+        }
+        Z[li * LS + swz16(xi)] = make_float2(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = make_float2(Fv.x + Gv.y, Gv.x - Fv.y);
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = Z[w * LS + swz16(wfreq<R>(j, lane))];
+    __syncwarp();
+    warp_fft_inv<R>(v, twl, Z + w * LS);
+    // out = x + v, and K's weighted input in v (zero beyond the n cells)
+    const float wt = (float)p.wk[k];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = lane + 32 * r;
+        float2 nv = make_float2(0.f, 0.f);
+        if (e < n) {
+            if (k == 0) {
+                const int ya = y0 + 2 * w, yb = ya + 1;
+                float qa = 0.f, qb = 0.f;
+                if (ya < n) {
+                    const long o = (long)ya * n + e;
+                    const float2 xv = x[o];
+                    const float2 q = make_float2(v[r].x + xv.x, xv.y);
+                    out[o] = q;
+                    qa = q.x;
+                }
+                if (yb < n) {
+                    const long o = (long)yb * n + e;
+                    const float2 xv = x[o];
+                    const float2 q = make_float2(v[r].y + xv.x, xv.y);
+                    out[o] = q;
+                    qb = q.x;
+                }
+                nv = make_float2(wt * qa, wt * qb);
+            } else {
+                const int y = y0 + w;
+                if (y < n) {
+                    const long o = ((long)k * n + y) * n + e;
+                    const float2 xv = x[o];
+                    const float2 q = make_float2(v[r].x + xv.x, v[r].y + xv.y);
+                    out[o] = q;
+                    nv = make_float2(wt * q.x, wt * q.y);
+                }
+            }
+        }
+        v[r] = nv;
+    }
+    __syncwarp();
+    // K: forward warp FFT of the weighted row(s), half spectra back into Tb
+    warp_fft_fwd<R>(v, twl, Z + w * LS);
+#pragma unroll
+    for (int j = 0; j < R; ++j) Z[w * LS + swz16(wfreq<R>(j, lane))] = v[j];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < H * rows; idx += blockDim.x) {
+        const int r = idx % rows, xi = idx / rows;
+        const int y = y0 + r;
+        if (y >= n) continue;
+        const int line = k == 0 ? r >> 1 : r;
+        const float2 Zp = Z[line * LS + swz16(xi)];
+        const float2 Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
+        const float2 Fv = make_float2(0.5f * (Zp.x + Zm.x), 0.5f * (Zp.y - Zm.y));
+        const float2 Gv = make_float2(0.5f * (Zp.y + Zm.y), -0.5f * (Zp.x - Zm.x));
+        if (k == 0) {
+            Tb[(long)xi * n + y] = (r & 1) ? Gv : Fv;
+        } else {
+            Tb[((long)chA(k) * H + xi) * n + y] = Fv;
+            Tb[((long)chB(k) * H + xi) * n + y] = Gv;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 2. mode mix at one frequency: X[c] (in) -> X[c] (out), tagged coefficients
 // ---------------------------------------------------------------------------

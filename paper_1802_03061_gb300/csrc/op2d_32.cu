@@ -5,6 +5,8 @@
 rte_status op2d_apply32_bf16(rte_plan p, const float2* x, float2* out, float a, float b, float c, const float2* z,
                              cudaStream_t s);
 rte_status op2d_time32_bf16(rte_plan p, int reps, double* ms, cudaStream_t s);
+rte_status op2d_apply32_bf16_stage(rte_plan p, const float2* x, float2* out, float a, float b, float c, int stage,
+                                   cudaStream_t s);
 
 rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b, float c, const float* z,
                         cudaStream_t s) {
@@ -27,6 +29,19 @@ rte_status op2d_rhs32(rte_plan p, float* out, cudaStream_t s) {
                                              reinterpret_cast<float2*>(p->Tsplit32), p->S32, p->tw32,
                                              p->col_split32, s, -1, p->S32p);
     if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_rhs32");
+    return RTE_OK;
+}
+
+// one stage of the FP32 application (0 row, 1 column, 2 inverse row + epilogue)
+rte_status op2d_apply32_stage(rte_plan p, const float* x, float* out, float a, float b, float c, int stage,
+                              cudaStream_t s) {
+    const float2* xx = reinterpret_cast<const float2*>(x);
+    float2* oo = reinterpret_cast<float2*>(out);
+    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC) return op2d_apply32_bf16_stage(p, xx, oo, a, b, c, stage, s);
+    cudaError_t e = op2d_run<float2, float2, float2>(p, MIX_K, xx, nullptr, oo, a, b, c, nullptr, reinterpret_cast<float2*>(p->T32),
+                                             reinterpret_cast<float2*>(p->Tsplit32), p->S32, p->tw32, p->col_split32,
+                                             s, stage, p->S32p);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "op2d_apply32_stage");
     return RTE_OK;
 }
 

@@ -236,6 +236,28 @@ static cudaError_t row_fwd_warp(int Q, dim3 grid, const TF* x, const double* f, 
     return cudaGetLastError();
 }
 
+// M's inverse row pass fused with K's forward row pass (k_row_invfwd_warp)
+static cudaError_t row_invfwd_warp(int Q, dim3 grid, float2* Tb, const float2* x, float2* out, const float2* tw,
+                                   const RowParams& rp, cudaStream_t s) {
+    const size_t sm = row_warp_smem<float2>(Q);
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_row_invfwd_warp<2>)) != cudaSuccess || (e = allow_smem(k_row_invfwd_warp<4>)) != cudaSuccess ||
+            (e = allow_smem(k_row_invfwd_warp<8>)) != cudaSuccess || (e = allow_smem(k_row_invfwd_warp<16>)) != cudaSuccess)
+            return e;
+        once = true;
+    }
+    switch (Q) {
+        case 64: k_row_invfwd_warp<2><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
+        case 128: k_row_invfwd_warp<4><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
+        case 256: k_row_invfwd_warp<8><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
+        case 512: k_row_invfwd_warp<16><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, typename TF>
 static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, const TF* z, TF* out, const T* tw,
                                 const RowParams& rp, typename real_of<T>::R a, typename real_of<T>::R b,

@@ -588,6 +588,31 @@ rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t 
     return RTE_OK;
 }
 
+// one preconditioned inner step: pv = M v, w = A pv = pv - K pv.  With the
+// warp row passes (2D, Q <= 512) M's inverse row pass and K's forward row
+// pass run as one kernel (k_row_invfwd_warp); otherwise M and A one after
+// the other.
+rte_status plan_apply_pcA32(rte_plan p, const float* v, float* pv, float* w, cudaStream_t s) {
+    if (!p->pc_ready) return RTE_EINVAL;
+    if (p->dim == 2 && row_warp_ok(p->Q) && p->rb_force < 2) {
+        cudaError_t e = pc2d_pass(p, 0, v, pv, s);
+        if (e == cudaSuccess) e = pc2d_pass(p, 1, v, pv, s);
+        if (e == cudaSuccess) {
+            RowParams rp = pc_rowparams(p, false);  // K's input weights mu_s sigma_hat_k
+            const dim3 grid((p->n + 7) / 8, p->L + 1);
+            e = row_invfwd_warp(p->Q, grid, (float2*)p->T32, (const float2*)v, (float2*)pv, p->tw32, rp, s);
+        }
+        rte_count_launches(3);
+        if (e != cudaSuccess) return rte_cuda_fail(e, "plan_apply_pcA32");
+        rte_status st = op2d_apply32_stage(p, pv, w, 1.0f, -1.0f, 0.0f, 1, s);
+        if (st == RTE_OK) st = op2d_apply32_stage(p, pv, w, 1.0f, -1.0f, 0.0f, 2, s);
+        return st;
+    }
+    rte_status st = plan_apply_pc32(p, v, pv, s);
+    if (st == RTE_OK) st = plan_apply32(p, pv, w, 1.0f, -1.0f, 0.0f, nullptr, s);
+    return st;
+}
+
 // average ms of each 2D pass over reps back-to-back launches (plan scratch)
 rte_status plan_time_pc(rte_plan p, int reps, double* ms, cudaStream_t s) {
     if (p->dim != 2) return RTE_EUNSUPPORTED;
