@@ -193,9 +193,49 @@ __device__ __forceinline__ void pc_mix_pair(float2* X, int QS, int s1, int s2, c
     pc_mix<L, true>(X, QS, s1, s2, P, QR, nl);
 }
 
-// column pass of the preconditioner: FFT_y of every channel, per frequency
-// the dense tagged (2L+1)^2 product with Pp, inverse FFT_y (as k_col_warp).
-// The block's slice of Pp is prefetched into L2 while the forward FFTs run.
+// 16-byte global -> shared copy that bypasses the registers (cp.async), and
+// its group bookkeeping
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// one mix step of the staged column pass: the inverted input channel cp with
+// its coefficients P[.][cp][.] in shared memory (rows of QR entries)
+template <int L, int PC, bool BC>
+__device__ __forceinline__ void pc_stage_term(float2* ra, float2* rb, float2 a, float2 b,
+                                              const __nv_bfloat16* __restrict__ buf, int QR, int t, int t2,
+                                              bool mirror) {
+    constexpr int NCH = 2 * L + 1;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const float v = __bfloat162float(buf[c * QR + t]);
+        float w = __bfloat162float(buf[c * QR + t2]);
+        if (mirror && ch_isB(c) != BC) w = -w;
+        const bool im = ((ch_mode(c) & 1) ^ PC) != 0;
+        if (im) {
+            ra[c].x -= v * a.y;
+            ra[c].y += v * a.x;
+            rb[c].x -= w * b.y;
+            rb[c].y += w * b.x;
+        } else {
+            ra[c].x += v * a.x;
+            ra[c].y += v * a.y;
+            rb[c].x += w * b.x;
+            rb[c].y += w * b.y;
+        }
+    }
+}
+
+// column pass of the preconditioner (Q = 32 R <= 512): FFT_y of the nl
+// inverted channels, per frequency pair (xi, Q - xi) the tagged product with
+// P, inverse FFT_y of every channel (as k_col_warp).  The table slice of one
+// inverted channel (17 rows of Q/2 + 8 BF16) is copied into shared memory by
+// cp.async, two stages ahead: the first two while the forward FFTs run, the
+// next one while a stage is being used.  Thread t < Q/2 takes the pair
+// (t, Q - t); thread 0 takes xi = 0 and xi = Q/2, each its own mirror.
 template <int L, int R>
 __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb, const __nv_bfloat16* __restrict__ Pp,
                                                      const float2* __restrict__ tw, int n, int H, int nl) {
@@ -203,20 +243,25 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
     constexpr int Q = 32 * R;
     constexpr int QR = Q / 2 + 8;
     constexpr int QS = wfft_shape<R>::SCRATCH;
-    constexpr unsigned CHUNK = 16384;
-    const unsigned slice = NCH * nl * QR * 2;  // bytes, a multiple of 16
+    constexpr int CPR = QR * 2 / 16;  // 16-byte chunks per table row
     extern __shared__ unsigned char smraw[];
     float2* X = reinterpret_cast<float2*>(smraw);  // [NCH][QS]
+    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(X + NCH * QS);  // [2][NCH][QR]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const __nv_bfloat16* Pk = Pp + (long)kx * NCH * nl * QR;
-    if (warp == nw - 1) {
-        const char* base = reinterpret_cast<const char*>(Pk);
-        for (unsigned off = lane * CHUNK; off < slice; off += 32 * CHUNK) {
-            const unsigned sz = slice - off < CHUNK ? slice - off : CHUNK;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(sz) : "memory");
+    auto issue = [&](int cp) {
+        __nv_bfloat16* dst = stage + (cp & 1) * NCH * QR;
+        for (int q = threadIdx.x; q < NCH * CPR; q += blockDim.x) {
+            const int c = q / CPR, k = q - c * CPR;
+            cp_async16(reinterpret_cast<char*>(dst + c * QR) + 16 * k,
+                       reinterpret_cast<const char*>(Pk + ((long)c * nl + cp) * QR) + 16 * k);
         }
-    }
+    };
+    issue(0);
+    cp_async_commit();
+    if (nl > 1) issue(1);
+    cp_async_commit();
     for (int c = warp; c < nl; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;
@@ -230,13 +275,38 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < Q / 2; t += blockDim.x) {
-        if (t == 0) {  // xi = 0 and xi = Q/2 are their own mirrors
-            pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR, nl);
-            pc_mix_one<L>(X, QS, wslot<R>(Q / 2), Pk + Q / 2, QR, nl);
-        } else {
-            pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(Q - t), Pk + t, QR, nl);
+    const int t = threadIdx.x;
+    const bool act = t < Q / 2;
+    const int s1 = wslot<R>(act ? t : 0), s2 = wslot<R>(t == 0 ? Q / 2 : (act ? Q - t : 0));
+    const int t2 = t == 0 ? Q / 2 : t;  // table column of the second frequency
+    float2 ra[NCH], rb[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        ra[c] = make_float2(0.f, 0.f);
+        rb[c] = make_float2(0.f, 0.f);
+    }
+    for (int cp = 0; cp < nl; ++cp) {
+        cp_async_wait1();  // this thread's copies of stage cp have landed
+        __syncthreads();   // everyone's (and, for cp = 0, the forward FFTs)
+        if (act) {
+            const __nv_bfloat16* buf = stage + (cp & 1) * NCH * QR;
+            const float2 a = X[cp * QS + s1], b = X[cp * QS + s2];
+            const int pcp = ch_mode(cp) & 1;
+            const bool bc = ch_isB(cp), mirror = t != 0;
+            if (pcp == 0 && !bc) pc_stage_term<L, 0, false>(ra, rb, a, b, buf, QR, t, t2, mirror);
+            else if (pcp == 0) pc_stage_term<L, 0, true>(ra, rb, a, b, buf, QR, t, t2, mirror);
+            else if (!bc) pc_stage_term<L, 1, false>(ra, rb, a, b, buf, QR, t, t2, mirror);
+            else pc_stage_term<L, 1, true>(ra, rb, a, b, buf, QR, t, t2, mirror);
+        }
+        __syncthreads();  // stage cp & 1 is free again
+        if (cp + 2 < nl) issue(cp + 2);
+        cp_async_commit();
+    }
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            X[c * QS + s1] = ra[c];
+            X[c * QS + s2] = rb[c];
         }
     }
     __syncthreads();
@@ -420,7 +490,10 @@ static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const floa
         if ((e = allow_smem(k_col_warp_pc<L, R>)) != cudaSuccess) return e;
         once = true;
     }
-    const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2);
+    // the columns' spectra and two staged table slices (2 x (2L+1) rows of Q/2 + 8 BF16)
+    const int Q = 32 * R;
+    const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2) +
+                        (size_t)2 * (2 * L + 1) * (Q / 2 + 8) * sizeof(__nv_bfloat16);
     k_col_warp_pc<L, R><<<H, 256, smem, s>>>(Tb, Pp, tw, n, H, nl);
     return cudaGetLastError();
 }
