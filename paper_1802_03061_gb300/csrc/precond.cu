@@ -338,23 +338,33 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc2(float2* __restrict__ Tb
     constexpr int R = 16, QW = 512, Q = 1024;
     constexpr int QR = Q / 2 + 8;
     constexpr int QS = wfft_shape<R>::SCRATCH;
-    constexpr unsigned CHUNK = 16384;
-    const unsigned slice = NCH * nl * QR * 2;
+    constexpr int CPR = QR * 2 / 16;
     extern __shared__ unsigned char smraw[];
     float2* twl = reinterpret_cast<float2*>(smraw);  // exp(-2 pi i t / 512)
     float2* X = twl + QW;                            // [NCH][QS]
+    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(X + NCH * QS);  // [2][NCH][QR]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const __nv_bfloat16* Pk = Pp + (long)kx * NCH * nl * QR;
-    if (warp == nw - 1) {
-        const char* base = reinterpret_cast<const char*>(Pk);
-        for (unsigned off = lane * CHUNK; off < slice; off += 32 * CHUNK) {
-            const unsigned sz = slice - off < CHUNK ? slice - off : CHUNK;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(sz) : "memory");
+    // stage g = r * nl + cp holds the table rows of the inverted channel cp
+    auto issue = [&](int g) {
+        const int cp = g % nl;
+        __nv_bfloat16* dst = stage + (g & 1) * NCH * QR;
+        for (int q = threadIdx.x; q < NCH * CPR; q += blockDim.x) {
+            const int c = q / CPR, k = q - c * CPR;
+            cp_async16(reinterpret_cast<char*>(dst + c * QR) + 16 * k,
+                       reinterpret_cast<const char*>(Pk + ((long)c * nl + cp) * QR) + 16 * k);
         }
-    }
+    };
+    const int ng = 2 * nl;
+    issue(0);
+    cp_async_commit();
+    issue(1);
+    cp_async_commit();
     for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
     __syncthreads();
+    const int t = threadIdx.x;
+    const bool act = t < QW / 2;
     for (int r = 0; r < 2; ++r) {
         for (int c = warp; c < nl; c += nw) {
             float2 v[R];
@@ -374,17 +384,43 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc2(float2* __restrict__ Tb
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1) Xc[k1 * 32 + lane] = v[k1];
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < QW / 2; t += blockDim.x) {
-            if (r == 0) {
-                if (t == 0) {  // xi = 0 and xi = Q/2 are their own mirrors
-                    pc_mix_one<L>(X, QS, wslot<R>(0), Pk, QR, nl);
-                    pc_mix_one<L>(X, QS, wslot<R>(QW / 2), Pk + QW, QR, nl);
-                } else {
-                    pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - t), Pk + 2 * t, QR, nl);
-                }
-            } else {
-                pc_mix_pair<L>(X, QS, wslot<R>(t), wslot<R>(QW - 1 - t), Pk + 2 * t + 1, QR, nl);
+        // residue 0: thread 0 takes xi = 0 and Q/2 (own mirrors, columns 0 and
+        // 512), thread t pairs k = t with 512 - t (column 2t); residue 1: k = t
+        // with 511 - t (column 2t + 1)
+        const int tt = act ? t : 0;
+        const bool single = r == 0 && t == 0;
+        const int s1 = wslot<R>(tt);
+        const int s2 = wslot<R>(single ? QW / 2 : (r == 0 ? QW - tt : QW - 1 - tt));
+        const int col1 = 2 * tt + r, col2 = single ? QW : col1;
+        float2 ra[NCH], rb[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            ra[c] = make_float2(0.f, 0.f);
+            rb[c] = make_float2(0.f, 0.f);
+        }
+        for (int cp = 0; cp < nl; ++cp) {
+            const int g = r * nl + cp;
+            cp_async_wait1();
+            __syncthreads();
+            if (act) {
+                const __nv_bfloat16* buf = stage + (g & 1) * NCH * QR;
+                const float2 a = X[cp * QS + s1], b = X[cp * QS + s2];
+                const int pcp = ch_mode(cp) & 1;
+                const bool bc = ch_isB(cp), mirror = !single;
+                if (pcp == 0 && !bc) pc_stage_term<L, 0, false>(ra, rb, a, b, buf, QR, col1, col2, mirror);
+                else if (pcp == 0) pc_stage_term<L, 0, true>(ra, rb, a, b, buf, QR, col1, col2, mirror);
+                else if (!bc) pc_stage_term<L, 1, false>(ra, rb, a, b, buf, QR, col1, col2, mirror);
+                else pc_stage_term<L, 1, true>(ra, rb, a, b, buf, QR, col1, col2, mirror);
+            }
+            __syncthreads();
+            if (g + 2 < ng) issue(g + 2);
+            cp_async_commit();
+        }
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                X[c * QS + s1] = ra[c];
+                X[c * QS + s2] = rb[c];
             }
         }
         __syncthreads();
@@ -419,7 +455,8 @@ static cudaError_t launch_col_pc2(float2* Tb, float2* Tz, const __nv_bfloat16* P
         if ((e = allow_smem(k_col_warp_pc2<L>)) != cudaSuccess) return e;
         once = true;
     }
-    const size_t smem = (size_t)(512 + (2 * L + 1) * wfft_shape<16>::SCRATCH) * sizeof(float2);
+    const size_t smem = (size_t)(512 + (2 * L + 1) * wfft_shape<16>::SCRATCH) * sizeof(float2) +
+                        (size_t)2 * (2 * L + 1) * (1024 / 2 + 8) * sizeof(__nv_bfloat16);
     k_col_warp_pc2<L><<<H, 256, smem, s>>>(Tb, Tz, Pp, tw, n, H, nl);
     return cudaGetLastError();
 }
