@@ -145,12 +145,17 @@ rte_status rte_apply_K64e(rte_plan plan, const void* x_dev, void* y_dev, void* c
  * as the plan's prec selects (FP32 for an FP64 plan). */
 rte_status rte_apply_K32(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
 /* The periodic preconditioner of the inner solves (see rte_opts.precond) on an
- * FP32 field: y = M x = crop((I - C)^{-1} pad(x)), C the convolution with the
- * plan's kernel samples on the Q^d periodic grid, inverted per frequency (a
- * scalar in 3D, a (2L+1) x (2L+1) matrix in 2D, stored in BF16).  Layout as
- * rte_apply_K32.  Builds the preconditioner data on the first call
- * (allocates device memory).  RTE_EUNSUPPORTED for 2D plans whose Q is not
- * 32 * 2^j (64 <= Q <= 512).  Not in the paper. */
+ * FP32 field.  C is the convolution with the plan's kernel samples on the Q^d
+ * periodic grid, diagonal in Fourier space.  3D: y = M x = crop((I - C)^{-1}
+ * pad(x)), a scalar per frequency.  2D: with T(xi) the (2L+1) x (2L+1) mode
+ * coupling of C and "low" the channels of the modes |k| <= lmax
+ * (rte_opts.precond_lmax, rte_precond_info), y = x + crop(P pad(x_low)) with
+ * P = T[:, low] (I - T_ll)^{-1} per frequency, stored in BF16: for lmax = L
+ * this is crop((I - C)^{-1} pad(x)); for smaller lmax the higher modes keep
+ * their coupling to the inverted ones.  Layout as rte_apply_K32.  Builds the
+ * preconditioner data on the first call (allocates device memory).
+ * RTE_EUNSUPPORTED for 2D plans whose column spectra do not fit the column
+ * passes (Q above 1024 at L = 8).  Not in the paper. */
 rte_status rte_apply_precond32(rte_plan plan, const void* x_dev, void* y_dev, void* cuda_stream);
 /* The built preconditioner's inverted modes: *lmax_out = lmax (2D, |k| <=
  * lmax; see rte_opts.precond_lmax), 0 for 3D.  RTE_EINVAL before it is built
@@ -223,7 +228,8 @@ rte_status rte_batch_plan(rte_batch b, int i, rte_plan* out);
  * the candidate padded lengths Q (the smallest even 2^a 3^b >= 2n-1, the
  * next two, and the smallest power of two in 64..1024 that is >= 2n-1, whose
  * column passes use the warp-register FFT) and row passes {0 = default: one warp per line with the FFT in
- * registers when Q = 32 * 2^j, 64 <= Q <= 512, else the shared-memory FFT
+ * registers when Q = 32 * 2^j, 64 <= Q <= 512 (the column passes also at
+ * Q = 1024), else the shared-memory FFT
  * with 8 rows per block; or the shared-memory FFT with 2, 4, 8, 16 rows per
  * block}, `reps` applications each, with CUDA
  * events on cuda_stream; returns the fastest (Q, rows per block) and its time
