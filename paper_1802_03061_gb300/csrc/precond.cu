@@ -12,17 +12,23 @@
 // GMRES / MINRES without a preconditioner); the answer is the same to the
 // solve's tolerance.
 //
+// 2D, block lower triangular in the modes: with "low" the channels of the
+// modes |k| <= lmax (nl = 2 lmax + 1 of them), the stored matrix is
+// P = T[:, low] (I - T_ll)^{-1} and M x = x + crop P pad(x_low).  For
+// lmax = L this is crop (I - T)^{-1} pad (P = (I - T)^{-1} - I); for smaller
+// lmax the higher modes keep their coupling to the inverted block and drop
+// T_lh and T_hh, which carry mu_s sigma_hat_k of the high modes only.
+//
 // T(xi) has entries that are purely real or purely imaginary, imaginary
 // exactly when the modes of the two channels differ in parity (see the mode
-// mix in op2d.cuh), so with Phi = diag(i^{parity}) the matrix Phi^-1 T Phi is
-// real and (I - T)^{-1} has the same pattern: one real number per entry.
-// Mirroring xi_y -> -xi_y reverses the angle of every kernel sample, which maps
-// mode k to -k; on the real channels (A_k, B_k) = ((u_k + u_-k)/2,
-// (u_k - u_-k)/2i) that is A -> A, B -> -B, so (I - T(xi_x, -xi_y))^{-1} =
-// S (I - T(xi_x, xi_y))^{-1} S with S = diag(+1 on A, -1 on B).  Only xi_y in
-// [0, Q/2] is stored, in BF16 (the preconditioner only has to be close, not
-// exact), as Pp[xi_x][c][c'][xi_y] with rows of pc_row(Q) = Q/2 + 8 entries,
-// scaled by 1/Q^2 for the unnormalised transforms of the passes.
+// mix in op2d.cuh), and so has P: one real number per entry.  Mirroring
+// xi_y -> -xi_y reverses the angle of every kernel sample, which maps mode k
+// to -k; on the real channels (A_k, B_k) = ((u_k + u_-k)/2, (u_k - u_-k)/2i)
+// that is A -> A, B -> -B, so P(xi_x, -xi_y) = S P(xi_x, xi_y) S with
+// S = diag(+1 on A, -1 on B).  Only xi_y in [0, Q/2] is stored, in BF16 (the
+// preconditioner only has to be close, not exact), as Pp[xi_x][c][c'][xi_y]
+// (c < 2L+1, c' < nl) with rows of pc_row(Q) = Q/2 + 8 entries, scaled by
+// 1/Q^2 for the unnormalised transforms of the passes.
 #include "op2d_launch.cuh"
 
 __host__ __device__ __forceinline__ int ch_mode(int c) { return (c + 1) >> 1; }
