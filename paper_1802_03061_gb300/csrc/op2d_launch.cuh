@@ -206,8 +206,9 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
 
 // warp row passes (Q in {64, 128, 256, 512}) for FP32 fields and compute.  The
 // kernels also instantiate for float-float on FP64 fields, but there the
-// shared-memory passes are faster (the float-float inverse needs 193 registers
-// per thread in the warp form), so the float-float passes stay Stockham.
+// shared-memory passes are faster: the warp forward needs 194 registers per
+// thread, and the warp inverse (128 registers) measured 43.2 us against 38.5 us
+// at 256^2, L = 8, Q = 512.
 template <typename T, typename TF> struct row_warp_types { static constexpr bool value = false; };
 template <> struct row_warp_types<float2, float2> { static constexpr bool value = true; };
 template <typename T> static inline size_t row_warp_smem(int Q) { return (size_t)(Q + 8 * (Q + 34)) * sizeof(T); }
