@@ -1,6 +1,8 @@
 // Host launchers of the 2D passes, instantiated per precision in op2d_64.cu
 // and op2d_32.cu.
 #pragma once
+#include <type_traits>
+
 #include "op2d.cuh"
 
 #define RTE_SMEM_OPTIN 232448   // 227 KB dynamic shared memory per block on sm_103a
@@ -143,7 +145,10 @@ static cudaError_t dispatch_col_warp(int L, float2* Tb, float2* Tz, const TS* Sp
 // Q in {64, 128, 256, 512} and Q = 1024 as two 512-point residues; the warp
 // row passes take Q <= 512
 static inline bool col_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024; }
-static inline bool row_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512; }
+static inline bool row_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024; }
+// shared memory of the Q = 1024 row kernels: 512-point twiddles, 8 lines of
+// Q + 2, 8 warp FFT scratches
+static inline size_t row_warp2_smem() { return (size_t)(512 + 8 * (1024 + 2) + 8 * wfft_shape<16>::SCRATCH) * sizeof(float2); }
 
 template <typename T, typename TS>
 static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split,
@@ -232,6 +237,17 @@ static cudaError_t row_fwd_warp(int Q, dim3 grid, const TF* x, const double* f, 
         case 128: k_row_fwd_warp<4, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
         case 256: k_row_fwd_warp<8, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
         case 512: k_row_fwd_warp<16, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 1024:
+            if constexpr (std::is_same<T, float2>::value && std::is_same<TF, float2>::value) {
+                static bool once2 = false;
+                if (!once2) {
+                    if ((e = allow_smem(k_row_fwd_warp2<16>)) != cudaSuccess) return e;
+                    once2 = true;
+                }
+                k_row_fwd_warp2<16><<<grid, 256, row_warp2_smem(), s>>>(x, f, out, tw, rp);
+                break;
+            }
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -279,6 +295,17 @@ static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, cons
         case 128: k_row_inv_warp<4, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
         case 256: k_row_inv_warp<8, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
         case 512: k_row_inv_warp<16, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 1024:
+            if constexpr (std::is_same<T, float2>::value && std::is_same<TF, float2>::value) {
+                static bool once2 = false;
+                if (!once2) {
+                    if ((e = allow_smem(k_row_inv_warp2<16>)) != cudaSuccess) return e;
+                    once2 = true;
+                }
+                k_row_inv_warp2<16><<<grid, 256, row_warp2_smem(), s>>>(in, x, z, out, tw, rp, a, b, c);
+                break;
+            }
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -710,7 +710,7 @@ rte_status plan_apply_pc32(rte_plan p, const float* x, float* out, cudaStream_t 
 // the other.
 rte_status plan_apply_pcA32(rte_plan p, const float* v, float* pv, float* w, cudaStream_t s) {
     if (!p->pc_ready) return RTE_EINVAL;
-    if (p->dim == 2 && row_warp_ok(p->Q) && p->rb_force < 2) {
+    if (p->dim == 2 && row_warp_ok(p->Q) && p->Q <= 512 && p->rb_force < 2) {
         cudaError_t e = pc2d_pass(p, 0, v, pv, s);
         if (e == cudaSuccess) e = pc2d_pass(p, 1, v, pv, s);
         if (e == cudaSuccess) {
