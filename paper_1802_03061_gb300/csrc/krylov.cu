@@ -719,13 +719,6 @@ __global__ void k_copy_T(const T* __restrict__ src, T* __restrict__ dst, long nr
         dst[e] = src[e];
 }
 
-// x += d
-template <typename T>
-__global__ void k_add_T(T* __restrict__ x, const T* __restrict__ d, long nr) {
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
-        x[e] += d[e];
-}
-
 // FP32 -> FP64 copy
 __global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, long nr) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long)gridDim.x * blockDim.x)
