@@ -717,7 +717,7 @@ def run_inhom(args):
     """The inhomogeneous-medium direct Nystrom apply (2D, isotropic): the
     paper's test medium mu_s = 1 + 10 exp(-|x - c|^2/4), mu_t = mu_s + 0.2, on
     an n x n grid; a step is one FP32 application y = K~ x (N^2 kernel
-    entries, each with a 5-point line integral of mu_t)."""
+    entries, N(N - 1)/2 distinct 5-point line integrals of mu_t)."""
     import torch
 
     import rte_synth
@@ -757,6 +757,8 @@ def run_inhom(args):
             "data": "synthetic",
             "config": {"workload": "inhom_%d: %dx%d, mu_t = 1.2 + 10 exp(-|x - c|^2/4), FP32 apply" % (n, n, n),
                        "kernel_entries_per_s": pairs / (ms * 1e-3),
+                       "optical_depths_per_apply": int(N * (N - 1) // 2),
+                       "symmetry": "K~_ij = K~_ji: each pair's line integral taken once",
                        "l2": "mu_t and x stay in L2 / shared memory (%d KB): compute-bound" % (N * 8 // 1024)},
             "gpu_launches": int(launches), "clocks": clk}
     if not args.no_cpu_baseline:

@@ -189,6 +189,75 @@ __global__ void __launch_bounds__(256) k_inhom_apply(const T* __restrict__ mu_g,
     }
 }
 
+// FP32, using the symmetry K~_ij = K~_ji (E(x, y) = E(y, x)): each unordered
+// pair's optical depth is computed once.  y starts as diag(K~) x (k_inhom_diag_x);
+// a block owns the 32 rows i0..i0+31 (its lanes) and the 256 columns
+// j0..j0+255 (32 per warp) and takes the pairs with j > i: row i gains
+// K~_ij x_j, column j gains K~_ij x_i.  Row sums meet over the warps in shared
+// memory, column sums over the lanes by shuffles; both reach y by one atomic
+// add per block and row or per warp and column (the summation order is not
+// fixed, unlike k_inhom_apply).  Blocks wholly below the diagonal return.
+__global__ void k_inhom_diag_x(const float* __restrict__ diag, const float* __restrict__ x, float* __restrict__ y,
+                               int N) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) y[i] = diag[i] * x[i];
+}
+
+__global__ void __launch_bounds__(256) k_inhom_apply_sym(const float* __restrict__ mu_g, const float* __restrict__ x,
+                                                         float* __restrict__ y, int n, float h, int mu_smem, Gl5 g5) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ float part[8][32];
+    const int N = n * n;
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 256;
+    if (j0 + 255 <= i0) return;  // no pair j > i in this block (uniform)
+    const float* mu = mu_g;
+    if (mu_smem) {
+        float* ms = reinterpret_cast<float*>(smraw);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) ms[k] = mu_g[k];
+        __syncthreads();
+        mu = ms;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = i0 + lane;
+    const bool live = i < N;
+    const int ii = live ? i : 0;
+    const int i1 = ii % n, i2 = ii / n;
+    const float xi = live ? x[ii] : 0.f;
+    const float scale = h * h / (float)(2.0 * kPi);
+    float acc = 0.f, comp = 0.f;
+    const int jb = j0 + warp * 32;
+    for (int jj = 0; jj < 32; ++jj) {
+        const int j = jb + jj;
+        if (j >= N) break;  // uniform over the warp
+        float e = 0.f;
+        if (live && j > i) {
+            const float du = (float)(j % n - i1), dv = (float)(j / n - i2);
+            const float r = h * sqrtf(du * du + dv * dv);
+            float mean = 0.f;
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                mean += (float)g5.w[q] * mu_seg(mu, n, (float)i1 + (float)g5.s[q] * du, (float)i2 + (float)g5.s[q] * dv);
+            e = expf(-r * mean) / r;
+        }
+        // row i: + e x_j (compensated); column j: + sum over the lanes of e x_i
+        const float term = e * x[j];
+        const float yk = term - comp;
+        const float t2 = acc + yk;
+        comp = (t2 - acc) - yk;
+        acc = t2;
+        float cs = e * xi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if (lane == 0 && cs != 0.f) atomicAdd(&y[j], scale * cs);
+    }
+    part[warp][lane] = acc - comp;
+    __syncthreads();
+    if (warp == 0 && live) {
+        float sum = 0.f;
+        for (int w = 0; w < 8; ++w) sum += part[w][lane];
+        if (sum != 0.f) atomicAdd(&y[i], scale * sum);
+    }
+}
+
 static size_t inhom_smem(int n, size_t el) {
     const size_t b = (size_t)n * n * el;
     return b <= 48 * 1024 ? b : 0;
@@ -274,7 +343,27 @@ static rte_status inhom_apply(rte_inhom op, const T* mu, const T* diag, const T*
 
 extern "C" rte_status rte_inhom_apply32(rte_inhom op, const float* x_dev, float* y_dev, void* stream) {
     if (!op || !x_dev || !y_dev || x_dev == y_dev) return RTE_EINVAL;
-    return inhom_apply<float>(op, op->mu32, op->diag32, x_dev, y_dev, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = op->n, N = n * n;
+    Gl5 g5;
+    for (int q = 0; q < 5; ++q) {
+        g5.s[q] = op->s5[q];
+        g5.w[q] = op->w5[q];
+    }
+    const size_t sm = inhom_smem(n, sizeof(float));
+    static bool once = false;
+    if (!once) {
+        cudaError_t e = cudaFuncSetAttribute(k_inhom_apply_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+        if (e != cudaSuccess) return rte_cuda_fail(e, "rte_inhom_apply32");
+        once = true;
+    }
+    k_inhom_diag_x<<<(unsigned)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096), 256, 0, s>>>(op->diag32, x_dev, y_dev, N);
+    const dim3 grid((unsigned)((N + 255) / 256), (unsigned)((N + 31) / 32));
+    k_inhom_apply_sym<<<grid, 256, sm, s>>>(op->mu32, x_dev, y_dev, n, (float)op->h, sm ? 1 : 0, g5);
+    rte_count_launches(2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rte_cuda_fail(e, "rte_inhom_apply32");
+    return RTE_OK;
 }
 
 extern "C" rte_status rte_inhom_apply64(rte_inhom op, const double* x_dev, double* y_dev, void* stream) {

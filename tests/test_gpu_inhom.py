@@ -36,7 +36,7 @@ def test_diagonal_matches_oracle(n):
     op.close()
 
 
-@pytest.mark.parametrize("n", [1, 2, 5, 12, 17])
+@pytest.mark.parametrize("n", [1, 2, 5, 12, 17, 40])
 def test_apply_matches_oracle(n):
     from paper_1802_03061_gb300 import Inhom
     mu = _mu(n, 100 + n)
