@@ -65,7 +65,8 @@ def real_sh(L, v):
     vectors v (..., 3) -> (..., M)."""
     v = np.asarray(v, dtype=np.float64)
     x, y, z = v[..., 0], v[..., 1], v[..., 2]
-    theta = np.arccos(np.clip(z, -1.0, 1.0))
+    # polar angle by arctan2: arccos(z) loses half the digits near the poles
+    theta = np.arctan2(np.hypot(x, y), z)
     phi = np.arctan2(y, x)
     out = np.empty(v.shape[:-1] + (n_channels(L),))
     for l in range(L + 1):
@@ -120,7 +121,7 @@ def _offset_tables(n, h, mu_t, L):
     zero = r == 0
     r_safe = np.where(zero, 1.0, r)
     kap = np.where(zero, 0.0, h ** 3 * np.exp(-mu_t * r) / (4.0 * math.pi * r_safe ** 2))
-    v = off / np.where(zero, 1.0, r / h)[..., None]
+    v = off / np.where(zero, 1.0, np.sqrt((off ** 2).sum(-1)))[..., None]
     v[zero] = (0.0, 0.0, 1.0)
     return kap, real_sh(L, v)
 

@@ -17,8 +17,12 @@ def _unit(rng, k):
 
 def test_real_harmonics_closed_forms():
     """Textbook Cartesian forms for l <= 2 (no Condon-Shortley phase):
-    Y_1 = sqrt(3/4pi) (y, z, x); Y_2 = sqrt(15/4pi) (xy, yz, (3z^2-1)/(2 sqrt3), xz, (x^2-y^2)/2)."""
+    Y_1 = sqrt(3/4pi) (y, z, x); Y_2 = sqrt(15/4pi) (xy, yz, (3z^2-1)/(2 sqrt3), xz, (x^2-y^2)/2),
+    also at and next to the poles (a polar angle from arccos(z) is off by
+    1e-8 there once z has rounded to 1)."""
     v = _unit(np.random.default_rng(1), 50)
+    # the poles and points 1e-9 off them, where z rounds to +-1 exactly
+    v = np.concatenate([v, [[0, 0, 1], [0, 0, -1], [1e-9, 0, 1], [0, -1e-9, -1], [1e-9, 1e-9, 1]]])
     x, y, z = v.T
     Y = A.real_sh(2, v)
     c1, c2 = math.sqrt(3 / (4 * math.pi)), math.sqrt(15 / (4 * math.pi))
