@@ -314,6 +314,48 @@ rte_status rte_inhom_apply64(rte_inhom op, const double* x_dev, double* y_dev, v
 rte_status rte_inhom_diag(rte_inhom op, double* diag_host);
 rte_status rte_inhom_destroy(rte_inhom op);
 
+/* ---------------------------------------------------------------------------
+ * 3D anisotropic scattering in real spherical harmonics (Sec. 3.1.2).
+ *
+ * The angular density is expanded in the real orthonormal harmonics Y_a,
+ * a = l^2 + l + m, |m| <= l <= L (no Condon-Shortley phase: Y_{l,0} = N P_l(z),
+ * Y_{l,+-m} = sqrt2 N_lm P_l^m(z)/(1-z^2)^{m/2} {Re, Im}(x + i y)^m, so
+ * Y_{1,-1}, Y_{1,0}, Y_{1,1} = sqrt(3/4pi) (y, z, x)), M = (L+1)^2 channels.
+ * The moments u_a = (4 pi)^{-1/2} int Phi Y_a dv (u_0 = the mean density)
+ * solve u = K u + b with
+ *   (K u)_a = sum_b K~^{ab} mu_s sigma_hat_{l_b} u_b,   b_a = K~^{a0} f,
+ *   K~^{ab}_{ij} = h^3 exp(-mu_t r)/(4 pi r^2) 4 pi Y_a(v) Y_b(v), v = (x_i - x_j)/r,
+ *   K~^{ab}_{ii} = the same kernel integrated over the cell (D_ab);
+ * sigma_hat_l: the phase function's Legendre moments (sigma_hat_0 = 1,
+ * |sigma_hat_l| <= 1; Henyey-Greenstein: g^l) -- the paper's coefficient of
+ * Y_l^0 times sqrt(4 pi/(2l+1)).  L = 0 is the isotropic equation.
+ * Fields: double (float for apply_K32) [M][n][n][n], x fastest, device memory;
+ * the source f: double [n][n][n].  Applied with FFTs on the zero-padded Q^3
+ * grid (Q = the smallest even 2^a 3^b >= 2n - 1), FP64 spectra for the FP64
+ * calls, FP32 for apply_K32.  Limits: L <= 4, n <= 1024, and the M channels of
+ * one Z line must fit in shared memory (RTE_EUNSUPPORTED otherwise; n = 128
+ * takes L <= 4).  Inputs and outputs may not alias.
+ * ------------------------------------------------------------------------- */
+typedef struct rte_aniso3d_s* rte_aniso3d;
+/* Computes D_ab and the M(M+1)/2 spectra on the device (synchronises). */
+rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, double mu_t, double mu_s, int L,
+                              const double* sigma_hat, void* cuda_stream);
+rte_status rte_aniso3d_info(rte_aniso3d op, int* M_out, int* Q_out);
+/* D_ab, row-major M x M, into host memory. */
+rte_status rte_aniso3d_cell_weights(rte_aniso3d op, double* out_host);
+/* y = K x (FP64) / in FP32. */
+rte_status rte_aniso3d_apply_K(rte_aniso3d op, const double* x_dev, double* y_dev, void* cuda_stream);
+rte_status rte_aniso3d_apply_K32(rte_aniso3d op, const float* x_dev, float* y_dev, void* cuda_stream);
+/* b = K~^{.0} f (Sec. 3.3, T.1). */
+rte_status rte_aniso3d_rhs(rte_aniso3d op, const double* f_dev, double* b_dev, void* cuda_stream);
+/* (I - K) u = b by restarted FP64 GMRES (Sec. 3.3, T.2; classical Gram-Schmidt
+ * twice, zero start) until ||b - (I - K) u|| <= tol ||b||; RTE_ENOCONV after
+ * maxit iterations (u holds the last iterate).  stats: iters, outer = cycles,
+ * converged, relres_true, ms_total, ms_pre = creation time.  Synchronises. */
+rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, double* u_dev, double tol, int restart,
+                             int maxit, rte_stats* stats, void* cuda_stream);
+rte_status rte_aniso3d_destroy(rte_aniso3d op);
+
 /* Diagnostics (no counterpart in the paper).
  * rte_time_passes: average duration in ms of each FFT pass of one K
  * application -- ms_out[0] row pass, [1] column pass (FFT, mode mix, inverse

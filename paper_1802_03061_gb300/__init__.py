@@ -9,4 +9,4 @@ of ``include/rte.h``; ``_binding`` mirrors it function by function and
 """
 from . import _binding
 from ._binding import RteError, make_opts  # noqa: F401
-from .plan import Batch, Inhom, Plan  # noqa: F401
+from .plan import Aniso3D, Batch, Inhom, Plan  # noqa: F401

@@ -78,6 +78,15 @@ def lib():
         L.rte_inhom_apply64.argtypes = [VP, VP, VP, VP]
         L.rte_inhom_diag.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
         L.rte_inhom_destroy.argtypes = [VP]
+        L.rte_aniso3d_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
+        L.rte_aniso3d_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.rte_aniso3d_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
+        for name in ("rte_aniso3d_apply_K", "rte_aniso3d_apply_K32", "rte_aniso3d_rhs"):
+            getattr(L, name).argtypes = [VP, VP, VP, VP]
+        L.rte_aniso3d_solve.argtypes = [VP, VP, VP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(rte_stats), VP]
+        L.rte_aniso3d_destroy.argtypes = [VP]
         L.rte_destroy.argtypes = [VP]
         L.rte_time_passes.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
         L.rte_time_passes.restype = ctypes.c_int
@@ -206,6 +215,52 @@ def rte_inhom_diag(op, count):
 
 def rte_inhom_destroy(op):
     lib().rte_inhom_destroy(op)
+
+
+def rte_aniso3d_create(n, h, mu_t, mu_s, L, sigma_hat, stream=0):
+    sh = (ctypes.c_double * (L + 1))(*[float(v) for v in sigma_hat])
+    out = VP()
+    _check(lib().rte_aniso3d_create(ctypes.byref(out), int(n), float(h), float(mu_t), float(mu_s), int(L), sh,
+                                    VP(stream)), "rte_aniso3d_create")
+    return out
+
+
+def rte_aniso3d_info(op):
+    M, Q = ctypes.c_int(), ctypes.c_int()
+    _check(lib().rte_aniso3d_info(op, ctypes.byref(M), ctypes.byref(Q)), "rte_aniso3d_info")
+    return M.value, Q.value
+
+
+def rte_aniso3d_cell_weights(op, M):
+    out = (ctypes.c_double * (M * M))()
+    _check(lib().rte_aniso3d_cell_weights(op, out), "rte_aniso3d_cell_weights")
+    return list(out)
+
+
+def rte_aniso3d_apply_K(op, x, y, stream=0):
+    _check(lib().rte_aniso3d_apply_K(op, VP(x), VP(y), VP(stream)), "rte_aniso3d_apply_K")
+
+
+def rte_aniso3d_apply_K32(op, x, y, stream=0):
+    _check(lib().rte_aniso3d_apply_K32(op, VP(x), VP(y), VP(stream)), "rte_aniso3d_apply_K32")
+
+
+def rte_aniso3d_rhs(op, f, b, stream=0):
+    _check(lib().rte_aniso3d_rhs(op, VP(f), VP(b), VP(stream)), "rte_aniso3d_rhs")
+
+
+def rte_aniso3d_solve(op, f, u, tol, restart, maxit, stream=0):
+    stats = rte_stats()
+    st = lib().rte_aniso3d_solve(op, VP(f), VP(u), float(tol), int(restart), int(maxit), ctypes.byref(stats),
+                                 VP(stream))
+    _check(st, "rte_aniso3d_solve", allow=(RTE_ENOCONV,))
+    d = stats.as_dict()
+    d["status"] = st
+    return d
+
+
+def rte_aniso3d_destroy(op):
+    lib().rte_aniso3d_destroy(op)
 
 
 def rte_precond_info(plan):

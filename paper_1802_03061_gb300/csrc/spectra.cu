@@ -54,41 +54,6 @@ __global__ void k_twiddles(double2* tw64, float2* tw32, int Q) {
     tw32[t] = make_float2((float)c, (float)-s);
 }
 
-// ---------------------------------------------------------------------------
-// Gauss-Legendre nodes on the device (Newton iteration on P_N)
-// ---------------------------------------------------------------------------
-__device__ void gl_node(int N, int i, double* x, double* w) {
-    double z = cos(M_PI * (i + 0.75) / (N + 0.5));
-    double pp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-        double p1 = 1.0, p2 = 0.0;
-        for (int j = 1; j <= N; ++j) {
-            double p3 = p2;
-            p2 = p1;
-            p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
-        }
-        pp = N * (z * p1 - p2) / (z * z - 1.0);
-        double z1 = z;
-        z = z1 - p1 / pp;
-        if (fabs(z - z1) < 1e-15) break;
-    }
-    // final derivative at the converged node
-    double p1 = 1.0, p2 = 0.0;
-    for (int j = 1; j <= N; ++j) {
-        double p3 = p2;
-        p2 = p1;
-        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
-    }
-    pp = N * (z * p1 - p2) / (z * z - 1.0);
-    *x = z;
-    *w = 2.0 / ((1.0 - z * z) * pp * pp);
-}
-
-__device__ __forceinline__ double radial_factor(double mu, double R) {
-    // int_0^R exp(-mu r) dr
-    return mu > 0.0 ? -expm1(-mu * R) / mu : R;
-}
-
 // 2D singular-cell weights (Sec. 2.3, diagonal of Eq. iso_discretization):
 // D_m = int_cell kappa(r) e^{i m theta} dr
 //     = (1/2pi) int_0^{2pi} cos(m phi) (1 - e^{-mu R(phi)})/mu dphi,

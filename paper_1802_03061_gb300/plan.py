@@ -259,3 +259,57 @@ class Inhom:
             B.rte_inhom_destroy(self.handle)
             self.handle = None
 
+
+class Aniso3D:
+    """3D anisotropic scattering in real spherical harmonics (see
+    rte_aniso3d_create): M = (L+1)^2 moment channels, fields (M, n, n, n)
+    float64 tensors (float32 for apply_K32), the source (n, n, n)."""
+
+    def __init__(self, n, mu_t, mu_s, sigma_hat, h=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.n = int(n)
+        self.h = 1.0 / self.n if h is None else float(h)
+        self.L = len(sigma_hat) - 1
+        self.handle = B.rte_aniso3d_create(self.n, self.h, mu_t, mu_s, self.L, sigma_hat, _stream_ptr(stream))
+        self.M, self.Q = B.rte_aniso3d_info(self.handle)
+
+    def _field(self, x, dt, chans):
+        x = torch.as_tensor(x).to(device="cuda", dtype=dt).contiguous()
+        want = ((chans,) if chans else ()) + (self.n,) * 3
+        if tuple(x.shape) != want:
+            raise ValueError("field shape must be %s" % (want,))
+        return x
+
+    def apply_K(self, x, stream=None):
+        x = self._field(x, torch.float64, self.M)
+        y = torch.empty_like(x)
+        B.rte_aniso3d_apply_K(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        return y
+
+    def apply_K32(self, x, stream=None):
+        x = self._field(x, torch.float32, self.M)
+        y = torch.empty_like(x)
+        B.rte_aniso3d_apply_K32(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        return y
+
+    def rhs(self, f, stream=None):
+        f = self._field(f, torch.float64, 0)
+        b = torch.empty((self.M,) + (self.n,) * 3, dtype=torch.float64, device="cuda")
+        B.rte_aniso3d_rhs(self.handle, f.data_ptr(), b.data_ptr(), _stream_ptr(stream))
+        return b
+
+    def solve(self, f, tol=1e-10, restart=40, maxit=400, stream=None):
+        f = self._field(f, torch.float64, 0)
+        u = torch.empty((self.M,) + (self.n,) * 3, dtype=torch.float64, device="cuda")
+        stats = B.rte_aniso3d_solve(self.handle, f.data_ptr(), u.data_ptr(), tol, restart, maxit, _stream_ptr(stream))
+        return u, stats
+
+    def cell_weights(self):
+        return np.array(B.rte_aniso3d_cell_weights(self.handle, self.M)).reshape(self.M, self.M)
+
+    def close(self):
+        if self.handle:
+            B.rte_aniso3d_destroy(self.handle)
+            self.handle = None
+

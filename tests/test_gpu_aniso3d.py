@@ -1,0 +1,129 @@
+"""GPU parity of the 3D anisotropic (spherical-harmonic) operator through the
+C ABI against the oracle (oracle/aniso3d.py).  Tolerances: FP64 1e-12
+relative L2 (FFT rounding over Q^3 points); FP32 1e-5 (FP32 spectra and
+FFTs); solves within 100 tol of the dense LU solution (condition number
+(1 + r)/(1 - r) <= 40 here)."""
+import numpy as np
+import pytest
+
+import oracle
+import rte_synth
+from oracle import aniso3d as A
+from _util import rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_03061_gb300 import build
+    build.build()
+
+
+def _hg(g, L):
+    return [g ** l for l in range(L + 1)]
+
+
+@pytest.mark.parametrize("L,mu_t,n", [(2, 3.0, 10), (3, 0.0, 4), (4, 40.0, 16)])
+def test_cell_weights_match_oracle(L, mu_t, n):
+    from paper_1802_03061_gb300 import Aniso3D
+    op = Aniso3D(n, mu_t, 0.5 * mu_t, _hg(0.5, L))
+    np.testing.assert_allclose(op.cell_weights(), A.cell_weights(L, mu_t, 1.0 / n), rtol=1e-12,
+                               atol=1e-14 * oracle.cell_weight_3d(mu_t, 1.0 / n))
+    op.close()
+
+
+@pytest.mark.parametrize("n,L", [(1, 1), (3, 2), (5, 1), (6, 3), (8, 2), (7, 4)])
+def test_apply_matches_oracle(n, L):
+    """Every Q (2, 6, 10 -> 12, 12, 16, 16) and L = 1..4, FP64 and FP32."""
+    from paper_1802_03061_gb300 import Aniso3D
+    mu_t, mu_s = 7.0, 6.3
+    sig = _hg(0.7, L)
+    op = Aniso3D(n, mu_t, mu_s, sig)
+    M = op.M
+    x = np.random.default_rng(10 * n + L).standard_normal((M, n, n, n))
+    ref = A.apply_K(n, 1.0 / n, mu_t, mu_s, sig, x).reshape(M, n, n, n)
+    assert rel(op.apply_K(x).cpu().numpy(), ref) < 1e-12
+    assert rel(op.apply_K32(x).cpu().numpy(), ref) < 1e-5
+    f = np.random.default_rng(n).random((n, n, n))
+    assert rel(op.rhs(f).cpu().numpy(), A.rhs(n, 1.0 / n, mu_t, L, f).reshape(M, n, n, n)) < 1e-12
+    op.close()
+
+
+@pytest.mark.parametrize("n,L", [(33, 2), (48, 1)])
+def test_sampled_rows_larger_grids(n, L):
+    """Q = 72 (a radix-3 length) and 96; sampled rows against the direct sum."""
+    from paper_1802_03061_gb300 import Aniso3D
+    mu_t, mu_s = 10.0, 9.0
+    sig = _hg(0.6, L)
+    op = Aniso3D(n, mu_t, mu_s, sig)
+    M = op.M
+    x = np.random.default_rng(n).standard_normal((M, n, n, n))
+    y = op.apply_K(x).cpu().numpy().reshape(M, -1)
+    y32 = op.apply_K32(x).cpu().numpy().reshape(M, -1)
+    rows = np.random.default_rng(1).choice(n ** 3, size=10, replace=False)
+    D = A.cell_weights(L, mu_t, 1.0 / n)
+    ref = A.apply_K(n, 1.0 / n, mu_t, mu_s, sig, x, rows=rows, D=D)
+    assert rel(y[:, rows], ref) < 1e-12
+    assert rel(y32[:, rows], ref) < 1e-5
+    op.close()
+
+
+def test_isotropic_case_matches_the_plan():
+    """L = 0 is the isotropic operator of rte_plan (d = 3)."""
+    from paper_1802_03061_gb300 import Aniso3D, Plan
+    n, mu_t, mu_s = 20, 6.0, 5.0
+    x = np.random.default_rng(3).standard_normal((n, n, n))
+    op = Aniso3D(n, mu_t, mu_s, [1.0])
+    p = Plan(n, mu_t=mu_t, mu_s=mu_s, dim=3)
+    y = op.apply_K(x[None]).cpu().numpy()[0]
+    yp = p.apply_K(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, yp) < 1e-12
+    op.close()
+
+
+@pytest.mark.parametrize("n,L,g", [(4, 2, 0.6), (5, 1, -0.4)])
+def test_solve_matches_dense(n, L, g):
+    from paper_1802_03061_gb300 import Aniso3D
+    mu_t, mu_s = 8.0, 7.6
+    sig = _hg(g, L)
+    f = np.random.default_rng(n).random((n, n, n))
+    op = Aniso3D(n, mu_t, mu_s, sig)
+    u, st = op.solve(f, tol=1e-11)
+    assert st["converged"] and st["relres_true"] <= 1e-11
+    want = A.solve_dense(n, 1.0 / n, mu_t, mu_s, sig, f)
+    assert rel(u.cpu().numpy(), want) < 100 * 1e-11 * (1 + 0.95) / (1 - 0.95)
+    op.close()
+
+
+def test_solve_larger_grid_sampled_residual():
+    """n = 32, L = 2, Henyey-Greenstein g = 0.8, a Gaussian-mixture source:
+    the residual u - K u - b at sampled cells from the direct sums."""
+    from paper_1802_03061_gb300 import Aniso3D
+    n, L, mu_t, mu_s = 32, 2, 20.0, 18.0
+    sig = _hg(0.8, L)
+    f = rte_synth.gaussian_3d(n, (0.4, 0.5, 0.5), 0.08) + rte_synth.gaussian_3d(n, (0.7, 0.3, 0.6), 0.05)
+    op = Aniso3D(n, mu_t, mu_s, sig)
+    u, st = op.solve(f, tol=1e-10, restart=40)
+    assert st["converged"], st
+    U = u.cpu().numpy().reshape(op.M, -1)
+    rows = np.random.default_rng(2).choice(n ** 3, size=6, replace=False)
+    D = A.cell_weights(L, mu_t, 1.0 / n)
+    r = U[:, rows] - A.apply_K(n, 1.0 / n, mu_t, mu_s, sig, U, rows=rows, D=D) \
+        - A.rhs(n, 1.0 / n, mu_t, L, f, rows=rows, D=D)
+    assert np.abs(r).max() < 1e-8 * np.abs(U).max()
+    op.close()
+
+
+def test_invalid_arguments():
+    from paper_1802_03061_gb300 import Aniso3D
+    from paper_1802_03061_gb300 import _binding as B
+    with pytest.raises(B.RteError):
+        Aniso3D(8, 2.0, 1.0, [1.0] * 6)  # L = 5
+    with pytest.raises(B.RteError):
+        Aniso3D(8, 2.0, 1.0, [0.9, 0.5])  # sigma_hat_0 != 1
+    with pytest.raises(B.RteError):
+        Aniso3D(8, 2.0, 3.0, [1.0, 0.5])  # mu_s > mu_t
