@@ -776,6 +776,74 @@ def run_inhom(args):
     print(json.dumps(line))
 
 
+def run_aniso3d(args):
+    """3D anisotropic scattering in real spherical harmonics: n^3 cells,
+    L = 2 (M = 9 moment channels), Henyey-Greenstein g = 0.8, mu_t = 20,
+    mu_s = 18, two Gaussian sources; a step is one FP64 GMRES solve to 1e-8
+    (b = K~ f included).  The FP64 and FP32 operator applications are timed
+    alongside."""
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Aniso3D
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    n, L, mu_t, mu_s, g = args.aniso_n, 2, 20.0, 18.0, 0.8
+    sig = [g ** l for l in range(L + 1)]
+    f = rte_synth.gaussian_3d(n, (0.4, 0.5, 0.5), 0.08) + rte_synth.gaussian_3d(n, (0.7, 0.3, 0.6), 0.05)
+    op = Aniso3D(n, mu_t, mu_s, sig)
+    fd = torch.from_numpy(f).cuda()
+    u = torch.empty((op.M, n, n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+    for _ in range(args.warmup):
+        st = B.rte_aniso3d_solve(op.handle, fd.data_ptr(), u.data_ptr(), 1e-8, 40, 400, sp)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = B.rte_kernel_launches()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(B.rte_aniso3d_solve(op.handle, fd.data_ptr(), u.data_ptr(), 1e-8, 40, 400, sp))
+    e1.record(stream)
+    e1.synchronize()
+    launches = B.rte_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    x = torch.randn((op.M, n, n, n), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    x32, y32 = x.float(), torch.empty((op.M, n, n, n), dtype=torch.float32, device="cuda")
+    t = {}
+    for name, fn in (("apply64_ms", lambda: B.rte_aniso3d_apply_K(op.handle, x.data_ptr(), y.data_ptr(), sp)),
+                     ("apply32_ms", lambda: B.rte_aniso3d_apply_K32(op.handle, x32.data_ptr(), y32.data_ptr(), sp))):
+        for _ in range(3):
+            fn()
+        e0.record(stream)
+        for _ in range(10):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        t[name] = e0.elapsed_time(e1) / 10
+    line = {"metric": "3D anisotropic RTE solves/s (spherical harmonics L = 2, FP64 GMRES to 1e-8)",
+            "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "aniso3d_%d: %d^3 cells, L = 2 (M = 9), HG g = 0.8, mu_t = 20, mu_s = 18"
+                                   % (n, n), "Q": op.Q, "iters": stats[-1]["iters"],
+                       "relres_true": stats[-1]["relres_true"], "converged": bool(stats[-1]["converged"]),
+                       "plan_ms": stats[-1]["ms_pre"], **t,
+                       "l2": "solution and Krylov basis (%d MB) exceed L2" % ((41 * op.M * n ** 3 * 8) >> 20)},
+            "gpu_launches": int(launches), "clocks": clk}
+    op.close()
+    print(json.dumps(line))
+
+
 def run_profile_solve(args):
     """One plan, one warm-up solve, one solve: a clean launch list for ncu.
     With the preconditioner on, its three passes are also launched twice on
@@ -818,8 +886,9 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inhom-n", type=int, default=256, help="inhom workload: cells per side")
+    ap.add_argument("--aniso-n", type=int, default=64, help="aniso3d workload: cells per side")
     ap.add_argument("--workload", default="hg2d_transport",
-                    choices=["hg2d_transport", "batch512", "iso3d", "learned", "inhom"])
+                    choices=["hg2d_transport", "batch512", "iso3d", "learned", "inhom", "aniso3d"])
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=4, help="learned workload: training epochs")
     ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
@@ -835,6 +904,8 @@ def main():
         return
     if args.workload == "inhom":
         return run_inhom(args)
+    if args.workload == "aniso3d":
+        return run_aniso3d(args)
     if args.workload == "batch512":
         run_batch(args)
         return
