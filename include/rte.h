@@ -348,12 +348,16 @@ rte_status rte_aniso3d_apply_K(rte_aniso3d op, const double* x_dev, double* y_de
 rte_status rte_aniso3d_apply_K32(rte_aniso3d op, const float* x_dev, float* y_dev, void* cuda_stream);
 /* b = K~^{.0} f (Sec. 3.3, T.1). */
 rte_status rte_aniso3d_rhs(rte_aniso3d op, const double* f_dev, double* b_dev, void* cuda_stream);
-/* (I - K) u = b by restarted FP64 GMRES (Sec. 3.3, T.2; classical Gram-Schmidt
- * twice, zero start) until ||b - (I - K) u|| <= tol ||b||; RTE_ENOCONV after
- * maxit iterations (u holds the last iterate).  stats: iters, outer = cycles,
+/* (I - K) u = b (Sec. 3.3, T.2) until ||b - (I - K) u|| <= tol ||b|| (FP64
+ * residual), zero start.  prec = RTE_PREC_FP64: restarted FP64 GMRES(restart)
+ * (classical Gram-Schmidt twice); RTE_PREC_MIXED_FP32: refinement steps, each
+ * an FP32 GMRES(restart) solve of (I - K) d = r/||r|| to max(1e-4, tol/(2 relres))
+ * followed by u += ||r|| d and an FP64 residual.  RTE_ENOCONV after maxit
+ * (inner) iterations, u holding the last iterate; RTE_EINVAL for another prec.
+ * stats: iters (inner), outer (FP64: restart cycles; mixed: refinement steps),
  * converged, relres_true, ms_total, ms_pre = creation time.  Synchronises. */
 rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, double* u_dev, double tol, int restart,
-                             int maxit, rte_stats* stats, void* cuda_stream);
+                             int maxit, int prec, rte_stats* stats, void* cuda_stream);
 rte_status rte_aniso3d_destroy(rte_aniso3d op);
 
 /* Diagnostics (no counterpart in the paper).

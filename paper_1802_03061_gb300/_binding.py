@@ -84,7 +84,7 @@ def lib():
         L.rte_aniso3d_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
         for name in ("rte_aniso3d_apply_K", "rte_aniso3d_apply_K32", "rte_aniso3d_rhs"):
             getattr(L, name).argtypes = [VP, VP, VP, VP]
-        L.rte_aniso3d_solve.argtypes = [VP, VP, VP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+        L.rte_aniso3d_solve.argtypes = [VP, VP, VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(rte_stats), VP]
         L.rte_aniso3d_destroy.argtypes = [VP]
         L.rte_destroy.argtypes = [VP]
@@ -249,10 +249,10 @@ def rte_aniso3d_rhs(op, f, b, stream=0):
     _check(lib().rte_aniso3d_rhs(op, VP(f), VP(b), VP(stream)), "rte_aniso3d_rhs")
 
 
-def rte_aniso3d_solve(op, f, u, tol, restart, maxit, stream=0):
+def rte_aniso3d_solve(op, f, u, tol, restart, maxit, prec="fp64", stream=0):
     stats = rte_stats()
-    st = lib().rte_aniso3d_solve(op, VP(f), VP(u), float(tol), int(restart), int(maxit), ctypes.byref(stats),
-                                 VP(stream))
+    st = lib().rte_aniso3d_solve(op, VP(f), VP(u), float(tol), int(restart), int(maxit), PREC[prec],
+                                 ctypes.byref(stats), VP(stream))
     _check(st, "rte_aniso3d_solve", allow=(RTE_ENOCONV,))
     d = stats.as_dict()
     d["status"] = st

@@ -100,6 +100,11 @@ struct rte_aniso3d_s {
     double* r = nullptr;     // len
     double* part = nullptr;  // (gm + 1) x nblk partial sums
     double* hd = nullptr;    // gm + 1 coefficients
+    // FP32 inner solves of the mixed refinement
+    float* V32 = nullptr;  // (gm + 1) x len
+    float* r32 = nullptr;
+    float* x32 = nullptr;
+    float* b32 = nullptr;
 };
 
 // D_ab over the six faces of the cell: on the face of the point p = (.., +-a, ..)
@@ -336,20 +341,23 @@ static cudaError_t aniso_run(rte_aniso3d op, const R* x, R* out, int rhs, double
 }
 
 // ---------------------------------------------------------------------------
-// FP64 restarted GMRES on (I - K) u = b (Sec. 3.3, T.2), classical
-// Gram-Schmidt applied twice; the small Hessenberg problem on the host.
+// Restarted GMRES on (I - K) u = b (Sec. 3.3, T.2): classical Gram-Schmidt
+// applied twice, inner products accumulated in FP64, the small Hessenberg
+// problem on the host.  T = double (the FP64 solve) or float (the inner solves
+// of the mixed refinement, whose residuals are FP64 applications).
 // ---------------------------------------------------------------------------
 #define ANISO_NBLK 304  // 2 x 152 SMs
 
 // part[i * nblk + blk] = sum over the block's chunk of V_i . w
-__global__ void __launch_bounds__(256) k_aniso_dots(const double* __restrict__ V, long len, const double* __restrict__ w,
+template <typename T>
+__global__ void __launch_bounds__(256) k_aniso_dots(const T* __restrict__ V, long len, const T* __restrict__ w,
                                                     double* __restrict__ part) {
     __shared__ double red[256];
     const int i = blockIdx.y;
-    const double* v = V + (long)i * len;
+    const T* v = V + (long)i * len;
     double acc = 0.0;
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
-        acc += v[t] * w[t];
+        acc += (double)v[t] * (double)w[t];
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -374,24 +382,37 @@ __global__ void k_aniso_sum(const double* __restrict__ part, int nblk, double* _
 }
 
 // w += sgn * sum_{i < k} c_i V_i
-__global__ void k_aniso_comb(double* __restrict__ w, const double* __restrict__ V, long len, int k,
-                             const double* __restrict__ c, double sgn) {
+template <typename T>
+__global__ void k_aniso_comb(T* __restrict__ w, const T* __restrict__ V, long len, int k, const double* __restrict__ c,
+                             double sgn) {
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int i = 0; i < k; ++i) acc += c[i] * V[(long)i * len + t];
-        w[t] += sgn * acc;
+        for (int i = 0; i < k; ++i) acc += c[i] * (double)V[(long)i * len + t];
+        w[t] = (T)((double)w[t] + sgn * acc);
     }
 }
 
 // dst = alpha * src  (or dst = b - dst when b != null)
-__global__ void k_aniso_scale(double* dst, const double* src, const double* b, long len, double alpha) {
+template <typename T>
+__global__ void k_aniso_scale(T* dst, const T* src, const T* b, long len, double alpha) {
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
-        dst[t] = b ? b[t] - dst[t] : alpha * src[t];
+        dst[t] = b ? (T)((double)b[t] - (double)dst[t]) : (T)(alpha * (double)src[t]);
 }
 
-static cudaError_t aniso_dots(rte_aniso3d op, const double* V, int k, const double* w, long len, double* h_host,
+// r32 = (float)(alpha * r)  /  u += alpha * (double)d32
+__global__ void k_aniso_narrow(float* __restrict__ dst, const double* __restrict__ src, long len, double alpha) {
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
+        dst[t] = (float)(alpha * src[t]);
+}
+__global__ void k_aniso_widen_add(double* __restrict__ u, const float* __restrict__ d, long len, double alpha) {
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
+        u[t] += alpha * (double)d[t];
+}
+
+template <typename T>
+static cudaError_t aniso_dots(rte_aniso3d op, const T* V, int k, const T* w, long len, double* h_host,
                               cudaStream_t s) {
-    k_aniso_dots<<<dim3(ANISO_NBLK, k), 256, 0, s>>>(V, len, w, op->part);
+    k_aniso_dots<T><<<dim3(ANISO_NBLK, k), 256, 0, s>>>(V, len, w, op->part);
     k_aniso_sum<<<k, 256, 0, s>>>(op->part, ANISO_NBLK, op->hd);
     rte_count_launches(2);
     cudaError_t e = cudaGetLastError();
@@ -400,10 +421,118 @@ static cudaError_t aniso_dots(rte_aniso3d op, const double* V, int k, const doub
     return cudaStreamSynchronize(s);
 }
 
-static rte_status aniso_apply64(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
-                                cudaStream_t s) {
+// (I - K) x  in the vector's precision (ca = 1, cb = -1), or K~^{.0} f (rhs)
+static rte_status aniso_apply(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
+                              cudaStream_t s) {
     cudaError_t e = aniso_run<double2, double, double>(op, x, y, rhs, ca, cb, op->S64, op->tw64, op->Bz64, s);
     if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d apply");
+    return RTE_OK;
+}
+static rte_status aniso_apply(rte_aniso3d op, const float* x, float* y, int rhs, double ca, double cb,
+                              cudaStream_t s) {
+    cudaError_t e = aniso_run<float2, float, float>(op, x, y, rhs, ca, cb, op->S32, op->tw32, op->Bz32, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d apply32");
+    return RTE_OK;
+}
+static rte_status aniso_apply64(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
+                                cudaStream_t s) {
+    return aniso_apply(op, x, y, rhs, ca, cb, s);
+}
+
+// GMRES(m) from x = 0 on (I - K) x = rhs until ||rhs - (I - K) x|| <= tol ||rhs||
+// (residuals in T) or maxit iterations; V holds m + 1 vectors, r one.
+template <typename T>
+static rte_status aniso_gmres(rte_aniso3d op, const T* rhs, T* x, T* V, T* r, long len, double tol, int m, int maxit,
+                              int* iters_out, int* cycles_out, double* relres_out, cudaStream_t s) {
+    const unsigned gb = ANISO_NBLK;
+    std::vector<double> Hm((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 1), h2(m + 1), y(m);
+    cudaError_t e = cudaSuccess;
+    rte_status st = RTE_OK;
+    double bn = 0.0;
+    if ((e = aniso_dots<T>(op, rhs, 1, rhs, len, &bn, s)) != cudaSuccess) return rte_cuda_fail(e, "aniso_gmres");
+    bn = sqrt(bn);
+    if ((e = cudaMemsetAsync(x, 0, len * sizeof(T), s)) != cudaSuccess) return rte_cuda_fail(e, "aniso_gmres");
+    k_aniso_scale<T><<<gb, 256, 0, s>>>(r, rhs, (const T*)nullptr, len, 1.0);
+    rte_count_launches(1);
+    double beta = bn, relres = bn > 0 ? 1.0 : 0.0;
+    int iters = 0, cycles = 0;
+    bool conv = !(bn > 0);
+    while (!conv && iters < maxit) {
+        ++cycles;
+        k_aniso_scale<T><<<gb, 256, 0, s>>>(V, r, (const T*)nullptr, len, 1.0 / beta);
+        rte_count_launches(1);
+        for (int i = 0; i <= m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        int j = 0;
+        for (; j < m && iters < maxit; ++j) {
+            T* w = V + (long)(j + 1) * len;
+            if ((st = aniso_apply(op, V + (long)j * len, w, 0, 1.0, -1.0, s)) != RTE_OK) return st;
+            // two passes of classical Gram-Schmidt
+            for (int pass = 0; pass < 2; ++pass) {
+                double* hp = pass ? h2.data() : hcol.data();
+                if ((e = aniso_dots<T>(op, V, j + 1, w, len, hp, s)) != cudaSuccess) break;
+                if ((e = cudaMemcpyAsync(op->hd, hp, (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+                    cudaSuccess)
+                    break;
+                k_aniso_comb<T><<<gb, 256, 0, s>>>(w, V, len, j + 1, op->hd, -1.0);
+                rte_count_launches(1);
+            }
+            if (e != cudaSuccess) break;
+            for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
+            double hn = 0.0;
+            if ((e = aniso_dots<T>(op, w, 1, w, len, &hn, s)) != cudaSuccess) break;
+            hn = sqrt(hn);
+            hcol[j + 1] = hn;
+            if (hn > 0) {
+                k_aniso_scale<T><<<gb, 256, 0, s>>>(w, w, (const T*)nullptr, len, 1.0 / hn);
+                rte_count_launches(1);
+            }
+            for (int i = 0; i < j; ++i) {  // previous Givens rotations
+                const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = t;
+            }
+            const double den = hypot(hcol[j], hcol[j + 1]);
+            cs[j] = den > 0 ? hcol[j] / den : 1.0;
+            sn[j] = den > 0 ? hcol[j + 1] / den : 0.0;
+            hcol[j] = den;
+            hcol[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; ++i) Hm[i * m + j] = hcol[i];
+            ++iters;
+            if (fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
+                ++j;
+                break;
+            }
+        }
+        if (e != cudaSuccess) break;
+        for (int i = j - 1; i >= 0; --i) {  // R y = g
+            double t = g[i];
+            for (int k = i + 1; k < j; ++k) t -= Hm[i * m + k] * y[k];
+            y[i] = Hm[i * m + i] != 0.0 ? t / Hm[i * m + i] : 0.0;
+        }
+        if (j > 0) {
+            if ((e = cudaMemcpyAsync(op->hd, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                break;
+            k_aniso_comb<T><<<gb, 256, 0, s>>>(x, V, len, j, op->hd, 1.0);
+            rte_count_launches(1);
+        }
+        // residual r = rhs - (I - K) x in T
+        if ((st = aniso_apply(op, x, r, 0, 1.0, -1.0, s)) != RTE_OK) return st;
+        k_aniso_scale<T><<<gb, 256, 0, s>>>(r, (const T*)nullptr, rhs, len, 0.0);
+        rte_count_launches(1);
+        double rn = 0.0;
+        if ((e = aniso_dots<T>(op, r, 1, r, len, &rn, s)) != cudaSuccess) break;
+        beta = sqrt(rn);
+        relres = beta / bn;
+        conv = relres <= tol;
+        if (!(beta > 0)) break;
+    }
+    if (e != cudaSuccess) return rte_cuda_fail(e, "aniso_gmres");
+    *iters_out += iters;
+    *cycles_out += cycles;
+    *relres_out = relres;
     return RTE_OK;
 }
 
@@ -412,8 +541,8 @@ static rte_status aniso_apply64(rte_aniso3d op, const double* x, double* y, int 
 // ---------------------------------------------------------------------------
 extern "C" rte_status rte_aniso3d_destroy(rte_aniso3d op) {
     if (!op) return RTE_OK;
-    void* ptrs[] = {op->tw64, op->tw32, op->S64, op->S32, op->pinfo, op->T1, op->T2,
-                    op->V,    op->bvec, op->r,   op->part, op->hd};
+    void* ptrs[] = {op->tw64, op->tw32, op->S64, op->S32,  op->pinfo, op->T1,  op->T2,  op->V,
+                    op->bvec, op->r,    op->part, op->hd, op->V32,   op->r32, op->x32, op->b32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete op;
@@ -573,126 +702,88 @@ extern "C" rte_status rte_aniso3d_rhs(rte_aniso3d op, const double* f_dev, doubl
 }
 
 extern "C" rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, double* u_dev, double tol, int restart,
-                                        int maxit, rte_stats* stats, void* stream) {
+                                        int maxit, int prec, rte_stats* stats, void* stream) {
     if (!op || !f_dev || !u_dev || !(tol > 0) || restart < 1 || restart > 200 || maxit < 1) return RTE_EINVAL;
+    if (prec != RTE_PREC_FP64 && prec != RTE_PREC_MIXED_FP32) return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const long len = (long)op->M * op->n * op->n * op->n;
-    if (op->gm != restart) {
-        for (double** q : {&op->V, &op->bvec, &op->r, &op->part, &op->hd})
+    const bool mixed = prec == RTE_PREC_MIXED_FP32;
+    if (op->gm != restart || (mixed && !op->V32)) {
+        for (void** q : {(void**)&op->V, (void**)&op->bvec, (void**)&op->r, (void**)&op->part, (void**)&op->hd,
+                         (void**)&op->V32, (void**)&op->r32, (void**)&op->x32, (void**)&op->b32})
             if (*q) {
                 cudaFree(*q);
                 *q = nullptr;
             }
         op->gm = 0;
-        if (cudaMalloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void**)&op->bvec, len * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void**)&op->r, len * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void**)&op->part, (size_t)(restart + 1) * ANISO_NBLK * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void**)&op->hd, (restart + 1) * sizeof(double)) != cudaSuccess) {
+        bool ok = cudaMalloc((void**)&op->bvec, len * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void**)&op->r, len * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void**)&op->part, (size_t)(restart + 1) * ANISO_NBLK * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void**)&op->hd, (restart + 1) * sizeof(double)) == cudaSuccess;
+        if (ok && !mixed) ok = cudaMalloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) == cudaSuccess;
+        if (ok && mixed)
+            ok = cudaMalloc((void**)&op->V32, (size_t)(restart + 1) * len * sizeof(float)) == cudaSuccess &&
+                 cudaMalloc((void**)&op->r32, len * sizeof(float)) == cudaSuccess &&
+                 cudaMalloc((void**)&op->x32, len * sizeof(float)) == cudaSuccess &&
+                 cudaMalloc((void**)&op->b32, len * sizeof(float)) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
             return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
         }
         op->gm = restart;
     }
-    const int m = restart;
-    const unsigned gb = ANISO_NBLK;
+    if (!mixed && !op->V) {
+        if (cudaMalloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
+        }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    std::vector<double> Hm((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 1), h2(m + 1), y(m);
-    rte_status st = aniso_apply64(op, f_dev, op->bvec, 1, 0.0, 1.0, s);  // b = K~^{.0} f (T.1)
+    int iters = 0, cycles = 0, outer = 0;
+    double relres = 1.0;
+    rte_status st = aniso_apply(op, f_dev, op->bvec, 1, 0.0, 1.0, s);  // b = K~^{.0} f (T.1)
     cudaError_t e = cudaSuccess;
-    double bn = 0.0;
-    if (st == RTE_OK) e = aniso_dots(op, op->bvec, 1, op->bvec, len, &bn, s);
-    bn = sqrt(bn);
-    if (st == RTE_OK && e == cudaSuccess) e = cudaMemsetAsync(u_dev, 0, len * sizeof(double), s);
-    // r = b (u = 0)
-    if (st == RTE_OK && e == cudaSuccess) {
-        k_aniso_scale<<<gb, 256, 0, s>>>(op->r, op->bvec, nullptr, len, 1.0);
-        rte_count_launches(1);
-        e = cudaGetLastError();
-    }
-    double beta = bn, relres = bn > 0 ? 1.0 : 0.0;
-    int iters = 0, cycles = 0;
-    bool conv = !(bn > 0);
-    while (st == RTE_OK && e == cudaSuccess && !conv && iters < maxit) {
-        ++cycles;
-        k_aniso_scale<<<gb, 256, 0, s>>>(op->V, op->r, nullptr, len, 1.0 / beta);
-        rte_count_launches(1);
-        for (int i = 0; i <= m; ++i) g[i] = 0.0;
-        g[0] = beta;
-        int j = 0;
-        for (; j < m && iters < maxit; ++j) {
-            double* w = op->V + (long)(j + 1) * len;
-            // w = (I - K) v_j
-            st = aniso_apply64(op, op->V + (long)j * len, w, 0, 1.0, -1.0, s);
-            if (st != RTE_OK) break;
-            // two passes of classical Gram-Schmidt
-            if ((e = aniso_dots(op, op->V, j + 1, w, len, hcol.data(), s)) != cudaSuccess) break;
-            if ((e = cudaMemcpyAsync(op->hd, hcol.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s)) !=
-                cudaSuccess)
-                break;
-            k_aniso_comb<<<gb, 256, 0, s>>>(w, op->V, len, j + 1, op->hd, -1.0);
-            if ((e = aniso_dots(op, op->V, j + 1, w, len, h2.data(), s)) != cudaSuccess) break;
-            if ((e = cudaMemcpyAsync(op->hd, h2.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s)) !=
-                cudaSuccess)
-                break;
-            k_aniso_comb<<<gb, 256, 0, s>>>(w, op->V, len, j + 1, op->hd, -1.0);
-            rte_count_launches(2);
-            for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
-            double hn = 0.0;
-            if ((e = aniso_dots(op, w, 1, w, len, &hn, s)) != cudaSuccess) break;
-            hn = sqrt(hn);
-            hcol[j + 1] = hn;
-            if (hn > 0) {
-                k_aniso_scale<<<gb, 256, 0, s>>>(w, w, nullptr, len, 1.0 / hn);
-                rte_count_launches(1);
-            }
-            // Givens rotations
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
-                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
-                hcol[i] = t;
-            }
-            const double den = hypot(hcol[j], hcol[j + 1]);
-            cs[j] = den > 0 ? hcol[j] / den : 1.0;
-            sn[j] = den > 0 ? hcol[j + 1] / den : 0.0;
-            hcol[j] = den;
-            hcol[j + 1] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            for (int i = 0; i <= j; ++i) Hm[i * m + j] = hcol[i];
-            ++iters;
-            if (fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
-                ++j;
-                break;
-            }
-        }
-        if (st != RTE_OK || e != cudaSuccess) break;
-        // u += V y, R y = g
-        for (int i = j - 1; i >= 0; --i) {
-            double t = g[i];
-            for (int k = i + 1; k < j; ++k) t -= Hm[i * m + k] * y[k];
-            y[i] = Hm[i * m + i] != 0.0 ? t / Hm[i * m + i] : 0.0;
-        }
-        if (j > 0) {
-            if ((e = cudaMemcpyAsync(op->hd, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-                break;
-            k_aniso_comb<<<gb, 256, 0, s>>>(u_dev, op->V, len, j, op->hd, 1.0);
+    if (st == RTE_OK && !mixed) {
+        st = aniso_gmres<double>(op, op->bvec, u_dev, op->V, op->r, len, tol, restart, maxit, &iters, &outer, &relres,
+                                 s);
+    } else if (st == RTE_OK) {
+        // T.2 refined: FP32 GMRES on (I - K) d = r/||r|| to max(1e-4, tol/(2 relres)),
+        // u += ||r|| d, every residual r = b - (I - K) u an FP64 application
+        const unsigned gb = ANISO_NBLK;
+        double bn = 0.0;
+        e = aniso_dots<double>(op, op->bvec, 1, op->bvec, len, &bn, s);
+        bn = sqrt(bn);
+        if (e == cudaSuccess) e = cudaMemsetAsync(u_dev, 0, len * sizeof(double), s);
+        if (e == cudaSuccess) {
+            k_aniso_scale<double><<<gb, 256, 0, s>>>(op->r, op->bvec, (const double*)nullptr, len, 1.0);
             rte_count_launches(1);
         }
-        // true residual r = b - (I - K) u
-        st = aniso_apply64(op, u_dev, op->r, 0, 1.0, -1.0, s);
-        if (st != RTE_OK) break;
-        k_aniso_scale<<<gb, 256, 0, s>>>(op->r, nullptr, op->bvec, len, 0.0);
-        rte_count_launches(1);
-        double rn = 0.0;
-        if ((e = aniso_dots(op, op->r, 1, op->r, len, &rn, s)) != cudaSuccess) break;
-        beta = sqrt(rn);
-        relres = beta / bn;
-        conv = relres <= tol;
-        if (!(beta > 0)) break;
+        double rn = bn;
+        relres = bn > 0 ? 1.0 : 0.0;
+        while (st == RTE_OK && e == cudaSuccess && relres > tol && iters < maxit && outer < 50) {
+            ++outer;
+            k_aniso_narrow<<<gb, 256, 0, s>>>(op->b32, op->r, len, 1.0 / rn);
+            rte_count_launches(1);
+            double itol = fmax(1e-4, 0.5 * tol / relres);
+            if (itol > 0.5) itol = 0.5;
+            double rr32 = 0.0;
+            st = aniso_gmres<float>(op, op->b32, op->x32, op->V32, op->r32, len, itol, restart, maxit - iters, &iters,
+                                    &cycles, &rr32, s);
+            if (st != RTE_OK) break;
+            k_aniso_widen_add<<<gb, 256, 0, s>>>(u_dev, op->x32, len, rn);
+            rte_count_launches(1);
+            if ((st = aniso_apply(op, u_dev, op->r, 0, 1.0, -1.0, s)) != RTE_OK) break;
+            k_aniso_scale<double><<<gb, 256, 0, s>>>(op->r, (const double*)nullptr, op->bvec, len, 0.0);
+            rte_count_launches(1);
+            double r2 = 0.0;
+            if ((e = aniso_dots<double>(op, op->r, 1, op->r, len, &r2, s)) != cudaSuccess) break;
+            rn = sqrt(r2);
+            relres = bn > 0 ? rn / bn : 0.0;
+            if (!(rn > 0)) break;
+        }
     }
     cudaEventRecord(e1, s);
     cudaError_t e2 = cudaEventSynchronize(e1);
@@ -703,10 +794,11 @@ extern "C" rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, dou
     if (st != RTE_OK) return st;
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d_solve");
+    const bool conv = relres <= tol;
     if (stats) {
         const double rr = op->mu_t > 0 ? op->mu_s / op->mu_t : 1.0;
         stats->iters = iters;
-        stats->outer = cycles;
+        stats->outer = outer;
         stats->converged = conv ? 1 : 0;
         stats->relres_true = relres;
         stats->ms_total = ms;

@@ -299,10 +299,12 @@ class Aniso3D:
         B.rte_aniso3d_rhs(self.handle, f.data_ptr(), b.data_ptr(), _stream_ptr(stream))
         return b
 
-    def solve(self, f, tol=1e-10, restart=40, maxit=400, stream=None):
+    def solve(self, f, tol=1e-10, restart=40, maxit=400, prec="fp64", stream=None):
+        """prec: "fp64" or "mixed_fp32" (FP32 inner GMRES, FP64 residuals)."""
         f = self._field(f, torch.float64, 0)
         u = torch.empty((self.M,) + (self.n,) * 3, dtype=torch.float64, device="cuda")
-        stats = B.rte_aniso3d_solve(self.handle, f.data_ptr(), u.data_ptr(), tol, restart, maxit, _stream_ptr(stream))
+        stats = B.rte_aniso3d_solve(self.handle, f.data_ptr(), u.data_ptr(), tol, restart, maxit, prec,
+                                    _stream_ptr(stream))
         return u, stats
 
     def cell_weights(self):
