@@ -271,12 +271,14 @@ template <typename T> static size_t zmix_smem(int Q, int M, int B) {
 // pair table (and a margin)
 static const size_t kZmixCap = (size_t)RTE_SMEM_OPTIN - RTE_ANISO_MAX_M * RTE_ANISO_MAX_M * sizeof(int) - 1024;
 
-// largest B <= 8 lines per Z block whose buffers fit (0: none does)
+// lines per Z block: the largest B <= 8 whose buffers stay within 48 KB, so that
+// at least four blocks share an SM (the pass is latency-bound: one 140 KB block
+// per SM kept 8 warps active and reached 3 % of the DRAM bandwidth); B = 1 when
+// even one line needs more, if it fits at all (0: it does not)
 template <typename T> static int zmix_lines(int Q, int M) {
-    const size_t cap = kZmixCap;
     for (int B = 8; B >= 1; --B)
-        if (zmix_smem<T>(Q, M, B) <= cap && (B == 1 || zmix_smem<T>(Q, M, B) <= 160 * 1024)) return B;
-    return 0;
+        if (zmix_smem<T>(Q, M, B) <= 48 * 1024) return B;
+    return zmix_smem<T>(Q, M, 1) <= kZmixCap ? 1 : 0;
 }
 
 template <typename K> static cudaError_t allow_big(K k) {
