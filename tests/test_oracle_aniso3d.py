@@ -151,3 +151,41 @@ def test_forward_scattering_solution_residual():
     u_iso1 = A.solve_dense(n, h, mu_t, mu_s, [1.0, 0.0, 0.0], f)
     far = (3, 3, 3)  # [z, y, x], diagonal from the source: flux along +x
     assert u[(3,) + far] > u_iso1[(3,) + far] > 0
+
+
+def test_transport_step_from_the_angular_form():
+    """Independent route through the angular density: a source cell j with
+    moments u_b gives Phi(v') = sqrt(4 pi) sum_b u_b Y_b(v'); the scattered
+    source S(v) = mu_s int sigma_HG(v.v') Phi(v') dv' by brute-force quadrature
+    with the Henyey-Greenstein function itself (not its moments); transporting
+    S along v = (x_i - x_j)/r gives the moments at cell i,
+    u_a(i) = (4 pi)^{-1/2} h^3 e^{-mu_t r} / r^2 Y_a(v) S(v)  (Sec. 3.1.2 with
+    y = x - s v, dy = s^2 ds dv).  The oracle's K with sigma_hat_l = g^l must
+    agree: this fixes the normalisation of sigma_hat, the 4 pi of W_ab and the
+    direction of v."""
+    n, h, mu_t, mu_s, g, L = 4, 0.25, 3.0, 2.5, 0.5, 2
+    M = A.n_channels(L)
+    rng = np.random.default_rng(11)
+    ub = rng.standard_normal(M)
+    j = (0, 1, 3)  # [z, y, x]
+    x = np.zeros((M, n, n, n))
+    x[(slice(None),) + j] = ub
+    y = A.apply_K(n, h, mu_t, mu_s, [g ** l for l in range(L + 1)], x).reshape(M, n, n, n)
+    # sphere quadrature: Gauss-Legendre in cos(theta) x uniform in psi
+    t, w = np.polynomial.legendre.leggauss(400)
+    npsi = 800
+    psi = 2 * math.pi * np.arange(npsi) / npsi
+    T, P = np.meshgrid(t, psi, indexing="ij")
+    s = np.sqrt(1 - T * T)
+    vq = np.stack([s * np.cos(P), s * np.sin(P), T], -1).reshape(-1, 3)
+    wq = np.repeat(w, npsi) * (2 * math.pi / npsi)
+    phi = math.sqrt(4 * math.pi) * A.real_sh(L, vq) @ ub
+    for i in [(3, 2, 0), (1, 1, 1), (2, 3, 2)]:
+        off = np.array([i[2] - j[2], i[1] - j[1], i[0] - j[0]], float) * h
+        r = np.linalg.norm(off)
+        v = off / r
+        cosg = vq @ v
+        sig = (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * cosg) ** 1.5)
+        S = mu_s * np.sum(wq * sig * phi)
+        want = h ** 3 * math.exp(-mu_t * r) / r ** 2 * A.real_sh(L, v[None])[0] * S / math.sqrt(4 * math.pi)
+        np.testing.assert_allclose(y[(slice(None),) + i], want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
