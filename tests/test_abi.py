@@ -67,3 +67,28 @@ def test_plan_create_3d_anisotropic_unsupported():
     with pytest.raises(B.RteError) as ei:
         B.rte_plan_create(3, 8, 0.125, 1.0, 0.5, 1, [1.0, 0.5])
     assert ei.value.status == B.RTE_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("args,status", [
+    (dict(n=8, mu_t=1.0, mu_s=2.0, L=1, sig=[1.0, 0.5]), "RTE_EINVAL"),        # mu_s > mu_t
+    (dict(n=8, mu_t=1.0, mu_s=0.5, L=1, sig=[0.9, 0.5]), "RTE_EINVAL"),        # sigma_hat_0 != 1
+    (dict(n=8, mu_t=1.0, mu_s=0.5, L=2, sig=[1.0, 0.5, -1.2]), "RTE_EINVAL"),  # |sigma_hat_l| > 1
+    (dict(n=0, mu_t=1.0, mu_s=0.5, L=0, sig=[1.0]), "RTE_EINVAL"),             # empty grid
+    (dict(n=8, mu_t=1.0, mu_s=0.5, L=5, sig=[1.0] * 6), "RTE_EINVAL"),         # degree beyond 4
+    (dict(n=600, mu_t=1.0, mu_s=0.5, L=4, sig=[1.0] * 5), "RTE_EUNSUPPORTED"),  # 25 channels x Q = 1296
+])
+def test_aniso3d_create_rejects_before_any_device_call(args, status):
+    """The spherical-harmonic operator checks its arguments and its shared
+    memory limit (all M channels of one z line in one block) on the host."""
+    from paper_1802_03061_gb300 import _binding as B
+    with pytest.raises(B.RteError) as ei:
+        B.rte_aniso3d_create(args["n"], 1.0 / max(args["n"], 1), args["mu_t"], args["mu_s"], args["L"], args["sig"])
+    assert ei.value.status == getattr(B, status)
+
+
+def test_aniso3d_null_handles_without_gpu():
+    from paper_1802_03061_gb300 import _binding as B
+    L = B.lib()
+    assert L.rte_aniso3d_destroy(None) == B.RTE_OK
+    assert L.rte_aniso3d_apply_K(None, None, None, None) == B.RTE_EINVAL
+    assert L.rte_aniso3d_info(None, None, None) == B.RTE_EINVAL
