@@ -341,6 +341,11 @@ typedef struct rte_aniso3d_s* rte_aniso3d;
 rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, double mu_t, double mu_s, int L,
                               const double* sigma_hat, void* cuda_stream);
 rte_status rte_aniso3d_info(rte_aniso3d op, int* M_out, int* Q_out);
+/* Host only (no device call): the M x M channel-pair table the spectra are
+ * stored by, row-major into out_host: pair index (unordered pairs a <= b
+ * numbered row by row) | 1 << 16 if the pair's spectrum is imaginary (W_ab odd
+ * under v -> -v) | 1 << 17 if W_ab is odd in y | 1 << 18 if odd in z. */
+rte_status rte_aniso3d_pair_table(int L, int* out_host);
 /* D_ab, row-major M x M, into host memory. */
 rte_status rte_aniso3d_cell_weights(rte_aniso3d op, double* out_host);
 /* y = K x (FP64) / in FP32. */

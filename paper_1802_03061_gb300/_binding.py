@@ -81,6 +81,7 @@ def lib():
         L.rte_aniso3d_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
         L.rte_aniso3d_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.rte_aniso3d_pair_table.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.rte_aniso3d_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
         for name in ("rte_aniso3d_apply_K", "rte_aniso3d_apply_K32", "rte_aniso3d_rhs"):
             getattr(L, name).argtypes = [VP, VP, VP, VP]
@@ -229,6 +230,13 @@ def rte_aniso3d_info(op):
     M, Q = ctypes.c_int(), ctypes.c_int()
     _check(lib().rte_aniso3d_info(op, ctypes.byref(M), ctypes.byref(Q)), "rte_aniso3d_info")
     return M.value, Q.value
+
+
+def rte_aniso3d_pair_table(L):
+    M = (L + 1) ** 2
+    out = (ctypes.c_int * (M * M))()
+    _check(lib().rte_aniso3d_pair_table(int(L), out), "rte_aniso3d_pair_table")
+    return list(out)
 
 
 def rte_aniso3d_cell_weights(op, M):

@@ -80,6 +80,25 @@ static void sh_parity(int a, int* px, int* py, int* pz) {
     *pz = ((l + am) & 1) ? -1 : 1;
 }
 
+// The channel-pair table: for a, b < M, pair index (a <= b numbered row by row)
+// | imaginary spectrum << 16 | odd in y << 17 | odd in z << 18, symmetric in
+// (a, b); pimag[pair] = the imaginary flag.
+static void aniso_pair_table(int M, int* pinfo, int* pimag) {
+    int pidx = 0;
+    for (int a = 0; a < M; ++a)
+        for (int b = a; b < M; ++b) {
+            int ax, ay, az, bx, by, bz;
+            sh_parity(a, &ax, &ay, &az);
+            sh_parity(b, &bx, &by, &bz);
+            const int px = ax * bx, py = ay * by, pz = az * bz;
+            const int imag = (px * py * pz) < 0 ? 1 : 0;
+            const int info = pidx | (imag << 16) | ((py < 0) << 17) | ((pz < 0) << 18);
+            pinfo[a * M + b] = pinfo[b * M + a] = info;
+            pimag[pidx] = imag;
+            ++pidx;
+        }
+}
+
 struct rte_aniso3d_s {
     int n = 0, L = 0, M = 0, Q = 0, H = 0, np = 0, Bz64 = 0, Bz32 = 0;
     double h = 0.0, mu_t = 0.0, mu_s = 0.0, ms_pre = 0.0;
@@ -584,22 +603,7 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     // pair table
     std::vector<int> pinfo(M * M);
     std::vector<int> pimag(op->np);
-    {
-        int pidx = 0;
-        std::vector<int> id(M * M);
-        for (int a = 0; a < M; ++a)
-            for (int b = a; b < M; ++b) {
-                int ax, ay, az, bx, by, bz;
-                sh_parity(a, &ax, &ay, &az);
-                sh_parity(b, &bx, &by, &bz);
-                const int px = ax * bx, py = ay * by, pz = az * bz;
-                const int imag = (px * py * pz) < 0 ? 1 : 0;
-                const int info = pidx | (imag << 16) | ((py < 0) << 17) | ((pz < 0) << 18);
-                pinfo[a * M + b] = pinfo[b * M + a] = info;
-                pimag[pidx] = imag;
-                ++pidx;
-            }
-    }
+    aniso_pair_table(M, pinfo.data(), pimag.data());
     cudaError_t e = cudaSuccess;
     double2* G = nullptr;
     double* Dd = nullptr;
@@ -669,6 +673,14 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     }
     op->ms_pre = ms;
     *out = op;
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_aniso3d_pair_table(int L, int* out_host) {
+    if (L < 0 || L > RTE_ANISO_MAX_L || !out_host) return RTE_EINVAL;
+    const int M = (L + 1) * (L + 1);
+    std::vector<int> pimag(M * (M + 1) / 2);
+    aniso_pair_table(M, out_host, pimag.data());
     return RTE_OK;
 }
 

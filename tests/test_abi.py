@@ -92,3 +92,32 @@ def test_aniso3d_null_handles_without_gpu():
     assert L.rte_aniso3d_destroy(None) == B.RTE_OK
     assert L.rte_aniso3d_apply_K(None, None, None, None) == B.RTE_EINVAL
     assert L.rte_aniso3d_info(None, None, None) == B.RTE_EINVAL
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 4])
+def test_aniso3d_pair_table_matches_harmonic_parities(L):
+    """The host table the spectra are stored by (rte_aniso3d_pair_table, no
+    device call): symmetric, one index per unordered pair, and the flags equal
+    the parities of Y_a Y_b measured from the oracle's harmonics at mirrored
+    directions (imaginary spectrum iff W_ab is odd under v -> -v)."""
+    import numpy as np
+    from oracle import aniso3d as A
+    from paper_1802_03061_gb300 import _binding as B
+    M = A.n_channels(L)
+    t = np.array(B.rte_aniso3d_pair_table(L)).reshape(M, M)
+    assert (t == t.T).all()
+    iu = np.triu_indices(M)
+    idx = t[iu] & 0xFFFF
+    assert sorted(idx.tolist()) == list(range(M * (M + 1) // 2))
+    v = np.array([[0.31, -0.52, 0.79]])
+    v /= np.linalg.norm(v)
+    Y = A.real_sh(L, v)[0]
+    par = []
+    for k in range(3):
+        m = v.copy()
+        m[:, k] *= -1
+        par.append(np.sign(np.round(A.real_sh(L, m)[0] / Y, 9)).astype(int))
+    px, py, pz = (np.outer(p, p) for p in par)
+    np.testing.assert_array_equal((t >> 16) & 1, (px * py * pz < 0).astype(int))
+    np.testing.assert_array_equal((t >> 17) & 1, (py < 0).astype(int))
+    np.testing.assert_array_equal((t >> 18) & 1, (pz < 0).astype(int))
