@@ -41,7 +41,10 @@ against Legendre polynomials; D_00 against the isotropic oracle's cell
 weight (QUADPACK in spherical coordinates), sum_m D_{lm,lm} = (2l+1) D_00,
 the parity zeros; L = 0 against the isotropic direct sum; the discrete
 parity-transpose symmetry; the outward first moment of a point source; a
-solve with sigma_hat_1 = 0 whose mean density is the isotropic solution.
+solve with sigma_hat_1 = 0 whose mean density is the isotropic solution; one
+transport step taken through the angular density instead (the
+Henyey-Greenstein function integrated by brute-force sphere quadrature), which
+fixes the normalisation of sigma_hat, the 4 pi of W_ab and the direction of v.
 
 Field layout: real arrays (M, n, n, n) indexed [a, iz, iy, ix], x fastest.
 """
