@@ -121,3 +121,43 @@ def test_aniso3d_pair_table_matches_harmonic_parities(L):
     np.testing.assert_array_equal((t >> 16) & 1, (px * py * pz < 0).astype(int))
     np.testing.assert_array_equal((t >> 17) & 1, (py < 0).astype(int))
     np.testing.assert_array_equal((t >> 18) & 1, (pz < 0).astype(int))
+
+
+def test_aniso3d_octant_storage_rebuilds_the_spectra():
+    """Each pair's spectrum is stored as the real octant xi in [0, Q/2]^3 of its
+    real or imaginary part; the pair table's flags (imaginary, odd in y, odd in
+    z) must rebuild the half spectrum xi_x in [0, Q/2], all xi_y, xi_z of the
+    sampled kernel h^3 e^{-mu r}/(4 pi r^2) 4 pi Y_a Y_b exactly (numpy FFT of
+    the oracle's harmonics; no device call)."""
+    import math
+
+    import numpy as np
+    from oracle import aniso3d as A
+    from paper_1802_03061_gb300 import _binding as B
+    L, n, Q, h, mu = 2, 5, 12, 0.2, 3.0
+    M, H = A.n_channels(L), Q // 2 + 1
+    t = np.array(B.rte_aniso3d_pair_table(L)).reshape(M, M)
+    o = np.arange(Q)
+    s = np.where(o < Q // 2, o, o - Q)
+    SZ, SY, SX = np.meshgrid(s, s, s, indexing="ij")
+    d = np.sqrt(SX ** 2 + SY ** 2 + SZ ** 2).astype(float)
+    valid = (abs(SX) < n) & (abs(SY) < n) & (abs(SZ) < n) & (d > 0)
+    ds = np.where(d > 0, d, 1.0)
+    v = np.stack([SX / ds, SY / ds, SZ / ds], -1)
+    Y = A.real_sh(L, v)
+    kap = np.where(valid, h ** 3 * np.exp(-mu * h * ds) / (4 * math.pi * (h * ds) ** 2), 0.0)
+    ky = np.arange(Q)[:, None]
+    kz = np.arange(Q)[None, :]
+    fy, fz = np.minimum(ky, Q - ky), np.minimum(kz, Q - kz)
+    for a in range(M):
+        for b in range(a, M):
+            g = 4 * math.pi * kap * Y[..., a] * Y[..., b]  # [oz, oy, ox]
+            G = np.fft.fftn(g).transpose(2, 1, 0)          # [kx, ky, kz]
+            info = t[a, b]
+            imag, oy, oz = (info >> 16) & 1, (info >> 17) & 1, (info >> 18) & 1
+            part = G.imag if imag else G.real
+            np.testing.assert_allclose(G.real if imag else G.imag, 0, atol=1e-13 * np.abs(G).max())
+            oct_ = part[:H, :H, :H]
+            sgn = np.where((ky > Q // 2) & bool(oy), -1.0, 1.0) * np.where((kz > Q // 2) & bool(oz), -1.0, 1.0)
+            rebuilt = sgn[None] * oct_[:, fy, fz]
+            np.testing.assert_allclose(rebuilt, part[:H], atol=1e-13 * np.abs(G).max())
