@@ -23,7 +23,10 @@ Functions and what pins them (tests/test_oracle_pins.py):
   ``sampled_residual_2d`` (and 3D analogues) -- the equation of Sec. 3.3
   (Eq. ani_AU) and of Sec. 2.3 for L = 0.  Pinned by mu_s = 0 (u = b),
   Neumann series versus LU, positivity, rotation equivariance, the Lemma
-  Linfcontraction bound and grid refinement.
+  Linfcontraction bound and grid refinement.  The sampled residuals are
+  pinned by their vanishing at the dense LU solution (all cells, L = 0, 3, 4
+  in 2D, and 3D) and by the identity r(u_LU + d) = -(I - K) d with (I - K)
+  taken from the assembled dense matrix.
 """
 import ctypes
 import math

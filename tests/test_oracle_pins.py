@@ -456,3 +456,64 @@ def test_paper_anisotropic_table_error_order_of_magnitude():
         ug, _, _ = oracle.gmres(lambda t: t - oracle.apply_K_2d(n, h, 1.2, 1.0, sig, t, D=D), b, tol=eps)
         err = oracle.rel_l2(ug, u)
         assert abs(math.log10(err) - math.log10(err_paper)) <= 2.0, (eps, err, err_paper)
+
+
+# ---------------------------------------------------------------------------
+# The sampled residual: the checker of every full-size GPU solve
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [0, 3, 4])
+def test_sampled_residual_2d_vanishes_at_the_dense_solution(L):
+    """Eq. ani_AU: at the LU solution of (I - K) u = K~ g the residual
+    b - u + K u is zero at every cell and every mode -L..L.  L = 3 and 4 put
+    the right-hand side's cell weights D_{-L..L} off the centre of the
+    D_{-2L..2L} table (a shifted window would bring in D_{+-4} at the wrong
+    modes), and all cells are sampled, in a scrambled order."""
+    n, h, mu = 6, 1.0 / 6, 7.0
+    sig = rte_synth.hg_sigma_hat(0.6, L)
+    f = rte_synth.gaussian_mixture_2d(n, [(0.35, 0.6), (0.7, 0.3)], [0.15, 0.1])
+    u, b = oracle.solve_dense_2d(n, h, mu, 0.9 * mu, sig, f)
+    rows = np.random.default_rng(5).permutation(n * n)
+    r, bs = oracle.sampled_residual_2d(n, h, mu, 0.9 * mu, sig, f, u, rows)
+    assert r.shape == (2 * L + 1, n * n)
+    assert np.abs(bs - b.reshape(2 * L + 1, -1)[:, rows]).max() <= 1e-14 * np.abs(b).max()
+    assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(bs)
+
+
+@pytest.mark.parametrize("L", [1, 3])
+def test_sampled_residual_2d_of_a_perturbation(L):
+    """For u = u_LU + d the residual is -(I - K) d, with (I - K) taken from the
+    assembled dense matrix (the C assembly, not the row sums the residual
+    uses): a wrong mode placement, sign or sigma weight fails here."""
+    n, h, mu = 6, 1.0 / 6, 4.0
+    mus = 0.8 * mu
+    sig = rte_synth.hg_sigma_hat(0.5, L)
+    f = rte_synth.gaussian_mixture_2d(n, [(0.4, 0.55)], [0.2])
+    u, _ = oracle.solve_dense_2d(n, h, mu, mus, sig, f)
+    rng = np.random.default_rng(11)
+    d = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    d = 0.5 * (d + d[::-1].conj())  # a J-symmetric perturbation, like every solver field
+    Kt = oracle.assemble_ktilde_2d(n, h, mu, L)
+    N = n * n
+    sig_full = np.repeat(np.concatenate([sig[:0:-1], sig]), N)
+    Ad = (d.reshape(-1) - mus * (Kt @ (sig_full * d.reshape(-1)))).reshape(2 * L + 1, N)
+    rows = rng.choice(N, size=17, replace=False)
+    r, _ = oracle.sampled_residual_2d(n, h, mu, mus, sig, f, u + d, rows)
+    assert np.abs(r + Ad[:, rows]).max() <= 1e-13 * np.abs(Ad).max()
+
+
+def test_sampled_residual_3d():
+    """3D: zero residual at the LU solution, and -(I - K) d for a perturbation
+    d, (I - K) from the assembled dense matrix."""
+    n, h, mu = 4, 0.25, 6.0
+    mus = 0.9 * mu
+    f = rte_synth.gaussian_3d(n, (0.4, 0.5, 0.6), 0.2)
+    u, b = oracle.solve_dense_3d(n, h, mu, mus, f)
+    rows = np.random.default_rng(3).permutation(n ** 3)
+    r, bs = oracle.sampled_residual_3d(n, h, mu, mus, f, u, rows)
+    assert np.abs(bs - b.reshape(-1)[rows]).max() <= 1e-14 * np.abs(b).max()
+    assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(bs)
+    d = np.random.default_rng(4).standard_normal(u.shape)
+    Ad = d.reshape(-1) - mus * (oracle.assemble_ktilde_3d(n, h, mu) @ d.reshape(-1))
+    r, _ = oracle.sampled_residual_3d(n, h, mu, mus, f, u + d, rows[:20])
+    assert np.abs(r + Ad[rows[:20]]).max() <= 1e-13 * np.abs(Ad).max()
