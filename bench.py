@@ -300,38 +300,19 @@ def run_native(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = ws / (float(np.mean(e2e_ms)) / 1e3)
 
-    # roofline of the dominant kernels: per-pass CUDA-event timing
+    # roofline of the FFT + mode-mix matvec (CUDA events, per-pass timing)
     reps = 50
-    ms32 = B.rte_time_passes(plan.handle, 1, reps, int(stream.cuda_stream))
-    ms64 = B.rte_time_passes(plan.handle, 0, reps, int(stream.cuda_stream))
-    H, Q, nch = plan.Q // 2 + 1, plan.Q, 2 * L + 1
-    s_spec = {"mixed_bf16": 4, "mixed_fp32": 8, "fp64": 16}[args.prec]
-    s_name = {"mixed_bf16": "BF16", "mixed_fp32": "FP32", "fp64": "FP32"}[args.prec]
-    col_bytes32 = nch * H * n * 8 * 2 + H * nch * Q * s_spec       # T in + T out + spectra
-    col_bytes64 = nch * H * n * 16 * 2 + H * nch * Q * 16
-    mv_bytes32 = 2 * n * n * nch * 4 + nch * (Q * Q // 2) * s_spec  # algorithmic bytes of one K application
+    sp = int(stream.cuda_stream)
+    ms32 = B.rte_time_passes(plan.handle, 1, reps, sp)
+    ms64 = B.rte_time_passes(plan.handle, 0, reps, sp)
     hbm_peak, peak_src = peaks()
-    ach = col_bytes32 / (ms32[1] * 1e-3) / 1e9
     cufft_ms = cufft_pair_ms((L + 1, n, n), (plan.Q, plan.Q), real=False)
-    op_roof = {"kernel": "k_col_warp: operator column pass (FFT_y, mode mix, iFFT_y), FP32, %s spectra" % s_name,
-               "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-               "traffic": COLPASS_TRAFFIC.get(("k_col_warp<8,16,float2>", n, L, plan.Q, args.prec)),
-               "peak_source": peak_src, "algorithmic_bytes_per_launch": col_bytes32, "ms_per_launch": ms32[1]}
-    roof = op_roof
+    roof = matvec_roofline(args.prec, n, L, plan.Q, ms64 if args.prec == "fp64" else ms32, hbm_peak, peak_src,
+                           clk.get("sm_mhz"))
     ms_pc = None
     if args.prec != "fp64" and args.precond:
-        # with the preconditioner on, its column pass is the solve's largest
-        # kernel (one launch per inner step, like the operator's, but longer):
-        # algorithmic bytes = T in (nl channels) + T out (2L+1) + the table
-        ms_pc = B.rte_time_passes(plan.handle, 3, reps, int(stream.cuda_stream))
-        nl = 2 * B.rte_precond_info(plan.handle) + 1
-        pc_bytes = nl * H * n * 8 + nch * H * n * 8 + nch * nl * (Q // 2 + 8) * H * 2
-        ach_pc = pc_bytes / (ms_pc[1] * 1e-3) / 1e9
-        roof = {"kernel": "k_col_warp_pc: preconditioner column pass (FFT_y of the inverted channels, "
-                          "BF16 table mix, iFFT_y), FP32", "bound": "hbm", "achieved": ach_pc, "peak": hbm_peak,
-                "unit": "GB/s", "frac": ach_pc / hbm_peak,
-                "traffic": PCPASS_TRAFFIC.get(("k_col_warp_pc<8,16>", n, L, plan.Q, nl)),
-                "peak_source": peak_src, "algorithmic_bytes_per_launch": pc_bytes, "ms_per_launch": ms_pc[1]}
+        # the preconditioner's passes, one application per inner step beside K's
+        ms_pc = B.rte_time_passes(plan.handle, 3, reps, sp)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -351,11 +332,10 @@ def run_native(args):
                    ("unpreconditioned" if args.precond else "preconditioned") + "_iters":
                        float(np.mean(alt_its)) if alt_its else None,
                    "pass_ms_precond": ms_pc,
-                   "roofline_operator_column": op_roof,
                    "bf16_spectra_ms_per_solve": float(np.mean(bf16_ms)) if bf16_ms else None,
                    "bf16_spectra_iters": float(np.mean(bf16_its)) if bf16_its else None,
                    "pass_ms_fp32": ms32, "pass_ms_fp64": ms64,
-                   "matvec_fp32_ms": sum(ms32), "matvec_fp32_useful_GBs": mv_bytes32 / (sum(ms32) * 1e-3) / 1e9,
+                   "matvec_fp32_ms": sum(ms32),
                    "pass_ms_float_float": B.rte_time_passes(plan.handle, 2, reps, int(stream.cuda_stream)),
                    "cufft_comparator_ms": cufft_ms,
                    "cufft_comparator": "torch.fft (cuFFT) fft2 + ifft2 of the %d zero-padded complex mode fields "
@@ -381,15 +361,62 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
-# DRAM bytes of one launch of the roofline kernel from an ncu capture (L2
-# flushed before the launch), summarised in
-# profiles/k_col_warp_hg2d_transport_256_L8.md; valid only for the kernel
-# version that capture measured and for this workload shape and precision
-# (None otherwise).
-COLPASS_TRAFFIC = {("k_col_warp<8,16,float2>", 256, 8, 512, "mixed_fp32"): 26912512}
-# the same for the preconditioner's column pass (inverted channels nl = 9),
-# profiles/k_col_warp_pc_hg2d_transport_256_L8.md
-PCPASS_TRAFFIC = {("k_col_warp_pc<8,16>", 256, 8, 512, 9): 25568256}
+# Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, L2
+# flushed before the launch) and executed warp instructions
+# (smsp__inst_executed.sum) of the three kernels of one FP32 K application,
+# from the ncu capture summarised in profiles/matvec_hg2d_transport_256_L8.md.
+# Valid only for the kernel versions that capture measured and for this shape
+# and precision (the roofline reports null otherwise).
+MATVEC_NCU = {}
+
+
+def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):
+    """Roofline of one K application by the algorithmic bytes of the method:
+    the 2L+1 real channels of the field in and out once and the 2L+1
+    half-plane spectra once, B_alg = 2 N (2L+1) s_f + (2L+1) (Q^2/2) s_S,
+    divided by the application's time (the three pass kernels back to back,
+    CUDA events).  Bytes the passes move through their intermediate are not
+    algorithmic; they are given separately as pass_bytes.  The column pass is
+    reported beside it against the same B_alg."""
+    nch = 2 * L + 1
+    H = Q // 2 + 1
+    s_f, s_spec, name = {"fp64": (8, 16, "FP64"), "mixed_fp32": (4, 8, "FP32"),
+                         "mixed_bf16": (4, 4, "BF16")}[prec]
+    t_f = 2 * s_f  # complex intermediate
+    b_alg = 2 * n * n * nch * s_f + nch * (Q * Q // 2) * s_spec
+    t_mv = float(sum(ms))
+    ach = b_alg / (t_mv * 1e-3) / 1e9
+    key = (n, L, Q, prec)
+    ncu = MATVEC_NCU.get(key)
+    clock_hz = (sm_mhz or 2070.0) * 1e6
+    issue_rate = 152 * 4 * clock_hz  # warp instructions per second, all SMs
+
+    def issue(insts, t_ms):
+        return None if insts is None else insts / issue_rate / (t_ms * 1e-3)
+
+    col_pass_bytes = nch * H * n * t_f * 2 + H * nch * Q * s_spec  # T in + T out + spectra
+    return {
+        "kernel": "K application, %s fields and spectra: row pass + fused column pass (FFT_y, mode mix, "
+                  "iFFT_y) + inverse row pass, 3 launches" % name,
+        "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+        "traffic": None if ncu is None else ncu["dram_bytes"],
+        "peak_source": peak_src, "algorithmic_bytes_per_launch": b_alg, "ms_per_launch": t_mv,
+        "algorithmic_bytes": "2 N (2L+1) s_f + (2L+1) (Q^2/2) s_S: N = %d cells, 2L+1 = %d real channels, "
+                             "s_f = %d, Q = %d, s_S = %d" % (n * n, nch, s_f, Q, s_spec),
+        "issue": issue(None if ncu is None else ncu["insts"], t_mv),
+        "issue_note": "warp instructions / (152 SMs x 4 x SM clock) / time: the fraction of the GPU's "
+                      "instruction issue the application uses",
+        "column_pass": {
+            "ms": ms[1], "frac": b_alg / (ms[1] * 1e-3) / 1e9 / hbm_peak,
+            "frac_note": "the whole application's B_alg over the column pass's time alone",
+            "pass_bytes": col_pass_bytes,
+            "pass_bytes_note": "T in + T out + spectra of this one pass (intermediates included: not "
+                               "algorithmic)",
+            "traffic": None if ncu is None else ncu.get("col_dram_bytes"),
+            "issue": issue(None if ncu is None else ncu.get("col_insts"), ms[1])},
+        "l2": "warm: back-to-back launches, the application's working set (%.1f MB) fits the 129 MB L2, as it "
+              "does inside the solve" % (b_alg / 1e6),
+    }
 
 
 def cufft_pair_ms(shape_in, s_fft, real, reps=20):
@@ -625,6 +652,75 @@ def run_iso3d(args):
                          "frac": alg32 / (mv32 * 1e-3) / 1e9 / hbm, "unit": "GB/s", "traffic": None,
                          "peak_source": src, "algorithmic_bytes_per_launch": alg32},
             "gpu_launches": int(launches), "clocks": clk}
+    plan.close()
+    print(json.dumps(line))
+
+
+def run_iso2d64(args):
+    """The 2D isotropic latency workload: 64 x 64 cells, mu_t = 1, mu_s = 0.5,
+    L = 0, one Gaussian bump (width 0.1) at the centre; plain FP64 GMRES to a
+    relative residual of 1e-10.  A step is one solve (b = K~ f and the GMRES
+    iterations, one graph launch).  At 4096 unknowns the solve is bound by
+    kernel latency, not by HBM or ALU: the line reports microseconds per solve
+    and iterations, and its roofline object says so."""
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Plan
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    prob = rte_synth.iso2d_bump()
+    n = prob["n"]
+    plan = Plan(n, mu_t=prob["mu_t"], mu_s=prob["mu_s"], sigma_hat=[1.0], prec="fp64", tol=1e-10, restart=40)
+    f = torch.from_numpy(prob["f"]).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        plan.solve(f)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = B.rte_kernel_launches()
+    tot, stats = 0.0, []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        u, st = plan.solve(f)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        stats.append(st)
+    launches = B.rte_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = tot / args.steps
+    # per-application time of the FP64 operator (3 kernels)
+    ms64 = B.rte_time_passes(plan.handle, 0, 50, int(stream.cuda_stream))
+    hbm, src = peaks()
+    H = plan.Q // 2 + 1
+    alg = 2 * n * n * 8 + H * H * 8  # real field in + out, real even octant of the spectrum (FP64)
+    line = {"metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "iso2d_bump_64: 64x64 cells, mu_t = 1, mu_s = 0.5, L = 0, Gaussian width 0.1 "
+                                   "at (0.5, 0.5); plain FP64 GMRES to 1e-10",
+                       "us_per_solve": ms * 1e3, "iters_mean": float(np.mean([s_["iters"] for s_ in stats])),
+                       "relres_max": max(s_["relres_true"] for s_ in stats),
+                       "all_converged": all(s_["converged"] for s_ in stats),
+                       "us_per_iteration": ms * 1e3 / max(1.0, float(np.mean([s_["iters"] for s_ in stats]))),
+                       "pass_us_fp64": [1e3 * v for v in ms64], "t_pre_ms": stats[0]["ms_pre"],
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "roofline": {"bound": "latency", "kernel": "FP64 K application (3 launches)",
+                         "achieved": alg / (sum(ms64) * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (sum(ms64) * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": src,
+                         "algorithmic_bytes_per_launch": alg, "ms_per_launch": sum(ms64),
+                         "note": "4096 unknowns: every kernel is a fraction of one wave, so launch and "
+                                 "dependency latency bound the solve; no HBM or ALU roofline claim"},
+            "e2e": None, "gpu_launches": int(launches), "clocks": clk}
     plan.close()
     print(json.dumps(line))
 
@@ -895,7 +991,7 @@ def main():
     ap.add_argument("--inhom-n", type=int, default=256, help="inhom workload: cells per side")
     ap.add_argument("--aniso-n", type=int, default=64, help="aniso3d workload: cells per side")
     ap.add_argument("--workload", default="hg2d_transport",
-                    choices=["hg2d_transport", "batch512", "iso3d", "learned", "inhom", "aniso3d"])
+                    choices=["hg2d_transport", "iso2d64", "batch512", "iso3d", "learned", "inhom", "aniso3d"])
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=4, help="learned workload: training epochs")
     ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
@@ -911,6 +1007,8 @@ def main():
         return
     if args.workload == "inhom":
         return run_inhom(args)
+    if args.workload == "iso2d64":
+        return run_iso2d64(args)
     if args.workload == "aniso3d":
         return run_aniso3d(args)
     if args.workload == "batch512":

@@ -209,16 +209,27 @@ typedef struct rte_batch_s* rte_batch;
  * Owns all device memory; RTE_ENOMEM if it does not fit. */
 rte_status rte_batch_create(rte_batch* out, int count, const rte_instance_desc* descs, const rte_opts* opts,
                             void* cuda_stream);
+/* Solve every instance: f[i] (device, n_i^2 doubles) is instance i's source
+ * and u[i] (device, 2(L_i+1) n_i^2 doubles, the FP64 mode-field layout)
+ * receives its solution; f and u are host arrays of `count` device pointers,
+ * caller-owned (the survey's boundary form of the batched solve).  The
+ * sources are gathered into the batch's packed buffer by one kernel, the
+ * graph runs, one kernel scatters the solutions.  stats_host (count entries,
+ * may be NULL) receives each instance's statistics (ms_total = the graph
+ * launch's device time).  Synchronises the stream once at exit.  Returns the
+ * first non-OK instance status; RTE_EINVAL for a null pointer. */
+rte_status rte_batch_solve(rte_batch b, const double* const* f, void* const* u, rte_stats* stats_host,
+                           void* cuda_stream);
 /* Offsets (in doubles) of instance i's source f (n^2 doubles) and solution u
  * (2(L+1)n^2 doubles, the FP64 mode-field layout) in the packed arrays that
- * rte_batch_solve takes; arrays of count+1 entries (last = total). */
+ * rte_batch_solve_packed takes; arrays of count+1 entries (last = total). */
 rte_status rte_batch_layout(rte_batch b, long* f_offsets_host, long* u_offsets_host);
-/* Solve every instance: f_packed_dev / u_packed_dev are caller-owned device
- * arrays in the rte_batch_layout packing.  stats_host (count entries, may be
- * NULL) receives each instance's statistics; ms_out (may be NULL) the device
- * time of the graph launch.  Returns the first non-OK instance status. */
-rte_status rte_batch_solve(rte_batch b, const double* f_packed_dev, double* u_packed_dev, rte_stats* stats_host,
-                           double* ms_out, void* cuda_stream);
+/* The same solve on packed arrays: f_packed_dev / u_packed_dev are
+ * caller-owned device arrays in the rte_batch_layout packing (one copy in,
+ * one copy out instead of the gather / scatter kernels); ms_out (may be
+ * NULL) receives the device time of the graph launch. */
+rte_status rte_batch_solve_packed(rte_batch b, const double* f_packed_dev, double* u_packed_dev,
+                                  rte_stats* stats_host, double* ms_out, void* cuda_stream);
 rte_status rte_batch_destroy(rte_batch b);
 /* The plan of instance i (owned by the batch; valid until rte_batch_destroy). */
 rte_status rte_batch_plan(rte_batch b, int i, rte_plan* out);
@@ -284,11 +295,32 @@ rte_status rte_guess_features(rte_plan p, int cin, const double* f_dev, const do
                               void* cuda_stream);
 rte_status rte_guess_targets(rte_plan p, int cout, const double* f_dev, const double* u_dev, const double* b_dev,
                              void* T_dev, void* cuda_stream);
-/* The learned initial guess: b_out_dev = K~ g (step T.1, FP64 mode field),
- * then u0_dev = b + s_b * net(features).  X_scratch_dev: bf16 [n][n][cin].
- * Pass u0 to rte_solve with opts->use_guess = 1. */
-rte_status rte_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, double* b_out_dev, void* X_scratch_dev,
-                           void* u0_dev, void* cuda_stream);
+/* The learned initial guess with caller-provided buffers: b_out_dev = K~ g
+ * (step T.1, FP64 mode field), then u0_dev = b + s_b * net(features).
+ * X_scratch_dev: bf16 [n][n][cin].  Pass u0 to rte_solve with
+ * opts->use_guess = 1. */
+rte_status rte_cnn_guess_apply(rte_cnn net, rte_plan p, const double* f_dev, double* b_out_dev, void* X_scratch_dev,
+                               void* u0_dev, void* cuda_stream);
+
+/* The learned guess as the boundary's handle (task extension (4): the
+ * network predicts the GMRES initial guess from the source and mu_t, mu_s,
+ * g; the paper has no counterpart).  rte_guess_load creates the network of
+ * the shape recorded in a weights file written by rte_cnn_save and loads it
+ * (synchronous, legacy default stream); RTE_EINVAL if the file is missing,
+ * truncated or not a weights file, RTE_ENOMEM when the device is full.  The
+ * handle owns the network and its scratch (the features and b = K~ g of the
+ * largest grid it has been applied to). */
+typedef struct rte_guess_s* rte_guess;
+rte_status rte_guess_load(rte_guess* out, const char* weights_path);
+/* u0_dev (FP64 mode field of plan p, device) = the learned initial guess for
+ * the source f_dev (double [n][n], device); pass it to rte_solve with
+ * opts->use_guess = 1 (the solve falls back to the zero start when the guess
+ * does not lower the residual).  The first call for a grid larger than any
+ * before allocates the handle's scratch (and synchronises the device); later
+ * calls are asynchronous on cuda_stream.  RTE_EINVAL for a 3D plan or when
+ * the plan's 2L+1 channels exceed the network's inputs or outputs. */
+rte_status rte_guess_apply(rte_guess g, rte_plan p, const double* f_dev, void* u0_dev, void* cuda_stream);
+rte_status rte_guess_destroy(rte_guess g);
 
 /* ---- Inhomogeneous medium, isotropic scattering, 2D (Sec. 2.3,
  * Eq. iso_discretization): the Nystrom matrix K~ applied directly, O(N^2).
@@ -378,6 +410,15 @@ rte_status rte_aniso3d_destroy(rte_aniso3d op);
  * the process (host-side counter; a replayed graph adds its kernel nodes). */
 rte_status rte_time_passes(rte_plan plan, int inner, int reps, double* ms_out_host, void* cuda_stream);
 long long rte_kernel_launches(void);
+/* Fault injection for tests of the error paths (no counterpart in the
+ * paper): every device and pinned-host allocation the library makes is
+ * counted; after this call the k-th one (k >= 1, counting from this call)
+ * fails as if the device were full (RTE_ENOMEM from the call that made it),
+ * and k <= 0 turns that off.  Outputs (any may be NULL), read before the
+ * reset: the allocations made since the previous call, and the library's
+ * live device and pinned-host allocations (a create call that failed must
+ * leave these where they were). */
+rte_status rte_debug_fail_alloc(long k, long* seen_out, long* live_dev_out, long* live_host_out);
 
 /* y = K x for a small 2D grid with no device allocation at all.  For
  * callers that may not allocate device memory where they call: plug-ins
@@ -387,17 +428,23 @@ long long rte_kernel_launches(void);
  * plan (rte_plan_create allocates), so this call rebuilds the plan data
  * (cell weights, kernel samples, spectra) and the pass intermediates on
  * every call inside one fixed static device array of
- * rte_noalloc_scratch_bytes() bytes (about 5 MB), which every GPU that loads
- * the library holds until process exit; then it applies the same FP64
- * passes as rte_apply_K.  Arguments as rte_plan_create + rte_apply_K:
- * x_dev, y_dev are caller-owned FP64 mode fields double2 [L+1][n][n] that
- * may not alias; sigma_hat is a host array of L+1 values.  Limits: n <= 64
- * and L <= 4; larger sizes return RTE_EUNSUPPORTED (use a plan).  The first
- * call on a device looks up the array's device address (a lookup, not an
- * allocation); make that first call before any stream capture.  All calls
- * share the array and it keeps the last call's contents; calls whose work
- * overlaps on the GPU race on it, so the caller must serialise them.
- * Asynchronous on cuda_stream.  (The paper has no counterpart of this
+ * rte_noalloc_scratch_bytes() bytes (about 5 MB), which every GPU that has
+ * loaded it holds until process exit; then it applies the same FP64 passes
+ * as rte_apply_K.  Arguments as rte_plan_create + rte_apply_K: x_dev, y_dev
+ * are caller-owned FP64 mode fields double2 [L+1][n][n] that may not alias;
+ * sigma_hat is a host array of L+1 values.  Limits: n <= 64 and L <= 4;
+ * larger sizes return RTE_EUNSUPPORTED (use a plan).
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address.  Under CUDA's default lazy module loading that
+ * lookup is also when the CUDA runtime loads the array onto the device, i.e.
+ * when its 5 MB of device memory are taken (RTE_ENOMEM if the device is
+ * full, RTE_ECUDA for another failure).  So make the first call on each device
+ * at start-up, where taking that memory is allowed, and before any stream
+ * capture; every later call takes no device memory.  (With
+ * CUDA_MODULE_LOADING=EAGER the array is loaded with the library instead.)
+ * All calls share the array and it keeps the last call's contents; calls
+ * whose work overlaps on the GPU race on it, so the caller must serialise
+ * them.  Asynchronous on cuda_stream.  (The paper has no counterpart of this
  * entry point.) */
 rte_status rte_apply_K_noalloc(int n, double h, double mu_t, double mu_s, int L, const double* sigma_hat,
                                const void* x_dev, void* y_dev, void* cuda_stream);

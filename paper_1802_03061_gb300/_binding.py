@@ -92,6 +92,9 @@ def lib():
         L.rte_time_passes.argtypes = [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP]
         L.rte_time_passes.restype = ctypes.c_int
         L.rte_kernel_launches.restype = ctypes.c_longlong
+        L.rte_debug_fail_alloc.argtypes = [ctypes.c_long, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                           ctypes.POINTER(ctypes.c_long)]
+        L.rte_debug_fail_alloc.restype = ctypes.c_int
         L.rte_apply_K_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_double), VP, VP, VP]
         L.rte_apply_K_noalloc.restype = ctypes.c_int
@@ -99,11 +102,14 @@ def lib():
         L.rte_batch_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.POINTER(rte_instance_desc),
                                        ctypes.POINTER(rte_opts), VP]
         L.rte_batch_layout.argtypes = [VP, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
-        L.rte_batch_solve.argtypes = [VP, VP, VP, ctypes.POINTER(rte_stats), ctypes.POINTER(ctypes.c_double), VP]
+        L.rte_batch_solve.argtypes = [VP, ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(rte_stats), VP]
+        L.rte_batch_solve_packed.argtypes = [VP, VP, VP, ctypes.POINTER(rte_stats), ctypes.POINTER(ctypes.c_double),
+                                             VP]
         L.rte_batch_destroy.argtypes = [VP]
         L.rte_autotune.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), VP]
-        for name in ("rte_batch_create", "rte_batch_layout", "rte_batch_solve", "rte_batch_destroy", "rte_autotune"):
+        for name in ("rte_batch_create", "rte_batch_layout", "rte_batch_solve", "rte_batch_solve_packed",
+                     "rte_batch_destroy", "rte_autotune"):
             getattr(L, name).restype = ctypes.c_int
         FP = ctypes.POINTER(ctypes.c_float)
         L.rte_cnn_create.argtypes = [ctypes.POINTER(VP), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -119,11 +125,15 @@ def lib():
         L.rte_cnn_load.argtypes = [VP, ctypes.c_char_p, VP]
         L.rte_guess_features.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP]
         L.rte_guess_targets.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP, VP]
-        L.rte_guess_apply.argtypes = [VP, VP, VP, VP, VP, VP, VP]
+        L.rte_cnn_guess_apply.argtypes = [VP, VP, VP, VP, VP, VP, VP]
+        L.rte_guess_load.argtypes = [ctypes.POINTER(VP), ctypes.c_char_p]
+        L.rte_guess_apply.argtypes = [VP, VP, VP, VP, VP]
+        L.rte_guess_destroy.argtypes = [VP]
         L.rte_batch_plan.argtypes = [VP, ctypes.c_int, ctypes.POINTER(VP)]
         for name in ("rte_cnn_create", "rte_cnn_destroy", "rte_cnn_forward", "rte_cnn_train_step", "rte_cnn_layer",
                      "rte_cnn_sync_weights", "rte_cnn_save", "rte_cnn_load", "rte_guess_features",
-                     "rte_guess_targets", "rte_guess_apply", "rte_batch_plan"):
+                     "rte_guess_targets", "rte_cnn_guess_apply", "rte_guess_load", "rte_guess_apply",
+                     "rte_guess_destroy", "rte_batch_plan"):
             getattr(L, name).restype = ctypes.c_int
         L.rte_status_str.argtypes = [ctypes.c_int]
         L.rte_status_str.restype = ctypes.c_char_p
@@ -334,6 +344,15 @@ def rte_apply_K_noalloc(n, h, mu_t, mu_s, L, sigma_hat, x, y, stream=0):
                                      VP(stream)), "rte_apply_K_noalloc")
 
 
+def rte_debug_fail_alloc(k):
+    """Make the k-th library allocation from now fail (0: none); returns the
+    allocations since the previous call and the live (device, host) counts."""
+    seen, dev, host = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+    _check(lib().rte_debug_fail_alloc(int(k), ctypes.byref(seen), ctypes.byref(dev), ctypes.byref(host)),
+           "rte_debug_fail_alloc")
+    return seen.value, dev.value, host.value
+
+
 def rte_noalloc_scratch_bytes():
     return int(lib().rte_noalloc_scratch_bytes())
 
@@ -363,12 +382,23 @@ def rte_batch_layout(batch, count):
     return list(f), list(u)
 
 
-def rte_batch_solve(batch, count, f_packed, u_packed, stream=0):
+def rte_batch_solve_packed(batch, count, f_packed, u_packed, stream=0):
     stats = (rte_stats * count)()
     ms = ctypes.c_double()
-    st = lib().rte_batch_solve(batch, VP(f_packed), VP(u_packed), stats, ctypes.byref(ms), VP(stream))
-    _check(st, "rte_batch_solve", allow=(RTE_ENOCONV,))
+    st = lib().rte_batch_solve_packed(batch, VP(f_packed), VP(u_packed), stats, ctypes.byref(ms), VP(stream))
+    _check(st, "rte_batch_solve_packed", allow=(RTE_ENOCONV,))
     return st, [x.as_dict() for x in stats], ms.value
+
+
+def rte_batch_solve(batch, f_ptrs, u_ptrs, stream=0):
+    """f_ptrs, u_ptrs: sequences of device pointers, one per instance."""
+    count = len(f_ptrs)
+    fa = (VP * count)(*[VP(int(p)) for p in f_ptrs])
+    ua = (VP * count)(*[VP(int(p)) for p in u_ptrs])
+    stats = (rte_stats * count)()
+    st = lib().rte_batch_solve(batch, fa, ua, stats, VP(stream))
+    _check(st, "rte_batch_solve", allow=(RTE_ENOCONV,))
+    return st, [x.as_dict() for x in stats]
 
 
 def rte_batch_destroy(batch):
@@ -437,8 +467,23 @@ def rte_guess_targets(plan, cout, f, u, b, T, stream=0):
     _check(lib().rte_guess_targets(plan, cout, VP(f), VP(u), VP(b), VP(T), VP(stream)), "rte_guess_targets")
 
 
-def rte_guess_apply(net, plan, f, b_out, Xs, u0, stream=0):
-    _check(lib().rte_guess_apply(net, plan, VP(f), VP(b_out), VP(Xs), VP(u0), VP(stream)), "rte_guess_apply")
+def rte_cnn_guess_apply(net, plan, f, b_out, Xs, u0, stream=0):
+    _check(lib().rte_cnn_guess_apply(net, plan, VP(f), VP(b_out), VP(Xs), VP(u0), VP(stream)),
+           "rte_cnn_guess_apply")
+
+
+def rte_guess_load(path):
+    out = VP()
+    _check(lib().rte_guess_load(ctypes.byref(out), str(path).encode()), "rte_guess_load")
+    return out
+
+
+def rte_guess_apply(guess, plan, f, u0, stream=0):
+    _check(lib().rte_guess_apply(guess, plan, VP(f), VP(u0), VP(stream)), "rte_guess_apply")
+
+
+def rte_guess_destroy(guess):
+    _check(lib().rte_guess_destroy(guess), "rte_guess_destroy")
 
 
 def rte_destroy(plan):

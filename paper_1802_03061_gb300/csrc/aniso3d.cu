@@ -565,7 +565,7 @@ extern "C" rte_status rte_aniso3d_destroy(rte_aniso3d op) {
     void* ptrs[] = {op->tw64, op->tw32, op->S64, op->S32,  op->pinfo, op->T1,  op->T2,  op->V,
                     op->bvec, op->r,    op->part, op->hd, op->V32,   op->r32, op->x32, op->b32};
     for (void* q : ptrs)
-        if (q) cudaFree(q);
+        if (q) rte_dev_free(q);
     delete op;
     return RTE_OK;
 }
@@ -607,18 +607,18 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     cudaError_t e = cudaSuccess;
     double2* G = nullptr;
     double* Dd = nullptr;
-    if (cudaMalloc((void**)&op->tw64, Q * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&op->tw32, Q * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc((void**)&op->S64, op->np * H3 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&op->S32, op->np * H3 * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&op->pinfo, M * M * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&op->T1, (size_t)n * H * n * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&op->T2, (size_t)M * H * Q * n * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&G, (size_t)P * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&Dd, M * M * sizeof(double)) != cudaSuccess) {
+    if (rte_dev_malloc((void**)&op->tw64, Q * sizeof(double2)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->tw32, Q * sizeof(float2)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->S64, op->np * H3 * sizeof(double)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->S32, op->np * H3 * sizeof(float)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->pinfo, M * M * sizeof(int)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->T1, (size_t)n * H * n * sizeof(double2)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->T2, (size_t)M * H * Q * n * sizeof(double2)) != cudaSuccess ||
+        rte_dev_malloc((void**)&G, (size_t)P * sizeof(double2)) != cudaSuccess ||
+        rte_dev_malloc((void**)&Dd, M * M * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
-        if (G) cudaFree(G);
-        if (Dd) cudaFree(Dd);
+        if (G) rte_dev_free(G);
+        if (Dd) rte_dev_free(Dd);
         rte_aniso3d_destroy(op);
         return rte_fail(RTE_ENOMEM, "rte_aniso3d_create");
     }
@@ -664,8 +664,8 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(G);
-    cudaFree(Dd);
+    rte_dev_free(G);
+    rte_dev_free(Dd);
     rte_count_launches(launches);
     if (e != cudaSuccess) {
         rte_aniso3d_destroy(op);
@@ -726,20 +726,20 @@ extern "C" rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, dou
         for (void** q : {(void**)&op->V, (void**)&op->bvec, (void**)&op->r, (void**)&op->part, (void**)&op->hd,
                          (void**)&op->V32, (void**)&op->r32, (void**)&op->x32, (void**)&op->b32})
             if (*q) {
-                cudaFree(*q);
+                rte_dev_free(*q);
                 *q = nullptr;
             }
         op->gm = 0;
-        bool ok = cudaMalloc((void**)&op->bvec, len * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc((void**)&op->r, len * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc((void**)&op->part, (size_t)(restart + 1) * ANISO_NBLK * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc((void**)&op->hd, (restart + 1) * sizeof(double)) == cudaSuccess;
-        if (ok && !mixed) ok = cudaMalloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) == cudaSuccess;
+        bool ok = rte_dev_malloc((void**)&op->bvec, len * sizeof(double)) == cudaSuccess &&
+                  rte_dev_malloc((void**)&op->r, len * sizeof(double)) == cudaSuccess &&
+                  rte_dev_malloc((void**)&op->part, (size_t)(restart + 1) * ANISO_NBLK * sizeof(double)) == cudaSuccess &&
+                  rte_dev_malloc((void**)&op->hd, (restart + 1) * sizeof(double)) == cudaSuccess;
+        if (ok && !mixed) ok = rte_dev_malloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) == cudaSuccess;
         if (ok && mixed)
-            ok = cudaMalloc((void**)&op->V32, (size_t)(restart + 1) * len * sizeof(float)) == cudaSuccess &&
-                 cudaMalloc((void**)&op->r32, len * sizeof(float)) == cudaSuccess &&
-                 cudaMalloc((void**)&op->x32, len * sizeof(float)) == cudaSuccess &&
-                 cudaMalloc((void**)&op->b32, len * sizeof(float)) == cudaSuccess;
+            ok = rte_dev_malloc((void**)&op->V32, (size_t)(restart + 1) * len * sizeof(float)) == cudaSuccess &&
+                 rte_dev_malloc((void**)&op->r32, len * sizeof(float)) == cudaSuccess &&
+                 rte_dev_malloc((void**)&op->x32, len * sizeof(float)) == cudaSuccess &&
+                 rte_dev_malloc((void**)&op->b32, len * sizeof(float)) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
@@ -747,7 +747,7 @@ extern "C" rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, dou
         op->gm = restart;
     }
     if (!mixed && !op->V) {
-        if (cudaMalloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) != cudaSuccess) {
+        if (rte_dev_malloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
         }

@@ -31,19 +31,45 @@ struct rte_batch_s {
     void* tmpl_host = nullptr;        // pinned options template
     size_t ref_sz = 0;
     void* exec = nullptr;
+    // rte_batch_solve with one device buffer per instance: the prefix
+    // offsets on the device, the two pointer tables (device) and their
+    // pinned host staging
+    long* off_dev = nullptr;          // [2][count + 1]: f offsets, then u offsets
+    void** ptr_dev = nullptr;         // [2][count]: f pointers, then u pointers
+    void** ptr_host = nullptr;
 };
+
+// dst_base[off[i] + e] = src[i][e] (gather) or dst[i][e] = src_base[off[i] + e]
+// (scatter) for every instance i = blockIdx.y
+__global__ void k_batch_gather(const double* const* src, const long* off, double* dst_base) {
+    const int i = blockIdx.y;
+    const long n = off[i + 1] - off[i];
+    const double* a = src[i];
+    double* d = dst_base + off[i];
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) d[e] = a[e];
+}
+__global__ void k_batch_scatter(const double* src_base, const long* off, double* const* dst) {
+    const int i = blockIdx.y;
+    const long n = off[i + 1] - off[i];
+    const double* a = src_base + off[i];
+    double* d = dst[i];
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) d[e] = a[e];
+}
 
 extern "C" rte_status rte_batch_destroy(rte_batch b) {
     if (!b) return RTE_OK;
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy((cudaGraphExec_t)b->exec);
     for (rte_plan p : b->plans) rte_destroy(p);
-    if (b->f_all) cudaFree(b->f_all);
-    if (b->u_all) cudaFree(b->u_all);
-    if (b->ref_tmpl) cudaFree(b->ref_tmpl);
-    if (b->ref_all) cudaFree(b->ref_all);
-    if (b->ref_host) cudaFreeHost(b->ref_host);
-    if (b->tmpl_host) cudaFreeHost(b->tmpl_host);
+    if (b->f_all) rte_dev_free(b->f_all);
+    if (b->u_all) rte_dev_free(b->u_all);
+    if (b->ref_tmpl) rte_dev_free(b->ref_tmpl);
+    if (b->ref_all) rte_dev_free(b->ref_all);
+    if (b->ref_host) rte_host_free(b->ref_host);
+    if (b->tmpl_host) rte_host_free(b->tmpl_host);
+    if (b->off_dev) rte_dev_free(b->off_dev);
+    if (b->ptr_dev) rte_dev_free(b->ptr_dev);
+    if (b->ptr_host) rte_host_free(b->ptr_host);
     delete b;
     return RTE_OK;
 }
@@ -85,14 +111,24 @@ extern "C" rte_status rte_batch_create(rte_batch* out, int count, const rte_inst
         b->u_off[i + 1] = b->u_off[i] + p->nr;
     }
     b->ref_sz = refdev_size();
-    if (cudaMalloc((void**)&b->f_all, b->f_off[count] * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&b->u_all, b->u_off[count] * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->ref_tmpl, b->ref_sz) != cudaSuccess || cudaMalloc(&b->ref_all, b->ref_sz * count) != cudaSuccess ||
-        cudaMallocHost(&b->ref_host, b->ref_sz * count) != cudaSuccess ||
-        cudaMallocHost(&b->tmpl_host, b->ref_sz) != cudaSuccess) {
+    if (rte_dev_malloc((void**)&b->f_all, b->f_off[count] * sizeof(double)) != cudaSuccess ||
+        rte_dev_malloc((void**)&b->u_all, b->u_off[count] * sizeof(double)) != cudaSuccess ||
+        rte_dev_malloc(&b->ref_tmpl, b->ref_sz) != cudaSuccess || rte_dev_malloc(&b->ref_all, b->ref_sz * count) != cudaSuccess ||
+        rte_host_malloc(&b->ref_host, b->ref_sz * count) != cudaSuccess ||
+        rte_host_malloc(&b->tmpl_host, b->ref_sz) != cudaSuccess ||
+        rte_dev_malloc((void**)&b->off_dev, 2 * (count + 1) * sizeof(long)) != cudaSuccess ||
+        rte_dev_malloc((void**)&b->ptr_dev, 2 * count * sizeof(void*)) != cudaSuccess ||
+        rte_host_malloc((void**)&b->ptr_host, 2 * count * sizeof(void*)) != cudaSuccess) {
         cudaGetLastError();
         rte_batch_destroy(b);
         return RTE_ENOMEM;
+    }
+    if (cudaMemcpy(b->off_dev, b->f_off.data(), (count + 1) * sizeof(long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->off_dev + count + 1, b->u_off.data(), (count + 1) * sizeof(long), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        st = rte_cuda_fail(cudaGetLastError(), "rte_batch_create: offsets");
+        rte_batch_destroy(b);
+        return st;
     }
     // preconditioner data (allocates): before any capture
     for (int i = 0; i < count && st == RTE_OK; ++i)
@@ -167,20 +203,18 @@ extern "C" rte_status rte_batch_layout(rte_batch b, long* f_offsets, long* u_off
     return RTE_OK;
 }
 
-extern "C" rte_status rte_batch_solve(rte_batch b, const double* f_packed, double* u_packed, rte_stats* stats,
-                                      double* ms_out, void* stream) {
-    if (!b || !f_packed || !u_packed) return RTE_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    fill_ref_template(b->tmpl_host, &b->opts);
-    RTE_CUDA_TRY(cudaMemcpyAsync(b->ref_tmpl, b->tmpl_host, b->ref_sz, cudaMemcpyHostToDevice, s));
-    RTE_CUDA_TRY(cudaMemcpyAsync(b->f_all, f_packed, b->f_off[b->count] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+// the graph launch and the statistics, shared by both solve entry points;
+// `scatter` (may be null) runs after the graph, before the states come back
+static rte_status batch_run(rte_batch b, rte_stats* stats, double* ms_out, cudaStream_t s,
+                            rte_status (*scatter)(rte_batch, void*, cudaStream_t), void* scatter_arg) {
     cudaEvent_t e0, e1;
     RTE_CUDA_TRY(cudaEventCreate(&e0));
     RTE_CUDA_TRY(cudaEventCreate(&e1));
     RTE_CUDA_TRY(cudaEventRecord(e0, s));
     RTE_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)b->exec, s));
     RTE_CUDA_TRY(cudaEventRecord(e1, s));
-    RTE_CUDA_TRY(cudaMemcpyAsync(u_packed, b->u_all, b->u_off[b->count] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rte_status sst = scatter(b, scatter_arg, s);
+    if (sst != RTE_OK) return sst;
     RTE_CUDA_TRY(cudaMemcpyAsync(b->ref_host, b->ref_all, b->ref_sz * b->count, cudaMemcpyDeviceToHost, s));
     RTE_CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
@@ -202,6 +236,57 @@ extern "C" rte_status rte_batch_solve(rte_batch b, const double* f_packed, doubl
         if (st != RTE_OK && worst == RTE_OK) worst = st;
     }
     return worst;
+}
+
+static rte_status batch_options_in(rte_batch b, cudaStream_t s) {
+    fill_ref_template(b->tmpl_host, &b->opts);
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->ref_tmpl, b->tmpl_host, b->ref_sz, cudaMemcpyHostToDevice, s));
+    return RTE_OK;
+}
+
+static rte_status scatter_packed(rte_batch b, void* u_packed, cudaStream_t s) {
+    RTE_CUDA_TRY(cudaMemcpyAsync(u_packed, b->u_all, b->u_off[b->count] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return RTE_OK;
+}
+
+static rte_status scatter_ptrs(rte_batch b, void*, cudaStream_t s) {
+    dim3 grid(64, b->count);
+    k_batch_scatter<<<grid, 256, 0, s>>>(b->u_all, b->off_dev + b->count + 1, (double* const*)(b->ptr_dev + b->count));
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_batch_solve_packed(rte_batch b, const double* f_packed, double* u_packed, rte_stats* stats,
+                                             double* ms_out, void* stream) {
+    if (!b || !f_packed || !u_packed) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    rte_status st = batch_options_in(b, s);
+    if (st != RTE_OK) return st;
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->f_all, f_packed, b->f_off[b->count] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return batch_run(b, stats, ms_out, s, scatter_packed, u_packed);
+}
+
+extern "C" rte_status rte_batch_solve(rte_batch b, const double* const* f, void* const* u, rte_stats* stats,
+                                      void* stream) {
+    if (!b || !f || !u) return RTE_EINVAL;
+    for (int i = 0; i < b->count; ++i)
+        if (!f[i] || !u[i]) return RTE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the pinned staging is rewritten only after the previous call's copy of
+    // it has finished (every solve synchronises the stream before returning)
+    for (int i = 0; i < b->count; ++i) {
+        b->ptr_host[i] = (void*)f[i];
+        b->ptr_host[b->count + i] = u[i];
+    }
+    rte_status st = batch_options_in(b, s);
+    if (st != RTE_OK) return st;
+    RTE_CUDA_TRY(cudaMemcpyAsync(b->ptr_dev, b->ptr_host, 2 * b->count * sizeof(void*), cudaMemcpyHostToDevice, s));
+    dim3 grid(64, b->count);
+    k_batch_gather<<<grid, 256, 0, s>>>((const double* const*)b->ptr_dev, b->off_dev, b->f_all);
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return batch_run(b, stats, nullptr, s, scatter_ptrs, nullptr);
 }
 
 extern "C" rte_status rte_batch_plan(rte_batch b, int i, rte_plan* out) {

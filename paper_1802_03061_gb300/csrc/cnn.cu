@@ -482,13 +482,13 @@ static cudaError_t conv_wgrad(rte_cnn c, const bf16* X, const bf16* dY, CnnLayer
 }
 
 static void cnn_free_acts(rte_cnn c) {
-    for (bf16* a : c->act) if (a) cudaFree(a);
+    for (bf16* a : c->act) if (a) rte_dev_free(a);
     c->act.clear();
-    if (c->out_f) cudaFree(c->out_f);
-    if (c->g0) cudaFree(c->g0);
-    if (c->g1) cudaFree(c->g1);
-    if (c->part) cudaFree(c->part);
-    if (c->loss_part) cudaFree(c->loss_part);
+    if (c->out_f) rte_dev_free(c->out_f);
+    if (c->g0) rte_dev_free(c->g0);
+    if (c->g1) rte_dev_free(c->g1);
+    if (c->part) rte_dev_free(c->part);
+    if (c->loss_part) rte_dev_free(c->loss_part);
     c->out_f = nullptr;
     c->g0 = c->g1 = nullptr;
     c->part = nullptr;
@@ -503,18 +503,18 @@ static rte_status cnn_ensure(rte_cnn c, int B, int H, int W) {
     c->act.assign(c->depth + 1, nullptr);
     for (int l = 0; l <= c->depth; ++l) {
         const int ch = l == 0 ? c->cin : c->layers[l - 1].cout;
-        if (cudaMalloc((void**)&c->act[l], P * ch * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (rte_dev_malloc((void**)&c->act[l], P * ch * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
     }
     const int wmax = c->width > c->cin ? c->width : c->cin;
-    if (cudaMalloc((void**)&c->out_f, P * c->cout * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&c->g0, P * wmax * sizeof(bf16)) != cudaSuccess ||
-        cudaMalloc((void**)&c->g1, P * wmax * sizeof(bf16)) != cudaSuccess) {
+    if (rte_dev_malloc((void**)&c->out_f, P * c->cout * sizeof(float)) != cudaSuccess ||
+        rte_dev_malloc((void**)&c->g0, P * wmax * sizeof(bf16)) != cudaSuccess ||
+        rte_dev_malloc((void**)&c->g1, P * wmax * sizeof(bf16)) != cudaSuccess) {
         cudaGetLastError();
         return RTE_ENOMEM;
     }
     c->part_cap = (long)nblk_pix(B, H) * 9 * 64 * 64;
-    if (cudaMalloc((void**)&c->part, c->part_cap * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&c->loss_part, 1024 * sizeof(float)) != cudaSuccess) {
+    if (rte_dev_malloc((void**)&c->part, c->part_cap * sizeof(float)) != cudaSuccess ||
+        rte_dev_malloc((void**)&c->loss_part, 1024 * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return RTE_ENOMEM;
     }
@@ -530,9 +530,9 @@ extern "C" rte_status rte_cnn_destroy(rte_cnn c) {
     cnn_free_acts(c);
     for (CnnLayer& L : c->layers) {
         void* ptrs[] = {L.w, L.bias, L.wb, L.mw, L.vw, L.mb, L.vb, L.gw, L.gb};
-        for (void* p : ptrs) if (p) cudaFree(p);
+        for (void* p : ptrs) if (p) rte_dev_free(p);
     }
-    if (c->loss_host) cudaFreeHost(c->loss_host);
+    if (c->loss_host) rte_host_free(c->loss_host);
     delete c;
     return RTE_OK;
 }
@@ -552,11 +552,11 @@ extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth
         L.cin = l == 0 ? cin : width;
         L.cout = l == depth - 1 ? cout : width;
         const long nw = 9L * L.cin * L.cout;
-        bool ok = cudaMalloc((void**)&L.w, nw * 4) == cudaSuccess && cudaMalloc((void**)&L.wb, nw * 2) == cudaSuccess &&
-                  cudaMalloc((void**)&L.mw, nw * 4) == cudaSuccess && cudaMalloc((void**)&L.vw, nw * 4) == cudaSuccess &&
-                  cudaMalloc((void**)&L.gw, nw * 4) == cudaSuccess && cudaMalloc((void**)&L.bias, L.cout * 4) == cudaSuccess &&
-                  cudaMalloc((void**)&L.mb, L.cout * 4) == cudaSuccess && cudaMalloc((void**)&L.vb, L.cout * 4) == cudaSuccess &&
-                  cudaMalloc((void**)&L.gb, L.cout * 4) == cudaSuccess;
+        bool ok = rte_dev_malloc((void**)&L.w, nw * 4) == cudaSuccess && rte_dev_malloc((void**)&L.wb, nw * 2) == cudaSuccess &&
+                  rte_dev_malloc((void**)&L.mw, nw * 4) == cudaSuccess && rte_dev_malloc((void**)&L.vw, nw * 4) == cudaSuccess &&
+                  rte_dev_malloc((void**)&L.gw, nw * 4) == cudaSuccess && rte_dev_malloc((void**)&L.bias, L.cout * 4) == cudaSuccess &&
+                  rte_dev_malloc((void**)&L.mb, L.cout * 4) == cudaSuccess && rte_dev_malloc((void**)&L.vb, L.cout * 4) == cudaSuccess &&
+                  rte_dev_malloc((void**)&L.gb, L.cout * 4) == cudaSuccess;
         if (!ok) { cudaGetLastError(); rte_cnn_destroy(c); return RTE_ENOMEM; }
         // He-uniform init; the last layer starts small so the first guess is ~b
         const float a = (l == depth - 1 ? 0.1f : 1.0f) * sqrtf(6.f / (9.f * L.cin));
@@ -569,7 +569,7 @@ extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth
         cudaMemsetAsync(L.vb, 0, L.cout * 4, s);
         rte_count_launches(2);
     }
-    if (cudaMallocHost((void**)&c->loss_host, 1024 * sizeof(float)) != cudaSuccess) {
+    if (rte_host_malloc((void**)&c->loss_host, 1024 * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         rte_cnn_destroy(c);
         return RTE_ENOMEM;
@@ -799,8 +799,8 @@ extern "C" rte_status rte_guess_targets(rte_plan p, int cout, const double* f_de
 }
 
 // b_out: caller buffer for b = K~ g (FP64 mode field), computed here
-extern "C" rte_status rte_guess_apply(rte_cnn c, rte_plan p, const double* f_dev, double* b_out_dev, void* X_scratch_dev,
-                                      void* u0_dev, void* stream) {
+extern "C" rte_status rte_cnn_guess_apply(rte_cnn c, rte_plan p, const double* f_dev, double* b_out_dev,
+                                          void* X_scratch_dev, void* u0_dev, void* stream) {
     if (!c || !p || p->dim != 2 || !f_dev || !b_out_dev || !X_scratch_dev || !u0_dev || 2 * p->L + 1 > c->cout)
         return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -816,4 +816,74 @@ extern "C" rte_status rte_guess_apply(rte_cnn c, rte_plan p, const double* f_dev
     rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rte_guess: a trained network loaded from its weights file, with its own
+// scratch (features and b = K~ g), sized on first use for a plan's grid
+// ---------------------------------------------------------------------------
+struct rte_guess_s {
+    rte_cnn net = nullptr;
+    void* X = nullptr;     // bf16 [n][n][cin]
+    double* b = nullptr;   // FP64 mode field [L+1][n][n] complex
+    size_t X_bytes = 0, b_bytes = 0;
+};
+
+extern "C" rte_status rte_guess_destroy(rte_guess g) {
+    if (!g) return RTE_OK;
+    if (g->X || g->b) cudaDeviceSynchronize();
+    if (g->X) rte_dev_free(g->X);
+    if (g->b) rte_dev_free(g->b);
+    rte_status st = rte_cnn_destroy(g->net);
+    delete g;
+    return st;
+}
+
+extern "C" rte_status rte_guess_load(rte_guess* out, const char* weights_path) {
+    if (!out || !weights_path) return RTE_EINVAL;
+    *out = nullptr;
+    FILE* f = fopen(weights_path, "rb");
+    if (!f) return rte_fail(RTE_EINVAL, "rte_guess_load: cannot open the file");
+    char magic[8];
+    int hdr[4];
+    const bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kCnnMagic, 8) == 0 && fread(hdr, sizeof(int), 4, f) == 4;
+    fclose(f);
+    if (!ok) return rte_fail(RTE_EINVAL, "rte_guess_load: not a network weights file");
+    rte_guess g = new rte_guess_s();
+    rte_status st = rte_cnn_create(&g->net, hdr[0], hdr[1], hdr[2], hdr[3], 0, nullptr);
+    if (st == RTE_OK) st = rte_cnn_load(g->net, weights_path, nullptr);
+    if (st == RTE_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = rte_cuda_fail(cudaGetLastError(), "rte_guess_load");
+    if (st != RTE_OK) {
+        rte_guess_destroy(g);
+        return st;
+    }
+    *out = g;
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_guess_apply(rte_guess g, rte_plan p, const double* f_dev, void* u0_dev, void* stream) {
+    if (!g || !p || p->dim != 2 || !f_dev || !u0_dev) return RTE_EINVAL;
+    if (2 * p->L + 5 > g->net->cin || 2 * p->L + 1 > g->net->cout) return RTE_EINVAL;
+    const size_t xb = (size_t)p->n * p->n * g->net->cin * sizeof(bf16);
+    const size_t bb = (size_t)p->nr * sizeof(double);
+    if (xb > g->X_bytes || bb > g->b_bytes) {
+        // grow the scratch (synchronises the device: earlier calls may still use it)
+        cudaDeviceSynchronize();
+        if (xb > g->X_bytes) {
+            if (g->X) rte_dev_free(g->X);
+            g->X = nullptr;
+            g->X_bytes = 0;
+            if (rte_dev_malloc(&g->X, xb) != cudaSuccess) return rte_cuda_fail(cudaErrorMemoryAllocation, "rte_guess_apply");
+            g->X_bytes = xb;
+        }
+        if (bb > g->b_bytes) {
+            if (g->b) rte_dev_free(g->b);
+            g->b = nullptr;
+            g->b_bytes = 0;
+            if (rte_dev_malloc((void**)&g->b, bb) != cudaSuccess)
+                return rte_cuda_fail(cudaErrorMemoryAllocation, "rte_guess_apply");
+            g->b_bytes = bb;
+        }
+    }
+    return rte_cnn_guess_apply(g->net, p, f_dev, g->b, g->X, u0_dev, stream);
 }

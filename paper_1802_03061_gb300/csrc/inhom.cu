@@ -265,10 +265,10 @@ static size_t inhom_smem(int n, size_t el) {
 
 extern "C" rte_status rte_inhom_destroy(rte_inhom op) {
     if (!op) return RTE_OK;
-    if (op->mu64) cudaFree(op->mu64);
-    if (op->mu32) cudaFree(op->mu32);
-    if (op->diag64) cudaFree(op->diag64);
-    if (op->diag32) cudaFree(op->diag32);
+    if (op->mu64) rte_dev_free(op->mu64);
+    if (op->mu32) rte_dev_free(op->mu32);
+    if (op->diag64) rte_dev_free(op->diag64);
+    if (op->diag32) rte_dev_free(op->diag32);
     delete op;
     return RTE_OK;
 }
@@ -295,10 +295,10 @@ extern "C" rte_status rte_inhom_create(rte_inhom* out, int n, double h, const do
     gauss_legendre(15, g15.x, g15.w);
     std::vector<float> m32(N);
     for (long k = 0; k < N; ++k) m32[k] = (float)mu_t_host[k];
-    if (cudaMalloc((void**)&op->mu64, N * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&op->mu32, N * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&op->diag64, N * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&op->diag32, N * sizeof(float)) != cudaSuccess) {
+    if (rte_dev_malloc((void**)&op->mu64, N * sizeof(double)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->mu32, N * sizeof(float)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->diag64, N * sizeof(double)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->diag32, N * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         rte_inhom_destroy(op);
         return rte_fail(RTE_ENOMEM, "rte_inhom_create");

@@ -10,6 +10,17 @@
 rte_status rte_cuda_fail(cudaError_t e, const char* what);
 // records msg as the last error text and returns st
 rte_status rte_fail(rte_status st, const char* msg);
+// allocation wrappers (rte_api.cu): cudaMalloc / cudaMallocAsync /
+// cudaMallocHost and their frees, with a live-allocation count and the
+// simulated failures of rte_debug_fail_alloc
+cudaError_t rte_dev_malloc(void** p, size_t bytes);
+cudaError_t rte_dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
+cudaError_t rte_host_malloc(void** p, size_t bytes);
+cudaError_t rte_dev_free(void* p);
+cudaError_t rte_dev_free_async(void* p, cudaStream_t s);
+cudaError_t rte_host_free(void* p);
+template <typename T> inline cudaError_t rte_dev_malloc(T** p, size_t bytes) { return rte_dev_malloc((void**)p, bytes); }
+template <typename T> inline cudaError_t rte_host_malloc(T** p, size_t bytes) { return rte_host_malloc((void**)p, bytes); }
 // host-side count of kernel launches issued by the library (graph replays
 // add the kernel nodes they contain)
 void rte_count_launches(long k);

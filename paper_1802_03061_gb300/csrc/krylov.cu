@@ -878,17 +878,17 @@ static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream
     G.m = m;
     if (ws.m != m || !ws.V) {
         krylov_free_ws(ws);
-        if (cudaMalloc(&ws.V, (size_t)(m + 2) * p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
-        if (cudaMalloc(&ws.w, (size_t)p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
-        if (cudaMalloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(p->nr) * sizeof(double)) != cudaSuccess) {
+        if (rte_dev_malloc(&ws.V, (size_t)(m + 2) * p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (rte_dev_malloc(&ws.w, (size_t)p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (rte_dev_malloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(p->nr) * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return RTE_ENOMEM;
         }
-        if (cudaMalloc((void**)&ws.st, sizeof(GmresDev)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (rte_dev_malloc((void**)&ws.st, sizeof(GmresDev)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
         RTE_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(GmresDev), s));
         ws.m = m;
     }
-    if (pc && !ws.Z && cudaMalloc(&ws.Z, (size_t)(m + 1) * p->nr * sizeof(T)) != cudaSuccess) {
+    if (pc && !ws.Z && rte_dev_malloc(&ws.Z, (size_t)(m + 1) * p->nr * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return RTE_ENOMEM;
     }
@@ -1569,11 +1569,11 @@ rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStr
 }
 
 void krylov_free_ws(KrylovWs& ws) {
-    if (ws.V) cudaFree(ws.V);
-    if (ws.w) cudaFree(ws.w);
-    if (ws.part) cudaFree(ws.part);
-    if (ws.st) cudaFree(ws.st);
-    if (ws.Z) cudaFree(ws.Z);
+    if (ws.V) rte_dev_free(ws.V);
+    if (ws.w) rte_dev_free(ws.w);
+    if (ws.part) rte_dev_free(ws.part);
+    if (ws.st) rte_dev_free(ws.st);
+    if (ws.Z) rte_dev_free(ws.Z);
     ws = KrylovWs();
 }
 

@@ -8,8 +8,14 @@
 // spectra -- plus the pass intermediates in one fixed static device array,
 // then runs the same FP64 passes as rte_apply_K.
 //
-// The scratch is a file-scope __device__ array of RTE_NOALLOC_BYTES bytes
-// that every GPU which loads this library holds until the process exits.
+// The scratch is a file-scope __device__ array of RTE_NOALLOC_BYTES bytes.
+// This translation unit is its own CUDA module (the library is built without
+// relocatable device code), and under the runtime's default lazy module
+// loading that module -- and with it the array's device memory -- is loaded
+// on a device at the first cudaGetSymbolAddress below, i.e. during the first
+// call on that device; from then on the device holds the array until the
+// process exits.  Callers therefore make their first call where taking that
+// memory is allowed (start-up) and before any stream capture.
 // All calls share it: two calls whose work overlaps on the GPU (different
 // streams, or different host threads) race on it and must be serialised by
 // the caller.  Every call writes each scratch byte it reads before reading

@@ -599,18 +599,18 @@ rte_status plan_precond_build(rte_plan p, cudaStream_t s) {
     if (p->pc_ready) return RTE_OK;
     if (!plan_precond_supported(p)) return RTE_EUNSUPPORTED;
     cudaError_t e = cudaSuccess;
-    if (!p->pv1 && cudaMalloc((void**)&p->pv1, p->nr * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond buffer");
-    if (!p->pv2 && cudaMalloc((void**)&p->pv2, p->nr * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond buffer");
+    if (!p->pv1 && rte_dev_malloc((void**)&p->pv1, p->nr * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond buffer");
+    if (!p->pv2 && rte_dev_malloc((void**)&p->pv2, p->nr * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond buffer");
     if (p->dim == 3) {
         const long tot = (long)p->H * p->H * p->H;
-        if (cudaMalloc((void**)&p->S3p, tot * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond spectrum");
+        if (rte_dev_malloc((void**)&p->S3p, tot * sizeof(float)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond spectrum");
         const double Q3 = (double)p->Q * p->Q * p->Q;
         k_build_pc3d<<<1024, 256, 0, s>>>(p->S3_64, p->S3p, tot, p->mu_s, Q3);
         e = cudaGetLastError();
     } else {
         p->pc_nl = 2 * pc_lmax(p) + 1;
         const long tot = (long)p->H * pc_row(p->Q) * p->nch * p->pc_nl;
-        if (cudaMalloc((void**)&p->Pp, tot * sizeof(__nv_bfloat16)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond matrices");
+        if (rte_dev_malloc((void**)&p->Pp, tot * sizeof(__nv_bfloat16)) != cudaSuccess) return rte_fail(RTE_ENOMEM, "precond matrices");
         if ((e = cudaMemsetAsync(p->Pp, 0, tot * sizeof(__nv_bfloat16), s)) != cudaSuccess)
             return rte_cuda_fail(e, "plan_precond_build");
         const RowParams rp = pc_rowparams(p, false);

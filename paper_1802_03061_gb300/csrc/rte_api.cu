@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.h"
 
 static thread_local char g_last_error[256] = "";
@@ -20,6 +22,77 @@ rte_status rte_fail(rte_status st, const char* msg) {
 }
 
 extern "C" const char* rte_last_error(void) { return g_last_error; }
+
+// ---------------------------------------------------------------------------
+// Every device and pinned-host allocation of the library goes through these
+// wrappers: they count the live allocations and, for tests of the error
+// paths, can make the k-th allocation fail as if the device were full
+// (rte_debug_fail_alloc).  A simulated failure touches no CUDA state.
+// ---------------------------------------------------------------------------
+static std::atomic<long> g_alloc_seen{0}, g_alloc_fail_at{0}, g_live_dev{0}, g_live_host{0};
+
+static bool alloc_injected_failure() {
+    const long k = ++g_alloc_seen;
+    const long at = g_alloc_fail_at.load();
+    return at > 0 && k == at;
+}
+
+cudaError_t rte_dev_malloc(void** p, size_t bytes) {
+    if (alloc_injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_dev;
+    return e;
+}
+
+cudaError_t rte_dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    if (alloc_injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) ++g_live_dev;
+    return e;
+}
+
+cudaError_t rte_host_malloc(void** p, size_t bytes) {
+    if (alloc_injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) ++g_live_host;
+    return e;
+}
+
+cudaError_t rte_dev_free(void* p) {
+    if (!p) return cudaSuccess;
+    --g_live_dev;
+    return cudaFree(p);
+}
+
+cudaError_t rte_dev_free_async(void* p, cudaStream_t s) {
+    if (!p) return cudaSuccess;
+    --g_live_dev;
+    return cudaFreeAsync(p, s);
+}
+
+cudaError_t rte_host_free(void* p) {
+    if (!p) return cudaSuccess;
+    --g_live_host;
+    return cudaFreeHost(p);
+}
+
+extern "C" rte_status rte_debug_fail_alloc(long k, long* seen_out, long* live_dev_out, long* live_host_out) {
+    if (seen_out) *seen_out = g_alloc_seen.load();
+    if (live_dev_out) *live_dev_out = g_live_dev.load();
+    if (live_host_out) *live_host_out = g_live_host.load();
+    g_alloc_seen = 0;
+    g_alloc_fail_at = k > 0 ? k : 0;
+    return RTE_OK;
+}
 
 static long long g_launches = 0;
 void rte_count_launches(long k) { __atomic_add_fetch(&g_launches, (long long)k, __ATOMIC_RELAXED); }
@@ -64,7 +137,7 @@ static void fill_defaults(rte_opts* o) {
 }
 
 template <typename P> static rte_status dalloc(P** p, size_t bytes) {
-    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+    if (rte_dev_malloc((void**)p, bytes) != cudaSuccess) {
         cudaGetLastError();
         snprintf(g_last_error, sizeof(g_last_error), "cudaMalloc(%zu) failed", bytes);
         return RTE_ENOMEM;
@@ -114,8 +187,8 @@ extern "C" rte_status rte_destroy(rte_plan p) {
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
                     p->d32, p->dscal, p->part64, p->f_dev, p->u_dev, p->ref};
     for (void* b : bufs)
-        if (b) cudaFree(b);
-    if (p->hst) cudaFreeHost(p->hst);
+        if (b) rte_dev_free(b);
+    if (p->hst) rte_host_free(p->hst);
     delete p;
     return RTE_OK;
 }
@@ -228,7 +301,7 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     TRY(dalloc(&p->f_dev, p->ncell * sizeof(double)));
     TRY(dalloc(&p->u_dev, p->nr * sizeof(double)));
     TRY(dalloc((char**)&p->ref, refdev_size()));
-    if (cudaMallocHost((void**)&p->hst, 64 * sizeof(double)) != cudaSuccess) {
+    if (rte_host_malloc((void**)&p->hst, 64 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         st = RTE_ENOMEM;
         goto fail;

@@ -265,7 +265,7 @@ rte_status plan_build_spectra(rte_plan p, cudaStream_t s) {
         RTE_CUDA_TRY(cudaGetLastError());
         const long P = (long)Q * Q;
         double2* G = nullptr;
-        RTE_CUDA_TRY(cudaMallocAsync((void**)&G, (size_t)nm * P * sizeof(double2), s));
+        RTE_CUDA_TRY(rte_dev_malloc_async((void**)&G, (size_t)nm * P * sizeof(double2), s));
         k_sample_2d<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(G, p->n, Q, 2 * p->L, p->h, p->mu_t, p->Dm);
         RTE_CUDA_TRY(cudaGetLastError());
         // rows (x direction): lines = (m, oy), contiguous
@@ -277,13 +277,13 @@ rte_status plan_build_spectra(rte_plan p, cudaStream_t s) {
         const long tot = (long)H * nm * Q;
         k_extract_2d<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, Q, H, nm, p->S64, p->S32, p->S16);
         RTE_CUDA_TRY(cudaGetLastError());
-        RTE_CUDA_TRY(cudaFreeAsync(G, s));
+        RTE_CUDA_TRY(rte_dev_free_async(G, s));
     } else {
         k_cell_weight_3d<<<1, 64, 0, s>>>(p->mu_t, p->h, p->Dm);
         RTE_CUDA_TRY(cudaGetLastError());
         const long P = (long)Q * Q * Q;
         double2* G = nullptr;
-        RTE_CUDA_TRY(cudaMallocAsync((void**)&G, (size_t)P * sizeof(double2), s));
+        RTE_CUDA_TRY(rte_dev_malloc_async((void**)&G, (size_t)P * sizeof(double2), s));
         k_sample_3d<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(G, p->n, Q, p->h, p->mu_t, p->Dm);
         RTE_CUDA_TRY(cudaGetLastError());
         const long Q2 = (long)Q * Q;
@@ -299,7 +299,7 @@ rte_status plan_build_spectra(rte_plan p, cudaStream_t s) {
         const long tot = (long)H * H * H;
         k_extract_3d<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, Q, H, p->S3_64, p->S3_32);
         RTE_CUDA_TRY(cudaGetLastError());
-        RTE_CUDA_TRY(cudaFreeAsync(G, s));
+        RTE_CUDA_TRY(rte_dev_free_async(G, s));
     }
     return RTE_OK;
 }

@@ -79,8 +79,8 @@ class GuessNet:
         b = plan.empty()
         u0 = plan.empty()
         Xs = torch.empty((n, n, self.cin), dtype=torch.bfloat16, device="cuda")
-        B.rte_guess_apply(self.handle, plan.handle, f_dev.data_ptr(), b.data_ptr(), Xs.data_ptr(), u0.data_ptr(),
-                          _stream_ptr(stream))
+        B.rte_cnn_guess_apply(self.handle, plan.handle, f_dev.data_ptr(), b.data_ptr(), Xs.data_ptr(),
+                              u0.data_ptr(), _stream_ptr(stream))
         return u0, b
 
     def state(self):

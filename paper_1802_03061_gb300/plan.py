@@ -203,9 +203,20 @@ class Batch:
     def solve(self, f_packed, u_packed=None, stream=None):
         if u_packed is None:
             u_packed = torch.zeros(self.u_off[-1], dtype=torch.float64, device="cuda")
-        st, stats, ms = B.rte_batch_solve(self.handle, self.count, f_packed.data_ptr(), u_packed.data_ptr(),
-                                          _stream_ptr(stream))
+        st, stats, ms = B.rte_batch_solve_packed(self.handle, self.count, f_packed.data_ptr(),
+                                                 u_packed.data_ptr(), _stream_ptr(stream))
         return u_packed, stats, ms
+
+    def solve_list(self, sources, solutions=None, stream=None):
+        """One device tensor per instance: sources[i] (n_i, n_i) float64, the
+        solutions complex128 (L_i+1, n_i, n_i) (allocated when None)."""
+        fs = [torch.as_tensor(f).to(device="cuda", dtype=torch.float64).contiguous() for f in sources]
+        if solutions is None:
+            solutions = [torch.zeros((len(d["sigma_hat"]), int(d["n"]), int(d["n"])), dtype=torch.complex128,
+                                     device="cuda") for d in self.instances]
+        st, stats = B.rte_batch_solve(self.handle, [f.data_ptr() for f in fs], [u.data_ptr() for u in solutions],
+                                      _stream_ptr(stream))
+        return solutions, stats
 
     def close(self):
         if getattr(self, "handle", None):

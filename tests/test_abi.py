@@ -19,10 +19,34 @@ def _declared():
     return names
 
 
+# the calls of the survey's boundary (plan, operators, solve, batch, learned guess)
+BOUNDARY = ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_rhs", "rte_solve", "rte_destroy", "rte_status_str",
+            "rte_batch_create", "rte_batch_solve", "rte_guess_load", "rte_guess_apply")
+
+
 def test_header_declares_the_boundary_calls():
     names = _declared()
-    for must in ("rte_plan_create", "rte_apply_K", "rte_solve", "rte_destroy", "rte_rhs"):
+    for must in BOUNDARY:
         assert must in names
+
+
+def test_boundary_calls_are_exported():
+    from paper_1802_03061_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    assert all(hasattr(lib, n) for n in BOUNDARY)
+
+
+def test_guess_load_rejects_a_missing_or_foreign_file_without_a_gpu(tmp_path):
+    """rte_guess_load reads and checks the file header before any device call."""
+    from paper_1802_03061_gb300 import _binding as B
+    with pytest.raises(B.RteError) as ei:
+        B.rte_guess_load(str(tmp_path / "missing.bin"))
+    assert ei.value.status == B.RTE_EINVAL
+    bad = tmp_path / "foreign.bin"
+    bad.write_bytes(b"NOTAWEIGHTSFILE!" * 4)
+    with pytest.raises(B.RteError) as ei:
+        B.rte_guess_load(str(bad))
+    assert ei.value.status == B.RTE_EINVAL
 
 
 def test_library_loads_and_exports_all_symbols():
