@@ -725,6 +725,94 @@ def run_iso2d64(args):
     print(json.dumps(line))
 
 
+def run_modemix(args):
+    """Mode coupling by FFTs along the mode axis against the direct mix: the
+    FP32 K application on 256 x 256 cells for L = 1..8 with both couplings
+    (the crossover), and with the mode-axis FFT for L = 12..64, where the
+    direct mix is not built.  A step is one FP32 K application at L = 32
+    (65 real channels, P = 144), CUDA events over back-to-back launches."""
+    import torch
+
+    from paper_1802_03061_gb300 import Plan
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    n = 256
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    def pass_ms(L, mix, reps=20):
+        p = Plan(n, mu_t=10.0, mu_s=9.0, sigma_hat=[0.6 ** k for k in range(L + 1)], prec="mixed_fp32",
+                 mode_mix=mix)
+        ms = B.rte_time_passes(p.handle, 1, reps, sp)
+        Q = p.Q
+        p.close()
+        return ms, Q
+
+    table = []
+    for L in (1, 2, 4, 6, 8):
+        d, Q = pass_ms(L, "direct")
+        f, _ = pass_ms(L, "fft")
+        table.append({"L": L, "Q": Q, "direct_ms": sum(d), "fft_ms": sum(f), "direct_col_ms": d[1],
+                      "fft_col_ms": f[1]})
+    for L in (12, 16, 24, 32, 48, 64):
+        f, Q = pass_ms(L, "fft", reps=10)
+        table.append({"L": L, "Q": Q, "direct_ms": None, "fft_ms": sum(f), "fft_col_ms": f[1]})
+    # the line: L = 32, FP32 K application through the public call
+    L = 32
+    p = Plan(n, mu_t=10.0, mu_s=9.0, sigma_hat=[0.6 ** k for k in range(L + 1)], prec="mixed_fp32")
+    x = p.empty(fp32=True).normal_()
+    y = p.empty(fp32=True)
+    for _ in range(args.warmup):
+        p.apply_K32(x, y)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = B.rte_kernel_launches()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        p.apply_K32(x, y)
+    e1.record(stream)
+    e1.synchronize()
+    launches = B.rte_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    hbm, src = peaks()
+    nch, Q = 2 * L + 1, p.Q
+    P = 4 * L + 1
+    while not _smooth23(P):
+        P += 1
+    alg = 2 * n * n * nch * 4 + nch * (Q * Q // 2) * 8
+    line = {"metric": "FP32 K applications/s, 256^2, L = 32 (mode-axis FFT coupling)", "value": 1e3 / ms,
+            "unit": "applications/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "modemix_256: 256x256 cells, HG g = 0.6, mu_t = 10, mu_s = 9; FP32 K application",
+                       "P": P, "crossover": table,
+                       "l2": "warm: back-to-back launches (the mode-axis spectra, %d MB, exceed L2)"
+                             % ((Q // 2 + 1) * Q * P * 8 >> 20)},
+            "roofline": {"bound": "hbm", "kernel": "K application with the mode-axis FFT coupling (5 launches)",
+                         "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": src,
+                         "algorithmic_bytes_per_launch": alg,
+                         "note": "B_alg counts the (2L+1) half-plane spectra of the method; the mode-axis "
+                                 "representation stores P = %d per frequency" % P},
+            "gpu_launches": int(launches), "clocks": clk}
+    p.close()
+    print(json.dumps(line))
+
+
+def _smooth23(q):
+    while q % 2 == 0:
+        q //= 2
+    while q % 3 == 0:
+        q //= 3
+    return q == 1
+
+
 def run_learned(args):
     """The learned-initial-guess workload: 2D 256^2, L = 4, HG g in [0, 0.7],
     mu_t log-U[1, 50], mu_s/mu_t U[0.5, 0.99], 1-6 Gaussians.  Training data
@@ -991,7 +1079,8 @@ def main():
     ap.add_argument("--inhom-n", type=int, default=256, help="inhom workload: cells per side")
     ap.add_argument("--aniso-n", type=int, default=64, help="aniso3d workload: cells per side")
     ap.add_argument("--workload", default="hg2d_transport",
-                    choices=["hg2d_transport", "iso2d64", "batch512", "iso3d", "learned", "inhom", "aniso3d"])
+                    choices=["hg2d_transport", "iso2d64", "batch512", "iso3d", "learned", "inhom", "aniso3d",
+                             "modemix"])
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=4, help="learned workload: training epochs")
     ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
@@ -1009,6 +1098,8 @@ def main():
         return run_inhom(args)
     if args.workload == "iso2d64":
         return run_iso2d64(args)
+    if args.workload == "modemix":
+        return run_modemix(args)
     if args.workload == "aniso3d":
         return run_aniso3d(args)
     if args.workload == "batch512":

@@ -36,7 +36,7 @@
  *
  * Errors: every call returns an rte_status; nothing else crosses the ABI.
  * RTE_EINVAL for bad arguments (null pointers, n < 1, h <= 0, mu_t < 0,
- * mu_s < 0, mu_s > mu_t (assumption (C2), Sec. 2.2), L < 0 or L > 8,
+ * mu_s < 0, mu_s > mu_t (assumption (C2), Sec. 2.2), L < 0 or L > 64,
  * |sigma_hat_0 - 1| > 1e-12 (the scattering kernel averages to one, Sec. 1),
  * |sigma_hat_k| > 1 (needed by the contraction argument, Sec. 3.2)),
  * RTE_EUNSUPPORTED for 3D with L > 0, RTE_ENOMEM when a device allocation
@@ -104,6 +104,12 @@ typedef struct {
                           themselves); 0 = the smallest lmax with (mu_s/mu_t) max_{k>lmax}
                           |sigma_hat_k| <= 0.03, >= L = all modes.  Read when the preconditioner
                           is built. */
+    int mode_mix;      /* [0] 2D: how the column pass forms the mode coupling sum_k' S_{k-k'} w_k'
+                          per frequency (the kernel depends only on k - k', Sec. 3.3.1):
+                          0 = the direct (2L+1)^2 sum for L <= 8 and a circular convolution along
+                          the mode axis by FFTs of length P >= 4L+1 above; 1 = direct (L <= 8 only,
+                          else RTE_EINVAL); 2 = the mode-axis FFT at every L.  Read at plan
+                          creation; plans with the mode-axis FFT have no preconditioner. */
 } rte_opts;
 
 typedef struct {

@@ -32,7 +32,7 @@ class rte_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_guess", ctypes.c_int),
                 ("q_policy", ctypes.c_int), ("inner_solver", ctypes.c_int), ("precond", ctypes.c_int),
-                ("precond_lmax", ctypes.c_int)]
+                ("precond_lmax", ctypes.c_int), ("mode_mix", ctypes.c_int)]
 
 
 class rte_stats(ctypes.Structure):
@@ -163,12 +163,15 @@ def _check(st, where, allow=()):
 INNER = {"gmres": 0, "minres": 1}
 
 
+MODE_MIX = {"auto": 0, "direct": 1, "fft": 2}
+
+
 def make_opts(prec="fp64", tol=1e-8, restart=40, maxit=2000, inner_tol=1e-4, use_guess=0, q_policy=0,
-              inner_solver="gmres", precond=0, precond_lmax=0):
+              inner_solver="gmres", precond=0, precond_lmax=0, mode_mix=0):
     return rte_opts(PREC[prec] if isinstance(prec, str) else int(prec), tol, restart, maxit, inner_tol,
                     int(use_guess), int(q_policy),
                     INNER[inner_solver] if isinstance(inner_solver, str) else int(inner_solver), int(precond),
-                    int(precond_lmax))
+                    int(precond_lmax), MODE_MIX[mode_mix] if isinstance(mode_mix, str) else int(mode_mix))
 
 
 def rte_plan_create(dim, n, h, mu_t, mu_s, L, sigma_hat, opts=None, stream=0):

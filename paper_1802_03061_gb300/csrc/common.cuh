@@ -6,7 +6,8 @@
 
 #include "ff.cuh"
 
-#define RTE_MAX_L 8                      // largest angular truncation |k| <= L
+#define RTE_MAX_L 64                     // largest angular truncation |k| <= L
+#define RTE_MAX_L_DIRECT 8               // largest L of the direct (compile-time) mode mix
 #define RTE_MAX_CH (2 * RTE_MAX_L + 1)   // real channels of a J-symmetric field
 #define RTE_MAX_STAGES 16
 

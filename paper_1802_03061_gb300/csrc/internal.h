@@ -93,6 +93,19 @@ struct rte_plan_s {
     float* pv2 = nullptr;
     bool pc_ready = false;
     int pc_nl = 0;                   // 2D: channels the preconditioner inverts (2 lmax + 1)
+    // mode coupling by a circular convolution along the mode axis (2D,
+    // rte_opts.mode_mix): length P >= 4L+1, twiddles exp(-2 pi i t/P) and
+    // per frequency the P-point DFT of S_m (m = -2L..2L at m mod P), scaled
+    // by 1/P: [H*Q][P] complex in FP64, FP32 and float-float
+    bool mix_fft = false;
+    int Pm = 0;
+    FftSched sched_m;
+    double2* twm64 = nullptr;
+    float2* twm32 = nullptr;
+    ffc* twmff = nullptr;
+    double2* Sm64 = nullptr;
+    float2* Sm32 = nullptr;
+    ffc* Smff = nullptr;
     // cell weights D_m, m = 0..2L (2D) or D (3D), computed on the device
     double* Dm = nullptr;
     // pass intermediates: 2D [nch][H][n] complex; 3D T1 [n][H][n], T2 [H][Q][n]
@@ -127,6 +140,9 @@ struct rte_plan_s {
 
 // spectra.cu
 rte_status plan_build_spectra(rte_plan p, cudaStream_t s);
+// the mode-axis DFTs of the spectra (p->mix_fft plans), from p->S64
+rte_status plan_build_modefft(rte_plan p, cudaStream_t s);
+int choose_P(int L);
 rte_status fft_lines_host(double2* data, const FftSched& sc, const double2* tw, long nlines, long nA, long sA,
                           long sB, long sE, cudaStream_t s);
 __global__ void k_twiddles(double2* tw64, float2* tw32, int Q);

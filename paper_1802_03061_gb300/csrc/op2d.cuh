@@ -823,6 +823,83 @@ __global__ void __launch_bounds__(256) k_col_fft_split(T* __restrict__ Tb, T* __
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mode coupling by FFTs along the mode axis (large L).  The kernel of the pair
+// (k, k') depends only on k - k' (Sec. 3.3.1 remark), so per frequency xi
+//   V_k = sum_{k'=-L..L} S_{k-k'} W_k',   k = -L..L,
+// is a linear convolution in the mode index.  With the inputs W_k' placed at
+// k' mod P and S_m at m mod P (m = -2L..2L), a circular convolution of length
+// P >= 4L+1 gives exactly these V_k (all needed differences k - k' are
+// distinct mod P): V = iDFT_P(DFT_P(S) DFT_P(W)), with DFT_P(S)/P precomputed
+// per frequency (Sm).  The complex modes come from the real channels' column
+// spectra A_k (Re w_k), B_k (Im w_k): W_{+-k} = A_k +- i B_k, and the real
+// output channels are Re v_k: (V_k + V_-k)/2, Im v_k: (V_k - V_-k)/(2i).
+// Cost per frequency O(P log P) against (2L+1)^2 for the direct mix.
+// One block handles MF_LINES consecutive frequencies id = xi_x Q + xi_y of Ts
+// ([nch][H][Q], channel stride H Q), in place.
+// ---------------------------------------------------------------------------
+#define MF_LINES 16
+
+struct ModeFftParams {
+    int L, P, nin;   // nin: input channels (nch, or 1 for the right-hand side)
+    long nfreq;      // H * Q
+    FftSched sc;     // schedule of length P
+};
+
+template <typename T> __device__ __forceinline__ T half_c(T v) { return cscale(v, (typename real_of<T>::R)0.5); }
+
+template <typename T, typename TS>
+__global__ void __launch_bounds__(256) k_mix_modefft(T* __restrict__ Ts, const TS* __restrict__ Sm,
+                                                     const T* __restrict__ twm, ModeFftParams p) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int P = p.P, L = p.L;
+    T* twl = sm;
+    T* buf = sm + P;
+    T* tmp = buf + MF_LINES * P;
+    load_twiddles(twl, twm, P);
+    const long f0 = (long)blockIdx.x * MF_LINES;
+    const long rem = p.nfreq - f0;
+    const int nf = rem < MF_LINES ? (int)rem : MF_LINES;
+    const long cs = p.nfreq;
+    for (int i = threadIdx.x; i < MF_LINES * P; i += blockDim.x) buf[i] = mk<T>(0, 0);
+    __syncthreads();
+    // gather W_{+-k} of each frequency (consecutive threads: consecutive frequencies)
+    const int kin = p.nin > 1 ? L : 0;
+    for (int i = threadIdx.x; i < (kin + 1) * MF_LINES; i += blockDim.x) {
+        const int k = i / MF_LINES, f = i - k * MF_LINES;
+        if (f >= nf) continue;
+        T* line = buf + f * P;
+        const long id = f0 + f;
+        if (k == 0) {
+            line[0] = Ts[id];
+        } else {
+            const T A = Ts[chA(k) * cs + id], B = Ts[chB(k) * cs + id];
+            line[k] = mk<T>(A.x - B.y, A.y + B.x);      // A + i B
+            line[P - k] = mk<T>(A.x + B.y, A.y - B.x);  // A - i B
+        }
+    }
+    __syncthreads();
+    T* r = fft_lines<-1>(buf, tmp, MF_LINES, P, p.sc, twl);
+    for (int i = threadIdx.x; i < nf * P; i += blockDim.x) r[i] = cmul(r[i], ld_spec(Sm, f0 * P + i, T()));
+    __syncthreads();
+    T* o = fft_lines<1>(r, r == buf ? tmp : buf, MF_LINES, P, p.sc, twl);
+    for (int i = threadIdx.x; i < (L + 1) * MF_LINES; i += blockDim.x) {
+        const int k = i / MF_LINES, f = i - k * MF_LINES;
+        if (f >= nf) continue;
+        const T* line = o + f * P;
+        const long id = f0 + f;
+        if (k == 0) {
+            Ts[id] = line[0];
+        } else {
+            const T vp = line[k], vm = line[P - k];
+            Ts[chA(k) * cs + id] = half_c(cadd(vp, vm));
+            const T d = half_c(csub(vp, vm));
+            Ts[chB(k) * cs + id] = mk<T>(d.y, -d.x);     // -i (V_k - V_-k)/2
+        }
+    }
+}
+
 // float-float mode mix.  The (2L+1)-channel state of a frequency (inputs and
 // spectra, 544 bytes at L = 8) does not fit in registers with useful
 // occupancy, so a block stages 32 frequencies in shared memory and its four

@@ -13,7 +13,8 @@ rte_status op2d_apply32(rte_plan p, const float* x, float* out, float a, float b
     const float2* xx = reinterpret_cast<const float2*>(x);
     const float2* zz = reinterpret_cast<const float2*>(z);
     float2* oo = reinterpret_cast<float2*>(out);
-    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC) return op2d_apply32_bf16(p, xx, oo, a, b, c, zz, s);
+    // plans with the mode-axis FFT coupling keep FP32 spectra only
+    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC && !p->mix_fft) return op2d_apply32_bf16(p, xx, oo, a, b, c, zz, s);
     float2* Tb = reinterpret_cast<float2*>(p->T32);
     float2* Ts = reinterpret_cast<float2*>(p->Tsplit32);
     cudaError_t e = op2d_run<float2, float2>(p, MIX_K, xx, nullptr, oo, a, b, c, zz, Tb, Ts, p->S32, p->tw32,
@@ -37,7 +38,8 @@ rte_status op2d_apply32_stage(rte_plan p, const float* x, float* out, float a, f
                               cudaStream_t s) {
     const float2* xx = reinterpret_cast<const float2*>(x);
     float2* oo = reinterpret_cast<float2*>(out);
-    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC) return op2d_apply32_bf16_stage(p, xx, oo, a, b, c, stage, s);
+    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC && !p->mix_fft)
+        return op2d_apply32_bf16_stage(p, xx, oo, a, b, c, stage, s);
     cudaError_t e = op2d_run<float2, float2, float2>(p, MIX_K, xx, nullptr, oo, a, b, c, nullptr, reinterpret_cast<float2*>(p->T32),
                                              reinterpret_cast<float2*>(p->Tsplit32), p->S32, p->tw32, p->col_split32,
                                              s, stage, p->S32p);
@@ -46,7 +48,7 @@ rte_status op2d_apply32_stage(rte_plan p, const float* x, float* out, float a, f
 }
 
 rte_status op2d_time32(rte_plan p, int reps, double* ms, cudaStream_t s) {
-    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC) return op2d_time32_bf16(p, reps, ms, s);
+    if (p->opts.prec == RTE_PREC_MIXED_BF16SPEC && !p->mix_fft) return op2d_time32_bf16(p, reps, ms, s);
     const float2* xx = reinterpret_cast<const float2*>(p->r32);
     float2* oo = reinterpret_cast<float2*>(p->d32);
     float2* Tb = reinterpret_cast<float2*>(p->T32);

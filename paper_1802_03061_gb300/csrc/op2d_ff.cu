@@ -43,9 +43,14 @@ __global__ void k_split_ff(const double* __restrict__ src, ff* __restrict__ dst,
 // plan time: float-float copies of the twiddles and spectra
 rte_status plan_split_ff(rte_plan p, cudaStream_t s) {
     k_split_ff2<<<64, 256, 0, s>>>(p->tw64, p->twff, p->Q);
-    if (p->dim == 2 && p->Sffp) k_split_ff2_slot<<<1024, 256, 0, s>>>(p->S64, p->Sffp, (long)p->H * p->nch, p->Q);
-    else if (p->dim == 2) k_split_ff2<<<1024, 256, 0, s>>>(p->S64, p->Sff, (long)p->H * p->nch * p->Q);
-    else k_split_ff<<<1024, 256, 0, s>>>(p->S3_64, p->S3ff, (long)p->H * p->H * p->H);
+    if (p->dim == 2) {
+        // plans with the mode-axis FFT coupling hold neither copy (their
+        // float-float spectra are the mode-axis DFTs, built with them)
+        if (p->Sffp) k_split_ff2_slot<<<1024, 256, 0, s>>>(p->S64, p->Sffp, (long)p->H * p->nch, p->Q);
+        else if (p->Sff) k_split_ff2<<<1024, 256, 0, s>>>(p->S64, p->Sff, (long)p->H * p->nch * p->Q);
+    } else {
+        k_split_ff<<<1024, 256, 0, s>>>(p->S3_64, p->S3ff, (long)p->H * p->H * p->H);
+    }
     rte_count_launches(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return rte_cuda_fail(e, "plan_split_ff");

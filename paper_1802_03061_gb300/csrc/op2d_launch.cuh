@@ -311,6 +311,44 @@ static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, cons
     return cudaGetLastError();
 }
 
+// the mode-axis FFT spectra and twiddles of a plan for compute type T
+static inline const float2* modefft_spec(const rte_plan p, float2*) { return p->Sm32; }
+static inline const double2* modefft_spec(const rte_plan p, double2*) { return p->Sm64; }
+static inline const ffc* modefft_spec(const rte_plan p, ffc*) { return p->Smff; }
+static inline const float2* modefft_tw(const rte_plan p, float2*) { return p->twm32; }
+static inline const double2* modefft_tw(const rte_plan p, double2*) { return p->twm64; }
+static inline const ffc* modefft_tw(const rte_plan p, ffc*) { return p->twmff; }
+
+// column pass with the mode-axis FFT coupling (p->mix_fft): column FFTs of
+// the input channels into Ts, k_mix_modefft in place, inverse column FFTs of
+// all channels back into Tb (3 launches)
+template <typename T>
+static cudaError_t col_modefft(rte_plan p, T* Tb, T* Ts, const T* tw, ColParams cp, cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_col_fft_split<T>)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_mix_modefft<T, T>)) != cudaSuccess) return e;
+        once = true;
+    }
+    cp.G = split_group<T>(p->nch, cp.Q);
+    const size_t smem = (size_t)(cp.Q + 2 * cp.G * cp.Q) * sizeof(T);
+    k_col_fft_split<T><<<cp.H, 256, smem, s>>>(Tb, Ts, tw, cp, 1, cp.nin);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ModeFftParams mp;
+    mp.L = p->L;
+    mp.P = p->Pm;
+    mp.nin = cp.nin;
+    mp.nfreq = (long)cp.H * cp.Q;
+    mp.sc = p->sched_m;
+    const size_t smm = (size_t)(p->Pm + 2 * MF_LINES * p->Pm) * sizeof(T);
+    k_mix_modefft<T, T><<<(unsigned)((mp.nfreq + MF_LINES - 1) / MF_LINES), 256, smm, s>>>(
+        Ts, modefft_spec(p, (T*)nullptr), modefft_tw(p, (T*)nullptr), mp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_col_fft_split<T><<<cp.H, 256, smem, s>>>(Tb, Ts, tw, cp, 0, p->nch);
+    return cudaGetLastError();
+}
+
 // out = a*x + b*(Op x) + c*z ; Op = K (MIX_K), K~ on the source f (MIX_RHS),
 // or K x + K~ f (MIX_KF)
 // stage: -1 all three passes; 0 row pass; 1 column pass; 2 inverse row pass
@@ -329,6 +367,10 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
     RowParams rp;
     rp.n = p->n; rp.Q = p->Q; rp.H = p->H; rp.L = p->L;
     rp.RB = rows_per_block<T>(p->Q);
+    // small grids: fewer rows per block until the row passes have a block per
+    // SM (the row FFTs, and the row pairs of mode 0, are the same for any even RB)
+    while (rp.RB > 2 && (long)((p->n + rp.RB - 1) / rp.RB) * (p->L + 1) < p->nsm) rp.RB = (rp.RB / 2) & ~1;
+    if (rp.RB < 2) rp.RB = 2;
     if (p->rb_force >= 2 && p->rb_force <= 16 && row_smem<T>(p->Q, p->rb_force & ~1) <= 200 * 1024)
         rp.RB = p->rb_force & ~1;
     rp.sc = p->sched;
@@ -367,8 +409,14 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
         cp.sc = p->sched;
         int launches = split ? 3 : 1;
         bool warp_path = false;
+        if (p->mix_fft) {
+            if ((e = col_modefft<T>(p, Tb, Ts, tw, cp, s)) != cudaSuccess) return e;
+            rte_count_launches(3);
+            warp_path = true;  // handled: skip the direct-mix paths below
+            launches = 0;
+        }
         if constexpr (sizeof(T) == sizeof(float2)) {
-            if (Sp && col_warp_ok(p->Q)) {
+            if (!warp_path && Sp && col_warp_ok(p->Q)) {
                 if ((e = dispatch_col_warp<TS>(p->L, (float2*)Tb, p->Tz32, Sp, (const float2*)tw, cp, s)) != cudaSuccess)
                     return e;
                 warp_path = true;
@@ -376,7 +424,7 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
             }
         }
         if constexpr (!allow_fused<T>::value) {
-            if (Sp && col_warp_ok(p->Q)) {
+            if (!warp_path && Sp && col_warp_ok(p->Q)) {
                 if ((e = colw_ff(p->L, Tb, Ts, Sp, tw, cp, s)) != cudaSuccess) return e;
                 warp_path = true;
                 launches = 3;

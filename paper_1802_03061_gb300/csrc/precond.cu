@@ -575,6 +575,7 @@ static RowParams pc_rowparams(rte_plan p, bool unit) {
 // 3D: every Q.  2D: the warp column pass (Q = 64..512, 32 * 2^j), else the
 // shared-memory pass while its columns fit in shared memory (Q <= 1024 at L = 8)
 bool plan_precond_supported(const rte_plan p) {
+    if (p->dim == 2 && p->mix_fft) return false;  // built on the direct-mix passes (L <= 8)
     if (p->dim == 3 || col_warp_ok(p->Q)) return true;
     return pc_fused_smem(p->nch, p->Q, col_group<float2>(p->nch, p->Q)) <= 200 * 1024;
 }

@@ -183,7 +183,7 @@ extern "C" rte_status rte_destroy(rte_plan p) {
     if (!p) return RTE_OK;
     cudaDeviceSynchronize();
     krylov_free(p);
-    void* bufs[] = {p->S3p, p->Pp, p->pv1, p->pv2, p->tw64, p->tw32, p->twff, p->Sff, p->Sffp, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->Tz32, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
+    void* bufs[] = {p->twm64, p->twm32, p->twmff, p->Sm64, p->Sm32, p->Smff, p->S3p, p->Pp, p->pv1, p->pv2, p->tw64, p->tw32, p->twff, p->Sff, p->Sffp, p->S3ff, p->S64, p->S32, p->S16, p->S32p, p->S16p, p->Tz32, p->S3_64, p->S3_32, p->Dm, p->T64, p->T32,
                     p->U64, p->U32, p->Tsplit, p->Tsplit32, p->b64, p->r64, p->x64, p->t64, p->r32,
                     p->d32, p->dscal, p->part64, p->f_dev, p->u_dev, p->ref};
     for (void* b : bufs)
@@ -214,6 +214,8 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     if (opts) o = *opts;
     fill_defaults(&o);
     if (o.prec < RTE_PREC_FP64 || o.prec > RTE_PREC_MIXED_BF16SPEC) return RTE_EINVAL;
+    if (o.mode_mix < 0 || o.mode_mix > 2) return RTE_EINVAL;
+    if (o.mode_mix == 1 && L > RTE_MAX_L_DIRECT) return RTE_EINVAL;
     int Q = choose_Q(n);
     if (o.q_policy > 0) {
         Q = o.q_policy;
@@ -233,6 +235,11 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
     for (int k = 0; k <= RTE_MAX_L; ++k) p->sigma_hat[k] = (k <= L && sigma_hat) ? sigma_hat[k] : (k == 0 ? 1.0 : 0.0);
     p->opts = o;
     make_sched(&p->sched, Q);
+    p->mix_fft = grid.dim == 2 && (o.mode_mix == 2 || (o.mode_mix == 0 && L > RTE_MAX_L_DIRECT));
+    if (p->mix_fft) {
+        p->Pm = choose_P(L);
+        make_sched(&p->sched_m, p->Pm);
+    }
     p->ncell = grid.dim == 2 ? (long)n * n : (long)n * n * n;
     p->nr = grid.dim == 2 ? 2L * (L + 1) * n * n : p->ncell;
     int dev = 0;
@@ -259,8 +266,18 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
         const size_t ns = (size_t)H * nch * Q;
         TRY(dalloc(&p->S64, ns * sizeof(double2)));
         TRY(dalloc(&p->S32, ns * sizeof(float2)));
-        TRY(dalloc(&p->S16, ns * sizeof(__nv_bfloat162)));
-        if (Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024) {
+        if (p->mix_fft) {
+            // the column passes use only the mode-axis DFTs of the spectra
+            const int P = p->Pm;
+            const size_t nf = (size_t)H * Q * P;
+            TRY(dalloc(&p->twm64, P * sizeof(double2)));
+            TRY(dalloc(&p->twm32, P * sizeof(float2)));
+            TRY(dalloc(&p->twmff, P * sizeof(ffc)));
+            TRY(dalloc(&p->Sm64, nf * sizeof(double2)));
+            TRY(dalloc(&p->Sm32, nf * sizeof(float2)));
+            TRY(dalloc(&p->Smff, nf * sizeof(ffc)));
+        } else if (Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024) {
+            TRY(dalloc(&p->S16, ns * sizeof(__nv_bfloat162)));
             TRY(dalloc(&p->S32p, ns * sizeof(float2)));
             TRY(dalloc(&p->S16p, ns * sizeof(__nv_bfloat162)));
             TRY(dalloc(&p->Sffp, ns * sizeof(ffc)));
@@ -268,6 +285,7 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
             // first residue's result waits here
             if (Q == 1024) TRY(dalloc(&p->Tz32, (size_t)nch * H * n * sizeof(float2)));
         } else {
+            TRY(dalloc(&p->S16, ns * sizeof(__nv_bfloat162)));
             TRY(dalloc(&p->Sff, ns * sizeof(ffc)));
         }
         const size_t nt = (size_t)nch * H * n;
@@ -277,7 +295,7 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
         p->col_split32 = (size_t)(Q + nch * Q + Q) * sizeof(float2) > 200 * 1024;
         // the float-float passes always take the split column path
         TRY(dalloc((double2**)&p->Tsplit, (size_t)nch * H * Q * sizeof(double2)));
-        if (p->col_split32) TRY(dalloc((float2**)&p->Tsplit32, (size_t)nch * H * Q * sizeof(float2)));
+        if (p->col_split32 || p->mix_fft) TRY(dalloc((float2**)&p->Tsplit32, (size_t)nch * H * Q * sizeof(float2)));
     } else {
         const size_t ns = (size_t)H * H * H;
         TRY(dalloc(&p->S3_64, ns * sizeof(double)));
@@ -307,6 +325,7 @@ extern "C" rte_status rte_plan_create(rte_plan* out, rte_grid grid, double h, do
         goto fail;
     }
     TRY(plan_build_spectra(p, s));
+    TRY(plan_build_modefft(p, s));
     if (grid.dim == 2) TRY(op2d_permute_spectra(p, s));
     TRY(plan_split_ff(p, s));
     // one application in each precision: validates the launch shapes and

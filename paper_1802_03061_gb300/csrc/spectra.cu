@@ -28,6 +28,15 @@ int choose_Q(int n) {
     return q;
 }
 
+// mode-axis FFT length: the smallest 2^a 3^b >= 4L + 1 (at least 2); every
+// difference k - k' in -2L..2L then has its own residue mod P
+int choose_P(int L) {
+    int q = 4 * L + 1;
+    if (q < 2) q = 2;
+    while (!smooth23(q)) ++q;
+    return q;
+}
+
 void make_sched(FftSched* s, int Q) {
     s->Q = Q;
     s->ns = 0;
@@ -60,36 +69,47 @@ __global__ void k_twiddles(double2* tw64, float2* tw32, int Q) {
 // R(phi) = (h/2)/max(|cos|,|sin|).  Eight smooth pieces between the corner
 // directions, 64-point Gauss-Legendre on each.  One block of 64 threads.
 __global__ void k_cell_weights_2d(double mu, double h, int mmax, double* D) {
-    __shared__ double acc[64][RTE_MAX_CH * 2 + 1];
+    __shared__ double acc[64];
     const int i = threadIdx.x;
     double x, w;
     gl_node(64, i, &x, &w);
-    double part[2 * RTE_MAX_CH + 1];
-    for (int m = 0; m <= mmax; ++m) part[m] = 0.0;
     const double a = 0.5 * h;
+    double c1[8], cm1[8], cm2[8], rad[8];
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
         const double phi = q * (M_PI / 4) + (x + 1.0) * (M_PI / 8);
         double s, c;
         sincos(phi, &s, &c);
         const double R = a / fmax(fabs(c), fabs(s));
-        const double rad = radial_factor(mu, R) * w * (M_PI / 8);
-        // cos(m phi) by the Chebyshev recurrence c_m = 2 cos(phi) c_{m-1} - c_{m-2}
-        double cm2 = 1.0, cm1 = c;
-        part[0] += rad;
-        if (mmax >= 1) part[1] += c * rad;
-        for (int m = 2; m <= mmax; ++m) {
-            const double cm = 2.0 * c * cm1 - cm2;
-            part[m] += cm * rad;
-            cm2 = cm1;
-            cm1 = cm;
-        }
+        rad[q] = radial_factor(mu, R) * w * (M_PI / 8);
+        c1[q] = c;
+        cm2[q] = 1.0;
+        cm1[q] = c;
     }
-    for (int m = 0; m <= mmax; ++m) acc[i][m] = part[m];
-    __syncthreads();
-    if (i <= mmax) {
-        double t = 0.0;
-        for (int j = 0; j < 64; ++j) t += acc[j][i];
-        D[i] = t / (2.0 * M_PI);
+    // cos(m phi) by the Chebyshev recurrence c_m = 2 cos(phi) c_{m-1} - c_{m-2};
+    // one block reduction per m (mmax up to 2 RTE_MAX_L)
+    for (int m = 0; m <= mmax; ++m) {
+        double part = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double cur;
+            if (m == 0) cur = 1.0;
+            else if (m == 1) cur = c1[q];
+            else {
+                cur = 2.0 * c1[q] * cm1[q] - cm2[q];
+                cm2[q] = cm1[q];
+                cm1[q] = cur;
+            }
+            part += cur * rad[q];
+        }
+        acc[i] = part;
+        __syncthreads();
+        if (i == 0) {
+            double t = 0.0;
+            for (int j = 0; j < 64; ++j) t += acc[j];
+            D[m] = t / (2.0 * M_PI);
+        }
+        __syncthreads();
     }
 }
 
@@ -240,7 +260,7 @@ __global__ void k_extract_2d(const double2* G, int Q, int H, int nm, double2* S6
     v.y *= sc;
     S64[idx] = v;
     S32[idx] = make_float2((float)v.x, (float)v.y);
-    S16[idx] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+    if (S16) S16[idx] = __floats2bfloat162_rn((float)v.x, (float)v.y);  // no BF16 copy for mode-FFT plans
 }
 
 // octant of the real even 3D spectrum: S3[kx][ky][kz] = Re G[kz][ky][kx] / Q^3
@@ -301,5 +321,76 @@ rte_status plan_build_spectra(rte_plan p, cudaStream_t s) {
         RTE_CUDA_TRY(cudaGetLastError());
         RTE_CUDA_TRY(rte_dev_free_async(G, s));
     }
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mode-axis DFTs of the spectra (plans that couple the modes by FFTs along the
+// mode axis): per frequency id = xi_x Q + xi_y the line s[m mod P] = S_m(xi),
+// m = -2L..2L, with S_{-m} = (-1)^m conj(S_m) (the kernel is real and even),
+// forward DFT of length P, scaled by 1/P; FP64 into Sm64, rounded copies in
+// Sm32 and float-float in Smff.  16 frequencies per block.
+// ---------------------------------------------------------------------------
+#define MFS_LINES 16
+__global__ void __launch_bounds__(256) k_modefft_spectra(const double2* __restrict__ S64, int H, int Q, int L, int P,
+                                                         FftSched sc, const double2* __restrict__ twm,
+                                                         double2* __restrict__ Sm64, float2* __restrict__ Sm32,
+                                                         ffc* __restrict__ Smff) {
+    extern __shared__ unsigned char smraw[];
+    double2* sm = reinterpret_cast<double2*>(smraw);
+    double2* twl = sm;
+    double2* buf = sm + P;
+    double2* tmp = buf + MFS_LINES * P;
+    load_twiddles(twl, twm, P);
+    const long nfreq = (long)H * Q;
+    const long f0 = (long)blockIdx.x * MFS_LINES;
+    const long rem = nfreq - f0;
+    const int nf = rem < MFS_LINES ? (int)rem : MFS_LINES;
+    const int nm = 2 * L + 1;
+    for (int i = threadIdx.x; i < MFS_LINES * P; i += blockDim.x) buf[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nm * MFS_LINES; i += blockDim.x) {
+        const int m = i / MFS_LINES, f = i - m * MFS_LINES;
+        if (f >= nf) continue;
+        const long id = f0 + f;
+        const long kx = id / Q, ky = id - kx * Q;
+        const double2 v = S64[(kx * nm + m) * Q + ky];
+        double2* line = buf + f * P;
+        line[m] = v;
+        if (m > 0) line[P - m] = (m & 1) ? make_double2(-v.x, v.y) : make_double2(v.x, -v.y);
+    }
+    __syncthreads();
+    double2* r = fft_lines<-1>(buf, tmp, MFS_LINES, P, sc, twl);
+    const double inv = 1.0 / P;
+    for (int i = threadIdx.x; i < nf * P; i += blockDim.x) {
+        const double2 v = make_double2(r[i].x * inv, r[i].y * inv);
+        Sm64[f0 * P + i] = v;
+        Sm32[f0 * P + i] = make_float2((float)v.x, (float)v.y);
+        Smff[f0 * P + i] = to_ffc(v);
+    }
+}
+
+__global__ void k_twiddles_ff(const double2* __restrict__ tw64, ffc* __restrict__ twff, int P) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < P) twff[t] = to_ffc(tw64[t]);
+}
+
+rte_status plan_build_modefft(rte_plan p, cudaStream_t s) {
+    if (!p->mix_fft) return RTE_OK;
+    const int P = p->Pm;
+    k_twiddles<<<(P + 255) / 256, 256, 0, s>>>(p->twm64, p->twm32, P);
+    k_twiddles_ff<<<(P + 255) / 256, 256, 0, s>>>(p->twm64, p->twmff, P);
+    RTE_CUDA_TRY(cudaGetLastError());
+    const size_t smem = (size_t)(P + 2 * MFS_LINES * P) * sizeof(double2);
+    static bool once = false;
+    if (!once) {
+        RTE_CUDA_TRY(cudaFuncSetAttribute(k_modefft_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+        once = true;
+    }
+    const long nfreq = (long)p->H * p->Q;
+    k_modefft_spectra<<<(unsigned)((nfreq + MFS_LINES - 1) / MFS_LINES), 256, smem, s>>>(
+        p->S64, p->H, p->Q, p->L, P, p->sched_m, p->twm64, p->Sm64, p->Sm32, p->Smff);
+    rte_count_launches(3);
+    RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }

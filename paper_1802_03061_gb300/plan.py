@@ -56,7 +56,7 @@ class Plan:
 
     def __init__(self, n, h=None, mu_t=1.0, mu_s=0.5, sigma_hat=(1.0,), dim=2, prec="fp64", tol=1e-8,
                  restart=40, maxit=2000, inner_tol=1e-4, q_policy=0, stream=None, inner_solver="gmres", precond=0,
-                 precond_lmax=0):
+                 precond_lmax=0, mode_mix=0):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.dim, self.n = dim, int(n)
@@ -65,7 +65,7 @@ class Plan:
         self.sigma_hat = [float(v) for v in sigma_hat]
         self.L = len(self.sigma_hat) - 1
         self.opts = B.make_opts(prec, tol, restart, maxit, inner_tol, 0, q_policy, inner_solver, precond,
-                                precond_lmax)
+                                precond_lmax, mode_mix)
         self.handle = B.rte_plan_create(dim, self.n, self.h, self.mu_t, self.mu_s, self.L, self.sigma_hat,
                                         self.opts, _stream_ptr(stream))
         self.info = B.rte_plan_info(self.handle)
@@ -135,7 +135,7 @@ class Plan:
         opts = B.make_opts(prec if prec is not None else o.prec, tol or o.tol, restart or o.restart,
                            maxit or o.maxit, inner_tol or o.inner_tol, use_guess, o.q_policy,
                            inner_solver if inner_solver is not None else o.inner_solver,
-                           precond if precond is not None else o.precond, o.precond_lmax)
+                           precond if precond is not None else o.precond, o.precond_lmax, o.mode_mix)
         stats = B.rte_solve(self.handle, f.data_ptr(), u.data_ptr(), opts, _stream_ptr(stream))
         return u, stats
 
@@ -146,7 +146,7 @@ class Plan:
             u_host = np.zeros(self.shape(), dtype=np.complex128 if self.dim == 2 else np.float64)
         o = self.opts
         opts = B.make_opts(prec if prec is not None else o.prec, tol or o.tol, o.restart, o.maxit, o.inner_tol, 0,
-                           o.q_policy, o.inner_solver, o.precond, o.precond_lmax)
+                           o.q_policy, o.inner_solver, o.precond, o.precond_lmax, o.mode_mix)
         stats = B.rte_solve_host(self.handle, f_host.ctypes.data, u_host.ctypes.data, opts, _stream_ptr(stream))
         return u_host, stats
 

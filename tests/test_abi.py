@@ -77,12 +77,22 @@ def test_binding_refuses_missing_library(tmp_path, monkeypatch):
     dict(n=8, mu_t=1.0, mu_s=0.5, L=1, sig=[1.0, 1.5]),     # |sigma_hat_k| > 1
     dict(n=0, mu_t=1.0, mu_s=0.5, L=0, sig=[1.0]),          # empty grid
     dict(n=8, mu_t=-1.0, mu_s=0.0, L=0, sig=[1.0]),         # negative mu_t
-    dict(n=8, mu_t=1.0, mu_s=0.5, L=9, sig=[1.0] * 10),     # L beyond the supported 8
+    dict(n=8, mu_t=1.0, mu_s=0.5, L=65, sig=[1.0] * 66),    # L beyond the supported 64
 ])
 def test_plan_create_rejects_invalid_arguments_before_any_device_call(args):
     from paper_1802_03061_gb300 import _binding as B
     with pytest.raises(B.RteError) as ei:
         B.rte_plan_create(2, args["n"], 0.125, args["mu_t"], args["mu_s"], args["L"], args["sig"])
+    assert ei.value.status == B.RTE_EINVAL
+
+
+@pytest.mark.parametrize("L,mix", [(9, "direct"), (3, 3), (2, -1)])
+def test_plan_create_rejects_bad_mode_mix_before_any_device_call(L, mix):
+    """The direct (2L+1)^2 mix runs to L = 8; larger L need the mode-axis FFT."""
+    from paper_1802_03061_gb300 import _binding as B
+    opts = B.make_opts("mixed_fp32", mode_mix=mix)
+    with pytest.raises(B.RteError) as ei:
+        B.rte_plan_create(2, 8, 0.125, 1.0, 0.5, L, [1.0] + [0.5] * L, opts)
     assert ei.value.status == B.RTE_EINVAL
 
 

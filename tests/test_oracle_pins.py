@@ -68,16 +68,16 @@ def _ring_2d(mu, h, m, npts=40):
     return tot
 
 
-def _self_similar_2d(mu, h, m, depth):
+def _self_similar_2d(mu, h, m, depth, npts=40):
     """D_m(h) = D_m(h/3) + ring(h), recursed `depth` times; the remaining
     D_m(h/3^depth) is taken from the massless scaling D_m(h) = 1.5 ring_0(h)
     (D is linear in h at mu = 0), whose mass correction is O(mu h 3^-depth)."""
     tot = 0.0
     hh = h
     for _ in range(depth):
-        tot += _ring_2d(mu, hh, m)
+        tot += _ring_2d(mu, hh, m, npts)
         hh /= 3.0
-    return tot + 1.5 * _ring_2d(0.0, hh, m)
+    return tot + 1.5 * _ring_2d(0.0, hh, m, npts)
 
 
 @pytest.mark.parametrize("mu,h,m", [(0.0, 1.0, 0), (0.0, 1.0, 4), (10.0, 1.0 / 64, 0),
@@ -87,6 +87,16 @@ def test_cell_weights_self_similar_subdivision(mu, h, m):
     ref = 1.5 * _ring_2d(0.0, h, m) if mu == 0.0 else _self_similar_2d(mu, h, m, depth)
     D = oracle.cell_weights_2d(mu, h, m)
     assert D[2 * m] == pytest.approx(ref, rel=1e-11, abs=1e-16)
+
+
+@pytest.mark.parametrize("m,rel", [(32, 1e-11), (64, 2e-11), (128, 2e-10)])
+def test_cell_weights_high_orders(m, rel):
+    """The weights of the large truncations (2L up to 128): the self-similar
+    subdivision with 160-point tensor rules per sub-cell (cos(m theta) runs
+    through m/4 periods on a sub-cell next to the centre)."""
+    ref = _self_similar_2d(10.0, 1.0 / 64, m, 16, npts=160)
+    D = oracle.cell_weights_2d(10.0, 1.0 / 64, m)
+    assert D[2 * m] == pytest.approx(ref, rel=rel)
 
 
 def _ring_3d(mu, h, npts=24):
