@@ -813,13 +813,58 @@ def _smooth23(q):
     return q == 1
 
 
+def cnn_throughput(net, n, reps=20):
+    """Tensor-core convolution throughput of the guess network (CUDA events):
+    the forward at B = 1 and B = 8 on n x n pixels, and one training step
+    (forward, data and weight gradients, Adam) at B = 8.  Flops: 2 x pixels
+    x 9 x sum over layers of cin cout (forward; a training step counts three
+    times that: forward, data gradient, weight gradient)."""
+    import torch
+
+    from paper_1802_03061_gb300 import _binding as B
+    macs = sum(B.rte_cnn_layer(net.handle, l)["cin"] * B.rte_cnn_layer(net.handle, l)["cout"]
+               for l in range(net.depth)) * 9
+    out = {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for Bn in (1, 8):
+        X = torch.randn((Bn, n, n, net.cin), device="cuda").to(torch.bfloat16)
+        Y = torch.empty((Bn, n, n, net.cout), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            B.rte_cnn_forward(net.handle, X.data_ptr(), Bn, n, n, Y.data_ptr())
+        e0.record()
+        for _ in range(reps):
+            B.rte_cnn_forward(net.handle, X.data_ptr(), Bn, n, n, Y.data_ptr())
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["forward_B%d_ms" % Bn] = ms
+        out["forward_B%d_tflops" % Bn] = 2.0 * macs * Bn * n * n / (ms * 1e-3) / 1e12
+    Bn = 8
+    X = torch.randn((Bn, n, n, net.cin), device="cuda").to(torch.bfloat16)
+    T = torch.randn((Bn, n, n, net.cout), device="cuda").to(torch.bfloat16)
+    for _ in range(2):
+        B.rte_cnn_train_step(net.handle, X.data_ptr(), T.data_ptr(), Bn, n, n, net.used, 0.0, want_loss=False)
+    e0.record()
+    for _ in range(reps // 2):
+        B.rte_cnn_train_step(net.handle, X.data_ptr(), T.data_ptr(), Bn, n, n, net.used, 0.0, want_loss=False)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / (reps // 2)
+    out["train_step_B8_ms"] = ms
+    out["train_step_B8_tflops"] = 3 * 2.0 * macs * Bn * n * n / (ms * 1e-3) / 1e12
+    return out
+
+
 def run_learned(args):
     """The learned-initial-guess workload: 2D 256^2, L = 4, HG g in [0, 0.7],
     mu_t log-U[1, 50], mu_s/mu_t U[0.5, 0.99], 1-6 Gaussians.  Training data
-    are solver-generated (batched mixed solves), the network is trained on the
-    GPU by the library's kernels, then held-out seeds are solved to the same
-    FP64 residual 1e-8 from the zero start and from the learned guess (guess
-    time included).  A step is one held-out solve with the learned guess."""
+    are solver-generated (batched mixed solves; --train instances, seeds
+    10^6..), the network is trained on the GPU by the library's kernels, then
+    held-out seeds 0.. (--steps of them, after --warmup) are solved to the
+    same FP64 residual 1e-8 from the zero start and from the learned guess
+    (guess time included), with and without the periodic preconditioner.  A
+    step is one held-out solve with the learned guess (preconditioned)."""
     import torch
 
     import rte_synth
@@ -831,11 +876,26 @@ def run_learned(args):
     _build.build()
     n, L = 256, 4
     t0 = time.perf_counter()
-    train = [rte_synth.learned_guess_instance(10 ** 6 + i, n=n, L=L) for i in range(args.train)]
+    class _Seeds:
+        """the training instances, drawn when a chunk of them is solved"""
+
+        def __init__(self, count):
+            self.count = count
+
+        def __len__(self):
+            return self.count
+
+        def __getitem__(self, i):
+            if isinstance(i, slice):
+                return [rte_synth.learned_guess_instance(10 ** 6 + j, n=n, L=L) for j in range(*i.indices(self.count))]
+            return rte_synth.learned_guess_instance(10 ** 6 + i, n=n, L=L)
+
+    train = _Seeds(args.train)
     net = learned.GuessNet(L=L, depth=6, seed=1)
     X, T, gst = learned.generate(train, net.cin, net.cout, chunk=128)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
+    del train
     loss0 = net.loss(X[:64], T[:64])
     t1 = time.perf_counter()
     net.train(X, T, epochs=args.epochs, batch=8, lr=2e-3)
@@ -844,15 +904,17 @@ def run_learned(args):
     loss1 = net.loss(X[:64], T[:64])
     del X, T
     torch.cuda.empty_cache()
+    cnn = cnn_throughput(net, n)
     held = [rte_synth.learned_guess_instance(i, n=n, L=L) for i in range(args.warmup + args.steps)]
-    learned.evaluate(net, held[:args.warmup])  # warm-up steps (discarded)
+    learned.evaluate(net, held[:args.warmup], preconds=(0, 1))  # warm-up steps (discarded)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     l0 = B.rte_kernel_launches()
-    rows = learned.evaluate(net, held[args.warmup:])
+    rows = learned.evaluate(net, held[args.warmup:], preconds=(0, 1))
     launches = B.rte_kernel_launches() - l0
     clk = clocks.stop()
     sm = learned.summarize(rows)
+    smp = learned.summarize(rows, "_pc")
     # plain FP64 GPU solves of the first held-out instances (the metric's comparison)
     fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     e0 = torch.cuda.Event(enable_timing=True)
@@ -876,22 +938,31 @@ def run_learned(args):
         e1.synchronize()
         fp64_ms.append(e0.elapsed_time(e1))
         p.close()
-    ms = sm["guess_ms"]
+    ms = smp["guess_ms"]
+    bf16_peak = 1917.3
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16_peak = float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        pass
     line = {"metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner (f32 spectra), f64 refinement; bf16 network", "data": "synthetic",
             "config": {"workload": "learned_guess_256_L4: 256x256, L=4, HG g U[0,0.7], mu_t log-U[1,50], "
                                    "mu_s/mu_t U[0.5,0.99], 1-6 Gaussians; held-out seeds 0..; tol 1e-8",
-                       "train_instances": args.train, "epochs": args.epochs, "generate_s": gen_s,
-                       "train_s": train_s, "loss_before": loss0, "loss_after": loss1,
-                       "zero_start_ms": sm["zero_ms"], "guess_ms": sm["guess_ms"],
-                       "zero_start_iters": sm["zero_iters"], "guess_iters": sm["guess_iters"],
-                       "guess_relres0_median": sm["guess_relres0_median"], "time_ratio": sm["time_ratio"],
-                       "all_converged": sm["all_converged"], "max_solution_diff": sm["max_solution_diff"],
+                       "train_instances": args.train, "held_out_instances": args.steps, "epochs": args.epochs,
+                       "network": "6 3x3 conv layers, width 64, %d input channels (multi-scale b), %d outputs"
+                                  % (net.cin, net.cout),
+                       "generate_s": gen_s, "train_s": train_s, "loss_before": loss0, "loss_after": loss1,
+                       "unpreconditioned": sm, "preconditioned": smp,
                        "fp64_ms_per_solve_first4": float(np.mean(fp64_ms)),
                        "guess_only_ms_first4": float(np.mean(guess_only_ms)),
-                       "speedup_vs_fp64": float(np.mean(fp64_ms)) / ms,
+                       "speedup_vs_fp64": float(np.mean(fp64_ms)) / ms, "cnn": cnn,
                        "l2": "flushed (256 MB write) before every timed solve"},
+            "roofline": {"bound": "tensor", "kernel": "k_conv_tc: guess network forward at B = 8 (tcgen05)",
+                         "achieved": cnn["forward_B8_tflops"], "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": cnn["forward_B8_tflops"] / bf16_peak, "traffic": None,
+                         "peak_source": "measured (cuBLAS bf16 burst)"},
             "gpu_launches": int(launches), "clocks": clk}
     net.close()
     print(json.dumps(line))

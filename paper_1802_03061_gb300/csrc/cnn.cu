@@ -1,8 +1,10 @@
 // Learned initial guess for the GMRES solve (task extension; the paper has
 // no counterpart): a small 3x3 convolutional network, NHWC BF16 activations,
-// FP32 accumulation on the BF16 tensor cores (mma.sync m16n8k16), trained on
-// the GPU by its own forward / data-gradient / weight-gradient kernels and
-// Adam.
+// FP32 accumulation on the BF16 tensor cores, trained on the GPU by its own
+// forward / data-gradient / weight-gradient kernels and Adam.  The forward
+// and data-gradient convolutions run on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in TMEM, k_conv_tc); the weight gradient, a
+// reduction over pixels, on warp-level mma.sync (k_conv_wgrad).
 //
 // Layer l: Y = act(conv3x3(X, W_l) + bias_l), same padding (zeros outside the
 // image), channel counts padded to multiples of 16.  Weights W_l[tap][cin][cout]
@@ -23,6 +25,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc05.cuh"
 
 typedef __nv_bfloat16 bf16;
 
@@ -41,98 +44,167 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
 }
 
 // ---------------------------------------------------------------------------
-// forward / data-gradient convolution
-//   out[p][n] = sum_tap sum_c X[p + s*d(tap)][c] * Wt(tap, c, n)
-//   Wt(tap, c, n) = W[tap*sT + c*sC + n*sN]; s = +1 (forward) or -1 (data gradient,
-//   dX[q] = sum_tap dY[q - d(tap)] W[tap]^T)
-// X: [B][H][Wd][CX] bf16; out: [B][H][Wd][NOUT] (bf16 or f32)
-// grid: (ceil(Wd/128), H, B), block 128 threads
+// forward / data-gradient convolution on tcgen05 tensor cores
+//   out[p][n] = sum_tap sum_c X[p + s d(tap)][c] Wk[tap][n][c]
+//   s = +1 (forward, Wk[tap][co][ci]: the weights transposed) or -1 (data
+//   gradient dX[q] = sum_tap dY[q - d(tap)] W[tap]^T, Wk = W[tap][ci][co])
+// One CTA: a run of 128 output pixels along x (the MMA's M = 128 rows, one
+// TMEM lane each) by all NOUT output channels (N), reduced over the 9 taps x
+// CX input channels (K, 16 per MMA).  The three input rows y-1, y, y+1 over
+// pixels x0-1 .. x0+128 (zeros outside the image) are staged once, per row
+// and 16-byte channel chunk as a run of 130 pixels of 16 bytes: in that
+// layout the operand of tap (dy, dx) is the same core-matrix view started
+// dx + 1 pixels (16 bytes) further in row dy + 1 (core matrices of 8
+// consecutive pixels: row-group stride 128 bytes, K-chunk stride 130 x 16),
+// so all 9 taps read one staged tile.  The tap's weights (N x CX, K-major
+// core matrices) are double-buffered: while one thread issues a tap's MMAs,
+// the CTA stages the next tap's weights; an mbarrier signalled by
+// tcgen05.commit frees a buffer.  Epilogue: tcgen05.ld of the FP32
+// accumulators, bias, ReLU, BF16 (or FP32) NHWC store.  (Staging all 9
+// taps' weights up front instead measured 1.7x slower: the larger shared
+// memory leaves one CTA per SM, so loads and MMAs no longer overlap.)
+// X: [B][H][Wd][CX] bf16; out: [B][H][Wd][NOUT]; grid (ceil(Wd/128), H, B), 128 threads.
 // ---------------------------------------------------------------------------
-template <int NOUT>
-__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ X, int CX, const bf16* __restrict__ W, long sT,
-                                              long sC, long sN, int flip, const float* __restrict__ bias, int relu,
-                                              bf16* __restrict__ Ybf, float* __restrict__ Yf, int H, int Wd) {
-    __shared__ __align__(16) bf16 As[CNN_TILE * CNN_APAD];
-    __shared__ __align__(16) bf16 Bs[NOUT * CNN_APAD];
-    const int x0 = blockIdx.x * CNN_TILE, y = blockIdx.y, b = blockIdx.z;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    constexpr int NT = NOUT / 8;
-    float acc[2][NT][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#define CONV_TC_PX 130   // staged pixels per row: 128 + the two halo pixels
+template <int CX, int NOUT> struct ConvTc {
+    static constexpr int KC = CX / 8;                          // 16-byte channel chunks
+    static constexpr int IN_BYTES = 3 * KC * CONV_TC_PX * 16;  // the three staged input rows
+    static constexpr int W_BYTES = NOUT * CX * 2;              // one tap's weights
+    static constexpr int NCOLS = NOUT < 32 ? 32 : NOUT;        // TMEM columns (a power of two >= 32)
+    // at most 512 / NCOLS CTAs may hold TMEM on an SM at once: pad the shared
+    // memory so that no more are resident (228 KB per SM)
+    static constexpr int PAD = 233472 / (512 / NCOLS + 1) + 1;
+    static constexpr int NEED = IN_BYTES + 2 * W_BYTES + 1024;  // + alignment slack
+    static constexpr int SMEM = NEED > PAD ? NEED : PAD;
+};
+#define CONV_TC_POLLS (1L << 20)  // polls before an mbarrier wait gives up (error flag) instead of hanging
+
+template <int CX, int NOUT>
+__device__ __forceinline__ void conv_tc_stage_w(uint8_t* Wb, const bf16* __restrict__ Wk, int tap, int tid) {
+    constexpr int KC = CX / 8;
+    const bf16* wt = Wk + (long)tap * NOUT * CX;
+    for (int c = tid; c < NOUT * KC; c += 128) {
+        const int nr = c / KC, kc = c - nr * KC;
+        const uint4 v = *reinterpret_cast<const uint4*>(wt + (long)nr * CX + kc * 8);
+        *reinterpret_cast<uint4*>(Wb + ((nr >> 3) * KC + kc) * 128 + (nr & 7) * 16) = v;
+    }
+}
+
+template <int CX, int NOUT>
+__global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, const bf16* __restrict__ Wk, int flip,
+                                                 const float* __restrict__ bias, int relu, bf16* __restrict__ Ybf,
+                                                 float* __restrict__ Yf, int H, int Wd, int* __restrict__ err) {
+    using C = ConvTc<CX, NOUT>;
+    constexpr int KC = C::KC;
+    constexpr uint32_t LBO = CONV_TC_PX * 16;  // next 16-byte channel chunk of a staged row
+    extern __shared__ uint8_t smraw[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    uint8_t* In = sbase;                 // [3 rows][KC][130 pixels][16 bytes]
+    uint8_t* Wbuf = sbase + C::IN_BYTES;  // 2 x [N/8][KC][8][16 bytes]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int x0 = blockIdx.x * 128, y = blockIdx.y, b = blockIdx.z;
+    if (warp == 0) tc_alloc(&tslot, C::NCOLS);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    // the input rows (consecutive threads: consecutive 16-byte chunks of a pixel, then pixels)
+    for (int c = tid; c < 3 * CONV_TC_PX * KC; c += 128) {
+        const int kc = c % KC, px = (c / KC) % CONV_TC_PX, r = c / (KC * CONV_TC_PX);
+        const int yy = y + r - 1, xx = x0 + px - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
+            v = *reinterpret_cast<const uint4*>(X + (((long)b * H + yy) * Wd + xx) * CX + kc * 8);
+        *reinterpret_cast<uint4*>(In + ((r * KC + kc) * CONV_TC_PX + px) * 16) = v;
+    }
+    conv_tc_stage_w<CX, NOUT>(Wbuf, Wk, 0, tid);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, NOUT);
     const int sgn = flip ? -1 : 1;
+    const uint32_t in0 = smem_u32(In), w0 = smem_u32(Wbuf);
+    bool ok = true;
     for (int tap = 0; tap < 9; ++tap) {
-        const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
-        const int yy = y + dy;
-        const int wt = tap;
-        for (int c0 = 0; c0 < CX; c0 += 16) {
-            __syncthreads();
-            // A tile: 128 pixels x 16 channels (one pixel per thread, 2 x 16 B)
-            {
-                const int i = threadIdx.x;
-                const int xx = x0 + i + dx;
-                uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
-                if (yy >= 0 && yy < H && xx >= 0 && xx < Wd && x0 + i < Wd) {
-                    const uint4* src = reinterpret_cast<const uint4*>(X + (((long)b * H + yy) * Wd + xx) * CX + c0);
-                    v0 = src[0];
-                    v1 = src[1];
+        const int st = tap & 1;
+        if (tid == 0) {
+            tc_fence_after();
+            const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
+            // output pixel m reads staged pixel m + dx + 1 of staged row dy + 1
+            const uint32_t a0 = in0 + (uint32_t)(((dy + 1) * KC) * CONV_TC_PX + dx + 1) * 16;
+            const uint32_t b0 = w0 + st * C::W_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < CX / 16; ++ks) {
+                // K = 16 = two 16-byte channel chunks per step
+                const uint64_t ad = tc_desc_kmajor(a0 + ks * 2 * LBO, LBO, 128);
+                const uint64_t bd = tc_desc_kmajor(b0 + ks * 256, 128, KC * 128);
+                tc_mma_bf16(tmem, ad, bd, IDESC, (tap | ks) ? 1u : 0u);
+            }
+            tc_commit(&mbar[st]);
+        }
+        if (tap + 1 < 9) {
+            // the next tap's weights go to the other buffer, last read by the
+            // MMAs of tap - 1: one thread waits for their commit, the barrier
+            // passes the outcome to all (uniform control flow)
+            if (tap >= 1) {
+                int bad = 0;
+                if (tid == 0) bad = !mbar_wait(&mbar[st ^ 1], ((tap - 1) >> 1) & 1, CONV_TC_POLLS);
+                if (__syncthreads_or(bad)) {
+                    ok = false;
+                    break;
                 }
-                uint4* dst = reinterpret_cast<uint4*>(As + i * CNN_APAD);
-                dst[0] = v0;
-                dst[1] = v1;
             }
-            // B tile: [n][k] = Wt(tap, c0 + k, n)
-            for (int e = threadIdx.x; e < NOUT * 16; e += blockDim.x) {
-                const int n = e / 16, k = e % 16;
-                Bs[n * CNN_APAD + k] = W[wt * sT + (long)(c0 + k) * sC + (long)n * sN];
-            }
+            fence_async_smem();
+            conv_tc_stage_w<CX, NOUT>(Wbuf + (st ^ 1) * C::W_BYTES, Wk, tap + 1, tid);
+            fence_async_smem();
             __syncthreads();
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = warp * 32 + mt * 16 + g;
-                af[mt][0] = ld32(As + r * CNN_APAD + 2 * t);
-                af[mt][1] = ld32(As + (r + 8) * CNN_APAD + 2 * t);
-                af[mt][2] = ld32(As + r * CNN_APAD + 2 * t + 8);
-                af[mt][3] = ld32(As + (r + 8) * CNN_APAD + 2 * t + 8);
-            }
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                uint32_t bfr[2];
-                const int n = nt * 8 + g;
-                bfr[0] = ld32(Bs + n * CNN_APAD + 2 * t);
-                bfr[1] = ld32(Bs + n * CNN_APAD + 2 * t + 8);
-                mma_bf16(acc[0][nt], af[0], bfr);
-                mma_bf16(acc[1][nt], af[1], bfr);
-            }
         }
     }
-    // epilogue: bias, activation, store
+    // the last commit (tap 8: buffer 0, fifth phase, parity 0) covers every
+    // MMA; buffer 1's fourth arrival (tap 7, parity 1) is waited for too so
+    // that no arrival is pending when the CTA exits
+    {
+        int bad = 0;
+        if (tid == 0) bad = !mbar_wait(&mbar[0], 0, CONV_TC_POLLS) || !mbar_wait(&mbar[1], 1, CONV_TC_POLLS);
+        if (__syncthreads_or(bad)) ok = false;
+    }
+    tc_fence_after();
+    float acc[NOUT];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+    for (int c0 = 0; c0 < NOUT; c0 += 16) tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc + c0);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, C::NCOLS);
+    if (!ok) {
+        if (lane == 0) atomicExch(err, 1);
+        return;
+    }
+    const int px = x0 + warp * 32 + lane;
+    if (px >= Wd) return;
+    const long o = (((long)b * H + y) * Wd + px) * NOUT;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int px = x0 + warp * 32 + mt * 16 + g + 8 * half;
-            if (px >= Wd) continue;
-            const long o = (((long)b * H + y) * Wd + px) * NOUT;
+    for (int n = 0; n < NOUT; ++n) {
+        float v = acc[n];
+        if (bias) v += bias[n];
+        if (relu) v = fmaxf(v, 0.f);
+        acc[n] = v;
+    }
+    if (Yf) {
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int n = nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (bias) { v0 += bias[n]; v1 += bias[n + 1]; }
-                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-                if (Yf) {
-                    Yf[o + n] = v0;
-                    Yf[o + n + 1] = v1;
-                } else {
-                    *reinterpret_cast<__nv_bfloat162*>(Ybf + o + n) = __floats2bfloat162_rn(v0, v1);
-                }
-            }
+        for (int n = 0; n < NOUT; n += 4)
+            *reinterpret_cast<float4*>(Yf + o + n) = make_float4(acc[n], acc[n + 1], acc[n + 2], acc[n + 3]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < NOUT; n += 8) {
+            __nv_bfloat162 h[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(acc[n + 2 * q], acc[n + 2 * q + 1]);
+            *reinterpret_cast<uint4*>(Ybf + o + n) = *reinterpret_cast<const uint4*>(h);
         }
     }
 }
@@ -279,8 +351,10 @@ __global__ void k_mse(const float* __restrict__ out, const bf16* __restrict__ tg
 }
 
 // Adam (Kingma & Ba) on FP32 master weights; BF16 copy refreshed
+// (weights [9][ci][co]: wbt, when given, receives the transposed copy [9][co][ci])
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
-                       bf16* __restrict__ wb, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       bf16* __restrict__ wb, bf16* __restrict__ wbt, int ci_n, int co_n, long n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -290,12 +364,22 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
         const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         w[i] = wi;
         if (wb) wb[i] = __float2bfloat16(wi);
+        if (wbt) {
+            const long co = i % co_n, ci = (i / co_n) % ci_n, tap = i / ((long)co_n * ci_n);
+            wbt[(tap * co_n + co) * ci_n + ci] = __float2bfloat16(wi);
+        }
     }
 }
 
-__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, long n) {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        b[i] = __float2bfloat16(a[i]);
+// BF16 copies of the FP32 weights [9][ci][co]: wb in place, wbt transposed [9][co][ci]
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, bf16* __restrict__ bt, int ci_n, int co_n,
+                          long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const bf16 v = __float2bfloat16(a[i]);
+        b[i] = v;
+        const long co = i % co_n, ci = (i / co_n) % ci_n, tap = i / ((long)co_n * ci_n);
+        bt[(tap * co_n + co) * ci_n + ci] = v;
+    }
 }
 
 // deterministic weight init: uniform(-a, a) from a counter hash (splitmix64)
@@ -362,6 +446,60 @@ __global__ void k_features(const double* __restrict__ bmode, const double* __res
     }
 }
 
+// multi-scale context (inputs with room for it, CIN >= 3 (2L+1) + 4): the
+// means of the 2L+1 scaled channels of b over the 8 x 8 and the 32 x 32 tile
+// that contain the pixel, in channels 2L+5 + c and 2L+5 + (2L+1) + c.  A 3x3
+// network sees 13 cells; these give every pixel the field's coarse shape
+// over 32 (resp. 128) cells around it at no extra layers.  One CTA per 32 x 32
+// tile (partial tiles at the border average their own cells).
+__global__ void __launch_bounds__(256) k_features_pooled(const double* __restrict__ bmode, int n, int L,
+                                                         const double* __restrict__ sc, int CIN, bf16* __restrict__ X) {
+    __shared__ float s8[16][2 * RTE_MAX_L_DIRECT + 1];
+    __shared__ float s32[2 * RTE_MAX_L_DIRECT + 1];
+    const long P = (long)n * n;
+    const int nch = 2 * L + 1;
+    const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * 32;
+    const double inv = sc[0] > 0 ? 1.0 / sc[0] : 0.0;
+    // channel c, sub-tile q (4 x 4 of 8 x 8 cells): one thread each, summing its cells
+    for (int job = threadIdx.x; job < 16 * nch; job += blockDim.x) {
+        const int c = job / 16, q = job % 16;
+        const int k = c == 0 ? 0 : (c + 1) / 2, im = c > 0 && (c % 2 == 0);
+        const int x0 = tx0 + (q % 4) * 8, y0 = ty0 + (q / 4) * 8;
+        double sum = 0.0;
+        int cnt = 0;
+        for (int yy = y0; yy < y0 + 8 && yy < n; ++yy)
+            for (int xx = x0; xx < x0 + 8 && xx < n; ++xx) {
+                sum += bmode[2 * (k * P + (long)yy * n + xx) + im];
+                ++cnt;
+            }
+        s8[q][c] = cnt ? (float)(sum * inv / cnt) : 0.f;
+    }
+    __syncthreads();
+    if (threadIdx.x < nch) {
+        const int c = threadIdx.x;
+        double sum = 0.0;
+        int cnt = 0;
+        for (int q = 0; q < 16; ++q) {
+            const int x0 = tx0 + (q % 4) * 8, y0 = ty0 + (q / 4) * 8;
+            const int wq = max(0, min(8, n - x0)) * max(0, min(8, n - y0));
+            sum += (double)s8[q][c] * wq;
+            cnt += wq;
+        }
+        s32[c] = cnt ? (float)(sum / cnt) : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+        const int xx = tx0 + (i % 32), yy = ty0 + (i / 32);
+        if (xx >= n || yy >= n) continue;
+        const int q = ((i / 32) / 8) * 4 + (i % 32) / 8;
+        bf16* xp = X + ((long)yy * n + xx) * CIN + nch + 4;
+        for (int c = 0; c < nch; ++c) {
+            xp[c] = __float2bfloat16(s8[q][c]);
+            xp[nch + c] = __float2bfloat16(s32[c]);
+        }
+    }
+}
+
 __global__ void k_targets(const double* __restrict__ umode, const double* __restrict__ bmode, int n, int L,
                           const double* __restrict__ sc, int COUT, bf16* __restrict__ Yt) {
     const long P = (long)n * n;
@@ -404,7 +542,8 @@ struct CnnLayer {
     int cin, cout;   // padded channel counts
     float* w = nullptr;
     float* bias = nullptr;
-    bf16* wb = nullptr;
+    bf16* wb = nullptr;    // BF16 copy [9][cin][cout]
+    bf16* wbt = nullptr;   // BF16 copy transposed [9][cout][cin] (forward MMA operand)
     float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr, *gw = nullptr, *gb = nullptr;
 };
 
@@ -421,6 +560,7 @@ struct rte_cnn_s {
     long part_cap = 0;
     float* loss_part = nullptr;
     float* loss_host = nullptr;
+    int* err = nullptr;        // set by a tensor-core convolution whose barrier wait gave up
     long step = 0;
 };
 
@@ -430,37 +570,46 @@ static int nblk_pix(int B, int H) {
     return (int)((rows + rpb - 1) / rpb);
 }
 
-static cudaError_t conv_fwd(const bf16* X, int CX, const CnnLayer& Lr, bool relu, bf16* Ybf, float* Yf, int B, int H,
-                            int W, cudaStream_t s) {
-    dim3 grid((W + CNN_TILE - 1) / CNN_TILE, H, B);
-    const long sT = (long)Lr.cin * Lr.cout, sC = Lr.cout, sN = 1;
-    if (Lr.cout == 64)
-        k_conv<64><<<grid, 128, 0, s>>>(X, CX, Lr.wb, sT, sC, sN, 0, Lr.bias, relu, Ybf, Yf, H, W);
-    else if (Lr.cout == 32)
-        k_conv<32><<<grid, 128, 0, s>>>(X, CX, Lr.wb, sT, sC, sN, 0, Lr.bias, relu, Ybf, Yf, H, W);
-    else if (Lr.cout == 16)
-        k_conv<16><<<grid, 128, 0, s>>>(X, CX, Lr.wb, sT, sC, sN, 0, Lr.bias, relu, Ybf, Yf, H, W);
-    else
-        return cudaErrorInvalidValue;
-    rte_count_launches(1);
+template <int CX, int NOUT>
+static cudaError_t launch_conv_tc(dim3 grid, const bf16* X, const bf16* Wk, int flip, const float* bias, int relu,
+                                  bf16* Ybf, float* Yf, int H, int W, int* err, cudaStream_t s) {
+    using C = ConvTc<CX, NOUT>;
+    static bool once = false;
+    if (!once) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CX, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        once = true;
+    }
+    k_conv_tc<CX, NOUT><<<grid, 128, C::SMEM, s>>>(X, Wk, flip, bias, relu, Ybf, Yf, H, W, err);
     return cudaGetLastError();
 }
 
-// dX[p][ci] = sum_tap sum_co dY[p - d(tap)][co] W[tap][ci][co]
-static cudaError_t conv_dgrad(const bf16* dY, const CnnLayer& Lr, bf16* dX, int B, int H, int W, cudaStream_t s) {
-    dim3 grid((W + CNN_TILE - 1) / CNN_TILE, H, B);
-        // Wt(tap, c = co, n = ci) = W[tap][ci][co]: sC = 1 (co), sN = cout (ci)
-    const long sT = (long)Lr.cin * Lr.cout, sC = 1, sN = Lr.cout;
-    if (Lr.cin == 64)
-        k_conv<64><<<grid, 128, 0, s>>>(dY, Lr.cout, Lr.wb, sT, sC, sN, 1, nullptr, 0, dX, nullptr, H, W);
-    else if (Lr.cin == 32)
-        k_conv<32><<<grid, 128, 0, s>>>(dY, Lr.cout, Lr.wb, sT, sC, sN, 1, nullptr, 0, dX, nullptr, H, W);
-    else if (Lr.cin == 16)
-        k_conv<16><<<grid, 128, 0, s>>>(dY, Lr.cout, Lr.wb, sT, sC, sN, 1, nullptr, 0, dX, nullptr, H, W);
-    else
-        return cudaErrorInvalidValue;
+// CX, NOUT in {16, 32, 64}
+static cudaError_t conv_tc(int CX, int NOUT, const bf16* X, const bf16* Wk, int flip, const float* bias, int relu,
+                           bf16* Ybf, float* Yf, int B, int H, int W, int* err, cudaStream_t s) {
+    const dim3 grid((W + CNN_TILE - 1) / CNN_TILE, H, B);
+#define CONV_TC_CASE(a, b) \
+    if (CX == a && NOUT == b) return launch_conv_tc<a, b>(grid, X, Wk, flip, bias, relu, Ybf, Yf, H, W, err, s);
+    CONV_TC_CASE(16, 16) CONV_TC_CASE(16, 32) CONV_TC_CASE(16, 64)
+    CONV_TC_CASE(32, 16) CONV_TC_CASE(32, 32) CONV_TC_CASE(32, 64)
+    CONV_TC_CASE(64, 16) CONV_TC_CASE(64, 32) CONV_TC_CASE(64, 64)
+#undef CONV_TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+// Y[p][co] = act(sum_tap sum_ci X[p + d(tap)][ci] W[tap][ci][co] + bias[co]),
+// the weights read transposed (wbt[tap][co][ci]: K-major for the MMA)
+static cudaError_t conv_fwd(const bf16* X, const CnnLayer& Lr, bool relu, bf16* Ybf, float* Yf, int B, int H, int W,
+                            int* err, cudaStream_t s) {
     rte_count_launches(1);
-    return cudaGetLastError();
+    return conv_tc(Lr.cin, Lr.cout, X, Lr.wbt, 0, Lr.bias, relu, Ybf, Yf, B, H, W, err, s);
+}
+
+// dX[p][ci] = sum_tap sum_co dY[p - d(tap)][co] W[tap][ci][co]  (W[tap] is K-major in co)
+static cudaError_t conv_dgrad(const bf16* dY, const CnnLayer& Lr, bf16* dX, int B, int H, int W, int* err,
+                              cudaStream_t s) {
+    rte_count_launches(1);
+    return conv_tc(Lr.cout, Lr.cin, dY, Lr.wb, 1, nullptr, 0, dX, nullptr, B, H, W, err, s);
 }
 
 static cudaError_t conv_wgrad(rte_cnn c, const bf16* X, const bf16* dY, CnnLayer& Lr, int B, int H, int W,
@@ -529,10 +678,11 @@ extern "C" rte_status rte_cnn_destroy(rte_cnn c) {
     cudaDeviceSynchronize();
     cnn_free_acts(c);
     for (CnnLayer& L : c->layers) {
-        void* ptrs[] = {L.w, L.bias, L.wb, L.mw, L.vw, L.mb, L.vb, L.gw, L.gb};
+        void* ptrs[] = {L.w, L.bias, L.wb, L.wbt, L.mw, L.vw, L.mb, L.vb, L.gw, L.gb};
         for (void* p : ptrs) if (p) rte_dev_free(p);
     }
     if (c->loss_host) rte_host_free(c->loss_host);
+    if (c->err) rte_dev_free(c->err);
     delete c;
     return RTE_OK;
 }
@@ -553,6 +703,7 @@ extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth
         L.cout = l == depth - 1 ? cout : width;
         const long nw = 9L * L.cin * L.cout;
         bool ok = rte_dev_malloc((void**)&L.w, nw * 4) == cudaSuccess && rte_dev_malloc((void**)&L.wb, nw * 2) == cudaSuccess &&
+                  rte_dev_malloc((void**)&L.wbt, nw * 2) == cudaSuccess &&
                   rte_dev_malloc((void**)&L.mw, nw * 4) == cudaSuccess && rte_dev_malloc((void**)&L.vw, nw * 4) == cudaSuccess &&
                   rte_dev_malloc((void**)&L.gw, nw * 4) == cudaSuccess && rte_dev_malloc((void**)&L.bias, L.cout * 4) == cudaSuccess &&
                   rte_dev_malloc((void**)&L.mb, L.cout * 4) == cudaSuccess && rte_dev_malloc((void**)&L.vb, L.cout * 4) == cudaSuccess &&
@@ -561,7 +712,7 @@ extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth
         // He-uniform init; the last layer starts small so the first guess is ~b
         const float a = (l == depth - 1 ? 0.1f : 1.0f) * sqrtf(6.f / (9.f * L.cin));
         k_init_uniform<<<256, 256, 0, s>>>(L.w, nw, seed * 131 + l, a);
-        k_to_bf16<<<256, 256, 0, s>>>(L.w, L.wb, nw);
+        k_to_bf16<<<256, 256, 0, s>>>(L.w, L.wb, L.wbt, L.cin, L.cout, nw);
         cudaMemsetAsync(L.bias, 0, L.cout * 4, s);
         cudaMemsetAsync(L.mw, 0, nw * 4, s);
         cudaMemsetAsync(L.vw, 0, nw * 4, s);
@@ -569,11 +720,13 @@ extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth
         cudaMemsetAsync(L.vb, 0, L.cout * 4, s);
         rte_count_launches(2);
     }
-    if (rte_host_malloc((void**)&c->loss_host, 1024 * sizeof(float)) != cudaSuccess) {
+    if (rte_host_malloc((void**)&c->loss_host, 1024 * sizeof(float)) != cudaSuccess ||
+        rte_dev_malloc((void**)&c->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         rte_cnn_destroy(c);
         return RTE_ENOMEM;
     }
+    cudaMemsetAsync(c->err, 0, sizeof(int), s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { rte_cnn_destroy(c); return rte_cuda_fail(e, "rte_cnn_create"); }
     *out = c;
@@ -588,8 +741,8 @@ static rte_status cnn_forward_internal(rte_cnn c, const bf16* X, int B, int H, i
     for (int l = 0; l < c->depth; ++l) {
         const CnnLayer& L = c->layers[l];
         const bool last = l == c->depth - 1;
-        cudaError_t e = conv_fwd(c->act[l], L.cin, L, !last, last ? nullptr : c->act[l + 1], last ? c->out_f : nullptr,
-                                 B, H, W, s);
+        cudaError_t e = conv_fwd(c->act[l], L, !last, last ? nullptr : c->act[l + 1], last ? c->out_f : nullptr,
+                                 B, H, W, c->err, s);
         if (e != cudaSuccess) return rte_cuda_fail(e, "cnn forward");
     }
     return RTE_OK;
@@ -620,7 +773,7 @@ static rte_status cnn_backward(rte_cnn c, const bf16* dOut, int B, int H, int W,
         cudaError_t e = conv_wgrad(c, c->act[l], gcur, L, B, H, W, s);
         if (e != cudaSuccess) return rte_cuda_fail(e, "cnn wgrad");
         if (l > 0) {
-            e = conv_dgrad(gcur, L, gnext, B, H, W, s);
+            e = conv_dgrad(gcur, L, gnext, B, H, W, c->err, s);
             if (e != cudaSuccess) return rte_cuda_fail(e, "cnn dgrad");
             bf16* t = gcur;
             gcur = gnext;
@@ -652,15 +805,20 @@ extern "C" rte_status rte_cnn_train_step(rte_cnn c, const void* X_dev, const voi
         const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
         for (CnnLayer& L : c->layers) {
             const long nw = 9L * L.cin * L.cout;
-            k_adam<<<256, 256, 0, s>>>(L.w, L.mw, L.vw, L.gw, L.wb, nw, lr, b1, b2, 1e-8f, c1, c2);
-            k_adam<<<1, 256, 0, s>>>(L.bias, L.mb, L.vb, L.gb, nullptr, L.cout, lr, b1, b2, 1e-8f, c1, c2);
+            k_adam<<<256, 256, 0, s>>>(L.w, L.mw, L.vw, L.gw, L.wb, L.wbt, L.cin, L.cout, nw, lr, b1, b2, 1e-8f, c1,
+                                       c2);
+            k_adam<<<1, 256, 0, s>>>(L.bias, L.mb, L.vb, L.gb, nullptr, nullptr, 1, 1, L.cout, lr, b1, b2, 1e-8f, c1,
+                                     c2);
             rte_count_launches(2);
         }
         RTE_CUDA_TRY(cudaGetLastError());
     }
     if (loss_out) {
+        int* err_host = reinterpret_cast<int*>(c->loss_host + 1000);  // spare pinned words past the partials
         RTE_CUDA_TRY(cudaMemcpyAsync(c->loss_host, c->loss_part, nb * sizeof(float), cudaMemcpyDeviceToHost, s));
+        RTE_CUDA_TRY(cudaMemcpyAsync(err_host, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
         RTE_CUDA_TRY(cudaStreamSynchronize(s));
+        if (*err_host) return rte_fail(RTE_ETIMEOUT, "cnn: a tensor-core convolution gave up waiting for its MMAs");
         double t = 0.0;
         for (int i = 0; i < nb; ++i) t += c->loss_host[i];
         *loss_out = (float)t;
@@ -687,7 +845,7 @@ extern "C" rte_status rte_cnn_sync_weights(rte_cnn c, void* stream) {
     if (!c) return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     for (CnnLayer& L : c->layers) {
-        k_to_bf16<<<256, 256, 0, s>>>(L.w, L.wb, 9L * L.cin * L.cout);
+        k_to_bf16<<<256, 256, 0, s>>>(L.w, L.wb, L.wbt, L.cin, L.cout, 9L * L.cin * L.cout);
         rte_count_launches(1);
     }
     RTE_CUDA_TRY(cudaGetLastError());
@@ -781,6 +939,12 @@ extern "C" rte_status rte_guess_features(rte_plan p, int cin, const double* f_de
     k_features<<<512, 256, 0, s>>>(b_dev, f_dev, p->n, p->L, p->dscal + 2, p0, p1, p2, cin, (bf16*)X_dev);
     rte_count_launches(1);
     RTE_CUDA_TRY(cudaGetLastError());
+    if (3 * p->nch + 4 <= cin && p->L <= RTE_MAX_L_DIRECT) {
+        const dim3 tiles((p->n + 31) / 32, (p->n + 31) / 32);
+        k_features_pooled<<<tiles, 256, 0, s>>>(b_dev, p->n, p->L, p->dscal + 2, cin, (bf16*)X_dev);
+        rte_count_launches(1);
+        RTE_CUDA_TRY(cudaGetLastError());
+    }
     return RTE_OK;
 }
 

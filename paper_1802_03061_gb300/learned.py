@@ -30,9 +30,15 @@ def _view(ptr, shape):
 class GuessNet:
     """The 3x3 network of the learned guess (library object rte_cnn)."""
 
-    def __init__(self, L, depth=6, seed=0):
+    def __init__(self, L, depth=6, seed=0, multiscale=True):
+        """multiscale: 32 input channels, the last 2 (2L+1) holding b averaged
+        over the 8 x 8 and 32 x 32 tiles around each pixel (where 3 (2L+1) + 4
+        channels fit, L <= 4); else 16 (or 32) channels of b, f, coefficients."""
         self.L = L
-        self.cin = 16 if 2 * L + 5 <= 16 else 32
+        if multiscale and 3 * (2 * L + 1) + 4 <= 32:
+            self.cin = 32
+        else:
+            self.cin = 16 if 2 * L + 5 <= 16 else 32
         self.cout = 16 if 2 * L + 1 <= 16 else 32
         self.depth = depth
         self.used = 2 * L + 1
@@ -146,9 +152,12 @@ def generate(instances, cin, cout, chunk=128, prec="mixed_fp32", restart=30):
     return X, T, stats_all
 
 
-def evaluate(net, instances, prec="mixed_fp32", restart=30, flush=True):
+def evaluate(net, instances, prec="mixed_fp32", restart=30, flush=True, preconds=(0,)):
     """Per instance: zero-start solve vs learned-guess solve (guess time
-    included), both to the same FP64 relative residual 1e-8."""
+    included), both to the same FP64 relative residual 1e-8 with the same
+    solver settings, for each setting of the periodic preconditioner in
+    `preconds` (keys "zero"/"guess" without it, "zero_pc"/"guess_pc" with it),
+    and the guess's initial relative residual."""
     rows = []
     fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda") if flush else None
     e0 = torch.cuda.Event(enable_timing=True)
@@ -158,46 +167,52 @@ def evaluate(net, instances, prec="mixed_fp32", restart=30, flush=True):
         plan = Plan(int(d["n"]), h=d["h"], mu_t=d["mu_t"], mu_s=d["mu_s"], sigma_hat=d["sigma_hat"], prec=prec,
                     restart=restart, maxit=4000)
         f = torch.from_numpy(d["f"]).cuda()
-        # warm both paths once (graph capture, workspaces)
-        plan.solve(f)
-        u0, _ = net.guess(plan, f)
-        plan.solve(f, u=u0.clone())
         res = {}
-        for mode in ("zero", "guess"):
-            if fl is not None:
-                fl.zero_()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            if mode == "zero":
-                u, st = plan.solve(f)
-            else:
-                u0, _ = net.guess(plan, f)
-                u, st = plan.solve(f, u=u0)
-            e1.record(stream)
-            e1.synchronize()
-            res[mode] = dict(ms=e0.elapsed_time(e1), iters=st["iters"], outer=st["outer"], relres=st["relres_true"],
-                             converged=st["converged"], u=u)
+        for pc in preconds:
+            sfx = "_pc" if pc else ""
+            # warm both paths once (graph capture, workspaces)
+            plan.solve(f, precond=pc)
+            u0, _ = net.guess(plan, f)
+            plan.solve(f, u=u0.clone(), precond=pc)
+            for mode in ("zero", "guess"):
+                if fl is not None:
+                    fl.zero_()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                if mode == "zero":
+                    u, st = plan.solve(f, precond=pc)
+                else:
+                    u0, _ = net.guess(plan, f)
+                    u, st = plan.solve(f, u=u0, precond=pc)
+                e1.record(stream)
+                e1.synchronize()
+                res[mode + sfx] = dict(ms=e0.elapsed_time(e1), iters=st["iters"], outer=st["outer"],
+                                       relres=st["relres_true"], converged=st["converged"], u=u)
+            res["diff" + sfx] = float(
+                torch.linalg.vector_norm(torch.view_as_real(res["zero" + sfx]["u"] - res["guess" + sfx]["u"])) /
+                torch.linalg.vector_norm(torch.view_as_real(res["zero" + sfx]["u"])))
+            del res["zero" + sfx]["u"], res["guess" + sfx]["u"]
         # initial residual of the guess
         u0, b = net.guess(plan, f)
         r = plan.apply_A(u0) - b
         res["guess_relres0"] = float(torch.linalg.vector_norm(torch.view_as_real(r)) /
                                      torch.linalg.vector_norm(torch.view_as_real(b)))
-        res["diff"] = float(torch.linalg.vector_norm(torch.view_as_real(res["zero"]["u"] - res["guess"]["u"])) /
-                            torch.linalg.vector_norm(torch.view_as_real(res["zero"]["u"])))
-        del res["zero"]["u"], res["guess"]["u"]
         rows.append(res)
         plan.close()
     return rows
 
 
-def summarize(rows):
-    z_ms = np.array([r["zero"]["ms"] for r in rows])
-    g_ms = np.array([r["guess"]["ms"] for r in rows])
-    z_it = np.array([r["zero"]["iters"] for r in rows])
-    g_it = np.array([r["guess"]["iters"] for r in rows])
+def summarize(rows, sfx=""):
+    """Means over the instances of one preconditioner setting (sfx "" or "_pc")."""
+    z_ms = np.array([r["zero" + sfx]["ms"] for r in rows])
+    g_ms = np.array([r["guess" + sfx]["ms"] for r in rows])
+    z_it = np.array([r["zero" + sfx]["iters"] for r in rows])
+    g_it = np.array([r["guess" + sfx]["iters"] for r in rows])
     r0 = np.array([r["guess_relres0"] for r in rows])
     return dict(count=len(rows), zero_ms=float(z_ms.mean()), guess_ms=float(g_ms.mean()),
                 zero_iters=float(z_it.mean()), guess_iters=float(g_it.mean()),
-                guess_relres0_median=float(np.median(r0)), time_ratio=float(g_ms.mean() / z_ms.mean()),
-                all_converged=bool(all(r["zero"]["converged"] and r["guess"]["converged"] for r in rows)),
-                max_solution_diff=float(max(r["diff"] for r in rows)))
+                guess_relres0_median=float(np.median(r0)), guess_relres0_p10=float(np.percentile(r0, 10)),
+                guess_relres0_p90=float(np.percentile(r0, 90)), time_ratio=float(g_ms.mean() / z_ms.mean()),
+                fewer_iters_frac=float(np.mean(g_it < z_it)), more_iters_frac=float(np.mean(g_it > z_it)),
+                all_converged=bool(all(r["zero" + sfx]["converged"] and r["guess" + sfx]["converged"] for r in rows)),
+                max_solution_diff=float(max(r["diff" + sfx] for r in rows)))

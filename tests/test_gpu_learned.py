@@ -95,3 +95,33 @@ def test_guess_handle_load_and_apply(tmp_path):
     assert ei.value.status == B.RTE_EINVAL
     p.close()
     net.close()
+
+
+def test_multiscale_features_are_tile_means_of_b():
+    """The network input of a multi-scale net (32 channels at L = 2): channels
+    2L+5.. hold the 8 x 8 and 32 x 32 tile means of the scaled b channels
+    (n = 48: partial 32-tiles at the border average their own cells)."""
+    from paper_1802_03061_gb300 import Plan
+    from paper_1802_03061_gb300 import _binding as B
+    n, L = 48, 2
+    nch = 2 * L + 1
+    d = rte_synth.learned_guess_instance(3, n=n, L=L)
+    p = Plan(n, mu_t=d["mu_t"], mu_s=d["mu_s"], sigma_hat=d["sigma_hat"], prec="mixed_fp32")
+    f = torch.from_numpy(d["f"]).cuda()
+    b = p.rhs(f)
+    X = torch.empty((n, n, 32), dtype=torch.bfloat16, device="cuda")
+    B.rte_guess_features(p.handle, 32, f.data_ptr(), b.data_ptr(), X.data_ptr())
+    Xh = X.float().cpu().numpy()
+    bh = b.cpu().numpy()
+    chans = [bh[0].real] + [v for k in range(1, L + 1) for v in (bh[k].real, bh[k].imag)]
+    s_b = np.sqrt(sum((c ** 2).sum() for c in chans) / (nch * n * n))
+    for c, ch in enumerate(chans):
+        sc = ch / s_b
+        assert np.abs(Xh[..., c] - sc).max() <= 1e-2 * np.abs(sc).max() + 1e-6
+        for t, off in ((8, nch + 4), (32, 2 * nch + 4)):
+            want = np.zeros_like(sc)
+            for y0 in range(0, n, t):
+                for x0 in range(0, n, t):
+                    want[y0:y0 + t, x0:x0 + t] = sc[y0:y0 + t, x0:x0 + t].mean()
+            assert np.abs(Xh[..., off + c] - want).max() <= 1e-2 * np.abs(sc).max() + 1e-6
+    p.close()
