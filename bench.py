@@ -367,7 +367,15 @@ def run_native(args):
 # from the ncu capture summarised in profiles/matvec_hg2d_transport_256_L8.md.
 # Valid only for the kernel versions that capture measured and for this shape
 # and precision (the roofline reports null otherwise).
-MATVEC_NCU = {}
+MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4751872 + 26899200 + 13705728,
+                                            "insts": 3634192 + 9583273 + 3405120,
+                                            "col_dram_bytes": 26899200, "col_insts": 9583273}}
+
+
+# the same for the five FP32 passes of the 128^3 application
+# (profiles/passes_iso3d_diffusion_128.md)
+ISO3D_NCU = {"dram_bytes": 8406272 + 16921600 + 42419712 + 33829888 + 25313536,
+             "insts": 7090176 + 9279744 + 23612160 + 9230208 + 6263808}
 
 
 def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):
@@ -649,8 +657,12 @@ def run_iso3d(args):
                        "l2": "flushed before every timed step"},
             "roofline": {"kernel": "3D FP32 K application (5 passes)", "bound": "hbm",
                          "achieved": alg32 / (mv32 * 1e-3) / 1e9, "peak": hbm,
-                         "frac": alg32 / (mv32 * 1e-3) / 1e9 / hbm, "unit": "GB/s", "traffic": None,
-                         "peak_source": src, "algorithmic_bytes_per_launch": alg32},
+                         "frac": alg32 / (mv32 * 1e-3) / 1e9 / hbm, "unit": "GB/s",
+                         "traffic": ISO3D_NCU["dram_bytes"] if n == 128 else None,
+                         "issue": (ISO3D_NCU["insts"] / (152 * 4 * (clk.get("sm_mhz") or 2070.0) * 1e6) /
+                                   (mv32 * 1e-3)) if n == 128 else None,
+                         "peak_source": src, "algorithmic_bytes_per_launch": alg32, "ms_per_launch": mv32,
+                         "algorithmic_bytes": "2 n^3 4 + (Q/2+1)^3 4: field in and out, FP32 octant spectrum"},
             "gpu_launches": int(launches), "clocks": clk}
     plan.close()
     print(json.dumps(line))
@@ -1134,6 +1146,45 @@ def run_profile_solve(args):
     plan.close()
 
 
+def run_profile_kernels(args):
+    """A short, fixed launch sequence for ncu captures of single kernels:
+    two FP32 K applications each of the 256^2, L = 8 plan (row, column,
+    inverse row passes) and of the 128^3 plan (five passes), then two forward
+    passes of the learned guess network (6 layers, 32 inputs) on 4 x 256^2
+    pixels."""
+    import torch
+
+    import rte_synth
+    from paper_1802_03061_gb300 import Plan, learned
+    from paper_1802_03061_gb300 import _binding as B
+    from paper_1802_03061_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    base = rte_synth.hg2d_transport()
+    p = Plan(base["n"], mu_t=base["mu_t"], mu_s=base["mu_s"], sigma_hat=base["sigma_hat"], prec="mixed_fp32")
+    x = p.empty(fp32=True).normal_()
+    for _ in range(2):
+        p.apply_K32(x)
+    torch.cuda.synchronize()
+    p.close()
+    pr = rte_synth.iso3d_diffusion()
+    p3 = Plan(pr["n"], mu_t=pr["mu_t"], mu_s=pr["mu_s"], sigma_hat=[1.0], dim=3, prec="mixed_fp32")
+    x3 = p3.empty(fp32=True).normal_()
+    for _ in range(2):
+        p3.apply_K32(x3)
+    torch.cuda.synchronize()
+    p3.close()
+    net = learned.GuessNet(L=4, depth=6, seed=1)
+    X = torch.randn((4, 256, 256, net.cin), device="cuda").to(torch.bfloat16)
+    Y = torch.empty((4, 256, 256, net.cout), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        B.rte_cnn_forward(net.handle, X.data_ptr(), 4, 256, 256, Y.data_ptr())
+    torch.cuda.synchronize()
+    net.close()
+    print(json.dumps({"profile_kernels": "done"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1155,6 +1206,8 @@ def main():
     ap.add_argument("--train", type=int, default=1024, help="learned workload: training instances")
     ap.add_argument("--epochs", type=int, default=4, help="learned workload: training epochs")
     ap.add_argument("--profile-solve", action="store_true", help="one warm-up and one solve only (for ncu)")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="two launches of the c2 and c3 FP32 passes and of the guess network (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         ws, rank, _ = dist_env()
@@ -1164,6 +1217,9 @@ def main():
         return
     if args.profile_solve:
         run_profile_solve(args)
+        return
+    if args.profile_kernels:
+        run_profile_kernels(args)
         return
     if args.workload == "inhom":
         return run_inhom(args)

@@ -85,9 +85,9 @@ __device__ __forceinline__ void conv_tc_stage_w(uint8_t* Wb, const bf16* __restr
     const bf16* wt = Wk + (long)tap * NOUT * CX;
     for (int c = tid; c < NOUT * KC; c += 128) {
         const int nr = c / KC, kc = c - nr * KC;
-        const uint4 v = *reinterpret_cast<const uint4*>(wt + (long)nr * CX + kc * 8);
-        *reinterpret_cast<uint4*>(Wb + ((nr >> 3) * KC + kc) * 128 + (nr & 7) * 16) = v;
+        cp_async16(Wb + ((nr >> 3) * KC + kc) * 128 + (nr & 7) * 16, wt + (long)nr * CX + kc * 8, 16);
     }
+    cp_async_wait_all();
 }
 
 template <int CX, int NOUT>
@@ -112,15 +112,16 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, con
         mbar_fence_init();
     }
     // the input rows (consecutive threads: consecutive 16-byte chunks of a pixel, then pixels)
+    // (asynchronous 16-byte copies, zero-filled outside the image: all of a
+    // thread's copies are in flight at once)
     for (int c = tid; c < 3 * CONV_TC_PX * KC; c += 128) {
         const int kc = c % KC, px = (c / KC) % CONV_TC_PX, r = c / (KC * CONV_TC_PX);
         const int yy = y + r - 1, xx = x0 + px - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
-            v = *reinterpret_cast<const uint4*>(X + (((long)b * H + yy) * Wd + xx) * CX + kc * 8);
-        *reinterpret_cast<uint4*>(In + ((r * KC + kc) * CONV_TC_PX + px) * 16) = v;
+        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+        const bf16* src = in ? X + (((long)b * H + yy) * Wd + xx) * CX + kc * 8 : X;
+        cp_async16(In + ((r * KC + kc) * CONV_TC_PX + px) * 16, src, in ? 16u : 0u);
     }
-    conv_tc_stage_w<CX, NOUT>(Wbuf, Wk, 0, tid);
+    conv_tc_stage_w<CX, NOUT>(Wbuf, Wk, 0, tid);  // waits for all of this thread's copies
     fence_async_smem();
     tc_fence_before();
     __syncthreads();

@@ -40,8 +40,14 @@ __host__ __device__ __forceinline__ int pc_row(int Q) { return Q / 2 + 8; }
 // of wfreq<R>
 template <int R> __device__ __forceinline__ int wslot(int xi) {
     using W = wfft_shape<R>;
-    const int b = (int)(__brev((unsigned)(xi / (R * R))) >> (32 - W::LP));
-    return ((xi / R) % R) * 32 + (((xi % R) << W::LP) | b);
+    const int g = xi % R, kap = (xi / R) % R, c = xi / (R * R);
+    if constexpr (R >= W::P) {
+        // register P t + c of lane P g + b holds kappa' = b + P t
+        return (W::P * (kap / W::P) + c) * 32 + ((g << W::LP) | (kap % W::P));
+    } else {
+        const int b = (int)(__brev((unsigned)c) >> (32 - W::LP));
+        return kap * 32 + ((g << W::LP) | b);
+    }
 }
 
 // 3D: S3p = (1/Q^3) / (1 - mu_s Q^3 S3)  (S3 already holds FFT(g) / Q^3)

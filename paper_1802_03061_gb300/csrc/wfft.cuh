@@ -129,20 +129,26 @@ template <int R> struct wfft_shape {
     static constexpr int SCRATCH = R * ST;                      // scratch elements per warp (Q + 32)
 };
 
-// frequency held by register j of lane L after the forward transform
-template <int R> __device__ __forceinline__ int wfreq(int j, int lane) {
-    using W = wfft_shape<R>;
-    const int b = lane & (W::P - 1);
-    const int c = (int)(__brev((unsigned)b) >> (32 - W::LP));
-    return (lane >> W::LP) + R * (j + R * c);
+// frequency held by register j of lane L = P g + b after the forward
+// transform.  R >= P (R = 8, 16): register j = P t + c holds
+// X[g + R (kappa' + R c)] with kappa' = b + P t (the P-point DFTs of the last
+// step run in registers after a transpose); R < P: register j holds
+// X[g + R (j + R brev(b))] (the last step runs as lane stages).
+__host__ __device__ __forceinline__ int wfreq_map(int R, int j, int lane) {
+    const int P = 32 / R;
+    const int LP = R == 16 ? 1 : R == 8 ? 2 : R == 4 ? 3 : 4;
+    const int g = lane >> LP, b = lane & (P - 1);
+    if (R >= P) {
+        const int t = j / P, c = j % P;
+        return g + R * ((b + P * t) + R * c);
+    }
+    int c = 0;
+    for (int i = 0; i < LP; ++i) c |= ((b >> i) & 1) << (LP - 1 - i);
+    return g + R * (j + R * c);
 }
+template <int R> __device__ __forceinline__ int wfreq(int j, int lane) { return wfreq_map(R, j, lane); }
 // the same with R known at run time (plan-time permutations)
-__device__ __forceinline__ int wfreq_rt(int R, int j, int lane) {
-    const int P = 32 / R, LP = __ffs(P) - 1;
-    const int b = lane & (P - 1);
-    const int c = (int)(__brev((unsigned)b) >> (32 - LP));
-    return (lane >> LP) + R * (j + R * c);
-}
+__device__ __forceinline__ int wfreq_rt(int R, int j, int lane) { return wfreq_map(R, j, lane); }
 
 // frequency of slot sl (= j * 32 + lane) of the column passes' spectra.
 // Q <= 512: the warp FFT's own order.  Q = 1024 runs as two 512-point warp
@@ -154,9 +160,58 @@ __device__ __forceinline__ int slot_freq(int sl, int Q) {
     return 2 * wfreq_rt(16, s >> 5, s & 31) + r;
 }
 
+// P-point DFT (P = 2, 4) in registers
+template <int P, int DIR, typename T> __device__ __forceinline__ void dft_small(T* u) {
+    if constexpr (P == 2) bfly2<DIR>(u);
+    if constexpr (P == 4) bfly4<DIR>(u);
+}
+
+// last step for R >= P: lane L = P g + b holds Y[g][b][kappa'] in v[kappa'];
+// the P-point DFTs over b (one per kappa') are gathered by a transpose in the
+// warp's scratch (lane rows of R + 1: conflict-free 8-byte accesses), lane
+// (g, b') computing those of kappa' = b' + P t; v[P t + c] = output c.  The
+// scratch needs 32 (R + 1) = R (32 + P) elements, the same as step 1's.
+template <int R, int DIR, typename T> __device__ __forceinline__ void warp_last_regs(T* v, T* S, int lane) {
+    using W = wfft_shape<R>;
+    constexpr int P = W::P, RS = R + 1;
+    const int g = lane >> W::LP, b = lane & (P - 1);
+#pragma unroll
+    for (int j = 0; j < R; ++j) S[lane * RS + j] = v[j];
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < R / P; ++t) {
+        T u[P];
+#pragma unroll
+        for (int bb = 0; bb < P; ++bb) u[bb] = S[(g * P + bb) * RS + b + P * t];
+        dft_small<P, DIR>(u);
+#pragma unroll
+        for (int c = 0; c < P; ++c) v[P * t + c] = u[c];
+    }
+    __syncwarp();
+}
+// its inverse: v[P t + c] -> lane (g, b) holds P Y[g][b][kappa'] in v[kappa']
+template <int R, typename T> __device__ __forceinline__ void warp_first_regs_inv(T* v, T* S, int lane) {
+    using W = wfft_shape<R>;
+    constexpr int P = W::P, RS = R + 1;
+    const int g = lane >> W::LP, b = lane & (P - 1);
+#pragma unroll
+    for (int t = 0; t < R / P; ++t) {
+        T u[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) u[c] = v[P * t + c];
+        dft_small<P, 1>(u);
+#pragma unroll
+        for (int bb = 0; bb < P; ++bb) S[(g * P + bb) * RS + b + P * t] = u[bb];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = S[lane * RS + j];
+    __syncwarp();
+}
+
 // forward: v[r] = x[lane + 32 r]  ->  v[j] = X[wfreq<R>(j, lane)]
 // tw: table exp(-2 pi i t / Q); S: this warp's scratch (wfft_shape<R>::SCRATCH
-// elements of shared memory)
+// elements of shared memory), free again when the call returns
 template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, const T* tw, T* S) {
     using W = wfft_shape<R>;
     const int lane = threadIdx.x & 31;
@@ -173,16 +228,26 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, 
     dft_regs<R, -1>(v);
 #pragma unroll
     for (int j = 1; j < R; ++j) v[j] = cmul(v[j], twid<-1>(tw, b * j * R));
+    if constexpr (R >= W::P) {
+        warp_last_regs<R, -1>(v, S, lane);
+    } else {
 #pragma unroll
-    for (int h = W::P / 2; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
+        for (int h = W::P / 2; h >= 1; h >>= 1) lane_stage_fwd<R>(v, tw, h, lane);
+    }
 }
 
 // inverse (unnormalised): v[j] = X[wfreq<R>(j, lane)]  ->  v[r] = Q x[lane + 32 r]
+// (S must be free on entry: the caller synchronises the warp after its own
+// last use of it)
 template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, const T* tw, T* S) {
     using W = wfft_shape<R>;
     const int lane = threadIdx.x & 31;
+    if constexpr (R >= W::P) {
+        warp_first_regs_inv<R>(v, S, lane);
+    } else {
 #pragma unroll
-    for (int h = 1; h <= W::P / 2; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
+        for (int h = 1; h <= W::P / 2; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
+    }
     const int g = lane >> W::LP, b = lane & (W::P - 1);
 #pragma unroll
     for (int j = 1; j < R; ++j) v[j] = cmul(v[j], twid<1>(tw, b * j * R));
