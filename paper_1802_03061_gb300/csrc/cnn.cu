@@ -1,10 +1,10 @@
 // Learned initial guess for the GMRES solve (task extension; the paper has
 // no counterpart): a small 3x3 convolutional network, NHWC BF16 activations,
 // FP32 accumulation on the BF16 tensor cores, trained on the GPU by its own
-// forward / data-gradient / weight-gradient kernels and Adam.  The forward
-// and data-gradient convolutions run on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in TMEM, k_conv_tc); the weight gradient, a
-// reduction over pixels, on warp-level mma.sync (k_conv_wgrad).
+// forward / data-gradient / weight-gradient kernels and Adam.  All three
+// convolution products run on the 5th-generation tensor cores (tcgen05.mma,
+// accumulators in TMEM): k_conv_tc (forward and data gradient, K-major
+// operands) and k_conv_wgrad_tc (weight gradient, M/N-major operands).
 //
 // Layer l: Y = act(conv3x3(X, W_l) + bias_l), same padding (zeros outside the
 // image), channel counts padded to multiples of 16.  Weights W_l[tap][cin][cout]
@@ -30,18 +30,8 @@
 typedef __nv_bfloat16 bf16;
 
 #define CNN_TILE 128       // pixels per block (along x)
-#define CNN_WARPS 4        // 32 pixels per warp
-#define CNN_APAD 24        // smem row pitch (bf16) for 16-wide k slices: conflict-free fragments
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 // ---------------------------------------------------------------------------
 // forward / data-gradient convolution on tcgen05 tensor cores
@@ -211,90 +201,157 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, con
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient partials: part[blk][tap][ci][co] = sum over the block's
-// pixels of X[p + d(tap)][ci] * dY[p][co]; grid (nblk_pix, 9), block 128.
-// Each block reduces over PIXB pixels (rows of Wd pixels, whole rows).
+// weight gradient on tcgen05: dW[tap][ci][co] = sum_p X[p + d(tap)][ci] dY[p][co]
+// GEMM with M = (tap row, ci), N = co, K = pixels.  Both operands are
+// M/N-major in their natural NHWC order (for a pixel, the channels are
+// contiguous), staged like the forward's input tile: per channel chunk a run
+// of pixels at a 16-byte stride.  RST = 128 / CI consecutive staged input rows
+// form one M = 128 operand (the row stride of the staged tile is KC x 130 x 16
+// bytes = KC x the chunk stride, so M blocks run on through the next row); G
+// such groups cover the rows y - 1, y, y + 1 (staged rows beyond y + 1 are
+// zeros and their results are dropped); the three x shifts dx are three start
+// addresses.  So one CTA holds 3 G accumulators of 128 x CO in TMEM and, for
+// each 128-pixel tile of its share, issues 3 G x 8 MMAs (K = 16 pixels each),
+// with the next tile's staging (cp.async) overlapping them (two stages, an
+// mbarrier per stage signalled by tcgen05.commit).  Partial sums per CTA go to
+// part[cta][tap][ci][co] (reduced in a fixed order by k_reduce_parts).
+// grid: CTAs over the B x H x ceil(W/128) tiles, 128 threads.
 // ---------------------------------------------------------------------------
+template <int CI, int CO> struct WgTc {
+    static constexpr int KCI = CI / 8, KCO = CO / 8;
+    static constexpr int RST = 128 / CI;             // staged rows per M = 128 group
+    static constexpr int G = (3 + RST - 1) / RST;    // groups covering dy = -1, 0, 1
+    static constexpr int S = G * RST;                // staged input rows
+    static constexpr int X_BYTES = S * KCI * CONV_TC_PX * 16;
+    static constexpr int Y_BYTES = KCO * 128 * 16;
+    static constexpr int STAGE = X_BYTES + Y_BYTES;
+    static constexpr int NACC = 3 * G;
+    static constexpr int NCOLS = NACC * CO <= 32 ? 32 : NACC * CO <= 64 ? 64 : NACC * CO <= 128 ? 128
+                                 : NACC * CO <= 256 ? 256 : 512;
+    static constexpr int PAD = 233472 / (512 / NCOLS + 1) + 1;  // no more resident CTAs than TMEM allows
+    static constexpr int NEED = 2 * STAGE + 1024;
+    static constexpr int SMEM = NEED > PAD ? NEED : PAD;
+};
+
 template <int CI, int CO>
-__global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY,
-                                                    float* __restrict__ part, int B, int H, int Wd, int rows_per_blk) {
-    // As: [ci][16 pixels], Bs: [co][16 pixels]
-    __shared__ __align__(16) bf16 As[CI * CNN_APAD];
-    __shared__ __align__(16) bf16 Bs[CO * CNN_APAD];
-    const int tap = blockIdx.y;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    // warp tiling of the CI x CO output: MT m-tiles (16) x NT n-tiles (8) per warp
-    constexpr int MTOT = CI / 16, NTOT = CO / 8;
-    constexpr int WM = (MTOT >= 2) ? 2 : 1;           // warps along m
-    constexpr int WN = CNN_WARPS / WM;                // warps along n
-    constexpr int MT = MTOT / WM, NT = NTOT / WN;
-    float acc[MT][NT > 0 ? NT : 1][4];
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < (NT > 0 ? NT : 1); ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const int wm = warp % WM, wn = warp / WM;
-    const long rows_total = (long)B * H;
-    const long r0 = (long)blockIdx.x * rows_per_blk;
-    for (long rr = r0; rr < r0 + rows_per_blk && rr < rows_total; ++rr) {
-        const int b = (int)(rr / H), y = (int)(rr % H);
-        const int yy = y + dy;
-        for (int x0 = 0; x0 < Wd; x0 += 16) {
-            __syncthreads();
-            for (int e = threadIdx.x; e < 16 * CI; e += blockDim.x) {
-                const int k = e / CI, ci = e % CI;
-                const int x = x0 + k, xx = x + dx;
-                bf16 v = __float2bfloat16(0.f);
-                if (x < Wd && yy >= 0 && yy < H && xx >= 0 && xx < Wd) v = X[(((long)b * H + yy) * Wd + xx) * CI + ci];
-                As[ci * CNN_APAD + k] = v;
+__global__ void __launch_bounds__(128) k_conv_wgrad_tc(const bf16* __restrict__ X, const bf16* __restrict__ dY,
+                                                       float* __restrict__ part, int B, int H, int Wd,
+                                                       int* __restrict__ err) {
+    using C = WgTc<CI, CO>;
+    constexpr int KCI = C::KCI, KCO = C::KCO;
+    extern __shared__ uint8_t smraw[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int xt_n = (Wd + 127) / 128;
+    const long ntiles = (long)B * H * xt_n;
+    if (warp == 0) tc_alloc(&tslot, C::NCOLS);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, CO, true);
+    bool ok = true;
+    int i = 0;  // local tile count
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int st = i & 1;
+        uint8_t* Xs = sbase + st * C::STAGE;
+        uint8_t* Ys = Xs + C::X_BYTES;
+        if (i >= 2) {
+            int bad = 0;
+            if (tid == 0) bad = !mbar_wait(&mbar[st], ((i - 2) >> 1) & 1, CONV_TC_POLLS);
+            if (__syncthreads_or(bad)) {
+                ok = false;
+                break;
             }
-            for (int e = threadIdx.x; e < 16 * CO; e += blockDim.x) {
-                const int k = e / CO, co = e % CO;
-                const int x = x0 + k;
-                bf16 v = __float2bfloat16(0.f);
-                if (x < Wd) v = dY[(((long)b * H + y) * Wd + x) * CO + co];
-                Bs[co * CNN_APAD + k] = v;
-            }
-            __syncthreads();
-            if (NT > 0) {
+        }
+        fence_async_smem();
+        const int xt = (int)(t % xt_n);
+        const long by = t / xt_n;
+        const int y = (int)(by % H), b = (int)(by / H);
+        const int x0 = xt * 128;
+        // input rows y - 1 .. y - 1 + S - 1 (those past y + 1 are not needed: zeros)
+        for (int c = tid; c < C::S * CONV_TC_PX * KCI; c += 128) {
+            const int kc = c % KCI, px = (c / KCI) % CONV_TC_PX, r = c / (KCI * CONV_TC_PX);
+            const int yy = y + r - 1, xx = x0 + px - 1;
+            const bool in = r < 3 && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+            const bf16* src = in ? X + (((long)b * H + yy) * Wd + xx) * CI + kc * 8 : X;
+            cp_async16(Xs + ((r * KCI + kc) * CONV_TC_PX + px) * 16, src, in ? 16u : 0u);
+        }
+        // output-gradient row y, pixels x0 .. x0 + 127
+        for (int c = tid; c < 128 * KCO; c += 128) {
+            const int kc = c % KCO, px = c / KCO;
+            const int xx = x0 + px;
+            const bool in = xx < Wd;
+            const bf16* src = in ? dY + (((long)b * H + y) * Wd + xx) * CO + kc * 8 : dY;
+            cp_async16(Ys + (kc * 128 + px) * 16, src, in ? 16u : 0u);
+        }
+        cp_async_wait_all();
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t xa = smem_u32(Xs), ya = smem_u32(Ys);
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    uint32_t af[4];
-                    const int r = (wm * MT + mt) * 16 + g;
-                    af[0] = ld32(As + r * CNN_APAD + 2 * t);
-                    af[1] = ld32(As + (r + 8) * CNN_APAD + 2 * t);
-                    af[2] = ld32(As + r * CNN_APAD + 2 * t + 8);
-                    af[3] = ld32(As + (r + 8) * CNN_APAD + 2 * t + 8);
+            for (int g = 0; g < C::G; ++g)
 #pragma unroll
-                    for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt) {
-                        uint32_t bfr[2];
-                        const int n = (wn * NT + nt) * 8 + g;
-                        bfr[0] = ld32(Bs + n * CNN_APAD + 2 * t);
-                        bfr[1] = ld32(Bs + n * CNN_APAD + 2 * t + 8);
-                        mma_bf16(acc[mt][nt], af, bfr);
+                for (int dxi = 0; dxi < 3; ++dxi) {
+                    const uint32_t acc = tmem + (uint32_t)((g * 3 + dxi) * CO);
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks) {
+                        // A: M blocks = channel chunks (then the next staged row) at 130 x 16 bytes,
+                        // K blocks = 8 pixels at 128 bytes; staged pixel p + dx + 1 for pixel p
+                        const uint64_t ad = tc_desc_kmajor(
+                            xa + (uint32_t)((g * C::RST * KCI) * CONV_TC_PX + 16 * ks + dxi) * 16, 128,
+                            CONV_TC_PX * 16);
+                        // B: N blocks = channel chunks at 128 x 16 bytes, K blocks at 128 bytes
+                        const uint64_t bd = tc_desc_kmajor(ya + (uint32_t)(16 * ks) * 16, 128, 128 * 16);
+                        tc_mma_bf16(acc, ad, bd, IDESC, (i > 0 || ks > 0) ? 1u : 0u);
                     }
                 }
+            tc_commit(&mbar[st]);
+        }
+    }
+    // wait for the last tile's commit (it covers every MMA) and for the other
+    // stage's last arrival, so that none is pending at exit
+    if (i > 0) {
+        int bad = 0;
+        if (tid == 0) {
+            const int il = i - 1;
+            bad = !mbar_wait(&mbar[il & 1], (il >> 1) & 1, CONV_TC_POLLS);
+            if (!bad && il >= 1) bad = !mbar_wait(&mbar[(il - 1) & 1], ((il - 1) >> 1) & 1, CONV_TC_POLLS);
+        }
+        if (__syncthreads_or(bad)) ok = false;
+    }
+    tc_fence_after();
+    // epilogue: TMEM lane m = 32 warp + lane is row (r_local = m / CI, ci = m % CI)
+    const int m = warp * 32 + lane;
+    const int rl = m / CI, ci = m % CI;
+    for (int g = 0; g < C::G; ++g) {
+        const int dy = g * C::RST + rl - 1;
+        for (int dxi = 0; dxi < 3; ++dxi) {
+            float v[CO];
+#pragma unroll
+            for (int c0 = 0; c0 < CO; c0 += 16)
+                tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((g * 3 + dxi) * CO + c0), v + c0);
+            if (ok && i > 0 && dy >= -1 && dy <= 1) {
+                const int tap = (dy + 1) * 3 + dxi;
+                float* dst = part + (((long)blockIdx.x * 9 + tap) * CI + ci) * CO;
+#pragma unroll
+                for (int co = 0; co < CO; co += 4) *reinterpret_cast<float4*>(dst + co) = make_float4(v[co], v[co + 1], v[co + 2], v[co + 3]);
             }
         }
     }
-    float* dst = part + ((long)blockIdx.x * 9 + tap) * CI * CO;
-    if (NT > 0) {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt) {
-                const int r = (wm * MT + mt) * 16 + g;
-                const int n = (wn * NT + nt) * 8 + 2 * t;
-                dst[r * CO + n] = acc[mt][nt][0];
-                dst[r * CO + n + 1] = acc[mt][nt][1];
-                dst[(r + 8) * CO + n] = acc[mt][nt][2];
-                dst[(r + 8) * CO + n + 1] = acc[mt][nt][3];
-            }
-    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, C::NCOLS);
+    if (!ok && lane == 0) atomicExch(err, 1);
 }
 
 // dW[i] = sum_b part[b][i] (fixed order), i < 9*CI*CO
@@ -562,6 +619,7 @@ struct rte_cnn_s {
     float* loss_part = nullptr;
     float* loss_host = nullptr;
     int* err = nullptr;        // set by a tensor-core convolution whose barrier wait gave up
+    int nsm = 152;             // SMs of the device (the weight gradient's CTA count)
     long step = 0;
 };
 
@@ -613,18 +671,37 @@ static cudaError_t conv_dgrad(const bf16* dY, const CnnLayer& Lr, bf16* dX, int 
     return conv_tc(Lr.cout, Lr.cin, dY, Lr.wb, 1, nullptr, 0, dX, nullptr, B, H, W, err, s);
 }
 
+template <int CI, int CO>
+static cudaError_t launch_wgrad_tc(int nb, const bf16* X, const bf16* dY, float* part, int B, int H, int W, int* err,
+                                   cudaStream_t s) {
+    using C = WgTc<CI, CO>;
+    static bool once = false;
+    if (!once) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::SMEM);
+        if (e != cudaSuccess) return e;
+        once = true;
+    }
+    k_conv_wgrad_tc<CI, CO><<<nb, 128, C::SMEM, s>>>(X, dY, part, B, H, W, err);
+    return cudaGetLastError();
+}
+
+// dW = sum over pixels of X[p + d(tap)] dY[p]^T on tcgen05 (k_conv_wgrad_tc),
+// one CTA per SM at most (partials reduced in a fixed order)
 static cudaError_t conv_wgrad(rte_cnn c, const bf16* X, const bf16* dY, CnnLayer& Lr, int B, int H, int W,
                               cudaStream_t s) {
-    const int nb = nblk_pix(B, H);
+    const long tiles = (long)B * H * ((W + 127) / 128);
+    const int nb = (int)(tiles < c->nsm ? tiles : c->nsm);
     const long per = 9L * Lr.cin * Lr.cout;
     if ((long)nb * per > c->part_cap) return cudaErrorInvalidValue;
-    dim3 grid(nb, 9);
-    if (Lr.cin == 64 && Lr.cout == 64) k_conv_wgrad<64, 64><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
-    else if (Lr.cin == 16 && Lr.cout == 64) k_conv_wgrad<16, 64><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
-    else if (Lr.cin == 32 && Lr.cout == 64) k_conv_wgrad<32, 64><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
-    else if (Lr.cin == 64 && Lr.cout == 16) k_conv_wgrad<64, 16><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
-    else if (Lr.cin == 64 && Lr.cout == 32) k_conv_wgrad<64, 32><<<grid, 128, 0, s>>>(X, dY, c->part, B, H, W, 16);
+    cudaError_t e;
+    if (Lr.cin == 64 && Lr.cout == 64) e = launch_wgrad_tc<64, 64>(nb, X, dY, c->part, B, H, W, c->err, s);
+    else if (Lr.cin == 16 && Lr.cout == 64) e = launch_wgrad_tc<16, 64>(nb, X, dY, c->part, B, H, W, c->err, s);
+    else if (Lr.cin == 32 && Lr.cout == 64) e = launch_wgrad_tc<32, 64>(nb, X, dY, c->part, B, H, W, c->err, s);
+    else if (Lr.cin == 64 && Lr.cout == 16) e = launch_wgrad_tc<64, 16>(nb, X, dY, c->part, B, H, W, c->err, s);
+    else if (Lr.cin == 64 && Lr.cout == 32) e = launch_wgrad_tc<64, 32>(nb, X, dY, c->part, B, H, W, c->err, s);
     else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
     k_reduce_parts<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(c->part, nb, per, Lr.gw);
     k_bias_grad<<<Lr.cout, 256, 0, s>>>(dY, (long)B * H * W, Lr.cout, Lr.gb);
     rte_count_launches(3);
@@ -662,7 +739,7 @@ static rte_status cnn_ensure(rte_cnn c, int B, int H, int W) {
         cudaGetLastError();
         return RTE_ENOMEM;
     }
-    c->part_cap = (long)nblk_pix(B, H) * 9 * 64 * 64;
+    c->part_cap = (long)c->nsm * 9 * 64 * 64;
     if (rte_dev_malloc((void**)&c->part, c->part_cap * sizeof(float)) != cudaSuccess ||
         rte_dev_malloc((void**)&c->loss_part, 1024 * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
@@ -693,6 +770,11 @@ extern "C" rte_status rte_cnn_create(rte_cnn* out, int cin, int width, int depth
     if (!out || depth < 2 || (cin != 16 && cin != 32) || (width != 64) || (cout != 16 && cout != 32)) return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     rte_cnn c = new rte_cnn_s();
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (c->nsm < 1) c->nsm = 1;
+    }
     c->cin = cin;
     c->width = width;
     c->depth = depth;

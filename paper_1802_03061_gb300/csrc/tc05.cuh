@@ -19,7 +19,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 // shared-memory matrix descriptor: start address, leading / stride byte
 // offsets (16-byte units), the fixed version field (bit 46) of the tcgen05
-// format, no swizzle
+// format, no swizzle.  K-major operands: leading = the K-adjacent core
+// stride, stride = the row-group (M or N) stride.  M/N-major operands (a
+// core matrix is then 8 K-rows of 8 consecutive M or N elements, 16 bytes
+// each, still 128 contiguous bytes): leading = the K-adjacent core stride,
+// stride = the M/N-adjacent core stride.
 __device__ __forceinline__ uint64_t tc_desc_kmajor(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -29,12 +33,15 @@ __device__ __forceinline__ uint64_t tc_desc_kmajor(uint32_t saddr, uint32_t lbo_
     return d;
 }
 
-// instruction descriptor of .kind::f16: BF16 A and B (both K-major), FP32
-// accumulator, M x N tile
-__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+// instruction descriptor of .kind::f16: BF16 A and B, FP32 accumulator,
+// M x N tile; mn_major: both operands M/N-major (the M or N index contiguous
+// in a core-matrix row) instead of K-major
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N, bool mn_major = false) {
     return (1u << 4)                       // accumulator format: F32
            | (1u << 7)                     // A format: BF16
            | (1u << 10)                    // B format: BF16
+           | (mn_major ? (1u << 15) : 0u)  // A major-ness
+           | (mn_major ? (1u << 16) : 0u)  // B major-ness
            | ((uint32_t)(N >> 3) << 17)    // N / 8
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
