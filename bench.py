@@ -1094,6 +1094,7 @@ def run_aniso3d(args):
     x32, y32 = x.float(), torch.empty((op.M, n, n, n), dtype=torch.float32, device="cuda")
     t = {}
     for name, fn in (("apply64_ms", lambda: B.rte_aniso3d_apply_K(op.handle, x.data_ptr(), y.data_ptr(), sp)),
+                     ("apply64e_ms", lambda: B.rte_aniso3d_apply_K64e(op.handle, x.data_ptr(), y.data_ptr(), sp)),
                      ("apply32_ms", lambda: B.rte_aniso3d_apply_K32(op.handle, x32.data_ptr(), y32.data_ptr(), sp))):
         for _ in range(3):
             fn()
@@ -1103,17 +1104,26 @@ def run_aniso3d(args):
         e1.record(stream)
         e1.synchronize()
         t[name] = e0.elapsed_time(e1) / 10
+    # roofline of the FP32 application (all five passes): the moments in and
+    # out once and the M(M+1)/2 FP32 spectra once
+    H = op.Q // 2 + 1
+    alg = 2 * op.M * n ** 3 * 4 + (op.M * (op.M + 1) // 2) * H ** 3 * 4
+    peak, src = peaks()
+    ach = alg / (t["apply32_ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "FP32 K application (5 launches)", "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "traffic": None, "algorithmic_bytes_per_launch": alg,
+            "peak_source": src}
     line = {"metric": "3D anisotropic RTE solves/s (spherical harmonics L = 2, FP64 residual 1e-8)",
             "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner, f64 refinement", "data": "synthetic",
+            "dtype": "f32 inner, float-float refinement", "data": "synthetic",
             "config": {"workload": "aniso3d_%d: %d^3 cells, L = 2 (M = 9), HG g = 0.8, mu_t = 20, mu_s = 18"
                                    % (n, n), "Q": op.Q, "iters": stats[-1]["iters"], "outer": stats[-1]["outer"],
                        "fp64_ms_per_solve": float(np.mean(fp64_ms)), "fp64_iters": fp64_iters,
                        "relres_true": stats[-1]["relres_true"], "converged": bool(stats[-1]["converged"]),
                        "plan_ms": stats[-1]["ms_pre"], **t,
                        "l2": "FP32 Krylov basis and FP64 vectors (%d MB) exceed L2" % ((41 * op.M * n ** 3 * 4) >> 20)},
-            "gpu_launches": int(launches), "clocks": clk}
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk}
     op.close()
     print(json.dumps(line))
 
@@ -1151,7 +1161,8 @@ def run_profile_kernels(args):
     two FP32 K applications each of the 256^2, L = 8 plan (row, column,
     inverse row passes) and of the 128^3 plan (five passes), then two forward
     passes of the learned guess network (6 layers, 32 inputs) on 4 x 256^2
-    pixels."""
+    pixels, then two FP32 and two float-float applications of the 64^3, L = 2
+    spherical-harmonic operator (five passes each)."""
     import torch
 
     import rte_synth
@@ -1182,6 +1193,15 @@ def run_profile_kernels(args):
         B.rte_cnn_forward(net.handle, X.data_ptr(), 4, 256, 256, Y.data_ptr())
     torch.cuda.synchronize()
     net.close()
+    from paper_1802_03061_gb300 import Aniso3D
+    an = Aniso3D(64, 20.0, 18.0, [1.0, 0.8, 0.64])
+    xa = torch.randn((an.M, 64, 64, 64), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        an.apply_K32(xa.float())
+    for _ in range(2):
+        an.apply_K64e(xa)
+    torch.cuda.synchronize()
+    an.close()
     print(json.dumps({"profile_kernels": "done"}))
 
 

@@ -369,10 +369,14 @@ rte_status rte_inhom_destroy(rte_inhom op);
  * Y_l^0 times sqrt(4 pi/(2l+1)).  L = 0 is the isotropic equation.
  * Fields: double (float for apply_K32) [M][n][n][n], x fastest, device memory;
  * the source f: double [n][n][n].  Applied with FFTs on the zero-padded Q^3
- * grid (Q = the smallest even 2^a 3^b >= 2n - 1), FP64 spectra for the FP64
- * calls, FP32 for apply_K32.  Limits: L <= 4, n <= 1024, and the M channels of
- * one Z line must fit in shared memory (RTE_EUNSUPPORTED otherwise; n = 128
- * takes L <= 4).  Inputs and outputs may not alias.
+ * grid: for 17 <= n <= 128 Q is the power of two 64, 128 or 256 >= 2n - 1 and
+ * each pass transforms all M channels in one launch with warp-register FFTs;
+ * otherwise Q is the smallest even 2^a 3^b >= 2n - 1 and the passes run channel
+ * by channel.  FP64 spectra for the FP64 calls, FP32 for apply_K32, a
+ * float-float copy of the FP64 spectra for apply_K64e.  Limits: L <= 4,
+ * n <= 1024, and the M channels of one Z line must fit in shared memory
+ * (RTE_EUNSUPPORTED otherwise; n = 128 takes L <= 4).  Inputs and outputs may
+ * not alias.
  * ------------------------------------------------------------------------- */
 typedef struct rte_aniso3d_s* rte_aniso3d;
 /* Computes D_ab and the M(M+1)/2 spectra on the device (synchronises). */
@@ -386,19 +390,28 @@ rte_status rte_aniso3d_info(rte_aniso3d op, int* M_out, int* Q_out);
 rte_status rte_aniso3d_pair_table(int L, int* out_host);
 /* D_ab, row-major M x M, into host memory. */
 rte_status rte_aniso3d_cell_weights(rte_aniso3d op, double* out_host);
-/* y = K x (FP64) / in FP32. */
+/* y = K x: native FP64 / FP64-accurate in float-float arithmetic on the FP32
+ * units (native FP64 when Q is not a power of two) / in FP32. */
 rte_status rte_aniso3d_apply_K(rte_aniso3d op, const double* x_dev, double* y_dev, void* cuda_stream);
+rte_status rte_aniso3d_apply_K64e(rte_aniso3d op, const double* x_dev, double* y_dev, void* cuda_stream);
 rte_status rte_aniso3d_apply_K32(rte_aniso3d op, const float* x_dev, float* y_dev, void* cuda_stream);
 /* b = K~^{.0} f (Sec. 3.3, T.1). */
 rte_status rte_aniso3d_rhs(rte_aniso3d op, const double* f_dev, double* b_dev, void* cuda_stream);
 /* (I - K) u = b (Sec. 3.3, T.2) until ||b - (I - K) u|| <= tol ||b|| (FP64
- * residual), zero start.  prec = RTE_PREC_FP64: restarted FP64 GMRES(restart)
- * (classical Gram-Schmidt twice); RTE_PREC_MIXED_FP32: refinement steps, each
- * an FP32 GMRES(restart) solve of (I - K) d = r/||r|| to max(1e-4, tol/(2 relres))
- * followed by u += ||r|| d and an FP64 residual.  RTE_ENOCONV after maxit
- * (inner) iterations, u holding the last iterate; RTE_EINVAL for another prec.
- * stats: iters (inner), outer (FP64: restart cycles; mixed: refinement steps),
- * converged, relres_true, ms_total, ms_pre = creation time.  Synchronises. */
+ * residual), zero start: the same device solver as rte_solve (one CUDA graph
+ * with device-side loop control; the host only launches it and reads the
+ * statistics).  prec = RTE_PREC_FP64: restarted FP64 GMRES(restart)
+ * (classical Gram-Schmidt twice), native FP64; RTE_PREC_MIXED_FP32: refinement
+ * steps, each an FP32 GMRES(restart) solve of (I - K) d = r/||r|| to
+ * max(1e-4, tol/(2 relres)) followed by u += ||r|| d and an FP64-accurate
+ * residual r = K~ (mu_s sigma_hat u + f) - u (float-float, native FP64 when Q
+ * is not a power of two).  restart 1..128.  RTE_ENOCONV after maxit (inner)
+ * iterations, u holding the last iterate; RTE_ENAN for a non-finite residual;
+ * RTE_EINVAL for another prec.  The first solve of a precision and restart
+ * allocates its workspace and builds its graph (RTE_ENOMEM on a failed
+ * allocation; a later call retries).  stats: iters (inner), outer (mixed:
+ * refinement steps; FP64: 0), converged, relres_true, ms_total (the graph),
+ * ms_pre = creation time.  Synchronises. */
 rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, double* u_dev, double tol, int restart,
                              int maxit, int prec, rte_stats* stats, void* cuda_stream);
 rte_status rte_aniso3d_destroy(rte_aniso3d op);

@@ -83,7 +83,7 @@ def lib():
         L.rte_aniso3d_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.rte_aniso3d_pair_table.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.rte_aniso3d_cell_weights.argtypes = [VP, ctypes.POINTER(ctypes.c_double)]
-        for name in ("rte_aniso3d_apply_K", "rte_aniso3d_apply_K32", "rte_aniso3d_rhs"):
+        for name in ("rte_aniso3d_apply_K", "rte_aniso3d_apply_K64e", "rte_aniso3d_apply_K32", "rte_aniso3d_rhs"):
             getattr(L, name).argtypes = [VP, VP, VP, VP]
         L.rte_aniso3d_solve.argtypes = [VP, VP, VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(rte_stats), VP]
@@ -260,6 +260,10 @@ def rte_aniso3d_cell_weights(op, M):
 
 def rte_aniso3d_apply_K(op, x, y, stream=0):
     _check(lib().rte_aniso3d_apply_K(op, VP(x), VP(y), VP(stream)), "rte_aniso3d_apply_K")
+
+
+def rte_aniso3d_apply_K64e(op, x, y, stream=0):
+    _check(lib().rte_aniso3d_apply_K64e(op, VP(x), VP(y), VP(stream)), "rte_aniso3d_apply_K64e")
 
 
 def rte_aniso3d_apply_K32(op, x, y, stream=0):

@@ -23,11 +23,8 @@
 
 #include <vector>
 
-#include "internal.h"
+#include "aniso3d.cuh"
 #include "op3d_passes.cuh"
-
-#define RTE_ANISO_MAX_L 4
-#define RTE_ANISO_MAX_M ((RTE_ANISO_MAX_L + 1) * (RTE_ANISO_MAX_L + 1))
 
 // Real orthonormal spherical harmonics of degree <= L at the unit vector
 // (x, y, z), no Condon-Shortley phase:
@@ -65,66 +62,16 @@ __device__ void sh_real(int L, double x, double y, double z, double* Y) {
     }
 }
 
-__host__ __device__ inline int chan_l(int a) {
-    int l = 0;
-    while ((l + 1) * (l + 1) <= a) ++l;
-    return l;
-}
-
-// parities of Y_{l,m} under x -> -x, y -> -y, z -> -z (+1 even, -1 odd)
-static void sh_parity(int a, int* px, int* py, int* pz) {
-    const int l = chan_l(a), m = a - l * l - l, am = m < 0 ? -m : m;
-    const int sm = (am & 1) ? -1 : 1;
-    *px = m >= 0 ? sm : -sm;
-    *py = m >= 0 ? 1 : -1;
-    *pz = ((l + am) & 1) ? -1 : 1;
-}
-
-// The channel-pair table: for a, b < M, pair index (a <= b numbered row by row)
-// | imaginary spectrum << 16 | odd in y << 17 | odd in z << 18, symmetric in
-// (a, b); pimag[pair] = the imaginary flag.
+// The channel-pair table (pair_info for every ordered pair, row-major);
+// pimag[pair] = the imaginary flag.
 static void aniso_pair_table(int M, int* pinfo, int* pimag) {
-    int pidx = 0;
     for (int a = 0; a < M; ++a)
-        for (int b = a; b < M; ++b) {
-            int ax, ay, az, bx, by, bz;
-            sh_parity(a, &ax, &ay, &az);
-            sh_parity(b, &bx, &by, &bz);
-            const int px = ax * bx, py = ay * by, pz = az * bz;
-            const int imag = (px * py * pz) < 0 ? 1 : 0;
-            const int info = pidx | (imag << 16) | ((py < 0) << 17) | ((pz < 0) << 18);
-            pinfo[a * M + b] = pinfo[b * M + a] = info;
-            pimag[pidx] = imag;
-            ++pidx;
+        for (int b = 0; b < M; ++b) {
+            const int info = pair_info(a, b, M);
+            pinfo[a * M + b] = info;
+            pimag[info & 0xffff] = (info >> 16) & 1;
         }
 }
-
-struct rte_aniso3d_s {
-    int n = 0, L = 0, M = 0, Q = 0, H = 0, np = 0, Bz64 = 0, Bz32 = 0;
-    double h = 0.0, mu_t = 0.0, mu_s = 0.0, ms_pre = 0.0;
-    double sig[RTE_ANISO_MAX_L + 1] = {};
-    double Dh[RTE_ANISO_MAX_M * RTE_ANISO_MAX_M] = {};
-    FftSched sc;
-    double2* tw64 = nullptr;
-    float2* tw32 = nullptr;
-    double* S64 = nullptr;  // [np][H][H][H], xi_z fastest
-    float* S32 = nullptr;
-    int* pinfo = nullptr;   // [M][M]: pair index | imaginary << 16 | odd in y << 17 | odd in z << 18
-    void* T1 = nullptr;     // n*H*n complex doubles
-    void* T2 = nullptr;     // M*H*Q*n complex doubles
-    // FP64 GMRES workspace
-    int gm = 0;
-    double* V = nullptr;     // (gm + 1) x len
-    double* bvec = nullptr;  // len
-    double* r = nullptr;     // len
-    double* part = nullptr;  // (gm + 1) x nblk partial sums
-    double* hd = nullptr;    // gm + 1 coefficients
-    // FP32 inner solves of the mixed refinement
-    float* V32 = nullptr;  // (gm + 1) x len
-    float* r32 = nullptr;
-    float* x32 = nullptr;
-    float* b32 = nullptr;
-};
 
 // D_ab over the six faces of the cell: on the face of the point p = (.., +-a, ..)
 // the solid-angle element is a dx dy / |p|^3 and the ray reaches |p|, so
@@ -304,23 +251,30 @@ template <typename K> static cudaError_t allow_big(K k) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, RTE_SMEM_OPTIN);
 }
 
-// out_a = ca * x_a + cb * (K x)_a  (rhs = 0; x has M channels), or
-// out_a = cb * (K~^{a0} f)_a       (rhs = 1; x = f, one channel).
-template <typename T, typename R, typename TS>
-static cudaError_t aniso_run(rte_aniso3d op, const R* x, R* out, int rhs, double ca, double cb, const TS* S,
-                             const T* tw, int Bz, cudaStream_t s) {
+template <typename T, typename R, typename TS> static cudaError_t stockham_prepare() {
     static bool once = false;
+    if (once) return cudaSuccess;
     cudaError_t e;
-    if (!once) {
-        if ((e = allow_big(k3_x_fwd<T, R>)) != cudaSuccess) return e;
-        if ((e = allow_big(k3_y_fwd<T>)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k3a_z_mix<T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZmixCap)) !=
-            cudaSuccess)
-            return e;
-        if ((e = allow_big(k3_y_inv<T>)) != cudaSuccess) return e;
-        if ((e = allow_big(k3_x_inv<T, R>)) != cudaSuccess) return e;
-        once = true;
-    }
+    if ((e = allow_big(k3_x_fwd<T, R>)) != cudaSuccess) return e;
+    if ((e = allow_big(k3_y_fwd<T>)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k3a_z_mix<T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZmixCap)) !=
+        cudaSuccess)
+        return e;
+    if ((e = allow_big(k3_y_inv<T>)) != cudaSuccess) return e;
+    if ((e = allow_big(k3_x_inv<T, R>)) != cudaSuccess) return e;
+    once = true;
+    return cudaSuccess;
+}
+
+// out_a = ca * x_a + cb * (K v)_a + cc * z_a  (rhs = 0; x has M channels,
+//         v_b = mu_s sigma_hat_{l_b} x_b, plus xf in channel 0 when xf is given), or
+// out_a = cb * (K~^{a0} f)_a                  (rhs = 1; x = f, one channel).
+// Stockham passes channel by channel (any Q = 2^a 3^b).
+template <typename T, typename R, typename TS>
+static cudaError_t aniso_run(rte_aniso3d op, const R* x, R* out, int rhs, double ca, double cb, const R* zv, double cc,
+                             const double* xf, const TS* S, const T* tw, int Bz, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = stockham_prepare<T, R, TS>()) != cudaSuccess) return e;
     const int n = op->n, Q = op->Q, H = op->H, M = op->M;
     P3 pp;
     pp.n = n;
@@ -338,7 +292,8 @@ static cudaError_t aniso_run(rte_aniso3d op, const R* x, R* out, int rhs, double
     long launches = 0;
     for (int b = 0; b < Min; ++b) {
         const double w = rhs ? 1.0 : op->mu_s * op->sig[chan_l(b)];
-        k3_x_fwd<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(x + b * N, T1, tw, pp, w, nullptr);
+        k3_x_fwd<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(x + b * N, T1, tw, pp, w,
+                                                                    (!rhs && b == 0) ? xf : nullptr);
         k3_y_fwd<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T1, T2 + b * chs, tw, pp);
         launches += 2;
     }
@@ -353,7 +308,8 @@ static cudaError_t aniso_run(rte_aniso3d op, const R* x, R* out, int rhs, double
     for (int a = 0; a < M; ++a) {
         k3_y_inv<T><<<dim3((n + B - 1) / B, H), 256, smy, s>>>(T2 + a * chs, T1, tw, pp);
         k3_x_inv<T, R><<<dim3((n + B - 1) / B, n), 256, smx, s>>>(T1, (rhs || ca == 0.0) ? nullptr : x + a * N,
-                                                                    nullptr, out + a * N, tw, pp, ca, cb, 0.0);
+                                                                    zv ? zv + a * N : nullptr, out + a * N, tw, pp,
+                                                                    ca, cb, cc);
         launches += 2;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -361,200 +317,74 @@ static cudaError_t aniso_run(rte_aniso3d op, const R* x, R* out, int rhs, double
     return cudaSuccess;
 }
 
-// ---------------------------------------------------------------------------
-// Restarted GMRES on (I - K) u = b (Sec. 3.3, T.2): classical Gram-Schmidt
-// applied twice, inner products accumulated in FP64, the small Hessenberg
-// problem on the host.  T = double (the FP64 solve) or float (the inner solves
-// of the mixed refinement, whose residuals are FP64 applications).
-// ---------------------------------------------------------------------------
-#define ANISO_NBLK 304  // 2 x 152 SMs
-
-// part[i * nblk + blk] = sum over the block's chunk of V_i . w
-template <typename T>
-__global__ void __launch_bounds__(256) k_aniso_dots(const T* __restrict__ V, long len, const T* __restrict__ w,
-                                                    double* __restrict__ part) {
-    __shared__ double red[256];
-    const int i = blockIdx.y;
-    const T* v = V + (long)i * len;
-    double acc = 0.0;
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
-        acc += (double)v[t] * (double)w[t];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(long)i * gridDim.x + blockIdx.x] = red[0];
-}
-
-// out[i] = sum of the nblk partial sums of row i (fixed order)
-__global__ void k_aniso_sum(const double* __restrict__ part, int nblk, double* __restrict__ out) {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int t = threadIdx.x; t < nblk; t += blockDim.x) acc += part[(long)blockIdx.x * nblk + t];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
-}
-
-// w += sgn * sum_{i < k} c_i V_i
-template <typename T>
-__global__ void k_aniso_comb(T* __restrict__ w, const T* __restrict__ V, long len, int k, const double* __restrict__ c,
-                             double sgn) {
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int i = 0; i < k; ++i) acc += c[i] * (double)V[(long)i * len + t];
-        w[t] = (T)((double)w[t] + sgn * acc);
-    }
-}
-
-// dst = alpha * src  (or dst = b - dst when b != null)
-template <typename T>
-__global__ void k_aniso_scale(T* dst, const T* src, const T* b, long len, double alpha) {
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
-        dst[t] = b ? (T)((double)b[t] - (double)dst[t]) : (T)(alpha * (double)src[t]);
-}
-
-// r32 = (float)(alpha * r)  /  u += alpha * (double)d32
-__global__ void k_aniso_narrow(float* __restrict__ dst, const double* __restrict__ src, long len, double alpha) {
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
-        dst[t] = (float)(alpha * src[t]);
-}
-__global__ void k_aniso_widen_add(double* __restrict__ u, const float* __restrict__ d, long len, double alpha) {
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (long)gridDim.x * blockDim.x)
-        u[t] += alpha * (double)d[t];
-}
-
-template <typename T>
-static cudaError_t aniso_dots(rte_aniso3d op, const T* V, int k, const T* w, long len, double* h_host,
-                              cudaStream_t s) {
-    k_aniso_dots<T><<<dim3(ANISO_NBLK, k), 256, 0, s>>>(V, len, w, op->part);
-    k_aniso_sum<<<k, 256, 0, s>>>(op->part, ANISO_NBLK, op->hd);
-    rte_count_launches(2);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(h_host, op->hd, k * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-    return cudaStreamSynchronize(s);
-}
-
-// (I - K) x  in the vector's precision (ca = 1, cb = -1), or K~^{.0} f (rhs)
-static rte_status aniso_apply(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
-                              cudaStream_t s) {
-    cudaError_t e = aniso_run<double2, double, double>(op, x, y, rhs, ca, cb, op->S64, op->tw64, op->Bz64, s);
+// FP64: native FP64 passes
+static rte_status aniso_apply64(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
+                                const double* zv, double cc, const double* xf, cudaStream_t s) {
+    cudaError_t e = op->RQ ? aniso_run_warp<double2, double, double>(op, x, y, rhs, ca, cb, zv, cc, xf, op->S64,
+                                                                     op->tw64, s)
+                           : aniso_run<double2, double, double>(op, x, y, rhs, ca, cb, zv, cc, xf, op->S64, op->tw64,
+                                                                op->Bz64, s);
     if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d apply");
     return RTE_OK;
 }
-static rte_status aniso_apply(rte_aniso3d op, const float* x, float* y, int rhs, double ca, double cb,
-                              cudaStream_t s) {
-    cudaError_t e = aniso_run<float2, float, float>(op, x, y, rhs, ca, cb, op->S32, op->tw32, op->Bz32, s);
+// FP64-accurate on the FP32 units: float-float warp passes (native FP64 on the
+// Stockham path)
+static rte_status aniso_apply64e(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
+                                 const double* zv, double cc, const double* xf, cudaStream_t s) {
+    if (!op->RQ) return aniso_apply64(op, x, y, rhs, ca, cb, zv, cc, xf, s);
+    cudaError_t e = aniso_run_warp<ffc, double, ff>(op, x, y, rhs, ca, cb, zv, cc, xf, op->Sff, op->twff, s);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d apply64e");
+    return RTE_OK;
+}
+static rte_status aniso_apply32(rte_aniso3d op, const float* x, float* y, double ca, double cb, cudaStream_t s) {
+    cudaError_t e = op->RQ ? aniso_run_warp<float2, float, float>(op, x, y, 0, ca, cb, nullptr, 0.0, nullptr,
+                                                                  op->S32, op->tw32, s)
+                           : aniso_run<float2, float, float>(op, x, y, 0, ca, cb, nullptr, 0.0, nullptr, op->S32,
+                                                             op->tw32, op->Bz32, s);
     if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d apply32");
     return RTE_OK;
 }
-static rte_status aniso_apply64(rte_aniso3d op, const double* x, double* y, int rhs, double ca, double cb,
-                                cudaStream_t s) {
-    return aniso_apply(op, x, y, rhs, ca, cb, s);
+
+// the solve's operator callbacks (captured into the solve graph)
+static rte_status an_A32(void* c, const float* x, float* y, cudaStream_t s) {
+    return aniso_apply32((rte_aniso3d)c, x, y, 1.0, -1.0, s);
+}
+static rte_status an_A64(void* c, const double* x, double* y, cudaStream_t s) {
+    return aniso_apply64((rte_aniso3d)c, x, y, 0, 1.0, -1.0, nullptr, 0.0, nullptr, s);
+}
+// b = K~^{.0} f (T.1): FP64-accurate in both modes
+static rte_status an_rhs(void* c, int mixed, cudaStream_t s) {
+    rte_aniso3d op = (rte_aniso3d)c;
+    return mixed ? aniso_apply64e(op, op->f, op->b64, 1, 0.0, 1.0, nullptr, 0.0, nullptr, s)
+                 : aniso_apply64(op, op->f, op->b64, 1, 0.0, 1.0, nullptr, 0.0, nullptr, s);
+}
+// r = b - (I - K) u.  Mixed: r = K~ (mu_s sigma_hat u + f) - u in one
+// float-float application (the source joins channel 0's input), equal to it
+// with the exact b; FP64: r = K u - u + b in native FP64.
+static rte_status an_resid(void* c, int mixed, cudaStream_t s) {
+    rte_aniso3d op = (rte_aniso3d)c;
+    if (mixed) return aniso_apply64e(op, op->u, op->r64, 0, -1.0, 1.0, nullptr, 0.0, op->f, s);
+    return aniso_apply64(op, op->u, op->r64, 0, -1.0, 1.0, op->b64, 1.0, nullptr, s);
 }
 
-// GMRES(m) from x = 0 on (I - K) x = rhs until ||rhs - (I - K) x|| <= tol ||rhs||
-// (residuals in T) or maxit iterations; V holds m + 1 vectors, r one.
-template <typename T>
-static rte_status aniso_gmres(rte_aniso3d op, const T* rhs, T* x, T* V, T* r, long len, double tol, int m, int maxit,
-                              int* iters_out, int* cycles_out, double* relres_out, cudaStream_t s) {
-    const unsigned gb = ANISO_NBLK;
-    std::vector<double> Hm((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 1), h2(m + 1), y(m);
-    cudaError_t e = cudaSuccess;
-    rte_status st = RTE_OK;
-    double bn = 0.0;
-    if ((e = aniso_dots<T>(op, rhs, 1, rhs, len, &bn, s)) != cudaSuccess) return rte_cuda_fail(e, "aniso_gmres");
-    bn = sqrt(bn);
-    if ((e = cudaMemsetAsync(x, 0, len * sizeof(T), s)) != cudaSuccess) return rte_cuda_fail(e, "aniso_gmres");
-    k_aniso_scale<T><<<gb, 256, 0, s>>>(r, rhs, (const T*)nullptr, len, 1.0);
-    rte_count_launches(1);
-    double beta = bn, relres = bn > 0 ? 1.0 : 0.0;
-    int iters = 0, cycles = 0;
-    bool conv = !(bn > 0);
-    while (!conv && iters < maxit) {
-        ++cycles;
-        k_aniso_scale<T><<<gb, 256, 0, s>>>(V, r, (const T*)nullptr, len, 1.0 / beta);
-        rte_count_launches(1);
-        for (int i = 0; i <= m; ++i) g[i] = 0.0;
-        g[0] = beta;
-        int j = 0;
-        for (; j < m && iters < maxit; ++j) {
-            T* w = V + (long)(j + 1) * len;
-            if ((st = aniso_apply(op, V + (long)j * len, w, 0, 1.0, -1.0, s)) != RTE_OK) return st;
-            // two passes of classical Gram-Schmidt
-            for (int pass = 0; pass < 2; ++pass) {
-                double* hp = pass ? h2.data() : hcol.data();
-                if ((e = aniso_dots<T>(op, V, j + 1, w, len, hp, s)) != cudaSuccess) break;
-                if ((e = cudaMemcpyAsync(op->hd, hp, (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s)) !=
-                    cudaSuccess)
-                    break;
-                k_aniso_comb<T><<<gb, 256, 0, s>>>(w, V, len, j + 1, op->hd, -1.0);
-                rte_count_launches(1);
-            }
-            if (e != cudaSuccess) break;
-            for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
-            double hn = 0.0;
-            if ((e = aniso_dots<T>(op, w, 1, w, len, &hn, s)) != cudaSuccess) break;
-            hn = sqrt(hn);
-            hcol[j + 1] = hn;
-            if (hn > 0) {
-                k_aniso_scale<T><<<gb, 256, 0, s>>>(w, w, (const T*)nullptr, len, 1.0 / hn);
-                rte_count_launches(1);
-            }
-            for (int i = 0; i < j; ++i) {  // previous Givens rotations
-                const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
-                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
-                hcol[i] = t;
-            }
-            const double den = hypot(hcol[j], hcol[j + 1]);
-            cs[j] = den > 0 ? hcol[j] / den : 1.0;
-            sn[j] = den > 0 ? hcol[j + 1] / den : 0.0;
-            hcol[j] = den;
-            hcol[j + 1] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            for (int i = 0; i <= j; ++i) Hm[i * m + j] = hcol[i];
-            ++iters;
-            if (fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
-                ++j;
-                break;
-            }
-        }
-        if (e != cudaSuccess) break;
-        for (int i = j - 1; i >= 0; --i) {  // R y = g
-            double t = g[i];
-            for (int k = i + 1; k < j; ++k) t -= Hm[i * m + k] * y[k];
-            y[i] = Hm[i * m + i] != 0.0 ? t / Hm[i * m + i] : 0.0;
-        }
-        if (j > 0) {
-            if ((e = cudaMemcpyAsync(op->hd, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-                break;
-            k_aniso_comb<T><<<gb, 256, 0, s>>>(x, V, len, j, op->hd, 1.0);
-            rte_count_launches(1);
-        }
-        // residual r = rhs - (I - K) x in T
-        if ((st = aniso_apply(op, x, r, 0, 1.0, -1.0, s)) != RTE_OK) return st;
-        k_aniso_scale<T><<<gb, 256, 0, s>>>(r, (const T*)nullptr, rhs, len, 0.0);
-        rte_count_launches(1);
-        double rn = 0.0;
-        if ((e = aniso_dots<T>(op, r, 1, r, len, &rn, s)) != cudaSuccess) break;
-        beta = sqrt(rn);
-        relres = beta / bn;
-        conv = relres <= tol;
-        if (!(beta > 0)) break;
-    }
-    if (e != cudaSuccess) return rte_cuda_fail(e, "aniso_gmres");
-    *iters_out += iters;
-    *cycles_out += cycles;
-    *relres_out = relres;
-    return RTE_OK;
+static KrylovOp aniso_krylov_op(rte_aniso3d op) {
+    KrylovOp o;
+    o.ctx = op;
+    o.nr = (long)op->M * op->n * op->n * op->n;
+    o.nw1 = o.nr;  // real moments: the plain Euclidean inner product
+    o.u = op->u;
+    o.b64 = op->b64;
+    o.r64 = op->r64;
+    o.x64 = op->x64;
+    o.part64 = op->part64;
+    o.r32 = op->r32;
+    o.d32 = op->d32;
+    o.ref = op->ref;
+    o.A32 = an_A32;
+    o.A64 = an_A64;
+    o.rhs = an_rhs;
+    o.resid = an_resid;
+    return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -562,12 +392,40 @@ static rte_status aniso_gmres(rte_aniso3d op, const T* rhs, T* x, T* V, T* r, lo
 // ---------------------------------------------------------------------------
 extern "C" rte_status rte_aniso3d_destroy(rte_aniso3d op) {
     if (!op) return RTE_OK;
-    void* ptrs[] = {op->tw64, op->tw32, op->S64, op->S32,  op->pinfo, op->T1,  op->T2,  op->V,
-                    op->bvec, op->r,    op->part, op->hd, op->V32,   op->r32, op->x32, op->b32};
+    for (int i = 0; i < 3; ++i)
+        if (op->graph[i]) cudaGraphExecDestroy((cudaGraphExec_t)op->graph[i]);
+    krylov_free_ws(op->k64);
+    krylov_free_ws(op->k32);
+    void* ptrs[] = {op->tw64, op->tw32, op->twff, op->S64, op->S32, op->Sff, op->wz,    op->pinfo, op->T1,  op->T2,
+                    op->u,    op->f,    op->b64,  op->r64, op->x64, op->part64, op->r32, op->d32,  op->ref};
     for (void* q : ptrs)
         if (q) rte_dev_free(q);
+    if (op->ref_host) rte_host_free(op->ref_host);
     delete op;
     return RTE_OK;
+}
+
+// float-float copies of the FP64 spectra and twiddles
+__global__ void k_aniso_split(const double* __restrict__ src, ff* __restrict__ dst, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = ff(src[i]);
+}
+__global__ void k_aniso_split2(const double2* __restrict__ src, ffc* __restrict__ dst, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = to_ffc(src[i]);
+}
+
+// Q: the warp FFT's power of two (64, 128, 256) for 17 <= n <= 128, else the
+// smallest even 2^a 3^b >= 2n - 1 with the Stockham passes
+static int aniso_choose_Q(int n, int* RQ) {
+    *RQ = 0;
+    if (n >= 17 && n <= 128) {
+        int q = 64;
+        while (q < 2 * n - 1) q *= 2;
+        *RQ = q / 32;
+        return q;
+    }
+    return choose_Q(n);
 }
 
 extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, double mu_t, double mu_s, int L,
@@ -581,19 +439,39 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     for (int l = 1; l <= L; ++l)
         if (!(fabs(sigma_hat[l]) <= 1.0)) return RTE_EINVAL;
     const int M = (L + 1) * (L + 1);
-    const int Q = choose_Q(n), H = Q / 2 + 1;
-    const int Bz64 = zmix_lines<double2>(Q, M), Bz32 = zmix_lines<float2>(Q, M);
-    if (Bz64 == 0 || Bz32 == 0) return rte_fail(RTE_EUNSUPPORTED, "rte_aniso3d_create: M x Q too large for one Z block");
+    int RQ = 0;
+    const int Q = aniso_choose_Q(n, &RQ), H = Q / 2 + 1;
+    int Bz64 = 0, Bz32 = 0, Bw16 = 0, Bw8 = 0;
+    if (RQ) {
+        Bw16 = aniso_warp_lines(RQ, M, 16);
+        Bw8 = aniso_warp_lines(RQ, M, 8);
+        if (Bw16 == 0 || Bw8 == 0)
+            return rte_fail(RTE_EUNSUPPORTED, "rte_aniso3d_create: M x Q too large for one Z block");
+    } else {
+        Bz64 = zmix_lines<double2>(Q, M);
+        Bz32 = zmix_lines<float2>(Q, M);
+        if (Bz64 == 0 || Bz32 == 0)
+            return rte_fail(RTE_EUNSUPPORTED, "rte_aniso3d_create: M x Q too large for one Z block");
+    }
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        // kernel attributes are set here, before any solve graph is captured
+        cudaError_t ep = RQ ? aniso_warp_prepare(RQ) : stockham_prepare<double2, double, double>();
+        if (ep == cudaSuccess && !RQ) ep = stockham_prepare<float2, float, float>();
+        if (ep != cudaSuccess) return rte_cuda_fail(ep, "rte_aniso3d_create");
+    }
     rte_aniso3d op = new rte_aniso3d_s();
     op->n = n;
     op->L = L;
     op->M = M;
     op->Q = Q;
     op->H = H;
+    op->RQ = RQ;
     op->np = M * (M + 1) / 2;
     op->Bz64 = Bz64;
     op->Bz32 = Bz32;
+    op->Bw16 = Bw16;
+    op->Bw8 = Bw8;
     op->h = h;
     op->mu_t = mu_t;
     op->mu_s = mu_s;
@@ -607,12 +485,16 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     cudaError_t e = cudaSuccess;
     double2* G = nullptr;
     double* Dd = nullptr;
+    const size_t t1slabs = RQ ? (size_t)M : 1;
     if (rte_dev_malloc((void**)&op->tw64, Q * sizeof(double2)) != cudaSuccess ||
         rte_dev_malloc((void**)&op->tw32, Q * sizeof(float2)) != cudaSuccess ||
         rte_dev_malloc((void**)&op->S64, op->np * H3 * sizeof(double)) != cudaSuccess ||
         rte_dev_malloc((void**)&op->S32, op->np * H3 * sizeof(float)) != cudaSuccess ||
+        (RQ && rte_dev_malloc((void**)&op->twff, Q * sizeof(ffc)) != cudaSuccess) ||
+        (RQ && rte_dev_malloc((void**)&op->Sff, op->np * H3 * sizeof(ff)) != cudaSuccess) ||
+        rte_dev_malloc((void**)&op->wz, M * sizeof(double)) != cudaSuccess ||
         rte_dev_malloc((void**)&op->pinfo, M * M * sizeof(int)) != cudaSuccess ||
-        rte_dev_malloc((void**)&op->T1, (size_t)n * H * n * sizeof(double2)) != cudaSuccess ||
+        rte_dev_malloc((void**)&op->T1, t1slabs * n * H * n * sizeof(double2)) != cudaSuccess ||
         rte_dev_malloc((void**)&op->T2, (size_t)M * H * Q * n * sizeof(double2)) != cudaSuccess ||
         rte_dev_malloc((void**)&G, (size_t)P * sizeof(double2)) != cudaSuccess ||
         rte_dev_malloc((void**)&Dd, M * M * sizeof(double)) != cudaSuccess) {
@@ -627,6 +509,9 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     e = cudaMemcpyAsync(op->pinfo, pinfo.data(), M * M * sizeof(int), cudaMemcpyHostToDevice, s);
+    double wz[RTE_ANISO_MAX_M];
+    for (int b = 0; b < M; ++b) wz[b] = mu_s * op->sig[chan_l(b)];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(op->wz, wz, M * sizeof(double), cudaMemcpyHostToDevice, s);
     long launches = 0;
     if (e == cudaSuccess) {
         k_twiddles<<<(Q + 255) / 256, 256, 0, s>>>(op->tw64, op->tw32, Q);
@@ -658,6 +543,12 @@ extern "C" rte_status rte_aniso3d_create(rte_aniso3d* out, int n, double h, doub
                 e = cudaGetLastError();
             }
         }
+    if (e == cudaSuccess && RQ) {
+        k_aniso_split<<<1024, 256, 0, s>>>(op->S64, op->Sff, op->np * H3);
+        k_aniso_split2<<<(Q + 255) / 256, 256, 0, s>>>(op->tw64, op->twff, Q);
+        launches += 2;
+        e = cudaGetLastError();
+    }
     cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms = 0.f;
@@ -699,126 +590,90 @@ extern "C" rte_status rte_aniso3d_cell_weights(rte_aniso3d op, double* out_host)
 
 extern "C" rte_status rte_aniso3d_apply_K(rte_aniso3d op, const double* x_dev, double* y_dev, void* stream) {
     if (!op || !x_dev || !y_dev || x_dev == y_dev) return RTE_EINVAL;
-    return aniso_apply64(op, x_dev, y_dev, 0, 0.0, 1.0, (cudaStream_t)stream);
+    return aniso_apply64(op, x_dev, y_dev, 0, 0.0, 1.0, nullptr, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rte_status rte_aniso3d_apply_K64e(rte_aniso3d op, const double* x_dev, double* y_dev, void* stream) {
+    if (!op || !x_dev || !y_dev || x_dev == y_dev) return RTE_EINVAL;
+    return aniso_apply64e(op, x_dev, y_dev, 0, 0.0, 1.0, nullptr, 0.0, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" rte_status rte_aniso3d_apply_K32(rte_aniso3d op, const float* x_dev, float* y_dev, void* stream) {
     if (!op || !x_dev || !y_dev || x_dev == y_dev) return RTE_EINVAL;
-    cudaError_t e = aniso_run<float2, float, float>(op, x_dev, y_dev, 0, 0.0, 1.0, op->S32, op->tw32, op->Bz32,
-                                                    (cudaStream_t)stream);
-    if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d_apply_K32");
-    return RTE_OK;
+    return aniso_apply32(op, x_dev, y_dev, 0.0, 1.0, (cudaStream_t)stream);
 }
 
 extern "C" rte_status rte_aniso3d_rhs(rte_aniso3d op, const double* f_dev, double* b_dev, void* stream) {
     if (!op || !f_dev || !b_dev) return RTE_EINVAL;
-    return aniso_apply64(op, f_dev, b_dev, 1, 0.0, 1.0, (cudaStream_t)stream);
+    return aniso_apply64(op, f_dev, b_dev, 1, 0.0, 1.0, nullptr, 0.0, nullptr, (cudaStream_t)stream);
 }
 
+// the solve's vectors, each allocated once (a failed allocation is retried
+// by the next call)
+static rte_status aniso_solve_buffers(rte_aniso3d op, bool mixed) {
+    const long N3 = (long)op->n * op->n * op->n, len = op->M * N3;
+    struct {
+        void** p;
+        size_t bytes;
+        bool need;
+    } bufs[] = {
+        {(void**)&op->u, len * sizeof(double), true},
+        {(void**)&op->f, N3 * sizeof(double), true},
+        {(void**)&op->b64, len * sizeof(double), true},
+        {(void**)&op->r64, len * sizeof(double), true},
+        {(void**)&op->part64, (size_t)krylov_tiles(len) * sizeof(double), true},
+        {(void**)&op->ref, refdev_size(), true},
+        {(void**)&op->x64, len * sizeof(double), !mixed},
+        {(void**)&op->r32, len * sizeof(float), mixed},
+        {(void**)&op->d32, len * sizeof(float), mixed},
+    };
+    for (auto& b : bufs)
+        if (b.need && !*b.p && rte_dev_malloc(b.p, b.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
+        }
+    if (!op->ref_host && rte_host_malloc(&op->ref_host, 2 * refdev_size()) != cudaSuccess) {
+        cudaGetLastError();
+        return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
+    }
+    return RTE_OK;
+}
+
+// T.1 then T.2 on the device: the plan's solve graph (restarted GMRES with
+// device-side control, FP64 or FP32 inner solves with float-float residuals)
+// on this operator; f and u are copied into and out of the handle's vectors.
 extern "C" rte_status rte_aniso3d_solve(rte_aniso3d op, const double* f_dev, double* u_dev, double tol, int restart,
                                         int maxit, int prec, rte_stats* stats, void* stream) {
-    if (!op || !f_dev || !u_dev || !(tol > 0) || restart < 1 || restart > 200 || maxit < 1) return RTE_EINVAL;
+    if (!op || !f_dev || !u_dev || !(tol > 0) || restart < 1 || restart > 128 || maxit < 1)
+        return RTE_EINVAL;
     if (prec != RTE_PREC_FP64 && prec != RTE_PREC_MIXED_FP32) return RTE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const long len = (long)op->M * op->n * op->n * op->n;
     const bool mixed = prec == RTE_PREC_MIXED_FP32;
-    if (op->gm != restart || (mixed && !op->V32)) {
-        for (void** q : {(void**)&op->V, (void**)&op->bvec, (void**)&op->r, (void**)&op->part, (void**)&op->hd,
-                         (void**)&op->V32, (void**)&op->r32, (void**)&op->x32, (void**)&op->b32})
-            if (*q) {
-                rte_dev_free(*q);
-                *q = nullptr;
-            }
-        op->gm = 0;
-        bool ok = rte_dev_malloc((void**)&op->bvec, len * sizeof(double)) == cudaSuccess &&
-                  rte_dev_malloc((void**)&op->r, len * sizeof(double)) == cudaSuccess &&
-                  rte_dev_malloc((void**)&op->part, (size_t)(restart + 1) * ANISO_NBLK * sizeof(double)) == cudaSuccess &&
-                  rte_dev_malloc((void**)&op->hd, (restart + 1) * sizeof(double)) == cudaSuccess;
-        if (ok && !mixed) ok = rte_dev_malloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) == cudaSuccess;
-        if (ok && mixed)
-            ok = rte_dev_malloc((void**)&op->V32, (size_t)(restart + 1) * len * sizeof(float)) == cudaSuccess &&
-                 rte_dev_malloc((void**)&op->r32, len * sizeof(float)) == cudaSuccess &&
-                 rte_dev_malloc((void**)&op->x32, len * sizeof(float)) == cudaSuccess &&
-                 rte_dev_malloc((void**)&op->b32, len * sizeof(float)) == cudaSuccess;
-        if (!ok) {
-            cudaGetLastError();
-            return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
-        }
-        op->gm = restart;
-    }
-    if (!mixed && !op->V) {
-        if (rte_dev_malloc((void**)&op->V, (size_t)(restart + 1) * len * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return rte_fail(RTE_ENOMEM, "rte_aniso3d_solve");
-        }
-    }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-    int iters = 0, cycles = 0, outer = 0;
-    double relres = 1.0;
-    rte_status st = aniso_apply(op, f_dev, op->bvec, 1, 0.0, 1.0, s);  // b = K~^{.0} f (T.1)
-    cudaError_t e = cudaSuccess;
-    if (st == RTE_OK && !mixed) {
-        st = aniso_gmres<double>(op, op->bvec, u_dev, op->V, op->r, len, tol, restart, maxit, &iters, &outer, &relres,
-                                 s);
-    } else if (st == RTE_OK) {
-        // T.2 refined: FP32 GMRES on (I - K) d = r/||r|| to max(1e-4, tol/(2 relres)),
-        // u += ||r|| d, every residual r = b - (I - K) u an FP64 application
-        const unsigned gb = ANISO_NBLK;
-        double bn = 0.0;
-        e = aniso_dots<double>(op, op->bvec, 1, op->bvec, len, &bn, s);
-        bn = sqrt(bn);
-        if (e == cudaSuccess) e = cudaMemsetAsync(u_dev, 0, len * sizeof(double), s);
-        if (e == cudaSuccess) {
-            k_aniso_scale<double><<<gb, 256, 0, s>>>(op->r, op->bvec, (const double*)nullptr, len, 1.0);
-            rte_count_launches(1);
-        }
-        double rn = bn;
-        relres = bn > 0 ? 1.0 : 0.0;
-        while (st == RTE_OK && e == cudaSuccess && relres > tol && iters < maxit && outer < 50) {
-            ++outer;
-            k_aniso_narrow<<<gb, 256, 0, s>>>(op->b32, op->r, len, 1.0 / rn);
-            rte_count_launches(1);
-            double itol = fmax(1e-4, 0.5 * tol / relres);
-            if (itol > 0.5) itol = 0.5;
-            double rr32 = 0.0;
-            st = aniso_gmres<float>(op, op->b32, op->x32, op->V32, op->r32, len, itol, restart, maxit - iters, &iters,
-                                    &cycles, &rr32, s);
-            if (st != RTE_OK) break;
-            k_aniso_widen_add<<<gb, 256, 0, s>>>(u_dev, op->x32, len, rn);
-            rte_count_launches(1);
-            if ((st = aniso_apply(op, u_dev, op->r, 0, 1.0, -1.0, s)) != RTE_OK) break;
-            k_aniso_scale<double><<<gb, 256, 0, s>>>(op->r, (const double*)nullptr, op->bvec, len, 0.0);
-            rte_count_launches(1);
-            double r2 = 0.0;
-            if ((e = aniso_dots<double>(op, op->r, 1, op->r, len, &r2, s)) != cudaSuccess) break;
-            rn = sqrt(r2);
-            relres = bn > 0 ? rn / bn : 0.0;
-            if (!(rn > 0)) break;
-        }
-    }
-    cudaEventRecord(e1, s);
-    cudaError_t e2 = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    const long N3 = (long)op->n * op->n * op->n, len = op->M * N3;
+    rte_status st = aniso_solve_buffers(op, mixed);
     if (st != RTE_OK) return st;
-    if (e == cudaSuccess) e = e2;
-    if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d_solve");
-    const bool conv = relres <= tol;
-    if (stats) {
-        const double rr = op->mu_t > 0 ? op->mu_s / op->mu_t : 1.0;
-        stats->iters = iters;
-        stats->outer = outer;
-        stats->converged = conv ? 1 : 0;
-        stats->relres_true = relres;
-        stats->ms_total = ms;
-        stats->ms_pre = op->ms_pre;
-        stats->est_err_bound = rr < 1 ? (1 + rr) / (1 - rr) * relres : INFINITY;
+    const KrylovOp o = aniso_krylov_op(op);
+    if (!op->graph[prec] || op->graph_m[prec] != restart) {
+        if (op->graph[prec]) cudaGraphExecDestroy((cudaGraphExec_t)op->graph[prec]);
+        op->graph[prec] = nullptr;
+        st = krylov_op_graph(o, mixed ? op->k32 : op->k64, prec, restart, s, &op->graph[prec], &op->ginfo[prec]);
+        if (st != RTE_OK) return st;
+        op->graph_m[prec] = restart;
     }
-    if (!isfinite(relres)) return rte_fail(RTE_ENOCONV, "rte_aniso3d_solve: non-finite residual");
-    return conv ? RTE_OK : RTE_ENOCONV;
+    RTE_CUDA_TRY(cudaMemcpyAsync(op->f, f_dev, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rte_opts ro;
+    memset(&ro, 0, sizeof(ro));
+    ro.prec = (rte_prec)prec;
+    ro.tol = tol;
+    ro.restart = restart;
+    ro.maxit = maxit;
+    ro.inner_tol = 1e-4;
+    const double rho = op->mu_t > 0 ? op->mu_s / op->mu_t : 0.0;
+    st = krylov_op_run(o, op->graph[prec], op->ginfo[prec], &ro, op->ref_host, rho, op->ms_pre, stats, s);
+    if (st == RTE_OK || st == RTE_ENOCONV) {
+        cudaError_t e = cudaMemcpyAsync(u_dev, op->u, len * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d_solve");
+    }
+    return st;
 }

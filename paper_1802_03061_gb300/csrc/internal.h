@@ -47,6 +47,41 @@ void krylov_free_ws(KrylovWs& ws);
 struct SolveGraphInfo {
     long long k_fixed = 0, k_guess = 0, k_outer = 0, k_cycle = 0, k_step = 0, k_restart = 0;
 };
+// The operator and the vectors a solve graph is built on (krylov.cu): the
+// plan's J-symmetric channels, or the spherical-harmonic operator's moments.
+// Each callback enqueues its kernels on the given stream (it is captured).
+struct KrylovOp {
+    void* ctx = nullptr;
+    long nr = 0;       // vector length (reals)
+    long nw1 = 0;      // elements [0, nw1) weigh 1 in the inner product, the rest 2
+    double* u = nullptr;       // solution
+    double* b64 = nullptr;     // right-hand side
+    double* r64 = nullptr;     // residual
+    double* x64 = nullptr;     // FP64 mode: correction of one refinement step
+    double* part64 = nullptr;  // reduction partials, krylov_tiles(nr)
+    float* r32 = nullptr;      // mixed mode: inner right-hand side
+    float* d32 = nullptr;      // mixed mode: inner solution
+    float* pv1 = nullptr;      // preconditioned steps: M v (with pcA32 only)
+    void* ref = nullptr;       // device refinement state, refdev_size() bytes
+    // y = (I - K) x
+    rte_status (*A32)(void* ctx, const float* x, float* y, cudaStream_t s) = nullptr;
+    rte_status (*A64)(void* ctx, const double* x, double* y, cudaStream_t s) = nullptr;
+    // y = (I - K) M x with z = M x (right preconditioning), or null
+    rte_status (*pcA32)(void* ctx, const float* x, float* z, float* y, cudaStream_t s) = nullptr;
+    // b64 = K~ f (FP32-accurate suffices when mixed: residuals are exact in b)
+    rte_status (*rhs)(void* ctx, int mixed, cudaStream_t s) = nullptr;
+    // r64 = b - (I - K) u, FP64-accurate
+    rte_status (*resid)(void* ctx, int mixed, cudaStream_t s) = nullptr;
+};
+long krylov_tiles(long nr);
+// graph of a whole solve of op (GMRES inner solves, no preconditioner) into *exec
+rte_status krylov_op_graph(const KrylovOp& op, KrylovWs& ws, int prec, int m, cudaStream_t s, void** exec,
+                           SolveGraphInfo* info);
+// options into op.ref (host staging `hst`, refdev_size() bytes), launch, read back
+// the state into hst + refdev_size(), collect statistics and the status
+rte_status krylov_op_run(const KrylovOp& op, void* exec, const SolveGraphInfo& info, const rte_opts* o, void* hst,
+                         double rho, double ms_pre, rte_stats* stats, cudaStream_t s);
+
 struct SolveGraph {
     void* exec = nullptr;  // cudaGraphExec_t of the whole solve
     int m = 0;

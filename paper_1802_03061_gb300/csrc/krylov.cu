@@ -839,11 +839,13 @@ static int grid_for(long nr) {
 }
 static int tiles(long nr) { return (int)((nr + TILE - 1) / TILE); }
 
-static rte_status apply_A_T(rte_plan p, const double* x, double* y, cudaStream_t s) {
-    return plan_apply64(p, MIX_K, x, y, 1.0, -1.0, 0.0, nullptr, s);
+long krylov_tiles(long nr) { return tiles(nr); }
+
+static rte_status apply_A_T(const KrylovOp& o, const double* x, double* y, cudaStream_t s) {
+    return o.A64(o.ctx, x, y, s);
 }
-static rte_status apply_A_T(rte_plan p, const float* x, float* y, cudaStream_t s) {
-    return plan_apply32(p, x, y, 1.0f, -1.0f, 0.0f, nullptr, s);
+static rte_status apply_A_T(const KrylovOp& o, const float* x, float* y, cudaStream_t s) {
+    return o.A32(o.ctx, x, y, s);
 }
 
 // weighted norm of v into *out (device)
@@ -859,7 +861,7 @@ static rte_status dev_norm(const T* v, long nr, long nw1, double* part, double* 
 }
 
 template <typename T> struct Gm {
-    rte_plan p;
+    const KrylovOp* op;
     T* V;
     T* w;
     T* vin;
@@ -871,16 +873,16 @@ template <typename T> struct Gm {
 };
 
 template <typename T>
-static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream_t s, bool pc) {
-    G.p = p;
-    G.nr = p->nr;
-    G.nw1 = p->dim == 2 ? 2L * p->n * p->n : p->nr;
+static rte_status gm_setup(Gm<T>& G, const KrylovOp& o, KrylovWs& ws, int m, cudaStream_t s, bool pc) {
+    G.op = &o;
+    G.nr = o.nr;
+    G.nw1 = o.nw1;
     G.m = m;
     if (ws.m != m || !ws.V) {
         krylov_free_ws(ws);
-        if (rte_dev_malloc(&ws.V, (size_t)(m + 2) * p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
-        if (rte_dev_malloc(&ws.w, (size_t)p->nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
-        if (rte_dev_malloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(p->nr) * sizeof(double)) != cudaSuccess) {
+        if (rte_dev_malloc(&ws.V, (size_t)(m + 2) * o.nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (rte_dev_malloc(&ws.w, (size_t)o.nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
+        if (rte_dev_malloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(o.nr) * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return RTE_ENOMEM;
         }
@@ -888,13 +890,13 @@ static rte_status gm_setup(Gm<T>& G, rte_plan p, KrylovWs& ws, int m, cudaStream
         RTE_CUDA_TRY(cudaMemsetAsync(ws.st, 0, sizeof(GmresDev), s));
         ws.m = m;
     }
-    if (pc && !ws.Z && rte_dev_malloc(&ws.Z, (size_t)(m + 1) * p->nr * sizeof(T)) != cudaSuccess) {
+    if (pc && !ws.Z && rte_dev_malloc(&ws.Z, (size_t)(m + 1) * o.nr * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return RTE_ENOMEM;
     }
     G.V = (T*)ws.V;
     G.Z = (T*)ws.Z;
-    G.vin = G.V + (long)(m + 1) * p->nr;  // slot m+1 is the matvec input
+    G.vin = G.V + (long)(m + 1) * o.nr;  // slot m+1 is the matvec input
     G.w = (T*)ws.w;
     G.st = (GmresDev*)ws.st;
     G.part = ws.part;
@@ -1140,12 +1142,12 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditiona
     rte_status e;
     if constexpr (sizeof(T) == sizeof(float)) {
         if (pc) {  // right preconditioning: w = A (M v), M v kept in pv1
-            e = plan_apply_pcA32(G.p, (const float*)G.vin, G.p->pv1, (float*)G.w, s);
+            e = G.op->pcA32(G.op->ctx, (const float*)G.vin, G.op->pv1, (float*)G.w, s);
         } else {
-            e = apply_A_T(G.p, G.vin, G.w, s);
+            e = apply_A_T(*G.op, G.vin, G.w, s);
         }
     } else {
-        e = apply_A_T(G.p, G.vin, G.w, s);
+        e = apply_A_T(*G.op, G.vin, G.w, s);
     }
     if (e != RTE_OK) return e;
     const int* jp = &G.st->j;
@@ -1154,12 +1156,12 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditiona
             if (nr % 4 == 0) {
                 k_step_dot4<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
                 k_step_upd4<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
-                                               G.nw1, G.part, loop, pc ? G.p->pv1 : nullptr,
+                                               G.nw1, G.part, loop, pc ? G.op->pv1 : nullptr,
                                                pc ? (float*)G.Z : nullptr);
             } else {
                 k_step_dot<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
                 k_step_upd<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
-                                              G.nw1, G.part, loop, pc ? G.p->pv1 : nullptr,
+                                              G.nw1, G.part, loop, pc ? G.op->pv1 : nullptr,
                                               pc ? (float*)G.Z : nullptr);
             }
             rte_count_launches(2);
@@ -1263,22 +1265,22 @@ static rte_status add_cond(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphConditi
 // Inputs/outputs are the plan's own f_dev / u_dev; options are read from
 // the plan's device RefDev at run time.
 template <typename T>
-static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool pc, cudaGraph_t g,
+static rte_status build_solve(const KrylovOp& o, KrylovWs& ws, int m, bool minres, bool pc, cudaGraph_t g,
                               cudaGraphNode_t* dep_io,
                               cudaStream_t cs, SolveGraphInfo* info) {
     const bool mixed = sizeof(T) == sizeof(float);
     const bool use_mr = mixed && minres && m >= 5;  // MINRES buffers: basis slots 0..5
-    const bool use_pc = mixed && pc && !use_mr;      // preconditioned inner GMRES
+    const bool use_pc = mixed && pc && !use_mr && o.pcA32;  // preconditioned inner GMRES
     const bool cgs2 = !mixed;
     Gm<T> G;
-    TRYS(gm_setup<T>(G, p, ws, m, cs, use_pc));
+    TRYS(gm_setup<T>(G, o, ws, m, cs, use_pc));
     RTE_CUDA_TRY(cudaStreamSynchronize(cs));
-    const long nr = p->nr;
+    const long nr = o.nr;
     const int gr = grid_for(nr), nb = tiles(nr);
     const long nw1 = G.nw1;
-    RefDev* ref = (RefDev*)p->ref;
-    T* rhs = mixed ? (T*)p->r32 : (T*)p->r64;
-    T* x = mixed ? (T*)p->d32 : (T*)p->x64;
+    RefDev* ref = (RefDev*)o.ref;
+    T* rhs = mixed ? (T*)o.r32 : (T*)o.r64;
+    T* x = mixed ? (T*)o.d32 : (T*)o.x64;
     cudaGraphConditionalHandle c_guess = 0, c_outer = 0, c_cycle = 0, c_loop = 0, c_restart = 0;
     // every handle must belong to a conditional node of the graph: the
     // restart-cycle handles exist only with GMRES inner solves
@@ -1297,23 +1299,13 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
     // in FP32 only (it is the first inner right-hand side and sets ||b||) and
     // every residual as r = K~ (mu_s sigma_hat u + f) - u: one FP64-accurate
     // application that equals b - (I - K) u with the exact b.
-    auto apply64 = mixed ? plan_apply64e : plan_apply64;
-    auto residual = [&]() -> rte_status {
-        if (mixed) return apply64(p, MIX_KF, p->u_dev, p->r64, -1.0, 1.0, 0.0, nullptr, cs);
-        return apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, cs);
-    };
+    auto residual = [&]() -> rte_status { return o.resid(o.ctx, mixed ? 1 : 0, cs); };
     SEG(g, dep, &info->k_fixed, {
-        if (mixed) {
-            TRYS(plan_rhs32(p, (float*)p->r32, cs));
-            k_widen<<<gr, 256, 0, cs>>>((const float*)p->r32, p->b64, nr);
-            rte_count_launches(1);
-        } else {
-            TRYS(apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, cs));
-        }
-        TRYS(dev_norm<double>(p->b64, nr, nw1, p->part64, &ref->bnorm, cs));
+        TRYS(o.rhs(o.ctx, mixed ? 1 : 0, cs));
+        TRYS(dev_norm<double>(o.b64, nr, nw1, o.part64, &ref->bnorm, cs));
         k_ref_start<<<1, 32, 0, cs>>>(ref, c_guess);
-        k_zero_unless_guess<<<gr, 256, 0, cs>>>(p->u_dev, nr, ref);
-        k_copy_vec<<<gr, 256, 0, cs>>>(p->b64, p->r64, nr);
+        k_zero_unless_guess<<<gr, 256, 0, cs>>>(o.u, nr, ref);
+        k_copy_vec<<<gr, 256, 0, cs>>>(o.b64, o.r64, nr);
         rte_count_launches(3);
     });
     // residual of a guess
@@ -1323,8 +1315,8 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
         cudaGraphNode_t d = nullptr;
         SEG(body, d, &info->k_guess, {
             TRYS(residual());
-            TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
-            k_guess_fallback<<<gr, 256, 0, cs>>>(p->u_dev, p->r64, p->b64, nr, ref);
+            TRYS(dev_norm<double>(o.r64, nr, nw1, o.part64, &ref->rnorm, cs));
+            k_guess_fallback<<<gr, 256, 0, cs>>>(o.u, o.r64, o.b64, nr, ref);
             k_guess_fallback_state<<<1, 32, 0, cs>>>(ref);
             k_ref_relres<<<1, 32, 0, cs>>>(ref);
             rte_count_launches(3);
@@ -1344,7 +1336,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
             float* B = (float*)G.V;
             float* W = B + 3 * nr;
             SEG(outer_body, d, &info->k_outer, {
-                k_scale_inv<double, float><<<gr, 256, 0, cs>>>(p->r64, p->r32, nr, &ref->rnorm);
+                k_scale_inv<double, float><<<gr, 256, 0, cs>>>(o.r64, o.r32, nr, &ref->rnorm);
                 rte_count_launches(1);
             });
             SEG(outer_body, d, &info->k_cycle, {
@@ -1358,7 +1350,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
             {
                 cudaGraphNode_t dl = nullptr;
                 SEG(loop_body, dl, &info->k_step, {
-                    TRYS(apply_A_T(p, (const float*)G.vin, (float*)G.w, cs));
+                    TRYS(apply_A_T(o, (const float*)G.vin, (float*)G.w, cs));
                     k_mr_dot<<<nb, 256, 0, cs>>>((const float*)G.vin, (const float*)G.w, B, G.st, nr, nw1, G.part);
                     k_mr_upd<<<nb, 256, 0, cs>>>((const float*)G.w, B, G.st, nr, nw1, G.part, c_loop);
                     k_mr_sol<<<nb, 256, 0, cs>>>((float*)G.vin, B, W, (float*)x, G.st, nr);
@@ -1366,11 +1358,11 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
                 });
             }
             SEG(outer_body, d, &info->k_outer, {
-                k_axpy_scaled<float><<<gr, 256, 0, cs>>>(p->u_dev, (const float*)x, nr, &ref->rnorm);
+                k_axpy_scaled<float><<<gr, 256, 0, cs>>>(o.u, (const float*)x, nr, &ref->rnorm);
                 k_mr_after<<<1, 32, 0, cs>>>(ref, G.st);
                 rte_count_launches(2);
                 TRYS(residual());
-                TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
+                TRYS(dev_norm<double>(o.r64, nr, nw1, o.part64, &ref->rnorm, cs));
                 k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
                 rte_count_launches(1);
             });
@@ -1382,7 +1374,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
         cudaGraphNode_t d = nullptr;
         SEG(outer_body, d, &info->k_outer, {
             if (mixed) {
-                k_scale_inv<double, float><<<gr, 256, 0, cs>>>(p->r64, p->r32, nr, &ref->rnorm);
+                k_scale_inv<double, float><<<gr, 256, 0, cs>>>(o.r64, o.r32, nr, &ref->rnorm);
                 rte_count_launches(1);
             }
             k_zero_T<T><<<gr, 256, 0, cs>>>(x, nr);
@@ -1424,7 +1416,7 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
             {
                 cudaGraphNode_t dr = nullptr;
                 SEG(restart_body, dr, &info->k_restart, {
-                    TRYS(apply_A_T(p, x, G.w, cs));
+                    TRYS(apply_A_T(o, x, G.w, cs));
                     k_rsub<T><<<gr, 256, 0, cs>>>(rhs, G.w, nr);
                     rte_count_launches(1);
                 });
@@ -1432,14 +1424,14 @@ static rte_status build_solve(rte_plan p, KrylovWs& ws, int m, bool minres, bool
         }
         SEG(outer_body, d, &info->k_outer, {
             if (mixed) {
-                k_axpy_scaled<float><<<gr, 256, 0, cs>>>(p->u_dev, (const float*)x, nr, &ref->rnorm);
+                k_axpy_scaled<float><<<gr, 256, 0, cs>>>(o.u, (const float*)x, nr, &ref->rnorm);
             } else {
-                k_add64<<<gr, 256, 0, cs>>>(p->u_dev, (const double*)x, nr);
+                k_add64<<<gr, 256, 0, cs>>>(o.u, (const double*)x, nr);
             }
             k_ref_after<<<1, 32, 0, cs>>>(ref, G.st);
             rte_count_launches(2);
             TRYS(residual());
-            TRYS(dev_norm<double>(p->r64, nr, nw1, p->part64, &ref->rnorm, cs));
+            TRYS(dev_norm<double>(o.r64, nr, nw1, o.part64, &ref->rnorm, cs));
             k_ref_check<<<1, 32, 0, cs>>>(ref, c_outer);
             rte_count_launches(1);
         });
@@ -1466,14 +1458,98 @@ bool solve_uses_precond(const rte_plan p, const rte_opts* o) {
     return o->prec != RTE_PREC_FP64 && o->precond != 0 && !solve_uses_minres(p, o) && plan_precond_supported(p);
 }
 
+// the plan as a KrylovOp: its own f_dev / u_dev and work vectors
+static rte_status plan_A32(void* c, const float* x, float* y, cudaStream_t s) {
+    return plan_apply32((rte_plan)c, x, y, 1.0f, -1.0f, 0.0f, nullptr, s);
+}
+static rte_status plan_A64(void* c, const double* x, double* y, cudaStream_t s) {
+    return plan_apply64((rte_plan)c, MIX_K, x, y, 1.0, -1.0, 0.0, nullptr, s);
+}
+static rte_status plan_pcA(void* c, const float* x, float* z, float* y, cudaStream_t s) {
+    return plan_apply_pcA32((rte_plan)c, x, z, y, s);
+}
+// mixed: b = K~ f in FP32 (the first inner right-hand side; it sets ||b||),
+// widened; FP64: one native FP64 application
+static rte_status plan_rhs(void* c, int mixed, cudaStream_t s) {
+    rte_plan p = (rte_plan)c;
+    if (!mixed) return plan_apply64(p, MIX_RHS, p->f_dev, p->b64, 0.0, 1.0, 0.0, nullptr, s);
+    TRYS(plan_rhs32(p, (float*)p->r32, s));
+    k_widen<<<grid_for(p->nr), 256, 0, s>>>((const float*)p->r32, p->b64, p->nr);
+    rte_count_launches(1);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+// FP64-accurate residuals: float-float on the FP32 units in the mixed mode,
+// r = K~ (mu_s sigma_hat u + f) - u in one application (equal to
+// b - (I - K) u with the exact b); native FP64 in the FP64 mode
+static rte_status plan_resid(void* c, int mixed, cudaStream_t s) {
+    rte_plan p = (rte_plan)c;
+    if (mixed) return plan_apply64e(p, MIX_KF, p->u_dev, p->r64, -1.0, 1.0, 0.0, nullptr, s);
+    return plan_apply64(p, MIX_K, p->u_dev, p->r64, -1.0, 1.0, 1.0, p->b64, s);
+}
+
+static KrylovOp plan_krylov_op(rte_plan p) {
+    KrylovOp o;
+    o.ctx = p;
+    o.nr = p->nr;
+    o.nw1 = p->dim == 2 ? 2L * p->n * p->n : p->nr;
+    o.u = p->u_dev;
+    o.b64 = p->b64;
+    o.r64 = p->r64;
+    o.x64 = (double*)p->x64;
+    o.part64 = p->part64;
+    o.r32 = (float*)p->r32;
+    o.d32 = (float*)p->d32;
+    o.pv1 = p->pv1;
+    o.ref = p->ref;
+    o.A32 = plan_A32;
+    o.A64 = plan_A64;
+    o.pcA32 = plan_pcA;
+    o.rhs = plan_rhs;
+    o.resid = plan_resid;
+    return o;
+}
+
 rte_status solve_graph_append(rte_plan p, int prec, int m, bool minres, bool pc, cudaGraph_t g,
                               cudaGraphNode_t* dep, cudaStream_t cs, SolveGraphInfo* info) {
     CountGuard guard;
     const rte_prec saved = p->opts.prec;
     p->opts.prec = (rte_prec)prec;  // selects the inner spectra precision at capture
-    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(p, p->k64, m, false, false, g, dep, cs, info)
-                                          : build_solve<float>(p, p->k32, m, minres, pc, g, dep, cs, info);
+    const KrylovOp o = plan_krylov_op(p);
+    rte_status st = prec == RTE_PREC_FP64 ? build_solve<double>(o, p->k64, m, false, false, g, dep, cs, info)
+                                          : build_solve<float>(o, p->k32, m, minres, pc, g, dep, cs, info);
     p->opts.prec = saved;
+    return st;
+}
+
+rte_status krylov_op_graph(const KrylovOp& o, KrylovWs& ws, int prec, int m, cudaStream_t s, void** exec,
+                           SolveGraphInfo* info) {
+    *exec = nullptr;
+    RTE_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaGraph_t g = nullptr;
+    RTE_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return rte_cuda_fail(e, "krylov_op_graph");
+    }
+    cudaGraphNode_t dep = nullptr;
+    rte_status st;
+    {
+        CountGuard guard;
+        *info = SolveGraphInfo();
+        st = prec == RTE_PREC_FP64 ? build_solve<double>(o, ws, m, false, false, g, &dep, cs, info)
+                                   : build_solve<float>(o, ws, m, false, false, g, &dep, cs, info);
+    }
+    cudaStreamDestroy(cs);
+    if (st == RTE_OK) {
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        if (e != cudaSuccess) st = rte_cuda_fail(e, "instantiate solve graph");
+        else *exec = ex;
+    }
+    cudaGraphDestroy(g);
     return st;
 }
 
@@ -1520,25 +1596,55 @@ rte_status solve_set_options(rte_plan p, const rte_opts* o, cudaStream_t s) {
     return RTE_OK;
 }
 
-rte_status solve_collect(rte_plan p, int prec, const RefDev* hr, rte_stats* stats, double ms) {
-    const SolveGraphInfo& gi = p->graphs[prec].info;
+static rte_status collect_core(const SolveGraphInfo& gi, int prec, const RefDev* hr, double rho, double ms_pre,
+                               rte_stats* stats, double ms) {
     rte_count_launches(gi.k_fixed + (hr->use_guess ? gi.k_guess : 0) + (long long)hr->outer * gi.k_outer +
                        (long long)hr->cycles * gi.k_cycle + (long long)hr->its * gi.k_step +
                        (long long)hr->restarts * gi.k_restart);
     if (stats) {
-        const double rho = p->mu_t > 0 ? p->mu_s / p->mu_t : 0.0;
         const double cond = rho < 1.0 ? (1.0 + rho) / (1.0 - rho) : INFINITY;
         stats->iters = hr->its;
         stats->outer = prec == RTE_PREC_FP64 ? 0 : hr->outer;
         stats->relres_true = hr->relres;
         stats->converged = hr->relres <= hr->tol ? 1 : 0;
         stats->ms_total = ms;
-        stats->ms_pre = p->ms_pre;
+        stats->ms_pre = ms_pre;
         stats->est_err_bound = cond * hr->relres;
     }
     if (hr->status == 7 || !isfinite(hr->relres)) return RTE_ENAN;
     if (!(hr->relres <= hr->tol)) return RTE_ENOCONV;
     return RTE_OK;
+}
+
+rte_status solve_collect(rte_plan p, int prec, const RefDev* hr, rte_stats* stats, double ms) {
+    const double rho = p->mu_t > 0 ? p->mu_s / p->mu_t : 0.0;
+    return collect_core(p->graphs[prec].info, prec, hr, rho, p->ms_pre, stats, ms);
+}
+
+rte_status krylov_op_run(const KrylovOp& op, void* exec, const SolveGraphInfo& info, const rte_opts* o, void* hst,
+                         double rho, double ms_pre, rte_stats* stats, cudaStream_t s) {
+    RefDev* h = (RefDev*)hst;
+    RefDev* hr = h + 1;
+    fill_ref_template(h, o);
+    cudaEvent_t ev0, ev1;
+    RTE_CUDA_TRY(cudaEventCreate(&ev0));
+    cudaError_t e = cudaEventCreate(&ev1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev0);
+        return rte_cuda_fail(e, "krylov_op_run");
+    }
+    e = cudaMemcpyAsync(op.ref, h, sizeof(RefDev), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch((cudaGraphExec_t)exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr, op.ref, sizeof(RefDev), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e != cudaSuccess) return rte_cuda_fail(e, "krylov_op_run");
+    return collect_core(info, (int)o->prec, hr, rho, ms_pre, stats, ms);
 }
 
 size_t refdev_size() { return sizeof(RefDev); }

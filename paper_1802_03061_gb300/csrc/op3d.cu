@@ -19,202 +19,7 @@
 
 #include "op3d_passes.cuh"
 
-template <typename RO, typename RR> __device__ __forceinline__ RO out_cast(RR v) { return static_cast<RO>(v); }
-
-template <int RQ, typename T, typename RI>
-__global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __restrict__ T1,
-                                                 const T* __restrict__ tw, int n, int H, double w,
-                                                 const double* __restrict__ xf) {
-    constexpr int Q = 32 * RQ, LS = Q + 34;  // a line also holds the warp's FFT scratch (Q + 32)
-    using RR = typename real_of<T>::R;
-    extern __shared__ unsigned char smraw[];
-    T* twl = reinterpret_cast<T*>(smraw);
-    T* Z = twl + Q;
-    const int z = blockIdx.y, y0 = blockIdx.x * 16;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    __syncthreads();
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const RR ww = (RR)w;
-    const int ya = y0 + 2 * wp, yb = ya + 1;
-    T v[RQ];
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int e = lane + 32 * r;
-        RR a = (RR)0, b = (RR)0;
-        if (e < n) {
-            if (ya < n) a = ww * (RR)x[((long)z * n + ya) * n + e];
-            if (yb < n) b = ww * (RR)x[((long)z * n + yb) * n + e];
-            if (xf) {  // the source joins unweighted: K x + K~ f in one application
-                if (ya < n) a = a + (RR)xf[((long)z * n + ya) * n + e];
-                if (yb < n) b = b + (RR)xf[((long)z * n + yb) * n + e];
-            }
-        }
-        v[r] = mk<T>(a, b);
-    }
-    warp_fft_fwd<RQ>(v, twl, Z + wp * LS);
-#pragma unroll
-    for (int j = 0; j < RQ; ++j) Z[wp * LS + swz16(wfreq<RQ>(j, lane))] = v[j];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < H * 16; idx += blockDim.x) {
-        const int r = idx & 15, xi = idx >> 4;
-        const int y = y0 + r;
-        if (y >= n) continue;
-        const int line = r >> 1;
-        const T Zp = Z[line * LS + swz16(xi)];
-        const T Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
-        T o;
-        if ((r & 1) == 0) o = mk<T>((RR)0.5 * (Zp.x + Zm.x), (RR)0.5 * (Zp.y - Zm.y));
-        else o = mk<T>((RR)0.5 * (Zp.y + Zm.y), (RR)-0.5 * (Zp.x - Zm.x));
-        T1[((long)z * H + xi) * n + y] = o;
-    }
-}
-
-template <int RQ, typename T>
-__global__ void __launch_bounds__(512) k3w_y_fwd(const T* __restrict__ T1, T* __restrict__ T2,
-                                                 const T* __restrict__ tw, int n, int H) {
-    constexpr int Q = 32 * RQ, ZS = 17;
-    extern __shared__ unsigned char smraw[];
-    T* twl = reinterpret_cast<T*>(smraw);
-    T* Y = twl + Q;  // [s][ZS] tile; before it is written, the 16 warps' FFT scratch
-    const int kx = blockIdx.y, z0 = blockIdx.x * 16;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    __syncthreads();
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int z = z0 + wp;
-    T v[RQ];
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int y = lane + 32 * r;
-        v[r] = (z < n && y < n) ? T1[((long)z * H + kx) * n + y] : mk<T>(0, 0);
-    }
-    warp_fft_fwd<RQ>(v, twl, Y + wp * wfft_shape<RQ>::SCRATCH);
-    __syncthreads();  // every warp is done with its scratch
-#pragma unroll
-    for (int k1 = 0; k1 < RQ; ++k1) Y[(k1 * 32 + lane) * ZS + wp] = v[k1];
-    __syncthreads();
-    const int nz = min(16, n - z0);
-    for (int idx = threadIdx.x; idx < Q * 16; idx += blockDim.x) {
-        const int zl = idx & 15, sl = idx >> 4;
-        if (zl < nz) T2[((long)kx * Q + sl) * n + z0 + zl] = Y[sl * ZS + zl];
-    }
-}
-
-template <int RQ, typename T, typename TS>
-__global__ void __launch_bounds__(256) k3w_z_mix(T* __restrict__ T2, const TS* __restrict__ S,
-                                                 const T* __restrict__ tw, int n, int H, long nlines) {
-    constexpr int Q = 32 * RQ;
-    using RR = typename real_of<T>::R;
-    extern __shared__ unsigned char smraw[];
-    T* twl = reinterpret_cast<T*>(smraw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* scr = twl + Q + warp * wfft_shape<RQ>::SCRATCH;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    __syncthreads();
-    const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (line >= nlines) return;
-    T v[RQ];
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int z = lane + 32 * r;
-        v[r] = z < n ? T2[line * n + z] : mk<T>(0, 0);
-    }
-    warp_fft_fwd<RQ>(v, twl, scr);
-    const int kx = (int)(line / Q), sl = (int)(line % Q);
-    const int ky = wfreq<RQ>(sl >> 5, sl & 31);  // slot -> frequency
-    const TS* Srow = S + ((long)kx * H + fold(ky, Q)) * H;
-#pragma unroll
-    for (int j = 0; j < RQ; ++j) {
-        const RR sv = (RR)Srow[fold(wfreq<RQ>(j, lane), Q)];
-        v[j] = mk<T>(v[j].x * sv, v[j].y * sv);
-    }
-    warp_fft_inv<RQ>(v, twl, scr);
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int z = lane + 32 * r;
-        if (z < n) T2[line * n + z] = v[r];
-    }
-}
-
-template <int RQ, typename T>
-__global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __restrict__ T1,
-                                                 const T* __restrict__ tw, int n, int H) {
-    constexpr int Q = 32 * RQ, ZS = 17;
-    extern __shared__ unsigned char smraw[];
-    T* twl = reinterpret_cast<T*>(smraw);
-    T* Y = twl + Q;  // [s][ZS] tile, then the 16 warps' FFT scratch
-    const int kx = blockIdx.y, z0 = blockIdx.x * 16;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    const int nz = min(16, n - z0);
-    for (int idx = threadIdx.x; idx < Q * 16; idx += blockDim.x) {
-        const int zl = idx & 15, sl = idx >> 4;
-        Y[sl * ZS + zl] = zl < nz ? T2[((long)kx * Q + sl) * n + z0 + zl] : mk<T>(0, 0);
-    }
-    __syncthreads();
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T v[RQ];
-#pragma unroll
-    for (int k1 = 0; k1 < RQ; ++k1) v[k1] = Y[(k1 * 32 + lane) * ZS + wp];
-    __syncthreads();  // the tile is read; its space becomes the warps' FFT scratch
-    warp_fft_inv<RQ>(v, twl, Y + wp * wfft_shape<RQ>::SCRATCH);
-    const int z = z0 + wp;
-    if (z >= n) return;
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int y = lane + 32 * r;
-        if (y < n) T1[((long)z * H + kx) * n + y] = v[r];
-    }
-}
-
-template <int RQ, typename T, typename RI>
-__global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const RI* __restrict__ x,
-                                                 const RI* __restrict__ zv, RI* __restrict__ out,
-                                                 const T* __restrict__ tw, int n, int H, double a, double b,
-                                                 double c) {
-    constexpr int Q = 32 * RQ, LS = Q + 34;
-    using RR = typename real_of<T>::R;
-    extern __shared__ unsigned char smraw[];
-    T* twl = reinterpret_cast<T*>(smraw);
-    T* Z = twl + Q;
-    const int z = blockIdx.y, y0 = blockIdx.x * 16;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
-    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
-        const int li = idx & 7, xi = idx >> 3;
-        const int ya = y0 + 2 * li, yb = ya + 1;
-        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
-        if (ya < n) Fv = T1[((long)z * H + xi) * n + ya];
-        if (yb < n) Gv = T1[((long)z * H + xi) * n + yb];
-        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
-    }
-    __syncthreads();
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T v[RQ];
-#pragma unroll
-    for (int j = 0; j < RQ; ++j) v[j] = Z[wp * LS + swz16(wfreq<RQ>(j, lane))];
-    __syncwarp();
-    warp_fft_inv<RQ>(v, twl, Z + wp * LS);
-    const RR ra = (RR)a, rb = (RR)b, rc = (RR)c;
-    const int ya = y0 + 2 * wp, yb = ya + 1;
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int e = lane + 32 * r;
-        if (e >= n) continue;
-        if (ya < n) {
-            const long o = ((long)z * n + ya) * n + e;
-            RR q = rb * v[r].x;
-            if (x) q = q + ra * (RR)x[o];
-            if (zv) q = q + rc * (RR)zv[o];
-            out[o] = out_cast<RI>(q);
-        }
-        if (yb < n) {
-            const long o = ((long)z * n + yb) * n + e;
-            RR q = rb * v[r].y;
-            if (x) q = q + ra * (RR)x[o];
-            if (zv) q = q + rc * (RR)zv[o];
-            out[o] = out_cast<RI>(q);
-        }
-    }
-}
+#include "op3d_warp.cuh"
 
 template <int RQ, typename T, typename R, typename TS>
 static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, double a, double b, double c,

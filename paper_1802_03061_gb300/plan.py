@@ -298,6 +298,13 @@ class Aniso3D:
         B.rte_aniso3d_apply_K(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
         return y
 
+    def apply_K64e(self, x, stream=None):
+        """K x to FP64 accuracy in float-float arithmetic (the residual's form)."""
+        x = self._field(x, torch.float64, self.M)
+        y = torch.empty_like(x)
+        B.rte_aniso3d_apply_K64e(self.handle, x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        return y
+
     def apply_K32(self, x, stream=None):
         x = self._field(x, torch.float32, self.M)
         y = torch.empty_like(x)
@@ -311,7 +318,8 @@ class Aniso3D:
         return b
 
     def solve(self, f, tol=1e-10, restart=40, maxit=400, prec="fp64", stream=None):
-        """prec: "fp64" or "mixed_fp32" (FP32 inner GMRES, FP64 residuals)."""
+        """prec: "fp64" or "mixed_fp32" (FP32 inner GMRES, FP64-accurate
+        residuals); the device solve graph of rte_solve on this operator."""
         f = self._field(f, torch.float64, 0)
         u = torch.empty((self.M,) + (self.n,) * 3, dtype=torch.float64, device="cuda")
         stats = B.rte_aniso3d_solve(self.handle, f.data_ptr(), u.data_ptr(), tol, restart, maxit, prec,

@@ -100,9 +100,37 @@ def test_inhom_create_fails_cleanly():
     _every_failure(lambda: B.rte_inhom_create(12, 1.0 / 12, np.ascontiguousarray(mu)), B.rte_inhom_destroy)
 
 
-def test_aniso3d_create_fails_cleanly():
+@pytest.mark.parametrize("n", [6, 20])  # the Stockham and the warp passes (float-float copies)
+def test_aniso3d_create_fails_cleanly(n):
     from paper_1802_03061_gb300 import _binding as B
-    _every_failure(lambda: B.rte_aniso3d_create(6, 1.0 / 6, 4.0, 3.0, 1, [1.0, 0.5]), B.rte_aniso3d_destroy)
+    _every_failure(lambda: B.rte_aniso3d_create(n, 1.0 / n, 4.0, 3.0, 1, [1.0, 0.5]), B.rte_aniso3d_destroy)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_aniso3d_first_solve_failure_leaves_the_handle_usable(prec):
+    """The first solve allocates its vectors and the Krylov workspace: a
+    failure there returns RTE_ENOMEM, and a later solve of the same handle
+    gives the result of an undisturbed one."""
+    from paper_1802_03061_gb300 import Aniso3D
+    from paper_1802_03061_gb300 import _binding as B
+    n = 20
+    f = rte_synth.gaussian_3d(n, (0.4, 0.5, 0.5), 0.1)
+    ref = Aniso3D(n, 6.0, 5.0, [1.0, 0.5])
+    B.rte_debug_fail_alloc(0)
+    want, st = ref.solve(f, tol=1e-9, prec=prec)
+    seen, _, _ = B.rte_debug_fail_alloc(0)
+    ref.close()
+    assert st["converged"] and seen >= 3
+    for k in range(1, seen + 1):
+        op = Aniso3D(n, 6.0, 5.0, [1.0, 0.5])
+        B.rte_debug_fail_alloc(k)
+        with pytest.raises(B.RteError) as ei:
+            op.solve(f, tol=1e-9, prec=prec)
+        assert ei.value.status == B.RTE_ENOMEM
+        B.rte_debug_fail_alloc(0)
+        u, st = op.solve(f, tol=1e-9, prec=prec)
+        assert st["converged"] and torch.equal(u, want)
+        op.close()
 
 
 def test_cnn_create_fails_cleanly():

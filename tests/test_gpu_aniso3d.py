@@ -1,8 +1,11 @@
 """GPU parity of the 3D anisotropic (spherical-harmonic) operator through the
-C ABI against the oracle (oracle/aniso3d.py).  Tolerances: FP64 1e-12
-relative L2 (FFT rounding over Q^3 points); FP32 1e-5 (FP32 spectra and
-FFTs); solves (FP64 GMRES or FP32 inner GMRES with FP64 residuals) within
-100 tol cond of the dense LU solution, cond = (1 + r)/(1 - r) = 39 here."""
+C ABI against the oracle (oracle/aniso3d.py).  Two pass families: the
+general-Q Stockham passes channel by channel (n <= 16 and n > 128) and the
+warp-register passes over all channels per launch (17 <= n <= 128, Q = 64,
+128, 256).  Tolerances: FP64 and float-float 1e-12 relative L2 (FFT
+rounding over Q^3 points); FP32 1e-5 (FP32 spectra and FFTs); solves (FP64
+GMRES or FP32 inner GMRES with FP64-accurate residuals) within 2 tol cond of
+the dense LU solution, cond = (1 + r)/(1 - r)."""
 import numpy as np
 import pytest
 
@@ -47,28 +50,40 @@ def test_apply_matches_oracle(n, L):
     x = np.random.default_rng(10 * n + L).standard_normal((M, n, n, n))
     ref = A.apply_K(n, 1.0 / n, mu_t, mu_s, sig, x).reshape(M, n, n, n)
     assert rel(op.apply_K(x).cpu().numpy(), ref) < 1e-12
+    assert rel(op.apply_K64e(x).cpu().numpy(), ref) < 1e-12
     assert rel(op.apply_K32(x).cpu().numpy(), ref) < 1e-5
     f = np.random.default_rng(n).random((n, n, n))
     assert rel(op.rhs(f).cpu().numpy(), A.rhs(n, 1.0 / n, mu_t, L, f).reshape(M, n, n, n)) < 1e-12
     op.close()
 
 
-@pytest.mark.parametrize("n,L", [(33, 2), (48, 1)])
-def test_sampled_rows_larger_grids(n, L):
-    """Q = 72 (a radix-3 length) and 96; sampled rows against the direct sum."""
+# warp passes: n = 17 (Q = 64, ragged against the 16-row tiles), 24 with L = 4
+# (M = 25), 33 and 48 (Q = 128), 97 (Q = 256); Stockham: 12 (Q = 24, radix 3)
+# and 130 (Q = 288 = 2^5 3^2)
+@pytest.mark.parametrize("n,L,Q", [(17, 2, 64), (24, 4, 64), (33, 2, 128), (48, 1, 128), (97, 1, 256), (12, 3, 24),
+                                   (130, 1, 288)])
+def test_sampled_rows_larger_grids(n, L, Q):
+    """Sampled rows (all M channels) of K x, K x in float-float and in FP32,
+    and of the right-hand side, against the direct sums."""
     from paper_1802_03061_gb300 import Aniso3D
     mu_t, mu_s = 10.0, 9.0
     sig = _hg(0.6, L)
     op = Aniso3D(n, mu_t, mu_s, sig)
+    assert op.Q == Q
     M = op.M
     x = np.random.default_rng(n).standard_normal((M, n, n, n))
     y = op.apply_K(x).cpu().numpy().reshape(M, -1)
+    ye = op.apply_K64e(x).cpu().numpy().reshape(M, -1)
     y32 = op.apply_K32(x).cpu().numpy().reshape(M, -1)
-    rows = np.random.default_rng(1).choice(n ** 3, size=10, replace=False)
+    rows = np.random.default_rng(1).choice(n ** 3, size=6 if n > 64 else 10, replace=False)
     D = A.cell_weights(L, mu_t, 1.0 / n)
     ref = A.apply_K(n, 1.0 / n, mu_t, mu_s, sig, x, rows=rows, D=D)
     assert rel(y[:, rows], ref) < 1e-12
+    assert rel(ye[:, rows], ref) < 1e-12
     assert rel(y32[:, rows], ref) < 1e-5
+    f = np.random.default_rng(n + 1).random((n, n, n))
+    b = op.rhs(f).cpu().numpy().reshape(M, -1)
+    assert rel(b[:, rows], A.rhs(n, 1.0 / n, mu_t, L, f, rows=rows, D=D)) < 1e-12
     op.close()
 
 
@@ -121,6 +136,32 @@ def test_solve_larger_grid_sampled_residual(prec):
     r = U[:, rows] - A.apply_K(n, 1.0 / n, mu_t, mu_s, sig, U, rows=rows, D=D) \
         - A.rhs(n, 1.0 / n, mu_t, L, f, rows=rows, D=D)
     assert np.abs(r).max() < 1e-8 * np.abs(U).max()
+    # a second solve of the same handle (cached graph) with another source and
+    # restart length, against a fresh handle's
+    f2 = rte_synth.gaussian_3d(n, (0.5, 0.6, 0.3), 0.1)
+    u2, st2 = op.solve(f2, tol=1e-10, restart=30, prec=prec)
+    u3, st3 = op.solve(f2, tol=1e-10, restart=30, prec=prec)
+    assert torch.equal(u2, u3) and st2["iters"] == st3["iters"]
+    fresh = Aniso3D(n, mu_t, mu_s, sig)
+    u4, _ = fresh.solve(f2, tol=1e-10, restart=30, prec=prec)
+    assert torch.equal(u2, u4)
+    fresh.close()
+    op.close()
+
+
+def test_solve_non_finite_source():
+    from paper_1802_03061_gb300 import Aniso3D
+    from paper_1802_03061_gb300 import _binding as B
+    op = Aniso3D(20, 5.0, 4.0, _hg(0.5, 1))
+    f = np.ones((20, 20, 20))
+    f[3, 4, 5] = np.nan
+    for prec in ("fp64", "mixed_fp32"):
+        with pytest.raises(B.RteError) as ei:
+            op.solve(f, prec=prec)
+        assert ei.value.status == B.RTE_ENAN
+    # the handle still solves afterwards
+    u, st = op.solve(np.ones((20, 20, 20)), tol=1e-9, prec="mixed_fp32")
+    assert st["converged"]
     op.close()
 
 
