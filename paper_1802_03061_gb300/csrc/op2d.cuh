@@ -280,6 +280,22 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
     const int rows = k == 0 ? 16 : 8;
     const int y0 = blockIdx.x * rows;
     if (y0 >= n) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the epilogue's x values (mode 0: rows ya, yb; mode k: row y), loaded
+    // before the transform so that their latency overlaps it: n <= Q/2, so
+    // only registers r < R/2 hold x < n
+    constexpr int RH = R / 2;
+    TF px0[RH], px1[RH];
+    {
+        const int ya = k == 0 ? y0 + 2 * w : y0 + w, yb = ya + 1;
+        const long ra = k == 0 ? (long)ya * n : ((long)k * n + ya) * n, rb = (long)yb * n;
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int e = lane + 32 * r;
+            px0[r] = (x && e < n && ya < n) ? x[ra + e] : TF{};
+            px1[r] = (x && k == 0 && e < n && yb < n) ? x[rb + e] : TF{};
+        }
+    }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     // Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
@@ -300,14 +316,13 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
         if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
     }
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T v[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = Z[w * LS + swz16(wfreq<R>(j, lane))];
     __syncwarp();
     warp_fft_inv<R>(v, twl, Z + w * LS);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < RH; ++r) {
         const int e = lane + 32 * r;
         if (e >= n) continue;
         if (k == 0) {
@@ -315,14 +330,14 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
             if (ya < n) {
                 const long o = (long)ya * n + e;
                 T q = mk<T>(b * v[r].x, (RR)0);
-                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (x) { const T xv = to_c<T>(px0[r]); q.x += a * xv.x; q.y += a * xv.y; }
                 if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
                 out[o] = to_f<TF>(q);
             }
             if (yb < n) {
                 const long o = (long)yb * n + e;
                 T q = mk<T>(b * v[r].y, (RR)0);
-                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (x) { const T xv = to_c<T>(px1[r]); q.x += a * xv.x; q.y += a * xv.y; }
                 if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
                 out[o] = to_f<TF>(q);
             }
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
             if (y < n) {
                 const long o = ((long)k * n + y) * n + e;
                 T q = mk<T>(b * v[r].x, b * v[r].y);
-                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (x) { const T xv = to_c<T>(px0[r]); q.x += a * xv.x; q.y += a * xv.y; }
                 if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
                 out[o] = to_f<TF>(q);
             }

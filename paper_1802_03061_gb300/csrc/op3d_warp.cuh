@@ -184,40 +184,50 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
         if (zv) zv += ch * N3;
         out += ch * N3;
     }
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ya = y0 + 2 * wp, yb = ya + 1;
+    // the epilogue's x values, loaded before the transform so that their
+    // latency overlaps it: n <= Q/2, so only registers r < RQ/2 hold x < n
+    constexpr int RH = RQ / 2;
+    RI pxa[RH], pxb[RH];
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+        const int e = lane + 32 * r;
+        pxa[r] = (x && e < n && ya < n) ? x[((long)z * n + ya) * n + e] : (RI)0;
+        pxb[r] = (x && e < n && yb < n) ? x[((long)z * n + yb) * n + e] : (RI)0;
+    }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
         const int li = idx & 7, xi = idx >> 3;
-        const int ya = y0 + 2 * li, yb = ya + 1;
+        const int la = y0 + 2 * li, lb = la + 1;
         T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
-        if (ya < n) Fv = T1[((long)z * H + xi) * n + ya];
-        if (yb < n) Gv = T1[((long)z * H + xi) * n + yb];
+        if (la < n) Fv = T1[((long)z * H + xi) * n + la];
+        if (lb < n) Gv = T1[((long)z * H + xi) * n + lb];
         Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
         if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
     }
     __syncthreads();
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T v[RQ];
 #pragma unroll
     for (int j = 0; j < RQ; ++j) v[j] = Z[wp * LS + swz16(wfreq<RQ>(j, lane))];
     __syncwarp();
     warp_fft_inv<RQ>(v, twl, Z + wp * LS);
     const RR ra = (RR)a, rb = (RR)b, rc = (RR)c;
-    const int ya = y0 + 2 * wp, yb = ya + 1;
 #pragma unroll
-    for (int r = 0; r < RQ; ++r) {
+    for (int r = 0; r < RH; ++r) {
         const int e = lane + 32 * r;
         if (e >= n) continue;
         if (ya < n) {
             const long o = ((long)z * n + ya) * n + e;
             RR q = rb * v[r].x;
-            if (x) q = q + ra * (RR)x[o];
+            if (x) q = q + ra * (RR)pxa[r];
             if (zv) q = q + rc * (RR)zv[o];
             out[o] = out_cast<RI>(q);
         }
         if (yb < n) {
             const long o = ((long)z * n + yb) * n + e;
             RR q = rb * v[r].y;
-            if (x) q = q + ra * (RR)x[o];
+            if (x) q = q + ra * (RR)pxb[r];
             if (zv) q = q + rc * (RR)zv[o];
             out[o] = out_cast<RI>(q);
         }
