@@ -72,6 +72,8 @@ __global__ void __launch_bounds__(256) k3wa_z_mix(T* __restrict__ T2, long chs, 
     const int nb = (int)min((long)B, nlines - l0);
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     for (int i = threadIdx.x; i < M * M; i += blockDim.x) pis[i] = pinfo[i];
+    pdl_wait();  // T2: the y pass's output
+    pdl_trigger();
     __syncthreads();
     for (int it = warp; it < Min * nb; it += 8) {
         const int c = it / nb, lb = it - c * nb;
@@ -174,6 +176,8 @@ __global__ void __launch_bounds__(32 * zpair_warps<LT>())
         twl[i] = tw[i];
         slot_of[wfreq<RQ>(i >> 5, i & 31)] = i;
     }
+    pdl_wait();  // T2: the y pass's output (the spectra are plan constants)
+    pdl_trigger();
     __syncthreads();
     for (int it = warp; it < Min * nb; it += NW) {
         const int c = it / nb, lb = it - c * nb;
@@ -327,11 +331,14 @@ static cudaError_t run_rq(rte_aniso3d op, const R* x, R* out, int rhs, double ca
     const int Min = rhs ? 1 : M;
     const unsigned gy = (unsigned)((n + 15) / 16);
     cudaError_t e;
-    k3w_x_fwd<RQ, T, R><<<dim3(gy, n, Min), 256, smx, s>>>(x, T1, tw, n, H, 1.0, rhs ? nullptr : xf,
-                                                          rhs ? nullptr : op->wz);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k3w_y_fwd<RQ, T><<<dim3(gy, H, Min), 512, smy, s>>>(T1, T2, tw, n, H);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double* xf0 = rhs ? nullptr : xf;
+    const double* wz0 = rhs ? nullptr : op->wz;
+    if ((e = launch_pdl(k3w_x_fwd<RQ, T, R>, dim3(gy, n, Min), dim3(256), smx, s, x, T1, tw, n, H, 1.0, xf0, wz0)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k3w_y_fwd<RQ, T>, dim3(gy, H, Min), dim3(512), smy, s, (const T*)T1, T2, tw, n, H)) !=
+        cudaSuccess)
+        return e;
     const long nlines = (long)H * Q;
     if (op->L <= 2) {
         const long bp = zpair_buf(RQ, M);
@@ -339,21 +346,26 @@ static cudaError_t run_rq(rte_aniso3d op, const R* x, R* out, int rhs, double ca
         const unsigned grid = (unsigned)H * H;
         const long H3 = (long)H * H * H;
         if (op->L == 0)
-            k3wa_z_pair<RQ, T, TS, 0><<<grid, 32 * zpair_warps<0>(), smp, s>>>(T2, chs, Min, S, H3, tw, n, H, (int)bp);
+            e = launch_pdl(k3wa_z_pair<RQ, T, TS, 0>, dim3(grid), dim3(32 * zpair_warps<0>()), smp, s, T2, chs, Min,
+                           S, H3, tw, n, H, (int)bp);
         else if (op->L == 1)
-            k3wa_z_pair<RQ, T, TS, 1><<<grid, 32 * zpair_warps<1>(), smp, s>>>(T2, chs, Min, S, H3, tw, n, H, (int)bp);
+            e = launch_pdl(k3wa_z_pair<RQ, T, TS, 1>, dim3(grid), dim3(32 * zpair_warps<1>()), smp, s, T2, chs, Min,
+                           S, H3, tw, n, H, (int)bp);
         else
-            k3wa_z_pair<RQ, T, TS, 2><<<grid, 32 * zpair_warps<2>(), smp, s>>>(T2, chs, Min, S, H3, tw, n, H, (int)bp);
+            e = launch_pdl(k3wa_z_pair<RQ, T, TS, 2>, dim3(grid), dim3(32 * zpair_warps<2>()), smp, s, T2, chs, Min,
+                           S, H3, tw, n, H, (int)bp);
     } else {
-        k3wa_z_mix<RQ, T, TS><<<(unsigned)((nlines + B - 1) / B), 256, smz, s>>>(
-            T2, chs, Min, M, S, (long)H * H * H, op->pinfo, M, tw, n, H, B, (int)bufl);
+        e = launch_pdl(k3wa_z_mix<RQ, T, TS>, dim3((unsigned)((nlines + B - 1) / B)), dim3(256), smz, s, T2, chs, Min,
+                       M, S, (long)H * H * H, (const int*)op->pinfo, M, tw, n, H, B, (int)bufl);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k3w_y_inv<RQ, T><<<dim3(gy, H, M), 512, smy, s>>>(T2, T1, tw, n, H);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k3w_x_inv<RQ, T, R><<<dim3(gy, n, M), 256, smx, s>>>(T1, (rhs || ca == 0.0) ? nullptr : x, zv, out, tw, n, H,
-                                                         ca, cb, cc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
+    if ((e = launch_pdl(k3w_y_inv<RQ, T>, dim3(gy, H, M), dim3(512), smy, s, (const T*)T2, T1, tw, n, H)) !=
+        cudaSuccess)
+        return e;
+    const R* xe = (rhs || ca == 0.0) ? nullptr : x;
+    if ((e = launch_pdl(k3w_x_inv<RQ, T, R>, dim3(gy, n, M), dim3(256), smx, s, (const T*)T1, xe, zv, out, tw, n, H,
+                        ca, cb, cc)) != cudaSuccess)
+        return e;
     rte_count_launches(5);
     return cudaSuccess;
 }

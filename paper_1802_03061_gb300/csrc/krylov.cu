@@ -386,6 +386,8 @@ __device__ __forceinline__ void ff_fma4(float& hi, float& lo, float4 a, const fl
 
 __global__ void __launch_bounds__(256) k_step_dot4(float* __restrict__ V, long nr, const float* __restrict__ w,
                                                    GmresDev* __restrict__ st, long nw1, double* __restrict__ part) {
+    pdl_wait();  // w: the operator's output
+    pdl_trigger();
     const int j = st->j, count = j + 1;
     const float s = (float)st->vscale;
     const bool rescale = s != 1.f;
@@ -471,6 +473,8 @@ __global__ void __launch_bounds__(256) k_step_upd4(const float* __restrict__ V, 
                                                    float* __restrict__ vin, GmresDev* __restrict__ st, long nw1,
                                                    double* __restrict__ part, cudaGraphConditionalHandle loop,
                                                    const float* __restrict__ zsrc, float* __restrict__ Z) {
+    pdl_wait();  // hA: the multi-dot's result
+    pdl_trigger();
     const int j = st->j, count = j + 1;
     const float s = (float)st->vscale;
     const int nb = gridDim.x;
@@ -557,6 +561,8 @@ __global__ void __launch_bounds__(256) k_step_upd4(const float* __restrict__ V, 
 
 __global__ void __launch_bounds__(256) k_step_dot(float* __restrict__ V, long nr, const float* __restrict__ w,
                                                   GmresDev* __restrict__ st, long nw1, double* __restrict__ part) {
+    pdl_wait();  // w: the operator's output
+    pdl_trigger();
     const int j = st->j, count = j + 1;
     const float s = (float)st->vscale;
     const bool rescale = s != 1.f;
@@ -617,6 +623,8 @@ __global__ void __launch_bounds__(256) k_step_upd(const float* __restrict__ V, l
                                                   float* __restrict__ vin, GmresDev* __restrict__ st, long nw1,
                                                   double* __restrict__ part, cudaGraphConditionalHandle loop,
                                                   const float* __restrict__ zsrc, float* __restrict__ Z) {
+    pdl_wait();  // hA: the multi-dot's result
+    pdl_trigger();
     const int j = st->j, count = j + 1;
     const float s = (float)st->vscale;
     const int nb = gridDim.x;
@@ -1153,19 +1161,20 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditiona
     const int* jp = &G.st->j;
     if constexpr (sizeof(T) == sizeof(float)) {
         if (!cgs2) {
+            const float* zs = pc ? G.op->pv1 : nullptr;
+            float* Zs = pc ? (float*)G.Z : nullptr;
             if (nr % 4 == 0) {
-                k_step_dot4<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
-                k_step_upd4<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
-                                               G.nw1, G.part, loop, pc ? G.op->pv1 : nullptr,
-                                               pc ? (float*)G.Z : nullptr);
+                RTE_CUDA_TRY(launch_pdl(k_step_dot4, dim3(nb), dim3(256), 0, s, (float*)G.V, nr,
+                                        (const float*)G.w, G.st, G.nw1, G.part));
+                RTE_CUDA_TRY(launch_pdl(k_step_upd4, dim3(nb), dim3(256), 0, s, (const float*)G.V, nr,
+                                        (const float*)G.w, (float*)G.vin, G.st, G.nw1, G.part, loop, zs, Zs));
             } else {
-                k_step_dot<<<nb, 256, 0, s>>>((float*)G.V, nr, (const float*)G.w, G.st, G.nw1, G.part);
-                k_step_upd<<<nb, 256, 0, s>>>((const float*)G.V, nr, (const float*)G.w, (float*)G.vin, G.st,
-                                              G.nw1, G.part, loop, pc ? G.op->pv1 : nullptr,
-                                              pc ? (float*)G.Z : nullptr);
+                RTE_CUDA_TRY(launch_pdl(k_step_dot, dim3(nb), dim3(256), 0, s, (float*)G.V, nr, (const float*)G.w,
+                                        G.st, G.nw1, G.part));
+                RTE_CUDA_TRY(launch_pdl(k_step_upd, dim3(nb), dim3(256), 0, s, (const float*)G.V, nr,
+                                        (const float*)G.w, (float*)G.vin, G.st, G.nw1, G.part, loop, zs, Zs));
             }
             rte_count_launches(2);
-            RTE_CUDA_TRY(cudaGetLastError());
             return RTE_OK;
         }
     }

@@ -209,6 +209,8 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const TF* __restrict__ x, 
     const int y0 = blockIdx.x * rows;
     if (y0 >= n) return;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // x may be the predecessor's output
+    pdl_trigger();
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RR wt = (RR)p.wk[k];
@@ -297,6 +299,8 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
         }
     }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // in: the column pass's output
+    pdl_trigger();
     // Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
         const int li = idx & 7, xi = idx >> 3;
@@ -543,6 +547,8 @@ __global__ void __launch_bounds__(256) k_row_invfwd_warp(float2* __restrict__ Tb
     const int y0 = blockIdx.x * rows;
     if (y0 >= n) return;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // Tb: the column pass's output
+    pdl_trigger();
     // M: Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
         const int li = idx & 7, xi = idx >> 3;
@@ -1063,6 +1069,8 @@ __global__ void __launch_bounds__(256) k_col_warp(float2* __restrict__ Tb, const
     float2* X = reinterpret_cast<float2*>(smraw);  // [NCH][QS]
     const int kx = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    pdl_wait();  // Tb: the row pass's output
+    pdl_trigger();
     for (int c = warp; c < nin; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;

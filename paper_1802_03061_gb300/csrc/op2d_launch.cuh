@@ -95,8 +95,7 @@ static cudaError_t launch_col_warp(float2* Tb, const TS* Sp, const float2* tw, c
     cudaError_t e;
     if (!once) { e = allow_smem(k_col_warp<L, R, TS>); if (e != cudaSuccess) return e; once = true; }
     const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2);
-    k_col_warp<L, R, TS><<<cp.H, 256, smem, s>>>(Tb, Sp, tw, cp.n, cp.H, cp.nin);
-    return cudaGetLastError();
+    return launch_pdl(k_col_warp<L, R, TS>, dim3(cp.H), dim3(256), smem, s, Tb, Sp, tw, cp.n, cp.H, cp.nin);
 }
 
 // Q = 1024: two 512-point residues per block (k_col_warp2), Tz holds the first
@@ -232,11 +231,12 @@ static cudaError_t row_fwd_warp(int Q, dim3 grid, const TF* x, const double* f, 
             return e;
         once = true;
     }
+    e = cudaSuccess;
     switch (Q) {
-        case 64: k_row_fwd_warp<2, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
-        case 128: k_row_fwd_warp<4, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
-        case 256: k_row_fwd_warp<8, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
-        case 512: k_row_fwd_warp<16, T, TF><<<grid, 256, sm, s>>>(x, f, out, tw, rp); break;
+        case 64: e = launch_pdl(k_row_fwd_warp<2, T, TF>, grid, dim3(256), sm, s, x, f, out, tw, rp); break;
+        case 128: e = launch_pdl(k_row_fwd_warp<4, T, TF>, grid, dim3(256), sm, s, x, f, out, tw, rp); break;
+        case 256: e = launch_pdl(k_row_fwd_warp<8, T, TF>, grid, dim3(256), sm, s, x, f, out, tw, rp); break;
+        case 512: e = launch_pdl(k_row_fwd_warp<16, T, TF>, grid, dim3(256), sm, s, x, f, out, tw, rp); break;
         case 1024:
             if constexpr (std::is_same<T, float2>::value && std::is_same<TF, float2>::value) {
                 static bool once2 = false;
@@ -250,6 +250,7 @@ static cudaError_t row_fwd_warp(int Q, dim3 grid, const TF* x, const double* f, 
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -265,13 +266,15 @@ static cudaError_t row_invfwd_warp(int Q, dim3 grid, float2* Tb, const float2* x
             return e;
         once = true;
     }
+    e = cudaSuccess;
     switch (Q) {
-        case 64: k_row_invfwd_warp<2><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
-        case 128: k_row_invfwd_warp<4><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
-        case 256: k_row_invfwd_warp<8><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
-        case 512: k_row_invfwd_warp<16><<<grid, 256, sm, s>>>(Tb, x, out, tw, rp); break;
+        case 64: e = launch_pdl(k_row_invfwd_warp<2>, grid, dim3(256), sm, s, Tb, x, out, tw, rp); break;
+        case 128: e = launch_pdl(k_row_invfwd_warp<4>, grid, dim3(256), sm, s, Tb, x, out, tw, rp); break;
+        case 256: e = launch_pdl(k_row_invfwd_warp<8>, grid, dim3(256), sm, s, Tb, x, out, tw, rp); break;
+        case 512: e = launch_pdl(k_row_invfwd_warp<16>, grid, dim3(256), sm, s, Tb, x, out, tw, rp); break;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -290,11 +293,12 @@ static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, cons
             return e;
         once = true;
     }
+    e = cudaSuccess;
     switch (Q) {
-        case 64: k_row_inv_warp<2, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
-        case 128: k_row_inv_warp<4, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
-        case 256: k_row_inv_warp<8, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
-        case 512: k_row_inv_warp<16, T, TF><<<grid, 256, sm, s>>>(in, x, z, out, tw, rp, a, b, c); break;
+        case 64: e = launch_pdl(k_row_inv_warp<2, T, TF>, grid, dim3(256), sm, s, in, x, z, out, tw, rp, a, b, c); break;
+        case 128: e = launch_pdl(k_row_inv_warp<4, T, TF>, grid, dim3(256), sm, s, in, x, z, out, tw, rp, a, b, c); break;
+        case 256: e = launch_pdl(k_row_inv_warp<8, T, TF>, grid, dim3(256), sm, s, in, x, z, out, tw, rp, a, b, c); break;
+        case 512: e = launch_pdl(k_row_inv_warp<16, T, TF>, grid, dim3(256), sm, s, in, x, z, out, tw, rp, a, b, c); break;
         case 1024:
             if constexpr (std::is_same<T, float2>::value && std::is_same<TF, float2>::value) {
                 static bool once2 = false;
@@ -308,6 +312,7 @@ static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, cons
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

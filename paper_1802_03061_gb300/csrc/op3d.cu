@@ -51,17 +51,21 @@ static cudaError_t op3d_run_warp(int n, int H, const R* x, R* out, double w, dou
         once = true;
     }
     const unsigned gy = (unsigned)((n + 15) / 16);
-    k3w_x_fwd<RQ, T, R><<<dim3(gy, n), 256, smx, s>>>(x, T1, tw, n, H, w, xf);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k3w_y_fwd<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T1, T2, tw, n, H);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double* nowz = nullptr;
+    if ((e = launch_pdl(k3w_x_fwd<RQ, T, R>, dim3(gy, n), dim3(256), smx, s, x, T1, tw, n, H, w, xf, nowz)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k3w_y_fwd<RQ, T>, dim3(gy, H), dim3(512), smy, s, (const T*)T1, T2, tw, n, H)) != cudaSuccess)
+        return e;
     const long nlines = (long)H * Q;
-    k3w_z_mix<RQ, T, TS><<<(unsigned)((nlines + 7) / 8), 256, smz, s>>>(T2, S, tw, n, H, nlines);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k3w_y_inv<RQ, T><<<dim3(gy, H), 512, smy, s>>>(T2, T1, tw, n, H);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k3w_x_inv<RQ, T, R><<<dim3(gy, n), 256, smx, s>>>(T1, x, z, out, tw, n, H, a, b, c);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(k3w_z_mix<RQ, T, TS>, dim3((unsigned)((nlines + 7) / 8)), dim3(256), smz, s, T2, S, tw, n, H,
+                        nlines)) != cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k3w_y_inv<RQ, T>, dim3(gy, H), dim3(512), smy, s, (const T*)T2, T1, tw, n, H)) != cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k3w_x_inv<RQ, T, R>, dim3(gy, n), dim3(256), smx, s, (const T*)T1, x, z, out, tw, n, H, a, b,
+                        c)) != cudaSuccess)
+        return e;
     rte_count_launches(5);
     return cudaSuccess;
 }

@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __
     if (wz) w = wz[ch];
     if (ch > 0) xf = nullptr;  // the source joins channel 0 only
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // x may be the predecessor's output
+    pdl_trigger();
     __syncthreads();
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RR ww = (RR)w;
@@ -77,6 +79,8 @@ __global__ void __launch_bounds__(512) k3w_y_fwd(const T* __restrict__ T1, T* __
     T1 += (long)ch * n * H * n;
     T2 += (long)ch * H * Q * n;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // T1: the x pass's output
+    pdl_trigger();
     __syncthreads();
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = z0 + wp;
@@ -108,6 +112,8 @@ __global__ void __launch_bounds__(256) k3w_z_mix(T* __restrict__ T2, const TS* _
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* scr = twl + Q + warp * wfft_shape<RQ>::SCRATCH;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // T2: the y pass's output
+    pdl_trigger();
     __syncthreads();
     const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (line >= nlines) return;
@@ -145,6 +151,8 @@ __global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __
     T1 += (long)ch * n * H * n;
     T2 += (long)ch * H * Q * n;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // T2: the z pass's output
+    pdl_trigger();
     const int nz = min(16, n - z0);
     for (int idx = threadIdx.x; idx < Q * 16; idx += blockDim.x) {
         const int zl = idx & 15, sl = idx >> 4;
@@ -197,6 +205,8 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
         pxb[r] = (x && e < n && yb < n) ? x[((long)z * n + yb) * n + e] : (RI)0;
     }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    pdl_wait();  // T1: the y' pass's output
+    pdl_trigger();
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
         const int li = idx & 7, xi = idx >> 3;
         const int la = y0 + 2 * li, lb = la + 1;

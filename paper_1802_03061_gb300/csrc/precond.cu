@@ -274,6 +274,8 @@ __global__ void __launch_bounds__(256, 2) k_col_warp_pc(float2* __restrict__ Tb,
     cp_async_commit();
     if (nl > 1) issue(1);
     cp_async_commit();
+    pdl_wait();  // Tb: the row pass's output (the table is a plan constant)
+    pdl_trigger();
     for (int c = warp; c < nl; c += nw) {
         float2 v[R];
         const float2* col = Tb + ((long)c * H + kx) * n;
@@ -543,8 +545,7 @@ static cudaError_t launch_col_pc(float2* Tb, const __nv_bfloat16* Pp, const floa
     const int Q = 32 * R;
     const size_t smem = (size_t)(2 * L + 1) * wfft_shape<R>::SCRATCH * sizeof(float2) +
                         (size_t)2 * (2 * L + 1) * (Q / 2 + 8) * sizeof(__nv_bfloat16);
-    k_col_warp_pc<L, R><<<H, 256, smem, s>>>(Tb, Pp, tw, n, H, nl);
-    return cudaGetLastError();
+    return launch_pdl(k_col_warp_pc<L, R>, dim3(H), dim3(256), smem, s, Tb, Pp, tw, n, H, nl);
 }
 
 template <int L>
