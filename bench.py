@@ -367,15 +367,15 @@ def run_native(args):
 # from the ncu capture summarised in profiles/matvec_hg2d_transport_256_L8.md.
 # Valid only for the kernel versions that capture measured and for this shape
 # and precision (the roofline reports null otherwise).
-MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4751872 + 26899200 + 13705728,
-                                            "insts": 3634192 + 9583273 + 3405120,
-                                            "col_dram_bytes": 26899200, "col_insts": 9583273}}
+MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4752128 + 26899456 + 13698048,
+                                            "insts": 3638544 + 9587385 + 3485360,
+                                            "col_dram_bytes": 26899456, "col_insts": 9587385}}
 
 
 # the same for the five FP32 passes of the 128^3 application
 # (profiles/passes_iso3d_diffusion_128.md)
-ISO3D_NCU = {"dram_bytes": 8406272 + 16921600 + 42419712 + 33829888 + 25313536,
-             "insts": 7090176 + 9279744 + 23612160 + 9230208 + 6263808}
+ISO3D_NCU = {"dram_bytes": 8405248 + 16922880 + 42420224 + 33831168 + 25313280,
+             "insts": 7311360 + 10253952 + 23678208 + 10419072 + 7116800}
 
 
 def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):
