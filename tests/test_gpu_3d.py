@@ -94,6 +94,23 @@ def test_apply_K_3d_warp_passes(n, q):
     p.close()
 
 
+# FP32 warp passes for q = 64, 128, 256: odd n (a row pair with one row), n
+# ragged against the 16-row and 16-z blocks, and the largest n of each length
+@pytest.mark.parametrize("n,q", [(13, 64), (32, 64), (47, 128), (64, 128), (101, 256), (128, 256)])
+def test_apply_K32_3d_warp_lengths(n, q):
+    mu_t, mu_s = 10.0, 9.0
+    p = _plan(n, mu_t, mu_s, prec="mixed_fp32", q_policy=q)
+    assert p.Q == q
+    x = np.random.default_rng(n + q).standard_normal((n, n, n)).astype(np.float32)
+    y = p.apply_K32(torch.from_numpy(x).cuda()).cpu().numpy().reshape(-1)
+    rows = np.random.default_rng(5).choice(n ** 3, size=48, replace=False)
+    if n <= 13:
+        rows = np.arange(n ** 3)
+    ref = oracle.apply_K_3d(n, 1.0 / n, mu_t, mu_s, x.astype(np.float64), rows=rows)
+    assert rel(y[rows], ref) < 1e-5
+    p.close()
+
+
 def test_apply_K_3d_full_size_sampled():
     """128^3 (zero padded to 256^3), mu_t = 100, mu_s = 99.5: FP64 K x against
     the oracle's direct sum at sampled cells."""
