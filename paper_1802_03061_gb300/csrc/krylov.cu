@@ -356,6 +356,88 @@ __global__ void k_givens(GmresDev* st, cudaGraphConditionalHandle loop) {
 }
 
 // --------------------------------------------------------------------------
+// FP64 Arnoldi step (CGS2) for short vectors (nr <= CGS64_SHORT): three
+// kernels and the basis scaling after the matvec instead of nine.  Block b
+// owns the elements [b chunk, (b+1) chunk), so the FP64 work spreads over
+// ceil(nr / 256) SMs (FP64 runs at 1/64 of the FP32 rate: one block doing a
+// 64^2 step alone took twice as long as the nine kernels); the last block to
+// finish sums the per-block partials in a fixed order (deterministic).
+//   PASS 0: h_A = <V_i, w>, i <= j
+//   PASS 1: w -= V h_A, then h_B = <V_i, w>
+//   PASS 2: w -= V h_B, ||w||, and the Givens update with h_A + h_B
+// --------------------------------------------------------------------------
+#define CGS64_SHORT 65536
+template <int PASS>
+__global__ void __launch_bounds__(256) k_cgs64(const double* __restrict__ V, long nr, double* __restrict__ w,
+                                               GmresDev* __restrict__ st, long nw1, double* __restrict__ part,
+                                               long chunk, cudaGraphConditionalHandle loop) {
+    const int j = st->j, count = j + 1;
+    const int nb = gridDim.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double c[GM_MMAX + 1];
+    __shared__ double red[GM_MMAX + 1][8];
+    __shared__ double col[GM_MMAX + 2];
+    __shared__ bool last;
+    const long e0 = (long)blockIdx.x * chunk, e1 = e0 + chunk < nr ? e0 + chunk : nr;
+    if (PASS > 0) {
+        for (int i = threadIdx.x; i < count; i += blockDim.x) c[i] = PASS == 1 ? st->hA[i] : st->hB[i];
+        __syncthreads();
+        for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            double acc = 0.0;
+            for (int i = 0; i < count; ++i) acc += c[i] * V[(long)i * nr + e];
+            w[e] -= acc;
+        }
+    }
+    const int ncol = PASS < 2 ? count : 1;
+    for (int i = 0; i < ncol; ++i) {
+        double sacc = 0.0;
+        for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const double we = w[e] * (e < nw1 ? 1.0 : 2.0);
+            sacc += (PASS < 2 ? V[(long)i * nr + e] : w[e]) * we;
+        }
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+        if (lane == 0) red[i][wid] = sacc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[i][q];
+        part[(long)i * nb + blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    unsigned int* cnt = PASS == 0 ? &st->cnt1 : PASS == 1 ? &st->cnt2 : &st->cnt3;
+    if (threadIdx.x == 0) last = atomicAdd(cnt, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (PASS < 2) {
+        double* h = PASS == 0 ? st->hA : st->hB;
+        for (int i = wid; i < count; i += 8) {
+            double t = 0.0;
+            for (int b = lane; b < nb; b += 32) t += __ldcg(part + (long)i * nb + b);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) h[i] = t;
+        }
+        if (threadIdx.x == 0) *cnt = 0u;
+        return;
+    }
+    if (wid != 0) return;
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += __ldcg(part + b);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    for (int i = lane; i < count; i += 32) col[i] = st->hA[i] + st->hB[i];
+    __syncwarp();
+    if (lane == 0) {
+        *cnt = 0u;
+        const double nrm = sqrt(t);
+        st->nrm = nrm;
+        givens_update(st, col, nrm, loop);
+    }
+}
+
+// --------------------------------------------------------------------------
 // fused FP32 Arnoldi step (CGS1): two kernels after the matvec instead of six.
 // V_j arrives unscaled (the previous step stored w without dividing by its
 // norm); with s = vscale, A V_j = s * w_raw.
@@ -848,6 +930,12 @@ static int grid_for(long nr) {
 static int tiles(long nr) { return (int)((nr + TILE - 1) / TILE); }
 
 long krylov_tiles(long nr) { return tiles(nr); }
+// columns of the per-block partial sums: one per TILE, or one per 256
+// elements for the short FP64 step (k_cgs64)
+static long part_cols(long nr) {
+    const long a = tiles(nr), b = (nr + 255) / 256;
+    return (nr <= CGS64_SHORT && b > a) ? b : a;
+}
 
 static rte_status apply_A_T(const KrylovOp& o, const double* x, double* y, cudaStream_t s) {
     return o.A64(o.ctx, x, y, s);
@@ -890,7 +978,7 @@ static rte_status gm_setup(Gm<T>& G, const KrylovOp& o, KrylovWs& ws, int m, cud
         krylov_free_ws(ws);
         if (rte_dev_malloc(&ws.V, (size_t)(m + 2) * o.nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
         if (rte_dev_malloc(&ws.w, (size_t)o.nr * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RTE_ENOMEM; }
-        if (rte_dev_malloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * tiles(o.nr) * sizeof(double)) != cudaSuccess) {
+        if (rte_dev_malloc((void**)&ws.part, (size_t)(GM_MMAX + 1) * part_cols(o.nr) * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return RTE_ENOMEM;
         }
@@ -1175,6 +1263,22 @@ static rte_status arnoldi_body(Gm<T>& G, bool cgs2, bool pc, cudaGraphConditiona
                                         (const float*)G.w, (float*)G.vin, G.st, G.nw1, G.part, loop, zs, Zs));
             }
             rte_count_launches(2);
+            return RTE_OK;
+        }
+    }
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if (cgs2 && nr <= CGS64_SHORT) {
+            const long chunk = 256;
+            const unsigned nbs = (unsigned)((nr + chunk - 1) / chunk);
+            double* V = (double*)G.V;
+            double* w = (double*)G.w;
+            k_cgs64<0><<<nbs, 256, 0, s>>>(V, nr, w, G.st, G.nw1, G.part, chunk, loop);
+            k_cgs64<1><<<nbs, 256, 0, s>>>(V, nr, w, G.st, G.nw1, G.part, chunk, loop);
+            k_cgs64<2><<<nbs, 256, 0, s>>>(V, nr, w, G.st, G.nw1, G.part, chunk, loop);
+            // after the Givens update st->j is the new basis index
+            k_scale_basis<double><<<gr, 256, 0, s>>>(w, V, (double*)G.vin, nr, G.st, 0);
+            rte_count_launches(4);
+            RTE_CUDA_TRY(cudaGetLastError());
             return RTE_OK;
         }
     }
