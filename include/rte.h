@@ -179,12 +179,15 @@ rte_status rte_rhs(rte_plan plan, const double* f_dev, void* b_dev, void* cuda_s
  * which is b - (I - K) u for the exact b; stats->relres_true is its norm over
  * ||b||.
  * opts NULL = the plan's options.  stats may be NULL.  Synchronises the
- * stream once at exit to fill stats. */
+ * stream once at exit to fill stats.  Once the solve graph has run, u_dev
+ * holds its last iterate whatever the status (RTE_ENOCONV, RTE_ENAN). */
 rte_status rte_solve(rte_plan plan, const double* f_dev, void* u_dev, const rte_opts* opts,
                      rte_stats* stats, void* cuda_stream);
 
 /* Same as rte_solve with host buffers: copies f_host to the device, solves,
- * copies u back to u_host (FP64 field layout above, host memory). */
+ * copies u back to u_host (FP64 field layout above, host memory; pinned
+ * memory keeps the copies asynchronous).  The copy back is queued behind the
+ * solve graph and the statistics, and one synchronisation covers all three. */
 rte_status rte_solve_host(rte_plan plan, const double* f_host, void* u_host, const rte_opts* opts,
                           rte_stats* stats, void* cuda_stream);
 

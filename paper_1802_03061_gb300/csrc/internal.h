@@ -166,6 +166,7 @@ struct rte_plan_s {
     double* u_dev = nullptr;
     KrylovWs k64, k32;
     SolveGraph graphs[3];    // per precision mode
+    void* ev[2] = {nullptr, nullptr};  // cudaEvent_t pair timing the solve graph (created on first use)
     void* ref = nullptr;     // device refinement state (krylov.cu)
     double* hst = nullptr;   // pinned host mirror of small device state (64 doubles)
     double ms_pre = 0.0;
@@ -225,7 +226,10 @@ rte_status op3d_apply32(rte_plan p, const float* x, float* out, float a, float b
                         const float* z, cudaStream_t s);
 
 // krylov.cu: the solve reads p->f_dev and writes p->u_dev
-rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* st, cudaStream_t s);
+// one solve of the plan's f_dev into u_dev; u_out (optional) receives a copy
+// of u_dev of kind `kind`, enqueued before the one synchronisation
+rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* st, cudaStream_t s, void* u_out = nullptr,
+                        cudaMemcpyKind kind = cudaMemcpyDeviceToDevice);
 rte_status krylov_free(rte_plan p);
 size_t refdev_size();
 bool solve_uses_minres(const rte_plan p, const rte_opts* o);

@@ -1763,15 +1763,16 @@ rte_status krylov_op_run(const KrylovOp& op, void* exec, const SolveGraphInfo& i
 size_t refdev_size() { return sizeof(RefDev); }
 
 // Solve for the plan's f_dev into u_dev (both plan-owned), one graph launch.
-rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStream_t s) {
+rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStream_t s, void* u_out,
+                        cudaMemcpyKind kind) {
     cudaGraphExec_t ex = nullptr;
     const int prec = (int)o->prec;
     // the FP64 workspace is only needed by the FP64 mode
     rte_status st = get_solve_graph(p, prec, o->restart, solve_uses_minres(p, o), solve_uses_precond(p, o), s, &ex);
     if (st != RTE_OK) return st;
-    cudaEvent_t ev0, ev1;
-    RTE_CUDA_TRY(cudaEventCreate(&ev0));
-    RTE_CUDA_TRY(cudaEventCreate(&ev1));
+    for (int i = 0; i < 2; ++i)
+        if (!p->ev[i]) RTE_CUDA_TRY(cudaEventCreate((cudaEvent_t*)&p->ev[i]));
+    cudaEvent_t ev0 = (cudaEvent_t)p->ev[0], ev1 = (cudaEvent_t)p->ev[1];
     st = solve_set_options(p, o, s);
     if (st != RTE_OK) return st;
     RTE_CUDA_TRY(cudaEventRecord(ev0, s));
@@ -1779,11 +1780,10 @@ rte_status krylov_solve(rte_plan p, const rte_opts* o, rte_stats* stats, cudaStr
     RTE_CUDA_TRY(cudaEventRecord(ev1, s));
     RefDev* hr = (RefDev*)(p->hst + 16);
     RTE_CUDA_TRY(cudaMemcpyAsync(hr, p->ref, sizeof(RefDev), cudaMemcpyDeviceToHost, s));
+    if (u_out) RTE_CUDA_TRY(cudaMemcpyAsync(u_out, p->u_dev, p->nr * sizeof(double), kind, s));
     RTE_CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     return solve_collect(p, prec, hr, stats, ms);
 }
 
@@ -1797,6 +1797,11 @@ void krylov_free_ws(KrylovWs& ws) {
 }
 
 rte_status krylov_free(rte_plan p) {
+    for (int i = 0; i < 2; ++i)
+        if (p->ev[i]) {
+            cudaEventDestroy((cudaEvent_t)p->ev[i]);
+            p->ev[i] = nullptr;
+        }
     for (int i = 0; i < 3; ++i) {
         if (p->graphs[i].exec) cudaGraphExecDestroy((cudaGraphExec_t)p->graphs[i].exec);
         p->graphs[i] = SolveGraph();

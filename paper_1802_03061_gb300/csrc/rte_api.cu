@@ -408,10 +408,7 @@ extern "C" rte_status rte_solve(rte_plan p, const double* f, void* u, const rte_
     cudaStream_t s = (cudaStream_t)stream;
     RTE_CUDA_TRY(cudaMemcpyAsync(p->f_dev, f, p->ncell * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (o.use_guess) RTE_CUDA_TRY(cudaMemcpyAsync(p->u_dev, u, p->nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    rte_status st = krylov_solve(p, &o, stats, s);
-    if (st != RTE_OK && st != RTE_ENOCONV) return st;
-    RTE_CUDA_TRY(cudaMemcpyAsync(u, p->u_dev, p->nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return st;
+    return krylov_solve(p, &o, stats, s, u, cudaMemcpyDeviceToDevice);
 }
 
 extern "C" rte_status rte_solve_host(rte_plan p, const double* f_host, void* u_host, const rte_opts* opts,
@@ -424,11 +421,7 @@ extern "C" rte_status rte_solve_host(rte_plan p, const double* f_host, void* u_h
     RTE_CUDA_TRY(cudaMemcpyAsync(p->f_dev, f_host, p->ncell * sizeof(double), cudaMemcpyHostToDevice, s));
     if (o.use_guess)
         RTE_CUDA_TRY(cudaMemcpyAsync(p->u_dev, u_host, p->nr * sizeof(double), cudaMemcpyHostToDevice, s));
-    rte_status st = krylov_solve(p, &o, stats, s);
-    if (st != RTE_OK && st != RTE_ENOCONV) return st;
-    RTE_CUDA_TRY(cudaMemcpyAsync(u_host, p->u_dev, p->nr * sizeof(double), cudaMemcpyDeviceToHost, s));
-    RTE_CUDA_TRY(cudaStreamSynchronize(s));
-    return st;
+    return krylov_solve(p, &o, stats, s, u_host, cudaMemcpyDeviceToHost);
 }
 
 extern "C" rte_status rte_plan_info(rte_plan p, int* n, int* Q, int* L, long* nreal) {
