@@ -214,7 +214,9 @@ def test_full_size_transport_256_sampled_residual():
     rows = np.random.default_rng(11).choice(n * n, size=24, replace=False)
     uf = packed_to_full(u.cpu().numpy())
     r, b = oracle.sampled_residual_2d(n, 1 / n, prob["mu_t"], prob["mu_s"], prob["sigma_hat"], prob["f"], uf, rows)
-    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-7
+    # rows S anywhere: ||r_S|| <= ||r|| <= tol ||b||, ||b|| (all modes) from the FP64 RHS
+    bnorm = _wnorm(p.rhs(torch.from_numpy(prob["f"])).cpu().numpy())
+    assert np.linalg.norm(r) <= 1.1e-8 * bnorm
     p.close()
 
 
