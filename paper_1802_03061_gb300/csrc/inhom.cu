@@ -159,9 +159,14 @@ __global__ void __launch_bounds__(256) k_inhom_apply(const T* __restrict__ mu_g,
     const int per = (N + 7) / 8, j0 = warp * per, j1 = min(N, j0 + per);
     T acc = (T)0, comp = (T)0;
     if (n > 1) {
-        for (int j = j0; j < j1; ++j) {
+        int c1 = j0 % n, c2 = j0 / n;  // the source cell of j, stepped along with j
+        for (int j = j0; j < j1; ++j, ++c1) {
+            if (c1 == n) {
+                c1 = 0;
+                ++c2;
+            }
             if (j == ii) continue;
-            const T du = (T)(j % n - i1), dv = (T)(j / n - i2);
+            const T du = (T)(c1 - i1), dv = (T)(c2 - i2);
             const T r = h * sqrt(du * du + dv * dv);
             T mean = (T)0;
 #pragma unroll
@@ -225,12 +230,18 @@ __global__ void __launch_bounds__(256) k_inhom_apply_sym(const float* __restrict
     const float scale = h * h / (float)(2.0 * kPi);
     float acc = 0.f, comp = 0.f;
     const int jb = j0 + warp * 32;
-    for (int jj = 0; jj < 32; ++jj) {
+    // the source cell (j1, j2) of j, stepped along with j (no division per pair)
+    int j1 = jb % n, j2 = jb / n;
+    for (int jj = 0; jj < 32; ++jj, ++j1) {
         const int j = jb + jj;
         if (j >= N) break;  // uniform over the warp
+        if (j1 == n) {
+            j1 = 0;
+            ++j2;
+        }
         float e = 0.f;
         if (live && j > i) {
-            const float du = (float)(j % n - i1), dv = (float)(j / n - i2);
+            const float du = (float)(j1 - i1), dv = (float)(j2 - i2);
             const float r = h * sqrtf(du * du + dv * dv);
             float mean = 0.f;
 #pragma unroll
