@@ -10,9 +10,13 @@
 // sigma_hat_l the Legendre moments of the phase function (sigma_hat_0 = 1).
 // L = 0 is the isotropic equation.  Every K~^{ab} is a convolution, applied
 // with FFTs on the zero-padded Q^3 grid (Sec. 2.3.1): the input channels
-// take the X and Y passes one by one, one Z pass transforms all M channels of
-// a (xi_x, xi_y) line, mixes them with the M x M spectra at each xi_z and
-// transforms back, and the output channels take the Y' and X' passes.
+// take the X and Y passes, one Z pass transforms all M channels of a
+// (xi_x, xi_y) line, mixes them with the M x M spectra at each xi_z and
+// transforms back, and the output channels take the Y' and X' passes.  For
+// Q = 64, 128, 256 the warp-register passes of aniso3d_warp.cu run each pass
+// over all channels in one launch; otherwise the general-Q Stockham passes
+// below run channel by channel.  The solve (T.1, T.2) is the plan's device
+// solve graph (krylov.cu) built on this operator.
 //
 // Each W_ab has a definite parity in x, y and z (Y_a does), so its spectrum
 // is real (even total parity) or imaginary (odd) with the same parities; it is

@@ -19,6 +19,12 @@
 // recomputes the residual for a restart).  Small one-thread kernels decide
 // the loop conditions from FP64 state in device memory, so the host only
 // launches the graph and reads the statistics at the end.
+//
+// The graph is built on a KrylovOp (internal.h): the operator as callbacks
+// that enqueue its kernels, and the work vectors.  The plan supplies one for
+// its J-symmetric channels (with the periodic preconditioner and MINRES as
+// options); the spherical-harmonic operator (aniso3d.cu) supplies one for its
+// real moments, where every element weighs 1.
 #include <math.h>
 #include <stddef.h>
 #include <stdio.h>
