@@ -356,11 +356,38 @@ static rte_status an_A32(void* c, const float* x, float* y, cudaStream_t s) {
 static rte_status an_A64(void* c, const double* x, double* y, cudaStream_t s) {
     return aniso_apply64((rte_aniso3d)c, x, y, 0, 1.0, -1.0, nullptr, 0.0, nullptr, s);
 }
-// b = K~^{.0} f (T.1): FP64-accurate in both modes
+__global__ void k_aniso_narrow(const double* __restrict__ src, float* __restrict__ dst, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+__global__ void k_aniso_widen(const float* __restrict__ src, double* __restrict__ dst, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+// b = K~^{.0} f (T.1).  FP64 mode: native FP64.  Mixed: in FP32 (the source
+// narrowed into d32, b formed in r32 and widened): b only seeds the first
+// inner right-hand side and ||b||, since every residual is the fused exact form
+// below
 static rte_status an_rhs(void* c, int mixed, cudaStream_t s) {
     rte_aniso3d op = (rte_aniso3d)c;
-    return mixed ? aniso_apply64e(op, op->f, op->b64, 1, 0.0, 1.0, nullptr, 0.0, nullptr, s)
-                 : aniso_apply64(op, op->f, op->b64, 1, 0.0, 1.0, nullptr, 0.0, nullptr, s);
+    if (!mixed) return aniso_apply64(op, op->f, op->b64, 1, 0.0, 1.0, nullptr, 0.0, nullptr, s);
+    const long N3 = (long)op->n * op->n * op->n, len = op->M * N3;
+    k_aniso_narrow<<<1024, 256, 0, s>>>(op->f, op->d32, N3);
+    rte_count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = op->RQ ? aniso_run_warp<float2, float, float>(op, op->d32, op->r32, 1, 0.0, 1.0, nullptr, 0.0, nullptr,
+                                                          op->S32, op->tw32, s)
+                   : aniso_run<float2, float, float>(op, op->d32, op->r32, 1, 0.0, 1.0, nullptr, 0.0, nullptr,
+                                                     op->S32, op->tw32, op->Bz32, s);
+    if (e == cudaSuccess) {
+        k_aniso_widen<<<1024, 256, 0, s>>>(op->r32, op->b64, len);
+        rte_count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return rte_cuda_fail(e, "rte_aniso3d rhs32");
+    return RTE_OK;
 }
 // r = b - (I - K) u.  Mixed: r = K~ (mu_s sigma_hat u + f) - u in one
 // float-float application (the source joins channel 0's input), equal to it
