@@ -295,6 +295,17 @@ rte_status rte_cnn_save(rte_cnn net, const char* path);
  * cuda_stream.  RTE_EINVAL (network unchanged) if the file is missing,
  * truncated, or of another shape. */
 rte_status rte_cnn_load(rte_cnn net, const char* path, void* cuda_stream);
+/* Training checkpoint (resume): everything rte_cnn_save writes plus the
+ * optimizer's state -- per layer the Adam first and second moments of the
+ * weights and biases -- and its step count (the bias correction), so that
+ * training steps after rte_cnn_load_state repeat those of the run that saved
+ * it.  File: "RTECNS01", int32 cin, width, depth, cout, int64 step, per layer
+ * int32 cin_l, cout_l, f32 w, bias, m_w, v_w, m_b, v_b (host byte order).
+ * save synchronises the device; load refreshes the BF16 copies on
+ * cuda_stream.  RTE_EINVAL (network unchanged) for an unwritable, missing,
+ * truncated or other-shaped file. */
+rte_status rte_cnn_save_state(rte_cnn net, const char* path);
+rte_status rte_cnn_load_state(rte_cnn net, const char* path, void* cuda_stream);
 /* Network input (cin channels, 2L+5 <= cin) / training target (cout
  * channels, 2L+1 <= cout) of plan p (2D) from the source f (double [n][n]),
  * b = K~ g and, for targets, the solution u (FP64 mode fields).  The scales

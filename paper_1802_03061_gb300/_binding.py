@@ -123,6 +123,8 @@ def lib():
         L.rte_cnn_sync_weights.argtypes = [VP, VP]
         L.rte_cnn_save.argtypes = [VP, ctypes.c_char_p]
         L.rte_cnn_load.argtypes = [VP, ctypes.c_char_p, VP]
+        L.rte_cnn_save_state.argtypes = [VP, ctypes.c_char_p]
+        L.rte_cnn_load_state.argtypes = [VP, ctypes.c_char_p, VP]
         L.rte_guess_features.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP]
         L.rte_guess_targets.argtypes = [VP, ctypes.c_int, VP, VP, VP, VP, VP]
         L.rte_cnn_guess_apply.argtypes = [VP, VP, VP, VP, VP, VP, VP]
@@ -131,7 +133,7 @@ def lib():
         L.rte_guess_destroy.argtypes = [VP]
         L.rte_batch_plan.argtypes = [VP, ctypes.c_int, ctypes.POINTER(VP)]
         for name in ("rte_cnn_create", "rte_cnn_destroy", "rte_cnn_forward", "rte_cnn_train_step", "rte_cnn_layer",
-                     "rte_cnn_sync_weights", "rte_cnn_save", "rte_cnn_load", "rte_guess_features",
+                     "rte_cnn_sync_weights", "rte_cnn_save", "rte_cnn_load", "rte_cnn_save_state", "rte_cnn_load_state", "rte_guess_features",
                      "rte_guess_targets", "rte_cnn_guess_apply", "rte_guess_load", "rte_guess_apply",
                      "rte_guess_destroy", "rte_batch_plan"):
             getattr(L, name).restype = ctypes.c_int
@@ -464,6 +466,14 @@ def rte_cnn_save(net, path):
 
 def rte_cnn_load(net, path, stream=0):
     _check(lib().rte_cnn_load(net, str(path).encode(), VP(stream)), "rte_cnn_load")
+
+
+def rte_cnn_save_state(net, path):
+    _check(lib().rte_cnn_save_state(net, str(path).encode()), "rte_cnn_save_state")
+
+
+def rte_cnn_load_state(net, path, stream=0):
+    _check(lib().rte_cnn_load_state(net, str(path).encode(), VP(stream)), "rte_cnn_load_state")
 
 
 def rte_guess_features(plan, cin, f, b, X, stream=0):

@@ -998,6 +998,82 @@ extern "C" rte_status rte_cnn_load(rte_cnn c, const char* path, void* stream) {
     return rte_cnn_sync_weights(c, stream);
 }
 
+// Training checkpoint: the weights file's contents plus, per layer, the Adam
+// moments of the weights and biases, and the optimizer's step count, so that a
+// resumed run continues the same trajectory:
+//   "RTECNS01", int32 cin, width, depth, cout, int64 step, then per layer
+//   int32 cin_l, cout_l and f32 w, bias, m_w, v_w, m_b, v_b.
+static const char kCnnStateMagic[8] = {'R', 'T', 'E', 'C', 'N', 'S', '0', '1'};
+
+extern "C" rte_status rte_cnn_save_state(rte_cnn c, const char* path) {
+    if (!c || !path) return RTE_EINVAL;
+    RTE_CUDA_TRY(cudaDeviceSynchronize());
+    FILE* f = fopen(path, "wb");
+    if (!f) return rte_fail(RTE_EINVAL, "rte_cnn_save_state: cannot open the file");
+    bool ok = fwrite(kCnnStateMagic, 1, 8, f) == 8;
+    const int hdr[4] = {c->cin, c->width, c->depth, c->cout};
+    const long long step = c->step;
+    ok = ok && fwrite(hdr, sizeof(int), 4, f) == 4 && fwrite(&step, sizeof(step), 1, f) == 1;
+    std::vector<float> buf;
+    for (const CnnLayer& L : c->layers) {
+        if (!ok) break;
+        const int dims[2] = {L.cin, L.cout};
+        ok = fwrite(dims, sizeof(int), 2, f) == 2;
+        const size_t nw = 9ull * L.cin * L.cout, nb = (size_t)L.cout;
+        const float* src[6] = {L.w, L.bias, L.mw, L.vw, L.mb, L.vb};
+        const size_t cnt[6] = {nw, nb, nw, nw, nb, nb};
+        for (int k = 0; k < 6 && ok; ++k) {
+            buf.resize(cnt[k]);
+            if (cudaMemcpy(buf.data(), src[k], cnt[k] * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                fclose(f);
+                return rte_cuda_fail(cudaGetLastError(), "rte_cnn_save_state");
+            }
+            ok = fwrite(buf.data(), sizeof(float), cnt[k], f) == cnt[k];
+        }
+    }
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return rte_fail(RTE_EINVAL, "rte_cnn_save_state: writing the file failed");
+    return RTE_OK;
+}
+
+extern "C" rte_status rte_cnn_load_state(rte_cnn c, const char* path, void* stream) {
+    if (!c || !path) return RTE_EINVAL;
+    FILE* f = fopen(path, "rb");
+    if (!f) return rte_fail(RTE_EINVAL, "rte_cnn_load_state: cannot open the file");
+    char magic[8];
+    int hdr[4];
+    long long step = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kCnnStateMagic, 8) == 0 &&
+              fread(hdr, sizeof(int), 4, f) == 4 && hdr[0] == c->cin && hdr[1] == c->width && hdr[2] == c->depth &&
+              hdr[3] == c->cout && fread(&step, sizeof(step), 1, f) == 1 && step >= 0;
+    std::vector<std::vector<float>> host(c->layers.size());
+    for (size_t l = 0; ok && l < c->layers.size(); ++l) {
+        const CnnLayer& L = c->layers[l];
+        int dims[2];
+        ok = fread(dims, sizeof(int), 2, f) == 2 && dims[0] == L.cin && dims[1] == L.cout;
+        if (!ok) break;
+        const size_t nw = 9ull * L.cin * L.cout, nb = (size_t)L.cout;
+        host[l].resize(3 * nw + 3 * nb);
+        ok = fread(host[l].data(), sizeof(float), host[l].size(), f) == host[l].size();
+    }
+    fclose(f);
+    if (!ok) return rte_fail(RTE_EINVAL, "rte_cnn_load_state: not a training checkpoint of this network's shape");
+    // nothing on the device changes unless the whole file was valid
+    for (size_t l = 0; l < c->layers.size(); ++l) {
+        const CnnLayer& L = c->layers[l];
+        const size_t nw = 9ull * L.cin * L.cout, nb = (size_t)L.cout;
+        float* dst[6] = {L.w, L.bias, L.mw, L.vw, L.mb, L.vb};
+        const size_t cnt[6] = {nw, nb, nw, nw, nb, nb};
+        const float* src = host[l].data();
+        for (int k = 0; k < 6; ++k) {
+            RTE_CUDA_TRY(cudaMemcpy(dst[k], src, cnt[k] * sizeof(float), cudaMemcpyHostToDevice));
+            src += cnt[k];
+        }
+    }
+    c->step = (long)step;
+    return rte_cnn_sync_weights(c, stream);
+}
+
 // ---------------------------------------------------------------------------
 // the learned guess for a plan: u0 = b + s_b * net(features(b, f, params))
 // (scales s_b, fmax computed on the device into the plan's dscal[2..3])

@@ -112,6 +112,14 @@ class GuessNet:
         """Weights from a file written by save() for a network of this shape."""
         B.rte_cnn_load(self.handle, path, _stream_ptr(stream))
 
+    def save_checkpoint(self, path):
+        """Training checkpoint: weights, Adam moments and step count (rte_cnn_save_state)."""
+        B.rte_cnn_save_state(self.handle, path)
+
+    def load_checkpoint(self, path, stream=None):
+        """Resume from save_checkpoint(): later training steps repeat the saving run's."""
+        B.rte_cnn_load_state(self.handle, path, _stream_ptr(stream))
+
     def close(self):
         if getattr(self, "handle", None):
             B.rte_cnn_destroy(self.handle)

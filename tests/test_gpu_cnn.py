@@ -139,3 +139,58 @@ def test_weights_file_round_trip(tmp_path):
     assert np.array_equal(fwd(net1), y1)
     for n in (net1, net2, other):
         B.rte_cnn_destroy(n)
+
+
+def test_training_checkpoint_resumes_the_same_trajectory(tmp_path):
+    """rte_cnn_save_state / rte_cnn_load_state: a network of another seed that
+    loads the checkpoint taken after 3 Adam steps and then takes the same 4
+    steps ends with the same weights, bit for bit, as the run that saved it;
+    loading the weights alone (fresh moments, step 0) does not.  A weights
+    file, a truncated checkpoint and another shape are refused."""
+    from paper_1802_03061_gb300 import _binding as B
+    rng = np.random.default_rng(11)
+    Bn, H, W = 2, 8, 64
+    X = torch.from_numpy(rng.standard_normal((Bn, H, W, 16)).astype(np.float32)).to(torch.bfloat16).cuda()
+    T = torch.from_numpy(rng.standard_normal((Bn, H, W, 16)).astype(np.float32)).to(torch.bfloat16).cuda()
+
+    def steps(net, k):
+        for _ in range(k):
+            B.rte_cnn_train_step(net, X.data_ptr(), T.data_ptr(), Bn, H, W, 1, 1e-3, want_loss=False)
+        torch.cuda.synchronize()
+
+    def weights(net):
+        out = []
+        for l in range(3):
+            d = B.rte_cnn_layer(net, l)
+            out.append(_view(d["w"], (9, d["cin"], d["cout"])).cpu().numpy().copy())
+            out.append(_view(d["b"], (d["cout"],)).cpu().numpy().copy())
+        return out
+
+    a = B.rte_cnn_create(16, 64, 3, 16, 5)
+    steps(a, 3)
+    ck, wf = tmp_path / "ck.bin", tmp_path / "w.bin"
+    B.rte_cnn_save_state(a, ck)
+    B.rte_cnn_save(a, wf)
+    steps(a, 4)
+    want = weights(a)
+    b = B.rte_cnn_create(16, 64, 3, 16, 7)
+    B.rte_cnn_load_state(b, ck)
+    steps(b, 4)
+    assert all(np.array_equal(x, y) for x, y in zip(weights(b), want))
+    c = B.rte_cnn_create(16, 64, 3, 16, 7)
+    B.rte_cnn_load(c, wf)
+    steps(c, 4)
+    assert not all(np.array_equal(x, y) for x, y in zip(weights(c), want))
+    before = weights(c)
+    with pytest.raises(B.RteError):
+        B.rte_cnn_load_state(c, wf)                 # a weights file is not a checkpoint
+    short = tmp_path / "short.bin"
+    short.write_bytes(ck.read_bytes()[:-4])
+    with pytest.raises(B.RteError):
+        B.rte_cnn_load_state(c, short)
+    other = B.rte_cnn_create(16, 64, 4, 16, 7)
+    with pytest.raises(B.RteError):
+        B.rte_cnn_load_state(other, ck)
+    assert all(np.array_equal(x, y) for x, y in zip(weights(c), before))
+    for n in (a, b, c, other):
+        B.rte_cnn_destroy(n)
