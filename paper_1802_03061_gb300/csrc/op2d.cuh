@@ -358,21 +358,25 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
     }
 }
 
-// FP32 row passes for Q = 1024 as two 512-point warp FFTs (residues r = xi
-// mod 2, n <= 512 nonzero inputs, as k_col_warp2): the line buffer Z holds the
-// 1024-point spectrum (swizzled) for the half-spectrum split / rebuild, and
-// each warp has a separate FFT scratch.  tw: the plan's 1024-point table.
+// Row passes as two warp FFTs of half the length (residues r = xi mod 2, n <=
+// Q/2 nonzero inputs, as k_col_warp2): FP32 at Q = 1024 (R = 16, both
+// passes) and the float-float forward pass at Q = 512 (R = 8, where a
+// one-warp 512-point float-float line needs too many registers).  The line buffer Z holds the Q-point spectrum
+// (swizzled) for the half-spectrum split / rebuild, and each warp has a
+// separate FFT scratch.  tw: the plan's Q-point table (compute type T, field
+// storage TF).
 // grid (ceil(n / 8), modes), block 256; rows per block 8 (k >= 1) or 16 (k = 0)
-template <int R>  // 16: Q = 1024
-__global__ void __launch_bounds__(256) k_row_fwd_warp2(const float2* __restrict__ x, const double* __restrict__ f,
-                                                       float2* __restrict__ out, const float2* __restrict__ tw,
+template <int R, typename T, typename TF>
+__global__ void __launch_bounds__(256) k_row_fwd_warp2(const TF* __restrict__ x, const double* __restrict__ f,
+                                                       T* __restrict__ out, const T* __restrict__ tw,
                                                        RowParams p) {
+    using RR = typename real_of<T>::R;
     constexpr int QW = 32 * R, Q = 2 * QW, LS = Q + 2;
     constexpr int SC = wfft_shape<R>::SCRATCH;
     extern __shared__ unsigned char smraw[];
-    float2* twl = reinterpret_cast<float2*>(smraw);  // exp(-2 pi i t / 512)
-    float2* Z = twl + QW;                            // [8][LS]
-    float2* scr = Z + 8 * LS;                        // [8][SC]
+    T* twl = reinterpret_cast<T*>(smraw);  // exp(-2 pi i t / QW)
+    T* Z = twl + QW;                       // [8][LS]
+    T* scr = Z + 8 * LS;                   // [8][SC]
     const int n = p.n, H = p.H;
     const int k = blockIdx.y;
     const int rows = k == 0 ? 16 : 8;
@@ -381,37 +385,37 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp2(const float2* __restrict_
     for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float wt = (float)p.wk[k];
-    float2 u[R];
+    const RR wt = (RR)p.wk[k];
+    T u[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int e = lane + 32 * r;
-        float2 val = make_float2(0.f, 0.f);
+        T val = mk<T>(0, 0);
         if (e < n) {
             if (k == 0) {
                 const int ya = y0 + 2 * w, yb = ya + 1;
-                float a = 0.f, b = 0.f;
+                RR a = (RR)0, b = (RR)0;
                 if (x) {
-                    if (ya < n) a = wt * x[(long)ya * n + e].x;
-                    if (yb < n) b = wt * x[(long)yb * n + e].x;
+                    if (ya < n) a = wt * to_c<T>(x[(long)ya * n + e]).x;
+                    if (yb < n) b = wt * to_c<T>(x[(long)yb * n + e]).x;
                 }
                 if (f) {
-                    if (ya < n) a = a + (float)f[(long)ya * n + e];
-                    if (yb < n) b = b + (float)f[(long)yb * n + e];
+                    if (ya < n) a = a + (RR)f[(long)ya * n + e];
+                    if (yb < n) b = b + (RR)f[(long)yb * n + e];
                 }
-                val = make_float2(a, b);
+                val = mk<T>(a, b);
             } else {
                 const int y = y0 + w;
                 if (y < n) {
-                    const float2 uu = x[((long)k * n + y) * n + e];
-                    val = make_float2(wt * uu.x, wt * uu.y);
+                    const T uu = to_c<T>(x[((long)k * n + y) * n + e]);
+                    val = mk<T>(wt * uu.x, wt * uu.y);
                 }
             }
         }
         u[r] = val;
     }
     for (int rs = 0; rs < 2; ++rs) {
-        float2 v[R];
+        T v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int e = lane + 32 * r;
@@ -428,10 +432,10 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp2(const float2* __restrict_
         const int y = y0 + r;
         if (y >= n) continue;
         const int line = k == 0 ? r >> 1 : r;
-        const float2 Zp = Z[line * LS + swz16(xi)];
-        const float2 Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
-        const float2 Fv = make_float2(0.5f * (Zp.x + Zm.x), 0.5f * (Zp.y - Zm.y));
-        const float2 Gv = make_float2(0.5f * (Zp.y + Zm.y), -0.5f * (Zp.x - Zm.x));
+        const T Zp = Z[line * LS + swz16(xi)];
+        const T Zm = Z[line * LS + swz16(xi == 0 ? 0 : Q - xi)];
+        const T Fv = mk<T>((RR)0.5 * (Zp.x + Zm.x), (RR)0.5 * (Zp.y - Zm.y));
+        const T Gv = mk<T>((RR)0.5 * (Zp.y + Zm.y), (RR)-0.5 * (Zp.x - Zm.x));
         if (k == 0) {
             out[(long)xi * n + y] = (r & 1) ? Gv : Fv;
         } else {
@@ -441,17 +445,19 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp2(const float2* __restrict_
     }
 }
 
-template <int R>  // 16: Q = 1024
-__global__ void __launch_bounds__(256) k_row_inv_warp2(const float2* __restrict__ in, const float2* __restrict__ x,
-                                                       const float2* __restrict__ z, float2* __restrict__ out,
-                                                       const float2* __restrict__ tw, RowParams p, float a, float b,
-                                                       float c) {
+template <int R, typename T, typename TF>
+__global__ void __launch_bounds__(256) k_row_inv_warp2(const T* __restrict__ in, const TF* __restrict__ x,
+                                                       const TF* __restrict__ z, TF* __restrict__ out,
+                                                       const T* __restrict__ tw, RowParams p,
+                                                       typename real_of<T>::R a, typename real_of<T>::R b,
+                                                       typename real_of<T>::R c) {
+    using RR = typename real_of<T>::R;
     constexpr int QW = 32 * R, Q = 2 * QW, LS = Q + 2;
     constexpr int SC = wfft_shape<R>::SCRATCH;
     extern __shared__ unsigned char smraw[];
-    float2* twl = reinterpret_cast<float2*>(smraw);
-    float2* Z = twl + QW;
-    float2* scr = Z + 8 * LS;
+    T* twl = reinterpret_cast<T*>(smraw);
+    T* Z = twl + QW;
+    T* scr = Z + 8 * LS;
     const int n = p.n, H = p.H;
     const int k = blockIdx.y;
     const int rows = k == 0 ? 16 : 8;
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(256) k_row_inv_warp2(const float2* __restrict_
     for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
     for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
         const int li = idx & 7, xi = idx >> 3;
-        float2 Fv = make_float2(0.f, 0.f), Gv = make_float2(0.f, 0.f);
+        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
         if (k == 0) {
             const int ya = y0 + 2 * li, yb = ya + 1;
             if (ya < n) Fv = in[(long)xi * n + ya];
@@ -472,14 +478,14 @@ __global__ void __launch_bounds__(256) k_row_inv_warp2(const float2* __restrict_
                 Gv = in[((long)chB(k) * H + xi) * n + y];
             }
         }
-        Z[li * LS + swz16(xi)] = make_float2(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = make_float2(Fv.x + Gv.y, Gv.x - Fv.y);
+        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 acc[R];
+    T acc[R];
     for (int rs = 0; rs < 2; ++rs) {
-        float2 v[R];
+        T v[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) v[j] = Z[w * LS + swz16(2 * wfreq<R>(j, lane) + rs)];
         warp_fft_inv<R>(v, twl, scr + w * SC);
@@ -499,26 +505,26 @@ __global__ void __launch_bounds__(256) k_row_inv_warp2(const float2* __restrict_
             const int ya = y0 + 2 * w, yb = ya + 1;
             if (ya < n) {
                 const long o = (long)ya * n + e;
-                float2 q = make_float2(b * acc[r].x, 0.f);
-                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
-                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
-                out[o] = q;
+                T q = mk<T>(b * acc[r].x, (RR)0);
+                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = to_f<TF>(q);
             }
             if (yb < n) {
                 const long o = (long)yb * n + e;
-                float2 q = make_float2(b * acc[r].y, 0.f);
-                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
-                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
-                out[o] = q;
+                T q = mk<T>(b * acc[r].y, (RR)0);
+                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = to_f<TF>(q);
             }
         } else {
             const int y = y0 + w;
             if (y < n) {
                 const long o = ((long)k * n + y) * n + e;
-                float2 q = make_float2(b * acc[r].x, b * acc[r].y);
-                if (x) { const float2 xv = x[o]; q.x += a * xv.x; q.y += a * xv.y; }
-                if (z) { const float2 zv = z[o]; q.x += c * zv.x; q.y += c * zv.y; }
-                out[o] = q;
+                T q = mk<T>(b * acc[r].x, b * acc[r].y);
+                if (x) { const T xv = to_c<T>(x[o]); q.x += a * xv.x; q.y += a * xv.y; }
+                if (z) { const T zv = to_c<T>(z[o]); q.x += c * zv.x; q.y += c * zv.y; }
+                out[o] = to_f<TF>(q);
             }
         }
     }

@@ -27,12 +27,13 @@ __global__ void k_split_ff2(const double2* __restrict__ src, ffc* __restrict__ d
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = to_ffc(src[i]);
 }
-// the same into the warp column passes' slot order: dst[row][sl] = src[row][slot_freq(sl, Q)]
+// the same into the float-float column passes' slot order:
+// dst[row][sl] = src[row][slot_freq_ff(sl, Q)]
 __global__ void k_split_ff2_slot(const double2* __restrict__ src, ffc* __restrict__ dst, long rows, int Q) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < rows * Q; i += (long)gridDim.x * blockDim.x) {
         const long row = i / Q;
         const int sl = (int)(i % Q);
-        dst[i] = to_ffc(src[row * Q + slot_freq(sl, Q)]);
+        dst[i] = to_ffc(src[row * Q + slot_freq_ff(sl, Q)]);
     }
 }
 __global__ void k_split_ff(const double* __restrict__ src, ff* __restrict__ dst, long n) {

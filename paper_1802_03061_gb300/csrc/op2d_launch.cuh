@@ -145,9 +145,13 @@ static cudaError_t dispatch_col_warp(int L, float2* Tb, float2* Tz, const TS* Sp
 // row passes take Q <= 512
 static inline bool col_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024; }
 static inline bool row_warp_ok(int Q) { return Q == 64 || Q == 128 || Q == 256 || Q == 512 || Q == 1024; }
-// shared memory of the Q = 1024 row kernels: 512-point twiddles, 8 lines of
-// Q + 2, 8 warp FFT scratches
-static inline size_t row_warp2_smem() { return (size_t)(512 + 8 * (1024 + 2) + 8 * wfft_shape<16>::SCRATCH) * sizeof(float2); }
+// shared memory of the two-residue row kernels (Q = 64 R): QW-point
+// twiddles, 8 lines of Q + 2, 8 warp FFT scratches
+template <typename T, int R> static inline size_t row_warp2_smem() {
+    return (size_t)(32 * R + 8 * (64 * R + 2) + 8 * wfft_shape<R>::SCRATCH) * sizeof(T);
+}
+// float-float forward row pass at Q = 512 as two 256-point residues
+static inline bool row_ff2_ok(int Q) { return Q == 512; }
 
 template <typename T, typename TS>
 static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, ColParams cp, bool split,
@@ -167,22 +171,24 @@ static cudaError_t dispatch_col(int L, T* Tb, T* Ts, const TS* S, const T* tw, C
 }
 
 // float-float column pass with the warp-register FFT: forward FFT of the
-// input channels' lines, pointwise mode mix on the slot-ordered spectra,
-// inverse FFT of all channels' lines (3 launches)
+// input channels' lines, pointwise mode mix on the slot-ordered spectra
+// (slot_freq_ff: Q = 512 and 1024 as two half-length residues), inverse FFT
+// of all channels' lines (3 launches)
 static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw, const ColParams& cp,
                            cudaStream_t s) {
     const int lin = cp.nin * cp.H, lout = (2 * L + 1) * cp.H;
     const unsigned gin = (unsigned)((lin + 7) / 8), gout = (unsigned)((lout + 7) / 8);
-    // twiddles + 8 FFT scratches (Q = 1024: those of the 512-point residues)
-    const int QW = cp.Q > 512 ? 512 : cp.Q;
+    // twiddles + 8 FFT scratches (Q = 512, 1024: those of the half-length residues)
+    const int QW = cp.Q >= 512 ? cp.Q / 2 : cp.Q;
     const size_t sm = (size_t)(QW + 8 * (QW + 32)) * sizeof(ffc);
     static bool once = false;
     cudaError_t e;
     if (!once) {
         if ((e = allow_smem(k_colw_fwd<2>)) != cudaSuccess || (e = allow_smem(k_colw_fwd<4>)) != cudaSuccess ||
-            (e = allow_smem(k_colw_fwd<8>)) != cudaSuccess || (e = allow_smem(k_colw_fwd<16>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_fwd<8>)) != cudaSuccess ||
             (e = allow_smem(k_colw_inv<2>)) != cudaSuccess || (e = allow_smem(k_colw_inv<4>)) != cudaSuccess ||
-            (e = allow_smem(k_colw_inv<8>)) != cudaSuccess || (e = allow_smem(k_colw_inv<16>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_inv<8>)) != cudaSuccess ||
+            (e = allow_smem(k_colw_fwd2<8>)) != cudaSuccess || (e = allow_smem(k_colw_inv2<8>)) != cudaSuccess ||
             (e = allow_smem(k_colw_fwd2<16>)) != cudaSuccess || (e = allow_smem(k_colw_inv2<16>)) != cudaSuccess)
             return e;
         once = true;
@@ -191,7 +197,7 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
         case 64: k_colw_fwd<2><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         case 128: k_colw_fwd<4><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         case 256: k_colw_fwd<8><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
-        case 512: k_colw_fwd<16><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
+        case 512: k_colw_fwd2<8><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         case 1024: k_colw_fwd2<16><<<gin, 256, sm, s>>>(Tb, Ts, tw, cp.n, lin); break;
         default: return cudaErrorInvalidValue;
     }
@@ -202,7 +208,7 @@ static cudaError_t colw_ff(int L, ffc* Tb, ffc* Ts, const ffc* Sp, const ffc* tw
         case 64: k_colw_inv<2><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
         case 128: k_colw_inv<4><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
         case 256: k_colw_inv<8><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
-        case 512: k_colw_inv<16><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
+        case 512: k_colw_inv2<8><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
         case 1024: k_colw_inv2<16><<<gout, 256, sm, s>>>(Tb, Ts, tw, cp.n, lout); break;
     }
     return cudaGetLastError();
@@ -241,10 +247,10 @@ static cudaError_t row_fwd_warp(int Q, dim3 grid, const TF* x, const double* f, 
             if constexpr (std::is_same<T, float2>::value && std::is_same<TF, float2>::value) {
                 static bool once2 = false;
                 if (!once2) {
-                    if ((e = allow_smem(k_row_fwd_warp2<16>)) != cudaSuccess) return e;
+                    if ((e = allow_smem(k_row_fwd_warp2<16, float2, float2>)) != cudaSuccess) return e;
                     once2 = true;
                 }
-                k_row_fwd_warp2<16><<<grid, 256, row_warp2_smem(), s>>>(x, f, out, tw, rp);
+                k_row_fwd_warp2<16, float2, float2><<<grid, 256, row_warp2_smem<float2, 16>(), s>>>(x, f, out, tw, rp);
                 break;
             }
             return cudaErrorInvalidValue;
@@ -303,16 +309,33 @@ static cudaError_t row_inv_warp(int Q, dim3 grid, const T* in, const TF* x, cons
             if constexpr (std::is_same<T, float2>::value && std::is_same<TF, float2>::value) {
                 static bool once2 = false;
                 if (!once2) {
-                    if ((e = allow_smem(k_row_inv_warp2<16>)) != cudaSuccess) return e;
+                    if ((e = allow_smem(k_row_inv_warp2<16, float2, float2>)) != cudaSuccess) return e;
                     once2 = true;
                 }
-                k_row_inv_warp2<16><<<grid, 256, row_warp2_smem(), s>>>(in, x, z, out, tw, rp, a, b, c);
+                k_row_inv_warp2<16, float2, float2><<<grid, 256, row_warp2_smem<float2, 16>(), s>>>(in, x, z, out, tw, rp, a, b, c);
                 break;
             }
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// float-float forward row pass at Q = 512 as two 256-point residues (R = 8).
+// The inverse stays on the shared-memory pass: as two residues (107
+// registers, its epilogue's x loads after the transforms) it measured 41.1 us
+// against 38.9 us at 256^2, L = 8; the forward 28.6 against 35.3 us.
+template <typename T, typename TF>
+static cudaError_t row_fwd_res(dim3 grid, const TF* x, const double* f, T* out, const T* tw, const RowParams& rp,
+                               cudaStream_t s) {
+    static bool once = false;
+    cudaError_t e;
+    if (!once) {
+        if ((e = allow_smem(k_row_fwd_warp2<8, T, TF>)) != cudaSuccess) return e;
+        once = true;
+    }
+    k_row_fwd_warp2<8, T, TF><<<grid, 256, row_warp2_smem<T, 8>(), s>>>(x, f, out, tw, rp);
     return cudaGetLastError();
 }
 
@@ -388,14 +411,23 @@ static cudaError_t op2d_run(rte_plan p, MixKind kind, const TF* x, const double*
     }
     const int nmod_in = use_x ? p->L + 1 : 1;
     const size_t smr = row_smem<T>(p->Q, rp.RB);
-    bool row_warp = false;
+    bool row_warp = false, row_res = false;
     if constexpr (row_warp_types<T, TF>::value) row_warp = row_warp_ok(p->Q) && p->rb_force < 2;
+    constexpr bool ffrows = std::is_same<T, ffc>::value && std::is_same<TF, double2>::value;
+    if constexpr (ffrows) row_res = row_ff2_ok(p->Q) && p->rb_force < 2;
     if (stage < 0 || stage == 0) {
         if (row_warp) {
             if constexpr (row_warp_types<T, TF>::value) {
                 const dim3 grid((p->n + 7) / 8, nmod_in);
                 if ((e = row_fwd_warp<T, TF>(p->Q, grid, use_x ? x : nullptr, use_f ? f : nullptr,
                                              Tb, tw, rp, s)) != cudaSuccess)
+                    return e;
+            }
+        } else if (row_res) {
+            if constexpr (ffrows) {
+                const dim3 grid((p->n + 7) / 8, nmod_in);
+                if ((e = row_fwd_res<T, TF>(grid, use_x ? x : nullptr, use_f ? f : nullptr, Tb, tw, rp, s)) !=
+                    cudaSuccess)
                     return e;
             }
         } else {

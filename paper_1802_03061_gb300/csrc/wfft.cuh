@@ -150,14 +150,25 @@ template <int R> __device__ __forceinline__ int wfreq(int j, int lane) { return 
 // the same with R known at run time (plan-time permutations)
 __device__ __forceinline__ int wfreq_rt(int R, int j, int lane) { return wfreq_map(R, j, lane); }
 
+// frequency of slot sl of a spectrum held as two warp FFTs of length QW =
+// Q / 2 (residues r = xi mod 2): slot r * QW + s holds xi = 2 wfreq_QW(s) + r
+__device__ __forceinline__ int slot_freq_res(int sl, int QW) {
+    const int r = sl / QW, s = sl % QW;
+    return 2 * wfreq_rt(QW / 32, s >> 5, s & 31) + r;
+}
 // frequency of slot sl (= j * 32 + lane) of the column passes' spectra.
 // Q <= 512: the warp FFT's own order.  Q = 1024 runs as two 512-point warp
-// FFTs (residues r = xi mod 2, see k_col_warp2): slot r * 512 + s holds
-// xi = 2 wfreq_512(s) + r.
+// FFTs (residues, see k_col_warp2).
 __device__ __forceinline__ int slot_freq(int sl, int Q) {
     if (Q <= 512) return wfreq_rt(Q / 32, sl >> 5, sl & 31);
-    const int r = sl >> 9, s = sl & 511;
-    return 2 * wfreq_rt(16, s >> 5, s & 31) + r;
+    return slot_freq_res(sl, 512);
+}
+// the same for the float-float column passes, which run Q = 512 as two
+// 256-point residues as well (a one-warp 512-point float-float line needs
+// too many registers)
+__device__ __forceinline__ int slot_freq_ff(int sl, int Q) {
+    if (Q < 512) return wfreq_rt(Q / 32, sl >> 5, sl & 31);
+    return slot_freq_res(sl, Q / 2);
 }
 
 // P-point DFT (P = 2, 4) in registers

@@ -63,14 +63,17 @@ def test_apply_K_fp64_matches_direct_sum(n, L, mu_t, mu_s, g):
     p.close()
 
 
+@pytest.mark.parametrize("q", [512, 1024])
 @pytest.mark.parametrize("n,L", [(20, 8), (33, 2), (7, 0), (40, 4)])
-def test_float_float_and_fp32_operators_at_q1024(n, L):
-    """Q = 1024 (two 512-point residues per column in the float-float column
-    pass): K64e and the native FP64 K to 1e-12 against the direct sum (K32 at
-    Q = 1024 is covered by test_apply_K32)."""
+def test_float_float_and_fp64_operators_at_residue_lengths(n, L, q):
+    """Q = 512 and 1024, where the float-float row and column passes run as
+    two half-length warp FFTs (residues xi mod 2; the forward row pass only at
+    512):
+    K64e, the float-float right-hand side and the native FP64 K to 1e-12
+    against the direct sum (K32 at these Q is covered by test_apply_K32)."""
     sig = rte_synth.hg_sigma_hat(0.5, L)
-    p = _plan(n, 10.0, 9.0, sig, q_policy=1024)
-    assert p.Q == 1024
+    p = _plan(n, 10.0, 9.0, sig, q_policy=q)
+    assert p.Q == q
     rng = np.random.default_rng(300 + n)
     x = random_packed(rng, L, n)
     ref = oracle.apply_K_2d(n, 1.0 / n, 10.0, 9.0, sig, packed_to_full(x))
@@ -78,6 +81,9 @@ def test_float_float_and_fp32_operators_at_q1024(n, L):
     assert rel(ye, ref[L:]) < 1e-12
     y = p.apply_K(torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(y, ref[L:]) < 1e-12
+    f = rte_synth.gaussian_mixture_2d(n, [(0.4, 0.6), (0.7, 0.3)], [0.1, 0.05])
+    b = p.rhs(torch.from_numpy(f)).cpu().numpy()
+    assert rel(b, oracle.rhs_2d(n, 1.0 / n, 10.0, L, f)[L:]) < 1e-12
     p.close()
 
 
@@ -228,8 +234,8 @@ def _wnorm(v):
     return float(np.sqrt(np.sum(w * np.sum(np.abs(v.reshape(v.shape[0], -1)) ** 2, axis=1))))
 
 
-@pytest.mark.parametrize("prec,q", [("mixed_fp32", 0), ("mixed_bf16", 0), ("mixed_fp32", 72), ("mixed_fp32", 1024),
-                                    ("mixed_bf16", 1024)])
+@pytest.mark.parametrize("prec,q", [("mixed_fp32", 0), ("mixed_bf16", 0), ("mixed_fp32", 72), ("mixed_fp32", 512),
+                                    ("mixed_fp32", 1024), ("mixed_bf16", 1024)])
 def test_mixed_residual_equals_unfused_residual(prec, q):
     """The mixed solve forms every residual as K~(mu_s sigma_hat u + g) - u in
     one float-float application and b in FP32 only.  The residual rebuilt from
