@@ -376,8 +376,8 @@ MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4752128 + 26899456 + 1
 
 # the same for the five FP32 passes of the 128^3 application
 # (profiles/passes_iso3d_diffusion_128.md)
-ISO3D_NCU = {"dram_bytes": 8405248 + 16922880 + 42420224 + 33831168 + 25313280,
-             "insts": 7311360 + 10253952 + 23678208 + 10419072 + 7116800}
+ISO3D_NCU = {"dram_bytes": 8405248 + 16923904 + 42427648 + 33833472 + 25313792,
+             "insts": 7467008 + 10782336 + 26485248 + 10831872 + 7068672}
 
 
 def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):

@@ -220,6 +220,33 @@ template <int R, typename T> __device__ __forceinline__ void warp_first_regs_inv
     __syncwarp();
 }
 
+// twiddle multiply v[k] *= W^k (DIR = -1) or conj(W)^k (DIR = +1),
+// W = exp(-2 pi i base / Q), k = 1..R-1 (base = lane in step 1, b R in step 2;
+// base (R - 1) < Q either way).  FP32 with R <= 8 reads W, W^2, W^4
+// from the table and forms W^3, W^5, W^6, W^7 as products of two of them (one
+// rounding each, next to the FFT's own log2 Q roundings): the 3D passes issue
+// from shared memory (transposes and twiddle reads), so fewer reads pay more
+// than the extra multiplies.  R = 16 (the register-heavy 2D passes) and the
+// float-float types read every power from the table, each just before use.
+template <int R, int DIR, typename T> __device__ __forceinline__ void lane_twiddle_mul(T* v, const T* tw, int base) {
+    if constexpr (sizeof(T) == 8 && R <= 8) {
+        T W[R];
+#pragma unroll
+        for (int k = 1; k < R; k <<= 1) W[k] = tw[base * k];
+#pragma unroll
+        for (int k = 3; k < R; ++k) {
+            if ((k & (k - 1)) == 0) continue;
+            const int hb = k >= 4 ? 4 : 2;  // highest power of two in k (k < 8)
+            W[k] = cmul(W[hb], W[k - hb]);
+        }
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], DIR < 0 ? W[k] : cconj(W[k]));
+    } else {
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twid<DIR>(tw, base * k));
+    }
+}
+
 // forward: v[r] = x[lane + 32 r]  ->  v[j] = X[wfreq<R>(j, lane)]
 // tw: table exp(-2 pi i t / Q); S: this warp's scratch (wfft_shape<R>::SCRATCH
 // elements of shared memory), free again when the call returns
@@ -227,8 +254,7 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, 
     using W = wfft_shape<R>;
     const int lane = threadIdx.x & 31;
     dft_regs<R, -1>(v);
-#pragma unroll
-    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<-1>(tw, lane * k1));
+    lane_twiddle_mul<R, -1>(v, tw, lane);
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) S[k1 * W::ST + lane] = v[k1];
     __syncwarp();
@@ -237,8 +263,7 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_fwd(T* v, 
     for (int m = 0; m < R; ++m) v[m] = S[g * W::ST + W::P * m + b];
     __syncwarp();
     dft_regs<R, -1>(v);
-#pragma unroll
-    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], twid<-1>(tw, b * j * R));
+    lane_twiddle_mul<R, -1>(v, tw, b * R);
     if constexpr (R >= W::P) {
         warp_last_regs<R, -1>(v, S, lane);
     } else {
@@ -260,8 +285,7 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, 
         for (int h = 1; h <= W::P / 2; h <<= 1) lane_stage_inv<R>(v, tw, h, lane);
     }
     const int g = lane >> W::LP, b = lane & (W::P - 1);
-#pragma unroll
-    for (int j = 1; j < R; ++j) v[j] = cmul(v[j], twid<1>(tw, b * j * R));
+    lane_twiddle_mul<R, 1>(v, tw, b * R);
     dft_regs<R, 1>(v);
 #pragma unroll
     for (int m = 0; m < R; ++m) S[g * W::ST + W::P * m + b] = v[m];
@@ -269,7 +293,6 @@ template <int R, typename T> __device__ __forceinline__ void warp_fft_inv(T* v, 
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) v[k1] = S[k1 * W::ST + lane];
     __syncwarp();
-#pragma unroll
-    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], twid<1>(tw, lane * k1));
+    lane_twiddle_mul<R, 1>(v, tw, lane);
     dft_regs<R, 1>(v);
 }
