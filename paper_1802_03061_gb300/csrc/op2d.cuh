@@ -184,6 +184,51 @@ __global__ void __launch_bounds__(256) k_row_inv(const T* __restrict__ in, const
     }
 }
 
+// The inverse warp row passes' first step: the half spectra of the block's 8
+// lines (mode k, rows from y0) into the line buffer Z as full spectra,
+// Z(xi) = F(xi) + i G(xi), Z(Q - xi) = conj F(xi) + i conj G(xi).  H = Q/2 + 1
+// is fixed by R, so each thread's trip count is a compile-time constant: all
+// of its loads are issued before the first write to Z and their latencies
+// overlap (a loop with a run-time bound waited for each load in turn).
+// Block of 256 threads; line stride LS = Q + 34.
+template <int R, typename T>
+__device__ __forceinline__ void rebuild_lines(const T* __restrict__ in, T* __restrict__ Z, int k, int y0, int n,
+                                              int H) {
+    constexpr int Q = 32 * R, LS = Q + 34, HH = Q / 2 + 1, NT = 256;
+    constexpr int IT = (HH * 8 + NT - 1) / NT;
+    T F[IT], G[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int idx = threadIdx.x + it * NT;
+        const int li = idx & 7, xi = idx >> 3;
+        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
+        if (idx < HH * 8) {
+            if (k == 0) {
+                const int ya = y0 + 2 * li, yb = ya + 1;
+                if (ya < n) Fv = in[(long)xi * n + ya];
+                if (yb < n) Gv = in[(long)xi * n + yb];
+            } else {
+                const int y = y0 + li;
+                if (y < n) {
+                    Fv = in[((long)chA(k) * H + xi) * n + y];
+                    Gv = in[((long)chB(k) * H + xi) * n + y];
+                }
+            }
+        }
+        F[it] = Fv;
+        G[it] = Gv;
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int idx = threadIdx.x + it * NT;
+        if (idx >= HH * 8) continue;
+        const int li = idx & 7, xi = idx >> 3;
+        const T Fv = F[it], Gv = G[it];
+        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 1w/3w. row passes with the warp FFT (Q = 32 R; FP32 or float-float compute
 // T, field storage TF): one warp per line (a row of u_k, or two packed rows
@@ -266,7 +311,7 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp(const TF* __restrict__ x, 
 }
 
 template <int R, typename T, typename TF>
-__global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, const TF* __restrict__ x,
+__global__ void __launch_bounds__(256, 2) k_row_inv_warp(const T* __restrict__ in, const TF* __restrict__ x,
                                                       const TF* __restrict__ z, TF* __restrict__ out,
                                                       const T* __restrict__ tw, RowParams p,
                                                       typename real_of<T>::R a, typename real_of<T>::R b,
@@ -301,24 +346,7 @@ __global__ void __launch_bounds__(256) k_row_inv_warp(const T* __restrict__ in, 
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     pdl_wait();  // in: the column pass's output
     pdl_trigger();
-    // Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
-    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
-        const int li = idx & 7, xi = idx >> 3;
-        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
-        if (k == 0) {
-            const int ya = y0 + 2 * li, yb = ya + 1;
-            if (ya < n) Fv = in[(long)xi * n + ya];
-            if (yb < n) Gv = in[(long)xi * n + yb];
-        } else {
-            const int y = y0 + li;
-            if (y < n) {
-                Fv = in[((long)chA(k) * H + xi) * n + y];
-                Gv = in[((long)chB(k) * H + xi) * n + y];
-            }
-        }
-        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
-    }
+    rebuild_lines<R, T>(in, Z, k, y0, n, H);
     __syncthreads();
     T v[R];
 #pragma unroll
@@ -556,23 +584,7 @@ __global__ void __launch_bounds__(256) k_row_invfwd_warp(float2* __restrict__ Tb
     pdl_wait();  // Tb: the column pass's output
     pdl_trigger();
     // M: Z(xi) = F(xi) + i G(xi); Z(Q-xi) = conj F(xi) + i conj G(xi)
-    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
-        const int li = idx & 7, xi = idx >> 3;
-        float2 Fv = make_float2(0.f, 0.f), Gv = make_float2(0.f, 0.f);
-        if (k == 0) {
-            const int ya = y0 + 2 * li, yb = ya + 1;
-            if (ya < n) Fv = Tb[(long)xi * n + ya];
-            if (yb < n) Gv = Tb[(long)xi * n + yb];
-        } else {
-            const int y = y0 + li;
-            if (y < n) {
-                Fv = Tb[((long)chA(k) * H + xi) * n + y];
-                Gv = Tb[((long)chB(k) * H + xi) * n + y];
-            }
-        }
-        Z[li * LS + swz16(xi)] = make_float2(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = make_float2(Fv.x + Gv.y, Gv.x - Fv.y);
-    }
+    rebuild_lines<R, float2>(Tb, Z, k, y0, n, H);
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2 v[R];

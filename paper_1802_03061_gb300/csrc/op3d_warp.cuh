@@ -154,9 +154,23 @@ __global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __
     pdl_wait();  // T2: the z pass's output
     pdl_trigger();
     const int nz = min(16, n - z0);
-    for (int idx = threadIdx.x; idx < Q * 16; idx += blockDim.x) {
-        const int zl = idx & 15, sl = idx >> 4;
-        Y[sl * ZS + zl] = zl < nz ? T2[((long)kx * Q + sl) * n + z0 + zl] : mk<T>(0, 0);
+    // Q * 16 / 512 = RQ elements per thread, in groups of four whose loads
+    // are all issued before their writes to the tile
+    constexpr int IT = Q * 16 / 512, GR = IT < 4 ? IT : 4;
+#pragma unroll
+    for (int g0 = 0; g0 < IT; g0 += GR) {
+        T vv[GR];
+#pragma unroll
+        for (int g = 0; g < GR; ++g) {
+            const int idx = threadIdx.x + (g0 + g) * 512;
+            const int zl = idx & 15, sl = idx >> 4;
+            vv[g] = zl < nz ? T2[((long)kx * Q + sl) * n + z0 + zl] : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int g = 0; g < GR; ++g) {
+            const int idx = threadIdx.x + (g0 + g) * 512;
+            Y[(idx >> 4) * ZS + (idx & 15)] = vv[g];
+        }
     }
     __syncthreads();
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -207,14 +221,33 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
     for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
     pdl_wait();  // T1: the y' pass's output
     pdl_trigger();
-    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
-        const int li = idx & 7, xi = idx >> 3;
-        const int la = y0 + 2 * li, lb = la + 1;
-        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
-        if (la < n) Fv = T1[((long)z * H + xi) * n + la];
-        if (lb < n) Gv = T1[((long)z * H + xi) * n + lb];
-        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+    {
+        // H = Q/2 + 1 is fixed by RQ: every load of this thread is issued
+        // before its first write to Z, so their latencies overlap
+        constexpr int HH = Q / 2 + 1, IT = (HH * 8 + 255) / 256;
+        T F[IT], G[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int idx = threadIdx.x + it * 256;
+            const int li = idx & 7, xi = idx >> 3;
+            const int la = y0 + 2 * li, lb = la + 1;
+            T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
+            if (idx < HH * 8) {
+                if (la < n) Fv = T1[((long)z * H + xi) * n + la];
+                if (lb < n) Gv = T1[((long)z * H + xi) * n + lb];
+            }
+            F[it] = Fv;
+            G[it] = Gv;
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int idx = threadIdx.x + it * 256;
+            if (idx >= HH * 8) continue;
+            const int li = idx & 7, xi = idx >> 3;
+            const T Fv = F[it], Gv = G[it];
+            Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+            if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+        }
     }
     __syncthreads();
     T v[RQ];
