@@ -369,15 +369,15 @@ def run_native(args):
 # from the ncu capture summarised in profiles/matvec_hg2d_transport_256_L8.md.
 # Valid only for the kernel versions that capture measured and for this shape
 # and precision (the roofline reports null otherwise).
-MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4752128 + 26899456 + 13698048,
-                                            "insts": 3638544 + 9587385 + 3485360,
+MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4752128 + 26899456 + 13704704,
+                                            "insts": 3638544 + 9587385 + 3342608,
                                             "col_dram_bytes": 26899456, "col_insts": 9587385}}
 
 
 # the same for the five FP32 passes of the 128^3 application
 # (profiles/passes_iso3d_diffusion_128.md)
-ISO3D_NCU = {"dram_bytes": 8405248 + 16923904 + 42427648 + 33833472 + 25313792,
-             "insts": 7467008 + 10782336 + 26485248 + 10831872 + 7068672}
+ISO3D_NCU = {"dram_bytes": 8405248 + 16925440 + 42423808 + 33832704 + 25315840,
+             "insts": 7467008 + 10782336 + 26485248 + 9494400 + 6817792}
 
 
 def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):
@@ -428,7 +428,7 @@ def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):
               "does inside the solve" % (b_alg / 1e6),
         "launch": "stream launches with programmatic dependent launch (a pass's prologue overlaps its "
                   "predecessor's tail); inside the captured solve graph the same kernels launch without it "
-                  "(measured faster there), about 41 us per application at this size",
+                  "(measured faster there)",
     }
 
 
