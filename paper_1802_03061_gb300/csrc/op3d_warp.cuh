@@ -28,10 +28,9 @@ __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __
     T1 += (long)ch * n * H * n;
     if (wz) w = wz[ch];
     if (ch > 0) xf = nullptr;  // the source joins channel 0 only
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    stage_twiddles<Q, 256>(twl, tw);
     pdl_wait();  // x may be the predecessor's output
     pdl_trigger();
-    __syncthreads();
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RR ww = (RR)w;
     const int ya = y0 + 2 * wp, yb = ya + 1;
@@ -50,6 +49,7 @@ __global__ void __launch_bounds__(256) k3w_x_fwd(const RI* __restrict__ x, T* __
         }
         v[r] = mk<T>(a, b);
     }
+    __syncthreads();  // the twiddles are staged (the loads above overlap the barrier)
     warp_fft_fwd<RQ>(v, twl, Z + wp * LS);
 #pragma unroll
     for (int j = 0; j < RQ; ++j) Z[wp * LS + swz16(wfreq<RQ>(j, lane))] = v[j];
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(512) k3w_y_fwd(const T* __restrict__ T1, T* __
     const int kx = blockIdx.y, z0 = blockIdx.x * 16, ch = blockIdx.z;
     T1 += (long)ch * n * H * n;
     T2 += (long)ch * H * Q * n;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    stage_twiddles<Q, 512>(twl, tw);
     pdl_wait();  // T1: the x pass's output
     pdl_trigger();
     __syncthreads();
@@ -111,18 +111,18 @@ __global__ void __launch_bounds__(256) k3w_z_mix(T* __restrict__ T2, const TS* _
     T* twl = reinterpret_cast<T*>(smraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* scr = twl + Q + warp * wfft_shape<RQ>::SCRATCH;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    stage_twiddles<Q, 256>(twl, tw);
     pdl_wait();  // T2: the y pass's output
     pdl_trigger();
-    __syncthreads();
     const long line = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (line >= nlines) return;
     T v[RQ];
 #pragma unroll
     for (int r = 0; r < RQ; ++r) {
         const int z = lane + 32 * r;
-        v[r] = z < n ? T2[line * n + z] : mk<T>(0, 0);
+        v[r] = (line < nlines && z < n) ? T2[line * n + z] : mk<T>(0, 0);
     }
+    __syncthreads();  // the twiddles are staged (the loads above overlap the barrier)
+    if (line >= nlines) return;
     warp_fft_fwd<RQ>(v, twl, scr);
     const int kx = (int)(line / Q), sl = (int)(line % Q);
     const int ky = wfreq<RQ>(sl >> 5, sl & 31);  // slot -> frequency
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(512) k3w_y_inv(const T* __restrict__ T2, T* __
     const int kx = blockIdx.y, z0 = blockIdx.x * 16, ch = blockIdx.z;
     T1 += (long)ch * n * H * n;
     T2 += (long)ch * H * Q * n;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    stage_twiddles<Q, 512>(twl, tw);
     pdl_wait();  // T2: the z pass's output
     pdl_trigger();
     const int nz = min(16, n - z0);
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k3w_x_inv(const T* __restrict__ T1, const
         pxa[r] = (x && e < n && ya < n) ? x[((long)z * n + ya) * n + e] : (RI)0;
         pxb[r] = (x && e < n && yb < n) ? x[((long)z * n + yb) * n + e] : (RI)0;
     }
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) twl[i] = tw[i];
+    stage_twiddles<Q, 256>(twl, tw);
     pdl_wait();  // T1: the y' pass's output
     pdl_trigger();
     {

@@ -21,6 +21,25 @@
 #pragma once
 #include "fft.cuh"
 
+// the Q-entry twiddle table into shared memory by a block of NT threads: the
+// trip count is a compile-time constant, so a thread's loads are all issued
+// before its stores (a loop over blockDim.x waits for each load in turn)
+template <int Q, int NT, typename T>
+__device__ __forceinline__ void stage_twiddles(T* __restrict__ sm, const T* __restrict__ g) {
+    constexpr int IT = (Q + NT - 1) / NT;
+    T t[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (i < Q) t[it] = g[i];
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int i = threadIdx.x + it * NT;
+        if (i < Q) sm[i] = t[it];
+    }
+}
+
 // bank swizzle of a line of Q (a multiple of 16) complex values in shared
 // memory: xi -> xi ^ ((xi >> 4) & 15) stays inside its aligned group of 16,
 // so it is a bijection; it spreads the frequencies that the 32 lanes of a
