@@ -376,8 +376,8 @@ MATVEC_NCU = {(256, 8, 512, "mixed_fp32"): {"dram_bytes": 4752128 + 26899456 + 1
 
 # the same for the five FP32 passes of the 128^3 application
 # (profiles/passes_iso3d_diffusion_128.md)
-ISO3D_NCU = {"dram_bytes": 8405248 + 16925440 + 42423808 + 33832704 + 25315840,
-             "insts": 7467008 + 10782336 + 26485248 + 9494400 + 6817792}
+ISO3D_NCU = {"dram_bytes": 8404480 + 16922880 + 42422272 + 33831936 + 25314304,
+             "insts": 7188480 + 10369536 + 24437760 + 9114624 + 6428672}
 
 
 def matvec_roofline(prec, n, L, Q, ms, hbm_peak, peak_src, sm_mhz):
