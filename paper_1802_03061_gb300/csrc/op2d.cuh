@@ -394,6 +394,37 @@ __global__ void __launch_bounds__(256, 2) k_row_inv_warp(const T* __restrict__ i
 // separate FFT scratch.  tw: the plan's Q-point table (compute type T, field
 // storage TF).
 // grid (ceil(n / 8), modes), block 256; rows per block 8 (k >= 1) or 16 (k = 0)
+// input register r of the two-residue forward row pass (weighted field of
+// mode k, the source joining mode 0 unweighted, two packed rows for k = 0)
+template <typename T, typename TF>
+__device__ __forceinline__ T row2_input(const TF* __restrict__ x, const double* __restrict__ f, int k, int y0,
+                                        int w, int e, int n, typename real_of<T>::R wt) {
+    using RR = typename real_of<T>::R;
+    T val = mk<T>(0, 0);
+    if (e < n) {
+        if (k == 0) {
+            const int ya = y0 + 2 * w, yb = ya + 1;
+            RR a = (RR)0, b = (RR)0;
+            if (x) {
+                if (ya < n) a = wt * to_c<T>(x[(long)ya * n + e]).x;
+                if (yb < n) b = wt * to_c<T>(x[(long)yb * n + e]).x;
+            }
+            if (f) {
+                if (ya < n) a = a + (RR)f[(long)ya * n + e];
+                if (yb < n) b = b + (RR)f[(long)yb * n + e];
+            }
+            val = mk<T>(a, b);
+        } else {
+            const int y = y0 + w;
+            if (y < n) {
+                const T uu = to_c<T>(x[((long)k * n + y) * n + e]);
+                val = mk<T>(wt * uu.x, wt * uu.y);
+            }
+        }
+    }
+    return val;
+}
+
 template <int R, typename T, typename TF>
 __global__ void __launch_bounds__(256) k_row_fwd_warp2(const TF* __restrict__ x, const double* __restrict__ f,
                                                        T* __restrict__ out, const T* __restrict__ tw,
@@ -414,40 +445,25 @@ __global__ void __launch_bounds__(256) k_row_fwd_warp2(const TF* __restrict__ x,
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RR wt = (RR)p.wk[k];
-    T u[R];
+    // FP32 (R = 16) loads its inputs again for the second residue (cache hits)
+    // rather than holding them across the first transform: 128 registers
+    // instead of 154, two blocks per SM.  Float-float keeps them (reloading
+    // its FP64 fields measured slower: 28.8 -> 35.0 us at Q = 512).
+    constexpr bool RELOAD = sizeof(T) == 8;
+    T u[RELOAD ? 1 : R];
+    if constexpr (!RELOAD) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = lane + 32 * r;
-        T val = mk<T>(0, 0);
-        if (e < n) {
-            if (k == 0) {
-                const int ya = y0 + 2 * w, yb = ya + 1;
-                RR a = (RR)0, b = (RR)0;
-                if (x) {
-                    if (ya < n) a = wt * to_c<T>(x[(long)ya * n + e]).x;
-                    if (yb < n) b = wt * to_c<T>(x[(long)yb * n + e]).x;
-                }
-                if (f) {
-                    if (ya < n) a = a + (RR)f[(long)ya * n + e];
-                    if (yb < n) b = b + (RR)f[(long)yb * n + e];
-                }
-                val = mk<T>(a, b);
-            } else {
-                const int y = y0 + w;
-                if (y < n) {
-                    const T uu = to_c<T>(x[((long)k * n + y) * n + e]);
-                    val = mk<T>(wt * uu.x, wt * uu.y);
-                }
-            }
-        }
-        u[r] = val;
+        for (int r = 0; r < R; ++r) u[r] = row2_input<T>(x, f, k, y0, w, lane + 32 * r, n, wt);
     }
     for (int rs = 0; rs < 2; ++rs) {
         T v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int e = lane + 32 * r;
-            v[r] = (rs && e < n) ? cmul(u[r], tw[e]) : u[r];
+            T val;
+            if constexpr (RELOAD) val = row2_input<T>(x, f, k, y0, w, e, n, wt);
+            else val = u[r];
+            v[r] = (rs && e < n) ? cmul(val, tw[e]) : val;
         }
         warp_fft_fwd<R>(v, twl, scr + w * SC);
 #pragma unroll
@@ -492,22 +508,42 @@ __global__ void __launch_bounds__(256) k_row_inv_warp2(const T* __restrict__ in,
     const int y0 = blockIdx.x * rows;
     if (y0 >= n) return;
     for (int i = threadIdx.x; i < QW; i += blockDim.x) twl[i] = tw[2 * i];
-    for (int idx = threadIdx.x; idx < H * 8; idx += blockDim.x) {
-        const int li = idx & 7, xi = idx >> 3;
-        T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
-        if (k == 0) {
-            const int ya = y0 + 2 * li, yb = ya + 1;
-            if (ya < n) Fv = in[(long)xi * n + ya];
-            if (yb < n) Gv = in[(long)xi * n + yb];
-        } else {
-            const int y = y0 + li;
-            if (y < n) {
-                Fv = in[((long)chA(k) * H + xi) * n + y];
-                Gv = in[((long)chB(k) * H + xi) * n + y];
+    // the half spectra in groups of four elements per thread whose loads are
+    // all issued before their writes to Z (H = Q/2 + 1 is fixed by R)
+    constexpr int HH = Q / 2 + 1, NT = 256, IT = (HH * 8 + NT - 1) / NT, CH = 4;
+#pragma unroll 1
+    for (int i0 = 0; i0 < IT; i0 += CH) {
+        T F[CH], G[CH];
+#pragma unroll
+        for (int g = 0; g < CH; ++g) {
+            const int idx = threadIdx.x + (i0 + g) * NT;
+            const int li = idx & 7, xi = idx >> 3;
+            T Fv = mk<T>(0, 0), Gv = mk<T>(0, 0);
+            if (idx < HH * 8) {
+                if (k == 0) {
+                    const int ya = y0 + 2 * li, yb = ya + 1;
+                    if (ya < n) Fv = in[(long)xi * n + ya];
+                    if (yb < n) Gv = in[(long)xi * n + yb];
+                } else {
+                    const int y = y0 + li;
+                    if (y < n) {
+                        Fv = in[((long)chA(k) * H + xi) * n + y];
+                        Gv = in[((long)chB(k) * H + xi) * n + y];
+                    }
+                }
             }
+            F[g] = Fv;
+            G[g] = Gv;
         }
-        Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
-        if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+#pragma unroll
+        for (int g = 0; g < CH; ++g) {
+            const int idx = threadIdx.x + (i0 + g) * NT;
+            if (idx >= HH * 8) continue;
+            const int li = idx & 7, xi = idx >> 3;
+            const T Fv = F[g], Gv = G[g];
+            Z[li * LS + swz16(xi)] = mk<T>(Fv.x - Gv.y, Fv.y + Gv.x);
+            if (xi > 0 && xi < Q - xi) Z[li * LS + swz16(Q - xi)] = mk<T>(Fv.x + Gv.y, Gv.x - Fv.y);
+        }
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
