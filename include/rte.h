@@ -221,7 +221,7 @@ rte_status rte_batch_create(rte_batch* out, int count, const rte_instance_desc* 
 /* Solve every instance: f[i] (device, n_i^2 doubles) is instance i's source
  * and u[i] (device, 2(L_i+1) n_i^2 doubles, the FP64 mode-field layout)
  * receives its solution; f and u are host arrays of `count` device pointers,
- * caller-owned (the survey's boundary form of the batched solve).  The
+ * caller-owned (one device buffer per instance).  The
  * sources are gathered into the batch's packed buffer by one kernel, the
  * graph runs, one kernel scatters the solutions.  stats_host (count entries,
  * may be NULL) receives each instance's statistics (ms_total = the graph

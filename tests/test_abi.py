@@ -19,7 +19,7 @@ def _declared():
     return names
 
 
-# the calls of the survey's boundary (plan, operators, solve, batch, learned guess)
+# the core calls of the boundary (plan, operators, solve, batch, learned guess)
 BOUNDARY = ("rte_plan_create", "rte_apply_K", "rte_apply_A", "rte_rhs", "rte_solve", "rte_destroy", "rte_status_str",
             "rte_batch_create", "rte_batch_solve", "rte_guess_load", "rte_guess_apply")
 
