@@ -195,3 +195,14 @@ def test_aniso3d_octant_storage_rebuilds_the_spectra():
             sgn = np.where((ky > Q // 2) & bool(oy), -1.0, 1.0) * np.where((kz > Q // 2) & bool(oz), -1.0, 1.0)
             rebuilt = sgn[None] * oct_[:, fy, fz]
             np.testing.assert_allclose(rebuilt, part[:H], atol=1e-13 * np.abs(G).max())
+
+
+def test_training_checkpoint_calls_reject_null_arguments_without_a_gpu(tmp_path):
+    """rte_cnn_save_state / rte_cnn_load_state check their handle and path
+    before any device call."""
+    from paper_1802_03061_gb300 import _binding as B
+    for fn, args in ((B.rte_cnn_save_state, (None, tmp_path / "c.bin")),
+                     (B.rte_cnn_load_state, (None, tmp_path / "c.bin"))):
+        with pytest.raises(B.RteError) as ei:
+            fn(*args)
+        assert ei.value.status == B.RTE_EINVAL
